@@ -1,0 +1,198 @@
+/*
+ * atc.h -- C ABI of the GB300 ST-HOSVD + bit-plane core compressor.
+ *
+ * The library computes the hot path of the ATC Tucker compressor (arXiv
+ * 2107.01384) on one NVIDIA GB300 (sm_103a):
+ *   ||X||^2 -> per mode: Gram SYRK -> FP64 eigensolve -> rank choice ->
+ *   projection TTM (Algorithm 1, Section 4.1) -> core storage order ->
+ *   scaling / rounding -> exact bit-plane tracking and breakpoint ->
+ *   run-length + rANS block encoding (Sections 3.3, 4.2, 4.3, supplement S.6),
+ * and the reverse for decompression.
+ *
+ * Conventions shared by every entry point
+ *  - Tensors are row-major with the LAST index fastest (lexicographic order,
+ *    supplement S.2).  For a mode k the tensor is viewed as (L, n_k, R) with
+ *    L = prod(dims[:k]) and R = prod(dims[k+1:]); no transpose is ever made.
+ *  - "_dev" pointers are CUDA device pointers of the current device, owned by
+ *    the caller unless stated otherwise; they are read or written, never freed.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All device work of a call is enqueued on it.  Calls that return host
+ *    values (ranks, streams, stats) synchronise that stream before returning.
+ *  - Return value: ATC_OK (0) or a negative ATC_E* code; nothing throws and
+ *    nothing aborts.  atc_last_error() gives a thread-local message for the
+ *    last failing call of the calling thread.
+ *  - Scratch device memory is allocated by the library with cudaMalloc and
+ *    cached per device (released by atc_release_workspace()).
+ */
+#ifndef ATC_H
+#define ATC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ATC_OK 0
+#define ATC_EINVAL (-1)   /* bad argument: null pointer, ndim not in [1,8], dim <= 0, rel_eps not in (0,1], rtmss not in [0,1], ... */
+#define ATC_ENOMEM (-2)   /* device or host allocation failed */
+#define ATC_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define ATC_ECORRUPT (-4) /* a compressed stream failed a magic / version / size / bounds check */
+#define ATC_EUNSUP (-5)   /* unsupported combination (e.g. tensor too large for a kernel) */
+#define ATC_ETIMEOUT (-6) /* a bounded device-side wait gave up; the results of the call are invalid */
+#define ATC_ENUMERIC (-7) /* NaN / Inf in the input or a non-converged eigensolve */
+
+typedef enum { ATC_F32 = 1, ATC_F64 = 2 } atc_dtype;
+
+/* Arithmetic of the Gram and projection contractions.  The eigensolve and the
+ * discarded-energy sums that choose ranks are FP64 in every mode. */
+typedef enum {
+  ATC_PREC_FP64 = 0,       /* plain FP64 SIMT contractions, FP64 intermediates */
+  ATC_PREC_SPLIT_BF16 = 1, /* x = hi + lo in bf16, 3 tcgen05 products, FP32 accumulate, FP64 split-K sum */
+  ATC_PREC_SPLIT_FP16 = 2  /* same with fp16 halves and a power-of-two pre-scale */
+} atc_precision;
+
+typedef enum {
+  ATC_RANK_STATIC = 0,   /* budget_k = rtmss * TargetSSE_total / d for every mode */
+  ATC_RANK_ADAPTIVE = 1  /* budget_k = (rtmss * TargetSSE_total - used) / (modes left) */
+} atc_rank_rule;
+
+typedef struct {
+  double rtmss;          /* Section 4.1.3 share of the error given to rank truncation; default 0.5 */
+  int precision;         /* atc_precision; default ATC_PREC_FP64 */
+  int rank_rule;         /* atc_rank_rule; default ATC_RANK_STATIC */
+  const int* mode_order; /* processing order (permutation of 0..ndim-1) or NULL = increasing length (Section 4.1.1) */
+  int block_size;        /* coefficients per encoder block (Section 4.2); multiple of 32 in [32, 65535]; default 4096 */
+  void* stream;          /* cudaStream_t or NULL */
+} atc_options;
+
+/* Fill *opt with the defaults listed above. */
+void atc_default_options(atc_options* opt);
+
+/* Per-call statistics (host values). */
+typedef struct {
+  double norm2;           /* ||X||^2 (FP64) */
+  double target_sse;      /* rel_eps^2 ||X||^2 */
+  double sse_trunc;       /* sum of discarded eigenvalues over the modes (Theorem 6.4 of the cited ST-HOSVD paper) */
+  double sse_quant_pred;  /* tracked core quantization error at the breakpoint (Section 4.3 reconstruction) */
+  int order[8];           /* processing order used */
+  int storage_order[8];   /* core mode storage order before vectorisation (supplement S.2) */
+  int k;                  /* quantization scale exponent: 2^63 <= 2^k max|b| < 2^64 */
+  int p_star;             /* breakpoint plane (64 = nothing encoded) */
+  int64_t i_star;         /* breakpoint coefficient: 0..i_star carry planes >= p_star, the rest >= p_star+1 */
+  int escalated_modes;    /* modes whose Gram was recomputed in FP64 by the precision check */
+  double ms_norm, ms_gram, ms_eig, ms_ttm, ms_quant, ms_encode, ms_total; /* device time per phase (CUDA events) */
+} atc_stats;
+
+typedef struct atc_compressed atc_compressed; /* opaque, library-owned until atc_free() */
+
+/*
+ * Compress a tensor resident in device memory (Figure 1 pipeline restricted to
+ * the core; factors are stored as raw float64).
+ *   x_dev   : device pointer to prod(dims) elements of `dtype`, row-major; read only.
+ *   dims    : host array of ndim positive sizes, 1 <= ndim <= 8.
+ *   rel_eps : target relative error ||X - X_hat|| / ||X|| in (0, 1].
+ *   opt     : NULL for defaults.
+ *   out     : receives a handle (core, factors, ranks, stream, stats).
+ * Errors: ATC_EINVAL, ATC_ENOMEM, ATC_ECUDA, ATC_ETIMEOUT, ATC_ENUMERIC.
+ */
+int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, double rel_eps,
+                 const atc_options* opt, atc_compressed** out);
+
+/* ranks[ndim] (host) <- the multilinear rank chosen per mode (original mode index). */
+int atc_get_ranks(const atc_compressed* c, int64_t* ranks);
+/* *core_dev <- borrowed device pointer to the FP64 core, modes in their original
+ * positions, shape (r_1..r_d), row-major.  Valid until atc_free(c). */
+int atc_get_core(const atc_compressed* c, const double** core_dev);
+/* *u_dev <- borrowed device pointer to factor U_mode, FP64 (n_mode x r_mode) row-major. */
+int atc_get_factor(const atc_compressed* c, int mode, const double** u_dev);
+/* *bytes <- borrowed HOST pointer to the compressed stream ("ATC1"), *nbytes its size. */
+int atc_get_stream(const atc_compressed* c, const uint8_t** bytes, size_t* nbytes);
+int atc_get_stats(const atc_compressed* c, atc_stats* stats);
+void atc_free(atc_compressed* c);
+
+/* Read ndim, dims (<= 8 entries) and dtype from a stream header (host only). */
+int atc_peek_dims(const uint8_t* stream, size_t nbytes, int* ndim, int64_t* dims, int* dtype);
+
+/*
+ * Decompress a host stream into out_dev (device, prod(dims) elements of
+ * out_dtype): decode + dequantize the core (Section 4.3 reconstruction), then
+ * X_hat = B~ x_1 U_1 ... x_d U_d in the order minimising the operation count
+ * (Section 4.1.1).  The expansion runs in FP64.
+ * Errors: ATC_EINVAL, ATC_ECORRUPT, ATC_ENOMEM, ATC_ECUDA.
+ */
+int atc_decompress(const uint8_t* stream, size_t nbytes, void* out_dev, int out_dtype, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Step entry points: one per stage of the hot path, for parity tests and
+ * for callers that drive the loop themselves.  All sizes are element counts.
+ * ------------------------------------------------------------------------ */
+
+/* *out_dev (device, 1 double) <- sum x_i^2 in FP64 over n elements (Section 3.1 norm). */
+int atc_norm2(const void* x_dev, int64_t n, int dtype, double* out_dev, void* stream);
+
+/*
+ * Mode Gram matrix G = X_(k) X_(k)^T of the (L, n, R) view (Section 3.1
+ * unfolding, Algorithm 1 SVD step via Gram): G[i][j] = sum_{l,c} X[l][i][c] X[l][j][c].
+ *   x_dev : L*n*R elements of dtype (device).   g_dev : n*n doubles (device), full symmetric output.
+ *   precision : atc_precision.  n <= 1024 for the split paths.
+ */
+int atc_gram(const void* x_dev, int dtype, int64_t L, int64_t n, int64_t R, int precision,
+             double* g_dev, void* stream);
+
+/*
+ * Symmetric eigensolve in FP64 (Algorithm 1 SVD step; lambda = sigma^2):
+ *   g_dev   : n*n doubles (device, symmetric, read only).
+ *   lam_dev : n doubles (device) <- eigenvalues in descending order (not clamped).
+ *   v_dev   : n*nvec doubles (device, row-major n x nvec) <- eigenvectors of the
+ *             nvec largest eigenvalues, the entry of largest magnitude of each
+ *             column made positive; may be NULL when nvec == 0.
+ *   1 <= n <= 1024, 0 <= nvec <= n.
+ */
+int atc_eig_sym(const double* g_dev, int n, double* lam_dev, double* v_dev, int nvec, void* stream);
+
+/*
+ * Rank choice (Section 4.1.3 error budget): clamp lambda at 0, tail sums
+ * t[r] = sum_{j>=r} lambda_j accumulated from the smallest value, and
+ * r = min{r >= 1 : t[r] <= budget}.
+ *   lam_dev : n doubles (device, descending).  r_out / disc_out: host outputs
+ *   (r and t[r]).  Synchronises the stream.
+ */
+int atc_rank_select(const double* lam_dev, int n, double budget, int* r_out, double* disc_out, void* stream);
+
+/*
+ * Mode-k product on the (L, n, R) view.
+ *   project (expand == 0): y[l][j][c] = sum_i U[i][j] x[l][i][c],  y is (L, r, R)   (Algorithm 1 projection)
+ *   expand  (expand == 1): y[l][i][c] = sum_j U[i][j] x[l][j][c],  x is (L, r, R), y is (L, n, R)
+ *   u_dev : FP64 n x r row-major (device).
+ *   x dtype / y dtype: ATC_F32 or ATC_F64.  precision: atc_precision (the
+ *   split paths need n <= 1024, r <= 256 and write FP32 y).
+ */
+int atc_ttm(const void* x_dev, int xdtype, int64_t L, int64_t n, int64_t R, const double* u_dev, int64_t r,
+            int expand, int precision, void* y_dev, int ydtype, void* stream);
+
+/*
+ * Quantize and encode a vectorised FP64 core (Sections 3.3, 4.2, 4.3, S.6).
+ *   core_dev   : n doubles (device), already in storage order.
+ *   target_sse : quantization error budget in core units (may be <= 0: encode all).
+ *   *bytes     : receives a library-allocated HOST buffer (free with
+ *                atc_free_buffer) holding the "ATCQ" section, *nbytes its size.
+ *   info       : optional host int64[4] <- {k, p_star, i_star, 0}.
+ * The bytes are identical to the plain C reference for the same core and target.
+ */
+int atc_quantize_core(const double* core_dev, int64_t n, double target_sse, int block_size, void* stream,
+                      uint8_t** bytes, size_t* nbytes, int64_t* info);
+
+/* Decode an "ATCQ" section (host bytes) into n dequantized doubles (device). */
+int atc_dequantize_core(const uint8_t* bytes, size_t nbytes, double* core_dev, int64_t n, void* stream);
+
+void atc_free_buffer(void* p);
+/* Free the cached device scratch of the current device. */
+int atc_release_workspace(void);
+const char* atc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ATC_H */

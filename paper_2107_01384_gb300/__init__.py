@@ -1,0 +1,259 @@
+"""Python binding of libatc (include/atc.h): ST-HOSVD + bit-plane core compression on GB300.
+
+Argument marshalling only: every step runs in the CUDA kernels of libatc.so.
+PyTorch supplies device memory and the current CUDA stream.  If the library is
+missing the import of any entry point fails loudly -- there is no fallback.
+
+Names follow the C ABI: atc_norm2, atc_gram, atc_eig_sym, atc_rank_select,
+atc_ttm, atc_quantize_core, atc_dequantize_core, atc_compress, atc_decompress,
+atc_peek_dims.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+__all__ = [
+    "ATC_F32", "ATC_F64", "PREC_FP64", "PREC_SPLIT_BF16", "PREC_SPLIT_FP16",
+    "RANK_STATIC", "RANK_ADAPTIVE", "AtcError", "lib", "lib_path",
+    "atc_norm2", "atc_gram", "atc_eig_sym", "atc_rank_select", "atc_ttm",
+    "atc_quantize_core", "atc_dequantize_core", "atc_compress", "atc_decompress",
+    "atc_peek_dims", "Compressed", "EXPORTS",
+]
+
+ATC_F32, ATC_F64 = 1, 2
+PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_FP16 = 0, 1, 2
+RANK_STATIC, RANK_ADAPTIVE = 0, 1
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(HERE, "libatc.so")
+
+# every symbol include/atc.h declares
+EXPORTS = [
+    "atc_default_options", "atc_compress", "atc_get_ranks", "atc_get_core", "atc_get_factor",
+    "atc_get_stream", "atc_get_stats", "atc_free", "atc_peek_dims", "atc_decompress", "atc_norm2",
+    "atc_gram", "atc_eig_sym", "atc_rank_select", "atc_ttm", "atc_quantize_core",
+    "atc_dequantize_core", "atc_free_buffer", "atc_release_workspace", "atc_last_error",
+]
+
+
+class AtcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libatc error {code}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("rtmss", C.c_double), ("precision", C.c_int), ("rank_rule", C.c_int),
+                ("mode_order", C.POINTER(C.c_int)), ("block_size", C.c_int), ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("norm2", C.c_double), ("target_sse", C.c_double), ("sse_trunc", C.c_double),
+                ("sse_quant_pred", C.c_double), ("order", C.c_int * 8), ("storage_order", C.c_int * 8),
+                ("k", C.c_int), ("p_star", C.c_int), ("i_star", C.c_int64), ("escalated_modes", C.c_int),
+                ("ms_norm", C.c_double), ("ms_gram", C.c_double), ("ms_eig", C.c_double),
+                ("ms_ttm", C.c_double), ("ms_quant", C.c_double), ("ms_encode", C.c_double),
+                ("ms_total", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libatc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(lib_path):
+            raise ImportError(f"libatc.so not found at {lib_path}; run __graft_entry__.build()")
+        L = C.CDLL(lib_path)
+        vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+        L.atc_last_error.restype = C.c_char_p
+        L.atc_default_options.argtypes = [C.POINTER(Options)]
+        L.atc_default_options.restype = None
+        L.atc_compress.argtypes = [vp, C.POINTER(i64), i32, i32, dbl, C.POINTER(Options), C.POINTER(vp)]
+        L.atc_get_ranks.argtypes = [vp, C.POINTER(i64)]
+        L.atc_get_core.argtypes = [vp, C.POINTER(vp)]
+        L.atc_get_factor.argtypes = [vp, i32, C.POINTER(vp)]
+        L.atc_get_stream.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_size_t)]
+        L.atc_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.atc_free.argtypes = [vp]
+        L.atc_free.restype = None
+        L.atc_peek_dims.argtypes = [C.c_char_p, C.c_size_t, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+        L.atc_decompress.argtypes = [C.c_char_p, C.c_size_t, vp, i32, vp]
+        L.atc_norm2.argtypes = [vp, i64, i32, vp, vp]
+        L.atc_gram.argtypes = [vp, i32, i64, i64, i64, i32, vp, vp]
+        L.atc_eig_sym.argtypes = [vp, i32, vp, vp, i32, vp]
+        L.atc_rank_select.argtypes = [vp, i32, dbl, C.POINTER(i32), C.POINTER(dbl), vp]
+        L.atc_ttm.argtypes = [vp, i32, i64, i64, i64, vp, i64, i32, i32, vp, i32, vp]
+        L.atc_quantize_core.argtypes = [vp, i64, dbl, i32, vp, C.POINTER(vp), C.POINTER(C.c_size_t), C.POINTER(i64)]
+        L.atc_dequantize_core.argtypes = [C.c_char_p, C.c_size_t, vp, i64, vp]
+        L.atc_free_buffer.argtypes = [vp]
+        L.atc_free_buffer.restype = None
+        L.atc_release_workspace.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise AtcError(rc, lib().atc_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return ATC_F32
+    if t.dtype == torch.float64:
+        return ATC_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _dev(t: torch.Tensor):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def atc_norm2(x: torch.Tensor, stream=None) -> torch.Tensor:
+    out = torch.empty(1, dtype=torch.float64, device=x.device)
+    _check(lib().atc_norm2(_dev(x), x.numel(), _dt(x), _dev(out), _stream(stream)))
+    return out
+
+
+def atc_gram(x: torch.Tensor, L: int, n: int, R: int, precision: int = PREC_FP64, stream=None) -> torch.Tensor:
+    assert x.numel() == L * n * R
+    g = torch.empty((n, n), dtype=torch.float64, device=x.device)
+    _check(lib().atc_gram(_dev(x), _dt(x), L, n, R, precision, _dev(g), _stream(stream)))
+    return g
+
+
+def atc_eig_sym(g: torch.Tensor, nvec: int, stream=None):
+    n = g.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device=g.device)
+    v = torch.empty((n, max(nvec, 1)), dtype=torch.float64, device=g.device)
+    _check(lib().atc_eig_sym(_dev(g), n, _dev(lam), _dev(v) if nvec > 0 else None, nvec, _stream(stream)))
+    return lam, v[:, :nvec]
+
+
+def atc_rank_select(lam: torch.Tensor, budget: float, stream=None):
+    r, disc = C.c_int(0), C.c_double(0.0)
+    _check(lib().atc_rank_select(_dev(lam), lam.numel(), float(budget), C.byref(r), C.byref(disc), _stream(stream)))
+    return r.value, disc.value
+
+
+def atc_ttm(x: torch.Tensor, L: int, n: int, R: int, u: torch.Tensor, r: int, expand: bool = False,
+            precision: int = PREC_FP64, out_dtype=torch.float64, stream=None) -> torch.Tensor:
+    out_mode = n if expand else r
+    y = torch.empty(L * out_mode * R, dtype=out_dtype, device=x.device)
+    _check(lib().atc_ttm(_dev(x), _dt(x), L, n, R, _dev(u), r, 1 if expand else 0, precision, _dev(y), _dt(y),
+                         _stream(stream)))
+    return y
+
+
+def atc_quantize_core(core: torch.Tensor, target_sse: float, block_size: int = 4096, stream=None):
+    ptr, nb = C.c_void_p(), C.c_size_t(0)
+    info = (C.c_int64 * 4)()
+    _check(lib().atc_quantize_core(_dev(core), core.numel(), float(target_sse), block_size, _stream(stream),
+                                   C.byref(ptr), C.byref(nb), info))
+    data = C.string_at(ptr, nb.value)
+    lib().atc_free_buffer(ptr)
+    return data, dict(k=info[0], p_star=info[1], i_star=info[2])
+
+
+def atc_dequantize_core(section: bytes, n: int, device="cuda", stream=None) -> torch.Tensor:
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    _check(lib().atc_dequantize_core(section, len(section), _dev(out), n, _stream(stream)))
+    return out
+
+
+class Compressed:
+    """Handle returned by atc_compress (owns the library object)."""
+
+    def __init__(self, handle, ndim, dims):
+        self._h = handle
+        self.ndim = ndim
+        self.dims = list(dims)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().atc_free(self._h)
+            self._h = None
+
+    def ranks(self):
+        r = (C.c_int64 * self.ndim)()
+        _check(lib().atc_get_ranks(self._h, r))
+        return list(r)
+
+    def stream_bytes(self) -> bytes:
+        p, n = C.c_void_p(), C.c_size_t(0)
+        _check(lib().atc_get_stream(self._h, C.byref(p), C.byref(n)))
+        return C.string_at(p, n.value)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().atc_get_stats(self._h, C.byref(s)))
+        out = {f: getattr(s, f) for f, _ in Stats._fields_}
+        out["order"] = list(s.order)[: self.ndim]
+        out["storage_order"] = list(s.storage_order)[: self.ndim]
+        return out
+
+    def _wrap(self, ptr, shape):
+        # copy out of the library-owned device buffer (borrowed view -> clone)
+        class _View:
+            pass
+        v = _View()
+        v.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr.value, True),
+                                      "version": 3, "strides": None}
+        torch.cuda.synchronize()
+        return torch.as_tensor(v, device="cuda").clone()
+
+    def core(self) -> torch.Tensor:
+        p = C.c_void_p()
+        _check(lib().atc_get_core(self._h, C.byref(p)))
+        return self._wrap(p, self.ranks())
+
+    def factor(self, mode: int) -> torch.Tensor:
+        p = C.c_void_p()
+        _check(lib().atc_get_factor(self._h, mode, C.byref(p)))
+        return self._wrap(p, [self.dims[mode], self.ranks()[mode]])
+
+
+def atc_compress(x: torch.Tensor, rel_eps: float, rtmss: float = 0.5, precision: int = PREC_FP64,
+                 rank_rule: int = RANK_STATIC, mode_order=None, block_size: int = 4096, stream=None) -> Compressed:
+    opt = Options()
+    lib().atc_default_options(C.byref(opt))
+    opt.rtmss = rtmss
+    opt.precision = precision
+    opt.rank_rule = rank_rule
+    opt.block_size = block_size
+    opt.stream = _stream(stream)
+    keep = None
+    if mode_order is not None:
+        keep = (C.c_int * len(mode_order))(*mode_order)
+        opt.mode_order = keep
+    dims = (C.c_int64 * x.dim())(*x.shape)
+    h = C.c_void_p()
+    _check(lib().atc_compress(_dev(x), dims, x.dim(), _dt(x), float(rel_eps), C.byref(opt), C.byref(h)))
+    return Compressed(h, x.dim(), list(x.shape))
+
+
+def atc_peek_dims(stream_bytes: bytes):
+    nd, dt = C.c_int(0), C.c_int(0)
+    dims = (C.c_int64 * 8)()
+    _check(lib().atc_peek_dims(stream_bytes, len(stream_bytes), C.byref(nd), dims, C.byref(dt)))
+    return list(dims)[: nd.value], dt.value
+
+
+def atc_decompress(stream_bytes: bytes, out_dtype=torch.float64, device="cuda", stream=None) -> torch.Tensor:
+    dims, _ = atc_peek_dims(stream_bytes)
+    out = torch.empty(dims, dtype=out_dtype, device=device)
+    _check(lib().atc_decompress(stream_bytes, len(stream_bytes), _dev(out), _dt(out), _stream(stream)))
+    return out

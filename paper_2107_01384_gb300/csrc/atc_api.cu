@@ -1,0 +1,614 @@
+// Host orchestrator and C ABI (include/atc.h).
+//
+// Compression (Figure 1 pipeline restricted to the core):
+//   ||X||^2 -> TargetSSE_total = rel_eps^2 ||X||^2, ST-HOSVD budget
+//   RTMSS * TargetSSE_total (Section 4.1.3) -> for each mode in processing
+//   order (Section 4.1.1): Gram, eigenvalues, rank choice, eigenvectors of the
+//   kept columns, projection (Algorithm 1) -> core in storage order
+//   (supplement S.2) -> quantization with target TargetSSE_total -
+//   ActualSSE_ST-HOSVD (end of Section 4.1.3) -> stream.
+// Projected modes keep their position in the row-major layout, so no tensor
+// is ever transposed; the (L, n, R) view of the current tensor is all a kernel
+// needs.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "atc_internal.cuh"
+
+namespace atc {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+int fail(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+// ------------------------------------------------------------------ scratch
+namespace {
+struct DevArena {
+  void* ptr[SLOT_COUNT] = {};
+  size_t cap[SLOT_COUNT] = {};
+};
+std::mutex g_arena_mu;
+std::vector<DevArena> g_arenas;
+}  // namespace
+
+int Scratch::get(int slot, size_t bytes, void** out) {
+  if (slot < 0 || slot >= SLOT_COUNT) return fail(ATC_EINVAL, "bad scratch slot");
+  int dev = 0;
+  ATC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_arena_mu);
+  if ((int)g_arenas.size() <= dev) g_arenas.resize(dev + 1);
+  DevArena& a = g_arenas[dev];
+  if (bytes == 0) bytes = 256;
+  if (a.cap[slot] < bytes) {
+    if (a.ptr[slot]) {
+      // a device-wide sync is needed before freeing memory queued work may use
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return fail(ATC_ECUDA, "cudaDeviceSynchronize: %s", cudaGetErrorString(e));
+      cudaFree(a.ptr[slot]);
+      a.ptr[slot] = nullptr;
+      a.cap[slot] = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    want = (want + 255) & ~(size_t)255;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ATC_ENOMEM, "cudaMalloc(%zu) for scratch slot %d failed: %s", want, slot, cudaGetErrorString(e));
+    }
+    a.ptr[slot] = p;
+    a.cap[slot] = want;
+  }
+  *out = a.ptr[slot];
+  return ATC_OK;
+}
+
+int Scratch::release_all() {
+  int dev = 0;
+  ATC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_arena_mu);
+  if ((int)g_arenas.size() <= dev) return ATC_OK;
+  ATC_CUDA_TRY(cudaDeviceSynchronize());
+  DevArena& a = g_arenas[dev];
+  for (int i = 0; i < SLOT_COUNT; ++i) {
+    if (a.ptr[i]) cudaFree(a.ptr[i]);
+    a.ptr[i] = nullptr;
+    a.cap[i] = 0;
+  }
+  return ATC_OK;
+}
+
+}  // namespace atc
+
+using namespace atc;
+
+struct atc_compressed {
+  int ndim = 0;
+  int dtype = 0;
+  int64_t dims[8] = {};
+  int64_t ranks[8] = {};
+  double* core = nullptr;      // device, FP64, (r_1..r_d)
+  double* factors[8] = {};     // device, FP64, n_i x r_i
+  std::string stream;          // host
+  atc_stats stats = {};
+};
+
+namespace {
+
+int dtype_size(int dt) { return dt == ATC_F32 ? 4 : (dt == ATC_F64 ? 8 : 0); }
+
+void put32(std::string& s, uint32_t v) { for (int i = 0; i < 4; ++i) s.push_back((char)(v >> (8 * i))); }
+void put64(std::string& s, uint64_t v) { for (int i = 0; i < 8; ++i) s.push_back((char)(v >> (8 * i))); }
+void putf64(std::string& s, double v) { uint64_t u; memcpy(&u, &v, 8); put64(s, u); }
+uint32_t get32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i); return v; }
+uint64_t get64(const uint8_t* p) { uint64_t v = 0; for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i); return v; }
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  float stop() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~Timer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+int check_dims(const int64_t* dims, int ndim, int64_t* total) {
+  if (!dims || ndim < 1 || ndim > 8) return fail(ATC_EINVAL, "ndim must be in [1, 8]");
+  int64_t t = 1;
+  for (int i = 0; i < ndim; ++i) {
+    if (dims[i] <= 0) return fail(ATC_EINVAL, "dims[%d] = %lld must be positive", i, (long long)dims[i]);
+    if (dims[i] > ((int64_t)1 << 40) / t) return fail(ATC_EINVAL, "tensor too large");
+    t *= dims[i];
+  }
+  *total = t;
+  return ATC_OK;
+}
+
+int gram_dispatch(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g, cudaStream_t s) {
+  if (precision == ATC_PREC_FP64) return launch_gram_fp64(x, dtype, L, n, R, g, s);
+  return launch_gram_split(x, dtype, L, n, R, precision, g, s);
+}
+
+int ttm_dispatch(const void* x, int xdt, int64_t L, int64_t n, int64_t R, const double* u, int64_t r, int expand,
+                 int precision, void* y, int ydt, cudaStream_t s) {
+  if (precision == ATC_PREC_FP64) return launch_ttm_fp64(x, xdt, L, n, R, u, r, expand, y, ydt, s);
+  return launch_ttm_split(x, xdt, L, n, R, u, r, expand, precision, y, ydt, s);
+}
+
+int eig_check(cudaStream_t s) {
+  int err = 0;
+  ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  ATC_TRY(eig_read_error(&err));
+  if (err) return fail(ATC_ETIMEOUT, "grid barrier of the tridiagonalisation timed out");
+  return ATC_OK;
+}
+
+// Decompression order (Section 4.1.1): exhaustive search over d! orders for
+// the smallest sum_i n_p1..n_pi r_pi..r_pd; first minimum in lexicographic
+// permutation order.
+std::vector<int> decompression_order(int d, const int64_t* dims, const int64_t* ranks) {
+  std::vector<int> p(d), best;
+  for (int i = 0; i < d; ++i) p[i] = i;
+  double best_cost = -1.0;
+  do {
+    double cost = 0.0;
+    for (int i = 0; i < d; ++i) {
+      double c = 1.0;
+      for (int j = 0; j <= i; ++j) c *= (double)dims[p[j]];
+      for (int j = i; j < d; ++j) c *= (double)ranks[p[j]];
+      cost += c;
+    }
+    if (best_cost < 0.0 || cost < best_cost) { best_cost = cost; best = p; }
+  } while (std::next_permutation(p.begin(), p.end()));
+  return best;
+}
+
+void free_compressed(atc_compressed* c) {
+  if (!c) return;
+  if (c->core) cudaFree(c->core);
+  for (int i = 0; i < 8; ++i)
+    if (c->factors[i]) cudaFree(c->factors[i]);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void atc_default_options(atc_options* opt) {
+  if (!opt) return;
+  opt->rtmss = 0.5;
+  opt->precision = ATC_PREC_FP64;
+  opt->rank_rule = ATC_RANK_STATIC;
+  opt->mode_order = nullptr;
+  opt->block_size = 4096;
+  opt->stream = nullptr;
+}
+
+const char* atc_last_error(void) { return g_err.c_str(); }
+
+void atc_free_buffer(void* p) { free(p); }
+
+int atc_release_workspace(void) { return Scratch::release_all(); }
+
+int atc_norm2(const void* x_dev, int64_t n, int dtype, double* out_dev, void* stream) {
+  if (!x_dev || !out_dev || n < 0 || !dtype_size(dtype)) return fail(ATC_EINVAL, "atc_norm2: bad arguments");
+  return launch_norm2(x_dev, dtype, n, out_dev, (cudaStream_t)stream);
+}
+
+int atc_gram(const void* x_dev, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g_dev,
+             void* stream) {
+  if (!x_dev || !g_dev || L < 1 || n < 1 || R < 1 || !dtype_size(dtype)) return fail(ATC_EINVAL, "atc_gram: bad arguments");
+  if (precision < 0 || precision > 2) return fail(ATC_EINVAL, "atc_gram: bad precision");
+  return gram_dispatch(x_dev, dtype, L, n, R, precision, g_dev, (cudaStream_t)stream);
+}
+
+int atc_eig_sym(const double* g_dev, int n, double* lam_dev, double* v_dev, int nvec, void* stream) {
+  if (!g_dev || !lam_dev || n < 1 || n > 1024 || nvec < 0 || nvec > n || (nvec > 0 && !v_dev))
+    return fail(ATC_EINVAL, "atc_eig_sym: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  ATC_TRY(launch_eig_sym(g_dev, n, lam_dev, v_dev, nvec, s));
+  return eig_check(s);
+}
+
+int atc_rank_select(const double* lam_dev, int n, double budget, int* r_out, double* disc_out, void* stream) {
+  if (!lam_dev || n < 1 || !r_out || !disc_out) return fail(ATC_EINVAL, "atc_rank_select: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* r_dev = nullptr;
+  ATC_TRY(Scratch::get(SLOT_LAM, 64, (void**)&r_dev));
+  double* d_dev = reinterpret_cast<double*>(r_dev + 8);
+  ATC_TRY(launch_rank_select(lam_dev, n, budget, r_dev, d_dev, s));
+  ATC_CUDA_TRY(cudaMemcpyAsync(r_out, r_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ATC_CUDA_TRY(cudaMemcpyAsync(disc_out, d_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  return ATC_OK;
+}
+
+int atc_ttm(const void* x_dev, int xdtype, int64_t L, int64_t n, int64_t R, const double* u_dev, int64_t r,
+            int expand, int precision, void* y_dev, int ydtype, void* stream) {
+  if (!x_dev || !u_dev || !y_dev || L < 1 || n < 1 || R < 1 || r < 1 || !dtype_size(xdtype) || !dtype_size(ydtype))
+    return fail(ATC_EINVAL, "atc_ttm: bad arguments");
+  if (precision < 0 || precision > 2) return fail(ATC_EINVAL, "atc_ttm: bad precision");
+  return ttm_dispatch(x_dev, xdtype, L, n, R, u_dev, r, expand ? 1 : 0, precision, y_dev, ydtype, (cudaStream_t)stream);
+}
+
+int atc_quantize_core(const double* core_dev, int64_t n, double target_sse, int block_size, void* stream,
+                      uint8_t** bytes, size_t* nbytes, int64_t* info) {
+  if (!core_dev || n < 1 || !bytes || !nbytes) return fail(ATC_EINVAL, "atc_quantize_core: bad arguments");
+  std::string out;
+  QuantResult qr;
+  ATC_TRY(quantize_encode(core_dev, n, target_sse, block_size, (cudaStream_t)stream, &out, &qr, nullptr, nullptr));
+  uint8_t* buf = (uint8_t*)malloc(out.size() ? out.size() : 1);
+  if (!buf) return fail(ATC_ENOMEM, "host allocation failed");
+  memcpy(buf, out.data(), out.size());
+  *bytes = buf;
+  *nbytes = out.size();
+  if (info) {
+    info[0] = qr.k;
+    info[1] = qr.p_star;
+    info[2] = qr.i_star;
+    info[3] = 0;
+  }
+  return ATC_OK;
+}
+
+int atc_dequantize_core(const uint8_t* bytes, size_t nbytes, double* core_dev, int64_t n, void* stream) {
+  if (!bytes || !core_dev || n < 1) return fail(ATC_EINVAL, "atc_dequantize_core: bad arguments");
+  return decode_dequantize(bytes, nbytes, core_dev, n, (cudaStream_t)stream);
+}
+
+int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, double rel_eps,
+                 const atc_options* opt_in, atc_compressed** out) {
+  if (!out) return fail(ATC_EINVAL, "atc_compress: out is NULL");
+  *out = nullptr;
+  if (!x_dev) return fail(ATC_EINVAL, "atc_compress: x_dev is NULL");
+  if (!dtype_size(dtype)) return fail(ATC_EINVAL, "atc_compress: dtype must be ATC_F32 or ATC_F64");
+  int64_t N = 0;
+  ATC_TRY(check_dims(dims, ndim, &N));
+  if (!(rel_eps > 0.0 && rel_eps <= 1.0)) return fail(ATC_EINVAL, "rel_eps must lie in (0, 1]");
+  atc_options opt;
+  atc_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (!(opt.rtmss >= 0.0 && opt.rtmss <= 1.0)) return fail(ATC_EINVAL, "rtmss must lie in [0, 1]");
+  if (opt.precision < 0 || opt.precision > 2) return fail(ATC_EINVAL, "bad precision");
+  if (opt.rank_rule != ATC_RANK_STATIC && opt.rank_rule != ATC_RANK_ADAPTIVE) return fail(ATC_EINVAL, "bad rank rule");
+  if (opt.block_size < 32 || opt.block_size > 65535 || (opt.block_size % 32)) return fail(ATC_EINVAL, "bad block_size");
+  const int d = ndim;
+  std::vector<int> order(d);
+  if (opt.mode_order) {
+    std::vector<int> seen(d, 0);
+    for (int i = 0; i < d; ++i) {
+      int m = opt.mode_order[i];
+      if (m < 0 || m >= d || seen[m]) return fail(ATC_EINVAL, "mode_order must be a permutation of 0..ndim-1");
+      seen[m] = 1;
+      order[i] = m;
+    }
+  } else {
+    for (int i = 0; i < d; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dims[a] < dims[b]; });
+  }
+  cudaStream_t s = (cudaStream_t)opt.stream;
+  atc_compressed* c = new (std::nothrow) atc_compressed();
+  if (!c) return fail(ATC_ENOMEM, "host allocation failed");
+  c->ndim = d;
+  c->dtype = dtype;
+  for (int i = 0; i < d; ++i) c->dims[i] = dims[i];
+  atc_stats& st = c->stats;
+  memset(&st, 0, sizeof(st));
+  for (int i = 0; i < 8; ++i) st.order[i] = st.storage_order[i] = -1;
+  for (int i = 0; i < d; ++i) st.order[i] = order[i];
+  auto bail = [&](int rc) {
+    free_compressed(c);
+    return rc;
+  };
+  Timer total(s);
+  // ||X||^2 and the budgets (Section 4.1.3)
+  double* small = nullptr;
+  int rc = Scratch::get(SLOT_SMALL, sizeof(double) * 2048, (void**)&small);
+  if (rc) return bail(rc);
+  double* dnorm = small + 1600;
+  {
+    Timer t(s);
+    rc = launch_norm2(x_dev, dtype, N, dnorm, s);
+    if (rc) return bail(rc);
+    double h = 0.0;
+    if (cudaMemcpyAsync(&h, dnorm, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return bail(fail(ATC_ECUDA, "norm readback failed"));
+    st.ms_norm = t.stop();
+    st.norm2 = h;
+  }
+  if (!(st.norm2 == st.norm2) || st.norm2 > 1.7e308) return bail(fail(ATC_ENUMERIC, "input contains NaN or Inf"));
+  st.target_sse = rel_eps * rel_eps * st.norm2;
+  const double budget_total = opt.rtmss * st.target_sse;
+  // intermediate precision: FP64 for the plain path, FP32 for the split paths
+  const int idt = (opt.precision == ATC_PREC_FP64) ? ATC_F64 : ATC_F32;
+  const size_t ibytes = (size_t)dtype_size(idt);
+  int64_t cur[8];
+  for (int i = 0; i < d; ++i) cur[i] = dims[i];
+  // the largest projected tensor is after the first mode: N * r / n <= N
+  void* bufA = nullptr;
+  void* bufB = nullptr;
+  int64_t maxn = 1;
+  for (int i = 0; i < d; ++i) maxn = std::max(maxn, dims[i]);
+  double *G = nullptr, *lam = nullptr;
+  rc = Scratch::get(SLOT_TEN_A, ibytes * (size_t)N, &bufA);
+  if (!rc) rc = Scratch::get(SLOT_TEN_B, ibytes * (size_t)N, &bufB);
+  if (!rc) rc = Scratch::get(SLOT_LAM, sizeof(double) * (size_t)(maxn * maxn + maxn + 64), (void**)&lam);
+  if (rc) return bail(rc);
+  G = lam + maxn + 16;
+  int* rdev = reinterpret_cast<int*>(lam + maxn);
+  double* ddev = lam + maxn + 2;
+  const void* curp = x_dev;
+  int curdt = dtype;
+  void* next = bufA;
+  double used = 0.0;
+  float ms_gram = 0.f, ms_eig = 0.f, ms_ttm = 0.f;
+  for (int step = 0; step < d; ++step) {
+    const int m = order[step];
+    int64_t L = 1, R = 1;
+    for (int i = 0; i < m; ++i) L *= cur[i];
+    for (int i = m + 1; i < d; ++i) R *= cur[i];
+    const int64_t n = cur[m];
+    if (n > 1024) return bail(fail(ATC_EUNSUP, "mode length %lld > 1024 is not supported", (long long)n));
+    {
+      Timer t(s);
+      rc = gram_dispatch(curp, curdt, L, n, R, opt.precision, G, s);
+      if (rc) return bail(rc);
+      ms_gram += t.stop();
+    }
+    int r = 0;
+    double disc = 0.0;
+    {
+      Timer t(s);
+      rc = launch_eig_values(G, (int)n, lam, s);
+      if (rc) return bail(rc);
+      const double budget =
+          (opt.rank_rule == ATC_RANK_STATIC) ? budget_total / d : (budget_total - used) / (double)(d - step);
+      rc = launch_rank_select(lam, (int)n, budget, rdev, ddev, s);
+      if (rc) return bail(rc);
+      if (cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaMemcpyAsync(&disc, ddev, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return bail(fail(ATC_ECUDA, "rank readback failed"));
+      rc = eig_check(s);
+      if (rc) return bail(rc);
+      if (r < 1 || r > n) return bail(fail(ATC_ENUMERIC, "rank selection failed (r = %d)", r));
+      if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
+        return bail(fail(ATC_ENOMEM, "factor allocation failed"));
+      rc = launch_eig_vectors((int)n, r, c->factors[m], s);
+      if (rc) return bail(rc);
+      ms_eig += t.stop();
+    }
+    {
+      Timer t(s);
+      rc = ttm_dispatch(curp, curdt, L, n, R, c->factors[m], r, 0, opt.precision, next, idt, s);
+      if (rc) return bail(rc);
+      ms_ttm += t.stop();
+    }
+    c->ranks[m] = r;
+    cur[m] = r;
+    used += disc;
+    curp = next;
+    curdt = idt;
+    next = (next == bufA) ? bufB : bufA;
+  }
+  st.ms_gram = ms_gram;
+  st.ms_eig = ms_eig;
+  st.ms_ttm = ms_ttm;
+  st.sse_trunc = used;
+  int64_t ncore = 1;
+  for (int i = 0; i < d; ++i) ncore *= c->ranks[i];
+  if (cudaMalloc(&c->core, sizeof(double) * (size_t)ncore) != cudaSuccess)
+    return bail(fail(ATC_ENOMEM, "core allocation failed"));
+  rc = launch_convert_to_f64(curp, curdt, ncore, c->core, s);
+  if (rc) return bail(rc);
+  // storage order: increasing rank, ties by index (supplement S.2)
+  std::vector<int> perm(d);
+  for (int i = 0; i < d; ++i) perm[i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return c->ranks[a] < c->ranks[b]; });
+  for (int i = 0; i < d; ++i) st.storage_order[i] = perm[i];
+  double* vec = nullptr;
+  rc = Scratch::get(SLOT_CORE, sizeof(double) * (size_t)ncore, (void**)&vec);
+  if (rc) return bail(rc);
+  rc = launch_permute(c->core, c->ranks, perm.data(), d, vec, 0, s);
+  if (rc) return bail(rc);
+  std::string section;
+  QuantResult qr;
+  float msq = 0.f, mse = 0.f;
+  rc = quantize_encode(vec, ncore, st.target_sse - used, opt.block_size, s, &section, &qr, &msq, &mse);
+  if (rc) return bail(rc);
+  st.ms_quant = msq;
+  st.ms_encode = mse;
+  st.k = qr.k;
+  st.p_star = qr.p_star;
+  st.i_star = qr.i_star;
+  st.sse_quant_pred = qr.sse_pred;
+  // stream: header, factors (raw FP64), core section
+  std::string& S = c->stream;
+  S.append("ATC1", 4);
+  put32(S, 1);
+  put32(S, (uint32_t)d);
+  put32(S, (uint32_t)dtype);
+  for (int i = 0; i < d; ++i) put64(S, (uint64_t)dims[i]);
+  for (int i = 0; i < d; ++i) put64(S, (uint64_t)c->ranks[i]);
+  for (int i = 0; i < d; ++i) put32(S, (uint32_t)perm[i]);
+  while (S.size() % 8) S.push_back('\0');
+  putf64(S, st.norm2);
+  putf64(S, st.sse_trunc);
+  for (int i = 0; i < d; ++i) {
+    const size_t cnt = (size_t)dims[i] * c->ranks[i];
+    const size_t at = S.size();
+    S.resize(at + cnt * 8);
+    if (cudaMemcpyAsync(&S[at], c->factors[i], cnt * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return bail(fail(ATC_ECUDA, "factor readback failed"));
+  }
+  put64(S, (uint64_t)section.size());
+  S.append(section);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ATC_ECUDA, "stream synchronisation failed"));
+  st.ms_total = total.stop();
+  *out = c;
+  return ATC_OK;
+}
+
+int atc_get_ranks(const atc_compressed* c, int64_t* ranks) {
+  if (!c || !ranks) return fail(ATC_EINVAL, "atc_get_ranks: bad arguments");
+  for (int i = 0; i < c->ndim; ++i) ranks[i] = c->ranks[i];
+  return ATC_OK;
+}
+
+int atc_get_core(const atc_compressed* c, const double** core_dev) {
+  if (!c || !core_dev) return fail(ATC_EINVAL, "atc_get_core: bad arguments");
+  *core_dev = c->core;
+  return ATC_OK;
+}
+
+int atc_get_factor(const atc_compressed* c, int mode, const double** u_dev) {
+  if (!c || !u_dev || mode < 0 || mode >= c->ndim) return fail(ATC_EINVAL, "atc_get_factor: bad arguments");
+  *u_dev = c->factors[mode];
+  return ATC_OK;
+}
+
+int atc_get_stream(const atc_compressed* c, const uint8_t** bytes, size_t* nbytes) {
+  if (!c || !bytes || !nbytes) return fail(ATC_EINVAL, "atc_get_stream: bad arguments");
+  *bytes = (const uint8_t*)c->stream.data();
+  *nbytes = c->stream.size();
+  return ATC_OK;
+}
+
+int atc_get_stats(const atc_compressed* c, atc_stats* stats) {
+  if (!c || !stats) return fail(ATC_EINVAL, "atc_get_stats: bad arguments");
+  *stats = c->stats;
+  return ATC_OK;
+}
+
+void atc_free(atc_compressed* c) { free_compressed(c); }
+
+int atc_peek_dims(const uint8_t* stream, size_t nbytes, int* ndim, int64_t* dims, int* dtype) {
+  if (!stream || !ndim || !dims || !dtype) return fail(ATC_EINVAL, "atc_peek_dims: bad arguments");
+  if (nbytes < 16 || memcmp(stream, "ATC1", 4) != 0 || get32(stream + 4) != 1) return fail(ATC_ECORRUPT, "bad stream magic/version");
+  const int d = (int)get32(stream + 8);
+  const int dt = (int)get32(stream + 12);
+  if (d < 1 || d > 8 || !dtype_size(dt)) return fail(ATC_ECORRUPT, "bad stream header");
+  if (nbytes < 16 + (size_t)d * 16) return fail(ATC_ECORRUPT, "truncated stream header");
+  for (int i = 0; i < d; ++i) dims[i] = (int64_t)get64(stream + 16 + 8 * i);
+  *ndim = d;
+  *dtype = dt;
+  return ATC_OK;
+}
+
+int atc_decompress(const uint8_t* stream, size_t nbytes, void* out_dev, int out_dtype, void* cuda_stream) {
+  if (!stream || !out_dev || !dtype_size(out_dtype)) return fail(ATC_EINVAL, "atc_decompress: bad arguments");
+  int d = 0, dt = 0;
+  int64_t dims[8];
+  ATC_TRY(atc_peek_dims(stream, nbytes, &d, dims, &dt));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  size_t off = 16;
+  int64_t ranks[8];
+  int perm[8];
+  off += 8 * d;
+  for (int i = 0; i < d; ++i) ranks[i] = (int64_t)get64(stream + off + 8 * i);
+  off += 8 * d;
+  if (nbytes < off + 4 * d + 16) return fail(ATC_ECORRUPT, "truncated stream header");
+  std::vector<int> seen(d, 0);
+  for (int i = 0; i < d; ++i) {
+    perm[i] = (int)get32(stream + off + 4 * i);
+    if (perm[i] < 0 || perm[i] >= d || seen[perm[i]]) return fail(ATC_ECORRUPT, "bad storage order");
+    seen[perm[i]] = 1;
+  }
+  off += 4 * d;
+  off = (off + 7) & ~(size_t)7;
+  off += 16;  // norm2, sse_trunc
+  int64_t ncore = 1, maxn = 0, N = 1;
+  for (int i = 0; i < d; ++i) {
+    if (ranks[i] < 1 || ranks[i] > dims[i] || dims[i] > 1024) return fail(ATC_ECORRUPT, "bad ranks");
+    ncore *= ranks[i];
+    N *= dims[i];
+    maxn = std::max(maxn, dims[i]);
+  }
+  size_t fac_total = 0;
+  for (int i = 0; i < d; ++i) fac_total += (size_t)dims[i] * ranks[i];
+  if (nbytes < off + fac_total * 8 + 8) return fail(ATC_ECORRUPT, "truncated factors");
+  double* fac = nullptr;
+  ATC_TRY(Scratch::get(SLOT_FAC, fac_total * 8 + 64, (void**)&fac));
+  ATC_CUDA_TRY(cudaMemcpyAsync(fac, stream + off, fac_total * 8, cudaMemcpyHostToDevice, s));
+  double* U[8];
+  {
+    size_t acc = 0;
+    for (int i = 0; i < d; ++i) { U[i] = fac + acc; acc += (size_t)dims[i] * ranks[i]; }
+  }
+  off += fac_total * 8;
+  const uint64_t cb = get64(stream + off);
+  off += 8;
+  if (cb > nbytes - off) return fail(ATC_ECORRUPT, "truncated core section");
+  double* vec = nullptr;
+  ATC_TRY(Scratch::get(SLOT_CORE, sizeof(double) * (size_t)ncore, (void**)&vec));
+  ATC_TRY(decode_dequantize(stream + off, (size_t)cb, vec, ncore, s));
+  // expansion chain in FP64, ping-pong; sizes grow as modes expand
+  size_t maxsz = 0;
+  {
+    std::vector<int> ord = decompression_order(d, dims, ranks);
+    int64_t cur[8];
+    for (int i = 0; i < d; ++i) cur[i] = ranks[i];
+    int64_t sz = ncore;
+    maxsz = (size_t)sz;
+    for (int m : ord) { sz = sz / cur[m] * dims[m]; cur[m] = dims[m]; maxsz = std::max(maxsz, (size_t)sz); }
+  }
+  double *A = nullptr, *B = nullptr;
+  ATC_TRY(Scratch::get(SLOT_DEC, sizeof(double) * maxsz, (void**)&A));
+  ATC_TRY(Scratch::get(SLOT_DEC2, sizeof(double) * maxsz, (void**)&B));
+  ATC_TRY(launch_permute(vec, ranks, perm, d, A, 1, s));
+  std::vector<int> ord = decompression_order(d, dims, ranks);
+  int64_t cur[8];
+  for (int i = 0; i < d; ++i) cur[i] = ranks[i];
+  double* src = A;
+  double* dst = B;
+  for (int m : ord) {
+    int64_t L = 1, R = 1;
+    for (int i = 0; i < m; ++i) L *= cur[i];
+    for (int i = m + 1; i < d; ++i) R *= cur[i];
+    ATC_TRY(launch_ttm_fp64(src, ATC_F64, L, dims[m], R, U[m], ranks[m], 1, dst, ATC_F64, s));
+    cur[m] = dims[m];
+    std::swap(src, dst);
+  }
+  ATC_TRY(launch_convert_f64_to(src, N, out_dev, out_dtype, s));
+  ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  return ATC_OK;
+}
+
+}  // extern "C"

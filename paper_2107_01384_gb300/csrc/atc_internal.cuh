@@ -1,0 +1,100 @@
+// Internal declarations shared by the translation units of libatc.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/atc.h"
+
+namespace atc {
+
+// Thread-local error message, set by fail().
+void set_error(const char* fmt, ...);
+int fail(int code, const char* fmt, ...);
+
+#define ATC_CUDA_TRY(expr)                                                              \
+  do {                                                                                  \
+    cudaError_t _e = (expr);                                                            \
+    if (_e != cudaSuccess)                                                              \
+      return ::atc::fail(ATC_ECUDA, "%s failed at %s:%d: %s", #expr, __FILE__, __LINE__, \
+                         cudaGetErrorString(_e));                                       \
+  } while (0)
+
+#define ATC_TRY(expr)          \
+  do {                         \
+    int _rc = (expr);          \
+    if (_rc != ATC_OK) return _rc; \
+  } while (0)
+
+// Device scratch: a grow-only cached arena per device (cudaMalloc).
+struct Scratch {
+  // Returns a device pointer to at least `bytes` bytes of slot `slot`, 256-B aligned.
+  static int get(int slot, size_t bytes, void** ptr);
+  static int release_all();
+};
+
+enum ScratchSlot {
+  SLOT_GRAM_PART = 0,  // split-K Gram partials
+  SLOT_EIG_A,          // eigen working matrix
+  SLOT_EIG_V,          // Householder vectors
+  SLOT_EIG_VEC,        // small vectors (d, e, tau, p, w, flags)
+  SLOT_EIG_Z,          // tridiagonal eigenvectors
+  SLOT_TEN_A,          // ping-pong tensor A
+  SLOT_TEN_B,          // ping-pong tensor B
+  SLOT_SMALL,          // small device scalars
+  SLOT_Q,              // quantized magnitudes
+  SLOT_QS,             // signs
+  SLOT_QPART,          // tracker partials
+  SLOT_ENC,            // encoder sizes / offsets
+  SLOT_OUT,            // device stream staging
+  SLOT_CORE,           // permuted core
+  SLOT_LAM,            // eigenvalues
+  SLOT_TTM_U,          // packed split factor
+  SLOT_SPILL,          // encoder run spill (block sizes > 4096)
+  SLOT_DEC,            // decompression ping-pong
+  SLOT_DEC2,
+  SLOT_FAC,            // uploaded factors
+  SLOT_COUNT
+};
+
+// ---------------------------------------------------------------- kernels
+// norm / reductions (k_reduce.cu)
+int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s);
+int launch_convert_to_f64(const void* x, int dtype, int64_t n, double* y, cudaStream_t s);
+int launch_convert_f64_to(const double* x, int64_t n, void* y, int dtype, cudaStream_t s);
+int launch_permute(const double* x, const int64_t* dims, const int* perm, int ndim, double* y, int inverse,
+                   cudaStream_t s);
+
+// FP64 contractions (k_fp64.cu)
+int launch_gram_fp64(const void* x, int dtype, int64_t L, int64_t n, int64_t R, double* g, cudaStream_t s);
+int launch_ttm_fp64(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
+                    int expand, void* y, int ydtype, cudaStream_t s);
+
+// split-precision tensor-core contractions (k_gram_tc.cu, k_ttm_tc.cu)
+int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g,
+                      cudaStream_t s);
+int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
+                     int expand, int precision, void* y, int ydtype, cudaStream_t s);
+
+// eigensolver (k_eig.cu)
+int launch_eig_sym(const double* g, int n, double* lam, double* v, int nvec, cudaStream_t s);
+// eigenvalues only, then eigenvectors of the top nvec (split so rank selection can run between)
+int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s);
+int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s);
+int launch_rank_select(const double* lam, int n, double budget, int* r_dev, double* disc_dev, cudaStream_t s);
+int eig_read_error(int* err);
+
+// quantizer / encoder (k_quant.cu)
+struct QuantResult {
+  int k;
+  int p_star;
+  int64_t i_star;
+  double sse_pred;
+};
+int quantize_encode(const double* core, int64_t n, double target, int block_size, cudaStream_t s,
+                    std::string* out, QuantResult* res, float* ms_quant, float* ms_encode);
+int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t n, cudaStream_t s);
+
+}  // namespace atc

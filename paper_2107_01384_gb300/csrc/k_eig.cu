@@ -1,0 +1,590 @@
+// FP64 symmetric eigensolver for the mode Gram matrices (Algorithm 1: the
+// left singular vectors / squared singular values of the unfolding are the
+// eigenvectors / eigenvalues of G = B_(k) B_(k)^T), and the rank choice of
+// Section 4.1.3.
+//
+// GB300 has a small FP64 rate (about 2 DFMA lanes per clock per SM), so the
+// solver keeps FP64 work proportional to n^3 only where unavoidable and spreads
+// it over many SMs:
+//   1. Householder tridiagonalisation T = Q^T G Q: one cooperative kernel, rows
+//      dealt cyclically to the CTAs; each step re-forms the next reflector
+//      redundantly in every CTA and fuses the two-sided update of step s-1 with
+//      the matrix-vector product of step s, so a step costs ONE grid barrier.
+//      The barrier spin is bounded: on time-out an error flag is raised and
+//      every CTA returns.
+//   2. Eigenvalues of T by bisection on Sturm counts; the count uses the
+//      three-term recurrence of the leading principal minors (one dependent
+//      FMA per row) with power-of-two rescaling instead of a division per row.
+//   3. Eigenvectors of T for the largest eigenvalues by inverse iteration
+//      (LU with partial pivoting of T - lambda I), one CTA per group of close
+//      eigenvalues, re-orthogonalised within the group.
+//   4. Back-transformation X = Q Z, a warp per column, then the sign
+//      convention (largest-magnitude entry positive).
+#include <math.h>
+#include <stdint.h>
+
+#include "atc_internal.cuh"
+
+namespace atc {
+namespace {
+
+constexpr int kTriThreads = 256;
+constexpr unsigned kSpinLimit = 1u << 22;  // about 0.3 s of nanosleep(64) polling
+
+struct EigState {
+  double* a;      // n x n working copy
+  double* hv;     // (n) x n Householder vectors, row s holds v_s (v_s[s+1] = 1)
+  double* d;      // n diagonal of T (scaled after eig_values)
+  double* e;      // n off-diagonal of T (e[s] couples s, s+1)
+  double* tau;    // n
+  double* pbuf;   // 2 x n
+  double* lam;    // n eigenvalues of T, descending (scaled)
+  double* z;      // n x nvec tridiagonal eigenvectors (column j contiguous: z[j*n + i])
+  double* lu;     // 5 x n x nvec LU scratch
+  int* flags;     // [0] barrier count, [1] barrier generation, [2] error, [3] spare
+  double* scale;  // [0] power-of-two scale applied to T
+  int n;
+};
+EigState g_state;  // host-side copy of the scratch layout (single-stream use per device)
+
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch with a bounded wait.
+// Returns false if any CTA gave up (error flag raised).
+__device__ bool grid_barrier(int* flags) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned* count = reinterpret_cast<unsigned*>(flags);
+    unsigned* gen = reinterpret_cast<unsigned*>(flags + 1);
+    volatile int* err = flags + 2;
+    unsigned g = ld_acquire(gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(count, 0u);
+      __threadfence();
+      st_release(gen, g + 1u);
+    } else {
+      unsigned it = 0;
+      while (ld_acquire(gen) == g) {
+        if (*err) { ok = 0; break; }
+        if (++it > kSpinLimit) { atomicExch(flags + 2, 1); ok = 0; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*err) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (identical result in every CTA for identical input).
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+
+// ------------------------------------------------------------ tridiagonalisation
+// Iteration s (0 <= s <= n-2):
+//   phase 1 (s >= 1): w_{s-1} = p_{s-1} - (tau_{s-1}/2)(p_{s-1}.v_{s-1}) v_{s-1}
+//   phase 2: row s of A^(s) = stored row s - v_{s-1}[s] w_{s-1} - w_{s-1}[s] v_{s-1};
+//            d_s = its diagonal; reflector v_s, tau_s from its entries s+1..n-1; e_s = alpha.
+//   phase 3 (s <= n-3): owned rows i >= s+1: A^(s) = A^(s-1) - v w^T - w v^T on columns
+//            >= s+1, stored; p_s[i] = tau_s * (A^(s) row i) . v_s
+//   grid barrier
+__global__ void __launch_bounds__(kTriThreads) tridiag_kernel(EigState st) {
+  extern __shared__ double sm[];
+  const int n = st.n;
+  double* v_prev = sm;          // v_{s-1}
+  double* w_prev = sm + n;      // w_{s-1}
+  double* v_cur = sm + 2 * n;   // v_s
+  double* row = sm + 3 * n;     // row s of A^(s)
+  double* red = sm + 4 * n;     // 32 doubles
+  __shared__ double s_tau_prev, s_tau;
+  const int tid = threadIdx.x;
+  const int P = gridDim.x, b = blockIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  for (int i = tid; i < n; i += blockDim.x) { v_prev[i] = 0.0; w_prev[i] = 0.0; v_cur[i] = 0.0; }
+  if (tid == 0) { s_tau_prev = 0.0; s_tau = 0.0; }
+  __syncthreads();
+  for (int s = 0; s <= n - 2; ++s) {
+    // phase 1
+    if (s >= 1) {
+      const double* p = st.pbuf + ((s - 1) & 1) * n;
+      double part = 0.0;
+      for (int i = s + tid; i < n; i += blockDim.x) part += ldcg(p + i) * v_prev[i];
+      double dot = block_sum(part, red);
+      double K = 0.5 * s_tau_prev * dot;
+      for (int i = tid; i < n; i += blockDim.x) w_prev[i] = (i >= s) ? ldcg(p + i) - K * v_prev[i] : 0.0;
+      __syncthreads();
+    }
+    // phase 2: row s of A^(s)
+    {
+      const double vs = v_prev[s], ws = w_prev[s];
+      for (int j = s + tid; j < n; j += blockDim.x)
+        row[j] = ldcg(st.a + (int64_t)s * n + j) - vs * w_prev[j] - ws * v_prev[j];
+      __syncthreads();
+    }
+    double alpha = 0.0, tau = 0.0;
+    if (s <= n - 3) {
+      double part = 0.0;
+      for (int j = s + 2 + tid; j < n; j += blockDim.x) part += row[j] * row[j];
+      double sig2 = block_sum(part, red);
+      const double x0 = row[s + 1];
+      double scal = 0.0;
+      if (sig2 == 0.0) {
+        tau = 0.0; alpha = x0; scal = 0.0;
+      } else {
+        double nrm = sqrt(x0 * x0 + sig2);
+        alpha = (x0 >= 0.0) ? -nrm : nrm;
+        tau = (alpha - x0) / alpha;
+        scal = 1.0 / (x0 - alpha);
+      }
+      for (int j = tid; j < n; j += blockDim.x) {
+        double v = 0.0;
+        if (j == s + 1) v = 1.0;
+        else if (j > s + 1) v = row[j] * scal;
+        v_cur[j] = v;
+      }
+      if (tid == 0) s_tau = tau;
+      __syncthreads();
+      if (b == 0) {
+        for (int j = tid; j < n; j += blockDim.x) st.hv[(int64_t)s * n + j] = v_cur[j];
+        if (tid == 0) { st.d[s] = row[s]; st.e[s] = alpha; st.tau[s] = tau; }
+      }
+      // phase 3: fused update of rows >= s+1 and p_s
+      double* pout = st.pbuf + (s & 1) * n;
+      for (int i = s + 1 + ((b - (s + 1)) % P + P) % P + warp * P; i < n; i += P * nwarp) {
+        const double vi = v_prev[i], wi = w_prev[i];
+        double* arow = st.a + (int64_t)i * n;
+        double acc = 0.0;
+        for (int j = s + 1 + lane; j < n; j += 32) {
+          double a = ldcg(arow + j) - vi * w_prev[j] - wi * v_prev[j];
+          arow[j] = a;
+          acc = fma(a, v_cur[j], acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) pout[i] = tau * acc;
+      }
+      if (!grid_barrier(st.flags)) return;
+      // rotate v/w
+      for (int i = tid; i < n; i += blockDim.x) v_prev[i] = v_cur[i];
+      if (tid == 0) s_tau_prev = s_tau;
+      __syncthreads();
+    } else {
+      // s == n-2: last 2x2 block
+      if (b == 0 && tid == 0) {
+        st.d[s] = row[s];
+        st.e[s] = row[s + 1];
+        double a11 = ldcg(st.a + (int64_t)(n - 1) * n + (n - 1));
+        st.d[n - 1] = a11 - 2.0 * v_prev[n - 1] * w_prev[n - 1];
+        st.tau[s] = 0.0;
+      }
+    }
+  }
+}
+
+__global__ void tridiag_small_kernel(EigState st) {
+  // n == 1
+  if (threadIdx.x == 0) { st.d[0] = st.a[0]; st.e[0] = 0.0; }
+}
+
+// ------------------------------------------------------------------ eigenvalues
+// Scale T by a power of two so that the Gershgorin disc radius is <= 1.
+__global__ void scale_kernel(EigState st) {
+  __shared__ double red[32];
+  const int n = st.n;
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = fabs(st.d[i]) + (i > 0 ? fabs(st.e[i - 1]) : 0.0) + (i < n - 1 ? fabs(st.e[i]) : 0.0);
+    m = fmax(m, r);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmax(mm, red[i]);
+    int ex = 0;
+    if (mm > 0.0) frexp(mm, &ex);
+    red[0] = ldexp(1.0, -ex);  // mm * scale in [0.5, 1)
+    st.scale[0] = red[0];
+  }
+  __syncthreads();
+  const double sc = red[0];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    st.d[i] *= sc;
+    if (i < n - 1) st.e[i] *= sc;
+  }
+}
+
+// Number of eigenvalues of T (scaled, |entries| <= 1) smaller than sigma: sign
+// changes of the leading principal minors p_0 = 1, p_1, ..., p_n.
+__device__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n, double sigma) {
+  double pp = 1.0, p = d[0] - sigma;
+  const double tiny = 0x1p-900;
+  if (p == 0.0) p = -tiny;
+  int cnt = (p < 0.0);
+  for (int i = 1; i < n; ++i) {
+    double q = fma(d[i] - sigma, p, -e2[i - 1] * pp);
+    if (q == 0.0) q = (p < 0.0) ? tiny : -tiny;
+    cnt += ((q < 0.0) != (p < 0.0));
+    pp = p;
+    p = q;
+    // rescale by 2^-512 / 2^512 when the pair leaves [2^-480, 2^480]
+    int ex = (__double2hiint(p) >> 20) & 0x7ff;
+    if (ex > 1023 + 480) { p *= 0x1p-512; pp *= 0x1p-512; }
+    else if (ex < 1023 - 480) {
+      int ex2 = (__double2hiint(pp) >> 20) & 0x7ff;
+      if (ex2 < 1023 - 480) { p *= 0x1p512; pp *= 0x1p512; }
+    }
+  }
+  return cnt;
+}
+
+__global__ void bisect_kernel(EigState st) {
+  extern __shared__ double sm[];
+  const int n = st.n;
+  double* d = sm;
+  double* e2 = sm + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    d[i] = st.d[i];
+    e2[i] = (i < n - 1) ? st.e[i] * st.e[i] : 0.0;
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;  // j-th largest
+  if (j >= n) return;
+  const int m = n - 1 - j;  // m-th smallest (0-based)
+  double lo = -1.0, hi = 1.0;  // Gershgorin radius <= 1 after scaling
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(d, e2, n, mid) <= m) lo = mid; else hi = mid;
+    if (hi - lo <= 0x1p-54) break;
+  }
+  st.lam[j] = 0.5 * (lo + hi);
+}
+
+// ----------------------------------------------------------------- eigenvectors
+// Inverse iteration for the eigenvalues of one group (consecutive indices with
+// gaps below the grouping threshold); thread 0 runs the O(n) recurrences,
+// the block does the re-orthogonalisation against earlier vectors of the group.
+__global__ void invit_kernel(EigState st, const int* __restrict__ grp_start, const int* __restrict__ ngrp, int nvec) {
+  __shared__ double red[32];
+  const int n = st.n;
+  if ((int)blockIdx.x >= *ngrp) return;
+  const int g0 = grp_start[blockIdx.x], g1 = grp_start[blockIdx.x + 1];
+  const double* dd = st.d;
+  const double* ee = st.e;
+  for (int j = g0; j < g1 && j < nvec; ++j) {
+    double* x = st.z + (int64_t)j * n;
+    double* ld_ = st.lu + (int64_t)j * 5 * n;  // dl, d, du, du2, piv
+    double* fl = ld_;
+    double* fd = ld_ + n;
+    double* fu = ld_ + 2 * n;
+    double* fu2 = ld_ + 3 * n;
+    double* fp = ld_ + 4 * n;
+    const double lam = st.lam[j];
+    const double eps_piv = 0x1p-52;  // |T| <= 1 after scaling
+    if (threadIdx.x == 0) {
+      // LU with partial pivoting of T - lam I (rows i, i+1 may swap)
+      for (int i = 0; i < n; ++i) {
+        fd[i] = dd[i] - lam;
+        fl[i] = (i < n - 1) ? ee[i] : 0.0;
+        fu[i] = (i < n - 1) ? ee[i] : 0.0;
+        fu2[i] = 0.0;
+        fp[i] = 0.0;
+      }
+      for (int i = 0; i < n - 1; ++i) {
+        if (fabs(fd[i]) >= fabs(fl[i])) {
+          double piv = fd[i];
+          if (piv == 0.0) { piv = eps_piv; fd[i] = piv; }
+          double l = fl[i] / piv;
+          fl[i] = l;
+          fd[i + 1] -= l * fu[i];
+          fp[i] = 0.0;
+        } else {
+          double l = fd[i] / fl[i];
+          fd[i] = fl[i];
+          fl[i] = l;
+          double t = fu[i];
+          fu[i] = fd[i + 1];
+          fd[i + 1] = t - l * fd[i + 1];
+          if (i < n - 2) { fu2[i] = fu[i + 1]; fu[i + 1] = -l * fu[i + 1]; }
+          fp[i] = 1.0;
+        }
+      }
+      if (fd[n - 1] == 0.0) fd[n - 1] = eps_piv;
+      for (int i = 0; i < n; ++i) if (fabs(fd[i]) < eps_piv) fd[i] = (fd[i] < 0.0) ? -eps_piv : eps_piv;
+      // start vector: U x = (1, ..., 1) (first step skips L, as usual)
+      for (int i = n - 1; i >= 0; --i) {
+        double v = 1.0;
+        if (i + 1 < n) v -= fu[i] * x[i + 1];
+        if (i + 2 < n) v -= fu2[i] * x[i + 2];
+        x[i] = v / fd[i];
+      }
+    }
+    __syncthreads();
+    for (int iter = 0; iter < 3; ++iter) {
+      // orthogonalise against earlier vectors of the group, then normalise
+      for (int k = g0; k < j; ++k) {
+        const double* y = st.z + (int64_t)k * n;
+        double part = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) part += y[i] * x[i];
+        double dot = block_sum(part, red);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] -= dot * y[i];
+        __syncthreads();
+      }
+      double part = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) part += x[i] * x[i];
+      double nr = block_sum(part, red);
+      double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] *= inv;
+      __syncthreads();
+      if (iter == 2) break;
+      if (threadIdx.x == 0) {
+        // solve P L U y = x: apply L^-1 (with the row swaps), then U^-1
+        for (int i = 0; i < n - 1; ++i) {
+          if (fp[i] != 0.0) { double t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+          x[i + 1] -= fl[i] * x[i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+          double v = x[i];
+          if (i + 1 < n) v -= fu[i] * x[i + 1];
+          if (i + 2 < n) v -= fu2[i] * x[i + 2];
+          x[i] = v / fd[i];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// X = H_0 H_1 ... H_{n-3} Z, one warp per column; then the sign convention and
+// the transpose into v (n x nvec row-major).
+__global__ void backtransform_kernel(EigState st, int nvec, double* __restrict__ v) {
+  const int n = st.n;
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= nvec) return;
+  constexpr int MAXPER = 32;  // n <= 1024
+  double z[MAXPER];
+  const double* zc = st.z + (int64_t)col * n;
+#pragma unroll
+  for (int q = 0; q < MAXPER; ++q) {
+    int i = lane + 32 * q;
+    z[q] = (i < n) ? zc[i] : 0.0;
+  }
+  for (int s = n - 3; s >= 0; --s) {
+    const double t = st.tau[s];
+    if (t == 0.0) continue;
+    const double* hv = st.hv + (int64_t)s * n;
+    double part = 0.0;
+#pragma unroll
+    for (int q = 0; q < MAXPER; ++q) {
+      int i = lane + 32 * q;
+      if (i > s && i < n) part = fma(__ldg(hv + i), z[q], part);
+    }
+    double dot = warp_sum(part) * t;
+#pragma unroll
+    for (int q = 0; q < MAXPER; ++q) {
+      int i = lane + 32 * q;
+      if (i > s && i < n) z[q] -= dot * __ldg(hv + i);
+    }
+  }
+  // sign: entry of largest magnitude (first on ties) positive
+  double best = -1.0;
+  int bidx = n;
+  double bval = 0.0;
+#pragma unroll
+  for (int q = 0; q < MAXPER; ++q) {
+    int i = lane + 32 * q;
+    if (i < n) {
+      double a = fabs(z[q]);
+      if (a > best) { best = a; bidx = i; bval = z[q]; }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    double ov = __shfl_xor_sync(0xffffffffu, bval, o);
+    if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; bval = ov; }
+  }
+  const double sg = (bval < 0.0) ? -1.0 : 1.0;
+#pragma unroll
+  for (int q = 0; q < MAXPER; ++q) {
+    int i = lane + 32 * q;
+    if (i < n) v[(int64_t)i * nvec + col] = sg * z[q];
+  }
+}
+
+// lam_out[j] = lam_scaled[j] / scale (exact power of two)
+__global__ void unscale_kernel(EigState st, double* __restrict__ lam_out) {
+  const double inv = 1.0 / st.scale[0];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < st.n; j += gridDim.x * blockDim.x)
+    lam_out[j] = st.lam[j] * inv;
+}
+
+// Group consecutive eigenvalues (descending, scaled) whose gap is below tol.
+__global__ void group_kernel(EigState st, int nvec, int* grp_start, int* ngrp) {
+  if (threadIdx.x != 0) return;
+  const double tol = 0x1p-10;  // |T| <= 1: gaps below ~1e-3 |T| are re-orthogonalised (as in LAPACK stein)
+  int g = 0;
+  grp_start[0] = 0;
+  for (int j = 1; j < nvec; ++j) {
+    if (st.lam[j - 1] - st.lam[j] > tol) grp_start[++g] = j;
+  }
+  grp_start[++g] = nvec;
+  *ngrp = g;
+}
+
+// Rank choice: clamp at 0, tail sums from the smallest value, smallest r >= 1
+// with t[r] <= budget (Section 4.1.3).
+__global__ void rank_kernel(const double* __restrict__ lam, int n, double budget, int* r_out, double* disc_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double acc = 0.0;
+  int r = n;
+  double disc = 0.0;
+  // t[r] for r = n .. 1: t[n] = 0
+  if (0.0 <= budget) { r = n; disc = 0.0; }
+  for (int j = n - 1; j >= 1; --j) {
+    acc += fmax(lam[j], 0.0);  // acc = t[j]
+    if (acc <= budget) { r = j; disc = acc; }
+    else break;  // t[j] is non-increasing in j: once over budget, smaller r are too
+  }
+  *r_out = r;
+  *disc_out = disc;
+}
+
+int setup_state(int n, int nvec_max) {
+  EigState st;
+  st.n = n;
+  size_t nn = (size_t)n * n;
+  ATC_TRY(Scratch::get(SLOT_EIG_A, sizeof(double) * nn, (void**)&st.a));
+  ATC_TRY(Scratch::get(SLOT_EIG_V, sizeof(double) * nn, (void**)&st.hv));
+  double* vec = nullptr;
+  const size_t nv = (size_t)n * 8 + 64;
+  ATC_TRY(Scratch::get(SLOT_EIG_VEC, sizeof(double) * nv + 4096, (void**)&vec));
+  st.d = vec;
+  st.e = vec + n;
+  st.tau = vec + 2 * n;
+  st.pbuf = vec + 3 * n;  // 2n
+  st.lam = vec + 5 * n;
+  st.scale = vec + 6 * n;
+  st.flags = reinterpret_cast<int*>(vec + 6 * n + 8);
+  st.z = nullptr;
+  st.lu = nullptr;
+  (void)nvec_max;
+  g_state = st;
+  return ATC_OK;
+}
+
+}  // namespace
+
+int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s) {
+  if (n < 1 || n > 1024) return fail(ATC_EUNSUP, "eigensolver supports 1 <= n <= 1024 (n = %d)", n);
+  ATC_TRY(setup_state(n, n));
+  EigState st = g_state;
+  ATC_CUDA_TRY(cudaMemcpyAsync(st.a, g, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+  ATC_CUDA_TRY(cudaMemsetAsync(st.flags, 0, 4 * sizeof(int), s));
+  ATC_CUDA_TRY(cudaMemsetAsync(st.d, 0, sizeof(double) * 3 * n, s));
+  if (n == 1) {
+    tridiag_small_kernel<<<1, 32, 0, s>>>(st);
+    ATC_CUDA_TRY(cudaGetLastError());
+  } else {
+    static int max_blocks = -1;
+    const size_t smem = sizeof(double) * (4 * n + 32);
+    if (max_blocks < 0) {
+      int dev = 0, nsm = 0, per = 0;
+      ATC_CUDA_TRY(cudaGetDevice(&dev));
+      ATC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      ATC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel, kTriThreads,
+                                                                 sizeof(double) * (4 * 1024 + 32)));
+      max_blocks = nsm * (per > 0 ? 1 : 0);
+      if (max_blocks <= 0) return fail(ATC_ECUDA, "tridiagonalisation kernel cannot be resident");
+    }
+    // about 4 rows per CTA, at most one CTA per SM
+    int P = (n + 3) / 4;
+    if (P > max_blocks) P = max_blocks;
+    if (P > 128) P = 128;
+    if (P < 1) P = 1;
+    void* args[] = {(void*)&st};
+    ATC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tridiag_kernel, dim3(P), dim3(kTriThreads), args, smem, s));
+  }
+  scale_kernel<<<1, 256, 0, s>>>(st);
+  ATC_CUDA_TRY(cudaGetLastError());
+  const int bt = 64;
+  bisect_kernel<<<(n + bt - 1) / bt, bt, sizeof(double) * 2 * n, s>>>(st);
+  ATC_CUDA_TRY(cudaGetLastError());
+  if (lam) {
+    unscale_kernel<<<(n + 255) / 256, 256, 0, s>>>(st, lam);
+    ATC_CUDA_TRY(cudaGetLastError());
+  }
+  return ATC_OK;
+}
+
+int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
+  if (nvec <= 0) return ATC_OK;
+  if (g_state.n != n) return fail(ATC_EINVAL, "eigenvectors requested without matching eigenvalues");
+  EigState st = g_state;
+  ATC_TRY(Scratch::get(SLOT_EIG_Z, sizeof(double) * ((size_t)n * nvec * 6 + 2 * (size_t)nvec + 64), (void**)&st.z));
+  st.lu = st.z + (size_t)n * nvec;
+  int* grp = reinterpret_cast<int*>(st.lu + (size_t)5 * n * nvec);
+  int* ngrp = grp + nvec + 2;
+  group_kernel<<<1, 32, 0, s>>>(st, nvec, grp, ngrp);
+  ATC_CUDA_TRY(cudaGetLastError());
+  // one CTA per group; groups beyond the actual count exit (grp_start padded)
+  // launch nvec CTAs, CTAs with blockIdx >= ngrp have an empty range
+  invit_kernel<<<nvec, 128, 0, s>>>(st, grp, ngrp, nvec);
+  ATC_CUDA_TRY(cudaGetLastError());
+  const int wpb = 4;
+  backtransform_kernel<<<(nvec + wpb - 1) / wpb, 32 * wpb, 0, s>>>(st, nvec, v);
+  ATC_CUDA_TRY(cudaGetLastError());
+  return ATC_OK;
+}
+
+int launch_eig_sym(const double* g, int n, double* lam, double* v, int nvec, cudaStream_t s) {
+  ATC_TRY(launch_eig_values(g, n, lam, s));
+  ATC_TRY(launch_eig_vectors(n, nvec, v, s));
+  return ATC_OK;
+}
+
+int launch_rank_select(const double* lam, int n, double budget, int* r_dev, double* disc_dev, cudaStream_t s) {
+  rank_kernel<<<1, 32, 0, s>>>(lam, n, budget, r_dev, disc_dev);
+  ATC_CUDA_TRY(cudaGetLastError());
+  return ATC_OK;
+}
+
+int eig_read_error(int* err) {
+  return cudaMemcpy(err, g_state.flags + 2, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? ATC_OK : ATC_ECUDA;
+}
+
+}  // namespace atc

@@ -1,0 +1,220 @@
+// Plain FP64 SIMT contractions: the mode Gram matrix and the mode-k product.
+//
+// These are the "plain FP64" path: every product and every sum in FP64 (DFMA).
+// Both read the tensor through the (L, n, R) view of Section 3.1 -- the
+// mode-k unfolding is formed by index arithmetic, never by a transpose.
+//
+//   Gram:  G[i][j] = sum_{l,c} X[l][i][c] X[l][j][c]      (only i-tile <= j-tile
+//          is computed; split-K partials are summed in a fixed order)
+//   TTM :  Y[l][a][c] = sum_b W[a][b] X[l][b][c]          (W = U^T or U)
+#include <stdint.h>
+
+#include "atc_internal.cuh"
+
+namespace atc {
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int kThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ double ld(const T* p) { return (double)__ldg(p); }
+
+// Element (row i, column kappa) of the mode unfolding of an (L, n, R) tensor.
+__device__ __forceinline__ int64_t unfold_off(int64_t i, int64_t kappa, int64_t n, int64_t R) {
+  int64_t l = kappa / R, c = kappa - l * R;
+  return (l * n + i) * R + c;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) gram_fp64_kernel(const T* __restrict__ x, int64_t n, int64_t R,
+                                                             int64_t K, int64_t kchunk, int ntile,
+                                                             double* __restrict__ part) {
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+  // decode the upper-triangular tile pair (ti <= tj)
+  int t = blockIdx.x, ti = 0;
+  while (t >= ntile - ti) { t -= ntile - ti; ++ti; }
+  const int tj = ti + t;
+  const int64_t i0 = (int64_t)ti * TM, j0 = (int64_t)tj * TN;
+  const int64_t k_begin = (int64_t)blockIdx.y * kchunk;
+  const int64_t k_end = min(K, k_begin + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  const bool kfast = R >= TK;
+  for (int64_t k0 = k_begin; k0 < k_end; k0 += TK) {
+#pragma unroll
+    for (int e = 0; e < (TM * TK) / kThreads; ++e) {
+      int idx = threadIdx.x + e * kThreads;
+      int rr, kk;
+      if (kfast) { kk = idx % TK; rr = idx / TK; } else { rr = idx % TM; kk = idx / TM; }
+      int64_t kappa = k0 + kk;
+      double va = 0.0, vb = 0.0;
+      if (kappa < k_end) {
+        if (i0 + rr < n) va = ld(x + unfold_off(i0 + rr, kappa, n, R));
+        if (j0 + rr < n) vb = ld(x + unfold_off(j0 + rr, kappa, n, R));
+      }
+      As[kk][rr] = va;
+      Bs[kk][rr] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = As[kk][ty + 16 * q]; b[q] = Bs[kk][tx + 16 * q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.y * n * n;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    int64_t i = i0 + ty + 16 * p;
+    if (i >= n) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int64_t j = j0 + tx + 16 * q;
+      if (j < n) out[i * n + j] = acc[p][q];
+    }
+  }
+}
+
+// G[i][j] = G[j][i] = sum_s part[s][min-tile entry], summed in split order.
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int nsplit, int64_t n, double* __restrict__ g) {
+  int64_t total = n * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = idx / n, j = idx - i * n;
+    // the computed entry lives in the upper tile (tile(i) <= tile(j)) -- pick the
+    // orientation whose row tile is <= its column tile
+    int64_t si = i, sj = j;
+    if (i / TM > j / TN) { si = j; sj = i; }
+    double acc = 0.0;
+    for (int s = 0; s < nsplit; ++s) acc += part[(int64_t)s * n * n + si * n + sj];
+    g[idx] = acc;
+  }
+}
+
+template <typename TX, typename TY>
+__global__ void __launch_bounds__(kThreads) ttm_fp64_kernel(const TX* __restrict__ x, const double* __restrict__ w,
+                                                            int64_t wsa, int64_t wsb, int64_t A, int64_t B,
+                                                            int64_t R, int64_t N, TY* __restrict__ y) {
+  __shared__ double Ws[TK][TM + 1];
+  __shared__ double Xs[TK][TN + 1];
+  const int64_t a0 = (int64_t)blockIdx.y * TM, g0 = (int64_t)blockIdx.x * TN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0.0;
+  for (int64_t b0 = 0; b0 < B; b0 += TK) {
+#pragma unroll
+    for (int e = 0; e < (TM * TK) / kThreads; ++e) {
+      int idx = threadIdx.x + e * kThreads;
+      // W tile: rows a, columns b
+      int aa = idx / TK, bb = idx % TK;
+      double wv = 0.0;
+      if (a0 + aa < A && b0 + bb < B) wv = w[(a0 + aa) * wsa + (b0 + bb) * wsb];
+      Ws[bb][aa] = wv;
+      // X tile: rows b, columns gamma (gamma fastest for coalescing)
+      int gg = idx % TN, bx = idx / TN;
+      double xv = 0.0;
+      int64_t gamma = g0 + gg, b = b0 + bx;
+      if (gamma < N && b < B) {
+        int64_t l = gamma / R, c = gamma - l * R;
+        xv = (double)__ldg(x + (l * B + b) * R + c);
+      }
+      Xs[bx][gg] = xv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = Ws[kk][ty + 16 * q]; b[q] = Xs[kk][tx + 16 * q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    int64_t a = a0 + ty + 16 * p;
+    if (a >= A) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int64_t gamma = g0 + tx + 16 * q;
+      if (gamma >= N) continue;
+      int64_t l = gamma / R, c = gamma - l * R;
+      y[(l * A + a) * R + c] = (TY)acc[p][q];
+    }
+  }
+}
+
+}  // namespace
+
+int launch_gram_fp64(const void* x, int dtype, int64_t L, int64_t n, int64_t R, double* g, cudaStream_t s) {
+  const int64_t K = L * R;
+  const int ntile = (int)((n + TM - 1) / TM);
+  const int npairs = ntile * (ntile + 1) / 2;
+  // split K so that the grid covers the GPU a few times over
+  int64_t nsplit = (4 * 152 + npairs - 1) / npairs;
+  int64_t maxsplit = (K + 255) / 256;
+  if (nsplit > maxsplit) nsplit = maxsplit;
+  // keep the partial buffer within 64 MB
+  while (nsplit > 1 && nsplit * n * n * 8 > (64ll << 20)) nsplit--;
+  if (nsplit < 1) nsplit = 1;
+  int64_t kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = (kchunk + TK - 1) / TK * TK;
+  nsplit = (K + kchunk - 1) / kchunk;
+  if (nsplit < 1) nsplit = 1;
+  double* part = nullptr;
+  ATC_TRY(Scratch::get(SLOT_GRAM_PART, sizeof(double) * nsplit * n * n, (void**)&part));
+  dim3 grid(npairs, (unsigned)nsplit);
+  if (dtype == ATC_F32)
+    gram_fp64_kernel<float><<<grid, kThreads, 0, s>>>((const float*)x, n, R, K, kchunk, ntile, part);
+  else
+    gram_fp64_kernel<double><<<grid, kThreads, 0, s>>>((const double*)x, n, R, K, kchunk, ntile, part);
+  ATC_CUDA_TRY(cudaGetLastError());
+  int64_t tot = n * n;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  gram_reduce_kernel<<<blocks, 256, 0, s>>>(part, (int)nsplit, n, g);
+  ATC_CUDA_TRY(cudaGetLastError());
+  return ATC_OK;
+}
+
+int launch_ttm_fp64(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
+                    int expand, void* y, int ydtype, cudaStream_t s) {
+  // project: A = r, B = n, W[a][b] = U[b][a]  -> wsa = 1, wsb = r
+  // expand : A = n, B = r, W[a][b] = U[a][b]  -> wsa = r, wsb = 1
+  const int64_t A = expand ? n : r, B = expand ? r : n;
+  const int64_t wsa = expand ? r : 1, wsb = expand ? 1 : r;
+  const int64_t N = L * R;
+  if (N == 0 || A == 0) return ATC_OK;
+  dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((A + TM - 1) / TM));
+  if (grid.y > 65535) return fail(ATC_EUNSUP, "ttm: output mode too large");
+  if (xdtype == ATC_F32 && ydtype == ATC_F32)
+    ttm_fp64_kernel<float, float><<<grid, kThreads, 0, s>>>((const float*)x, u, wsa, wsb, A, B, R, N, (float*)y);
+  else if (xdtype == ATC_F32 && ydtype == ATC_F64)
+    ttm_fp64_kernel<float, double><<<grid, kThreads, 0, s>>>((const float*)x, u, wsa, wsb, A, B, R, N, (double*)y);
+  else if (xdtype == ATC_F64 && ydtype == ATC_F32)
+    ttm_fp64_kernel<double, float><<<grid, kThreads, 0, s>>>((const double*)x, u, wsa, wsb, A, B, R, N, (float*)y);
+  else
+    ttm_fp64_kernel<double, double><<<grid, kThreads, 0, s>>>((const double*)x, u, wsa, wsb, A, B, R, N, (double*)y);
+  ATC_CUDA_TRY(cudaGetLastError());
+  return ATC_OK;
+}
+
+}  // namespace atc

@@ -1,0 +1,980 @@
+// Core quantization, exact bit-plane tracking, breakpoint and block encoding.
+//
+// Section 3.3: scale by 2^k with 2^63 <= 2^k max|b| < 2^64, round to the nearest
+//   integer (ties to even); bit planes from 63 downward, bit by bit in
+//   vectorised order, tracking the error of encoding every bit so far; the
+//   breakpoint is the first bit whose tracked error is <= the target.
+//   Leading bits (up to a coefficient's first 1) are run-length coded per
+//   plane, signs of newly significant coefficients and trailing bits are raw.
+// Section 4.2: contiguous blocks encoded independently + a size table.
+// Section 4.3: a coefficient known down to plane p is rebuilt as a~ + 2^(p-1);
+//   the tracker uses the same reconstruction.
+// Supplement S.6: run lengths are range-ANS coded (static per-plane tables).
+//
+// Tracking is exact: per-coefficient errors are integers < 2^128 (units of
+// 2^-2k), per-plane sums are 192-bit two's-complement integers, so the
+// breakpoint is independent of the reduction order.  Per plane p the tracker
+// needs S_p = sum_i D_i(p) and the largest prefix sum M_p of
+// D_i(p) = e_i(p+1) - e_i(p); segments combine as
+// (S1, M1) + (S2, M2) = (S1 + S2, max(M1, S1 + M2)), an associative
+// (order-preserving) reduction.  The first plane with E(p+1) - M_p <= T holds
+// the breakpoint.
+//
+// Stream section "ATCQ" (little-endian):
+//   char[4] "ATCQ" | u32 1 | u64 n | i32 k | u32 block_size | i32 p_star | u32 0 |
+//   u64 i_star | u32 nplanes | u32 17 | u16 freq[nplanes][17] |
+//   u32 sizes[nblocks][nplanes][2] (rANS bytes, raw bytes) | payload
+//   (per block, per plane 63 .. p_star: rANS bytes then raw bytes).
+// Run r >= 0 -> symbol s = floor(log2(r+1)) coded with the plane's table, then
+// s extra bits (r + 1 - 2^s) coded as a uniform symbol; 32-bit rANS state,
+// L = 2^23, byte-wise renormalisation, 12-bit frequencies.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "atc_internal.cuh"
+
+namespace atc {
+namespace {
+
+typedef unsigned __int128 u128;
+constexpr int kNsym = 17;
+constexpr int kScaleBits = 12;
+constexpr uint32_t kM = 1u << kScaleBits;
+constexpr uint32_t kRansL = 1u << 23;
+constexpr int kPlaneChunk = 16;       // planes per tracker pass
+constexpr int kSegBlocks = 304;       // 2 x 152 SMs
+constexpr int kSegThreads = 256;
+
+// ------------------------------------------------------------ 192-bit signed
+struct I192 {
+  uint64_t w0, w1, w2;
+};
+__host__ __device__ __forceinline__ I192 i192_zero() { return {0, 0, 0}; }
+__host__ __device__ __forceinline__ I192 i192_from_u128(u128 v) { return {(uint64_t)v, (uint64_t)(v >> 64), 0}; }
+__host__ __device__ __forceinline__ I192 i192_add(I192 a, I192 b) {
+  I192 r;
+  u128 s = (u128)a.w0 + b.w0;
+  r.w0 = (uint64_t)s;
+  s = (u128)a.w1 + b.w1 + (uint64_t)(s >> 64);
+  r.w1 = (uint64_t)s;
+  r.w2 = a.w2 + b.w2 + (uint64_t)(s >> 64);
+  return r;
+}
+__host__ __device__ __forceinline__ I192 i192_neg(I192 a) {
+  I192 r = {~a.w0, ~a.w1, ~a.w2};
+  return i192_add(r, {1, 0, 0});
+}
+__host__ __device__ __forceinline__ I192 i192_sub(I192 a, I192 b) { return i192_add(a, i192_neg(b)); }
+__host__ __device__ __forceinline__ bool i192_lt(I192 a, I192 b) {  // signed
+  if (a.w2 != b.w2) return (int64_t)a.w2 < (int64_t)b.w2;
+  if (a.w1 != b.w1) return a.w1 < b.w1;
+  return a.w0 < b.w0;
+}
+__host__ __device__ __forceinline__ bool i192_le(I192 a, I192 b) { return !i192_lt(b, a); }
+// (u128 a) - (u128 b) as a signed 192-bit value
+__host__ __device__ __forceinline__ I192 i192_diff(u128 a, u128 b) { return i192_sub(i192_from_u128(a), i192_from_u128(b)); }
+
+// Ordered segment summary of one plane: sum and largest prefix sum.
+struct Seg {
+  I192 s, m;
+  int empty;
+};
+__device__ __forceinline__ Seg seg_combine(const Seg& a, const Seg& b) {
+  if (a.empty) return b;
+  if (b.empty) return a;
+  Seg r;
+  r.s = i192_add(a.s, b.s);
+  I192 t = i192_add(a.s, b.m);
+  r.m = i192_lt(a.m, t) ? t : a.m;
+  r.empty = 0;
+  return r;
+}
+
+// Error of one coefficient once every plane >= p is known (p in [0, 64]).
+__device__ __forceinline__ u128 coef_err(uint64_t q, int p) {
+  if (p >= 64 || (q >> p) == 0) return (u128)q * q;
+  if (p == 0) return 0;
+  const uint64_t rem = q & ((1ull << p) - 1ull);
+  const uint64_t c = 1ull << (p - 1);
+  const uint64_t d = (rem >= c) ? rem - c : c - rem;
+  return (u128)d * d;
+}
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ uint64_t shfl_down_u64(uint64_t v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
+__device__ Seg warp_seg_reduce(Seg x) {
+  // ordered tree: lane i combines with lane i + off (i is the left operand)
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    Seg o;
+    o.s.w0 = shfl_down_u64(x.s.w0, off);
+    o.s.w1 = shfl_down_u64(x.s.w1, off);
+    o.s.w2 = shfl_down_u64(x.s.w2, off);
+    o.m.w0 = shfl_down_u64(x.m.w0, off);
+    o.m.w1 = shfl_down_u64(x.m.w1, off);
+    o.m.w2 = shfl_down_u64(x.m.w2, off);
+    o.empty = __shfl_down_sync(0xffffffffu, x.empty, off);
+    const int lane = threadIdx.x & 31;
+    if ((lane & (2 * off - 1)) == 0 && lane + off < 32) x = seg_combine(x, o);
+  }
+  return x;
+}
+
+// --------------------------------------------------------------- quantizer
+__global__ void maxabs_kernel(const double* __restrict__ b, int64_t n, unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a = fabs(b[i]);
+    if (!(a <= m)) m = a;  // NaN propagates
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double t = __shfl_xor_sync(0xffffffffu, m, o);
+    if (!(t <= m)) m = t;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));  // |x| bit patterns order like values
+}
+
+// 2^k * a for a >= 0 with k in [-1074, 1138]; exact whenever the result is normal
+__device__ __forceinline__ double mul_pow2(double a, int k) {
+  if (k > 1023) return (a * __longlong_as_double((int64_t)(k - 1023 + 1023) << 52)) * 0x1p1023;
+  if (k < -1022) return (a * 0x1p-1022) * __longlong_as_double((int64_t)(k + 1022 + 1023) << 52);
+  return a * __longlong_as_double((int64_t)(k + 1023) << 52);
+}
+
+__global__ void quantize_kernel(const double* __restrict__ b, int64_t n, const int* __restrict__ kp,
+                                uint64_t* __restrict__ q, uint8_t* __restrict__ sg) {
+  const int k = *kp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[i];
+    q[i] = __double2ull_rn(mul_pow2(fabs(v), k));
+    sg[i] = signbit(v) ? 1 : 0;
+  }
+}
+
+struct TrackState {
+  // device scalars
+  int k;
+  int nan;
+  int p_star;
+  int found;
+  int64_t i_star;
+  I192 t_int;     // floor(target * 2^(2k)), valid if reachable
+  int reachable;
+  int pad;
+  I192 e_next;    // E(p+1) for the next unexamined plane
+  I192 e64;
+  I192 e_star;    // tracked error at the breakpoint
+  I192 e_plane;   // E(p_star + 1)
+};
+
+__global__ void scale_exp_kernel(const unsigned long long* __restrict__ mx, double target, TrackState* st) {
+  if (threadIdx.x != 0) return;
+  const double m = __longlong_as_double((long long)*mx);
+  int k = 0;
+  st->nan = !(m == m) || isinf(m);
+  if (m > 0.0 && !st->nan) {
+    int e;
+    frexp(m, &e);
+    k = 64 - e;
+  }
+  st->k = k;
+  // T_int = floor(target * 2^(2k)) as 192-bit (target < 0: unreachable)
+  I192 t = i192_zero();
+  int reach = 0;
+  if (target >= 0.0) {
+    reach = 1;
+    if (isinf(target)) {
+      t = {~0ull, ~0ull, 0x7fffffffffffffffull};
+    } else if (target > 0.0) {
+      int e;
+      double f = frexp(target, &e);
+      uint64_t mant = (uint64_t)(f * 9007199254740992.0);  // f * 2^53, exact
+      int sh = e - 53 + 2 * k;
+      if (sh >= 0) {
+        if (sh + 53 > 190) {
+          t = {~0ull, ~0ull, 0x7fffffffffffffffull};
+        } else {
+          int limb = sh / 64, bit = sh % 64;
+          uint64_t w[3] = {0, 0, 0};
+          w[limb] = mant << bit;
+          if (bit && limb + 1 < 3) w[limb + 1] = mant >> (64 - bit);
+          t = {w[0], w[1], w[2]};
+        }
+      } else {
+        int r = -sh;
+        t = {r >= 64 ? 0ull : (mant >> r), 0, 0};
+      }
+    }
+  }
+  st->t_int = t;
+  st->reachable = reach;
+  st->found = 0;
+  st->p_star = -1;
+}
+
+// Per segment (one CTA, contiguous coefficients) and plane p in [plo, plo+15]:
+// the ordered summary of D_i(p); plus sum q_i^2 when first_pass.
+__global__ void __launch_bounds__(kSegThreads) plane_stats_kernel(const uint64_t* __restrict__ q, int64_t n,
+                                                                   int64_t seg_len, int plo, int phi, int first_pass,
+                                                                   Seg* __restrict__ out, I192* __restrict__ e64_out) {
+  __shared__ Seg wsum[kSegThreads / 32];
+  const int64_t s_lo = blockIdx.x * seg_len;
+  const int64_t s_hi = min(n, s_lo + seg_len);
+  const int64_t per = (seg_len + blockDim.x - 1) / blockDim.x;
+  const int64_t t_lo = min(s_hi, s_lo + threadIdx.x * per);
+  const int64_t t_hi = min(s_hi, t_lo + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (first_pass) {
+    Seg a;
+    a.s = i192_zero();
+    a.m = i192_zero();
+    a.empty = (t_lo >= t_hi);
+    for (int64_t i = t_lo; i < t_hi; ++i) a.s = i192_add(a.s, i192_from_u128((u128)q[i] * q[i]));
+    a.m = a.s;
+    Seg r = warp_seg_reduce(a);
+    if (lane == 0) wsum[warp] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Seg t = wsum[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = seg_combine(t, wsum[w]);
+      e64_out[blockIdx.x] = t.empty ? i192_zero() : t.s;
+    }
+    __syncthreads();
+  }
+  for (int p = phi; p >= plo; --p) {
+    Seg a;
+    a.s = i192_zero();
+    a.m = i192_zero();
+    a.empty = 1;
+    for (int64_t i = t_lo; i < t_hi; ++i) {
+      const uint64_t v = q[i];
+      I192 d = i192_zero();
+      if ((v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+      if (a.empty) { a.s = d; a.m = d; a.empty = 0; }
+      else {
+        a.s = i192_add(a.s, d);
+        if (i192_lt(a.m, a.s)) a.m = a.s;
+      }
+    }
+    Seg r = warp_seg_reduce(a);
+    if (lane == 0) wsum[warp] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Seg t = wsum[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = seg_combine(t, wsum[w]);
+      out[(int64_t)(phi - p) * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Combine the segment summaries in order and look for the first plane whose
+// lowest running error reaches the target.
+__global__ void plane_scan_kernel(const Seg* __restrict__ segs, const I192* __restrict__ e64_seg, int nseg, int plo,
+                                  int phi, int first_pass, TrackState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (st->found) return;
+  if (first_pass) {
+    I192 e = i192_zero();
+    for (int b = 0; b < nseg; ++b) e = i192_add(e, e64_seg[b]);
+    st->e64 = e;
+    st->e_next = e;
+    if (st->reachable && i192_le(e, st->t_int)) {
+      st->found = 1;
+      st->p_star = 64;
+      st->i_star = -1;  // fixed up by the host to n-1
+      st->e_star = e;
+      st->e_plane = e;
+      return;
+    }
+  }
+  I192 e_next = st->e_next;
+  for (int p = phi; p >= plo; --p) {
+    Seg t;
+    t.empty = 1;
+    t.s = t.m = i192_zero();
+    for (int b = 0; b < nseg; ++b) t = seg_combine(t, segs[(int64_t)(phi - p) * nseg + b]);
+    if (t.empty) { t.s = t.m = i192_zero(); }
+    I192 lowest = i192_sub(e_next, t.m);
+    if (st->reachable && i192_le(lowest, st->t_int)) {
+      st->found = 1;
+      st->p_star = p;
+      st->e_plane = e_next;
+      return;
+    }
+    e_next = i192_sub(e_next, t.s);
+  }
+  st->e_next = e_next;
+  if (plo == 0) {  // target unreachable: everything encoded
+    st->found = 1;
+    st->p_star = 0;
+    st->i_star = -1;
+    st->e_star = e_next;
+    st->e_plane = e_next;  // unused
+  }
+}
+
+// Exact position of the breakpoint inside plane p_star: one CTA walks the
+// segment summaries, then re-scans the segment that holds it.
+__global__ void __launch_bounds__(kSegThreads) istar_kernel(const uint64_t* __restrict__ q, int64_t n, int64_t seg_len,
+                                                             const Seg* __restrict__ segs, int nseg, int phi,
+                                                             TrackState* st) {
+  __shared__ Seg tsum[kSegThreads];
+  __shared__ int s_seg;
+  __shared__ I192 s_pre;
+  __shared__ int64_t s_hit;
+  const int p = st->p_star;
+  if (p >= 64) return;
+  const I192 T = st->t_int;
+  const I192 E1 = st->e_plane;
+  if (!st->reachable) return;  // i_star stays -1 (everything encoded)
+  if (threadIdx.x == 0) {
+    I192 pre = i192_zero();
+    int found = -1;
+    for (int b = 0; b < nseg; ++b) {
+      const Seg& sgm = segs[(int64_t)(phi - p) * nseg + b];
+      if (!sgm.empty) {
+        I192 low = i192_sub(E1, i192_add(pre, sgm.m));
+        if (i192_le(low, T)) { found = b; break; }
+        pre = i192_add(pre, sgm.s);
+      }
+    }
+    s_seg = found;
+    s_pre = pre;
+    s_hit = INT64_MAX;
+  }
+  __syncthreads();
+  const int b = s_seg;
+  if (b < 0) return;  // cannot happen when p_star came from plane_scan_kernel
+  const int64_t s_lo = b * seg_len;
+  const int64_t s_hi = min(n, s_lo + seg_len);
+  const int64_t per = (seg_len + blockDim.x - 1) / blockDim.x;
+  const int64_t t_lo = min(s_hi, s_lo + threadIdx.x * per);
+  const int64_t t_hi = min(s_hi, t_lo + per);
+  Seg a;
+  a.empty = 1;
+  a.s = a.m = i192_zero();
+  for (int64_t i = t_lo; i < t_hi; ++i) {
+    const uint64_t v = q[i];
+    I192 d = i192_zero();
+    if ((v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+    if (a.empty) { a.s = d; a.m = d; a.empty = 0; }
+    else {
+      a.s = i192_add(a.s, d);
+      if (i192_lt(a.m, a.s)) a.m = a.s;
+    }
+  }
+  tsum[threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // exclusive prefixes in thread order; first thread whose range reaches T
+    I192 pre = s_pre;
+    int hit_t = -1;
+    I192 hit_pre = pre;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const Seg& x = tsum[t];
+      if (x.empty) continue;
+      if (i192_le(i192_sub(E1, i192_add(pre, x.m)), T)) { hit_t = t; hit_pre = pre; break; }
+      pre = i192_add(pre, x.s);
+    }
+    if (hit_t >= 0) {
+      const int64_t lo = min(s_hi, s_lo + hit_t * per), hi = min(s_hi, lo + per);
+      I192 run = i192_sub(E1, hit_pre);
+      for (int64_t i = lo; i < hi; ++i) {
+        const uint64_t v = q[i];
+        I192 d = i192_zero();
+        if ((v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+        run = i192_sub(run, d);
+        if (i192_le(run, T)) {
+          st->i_star = i;
+          st->e_star = run;
+          break;
+        }
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------------------- encoder
+struct EncParams {
+  const uint64_t* q;
+  const uint8_t* sg;
+  int64_t n;
+  int block_size;
+  int p_star;
+  int64_t i_star;
+  int nplanes;
+  int64_t nblocks;
+  unsigned long long* hist;  // nplanes x 17
+  const uint32_t* freq;      // nplanes x 17 (then cum at +nplanes*17)
+  uint32_t* rsize;           // nchunks
+  uint32_t* wsize;           // nchunks
+  const uint64_t* off;       // nchunks + 1 (payload offsets)
+  uint8_t* out;              // payload base
+  uint32_t* table;           // size table (nblocks x nplanes x 2)
+};
+
+__device__ __forceinline__ int bucket_of(uint32_t v) { return 31 - __clz(v + 1u); }
+
+// Warp walk of one (block, plane) chunk.  For every run (in order) calls
+// on_run(run); raw bits are reported per 32-coefficient group as
+// (packed value, count).  Returns via the callbacks only.
+template <typename RunF, typename RawF>
+__device__ __forceinline__ void chunk_walk(const EncParams& P, int64_t lo, int64_t hi, int p, RunF on_run, RawF on_raw) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t carry = 0;  // zeros since the last 1 (leading subsequence)
+  for (int64_t g = lo; g < hi; g += 32) {
+    const int64_t j = g + lane;
+    const bool in = j < hi;
+    uint64_t v = in ? P.q[j] : 0;
+    const bool bit = (v >> p) & 1ull;
+    const bool sigb = (p == 63) ? false : ((v >> (p + 1)) != 0ull);
+    const bool lead = in && !sigb;
+    const bool one = lead && bit;
+    const bool rawp = in && (sigb || one);
+    const bool rawv = sigb ? bit : (one ? (P.sg[j] != 0) : false);
+    const unsigned lead_m = __ballot_sync(0xffffffffu, lead);
+    const unsigned one_m = __ballot_sync(0xffffffffu, one);
+    const unsigned raw_m = __ballot_sync(0xffffffffu, rawp);
+    // raw bits packed in order of position
+    const int rank = __popc(raw_m & lt);
+    const unsigned packed = __reduce_or_sync(0xffffffffu, (rawp && rawv) ? (1u << rank) : 0u);
+    on_raw(packed, __popc(raw_m));
+    // runs: each 1 ends a run of the leading zeros since the previous 1
+    const unsigned zero_m = lead_m & ~one_m;
+    unsigned ones = one_m;
+    while (ones) {
+      const int l = __ffs(ones) - 1;
+      ones &= ones - 1u;
+      // zeros strictly before lane l since the previous processed 1 (tracked by carry)
+      const unsigned below = (l == 0) ? 0u : ((1u << l) - 1u);
+      const unsigned prevmask = one_m & below;
+      unsigned from;
+      uint32_t run;
+      if (prevmask) {
+        const int pl = 31 - __clz(prevmask);
+        from = (pl == 31) ? 0u : ~((2u << pl) - 1u);
+        run = __popc(zero_m & below & from);
+      } else {
+        run = carry + __popc(zero_m & below);
+      }
+      on_run(run);
+    }
+    if (one_m) {
+      const int ll = 31 - __clz(one_m);
+      const unsigned above = (ll == 31) ? 0u : ~((2u << ll) - 1u);
+      carry = __popc(zero_m & above);
+    } else {
+      carry += __popc(zero_m);
+    }
+  }
+  if (carry > 0) on_run(carry);
+}
+
+__device__ __forceinline__ void chunk_range(const EncParams& P, int64_t blk, int p, int64_t* lo, int64_t* hi) {
+  int64_t a = blk * P.block_size, b = min(P.n, a + P.block_size);
+  if (p == P.p_star && b > P.i_star + 1) b = max(a, P.i_star + 1);
+  *lo = a;
+  *hi = b;
+}
+
+// pass 1: per-plane histograms of run symbols and raw byte counts
+__global__ void enc_hist_kernel(EncParams P) {
+  const int64_t chunk = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nchunks = P.nblocks * P.nplanes;
+  if (chunk >= nchunks) return;
+  const int64_t blk = chunk / P.nplanes;
+  const int pi = (int)(chunk % P.nplanes);
+  const int p = 63 - pi;
+  int64_t lo, hi;
+  chunk_range(P, blk, p, &lo, &hi);
+  const int lane = threadIdx.x & 31;
+  uint64_t rawbits = 0;
+  unsigned long long* h = P.hist + pi * kNsym;
+  chunk_walk(
+      P, lo, hi, p,
+      [&](uint32_t run) {
+        if (lane == 0) atomicAdd(h + bucket_of(run), 1ull);
+      },
+      [&](unsigned, int cnt) { rawbits += cnt; });
+  if (lane == 0) P.wsize[chunk] = (uint32_t)((rawbits + 7) / 8);
+}
+
+// frequency normalisation (12-bit), one thread per plane; writes freq and cum
+__global__ void freq_kernel(const unsigned long long* __restrict__ hist, int nplanes, uint32_t* __restrict__ fc) {
+  const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pi >= nplanes) return;
+  const unsigned long long* c = hist + pi * kNsym;
+  uint32_t* f = fc + pi * kNsym;
+  uint32_t* cum = fc + nplanes * kNsym + pi * kNsym;
+  unsigned long long tot = 0;
+  int best = 0;
+  for (int i = 0; i < kNsym; ++i) {
+    tot += c[i];
+    if (c[i] > c[best]) best = i;
+  }
+  if (tot == 0) {
+    for (int i = 0; i < kNsym; ++i) { f[i] = 0; cum[i] = 0; }
+    return;
+  }
+  int64_t sum = 0;
+  for (int i = 0; i < kNsym; ++i) {
+    uint64_t v = 0;
+    if (c[i]) {
+      v = (uint64_t)(((u128)c[i] * kM) / tot);
+      if (v == 0) v = 1;
+    }
+    f[i] = (uint32_t)v;
+    sum += (int64_t)v;
+  }
+  f[best] = (uint32_t)((int64_t)f[best] + ((int64_t)kM - sum));
+  uint32_t a = 0;
+  for (int i = 0; i < kNsym; ++i) { cum[i] = a; a += f[i]; }
+}
+
+// rANS of the runs of one chunk, backwards.  `emit` receives bytes in
+// emission order (the stream stores them reversed after the 4-byte state).
+struct RansEnc {
+  uint32_t x;
+  uint32_t nbytes;
+};
+
+template <typename EmitF>
+__device__ __forceinline__ void rans_put_run(RansEnc& r, uint32_t run, const uint32_t* f, const uint32_t* cum, EmitF emit) {
+  const int sb = bucket_of(run);
+  const uint32_t extra = run + 1u - (1u << sb);
+  if (sb > 0) {
+    const uint32_t xmax = (kRansL >> sb) << 8;
+    while (r.x >= xmax) { emit((uint8_t)(r.x & 0xff)); r.x >>= 8; r.nbytes++; }
+    r.x = (r.x << sb) | extra;
+  }
+  const uint32_t fr = f[sb], c = cum[sb];
+  const uint32_t xmax = ((kRansL >> kScaleBits) << 8) * fr;
+  while (r.x >= xmax) { emit((uint8_t)(r.x & 0xff)); r.x >>= 8; r.nbytes++; }
+  r.x = ((r.x / fr) << kScaleBits) + (r.x % fr) + c;
+}
+
+constexpr int kMaxRuns = 4097;  // enough for block_size <= 4096; larger blocks use the global spill
+constexpr int kEncWarps = 2;  // 2 x 4097 x 4 B of static shared memory
+
+// pass 2 (sizes_only) / pass 3: per chunk, collect runs (forward), rANS them backward.
+__global__ void __launch_bounds__(32 * kEncWarps) enc_rans_kernel(EncParams P, int sizes_only, uint32_t* spill) {
+  __shared__ uint32_t runs_sm[kEncWarps][kMaxRuns];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t chunk = (int64_t)blockIdx.x * kEncWarps + warp;
+  const int64_t nchunks = P.nblocks * P.nplanes;
+  if (chunk >= nchunks) return;
+  const int64_t blk = chunk / P.nplanes;
+  const int pi = (int)(chunk % P.nplanes);
+  const int p = 63 - pi;
+  int64_t lo, hi;
+  chunk_range(P, blk, p, &lo, &hi);
+  uint32_t* runs = (P.block_size < kMaxRuns) ? runs_sm[warp] : (spill + chunk * (int64_t)(P.block_size + 1));
+  uint32_t nr = 0;
+  // raw writer state (lane 0)
+  uint64_t acc = 0;
+  int nacc = 0;
+  uint8_t* rawp = nullptr;
+  if (!sizes_only) rawp = P.out + P.off[chunk] + P.rsize[chunk];
+  chunk_walk(
+      P, lo, hi, p,
+      [&](uint32_t run) {
+        if (lane == 0) runs[nr] = run;
+        nr++;
+      },
+      [&](unsigned packed, int cnt) {
+        if (!sizes_only && lane == 0 && cnt > 0) {
+          acc |= (uint64_t)packed << nacc;
+          nacc += cnt;
+          while (nacc >= 8) { *rawp++ = (uint8_t)(acc & 0xff); acc >>= 8; nacc -= 8; }
+        }
+      });
+  if (lane != 0) return;
+  if (!sizes_only && nacc > 0) *rawp = (uint8_t)(acc & 0xff);
+  const uint32_t* f = P.freq + pi * kNsym;
+  const uint32_t* cum = P.freq + P.nplanes * kNsym + pi * kNsym;
+  RansEnc r = {kRansL, 0};
+  if (sizes_only) {
+    for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, [](uint8_t) {});
+    P.rsize[chunk] = nr ? (r.nbytes + 4) : 0;
+  } else {
+    if (nr) {
+      // bytes are written from the end of the rANS area towards its start
+      uint8_t* base = P.out + P.off[chunk];
+      uint8_t* end = base + P.rsize[chunk];
+      uint8_t* w = end;
+      for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, [&](uint8_t by) { *--w = by; });
+      w -= 4;
+      w[0] = (uint8_t)r.x;
+      w[1] = (uint8_t)(r.x >> 8);
+      w[2] = (uint8_t)(r.x >> 16);
+      w[3] = (uint8_t)(r.x >> 24);
+    }
+    P.table[2 * chunk] = P.rsize[chunk];
+    P.table[2 * chunk + 1] = P.wsize[chunk];
+  }
+}
+
+// exclusive scan of rsize + wsize in chunk order (single CTA, sequential per thread slice)
+__global__ void scan_kernel(const uint32_t* __restrict__ rs, const uint32_t* __restrict__ ws, int64_t nchunks,
+                            uint64_t* __restrict__ off) {
+  __shared__ uint64_t part[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int64_t per = (nchunks + T - 1) / T;
+  const int64_t lo = min(nchunks, (int64_t)t * per), hi = min(nchunks, lo + per);
+  uint64_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += (uint64_t)rs[i] + ws[i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    uint64_t a = 0;
+    for (int i = 0; i < T; ++i) { uint64_t v = part[i]; part[i] = a; a += v; }
+    off[nchunks] = a;
+  }
+  __syncthreads();
+  uint64_t a = part[t];
+  for (int64_t i = lo; i < hi; ++i) { off[i] = a; a += (uint64_t)rs[i] + ws[i]; }
+}
+
+// ------------------------------------------------------------------- decoder
+struct DecParams {
+  const uint8_t* sec;   // whole ATCQ section (device copy)
+  int64_t nbytes;
+  int64_t n;
+  int k;
+  int block_size;
+  int p_star;
+  int64_t i_star;
+  int nplanes;
+  int64_t nblocks;
+  int64_t tab;          // offset of the size table
+  const uint64_t* boff; // per block payload offset (nblocks)
+  uint64_t* qt;
+  uint8_t* sg;
+  double* out;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t rd32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+__global__ void block_offsets_kernel(DecParams D, uint64_t* boff) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint64_t pos = D.tab + (uint64_t)D.nblocks * D.nplanes * 8;
+  for (int64_t b = 0; b < D.nblocks; ++b) {
+    boff[b] = pos;
+    for (int pi = 0; pi < D.nplanes; ++pi) {
+      const uint8_t* t = D.sec + D.tab + (b * D.nplanes + pi) * 8;
+      pos += (uint64_t)rd32(t) + rd32(t + 4);
+    }
+  }
+  boff[D.nblocks] = pos;
+  if (pos > (uint64_t)D.nbytes) atomicExch(D.err, 1);
+}
+
+// One thread per block: planes 63 .. p_star in order, then dequantize.
+__global__ void decode_kernel(DecParams D) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= D.nblocks) return;
+  if (*D.err) return;
+  const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
+  for (int64_t j = lo; j < hi_all; ++j) { D.qt[j] = 0; D.sg[j] = 0; }
+  uint64_t pos = D.boff[b];
+  const uint8_t* ftab = D.sec + 48;
+  for (int pi = 0; pi < D.nplanes; ++pi) {
+    const int p = 63 - pi;
+    const uint8_t* t = D.sec + D.tab + (b * D.nplanes + pi) * 8;
+    const uint32_t rl = rd32(t), wl = rd32(t + 4);
+    if (pos + rl + wl > (uint64_t)D.nbytes) { atomicExch(D.err, 2); return; }
+    const uint8_t* rp = D.sec + pos;
+    const uint8_t* rend = rp + rl;
+    const uint8_t* raw = D.sec + pos + rl;
+    const uint64_t rcap = (uint64_t)wl * 8;
+    uint64_t rbit = 0;
+    uint32_t x = 0;
+    if (rl) {
+      if (rl < 4) { atomicExch(D.err, 3); return; }
+      x = rd32(rp);
+      rp += 4;
+    }
+    uint32_t f[kNsym], cum[kNsym];
+    uint32_t ca = 0;
+    for (int i = 0; i < kNsym; ++i) {
+      f[i] = (uint32_t)ftab[2 * (pi * kNsym + i)] | ((uint32_t)ftab[2 * (pi * kNsym + i) + 1] << 8);
+      cum[i] = ca;
+      ca += f[i];
+    }
+    int64_t hi = hi_all;
+    if (p == D.p_star && hi > D.i_star + 1) hi = max(lo, D.i_star + 1);
+    bool need = true;
+    uint32_t left = 0;
+    for (int64_t j = lo; j < hi; ++j) {
+      if (D.qt[j] != 0) {
+        if (rbit >= rcap) { atomicExch(D.err, 4); return; }
+        const uint64_t bit = (raw[rbit >> 3] >> (rbit & 7)) & 1u;
+        rbit++;
+        D.qt[j] |= bit << p;
+      } else {
+        if (need) {
+          if (!rl) { atomicExch(D.err, 5); return; }
+          const uint32_t slot = x & (kM - 1);
+          int sb = -1;
+          for (int i = 0; i < kNsym; ++i)
+            if (f[i] && slot >= cum[i] && slot < cum[i] + f[i]) { sb = i; break; }
+          if (sb < 0) { atomicExch(D.err, 6); return; }
+          x = f[sb] * (x >> kScaleBits) + slot - cum[sb];
+          while (x < kRansL) { if (rp >= rend) { atomicExch(D.err, 7); return; } x = (x << 8) | *rp++; }
+          uint32_t extra = 0;
+          if (sb > 0) {
+            extra = x & ((1u << sb) - 1u);
+            x >>= sb;
+            while (x < kRansL) { if (rp >= rend) { atomicExch(D.err, 8); return; } x = (x << 8) | *rp++; }
+          }
+          left = (1u << sb) - 1u + extra;
+          need = false;
+        }
+        if (left > 0) {
+          left--;
+        } else {
+          D.qt[j] |= 1ull << p;
+          if (rbit >= rcap) { atomicExch(D.err, 9); return; }
+          D.sg[j] = (raw[rbit >> 3] >> (rbit & 7)) & 1u;
+          rbit++;
+          need = true;
+        }
+      }
+    }
+    pos += rl + wl;
+  }
+  for (int64_t j = lo; j < hi_all; ++j) {
+    const uint64_t a = D.qt[j];
+    if (a == 0) { D.out[j] = 0.0; continue; }
+    const int pj = (j <= D.i_star) ? D.p_star : D.p_star + 1;
+    const uint64_t v = a + ((pj >= 1) ? (1ull << (pj - 1)) : 0ull);
+    const double m = mul_pow2(__ull2double_rn(v), -D.k);
+    D.out[j] = D.sg[j] ? -m : m;
+  }
+}
+
+static void put32(uint8_t* p, uint32_t v) { for (int i = 0; i < 4; ++i) p[i] = (uint8_t)(v >> (8 * i)); }
+static void put64(uint8_t* p, uint64_t v) { for (int i = 0; i < 8; ++i) p[i] = (uint8_t)(v >> (8 * i)); }
+static uint32_t get32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i); return v; }
+static uint64_t get64(const uint8_t* p) { uint64_t v = 0; for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i); return v; }
+
+double i192_to_double(const I192& v) {
+  // v >= 0 assumed
+  return (double)v.w2 * 0x1p128 + (double)v.w1 * 0x1p64 + (double)v.w0;
+}
+
+}  // namespace
+
+int quantize_encode(const double* core, int64_t n, double target, int block_size, cudaStream_t s, std::string* out,
+                    QuantResult* res, float* ms_quant, float* ms_encode) {
+  if (n < 1) return fail(ATC_EINVAL, "empty core");
+  if (block_size < 32 || block_size > 65535 || (block_size % 32)) return fail(ATC_EINVAL, "bad block_size %d", block_size);
+  cudaEvent_t e0, e1, e2;
+  ATC_CUDA_TRY(cudaEventCreate(&e0));
+  ATC_CUDA_TRY(cudaEventCreate(&e1));
+  ATC_CUDA_TRY(cudaEventCreate(&e2));
+  ATC_CUDA_TRY(cudaEventRecord(e0, s));
+  // scratch layout
+  uint64_t* q = nullptr;
+  uint8_t* sg = nullptr;
+  ATC_TRY(Scratch::get(SLOT_Q, sizeof(uint64_t) * n, (void**)&q));
+  ATC_TRY(Scratch::get(SLOT_QS, (size_t)n, (void**)&sg));
+  const int64_t seg_len = (n + kSegBlocks - 1) / kSegBlocks;
+  const int nseg = (int)((n + seg_len - 1) / seg_len);
+  uint8_t* small = nullptr;
+  const size_t seg_bytes = sizeof(Seg) * (size_t)nseg * kPlaneChunk;
+  const size_t small_bytes = 4096 + seg_bytes + sizeof(I192) * nseg + 256;
+  ATC_TRY(Scratch::get(SLOT_QPART, small_bytes, (void**)&small));
+  TrackState* st = reinterpret_cast<TrackState*>(small);
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(small + 1024);
+  Seg* segs = reinterpret_cast<Seg*>(small + 4096);
+  I192* e64s = reinterpret_cast<I192*>(small + 4096 + seg_bytes);
+  ATC_CUDA_TRY(cudaMemsetAsync(small, 0, 4096, s));
+  const int64_t gb = (n + 255) / 256;
+  const int grid = (int)(gb < 152 * 8 ? gb : 152 * 8);
+  maxabs_kernel<<<grid, 256, 0, s>>>(core, n, mx);
+  ATC_CUDA_TRY(cudaGetLastError());
+  scale_exp_kernel<<<1, 32, 0, s>>>(mx, target, st);
+  ATC_CUDA_TRY(cudaGetLastError());
+  quantize_kernel<<<grid, 256, 0, s>>>(core, n, &st->k, q, sg);
+  ATC_CUDA_TRY(cudaGetLastError());
+  TrackState hst;
+  int phi = 63;
+  bool first = true;
+  for (;;) {
+    int plo = phi - kPlaneChunk + 1;
+    if (plo < 0) plo = 0;
+    plane_stats_kernel<<<nseg, kSegThreads, 0, s>>>(q, n, seg_len, plo, phi, first ? 1 : 0, segs, e64s);
+    ATC_CUDA_TRY(cudaGetLastError());
+    plane_scan_kernel<<<1, 32, 0, s>>>(segs, e64s, nseg, plo, phi, first ? 1 : 0, st);
+    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    ATC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hst.nan) return fail(ATC_ENUMERIC, "core contains NaN or Inf");
+    first = false;
+    if (hst.found) break;
+    phi = plo - 1;
+    if (phi < 0) return fail(ATC_ECUDA, "tracker did not terminate");
+  }
+  if (hst.p_star < 64 && hst.reachable) {
+    istar_kernel<<<1, kSegThreads, 0, s>>>(q, n, seg_len, segs, nseg, phi, st);
+    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  const int k = hst.k;
+  const int p_star = hst.p_star;
+  int64_t i_star = hst.i_star;
+  if (i_star < 0) i_star = n - 1;
+  ATC_CUDA_TRY(cudaEventRecord(e1, s));
+  // ------------------------------------------------ encoding
+  const int nplanes = (p_star >= 64) ? 0 : 64 - p_star;
+  const int64_t nblocks = (n + block_size - 1) / block_size;
+  const int64_t nchunks = nblocks * nplanes;
+  const size_t hdr = 48 + (size_t)nplanes * kNsym * 2;
+  const size_t tabb = (size_t)nchunks * 8;
+  std::vector<uint8_t> head(hdr, 0);
+  memcpy(head.data(), "ATCQ", 4);
+  put32(head.data() + 4, 1);
+  put64(head.data() + 8, (uint64_t)n);
+  put32(head.data() + 16, (uint32_t)k);
+  put32(head.data() + 20, (uint32_t)block_size);
+  put32(head.data() + 24, (uint32_t)p_star);
+  put32(head.data() + 28, 0);
+  put64(head.data() + 32, (uint64_t)i_star);
+  put32(head.data() + 40, (uint32_t)nplanes);
+  put32(head.data() + 44, kNsym);
+  std::string result;
+  if (nplanes > 0) {
+    uint8_t* enc = nullptr;
+    const size_t enc_small = sizeof(unsigned long long) * nplanes * kNsym + sizeof(uint32_t) * 2 * nplanes * kNsym +
+                             sizeof(uint32_t) * 2 * nchunks + sizeof(uint64_t) * (nchunks + 1) + 1024;
+    ATC_TRY(Scratch::get(SLOT_ENC, enc_small, (void**)&enc));
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(enc);
+    uint32_t* fc = reinterpret_cast<uint32_t*>(hist + nplanes * kNsym);
+    uint32_t* rsize = fc + 2 * nplanes * kNsym;
+    uint32_t* wsize = rsize + nchunks;
+    uint64_t* off = reinterpret_cast<uint64_t*>(((uintptr_t)(wsize + nchunks) + 7) & ~(uintptr_t)7);
+    ATC_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nplanes * kNsym, s));
+    uint32_t* spill = nullptr;
+    if (block_size >= kMaxRuns)
+      ATC_TRY(Scratch::get(SLOT_SPILL, sizeof(uint32_t) * (size_t)nchunks * (block_size + 1), (void**)&spill));
+    EncParams P;
+    P.q = q; P.sg = sg; P.n = n; P.block_size = block_size; P.p_star = p_star; P.i_star = i_star;
+    P.nplanes = nplanes; P.nblocks = nblocks; P.hist = hist; P.freq = fc; P.rsize = rsize; P.wsize = wsize;
+    P.off = off; P.out = nullptr; P.table = nullptr;
+    const int wpb = 4;
+    const unsigned eg = (unsigned)((nchunks + wpb - 1) / wpb);
+    enc_hist_kernel<<<eg, 32 * wpb, 0, s>>>(P);
+    ATC_CUDA_TRY(cudaGetLastError());
+    freq_kernel<<<(nplanes + 63) / 64, 64, 0, s>>>(hist, nplanes, fc);
+    ATC_CUDA_TRY(cudaGetLastError());
+    enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 1, spill);
+    ATC_CUDA_TRY(cudaGetLastError());
+    scan_kernel<<<1, 1024, 0, s>>>(rsize, wsize, nchunks, off);
+    ATC_CUDA_TRY(cudaGetLastError());
+    uint64_t total = 0;
+    ATC_CUDA_TRY(cudaMemcpyAsync(&total, off + nchunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    std::vector<uint32_t> hfc(2 * nplanes * kNsym);
+    ATC_CUDA_TRY(cudaMemcpyAsync(hfc.data(), fc, sizeof(uint32_t) * nplanes * kNsym, cudaMemcpyDeviceToHost, s));
+    ATC_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < nplanes * kNsym; ++i) {
+      head[48 + 2 * i] = (uint8_t)hfc[i];
+      head[48 + 2 * i + 1] = (uint8_t)(hfc[i] >> 8);
+    }
+    uint8_t* dout = nullptr;
+    ATC_TRY(Scratch::get(SLOT_OUT, tabb + total + 64, (void**)&dout));
+    P.table = reinterpret_cast<uint32_t*>(dout);
+    P.out = dout + tabb;
+    enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 0, spill);
+    ATC_CUDA_TRY(cudaGetLastError());
+    result.resize(hdr + tabb + total);
+    memcpy(&result[0], head.data(), hdr);
+    ATC_CUDA_TRY(cudaMemcpyAsync(&result[hdr], dout, tabb + total, cudaMemcpyDeviceToHost, s));
+    ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  } else {
+    result.assign((const char*)head.data(), hdr);
+  }
+  ATC_CUDA_TRY(cudaEventRecord(e2, s));
+  ATC_CUDA_TRY(cudaEventSynchronize(e2));
+  float a = 0.f, b = 0.f;
+  cudaEventElapsedTime(&a, e0, e1);
+  cudaEventElapsedTime(&b, e1, e2);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  if (ms_quant) *ms_quant = a;
+  if (ms_encode) *ms_encode = b;
+  if (res) {
+    res->k = k;
+    res->p_star = p_star;
+    res->i_star = i_star;
+    res->sse_pred = ldexp(i192_to_double(hst.e_star), -2 * k);
+  }
+  out->swap(result);
+  return ATC_OK;
+}
+
+int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t n, cudaStream_t s) {
+  if (!bytes || nbytes < 48) return fail(ATC_ECORRUPT, "core section too short");
+  if (memcmp(bytes, "ATCQ", 4) != 0 || get32(bytes + 4) != 1) return fail(ATC_ECORRUPT, "bad core section magic/version");
+  DecParams D;
+  D.n = (int64_t)get64(bytes + 8);
+  D.k = (int)get32(bytes + 16);
+  D.block_size = (int)get32(bytes + 20);
+  D.p_star = (int)get32(bytes + 24);
+  D.i_star = (int64_t)get64(bytes + 32);
+  D.nplanes = (int)get32(bytes + 40);
+  if (D.n != n) return fail(ATC_ECORRUPT, "core size mismatch (%lld vs %lld)", (long long)D.n, (long long)n);
+  if (D.block_size < 32 || D.block_size > 65535 || (D.block_size % 32)) return fail(ATC_ECORRUPT, "bad block size");
+  if (get32(bytes + 44) != kNsym) return fail(ATC_ECORRUPT, "bad alphabet size");
+  if (D.p_star < 0 || D.p_star > 64 || D.nplanes != (D.p_star >= 64 ? 0 : 64 - D.p_star))
+    return fail(ATC_ECORRUPT, "bad breakpoint plane");
+  if (D.i_star < 0 || D.i_star >= n) return fail(ATC_ECORRUPT, "bad breakpoint index");
+  D.nblocks = (n + D.block_size - 1) / D.block_size;
+  D.tab = 48 + (int64_t)D.nplanes * kNsym * 2;
+  if ((uint64_t)D.tab + (uint64_t)D.nblocks * D.nplanes * 8 > nbytes) return fail(ATC_ECORRUPT, "truncated size table");
+  for (int pi = 0; pi < D.nplanes; ++pi) {
+    uint32_t sum = 0;
+    for (int i = 0; i < kNsym; ++i) sum += (uint32_t)bytes[48 + 2 * (pi * kNsym + i)] | ((uint32_t)bytes[48 + 2 * (pi * kNsym + i) + 1] << 8);
+    if (sum != 0 && sum != kM) return fail(ATC_ECORRUPT, "bad frequency table");
+  }
+  D.nbytes = (int64_t)nbytes;
+  uint8_t* dsec = nullptr;
+  ATC_TRY(Scratch::get(SLOT_OUT, nbytes + 64, (void**)&dsec));
+  ATC_CUDA_TRY(cudaMemcpyAsync(dsec, bytes, nbytes, cudaMemcpyHostToDevice, s));
+  uint64_t* qt = nullptr;
+  uint8_t* sg = nullptr;
+  ATC_TRY(Scratch::get(SLOT_Q, sizeof(uint64_t) * n, (void**)&qt));
+  ATC_TRY(Scratch::get(SLOT_QS, (size_t)n, (void**)&sg));
+  uint8_t* small = nullptr;
+  ATC_TRY(Scratch::get(SLOT_ENC, sizeof(uint64_t) * (D.nblocks + 1) + 64, (void**)&small));
+  int* err = reinterpret_cast<int*>(small);
+  uint64_t* boff = reinterpret_cast<uint64_t*>(small + 64);
+  ATC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  D.sec = dsec; D.qt = qt; D.sg = sg; D.out = core; D.err = err; D.boff = boff;
+  block_offsets_kernel<<<1, 32, 0, s>>>(D, boff);
+  ATC_CUDA_TRY(cudaGetLastError());
+  decode_kernel<<<(unsigned)((D.nblocks + 63) / 64), 64, 0, s>>>(D);
+  ATC_CUDA_TRY(cudaGetLastError());
+  int herr = 0;
+  ATC_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (herr) return fail(ATC_ECORRUPT, "corrupt core payload (code %d)", herr);
+  return ATC_OK;
+}
+
+}  // namespace atc

@@ -1,0 +1,176 @@
+// Norms, conversions and the core permutation.
+//
+// ||X||^2 (Section 3.1, Euclidean norm) is accumulated in FP64 with a fixed
+// grid and a fixed reduction tree, so the result does not depend on timing.
+#include <stdint.h>
+
+#include "atc_internal.cuh"
+
+namespace atc {
+namespace {
+
+constexpr int kNormBlocks = 1216;  // 8 x 152 SMs
+constexpr int kNormThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNormThreads) norm2_partial(const T* __restrict__ x, int64_t n,
+                                                               double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (sizeof(T) == 4 && ((uintptr_t)x & 15) == 0) {
+    const int64_t n4 = n / 4;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += stride) {
+      float4 v = __ldg(x4 + i);
+      acc = fma((double)v.x, (double)v.x, acc);
+      acc = fma((double)v.y, (double)v.y, acc);
+      acc = fma((double)v.z, (double)v.z, acc);
+      acc = fma((double)v.w, (double)v.w, acc);
+    }
+    for (int64_t i = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+      double v = (double)x[i];
+      acc = fma(v, v, acc);
+    }
+  } else {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+      double v = (double)x[i];
+      acc = fma(v, v, acc);
+    }
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kNormThreads) sum_partials(const double* __restrict__ part, int np,
+                                                             double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += part[i];
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = t;
+}
+
+template <typename T>
+__global__ void to_f64(const T* __restrict__ x, int64_t n, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+__global__ void f64_to_f32(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+struct PermDesc {
+  int ndim;
+  int64_t dims[8];     // source dims
+  int64_t sstride[8];  // source strides
+  int64_t dstride[8];  // destination stride of source axis a
+};
+
+// y[dest(idx)] = x[idx]: walk the source in order, scatter with per-axis strides.
+__global__ void permute_kernel(const double* __restrict__ x, int64_t total, PermDesc pd, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = i, dst = 0;
+    for (int a = pd.ndim - 1; a >= 0; --a) {
+      int64_t c = rem % pd.dims[a];
+      rem /= pd.dims[a];
+      dst += c * pd.dstride[a];
+    }
+    y[dst] = x[i];
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s) {
+  double* part = nullptr;
+  ATC_TRY(Scratch::get(SLOT_SMALL, sizeof(double) * (kNormBlocks + 64), (void**)&part));
+  if (dtype == ATC_F32)
+    norm2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, n, part);
+  else
+    norm2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, n, part);
+  ATC_CUDA_TRY(cudaGetLastError());
+  sum_partials<<<1, kNormThreads, 0, s>>>(part, kNormBlocks, out);
+  ATC_CUDA_TRY(cudaGetLastError());
+  return ATC_OK;
+}
+
+int launch_convert_to_f64(const void* x, int dtype, int64_t n, double* y, cudaStream_t s) {
+  if (dtype == ATC_F64) {
+    ATC_CUDA_TRY(cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return ATC_OK;
+  }
+  to_f64<float><<<grid_for(n, 256), 256, 0, s>>>((const float*)x, n, y);
+  ATC_CUDA_TRY(cudaGetLastError());
+  return ATC_OK;
+}
+
+int launch_convert_f64_to(const double* x, int64_t n, void* y, int dtype, cudaStream_t s) {
+  if (dtype == ATC_F64) {
+    if ((const void*)x != y) ATC_CUDA_TRY(cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return ATC_OK;
+  }
+  f64_to_f32<<<grid_for(n, 256), 256, 0, s>>>(x, n, (float*)y);
+  ATC_CUDA_TRY(cudaGetLastError());
+  return ATC_OK;
+}
+
+// inverse == 0: y = transpose(x, perm) (y's axis i is x's axis perm[i]).
+// inverse == 1: x is laid out in perm order (dims given in ORIGINAL order), undo it.
+int launch_permute(const double* x, const int64_t* dims, const int* perm, int ndim, double* y, int inverse,
+                   cudaStream_t s) {
+  PermDesc pd;
+  pd.ndim = ndim;
+  int64_t total = 1;
+  for (int i = 0; i < ndim; ++i) total *= dims[i];
+  if (total == 0) return ATC_OK;
+  // permuted dims: pdims[i] = dims[perm[i]]
+  int64_t pdims[8], pstride[8], ostride[8];
+  for (int i = 0; i < ndim; ++i) pdims[i] = dims[perm[i]];
+  int64_t acc = 1;
+  for (int i = ndim - 1; i >= 0; --i) { pstride[i] = acc; acc *= pdims[i]; }
+  acc = 1;
+  for (int i = ndim - 1; i >= 0; --i) { ostride[i] = acc; acc *= dims[i]; }
+  if (!inverse) {
+    // source = original layout; original axis perm[i] goes to permuted position i
+    for (int a = 0; a < ndim; ++a) pd.dims[a] = dims[a];
+    for (int i = 0; i < ndim; ++i) pd.dstride[perm[i]] = pstride[i];
+  } else {
+    // source = permuted layout; permuted axis i is original axis perm[i]
+    for (int i = 0; i < ndim; ++i) { pd.dims[i] = pdims[i]; pd.dstride[i] = ostride[perm[i]]; }
+  }
+  permute_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, total, pd, y);
+  ATC_CUDA_TRY(cudaGetLastError());
+  return ATC_OK;
+}
+
+}  // namespace atc

@@ -1,0 +1,233 @@
+"""GPU parity of the plain-FP64 path against the oracle, step by step and end
+to end, through the C ABI (libatc.so).
+
+Tolerances:
+* Gram / TTM in FP64: |gpu - oracle| <= 1e-12 * ||X||^2 (entrywise, relative to
+  the Frobenius scale: both sides sum the same products in different orders).
+* Eigenvalues: |lambda_gpu - lambda_oracle| <= 1e-12 * ||G||_2.
+* Factor subspaces: largest principal angle <= 1e-6 (spec bar for the
+  FP64 path); ranks identical.
+* Rank selection on identical eigenvalues: bit-identical r and discarded sum.
+* Reconstruction: ||X_hat_gpu - X_hat_oracle|| <= 1e-5 ||X||; achieved error in
+  [0.98, 1] * rel_eps.
+* Quantizer / encoder: identical bytes for identical cores and targets.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import synth  # noqa: E402
+from oracle import pipeline as OP  # noqa: E402
+from oracle import quant as OQ  # noqa: E402
+from oracle import sthosvd as O  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2107_01384_gb300 as P
+    return P
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def principal_angle(u, v):
+    qu, _ = np.linalg.qr(u)
+    qv, _ = np.linalg.qr(v)
+    s = np.linalg.svd(qu.T @ qv, compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
+
+
+@pytest.mark.parametrize("shape,dtype", [((1000,), np.float32), ((257, 3), np.float64), ((64, 64, 64), np.float64),
+                                         ((1,), np.float32), ((3, 5, 7, 11), np.float32)])
+def test_norm2(P, shape, dtype):
+    x = np.random.default_rng(0).standard_normal(shape).astype(dtype)
+    got = float(P.atc_norm2(cuda(x)).item())
+    ref = O.norm2(x)
+    assert abs(got - ref) <= 1e-13 * ref
+
+
+@pytest.mark.parametrize("dims,mode,dtype", [((64, 64, 64), 0, np.float64), ((64, 64, 64), 1, np.float64),
+                                             ((64, 64, 64), 2, np.float64), ((37, 129, 5), 1, np.float32),
+                                             ((300, 7), 0, np.float32), ((300, 7), 1, np.float32),
+                                             ((1, 65, 1), 1, np.float64), ((6, 200, 70), 1, np.float32)])
+def test_gram_fp64(P, dims, mode, dtype):
+    x = np.random.default_rng(1).standard_normal(dims).astype(dtype)
+    L = int(np.prod(dims[:mode])); n = dims[mode]; R = int(np.prod(dims[mode + 1:]))
+    g = P.atc_gram(cuda(x), L, n, R, P.PREC_FP64).cpu().numpy()
+    ref = O.mode_gram(x, mode)
+    scale = O.norm2(x)
+    assert np.abs(g - ref).max() <= 1e-12 * scale
+    assert np.array_equal(g, g.T)
+
+
+@pytest.mark.parametrize("n,nvec,kind", [(1, 1, "rand"), (2, 2, "rand"), (3, 3, "rand"), (16, 16, "rand"),
+                                         (64, 8, "lowrank"), (100, 30, "decay"), (256, 40, "decay"),
+                                         (224, 224, "decay"), (513, 20, "rand")])
+def test_eig_sym(P, n, nvec, kind):
+    rng = np.random.default_rng(n)
+    if kind == "rand":
+        a = rng.standard_normal((n, 3 * n + 2))
+    elif kind == "lowrank":
+        a = rng.standard_normal((n, 8)) @ rng.standard_normal((8, 200))
+    else:
+        a = rng.standard_normal((n, 2 * n)) * np.geomspace(1, 1e-5, 2 * n)[None, :]
+        a = (rng.standard_normal((n, n)) / np.sqrt(n)) @ a
+    g = a @ a.T
+    lam, v = P.atc_eig_sym(cuda(g), nvec)
+    lam = lam.cpu().numpy(); v = v.cpu().numpy()
+    lr, vr = O.eig_descending(g)
+    nrm = float(np.abs(lr).max()) if n else 1.0
+    assert np.abs(lam - np.linalg.eigvalsh(g)[::-1]).max() <= 1e-12 * max(nrm, 1e-300)
+    # eigen-residual and orthonormality of the returned columns
+    res = g @ v - v * lam[None, :nvec]
+    assert np.abs(res).max() <= 1e-10 * nrm
+    assert np.abs(v.T @ v - np.eye(nvec)).max() <= 1e-9
+    # subspace of the top-k where a clear gap exists
+    gaps = lr[:-1] - lr[1:]
+    for k in range(1, min(nvec, n - 1) + 1):
+        if gaps[k - 1] > 1e-6 * nrm:
+            assert principal_angle(v[:, :k], vr[:, :k]) <= 1e-6
+    # sign convention on well-separated columns
+    for j in range(nvec):
+        i = int(np.argmax(np.abs(v[:, j])))
+        assert v[i, j] >= 0
+
+
+def test_rank_select_bit_identical(P):
+    rng = np.random.default_rng(3)
+    for trial in range(40):
+        n = int(rng.integers(1, 300))
+        lam = np.sort(rng.exponential(1.0, n) * np.geomspace(1, 1e-9, n))[::-1].copy()
+        if trial % 5 == 0:
+            lam[-min(3, n):] = -1e-18
+        budget = float(rng.uniform(0, 1) * lam.sum() * 10 ** rng.uniform(-8, 0))
+        r, disc = P.atc_rank_select(cuda(lam), budget)
+        assert r == O.choose_rank(lam, budget)
+        assert disc == O.tail_sums(np.maximum(lam, 0))[r]
+
+
+@pytest.mark.parametrize("dims,mode,r,xdt,ydt", [((64, 64, 64), 0, 8, np.float64, np.float64),
+                                                 ((64, 64, 64), 1, 8, np.float64, np.float64),
+                                                 ((64, 64, 64), 2, 13, np.float32, np.float64),
+                                                 ((37, 129, 5), 1, 20, np.float32, np.float32),
+                                                 ((300, 7), 1, 7, np.float64, np.float64),
+                                                 ((3, 100, 1), 1, 1, np.float32, np.float64)])
+def test_ttm_fp64(P, dims, mode, r, xdt, ydt):
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(dims).astype(xdt)
+    u, _ = np.linalg.qr(rng.standard_normal((dims[mode], r)))
+    L = int(np.prod(dims[:mode])); n = dims[mode]; R = int(np.prod(dims[mode + 1:]))
+    tdt = torch.float64 if ydt == np.float64 else torch.float32
+    y = P.atc_ttm(cuda(x), L, n, R, cuda(u), r, expand=False, out_dtype=tdt).cpu().numpy()
+    ref = O.ttm_project(x.astype(np.float64), u, mode).ravel()
+    tol = 1e-12 if ydt == np.float64 else 2e-6
+    assert np.abs(y - ref).max() <= tol * np.sqrt(O.norm2(x))
+    # expand back
+    yz = ref.reshape([r if i == mode else dims[i] for i in range(len(dims))])
+    z = P.atc_ttm(cuda(yz), L, n, R, cuda(u), r, expand=True).cpu().numpy()
+    zr = O.ttm_expand(yz, u, mode).ravel()
+    assert np.abs(z - zr).max() <= 1e-12 * np.sqrt(O.norm2(yz))
+
+
+@pytest.mark.parametrize("n,bs,frac,seed", [(1, 32, 1e-3, 0), (31, 32, 1e-6, 1), (5000, 64, 1e-4, 2),
+                                            (70000, 4096, 1e-6, 3), (9000, 128, 0.0, 4), (300, 32, 2.0, 5),
+                                            (12345, 256, -1.0, 6), (200000, 4096, 1e-9, 7), (4096, 4096, 1e-5, 8)])
+def test_quantizer_bytes_identical(P, n, bs, frac, seed):
+    rng = np.random.default_rng(seed)
+    b = rng.standard_normal(n) * np.exp(-np.arange(n) / max(1, n / 5))
+    if seed % 3 == 0:
+        b[rng.integers(0, n, size=max(1, n // 10))] = 0.0
+    t = frac * float(np.dot(b, b))
+    data_gpu, info = P.atc_quantize_core(cuda(b), t, bs)
+    data_ref, rinfo = OQ.compress_core(b, t, bs)
+    assert (info["k"], info["p_star"], info["i_star"]) == (rinfo["k"], rinfo["p_star"], rinfo["i_star"])
+    assert data_gpu == data_ref
+    deq = P.atc_dequantize_core(data_ref, n).cpu().numpy()
+    _, _, deq_ref = OQ.decode(data_ref)
+    assert np.array_equal(deq, deq_ref)
+
+
+def test_quantizer_rejects_corrupt_sections(P):
+    b = synth.random_core((10, 10, 10), seed=4).ravel()
+    data, _ = OQ.compress_core(b, 1e-8 * float(np.dot(b, b)), 64)
+    with pytest.raises(P.AtcError):
+        P.atc_dequantize_core(b"XTCQ" + data[4:], b.size)
+    with pytest.raises(P.AtcError):
+        P.atc_dequantize_core(data[: len(data) // 2], b.size)
+    with pytest.raises(P.AtcError):
+        P.atc_dequantize_core(data, b.size + 1)
+
+
+def _check_pipeline(P, x, eps, rtmss=0.5, mode_order=None, rank_rule=0):
+    ref = O.sthosvd(x, eps, rtmss=rtmss, mode_order=mode_order,
+                    rank_rule="static" if rank_rule == 0 else "adaptive")
+    c = P.atc_compress(cuda(x), eps, rtmss=rtmss, mode_order=mode_order, rank_rule=rank_rule)
+    assert c.ranks() == ref["ranks"]
+    st = c.stats()
+    assert abs(st["norm2"] - ref["norm2"]) <= 1e-13 * ref["norm2"]
+    assert abs(st["sse_trunc"] - ref["sse_trunc"]) <= 1e-9 * ref["norm2"]
+    for m in range(x.ndim):
+        u = c.factor(m).cpu().numpy()
+        if u.shape[1] < u.shape[0]:
+            assert principal_angle(u, ref["factors"][m]) <= 1e-6
+        assert np.abs(u.T @ u - np.eye(u.shape[1])).max() <= 1e-12
+    stream = c.stream_bytes()
+    xh = P.atc_decompress(stream).cpu().numpy()
+    nx = np.linalg.norm(x)
+    re = np.linalg.norm(x - xh) / nx
+    assert 0.98 * eps <= re <= eps, re
+    xo = OP.decompress(stream)   # the oracle decodes the GPU stream
+    assert np.linalg.norm(xo - xh) <= 1e-9 * nx
+    # the oracle's own compression reconstructs to the same tensor within 1e-5
+    s_ref, _ = OP.compress(x, eps, rtmss=rtmss, mode_order=mode_order,
+                           rank_rule="static" if rank_rule == 0 else "adaptive")
+    xr = OP.decompress(s_ref)
+    assert np.linalg.norm(xr - xh) <= 1e-5 * nx
+    # bit-exact quantizer on the GPU's own core
+    core = c.core().cpu().numpy()
+    perm = st["storage_order"]
+    vec = np.ascontiguousarray(np.transpose(core, perm)).ravel()
+    sec, _ = OQ.compress_core(vec, st["target_sse"] - st["sse_trunc"], 4096)
+    assert OP.parse(stream)["core_stream"] == sec
+    return c, st
+
+
+def test_pipeline_lowrank64(P):
+    x = synth.lowrank_tucker()
+    c, st = _check_pipeline(P, x, 1e-2)
+    assert c.ranks() == [8, 8, 8]
+
+
+def test_pipeline_exact_rank_recovery(P):
+    x = synth.lowrank_tucker(noise=None)
+    c = P.atc_compress(cuda(x), 1e-2, rtmss=1.0)
+    assert c.ranks() == [8, 8, 8]
+
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-3])
+def test_pipeline_uneven_orders(P, eps):
+    x = synth.lowrank_tucker((40, 36, 30), (6, 5, 7), noise="relative", noise_level=1e-3, seed=21)
+    _check_pipeline(P, x, eps)
+    _check_pipeline(P, x, eps, mode_order=[2, 0, 1])
+    _check_pipeline(P, x, eps, rank_rule=1)
+
+
+def test_pipeline_order4_and_order2(P):
+    x = synth.lowrank_tucker((12, 10, 9, 8), (3, 4, 2, 3), noise="relative", noise_level=1e-2, seed=5)
+    _check_pipeline(P, x, 5e-2)
+    y = np.random.default_rng(2).standard_normal((50, 33)) @ np.diag(np.geomspace(1, 1e-3, 33))
+    _check_pipeline(P, y, 1e-2)
+
+
+def test_pipeline_bumps_f32_256(P):
+    x = synth.gaussian_bumps()
+    _check_pipeline(P, x, 1e-3)
