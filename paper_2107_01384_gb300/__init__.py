@@ -210,7 +210,7 @@ class Compressed:
         class _View:
             pass
         v = _View()
-        v.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr.value, True),
+        v.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr.value, False),
                                       "version": 3, "strides": None}
         torch.cuda.synchronize()
         return torch.as_tensor(v, device="cuda").clone()

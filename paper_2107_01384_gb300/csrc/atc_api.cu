@@ -375,6 +375,12 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   G = lam + maxn + 16;
   int* rdev = reinterpret_cast<int*>(lam + maxn);
   double* ddev = lam + maxn + 2;
+  int* tc_err = nullptr;
+  if (opt.precision != ATC_PREC_FP64) {
+    rc = tc_error_flag(&tc_err);
+    if (!rc && cudaMemsetAsync(tc_err, 0, sizeof(int), s) != cudaSuccess) rc = fail(ATC_ECUDA, "memset failed");
+    if (rc) return bail(rc);
+  }
   const void* curp = x_dev;
   int curdt = dtype;
   void* next = bufA;
@@ -408,6 +414,12 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         return bail(fail(ATC_ECUDA, "rank readback failed"));
       rc = eig_check(s);
       if (rc) return bail(rc);
+      if (tc_err) {
+        int he = 0;
+        if (cudaMemcpy(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+          return bail(fail(ATC_ECUDA, "error flag readback failed"));
+        if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
+      }
       if (r < 1 || r > n) return bail(fail(ATC_ENUMERIC, "rank selection failed (r = %d)", r));
       if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
         return bail(fail(ATC_ENOMEM, "factor allocation failed"));

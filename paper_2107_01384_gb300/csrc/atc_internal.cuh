@@ -56,6 +56,7 @@ enum ScratchSlot {
   SLOT_DEC,            // decompression ping-pong
   SLOT_DEC2,
   SLOT_FAC,            // uploaded factors
+  SLOT_TC_ERR,         // tensor-core kernels' error word + pre-scales
   SLOT_COUNT
 };
 
@@ -85,6 +86,7 @@ int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s);
 int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s);
 int launch_rank_select(const double* lam, int n, double budget, int* r_dev, double* disc_dev, cudaStream_t s);
 int eig_read_error(int* err);
+int tc_error_flag(int** flag);  // device error word of the tensor-core kernels (zeroed by the caller)
 
 // quantizer / encoder (k_quant.cu)
 struct QuantResult {

@@ -184,7 +184,11 @@ def _check_pipeline(P, x, eps, rtmss=0.5, mode_order=None, rank_rule=0):
     xh = P.atc_decompress(stream).cpu().numpy()
     nx = np.linalg.norm(x)
     re = np.linalg.norm(x - xh) / nx
-    assert 0.98 * eps <= re <= eps, re
+    assert re <= eps, re
+    if int(np.prod(c.ranks())) >= 1000:
+        # the breakpoint moves one bit at a time: with enough coefficients the
+        # error lands within 2% of the target (tiny cores step too coarsely)
+        assert re >= 0.98 * eps, re
     xo = OP.decompress(stream)   # the oracle decodes the GPU stream
     assert np.linalg.norm(xo - xh) <= 1e-9 * nx
     # the oracle's own compression reconstructs to the same tensor within 1e-5
@@ -192,6 +196,8 @@ def _check_pipeline(P, x, eps, rtmss=0.5, mode_order=None, rank_rule=0):
                            rank_rule="static" if rank_rule == 0 else "adaptive")
     xr = OP.decompress(s_ref)
     assert np.linalg.norm(xr - xh) <= 1e-5 * nx
+    re_ref = np.linalg.norm(x - xr) / nx
+    assert abs(re - re_ref) <= 1e-4 * eps
     # bit-exact quantizer on the GPU's own core
     core = c.core().cpu().numpy()
     perm = st["storage_order"]
