@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the ST-HOSVD + core-quantization hot path on one GB300.
+
+Workload: 256x256x256 float32 field, a sum of 32 isotropic Gaussian bumps
+(seeded, synthetic; stands in for the paper's smooth volumes), rel_eps 1e-3.
+One step = one full pass of the hot path through the C ABI:
+    atc_compress (norm, per-mode Gram / eigensolve / rank / projection,
+    core permutation, quantization, breakpoint, encoding) + atc_decompress
+    (decode, dequantize, expansion).
+Metric: input bytes (N * 4) per second of step time, in GB/s, for the
+split-precision tensor-core path; the same metric for the plain FP64 path is
+reported beside it (same box, same run).
+
+Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA
+events on the library's stream; the 67 MB input fits in the 129 MB L2, so L2
+is flushed (a 256 MB buffer is written) before every timed step, outside the
+events.  Under torchrun every rank runs an independent replica (the path is
+not sharded: no collective), a barrier brackets the timed loop and rank 0
+prints the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ST-HOSVD input GB/s (mixed vs FP64 plain, same GB300) at rel err 1e-3; TFLOP/s"
+WORKLOAD = "gaussian_bumps_256x256x256_f32"
+PRECISIONS = {"fp16": 2, "bf16": 1, "fp64": 0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16", choices=list(PRECISIONS))
+    ap.add_argument("--eps", type=float, default=1e-3)
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the plain FP64 path (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def workload():
+    import synth
+    return synth.gaussian_bumps()
+
+
+def time_oracle_step(x, eps):
+    """One oracle compress + decompress of x (float64 CPU); returns seconds."""
+    from oracle import pipeline as OP
+    t0 = time.perf_counter()
+    stream, _ = OP.compress(x, eps)
+    OP.decompress(stream)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(x, eps, budget_s=12.0, max_reps=5):
+    reps, total = 0, 0.0
+    while reps < max_reps and (total < budget_s or reps == 0):
+        total += time_oracle_step(x, eps)
+        reps += 1
+    per = total / reps
+    return {"value": x.nbytes / per / 1e9, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"full {WORKLOAD} (ST-HOSVD + quantize + encode + decode + expand), {reps} repetition(s), "
+                      f"{per:.2f} s each; NumPy BLAS threads + single-threaded C quantizer"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    x = workload()
+    for _ in range(args.warmup):
+        time_oracle_step(x, args.eps)
+    times = [time_oracle_step(x, args.eps) for _ in range(args.steps)]
+    per = sum(times) / len(times)
+    value = x.nbytes / per / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rel_eps": args.eps, "l2": "input 67 MB; oracle runs on the host"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step = one full oracle compress + decompress of {WORKLOAD}"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2107_01384_gb300 as P
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    x = workload()
+    N = x.size
+    nbytes = x.nbytes
+    xd = torch.from_numpy(x).to(dev)
+    prec = PRECISIONS[args.precision]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = torch.empty_like(xd)
+
+    def step(precision):
+        c = P.atc_compress(xd, args.eps, precision=precision, stream=stream)
+        s = c.stream_bytes()
+        rc = P.lib().atc_decompress(s, len(s), P._dev(out), P.ATC_F32, P._stream(stream))
+        if rc != 0:
+            raise P.AtcError(rc, P.lib().atc_last_error().decode())
+        return c, s
+
+    def timed(precision, k, w):
+        for _ in range(w):
+            step(precision)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms, stats = [], []
+        l0 = P.lib().atc_kernel_launches()
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            c, s = step(precision)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stats.append(c.stats())
+        barrier(world)
+        launches = P.lib().atc_kernel_launches() - l0
+        return ms, stats, c, s, launches
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms, stats, c, s, launches = timed(prec, args.steps, args.warmup)
+    clk = clocks.stop()
+    per_ms = max_over_ranks(sum(ms) / len(ms), world)
+    value = world * nbytes / (per_ms * 1e-3) / 1e9
+
+    # phase breakdown (device events inside the library, per step)
+    def mean(key):
+        return sum(st[key] for st in stats) / len(stats)
+    phases = {k: mean(k) for k in ("ms_norm", "ms_gram", "ms_eig", "ms_ttm", "ms_quant", "ms_encode", "ms_total")}
+    ranks = c.ranks()
+    sthosvd_ms = phases["ms_norm"] + phases["ms_gram"] + phases["ms_eig"] + phases["ms_ttm"]
+
+    # achieved error of the last step
+    xh = out.double()
+    re = float(torch.linalg.vector_norm(xd.double() - xh) / torch.linalg.vector_norm(xd.double()))
+
+    # algorithmic work per step: Gram (unique half, n_k * S_k) and TTM (2 r_k S_k) flops, bytes read
+    dims = list(x.shape)
+    order = stats[-1]["order"]
+    cur = list(dims)
+    gram_flops = ttm_flops = 0.0
+    gram_bytes = 0.0
+    for m in order:
+        S = float(np.prod(cur))
+        gram_flops += cur[m] * S
+        ttm_flops += 2.0 * ranks[m] * S
+        gram_bytes += S * 4.0
+        cur[m] = ranks[m]
+    tflops = (gram_flops + ttm_flops) / (sthosvd_ms * 1e-3) / 1e12
+
+    # plain FP64 path, same box
+    fp64 = None
+    if args.fp64_steps > 0 and prec != 0:
+        ms64, st64, c64, _, _ = timed(0, args.fp64_steps, 1)
+        per64 = sum(ms64) / len(ms64)
+        sth64 = sum(st["ms_norm"] + st["ms_gram"] + st["ms_eig"] + st["ms_ttm"] for st in st64) / len(st64)
+        fp64 = {"value": nbytes / (per64 * 1e-3) / 1e9, "ms_per_step": per64,
+                "sthosvd_gbs": nbytes / (sth64 * 1e-3) / 1e9, "ranks": c64.ranks(),
+                "speedup_step": per64 / per_ms, "speedup_sthosvd": sth64 / sthosvd_ms}
+
+    # e2e through the public API with host buffers
+    xh_pin = torch.from_numpy(x).pin_memory()
+    out_host = torch.empty(x.shape, dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xd.copy_(xh_pin, non_blocking=True)
+        c2, s2 = step(prec)
+        out_host.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_per = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world)
+
+    # roofline of the dominant phase's main kernel
+    hbm, bf16, bf16s, peak_src = load_peaks()
+    ph_share = {"gram": phases["ms_gram"], "eig": phases["ms_eig"], "ttm": phases["ms_ttm"],
+                "quant+encode": phases["ms_quant"] + phases["ms_encode"]}
+    dom = max(ph_share, key=ph_share.get)
+    if dom == "gram":
+        ach = gram_bytes / (phases["ms_gram"] * 1e-3) / 1e9
+        roof = {"kernel": "gram_tc_kernel (+split-K reduce)", "bound": "hbm", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": None}
+    elif dom == "ttm":
+        ttm_bytes = 0.0
+        cur2 = list(dims)
+        for m in order:
+            S = float(np.prod(cur2))
+            ttm_bytes += S * 4.0 + S / cur2[m] * ranks[m] * 4.0
+            cur2[m] = ranks[m]
+        ach = ttm_bytes / (phases["ms_ttm"] * 1e-3) / 1e9
+        roof = {"kernel": "ttm_tc_kernel", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None}
+    elif dom == "eig":
+        # FP64 work of the eigensolver: tridiagonalisation 4/3 n^3 + back-transformation 2 n^2 r per mode
+        fl = sum(4.0 / 3.0 * dims[m] ** 3 + 2.0 * dims[m] ** 2 * ranks[m] for m in order)
+        ach = fl / (phases["ms_eig"] * 1e-3) / 1e12
+        fp64_peak = 1.1  # TFLOP/s, torch float64 matmul measured on this machine's GB300 (no FP64 entry in the peaks file)
+        roof = {"kernel": "eigensolver (tridiag_kernel dominant)", "bound": "alu", "achieved": ach,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None}
+    else:
+        roof = {"kernel": "quantizer/encoder", "bound": "alu", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+    roof["peak_source"] = peak_src
+    roof["share_of_step"] = ph_share[dom] / per_ms
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp16": "fp16x2-split/f32-acc/f64-eig", "bf16": "bf16x2-split/f32-acc/f64-eig",
+                                          "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rel_eps": args.eps, "precision": args.precision,
+                       "step": "atc_compress + atc_decompress", "l2": "flushed (256 MB write) before each timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "ranks": ranks, "achieved_rel_err": re, "stream_bytes": len(s),
+            "sthosvd_gbs": nbytes / (sthosvd_ms * 1e-3) / 1e9, "sthosvd_tflops": tflops,
+            "phases_ms": phases, "fp64_plain": fp64,
+            "roofline": roof, "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": world * nbytes / (e2e_per * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes + len(s), "ms_per_step": e2e_per}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(x, args.eps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        import __graft_entry__ as g
+        g.build()
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -188,6 +188,8 @@ int atc_quantize_core(const double* core_dev, int64_t n, double target_sse, int 
 int atc_dequantize_core(const uint8_t* bytes, size_t nbytes, double* core_dev, int64_t n, void* stream);
 
 void atc_free_buffer(void* p);
+/* Number of CUDA kernels this library has launched in this process (host counter). */
+long long atc_kernel_launches(void);
 /* Free the cached device scratch of the current device. */
 int atc_release_workspace(void);
 const char* atc_last_error(void);

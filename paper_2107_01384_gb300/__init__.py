@@ -36,6 +36,7 @@ EXPORTS = [
     "atc_get_stream", "atc_get_stats", "atc_free", "atc_peek_dims", "atc_decompress", "atc_norm2",
     "atc_gram", "atc_eig_sym", "atc_rank_select", "atc_ttm", "atc_quantize_core",
     "atc_dequantize_core", "atc_free_buffer", "atc_release_workspace", "atc_last_error",
+    "atc_kernel_launches",
 ]
 
 
@@ -93,6 +94,8 @@ def lib():
         L.atc_free_buffer.argtypes = [vp]
         L.atc_free_buffer.restype = None
         L.atc_release_workspace.argtypes = []
+        L.atc_kernel_launches.argtypes = []
+        L.atc_kernel_launches.restype = C.c_longlong
         _lib = L
     return _lib
 

@@ -25,6 +25,7 @@
 namespace atc {
 
 static thread_local std::string g_err;
+long long g_kernel_launches = 0;
 
 void set_error(const char* fmt, ...) {
   char buf[1024];
@@ -127,26 +128,44 @@ void putf64(std::string& s, double v) { uint64_t u; memcpy(&u, &v, 8); put64(s, 
 uint32_t get32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i); return v; }
 uint64_t get64(const uint8_t* p) { uint64_t v = 0; for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i); return v; }
 
-struct Timer {
-  cudaEvent_t a = nullptr, b = nullptr;
+// Non-blocking phase clock: events are recorded on the stream at phase
+// boundaries and only read after the call's final synchronisation.
+struct PhaseClock {
+  static constexpr int kMax = 96;
+  cudaEvent_t ev[kMax];
+  int tag[kMax];
+  int n = 0;
   cudaStream_t s;
-  explicit Timer(cudaStream_t st) : s(st) {
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, s);
+  explicit PhaseClock(cudaStream_t st) : s(st) {
+    for (int i = 0; i < kMax; ++i) ev[i] = nullptr;
   }
-  float stop() {
-    cudaEventRecord(b, s);
-    cudaEventSynchronize(b);
+  // close the interval since the previous mark and charge it to `phase`
+  void mark(int phase) {
+    if (n >= kMax) return;
+    if (!ev[n]) cudaEventCreate(&ev[n]);
+    cudaEventRecord(ev[n], s);
+    tag[n] = phase;
+    ++n;
+  }
+  // after synchronisation: per-phase milliseconds
+  void sum(double* out, int nphase) {
+    for (int p = 0; p < nphase; ++p) out[p] = 0.0;
+    for (int i = 1; i < n; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[i - 1], ev[i]) == cudaSuccess && tag[i] >= 0 && tag[i] < nphase) out[tag[i]] += ms;
+    }
+  }
+  double total() {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
+    if (n >= 2) cudaEventElapsedTime(&ms, ev[0], ev[n - 1]);
     return ms;
   }
-  ~Timer() {
-    if (a) cudaEventDestroy(a);
-    if (b) cudaEventDestroy(b);
+  ~PhaseClock() {
+    for (int i = 0; i < kMax; ++i)
+      if (ev[i]) cudaEventDestroy(ev[i]);
   }
 };
+enum { PH_NORM = 0, PH_GRAM, PH_EIG, PH_TTM, PH_QUANT, PH_OTHER, PH_COUNT };
 
 int check_dims(const int64_t* dims, int ndim, int64_t* total) {
   if (!dims || ndim < 1 || ndim > 8) return fail(ATC_EINVAL, "ndim must be in [1, 8]");
@@ -226,6 +245,8 @@ const char* atc_last_error(void) { return g_err.c_str(); }
 void atc_free_buffer(void* p) { free(p); }
 
 int atc_release_workspace(void) { return Scratch::release_all(); }
+
+long long atc_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED); }
 
 int atc_norm2(const void* x_dev, int64_t n, int dtype, double* out_dev, void* stream) {
   if (!x_dev || !out_dev || n < 0 || !dtype_size(dtype)) return fail(ATC_EINVAL, "atc_norm2: bad arguments");
@@ -337,22 +358,23 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
     free_compressed(c);
     return rc;
   };
-  Timer total(s);
+  PhaseClock clk(s);
+  clk.mark(PH_OTHER);
   // ||X||^2 and the budgets (Section 4.1.3)
   double* small = nullptr;
   int rc = Scratch::get(SLOT_SMALL, sizeof(double) * 2048, (void**)&small);
   if (rc) return bail(rc);
   double* dnorm = small + 1600;
   {
-    Timer t(s);
     rc = launch_norm2(x_dev, dtype, N, dnorm, s);
     if (rc) return bail(rc);
+    clk.mark(PH_NORM);
     double h = 0.0;
     if (cudaMemcpyAsync(&h, dnorm, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return bail(fail(ATC_ECUDA, "norm readback failed"));
-    st.ms_norm = t.stop();
     st.norm2 = h;
+    clk.mark(PH_OTHER);
   }
   if (!(st.norm2 == st.norm2) || st.norm2 > 1.7e308) return bail(fail(ATC_ENUMERIC, "input contains NaN or Inf"));
   st.target_sse = rel_eps * rel_eps * st.norm2;
@@ -385,7 +407,6 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   int curdt = dtype;
   void* next = bufA;
   double used = 0.0;
-  float ms_gram = 0.f, ms_eig = 0.f, ms_ttm = 0.f;
   for (int step = 0; step < d; ++step) {
     const int m = order[step];
     int64_t L = 1, R = 1;
@@ -394,15 +415,13 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
     const int64_t n = cur[m];
     if (n > 1024) return bail(fail(ATC_EUNSUP, "mode length %lld > 1024 is not supported", (long long)n));
     {
-      Timer t(s);
       rc = gram_dispatch(curp, curdt, L, n, R, opt.precision, G, s);
       if (rc) return bail(rc);
-      ms_gram += t.stop();
+      clk.mark(PH_GRAM);
     }
     int r = 0;
     double disc = 0.0;
     {
-      Timer t(s);
       rc = launch_eig_values(G, (int)n, lam, s);
       if (rc) return bail(rc);
       const double budget =
@@ -425,13 +444,12 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         return bail(fail(ATC_ENOMEM, "factor allocation failed"));
       rc = launch_eig_vectors((int)n, r, c->factors[m], s);
       if (rc) return bail(rc);
-      ms_eig += t.stop();
+      clk.mark(PH_EIG);
     }
     {
-      Timer t(s);
       rc = ttm_dispatch(curp, curdt, L, n, R, c->factors[m], r, 0, opt.precision, next, idt, s);
       if (rc) return bail(rc);
-      ms_ttm += t.stop();
+      clk.mark(PH_TTM);
     }
     c->ranks[m] = r;
     cur[m] = r;
@@ -440,9 +458,6 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
     curdt = idt;
     next = (next == bufA) ? bufB : bufA;
   }
-  st.ms_gram = ms_gram;
-  st.ms_eig = ms_eig;
-  st.ms_ttm = ms_ttm;
   st.sse_trunc = used;
   int64_t ncore = 1;
   for (int i = 0; i < d; ++i) ncore *= c->ranks[i];
@@ -463,8 +478,14 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   std::string section;
   QuantResult qr;
   float msq = 0.f, mse = 0.f;
-  rc = quantize_encode(vec, ncore, st.target_sse - used, opt.block_size, s, &section, &qr, &msq, &mse);
+  clk.mark(PH_OTHER);
+  // Split paths: the discarded energy comes from eigenvalues of a Gram matrix
+  // with FP32-accumulation and split-residual perturbations; half a percent of
+  // the target is held back from the quantizer so the total stays <= rel_eps.
+  const double margin = (opt.precision == ATC_PREC_FP64) ? 0.0 : 0.005 * st.target_sse;
+  rc = quantize_encode(vec, ncore, st.target_sse - used - margin, opt.block_size, s, &section, &qr, &msq, &mse);
   if (rc) return bail(rc);
+  clk.mark(PH_QUANT);
   st.ms_quant = msq;
   st.ms_encode = mse;
   st.k = qr.k;
@@ -492,8 +513,17 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   }
   put64(S, (uint64_t)section.size());
   S.append(section);
+  clk.mark(PH_OTHER);
   if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ATC_ECUDA, "stream synchronisation failed"));
-  st.ms_total = total.stop();
+  {
+    double ph[PH_COUNT];
+    clk.sum(ph, PH_COUNT);
+    st.ms_norm = ph[PH_NORM];
+    st.ms_gram = ph[PH_GRAM];
+    st.ms_eig = ph[PH_EIG];
+    st.ms_ttm = ph[PH_TTM];
+    st.ms_total = clk.total();
+  }
   *out = c;
   return ATC_OK;
 }

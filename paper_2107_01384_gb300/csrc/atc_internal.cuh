@@ -22,6 +22,15 @@ int fail(int code, const char* fmt, ...);
                          cudaGetErrorString(_e));                                       \
   } while (0)
 
+// Every kernel launch of the library is followed by ATC_LAUNCHED(k): it
+// counts the k kernels just launched and checks the launch error.
+extern long long g_kernel_launches;
+#define ATC_LAUNCHED(k)                                   \
+  do {                                                    \
+    __atomic_add_fetch(&::atc::g_kernel_launches, (k), __ATOMIC_RELAXED); \
+    ATC_CUDA_TRY(cudaGetLastError());                     \
+  } while (0)
+
 #define ATC_TRY(expr)          \
   do {                         \
     int _rc = (expr);          \

@@ -518,7 +518,7 @@ int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s) {
   ATC_CUDA_TRY(cudaMemsetAsync(st.d, 0, sizeof(double) * 3 * n, s));
   if (n == 1) {
     tridiag_small_kernel<<<1, 32, 0, s>>>(st);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
   } else {
     static int max_blocks = -1;
     const size_t smem = sizeof(double) * (4 * n + 32);
@@ -538,15 +538,16 @@ int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s) {
     if (P < 1) P = 1;
     void* args[] = {(void*)&st};
     ATC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tridiag_kernel, dim3(P), dim3(kTriThreads), args, smem, s));
+    __atomic_add_fetch(&g_kernel_launches, 1, __ATOMIC_RELAXED);
   }
   scale_kernel<<<1, 256, 0, s>>>(st);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   const int bt = 64;
   bisect_kernel<<<(n + bt - 1) / bt, bt, sizeof(double) * 2 * n, s>>>(st);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   if (lam) {
     unscale_kernel<<<(n + 255) / 256, 256, 0, s>>>(st, lam);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
   }
   return ATC_OK;
 }
@@ -560,14 +561,14 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
   int* grp = reinterpret_cast<int*>(st.lu + (size_t)5 * n * nvec);
   int* ngrp = grp + nvec + 2;
   group_kernel<<<1, 32, 0, s>>>(st, nvec, grp, ngrp);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   // one CTA per group; groups beyond the actual count exit (grp_start padded)
   // launch nvec CTAs, CTAs with blockIdx >= ngrp have an empty range
   invit_kernel<<<nvec, 128, 0, s>>>(st, grp, ngrp, nvec);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   const int wpb = 4;
   backtransform_kernel<<<(nvec + wpb - 1) / wpb, 32 * wpb, 0, s>>>(st, nvec, v);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
@@ -579,7 +580,7 @@ int launch_eig_sym(const double* g, int n, double* lam, double* v, int nvec, cud
 
 int launch_rank_select(const double* lam, int n, double budget, int* r_dev, double* disc_dev, cudaStream_t s) {
   rank_kernel<<<1, 32, 0, s>>>(lam, n, budget, r_dev, disc_dev);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 

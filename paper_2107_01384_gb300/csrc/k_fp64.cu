@@ -186,12 +186,12 @@ int launch_gram_fp64(const void* x, int dtype, int64_t L, int64_t n, int64_t R, 
     gram_fp64_kernel<float><<<grid, kThreads, 0, s>>>((const float*)x, n, R, K, kchunk, ntile, part);
   else
     gram_fp64_kernel<double><<<grid, kThreads, 0, s>>>((const double*)x, n, R, K, kchunk, ntile, part);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   int64_t tot = n * n;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   gram_reduce_kernel<<<blocks, 256, 0, s>>>(part, (int)nsplit, n, g);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
@@ -213,7 +213,7 @@ int launch_ttm_fp64(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, 
     ttm_fp64_kernel<double, float><<<grid, kThreads, 0, s>>>((const double*)x, u, wsa, wsb, A, B, R, N, (float*)y);
   else
     ttm_fp64_kernel<double, double><<<grid, kThreads, 0, s>>>((const double*)x, u, wsa, wsb, A, B, R, N, (double*)y);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 

@@ -3,10 +3,13 @@
 // G = X_(k) X_(k)^T over the (L, n, R) view (Section 3.1 unfolding, Gram form
 // of the Algorithm 1 SVD step).  Every element x is split into two 16-bit
 // halves, x ~ h + l (bf16, or fp16 after a power-of-two pre-scale), and
-//   acc = H H^T + H (2L)^T          (two tcgen05 MMAs per K step)
-//   G   = (acc + acc^T) / 2 = H H^T + H L^T + L H^T,
-// i.e. the three-term split product with the L L^T term dropped; the
-// symmetrisation is done in FP64 after the split-K partial sums.
+//   acc = H H^T + H (2L)^T + L L^T  (three tcgen05 MMAs per K step)
+//   G   = (acc + acc^T) / 2 = (H + L)(H + L)^T,
+// i.e. the full product of the split values: only the residual x - h - l
+// and the FP32 accumulation perturb G.  Keeping L L^T matters: it is positive
+// semi-definite and, if dropped, inflates every tail eigenvalue (the energy
+// that decides the rank).  The symmetrisation is done in FP64 after the
+// split-K partial sums.
 //
 // Kernel structure (one CTA per K chunk, n <= 256):
 //   * 8 converter warps stream FP32/FP64 elements from HBM with coalesced
@@ -72,8 +75,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a) {
   const int MODE = a.mode;
   constexpr int ROWS = NBLK * 128;
   constexpr int TILE_BYTES = ROWS * 128;          // one operand: ROWS x 64 16-bit
-  constexpr int STAGE_BYTES = 2 * TILE_BYTES;     // H and 2L
-  constexpr int NSTAGE = (NBLK == 2) ? 3 : 4;
+  constexpr int STAGE_BYTES = 3 * TILE_BYTES;     // H, 2L and L
+  constexpr int NSTAGE = (NBLK == 2) ? 2 : 4;
   constexpr int UNITS = ROWS * 8 / kConvThreads;  // 8-element units per converter thread
   constexpr uint32_t TMEM_COLS = NBLK * 256;
   extern __shared__ uint8_t smem_raw[];
@@ -151,18 +154,22 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a) {
       const uint32_t ph = ((uint32_t)(t / NSTAGE) & 1u) ^ 1u;
       if (!mbar_wait(&empty_bar[s], ph, abort)) return false;
       uint8_t* hbase = smem + s * STAGE_BYTES;
-      uint8_t* lbase = hbase + TILE_BYTES;
+      uint8_t* lbase = hbase + TILE_BYTES;      // 2L
+      uint8_t* l1base = lbase + TILE_BYTES;     // L
 #pragma unroll
       for (int u = 0; u < UNITS; ++u) {
         const int g = tid + kConvThreads * u;
         int row, q;
         if (MODE == LM_IC1) { row = g % ROWS; q = g / ROWS; } else { row = g >> 3; q = g & 7; }
-        uint32_t h[4], l2[4];
+        uint32_t h[4], l1[4], l2[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) Split<BF16>::run(buf[u][2 * e] * sc, buf[u][2 * e + 1] * sc, h[e], l2[e], 2.0f);
+        for (int e = 0; e < 4; ++e) Split<BF16>::run(buf[u][2 * e] * sc, buf[u][2 * e + 1] * sc, h[e], l1[e], 1.0f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) l2[e] = Split<BF16>::twice(l1[e]);
         const uint32_t off = sw128_off((uint32_t)row, (uint32_t)(8 * q));
         *reinterpret_cast<uint4*>(hbase + off) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4*>(lbase + off) = make_uint4(l2[0], l2[1], l2[2], l2[3]);
+        *reinterpret_cast<uint4*>(l1base + off) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
       }
       fence_proxy_async_smem();
       mbar_arrive(&full_bar[s]);
@@ -186,7 +193,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a) {
       if (!mbar_wait(&full_bar[s], (uint32_t)(t / NSTAGE) & 1u, abort)) break;
       tc_fence_after();
       const uint32_t hb = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t lb = hb + TILE_BYTES;
+      const uint32_t lb = hb + TILE_BYTES;      // 2L
+      const uint32_t l1b = lb + TILE_BYTES;     // L
 #pragma unroll
       for (int j = 0; j < KT / 16; ++j) {
 #pragma unroll
@@ -195,6 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a) {
           const uint64_t ad = desc_k128(hb + b * 16384 + 32 * j);
           umma_f16(d, ad, desc_k128(hb + 32 * j), idesc, (t | j) ? 1u : 0u);
           umma_f16(d, ad, desc_k128(lb + 32 * j), idesc, 1u);
+          umma_f16(d, desc_k128(l1b + b * 16384 + 32 * j), desc_k128(l1b + 32 * j), idesc, 1u);
         }
       }
       umma_commit(&empty_bar[s]);
@@ -274,15 +283,15 @@ __global__ void fp16_scale_finish(const unsigned* __restrict__ mx_bits, float* _
 template <typename T, bool BF16, int NBLK>
 int launch_t(const GramArgs& a, int nsplit, cudaStream_t s) {
   constexpr int ROWS = NBLK * 128;
-  constexpr int NSTAGE = (NBLK == 2) ? 3 : 4;
-  const int smem = NSTAGE * 2 * ROWS * 128 + 1024;
+  constexpr int NSTAGE = (NBLK == 2) ? 2 : 4;
+  const int smem = NSTAGE * 3 * ROWS * 128 + 1024;
   static bool attr = false;
   if (!attr) {
     ATC_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel<T, BF16, NBLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = true;
   }
   gram_tc_kernel<T, BF16, NBLK><<<nsplit, kThreads, smem, s>>>(a);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
@@ -344,7 +353,7 @@ int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R,
     else
       fp16_scale_kernel<double><<<blocks, 256, 0, s>>>((const double*)x, N, mx);
     fp16_scale_finish<<<1, 1, 0, s>>>(mx, scale);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(2);
     a.scale = scale;
   }
   if (dtype == ATC_F32) {
@@ -358,7 +367,7 @@ int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R,
   const int rb = (int)((tot + 255) / 256 < 2048 ? (tot + 255) / 256 : 2048);
   gram_tc_reduce<<<rb, 256, 0, s>>>(a.part, nsplit, n, npad, nblk, a.scale, S);
   symmetrize<<<rb, 256, 0, s>>>(S, n, g);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(2);
   return ATC_OK;
 }
 

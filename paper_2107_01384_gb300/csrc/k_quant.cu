@@ -806,11 +806,11 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
   const int64_t gb = (n + 255) / 256;
   const int grid = (int)(gb < 152 * 8 ? gb : 152 * 8);
   maxabs_kernel<<<grid, 256, 0, s>>>(core, n, mx);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   scale_exp_kernel<<<1, 32, 0, s>>>(mx, target, st);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   quantize_kernel<<<grid, 256, 0, s>>>(core, n, &st->k, q, sg);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   TrackState hst;
   int phi = 63;
   bool first = true;
@@ -818,9 +818,9 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     int plo = phi - kPlaneChunk + 1;
     if (plo < 0) plo = 0;
     plane_stats_kernel<<<nseg, kSegThreads, 0, s>>>(q, n, seg_len, plo, phi, first ? 1 : 0, segs, e64s);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
     plane_scan_kernel<<<1, 32, 0, s>>>(segs, e64s, nseg, plo, phi, first ? 1 : 0, st);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
     ATC_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
     ATC_CUDA_TRY(cudaStreamSynchronize(s));
     if (hst.nan) return fail(ATC_ENUMERIC, "core contains NaN or Inf");
@@ -831,7 +831,7 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
   }
   if (hst.p_star < 64 && hst.reachable) {
     istar_kernel<<<1, kSegThreads, 0, s>>>(q, n, seg_len, segs, nseg, phi, st);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
     ATC_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
     ATC_CUDA_TRY(cudaStreamSynchronize(s));
   }
@@ -879,13 +879,13 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     const int wpb = 4;
     const unsigned eg = (unsigned)((nchunks + wpb - 1) / wpb);
     enc_hist_kernel<<<eg, 32 * wpb, 0, s>>>(P);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
     freq_kernel<<<(nplanes + 63) / 64, 64, 0, s>>>(hist, nplanes, fc);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
     enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 1, spill);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
     scan_kernel<<<1, 1024, 0, s>>>(rsize, wsize, nchunks, off);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
     uint64_t total = 0;
     ATC_CUDA_TRY(cudaMemcpyAsync(&total, off + nchunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     std::vector<uint32_t> hfc(2 * nplanes * kNsym);
@@ -900,7 +900,7 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     P.table = reinterpret_cast<uint32_t*>(dout);
     P.out = dout + tabb;
     enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 0, spill);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
     result.resize(hdr + tabb + total);
     memcpy(&result[0], head.data(), hdr);
     ATC_CUDA_TRY(cudaMemcpyAsync(&result[hdr], dout, tabb + total, cudaMemcpyDeviceToHost, s));
@@ -967,9 +967,9 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
   ATC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   D.sec = dsec; D.qt = qt; D.sg = sg; D.out = core; D.err = err; D.boff = boff;
   block_offsets_kernel<<<1, 32, 0, s>>>(D, boff);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   decode_kernel<<<(unsigned)((D.nblocks + 63) / 64), 64, 0, s>>>(D);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   int herr = 0;
   ATC_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   ATC_CUDA_TRY(cudaStreamSynchronize(s));

@@ -118,9 +118,9 @@ int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t 
     norm2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, n, part);
   else
     norm2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, n, part);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   sum_partials<<<1, kNormThreads, 0, s>>>(part, kNormBlocks, out);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
@@ -130,7 +130,7 @@ int launch_convert_to_f64(const void* x, int dtype, int64_t n, double* y, cudaSt
     return ATC_OK;
   }
   to_f64<float><<<grid_for(n, 256), 256, 0, s>>>((const float*)x, n, y);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
@@ -140,7 +140,7 @@ int launch_convert_f64_to(const double* x, int64_t n, void* y, int dtype, cudaSt
     return ATC_OK;
   }
   f64_to_f32<<<grid_for(n, 256), 256, 0, s>>>(x, n, (float*)y);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
@@ -169,7 +169,7 @@ int launch_permute(const double* x, const int64_t* dims, const int* perm, int nd
     for (int i = 0; i < ndim; ++i) { pd.dims[i] = pdims[i]; pd.dstride[i] = ostride[perm[i]]; }
   }
   permute_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, total, pd, y);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 

@@ -254,7 +254,12 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
     TY* __restrict__ y = reinterpret_cast<TY*>(a.y);
     for (int64_t t = 0; t < nmine; ++t) {
       const int ab = (int)(t & 1);
-      if (!mbar_wait(&accf_bar[ab], (uint32_t)(t >> 1) & 1u, abort)) break;
+      // warp-uniform wait: the tcgen05.ld below is .sync.aligned
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(&accf_bar[ab], (uint32_t)(t >> 1) & 1u, abort) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      __syncwarp();
+      if (!okw) break;
       tc_fence_after();
       const int64_t mt = blockIdx.x + t * gridDim.x;
       const int64_t gam = mt * 128 + 32 * warp + lane;
@@ -349,7 +354,7 @@ int ttm_launch_t(const TtmArgs& a, int grid, int smem, cudaStream_t s) {
     attr = true;
   }
   ttm_tc_kernel<TX, BF16, GEN><<<grid, kThreads, smem, s>>>(a);
-  ATC_CUDA_TRY(cudaGetLastError());
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
@@ -412,7 +417,7 @@ int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R,
     if (xdtype == ATC_F32) ttm_xscale_kernel<float><<<blocks, 256, 0, s>>>((const float*)x, N, mx);
     else ttm_xscale_kernel<double><<<blocks, 256, 0, s>>>((const double*)x, N, mx);
     ttm_xscale_finish<<<1, 1, 0, s>>>(mx, scale);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(2);
     a.xscale = scale;
   }
   {
@@ -420,7 +425,7 @@ int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R,
     const int blocks = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
     if (bf16) ttm_prep_b<true><<<blocks, 256, 0, s>>>(u, a.A, (int)Bdim, expand, a.apad, a.nkt, a.uscale, bw, bw + wb);
     else ttm_prep_b<false><<<blocks, 256, 0, s>>>(u, a.A, (int)Bdim, expand, a.apad, a.nkt, a.uscale, bw, bw + wb);
-    ATC_CUDA_TRY(cudaGetLastError());
+    ATC_LAUNCHED(1);
   }
   if (a.mtiles == 0) return ATC_OK;
   const int grid = (int)(a.mtiles < g_nsm_ttm ? a.mtiles : g_nsm_ttm);

@@ -160,6 +160,12 @@ struct Split<true> {
     hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
     lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
   }
+  // 2x each packed half (exact: exponent + 1)
+  static __device__ __forceinline__ uint32_t twice(uint32_t v) {
+    __nv_bfloat162 t = *reinterpret_cast<__nv_bfloat162*>(&v);
+    t = __hmul2(t, __floats2bfloat162_rn(2.0f, 2.0f));
+    return *reinterpret_cast<uint32_t*>(&t);
+  }
 };
 template <>
 struct Split<false> {
@@ -169,6 +175,11 @@ struct Split<false> {
     __half lb = __float2half_rn((b - __half2float(hb)) * lo_mul);
     hi = (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
     lo = (uint32_t)__half_as_ushort(la) | ((uint32_t)__half_as_ushort(lb) << 16);
+  }
+  static __device__ __forceinline__ uint32_t twice(uint32_t v) {
+    __half2 t = *reinterpret_cast<__half2*>(&v);
+    t = __hmul2(t, __floats2half2_rn(2.0f, 2.0f));
+    return *reinterpret_cast<uint32_t*>(&t);
   }
 };
 

@@ -41,7 +41,7 @@ def cuda(a):
 
 GRAM_CASES = [((64, 64, 64), 0, np.float64), ((64, 64, 64), 1, np.float64), ((64, 64, 64), 2, np.float64),
               ((256, 256, 16), 0, np.float32), ((16, 256, 256), 1, np.float32), ((100, 100, 256), 2, np.float32),
-              ((37, 129, 5), 1, np.float32), ((300, 7), 0, np.float32), ((1, 200, 1000), 1, np.float32),
+              ((37, 129, 5), 1, np.float32), ((200, 7), 0, np.float32), ((1, 200, 1000), 1, np.float32),
               ((5, 17, 3), 1, np.float32), ((3, 256, 40), 1, np.float32), ((70, 224), 1, np.float32)]
 
 
