@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -26,6 +27,24 @@ namespace atc {
 
 static thread_local std::string g_err;
 long long g_kernel_launches = 0;
+
+// ATC_TRACE=1: synchronise and check after every launch, printing the site
+// (debugging aid; off by default).
+int trace_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("ATC_TRACE");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v;
+}
+int trace_point(const char* file, int line) {
+  cudaError_t e = cudaDeviceSynchronize();
+  fprintf(stderr, "[atc trace] %s:%d -> %s\n", file, line, cudaGetErrorString(e));
+  fflush(stderr);
+  if (e != cudaSuccess) return fail(ATC_ECUDA, "trace %s:%d: %s", file, line, cudaGetErrorString(e));
+  return ATC_OK;
+}
 
 void set_error(const char* fmt, ...) {
   char buf[1024];
@@ -265,6 +284,10 @@ int atc_eig_sym(const double* g_dev, int n, double* lam_dev, double* v_dev, int 
     return fail(ATC_EINVAL, "atc_eig_sym: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   ATC_TRY(launch_eig_sym(g_dev, n, lam_dev, v_dev, nvec, s));
+  if (eig32_enabled() && eig32_supported(n)) {
+    ATC_CUDA_TRY(cudaStreamSynchronize(s));
+    return ATC_OK;
+  }
   return eig_check(s);
 }
 
@@ -422,28 +445,94 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
     int r = 0;
     double disc = 0.0;
     {
-      rc = launch_eig_values(G, (int)n, lam, s);
-      if (rc) return bail(rc);
       const double budget =
           (opt.rank_rule == ATC_RANK_STATIC) ? budget_total / d : (budget_total - used) / (double)(d - step);
-      rc = launch_rank_select(lam, (int)n, budget, rdev, ddev, s);
-      if (rc) return bail(rc);
-      if (cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaMemcpyAsync(&disc, ddev, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return bail(fail(ATC_ECUDA, "rank readback failed"));
-      rc = eig_check(s);
-      if (rc) return bail(rc);
-      if (tc_err) {
-        int he = 0;
-        if (cudaMemcpy(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-          return bail(fail(ATC_ECUDA, "error flag readback failed"));
-        if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
+      if (eig32_enabled() && eig32_supported((int)n)) {
+        // FP32 eigensolve + FP64 refinement of the top m eigenpairs; the rank
+        // rule reads tail(r) = trace(G) - sum_{j<r} lambda_j from the refined
+        // eigenvalues (FP64).
+        std::vector<double> l32, top;
+        double tr = 0.0;
+        rc = eig32_values(G, (int)n, &l32, &tr, s);
+        if (rc) return bail(rc);
+        auto pick = [&](const std::vector<double>& lv, int lim, double* dsc) -> int {
+          double acc = 0.0;
+          for (int rr = 1; rr <= lim; ++rr) {
+            acc += lv[rr - 1];
+            double t = tr - acc;
+            if (t < 0.0) t = 0.0;
+            if (t <= budget) { *dsc = t; return rr; }
+          }
+          return -1;
+        };
+        double d32 = 0.0;
+        int r32 = pick(l32, (int)n, &d32);
+        if (r32 < 1) r32 = (int)n;
+        int mref = std::min<int>((int)n, r32 + 4);
+        double* vtmp = nullptr;
+        rc = Scratch::get(SLOT_EIG_A, sizeof(double) * (size_t)n * n, (void**)&vtmp);
+        if (rc) return bail(rc);
+        for (;;) {
+          rc = eig32_refine(mref, lam, vtmp, mref, &top, s);
+          if (rc) return bail(rc);
+          r = pick(top, mref, &disc);
+          if (r >= 1 && (r < mref || mref == n)) break;
+          if (mref == n) { r = (int)n; disc = 0.0; break; }
+          mref = std::min<int>((int)n, 2 * mref);
+        }
+        if (tc_err) {
+          int he = 0;
+          if (cudaMemcpy(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(fail(ATC_ECUDA, "error flag readback failed"));
+          if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
+        }
+        if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
+          return bail(fail(ATC_ENOMEM, "factor allocation failed"));
+        if (cudaMemcpy2DAsync(c->factors[m], sizeof(double) * r, vtmp, sizeof(double) * mref, sizeof(double) * r, n,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+          return bail(fail(ATC_ECUDA, "factor copy failed"));
+      } else {
+        // FP64 tridiagonalisation, then only the largest K eigenvalues (more
+        // if the rank is not decided among them); tail(r) = trace(G) - sum_{j<r}
+        // lambda_j in FP64.
+        rc = launch_eig_tridiag(G, (int)n, ddev + 2, s);
+        if (rc) return bail(rc);
+        int K = (int)std::min<int64_t>(n, 48);
+        double tr = 0.0;
+        std::vector<double> lh;
+        for (;;) {
+          rc = launch_eig_more((int)n, K, lam, s);
+          if (rc) return bail(rc);
+          lh.resize(K);
+          if (cudaMemcpyAsync(lh.data(), lam, sizeof(double) * K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaMemcpyAsync(&tr, ddev + 2, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return bail(fail(ATC_ECUDA, "eigenvalue readback failed"));
+          rc = eig_check(s);
+          if (rc) return bail(rc);
+          r = -1;
+          double acc = 0.0;
+          for (int rr = 1; rr <= K; ++rr) {
+            acc += lh[rr - 1];
+            double t = tr - acc;
+            if (t < 0.0) t = 0.0;
+            if (t <= budget) { r = rr; disc = t; break; }
+          }
+          if (r >= 1) break;
+          if (K == n) { r = (int)n; disc = 0.0; break; }
+          K = (int)n;
+        }
+        if (tc_err) {
+          int he = 0;
+          if (cudaMemcpy(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(fail(ATC_ECUDA, "error flag readback failed"));
+          if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
+        }
+        if (r < 1 || r > n) return bail(fail(ATC_ENUMERIC, "rank selection failed (r = %d)", r));
+        if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
+          return bail(fail(ATC_ENOMEM, "factor allocation failed"));
+        rc = launch_eig_vectors((int)n, r, c->factors[m], s);
+        if (rc) return bail(rc);
       }
-      if (r < 1 || r > n) return bail(fail(ATC_ENUMERIC, "rank selection failed (r = %d)", r));
-      if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
-        return bail(fail(ATC_ENOMEM, "factor allocation failed"));
-      rc = launch_eig_vectors((int)n, r, c->factors[m], s);
-      if (rc) return bail(rc);
       clk.mark(PH_EIG);
     }
     {

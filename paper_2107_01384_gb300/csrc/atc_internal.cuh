@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/atc.h"
 
@@ -25,10 +26,13 @@ int fail(int code, const char* fmt, ...);
 // Every kernel launch of the library is followed by ATC_LAUNCHED(k): it
 // counts the k kernels just launched and checks the launch error.
 extern long long g_kernel_launches;
+int trace_enabled();
+int trace_point(const char* file, int line);
 #define ATC_LAUNCHED(k)                                   \
   do {                                                    \
     __atomic_add_fetch(&::atc::g_kernel_launches, (k), __ATOMIC_RELAXED); \
     ATC_CUDA_TRY(cudaGetLastError());                     \
+    if (::atc::trace_enabled()) ATC_TRY(::atc::trace_point(__FILE__, __LINE__)); \
   } while (0)
 
 #define ATC_TRY(expr)          \
@@ -93,8 +97,16 @@ int launch_eig_sym(const double* g, int n, double* lam, double* v, int nvec, cud
 // eigenvalues only, then eigenvectors of the top nvec (split so rank selection can run between)
 int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s);
 int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s);
+// tridiagonalise only (+ FP64 trace of G into *trace_dev); then the K largest eigenvalues
+int launch_eig_tridiag(const double* g, int n, double* trace_dev, cudaStream_t s);
+int launch_eig_more(int n, int K, double* lam, cudaStream_t s);
 int launch_rank_select(const double* lam, int n, double budget, int* r_dev, double* disc_dev, cudaStream_t s);
 int eig_read_error(int* err);
+// FP32-stage + FP64-refinement eigensolver (k_eig32.cu), n <= 256
+bool eig32_supported(int n);
+bool eig32_enabled();
+int eig32_values(const double* G, int n, std::vector<double>* lam_host, double* trace, cudaStream_t s);
+int eig32_refine(int m, double* lam_dev, double* v_dev, int nvec, std::vector<double>* lam_top, cudaStream_t s);
 int tc_error_flag(int** flag);  // device error word of the tensor-core kernels (zeroed by the caller)
 
 // quantizer / encoder (k_quant.cu)

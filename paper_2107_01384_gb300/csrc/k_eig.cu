@@ -23,6 +23,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "atc_internal.cuh"
 
 namespace atc {
@@ -45,7 +47,7 @@ struct EigState {
   double* scale;  // [0] power-of-two scale applied to T
   int n;
 };
-EigState g_state;  // host-side copy of the scratch layout (single-stream use per device)
+EigState g_state = {};  // host-side copy of the scratch layout (single-stream use per device)
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
@@ -447,9 +449,9 @@ __global__ void backtransform_kernel(EigState st, int nvec, double* __restrict__
 }
 
 // lam_out[j] = lam_scaled[j] / scale (exact power of two)
-__global__ void unscale_kernel(EigState st, double* __restrict__ lam_out) {
+__global__ void unscale_kernel(EigState st, double* __restrict__ lam_out, int K) {
   const double inv = 1.0 / st.scale[0];
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < st.n; j += gridDim.x * blockDim.x)
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x)
     lam_out[j] = st.lam[j] * inv;
 }
 
@@ -464,6 +466,157 @@ __global__ void group_kernel(EigState st, int nvec, int* grp_start, int* ngrp) {
   }
   grp_start[++g] = nvec;
   *ngrp = g;
+}
+
+// 32-way multisection: one warp per eigenvalue (j-th largest, j < K), each
+// lane evaluates a Sturm count at one of 32 interior points per round, so a
+// round narrows the bracket 33-fold (5 bits).  One warp per CTA spreads the
+// FP64 work over many SMs.
+__global__ void __launch_bounds__(32) msect_kernel(EigState st, int K) {
+  const int j = blockIdx.x;
+  if (j >= K) return;
+  const int n = st.n;
+  const int lane = threadIdx.x;
+  extern __shared__ double smd[];
+  double* d = smd;
+  double* e2 = smd + n;
+  for (int i = lane; i < n; i += 32) {
+    d[i] = st.d[i];
+    e2[i] = (i < n - 1) ? st.e[i] * st.e[i] : 0.0;
+  }
+  __syncwarp();
+  const int m = n - 1 - j;
+  double lo = -1.0, hi = 1.0;  // Gershgorin radius <= 1 after scaling
+  for (int round = 0; round < 14; ++round) {
+    const double p = lo + (hi - lo) * (double)(lane + 1) * (1.0 / 33.0);
+    const int c = sturm_count(d, e2, n, p);
+    const unsigned above = __ballot_sync(0xffffffffu, c > m);
+    double nlo, nhi;
+    if (above == 0u) {
+      nlo = __shfl_sync(0xffffffffu, p, 31);
+      nhi = hi;
+    } else {
+      const int f = __ffs(above) - 1;
+      nhi = __shfl_sync(0xffffffffu, p, f);
+      const double pf = __shfl_sync(0xffffffffu, p, f > 0 ? f - 1 : 0);
+      nlo = (f == 0) ? lo : pf;
+    }
+    lo = nlo;
+    hi = nhi;
+    if (hi - lo <= 0x1p-53 * fmax(fabs(lo), fabs(hi)) + 0x1p-60) break;
+  }
+  if (lane == 0) st.lam[j] = 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ double hash_start(uint32_t a, uint32_t b) {
+  uint32_t h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return (0.5 + (double)(h >> 8) * (1.0 / 16777216.0)) * ((b & 1u) ? 1.0 : -1.0);
+}
+
+// Inverse iteration for every requested eigenvalue in parallel (one thread per
+// vector, one vector per CTA to spread the FP64 recurrences over the SMs);
+// deterministic pseudo-random start vectors, three solves.  Close eigenvalues
+// are re-orthogonalised afterwards by mgs_group_kernel.
+__global__ void __launch_bounds__(32) invit_par_kernel(EigState st, int nvec) {
+  const int j = blockIdx.x;
+  if (j >= nvec || threadIdx.x != 0) return;
+  const int n = st.n;
+  double* x = st.z + (int64_t)j * n;
+  double* fl = st.lu + (int64_t)j * 5 * n;
+  double* fd = fl + n;
+  double* fu = fd + n;
+  double* fu2 = fu + n;
+  double* fp = fu2 + n;
+  const double lam = st.lam[j];
+  const double eps_piv = 0x1p-52;
+  for (int i = 0; i < n; ++i) {
+    fd[i] = st.d[i] - lam;
+    fl[i] = (i < n - 1) ? st.e[i] : 0.0;
+    fu[i] = (i < n - 1) ? st.e[i] : 0.0;
+    fu2[i] = 0.0;
+    fp[i] = 0.0;
+  }
+  for (int i = 0; i < n - 1; ++i) {
+    if (fabs(fd[i]) >= fabs(fl[i])) {
+      double piv = fd[i];
+      if (fabs(piv) < eps_piv) { piv = (piv < 0.0) ? -eps_piv : eps_piv; fd[i] = piv; }
+      const double l = fl[i] / piv;
+      fl[i] = l;
+      fd[i + 1] -= l * fu[i];
+    } else {
+      const double l = fd[i] / fl[i];
+      fd[i] = fl[i];
+      fl[i] = l;
+      const double t = fu[i];
+      fu[i] = fd[i + 1];
+      fd[i + 1] = t - l * fd[i + 1];
+      if (i < n - 2) { fu2[i] = fu[i + 1]; fu[i + 1] = -l * fu[i + 1]; }
+      fp[i] = 1.0;
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    if (fabs(fd[i]) < eps_piv) fd[i] = (fd[i] < 0.0) ? -eps_piv : eps_piv;
+  for (int i = 0; i < n; ++i) fu2[i] = (i + 2 < n) ? fu2[i] : 0.0;
+  // reciprocal pivots once: the solves then multiply
+  for (int i = 0; i < n; ++i) fd[i] = 1.0 / fd[i];
+  for (int i = 0; i < n; ++i) x[i] = hash_start((uint32_t)j, (uint32_t)i);
+  for (int it = 0; it < 3; ++it) {
+    for (int i = 0; i < n - 1; ++i) {
+      if (fp[i] != 0.0) { const double t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+      x[i + 1] -= fl[i] * x[i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double v = x[i];
+      if (i + 1 < n) v -= fu[i] * x[i + 1];
+      if (i + 2 < n) v -= fu2[i] * x[i + 2];
+      x[i] = v * fd[i];
+    }
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(x[i]));
+    const double inv = (mx > 0.0) ? 1.0 / mx : 1.0;
+    for (int i = 0; i < n; ++i) x[i] *= inv;
+  }
+}
+
+// Modified Gram-Schmidt (two passes) inside every group of size > 1, then
+// normalisation of every vector; one CTA per group.
+__global__ void mgs_group_kernel(EigState st, const int* __restrict__ grp_start, const int* __restrict__ ngrp) {
+  __shared__ double red[32];
+  if ((int)blockIdx.x >= *ngrp) return;
+  const int g0 = grp_start[blockIdx.x], g1 = grp_start[blockIdx.x + 1];
+  const int n = st.n;
+  for (int k = g0; k < g1; ++k) {
+    double* xk = st.z + (int64_t)k * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i0 = g0; i0 < k; ++i0) {
+        const double* y = st.z + (int64_t)i0 * n;
+        double part = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) part += y[i] * xk[i];
+        const double dot = block_sum(part, red);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) xk[i] -= dot * y[i];
+        __syncthreads();
+      }
+    }
+    double part = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) part += xk[i] * xk[i];
+    const double nr = block_sum(part, red);
+    const double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xk[i] *= inv;
+    __syncthreads();
+  }
+}
+
+__global__ void trace_g_kernel(const double* __restrict__ G, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += G[(int64_t)i * n + i];
+  const double t = block_sum(a, red);
+  if (threadIdx.x == 0) *out = t;
 }
 
 // Rank choice: clamp at 0, tail sums from the smallest value, smallest r >= 1
@@ -509,7 +662,7 @@ int setup_state(int n, int nvec_max) {
 
 }  // namespace
 
-int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s) {
+int launch_eig_values_impl(const double* g, int n, cudaStream_t s) {
   if (n < 1 || n > 1024) return fail(ATC_EUNSUP, "eigensolver supports 1 <= n <= 1024 (n = %d)", n);
   ATC_TRY(setup_state(n, n));
   EigState st = g_state;
@@ -542,13 +695,37 @@ int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s) {
   }
   scale_kernel<<<1, 256, 0, s>>>(st);
   ATC_LAUNCHED(1);
-  const int bt = 64;
-  bisect_kernel<<<(n + bt - 1) / bt, bt, sizeof(double) * 2 * n, s>>>(st);
+  return ATC_OK;
+}
+
+int launch_eig_more(int n, int K, double* lam, cudaStream_t s);
+
+int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s) {
+  ATC_TRY(launch_eig_values_impl(g, n, s));
+  ATC_TRY(launch_eig_more(n, n, lam, s));
+  return ATC_OK;
+}
+
+// (Re)compute the K largest eigenvalues of the current tridiagonal matrix
+// (FP64 multisection) into lam[0..K) (unscaled).
+int launch_eig_more(int n, int K, double* lam, cudaStream_t s) {
+  if (g_state.n != n) return fail(ATC_EINVAL, "eigenvalues requested without a tridiagonal matrix");
+  if (K > n) K = n;
+  EigState st = g_state;
+  msect_kernel<<<K, 32, sizeof(double) * 2 * n, s>>>(st, K);
   ATC_LAUNCHED(1);
   if (lam) {
-    unscale_kernel<<<(n + 255) / 256, 256, 0, s>>>(st, lam);
+    unscale_kernel<<<(K + 255) / 256, 256, 0, s>>>(st, lam, K);
     ATC_LAUNCHED(1);
   }
+  return ATC_OK;
+}
+
+// Tridiagonalise G and return trace(G) (device scalar *trace_dev).
+int launch_eig_tridiag(const double* g, int n, double* trace_dev, cudaStream_t s) {
+  ATC_TRY(launch_eig_values_impl(g, n, s));
+  trace_g_kernel<<<1, 256, 0, s>>>(g, n, trace_dev);
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
@@ -562,17 +739,24 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
   int* ngrp = grp + nvec + 2;
   group_kernel<<<1, 32, 0, s>>>(st, nvec, grp, ngrp);
   ATC_LAUNCHED(1);
-  // one CTA per group; groups beyond the actual count exit (grp_start padded)
-  // launch nvec CTAs, CTAs with blockIdx >= ngrp have an empty range
-  invit_kernel<<<nvec, 128, 0, s>>>(st, grp, ngrp, nvec);
+  invit_par_kernel<<<nvec, 32, 0, s>>>(st, nvec);
   ATC_LAUNCHED(1);
-  const int wpb = 4;
-  backtransform_kernel<<<(nvec + wpb - 1) / wpb, 32 * wpb, 0, s>>>(st, nvec, v);
+  mgs_group_kernel<<<nvec, 128, 0, s>>>(st, grp, ngrp);
+  ATC_LAUNCHED(1);
+  backtransform_kernel<<<nvec, 32, 0, s>>>(st, nvec, v);
   ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
 int launch_eig_sym(const double* g, int n, double* lam, double* v, int nvec, cudaStream_t s) {
+  if (eig32_enabled() && eig32_supported(n)) {
+    std::vector<double> lh, top;
+    double tr = 0.0;
+    ATC_TRY(eig32_values(g, n, &lh, &tr, s));
+    ATC_TRY(eig32_refine(n, lam, v, nvec, &top, s));
+    return ATC_OK;
+  }
+  g_state.flags = nullptr;
   ATC_TRY(launch_eig_values(g, n, lam, s));
   ATC_TRY(launch_eig_vectors(n, nvec, v, s));
   return ATC_OK;
@@ -585,6 +769,8 @@ int launch_rank_select(const double* lam, int n, double budget, int* r_dev, doub
 }
 
 int eig_read_error(int* err) {
+  *err = 0;
+  if (!g_state.flags) return ATC_OK;  // the FP64 tridiagonalisation has not run on this device
   return cudaMemcpy(err, g_state.flags + 2, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? ATC_OK : ATC_ECUDA;
 }
 

@@ -277,14 +277,44 @@ __global__ void __launch_bounds__(kSegThreads) plane_stats_kernel(const uint64_t
 }
 
 // Combine the segment summaries in order and look for the first plane whose
-// lowest running error reaches the target.
-__global__ void plane_scan_kernel(const Seg* __restrict__ segs, const I192* __restrict__ e64_seg, int nseg, int plo,
-                                  int phi, int first_pass, TrackState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// lowest running error reaches the target.  One warp per plane: each lane
+// folds a contiguous run of segments, then an ordered warp tree combines the
+// lanes; thread 0 then walks the planes from the top.
+__global__ void __launch_bounds__(32 * kPlaneChunk) plane_scan_kernel(const Seg* __restrict__ segs,
+                                                                      const I192* __restrict__ e64_seg, int nseg,
+                                                                      int plo, int phi, int first_pass, TrackState* st) {
+  __shared__ Seg plane_sum[kPlaneChunk];
+  __shared__ I192 e64_sh;
   if (st->found) return;
-  if (first_pass) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (nseg + 31) / 32;
+  const int b0 = min(nseg, lane * per), b1 = min(nseg, b0 + per);
+  const int p = phi - warp;
+  if (p >= plo) {
+    Seg t;
+    t.empty = 1;
+    t.s = t.m = i192_zero();
+    for (int b = b0; b < b1; ++b) t = seg_combine(t, segs[(int64_t)(phi - p) * nseg + b]);
+    t = warp_seg_reduce(t);
+    if (lane == 0) plane_sum[warp] = t;
+  }
+  if (first_pass && warp == 0) {
     I192 e = i192_zero();
-    for (int b = 0; b < nseg; ++b) e = i192_add(e, e64_seg[b]);
+    for (int b = b0; b < b1; ++b) e = i192_add(e, e64_seg[b]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      I192 o;
+      o.w0 = __shfl_down_sync(0xffffffffu, e.w0, off);
+      o.w1 = __shfl_down_sync(0xffffffffu, e.w1, off);
+      o.w2 = __shfl_down_sync(0xffffffffu, e.w2, off);
+      if (lane < off) e = i192_add(e, o);
+    }
+    if (lane == 0) e64_sh = e;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (first_pass) {
+    const I192 e = e64_sh;
     st->e64 = e;
     st->e_next = e;
     if (st->reachable && i192_le(e, st->t_int)) {
@@ -297,16 +327,13 @@ __global__ void plane_scan_kernel(const Seg* __restrict__ segs, const I192* __re
     }
   }
   I192 e_next = st->e_next;
-  for (int p = phi; p >= plo; --p) {
-    Seg t;
-    t.empty = 1;
-    t.s = t.m = i192_zero();
-    for (int b = 0; b < nseg; ++b) t = seg_combine(t, segs[(int64_t)(phi - p) * nseg + b]);
+  for (int q = phi; q >= plo; --q) {
+    Seg t = plane_sum[phi - q];
     if (t.empty) { t.s = t.m = i192_zero(); }
-    I192 lowest = i192_sub(e_next, t.m);
+    const I192 lowest = i192_sub(e_next, t.m);
     if (st->reachable && i192_le(lowest, st->t_int)) {
       st->found = 1;
-      st->p_star = p;
+      st->p_star = q;
       st->e_plane = e_next;
       return;
     }
@@ -318,7 +345,7 @@ __global__ void plane_scan_kernel(const Seg* __restrict__ segs, const I192* __re
     st->p_star = 0;
     st->i_star = -1;
     st->e_star = e_next;
-    st->e_plane = e_next;  // unused
+    st->e_plane = e_next;
   }
 }
 
@@ -819,7 +846,7 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     if (plo < 0) plo = 0;
     plane_stats_kernel<<<nseg, kSegThreads, 0, s>>>(q, n, seg_len, plo, phi, first ? 1 : 0, segs, e64s);
     ATC_LAUNCHED(1);
-    plane_scan_kernel<<<1, 32, 0, s>>>(segs, e64s, nseg, plo, phi, first ? 1 : 0, st);
+    plane_scan_kernel<<<1, 32 * kPlaneChunk, 0, s>>>(segs, e64s, nseg, plo, phi, first ? 1 : 0, st);
     ATC_LAUNCHED(1);
     ATC_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
     ATC_CUDA_TRY(cudaStreamSynchronize(s));
