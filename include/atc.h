@@ -184,6 +184,24 @@ int atc_ttm(const void* x_dev, int xdtype, int64_t L, int64_t n, int64_t R, cons
 int atc_quantize_core(const double* core_dev, int64_t n, double target_sse, int block_size, void* stream,
                       uint8_t** bytes, size_t* nbytes, int64_t* info);
 
+/*
+ * atc_gram with precision ATC_PREC_FP64, for callers that cannot allocate
+ * device memory (for example code running while somebody else builds a CUDA
+ * graph around it, or a host that gives this library a fixed memory budget).
+ * The paper has no counterpart: it is an integration variant of the Gram step.
+ *   Same arguments, layout and result as atc_gram (g_dev: n*n doubles, full
+ *   symmetric).  It calls no cudaMalloc, cudaFree or allocating library
+ *   routine: the split-K partial sums live in a 4 MiB array in this library's
+ *   device memory, held by every GPU that loads the library until exit.
+ *   Limit: n * n <= 524288 (n <= 724); larger n returns ATC_EINVAL.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the one array: calls that overlap on the GPU (different
+ *   streams or threads at the same time) race and give wrong results.
+ */
+int atc_gram_fp64_noalloc(const void* x_dev, int dtype, int64_t L, int64_t n, int64_t R, double* g_dev,
+                          void* stream);
+
 /* Decode an "ATCQ" section (host bytes) into n dequantized doubles (device). */
 int atc_dequantize_core(const uint8_t* bytes, size_t nbytes, double* core_dev, int64_t n, void* stream);
 

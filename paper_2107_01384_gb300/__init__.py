@@ -18,7 +18,7 @@ import torch
 __all__ = [
     "ATC_F32", "ATC_F64", "PREC_FP64", "PREC_SPLIT_BF16", "PREC_SPLIT_FP16",
     "RANK_STATIC", "RANK_ADAPTIVE", "AtcError", "lib", "lib_path",
-    "atc_norm2", "atc_gram", "atc_eig_sym", "atc_rank_select", "atc_ttm",
+    "atc_norm2", "atc_gram", "atc_gram_fp64_noalloc", "atc_eig_sym", "atc_rank_select", "atc_ttm",
     "atc_quantize_core", "atc_dequantize_core", "atc_compress", "atc_decompress",
     "atc_peek_dims", "Compressed", "EXPORTS",
 ]
@@ -36,7 +36,7 @@ EXPORTS = [
     "atc_get_stream", "atc_get_stats", "atc_free", "atc_peek_dims", "atc_decompress", "atc_norm2",
     "atc_gram", "atc_eig_sym", "atc_rank_select", "atc_ttm", "atc_quantize_core",
     "atc_dequantize_core", "atc_free_buffer", "atc_release_workspace", "atc_last_error",
-    "atc_kernel_launches",
+    "atc_kernel_launches", "atc_gram_fp64_noalloc",
 ]
 
 
@@ -89,6 +89,7 @@ def lib():
         L.atc_eig_sym.argtypes = [vp, i32, vp, vp, i32, vp]
         L.atc_rank_select.argtypes = [vp, i32, dbl, C.POINTER(i32), C.POINTER(dbl), vp]
         L.atc_ttm.argtypes = [vp, i32, i64, i64, i64, vp, i64, i32, i32, vp, i32, vp]
+        L.atc_gram_fp64_noalloc.argtypes = [vp, i32, i64, i64, i64, vp, vp]
         L.atc_quantize_core.argtypes = [vp, i64, dbl, i32, vp, C.POINTER(vp), C.POINTER(C.c_size_t), C.POINTER(i64)]
         L.atc_dequantize_core.argtypes = [C.c_char_p, C.c_size_t, vp, i64, vp]
         L.atc_free_buffer.argtypes = [vp]
@@ -136,6 +137,14 @@ def atc_gram(x: torch.Tensor, L: int, n: int, R: int, precision: int = PREC_FP64
     g = torch.empty((n, n), dtype=torch.float64, device=x.device)
     _check(lib().atc_gram(_dev(x), _dt(x), L, n, R, precision, _dev(g), _stream(stream)))
     return g
+
+
+def atc_gram_fp64_noalloc(x: torch.Tensor, L: int, n: int, R: int, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """FP64 Gram matrix into the caller's `out` (n x n float64) with no device
+    allocation inside the library (see include/atc.h)."""
+    assert x.numel() == L * n * R and out.numel() == n * n and out.dtype == torch.float64
+    _check(lib().atc_gram_fp64_noalloc(_dev(x), _dt(x), L, n, R, _dev(out), _stream(stream)))
+    return out
 
 
 def atc_eig_sym(g: torch.Tensor, nvec: int, stream=None):

@@ -9,6 +9,8 @@
 //   TTM :  Y[l][a][c] = sum_b W[a][b] X[l][b][c]          (W = U^T or U)
 #include <stdint.h>
 
+#include <mutex>
+
 #include "atc_internal.cuh"
 
 namespace atc {
@@ -217,4 +219,78 @@ int launch_ttm_fp64(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, 
   return ATC_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Gram matrix without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
+// being built around it by someone else, real-time paths that must not block
+// on the allocator, or hosts that hand this library a fixed memory budget.
+// For them the split-K partial sums of the FP64 Gram kernel live in the
+// file-scope device array below instead of the cached scratch arena.  Every
+// GPU that loads this library holds the array (4 MiB) until the process exits.
+namespace {
+constexpr size_t kNoAllocDoubles = (size_t)1 << 19;  // 4 MiB of FP64 partial sums
+__device__ __align__(256) double g_noalloc_part[kNoAllocDoubles];
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_part, per device
+std::mutex g_noalloc_mu;
+}  // namespace
+
 }  // namespace atc
+
+extern "C" int atc_gram_fp64_noalloc(const void* x_dev, int dtype, int64_t L, int64_t n, int64_t R, double* g_dev,
+                                     void* stream) {
+  using namespace atc;
+  if (!x_dev || !g_dev || L < 1 || n < 1 || R < 1 || (dtype != ATC_F32 && dtype != ATC_F64))
+    return fail(ATC_EINVAL, "atc_gram_fp64_noalloc: bad arguments");
+  if ((size_t)n * (size_t)n > kNoAllocDoubles)
+    return fail(ATC_EINVAL, "atc_gram_fp64_noalloc: n = %lld exceeds the no-allocation maximum (n*n <= %zu, n <= 724)",
+                (long long)n, kNoAllocDoubles);
+  int dev = 0;
+  ATC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(ATC_EUNSUP, "atc_gram_fp64_noalloc: device index %d", dev);
+  double* part = nullptr;
+  {
+    // one-time set-up per device, with that device current: the host-side
+    // name of the array is not a device address, so ask the runtime for it
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_part);
+      if (e != cudaSuccess)
+        return fail(ATC_ECUDA, "cudaGetSymbolAddress(no-allocation scratch): %s", cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    part = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t K = L * R;
+  const int ntile = (int)((n + TM - 1) / TM);
+  const int npairs = ntile * (ntile + 1) / 2;
+  int64_t nsplit = (4 * 152 + npairs - 1) / npairs;
+  const int64_t maxsplit = (K + 255) / 256;
+  if (nsplit > maxsplit) nsplit = maxsplit;
+  const int64_t cap = (int64_t)(kNoAllocDoubles / ((size_t)n * (size_t)n));
+  if (nsplit > cap) nsplit = cap;
+  if (nsplit < 1) nsplit = 1;
+  int64_t kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = (kchunk + TK - 1) / TK * TK;
+  nsplit = (K + kchunk - 1) / kchunk;
+  if (nsplit < 1) nsplit = 1;
+  // every entry the reduction reads (upper tiles of each split) is written by
+  // the Gram kernel of this call, so the array needs no clearing
+  dim3 grid(npairs, (unsigned)nsplit);
+  if (dtype == ATC_F32)
+    gram_fp64_kernel<float><<<grid, kThreads, 0, s>>>((const float*)x_dev, n, R, K, kchunk, ntile, part);
+  else
+    gram_fp64_kernel<double><<<grid, kThreads, 0, s>>>((const double*)x_dev, n, R, K, kchunk, ntile, part);
+  ATC_LAUNCHED(1);
+  const int64_t tot = n * n;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  gram_reduce_kernel<<<blocks, 256, 0, s>>>(part, (int)nsplit, n, g_dev);
+  ATC_LAUNCHED(1);
+  return ATC_OK;
+}
+
