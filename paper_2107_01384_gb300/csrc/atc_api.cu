@@ -198,15 +198,20 @@ int check_dims(const int64_t* dims, int ndim, int64_t* total) {
   return ATC_OK;
 }
 
-int gram_dispatch(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g, cudaStream_t s) {
+// extra eigenvectors beyond the provisional rank of a split path, from which
+// the certified rank is chosen
+constexpr int kCertExtra = 4;
+
+int gram_dispatch(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g, cudaStream_t s,
+                  const SliceScale* xs = nullptr) {
   if (precision == ATC_PREC_FP64) return launch_gram_fp64(x, dtype, L, n, R, g, s);
-  return launch_gram_split(x, dtype, L, n, R, precision, g, s);
+  return launch_gram_split(x, dtype, L, n, R, precision, g, s, xs);
 }
 
 int ttm_dispatch(const void* x, int xdt, int64_t L, int64_t n, int64_t R, const double* u, int64_t r, int expand,
-                 int precision, void* y, int ydt, cudaStream_t s) {
+                 int precision, void* y, int ydt, cudaStream_t s, const SliceScale* xs = nullptr) {
   if (precision == ATC_PREC_FP64) return launch_ttm_fp64(x, xdt, L, n, R, u, r, expand, y, ydt, s);
-  return launch_ttm_split(x, xdt, L, n, R, u, r, expand, precision, y, ydt, s);
+  return launch_ttm_split(x, xdt, L, n, R, u, r, expand, precision, y, ydt, s, xs);
 }
 
 int eig_check(cudaStream_t s) {
@@ -410,11 +415,13 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   // the largest projected tensor is after the first mode: N * r / n <= N
   void* bufA = nullptr;
   void* bufB = nullptr;
+  void* bufC = nullptr;
   int64_t maxn = 1;
   for (int i = 0; i < d; ++i) maxn = std::max(maxn, dims[i]);
   double *G = nullptr, *lam = nullptr;
   rc = Scratch::get(SLOT_TEN_A, ibytes * (size_t)N, &bufA);
   if (!rc) rc = Scratch::get(SLOT_TEN_B, ibytes * (size_t)N, &bufB);
+  if (!rc && opt.precision != ATC_PREC_FP64) rc = Scratch::get(SLOT_TEN_C, ibytes * (size_t)N, &bufC);
   if (!rc) rc = Scratch::get(SLOT_LAM, sizeof(double) * (size_t)(maxn * maxn + maxn + 64), (void**)&lam);
   if (rc) return bail(rc);
   G = lam + maxn + 16;
@@ -429,16 +436,29 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   const void* curp = x_dev;
   int curdt = dtype;
   void* next = bufA;
+  // a work buffer that is neither `a` nor `b` (three exist on the split paths)
+  auto other = [&](const void* a, const void* b) -> void* {
+    for (void* q : {bufA, bufB, bufC})
+      if (q && q != a && q != b) return q;
+    return nullptr;
+  };
   double used = 0.0;
   for (int step = 0; step < d; ++step) {
+    bool have_y = false;  // the projected tensor of this mode is already in `next`
     const int m = order[step];
     int64_t L = 1, R = 1;
     for (int i = 0; i < m; ++i) L *= cur[i];
     for (int i = m + 1; i < d; ++i) R *= cur[i];
     const int64_t n = cur[m];
     if (n > 1024) return bail(fail(ATC_EUNSUP, "mode length %lld > 1024 is not supported", (long long)n));
+    // split paths: one slice scale of the current tensor serves its Gram and its projection
+    const SliceScale* xs = nullptr;
+    if (opt.precision != ATC_PREC_FP64) {
+      rc = slice_scale(curp, curdt, L * n * R, s, &xs);
+      if (rc) return bail(rc);
+    }
     {
-      rc = gram_dispatch(curp, curdt, L, n, R, opt.precision, G, s);
+      rc = gram_dispatch(curp, curdt, L, n, R, opt.precision, G, s, xs);
       if (rc) return bail(rc);
       clk.mark(PH_GRAM);
     }
@@ -528,15 +548,76 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
           if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
         }
         if (r < 1 || r > n) return bail(fail(ATC_ENUMERIC, "rank selection failed (r = %d)", r));
-        if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
-          return bail(fail(ATC_ENOMEM, "factor allocation failed"));
-        rc = launch_eig_vectors((int)n, r, c->factors[m], s);
-        if (rc) return bail(rc);
+        if (opt.precision != ATC_PREC_FP64 && r < n) {
+          clk.mark(PH_EIG);
+          // Split paths: the eigenvalues of the sliced Gram carry a small
+          // systematic shift (the dropped low-order slice products are
+          // correlated for smooth data), far below what moves the eigenvectors
+          // but not always below the distance of the tail from the budget.
+          // So the rank is certified on the tensor itself: with U the leading
+          // rh eigenvectors and Y = U^T ._m X (tensor cores),
+          //   tail(r) = ||X - U ._m Y||^2 + sum_{j >= r} ||Y_j||^2   (U orthonormal),
+          // which is second order in the rounding errors of Y and U.
+          int rh = (int)std::min<int64_t>(n, (int64_t)r + kCertExtra);
+          for (;;) {
+            if (rh > K) {
+              rc = launch_eig_more((int)n, rh, lam, s);
+              if (rc) return bail(rc);
+              K = rh;
+            }
+            double* cand = nullptr;
+            rc = Scratch::get(SLOT_CAND, sizeof(double) * ((size_t)n * rh + rh + 8), (void**)&cand);
+            if (rc) return bail(rc);
+            double* edev = cand + (size_t)n * rh;  // e[0..rh), then rho
+            rc = launch_eig_vectors((int)n, rh, cand, s);
+            if (!rc) rc = ttm_dispatch(curp, curdt, L, n, R, cand, rh, 0, opt.precision, next, idt, s, xs);
+            if (!rc) rc = launch_ttm_residual((const float*)next, L, rh, R, cand, n, curp, curdt, edev + rh, s);
+            if (!rc) rc = launch_row_energy((const float*)next, L, rh, R, edev, s);
+            if (rc) return bail(rc);
+            std::vector<double> eh((size_t)rh + 1), t((size_t)rh + 1);
+            if (cudaMemcpyAsync(eh.data(), edev, sizeof(double) * (rh + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+              return bail(fail(ATC_ECUDA, "residual readback failed"));
+            rc = eig_check(s);
+            if (rc) return bail(rc);
+            t[rh] = (rh == n) ? 0.0 : eh[rh];
+            for (int j = rh - 1; j >= 0; --j) t[j] = t[j + 1] + eh[j];
+            int rn = -1;
+            for (int rr = 1; rr <= rh; ++rr)
+              if (t[rr] <= budget) { rn = rr; break; }
+            if (rn < 0 && rh < n) {
+              rh = (int)std::min<int64_t>(n, 2 * (int64_t)rh);
+              continue;
+            }
+            if (rn < 0) rn = (int)n;
+            r = rn;
+            disc = t[rn];
+            if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
+              return bail(fail(ATC_ENOMEM, "factor allocation failed"));
+            if (cudaMemcpy2DAsync(c->factors[m], sizeof(double) * r, cand, sizeof(double) * rh, sizeof(double) * r, n,
+                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+              return bail(fail(ATC_ECUDA, "factor copy failed"));
+            if (r < rh && L > 1) {
+              // keep the leading r of the rh projected rows (for L == 1 they already form the prefix)
+              void* tgt = other(next, curp);
+              rc = launch_compact((const float*)next, L, rh, R, r, (float*)tgt, s);
+              if (rc) return bail(rc);
+              next = tgt;
+            }
+            have_y = true;
+            clk.mark(PH_TTM);
+            break;
+          }
+        } else {
+          if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
+            return bail(fail(ATC_ENOMEM, "factor allocation failed"));
+          rc = launch_eig_vectors((int)n, r, c->factors[m], s);
+          if (rc) return bail(rc);
+        }
       }
       clk.mark(PH_EIG);
     }
-    {
-      rc = ttm_dispatch(curp, curdt, L, n, R, c->factors[m], r, 0, opt.precision, next, idt, s);
+    if (!have_y) {
+      rc = ttm_dispatch(curp, curdt, L, n, R, c->factors[m], r, 0, opt.precision, next, idt, s, xs);
       if (rc) return bail(rc);
       clk.mark(PH_TTM);
     }
@@ -545,7 +626,7 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
     used += disc;
     curp = next;
     curdt = idt;
-    next = (next == bufA) ? bufB : bufA;
+    next = other(curp, nullptr);
   }
   st.sse_trunc = used;
   int64_t ncore = 1;

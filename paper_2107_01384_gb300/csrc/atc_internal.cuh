@@ -70,6 +70,9 @@ enum ScratchSlot {
   SLOT_DEC2,
   SLOT_FAC,            // uploaded factors
   SLOT_TC_ERR,         // tensor-core kernels' error word + pre-scales
+  SLOT_ENERGY,         // row-energy partials
+  SLOT_TEN_C,          // third tensor buffer (compaction target)
+  SLOT_CAND,           // candidate factor of the residual-certified rank choice
   SLOT_COUNT
 };
 
@@ -78,6 +81,10 @@ enum ScratchSlot {
 int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s);
 int launch_convert_to_f64(const void* x, int dtype, int64_t n, double* y, cudaStream_t s);
 int launch_convert_f64_to(const double* x, int64_t n, void* y, int dtype, cudaStream_t s);
+// e[j] = sum over (l, c) of y[(l r + j) R + c]^2 in FP64 (fixed order)
+int launch_row_energy(const float* y, int64_t L, int64_t r, int64_t R, double* e, cudaStream_t s);
+// (L, rh, R) -> (L, r, R): the leading r of every rh rows
+int launch_compact(const float* y, int64_t L, int64_t rh, int64_t R, int64_t r, float* out, cudaStream_t s);
 int launch_permute(const double* x, const int64_t* dims, const int* perm, int ndim, double* y, int inverse,
                    cudaStream_t s);
 
@@ -87,10 +94,24 @@ int launch_ttm_fp64(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, 
                     int expand, void* y, int ydtype, cudaStream_t s);
 
 // split-precision tensor-core contractions (k_gram_tc.cu, k_ttm_tc.cu)
+// Common power-of-two scale of a tensor's fixed-point slices: the kernels read
+// v = x * 2^shift with |v| < 256 (shift = 8 - E, max|x| < 2^E).
+struct SliceScale {
+  unsigned maxbits;  // max |x| as float bits
+  int shift;
+};
+int slice_scale(const void* x, int dtype, int64_t N, cudaStream_t s, const SliceScale** out);
+// xs: the input's slice scale from slice_scale(), or nullptr to compute it here
 int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g,
-                      cudaStream_t s);
+                      cudaStream_t s, const SliceScale* xs = nullptr);
 int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
-                     int expand, int precision, void* y, int ydtype, cudaStream_t s);
+                     int expand, int precision, void* y, int ydtype, cudaStream_t s,
+                     const SliceScale* xs = nullptr);
+// *rho = sum (x - U ._k y)^2 over the (L, n, R) tensor x (FP32 or FP64), with
+// y the (L, r, R) FP32 projection and U the n x r FP64 factor, on the tensor
+// cores (expansion with fixed-point slices, residual fused into the epilogue)
+int launch_ttm_residual(const float* y, int64_t L, int64_t r, int64_t R, const double* u, int64_t n, const void* x,
+                        int xdtype, double* rho, cudaStream_t s);
 
 // eigensolver (k_eig.cu)
 int launch_eig_sym(const double* g, int n, double* lam, double* v, int nvec, cudaStream_t s);

@@ -109,7 +109,62 @@ int grid_for(int64_t n, int threads) {
   return (int)b;
 }
 
+// e[j] partials: block (ch, j) sums y[(l r + j) R + c]^2 over its share of
+// the (l, c) fibers; the partials are then summed in chunk order.
+constexpr int kEnChunks = 64;
+__global__ void __launch_bounds__(kNormThreads) row_energy_partial(const float* __restrict__ y, int64_t LR, int64_t r,
+                                                                   int64_t R, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int64_t j = blockIdx.y;
+  const int64_t per = (LR + gridDim.x - 1) / gridDim.x;
+  const int64_t g0 = (int64_t)blockIdx.x * per, g1 = min(LR, g0 + per);
+  double v = 0.0;
+  for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    const int64_t l = g / R, c = g - l * R;
+    const double t = (double)y[(l * r + j) * R + c];
+    v = fma(t, t, v);
+  }
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) part[j * gridDim.x + blockIdx.x] = v;
+}
+__global__ void row_energy_finish(const double* __restrict__ part, int nch, int64_t r, double* __restrict__ e) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < r; j += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int c = 0; c < nch; ++c) v += part[j * nch + c];
+    e[j] = v;
+  }
+}
+// (L, rh, R) -> (L, r, R), r <= rh: keep the leading r rows of every slab
+__global__ void compact_kernel(const float* __restrict__ y, int64_t L, int64_t rh, int64_t R, int64_t r,
+                               float* __restrict__ out) {
+  const int64_t total = L * r * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i % R, t = i / R, j = t % r, l = t / r;
+    out[i] = y[(l * rh + j) * R + c];
+  }
+}
+
 }  // namespace
+
+int launch_row_energy(const float* y, int64_t L, int64_t r, int64_t R, double* e, cudaStream_t s) {
+  if (r <= 0) return ATC_OK;
+  if (r > 65535) return fail(ATC_EUNSUP, "row energy: too many rows");
+  double* part = nullptr;
+  ATC_TRY(Scratch::get(SLOT_ENERGY, sizeof(double) * (size_t)r * kEnChunks + 256, (void**)&part));
+  row_energy_partial<<<dim3(kEnChunks, (unsigned)r), kNormThreads, 0, s>>>(y, L * R, r, R, part);
+  row_energy_finish<<<(unsigned)((r + 255) / 256), 256, 0, s>>>(part, kEnChunks, r, e);
+  ATC_LAUNCHED(2);
+  return ATC_OK;
+}
+
+int launch_compact(const float* y, int64_t L, int64_t rh, int64_t R, int64_t r, float* out, cudaStream_t s) {
+  const int64_t total = L * r * R;
+  if (total <= 0) return ATC_OK;
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  compact_kernel<<<blocks, 256, 0, s>>>(y, L, rh, R, r, out);
+  ATC_LAUNCHED(1);
+  return ATC_OK;
+}
 
 int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s) {
   double* part = nullptr;

@@ -3,23 +3,33 @@
 // Projection (Algorithm 1): Y[l][j][c] = sum_i U[i][j] X[l][i][c], i.e. for
 // every "column" gamma = (l, c) of the (L, n, R) view, y_gamma = U^T x_gamma.
 // As a GEMM: D[gamma][j] = sum_i A[gamma][i] B[j][i] with M = gamma (128 per
-// tile, any L and R), N = r (padded to 16, <= 256), K = n.  The same kernel
-// runs the expansion Y = U ._k X with B[a][b] = U[a][b].
-// Three split products (x ~ xh + xl, u ~ uh + ul in bf16 or pre-scaled fp16):
-//   D = Xh Uh^T + Xl Uh^T + Xh Ul^T,  FP32 accumulation in TMEM.
+// tile, any L and R), N = a chunk of <= 32 output indices j (padded to 16),
+// K = n.  The same kernel runs the expansion Y = U ._k X with B[a][b] = U[a][b],
+// and, in residual mode, sums (X' - U ._k Y)^2 instead of writing the product.
+// Both operands are cut into three integer slices (tc::slice3i): X on the
+// tensor's power-of-two scale, the factor on the scale 2^8 (|U| <= 1).  The
+// nine slice products go, by order s + t, into five TMEM accumulators.  By
+// Cauchy-Schwarz every partial sum of an order is below 2^16 sqrt(n) (a factor
+// column or row has norm <= 1), so for the sizes here the FP32 tensor-core
+// accumulation is exact without flushing, and the epilogue rounds the
+// combined orders once: the output carries an unbiased round-to-nearest
+// error instead of the one-signed drift of truncating FP32 accumulation.
 //
 // Warp roles (448 threads):
-//   warps 0-3  epilogue: tcgen05.ld of a finished accumulator -> Y (FP32/FP64),
-//              overlapped with the next tile's MMAs (two TMEM accumulators);
+//   warps 0-3  epilogue: tcgen05.ld of a finished accumulator set -> Y (FP32),
+//              overlapped with the next tile's MMAs (two TMEM buffers);
 //   warps 4-11 converters: coalesced loads of X (the unfolding is index
-//              arithmetic), split, K-major 128-byte-swizzled stores to smem;
-//   warp 12    MMA issuer (one elected thread);
+//              arithmetic), slicing, K-major 128-byte-swizzled stores to smem;
+//   warp 12    MMA issuer (one elected thread), 9 MMAs per K step;
 //   warp 13    B producer: bulk-async copies (cp.async.bulk, TMA engine) of the
-//              pre-split, pre-swizzled factor tiles, completing on the
+//              pre-sliced, pre-swizzled factor tiles, completing on the
 //              stage's mbarrier.
+// TMEM: buffer b at column 256 b, order o at +32 o.
 // All waits are bounded (2 s); on time-out the CTA raises an error flag,
 // waits for its own MMAs, frees TMEM and returns.
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "atc_internal.cuh"
 #include "tc_common.cuh"
@@ -36,24 +46,29 @@ constexpr int kProdWarp = kMmaWarp + 1;           // 13
 constexpr int kThreads = (kProdWarp + 1) * 32;    // 448
 constexpr int KT = 64;
 constexpr int UNITS = 128 * 8 / kConvThreads;     // 4
+constexpr int kMaxN = 32;                         // output indices per launch
+constexpr uint32_t kOrdStride = 32;               // TMEM columns per order (allocation granule)
 
 enum { TM_ROW = 0, TM_ROWVEC = 1, TM_GEN = 2 };
 
 struct TtmArgs {
   const void* x;
   int64_t L, Bdim, R;    // input view (L, Bdim, R); K = Bdim
-  int A;                 // output mode size (N of the MMA, <= 256)
+  int A;                 // output indices in this chunk (N of the MMA, <= kMaxN)
   int apad;              // A padded to 16
+  int64_t Atot, j0;      // output mode size and this chunk's first index
   int nkt;               // K tiles
   int64_t mtiles;        // ceil(L*R / 128)
-  const uint8_t* bh;     // [nkt][apad][128 B] pre-swizzled
-  const uint8_t* bl;
-  void* y;               // (L, A, R)
-  const float* xscale;   // device pre-scale of x or nullptr
-  float uscale;          // pre-scale of the factor
+  const uint8_t* bw;     // [3 slices][nkt][apad][128 B] pre-swizzled
+  void* y;               // (L, Atot, R)
+  const SliceScale* xs;  // slice scale of x
   int* err;
   int nstage;            // pipeline depth (<= 4)
   int rowmode;           // TM_ROW / TM_ROWVEC when R == 1
+  // residual mode: instead of writing Y, accumulate sum (xres - Y)^2 over this
+  // chunk's outputs, one FP64 partial per CTA in res_part[blockIdx.x]
+  const void* xres;      // (L, Atot, R) tensor compared with the product
+  double* res_part;
 };
 
 template <typename T>
@@ -75,6 +90,12 @@ __device__ __forceinline__ void ld8<double>(const double* p, float (&v)[8]) {
   }
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),
@@ -82,7 +103,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-template <typename TX, bool BF16, bool GEN>
+template <typename TX, bool BF16, bool GEN, bool RES, typename TR>
 __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
   typedef float TY;
   constexpr int MAXST = 4;
@@ -93,14 +114,16 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
   __shared__ uint64_t full_bar[MAXST], bfull_bar[MAXST], empty_bar[MAXST], accf_bar[2], acce_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ double res_smem[kEpiWarps];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   volatile int* abort = &abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t B_BYTES = (uint32_t)a.apad * 128u;
-  const uint32_t STAGE = 2 * A_BYTES + ((2 * B_BYTES + 1023u) & ~1023u);
+  const uint32_t STAGE = 3 * A_BYTES + ((3 * B_BYTES + 1023u) & ~1023u);
   const int64_t nmine = (a.mtiles > blockIdx.x) ? (a.mtiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t iters = nmine * a.nkt;
   const int64_t LR = a.L * a.R;
+  const int shift = a.xs->shift;
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -125,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
   if (warp >= kEpiWarps && warp < kMmaWarp) {
     // ------------------------------------------------------------ converters
     const int ct = tid - kEpiWarps * 32;
-    const float sc = a.xscale ? *a.xscale : 1.0f;
+    const float sc = ldexpf(1.0f, shift);
     const TX* __restrict__ x = reinterpret_cast<const TX*>(a.x);
     float bufA[UNITS][8], bufB[UNITS][8];
     auto load = [&](float (&buf)[UNITS][8], int64_t it) {
@@ -167,19 +190,26 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
       const int s = (int)(it % NSTAGE);
       const uint32_t ph = ((uint32_t)(it / NSTAGE) & 1u) ^ 1u;
       if (!mbar_wait(&empty_bar[s], ph, abort)) return false;
-      uint8_t* ah = smem + (size_t)s * STAGE;
-      uint8_t* al = ah + A_BYTES;
+      uint8_t* a0s = smem + (size_t)s * STAGE;
 #pragma unroll
       for (int u = 0; u < UNITS; ++u) {
         const int g = ct + kConvThreads * u;
         int m, q;
         if (MODE == TM_GEN) { m = g & 127; q = g >> 7; } else { m = g >> 3; q = g & 7; }
-        uint32_t h[4], l[4];
+        uint32_t p0[4], p1[4], p2[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) Split<BF16>::run(buf[u][2 * e] * sc, buf[u][2 * e + 1] * sc, h[e], l[e], 1.0f);
+        for (int e = 0; e < 4; ++e) {
+          float a0x, a1x, a2x, a0y, a1y, a2y;
+          slice3i(buf[u][2 * e] * sc, a0x, a1x, a2x);
+          slice3i(buf[u][2 * e + 1] * sc, a0y, a1y, a2y);
+          p0[e] = Pack<BF16>::two(a0x, a0y);
+          p1[e] = Pack<BF16>::two(a1x, a1y);
+          p2[e] = Pack<BF16>::two(a2x, a2y);
+        }
         const uint32_t off = sw128_off((uint32_t)m, (uint32_t)(8 * q));
-        *reinterpret_cast<uint4*>(ah + off) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(al + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint4*>(a0s + off) = make_uint4(p0[0], p0[1], p0[2], p0[3]);
+        *reinterpret_cast<uint4*>(a0s + A_BYTES + off) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
+        *reinterpret_cast<uint4*>(a0s + 2 * A_BYTES + off) = make_uint4(p2[0], p2[1], p2[2], p2[3]);
       }
       fence_proxy_async_smem();
       mbar_arrive(&full_bar[s]);
@@ -197,15 +227,17 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
   } else if (warp == kProdWarp) {
     // ---------------------------------------------------------- B producer
     if (lane == 0) {
+      const size_t slice_bytes = (size_t)a.nkt * B_BYTES;
       int64_t issued = 0;
       for (int64_t it = 0; it < iters; ++it) {
         const int s = (int)(it % NSTAGE);
         const int kt = (int)(it % a.nkt);
         if (!mbar_wait(&empty_bar[s], ((uint32_t)(it / NSTAGE) & 1u) ^ 1u, abort)) break;
-        uint8_t* bb = smem + (size_t)s * STAGE + 2 * A_BYTES;
-        mbar_arrive_expect_tx(&bfull_bar[s], 2 * B_BYTES);
-        bulk_g2s(bb, a.bh + (size_t)kt * B_BYTES, B_BYTES, &bfull_bar[s]);
-        bulk_g2s(bb + B_BYTES, a.bl + (size_t)kt * B_BYTES, B_BYTES, &bfull_bar[s]);
+        uint8_t* bb = smem + (size_t)s * STAGE + 3 * A_BYTES;
+        mbar_arrive_expect_tx(&bfull_bar[s], 3 * B_BYTES);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          bulk_g2s(bb + q * B_BYTES, a.bw + q * slice_bytes + (size_t)kt * B_BYTES, B_BYTES, &bfull_bar[s]);
         issued = it + 1;
       }
       // drain: every issued copy must land before the CTA may exit
@@ -229,17 +261,23 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
           if (!mbar_wait(&full_bar[s], (uint32_t)(it / NSTAGE) & 1u, abort) ||
               !mbar_wait(&bfull_bar[s], (uint32_t)(it / NSTAGE) & 1u, abort)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t ah = smem_u32(smem + (size_t)s * STAGE);
-          const uint32_t al = ah + A_BYTES;
-          const uint32_t bh = ah + 2 * A_BYTES;
-          const uint32_t bl = bh + B_BYTES;
+          const uint32_t xa = smem_u32(smem + (size_t)s * STAGE);
+          const uint32_t wa = xa + 3 * A_BYTES;
 #pragma unroll
           for (int j = 0; j < KT / 16; ++j) {
-            const uint64_t dah = desc_k128(ah + 32 * j), dal = desc_k128(al + 32 * j);
-            const uint64_t dbh = desc_k128(bh + 32 * j), dbl = desc_k128(bl + 32 * j);
-            umma_f16(d, dah, dbh, idesc, (kt | j) ? 1u : 0u);
-            umma_f16(d, dal, dbh, idesc, 1u);
-            umma_f16(d, dah, dbl, idesc, 1u);
+            const uint32_t o = 32u * j;
+            const uint64_t X0 = desc_k128(xa + o), X1 = desc_k128(xa + A_BYTES + o), X2 = desc_k128(xa + 2 * A_BYTES + o);
+            const uint64_t W0 = desc_k128(wa + o), W1 = desc_k128(wa + B_BYTES + o), W2 = desc_k128(wa + 2 * B_BYTES + o);
+            const uint32_t acc = (kt | j) ? 1u : 0u;
+            umma_f16(d, X0, W0, idesc, acc);
+            umma_f16(d + kOrdStride, X0, W1, idesc, acc);
+            umma_f16(d + kOrdStride, X1, W0, idesc, 1u);
+            umma_f16(d + 2 * kOrdStride, X0, W2, idesc, acc);
+            umma_f16(d + 2 * kOrdStride, X1, W1, idesc, 1u);
+            umma_f16(d + 2 * kOrdStride, X2, W0, idesc, 1u);
+            umma_f16(d + 3 * kOrdStride, X1, W2, idesc, acc);
+            umma_f16(d + 3 * kOrdStride, X2, W1, idesc, 1u);
+            umma_f16(d + 4 * kOrdStride, X2, W2, idesc, acc);
           }
           umma_commit(&empty_bar[s]);
         }
@@ -250,8 +288,12 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
     }
   } else {
     // ------------------------------------------------------------- epilogue
-    const float inv = 1.0f / ((a.xscale ? *a.xscale : 1.0f) * a.uscale);
+    // y = (sum_o 2^-8o acc_o) 2^-(shift + 8): one rounding, then exact power-of-two scaling
+    const int e_out = -(shift + 8);
+    const float f1 = ldexpf(1.0f, e_out / 2), f2 = ldexpf(1.0f, e_out - e_out / 2);
     TY* __restrict__ y = reinterpret_cast<TY*>(a.y);
+    const TR* __restrict__ xr = reinterpret_cast<const TR*>(a.xres);
+    float racc = 0.f;  // residual mode: this thread's sum of squares
     for (int64_t t = 0; t < nmine; ++t) {
       const int ab = (int)(t & 1);
       // warp-uniform wait: the tcgen05.ld below is .sync.aligned
@@ -265,22 +307,48 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
       const int64_t gam = mt * 128 + 32 * warp + lane;
       const bool valid = gam < LR;
       const int64_t l = valid ? gam / a.R : 0, c = valid ? gam - l * a.R : 0;
-      TY* yo = y + (l * a.A) * a.R + c;
+      TY* yo = y + (l * a.Atot + a.j0) * a.R + c;
+      const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)ab * 256u;
 #pragma unroll 1
-      for (int c0 = 0; c0 < a.apad; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + (uint32_t)ab * 256u + (uint32_t)c0 + ((uint32_t)(32 * warp) << 16), r);
+      for (int c0 = 0; c0 < a.apad; c0 += 8) {
+        uint32_t r0[8], r1[8], r2[8], r3[8], r4[8];
+        tmem_ld8(tb + (uint32_t)c0, r0);
+        tmem_ld8(tb + kOrdStride + (uint32_t)c0, r1);
+        tmem_ld8(tb + 2 * kOrdStride + (uint32_t)c0, r2);
+        tmem_ld8(tb + 3 * kOrdStride + (uint32_t)c0, r3);
+        tmem_ld8(tb + 4 * kOrdStride + (uint32_t)c0, r4);
         tmem_ld_wait();
         if (valid) {
+          const TR* xo = RES ? xr + (l * a.Atot + a.j0) * a.R + c : nullptr;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
+          for (int e = 0; e < 8; ++e) {
             const int j = c0 + e;
-            if (j < a.A) yo[(int64_t)j * a.R] = (TY)(__uint_as_float(r[e]) * inv);
+            if (j < a.A) {
+              float sv, tv;
+              combine_orders(__uint_as_float(r0[e]), __uint_as_float(r1[e]), __uint_as_float(r2[e]),
+                             __uint_as_float(r3[e]), __uint_as_float(r4[e]), sv, tv);
+              const float z = ((sv + tv) * f1) * f2;
+              if (RES) {
+                const float dd = (float)(__ldg(xo + (int64_t)j * a.R) - (TR)z);
+                racc = fmaf(dd, dd, racc);
+              } else {
+                yo[(int64_t)j * a.R] = (TY)z;
+              }
+            }
           }
         }
       }
       tc_fence_before();
       mbar_arrive(&acce_bar[ab]);
+    }
+    if (RES) {
+      // fixed-order FP64 reduction over the 128 epilogue threads
+      double v = (double)racc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) res_smem[warp] = v;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (tid == 0) a.res_part[blockIdx.x] = ((res_smem[0] + res_smem[1]) + (res_smem[2] + res_smem[3]));
     }
   }
   tc_fence_before();
@@ -296,13 +364,15 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
 namespace atc {
 namespace {
 
-// W tiles for the MMA B operand: W[a][b] = U[b][a] (projection) or U[a][b]
-// (expansion), split into two 16-bit halves, laid out per K tile exactly as
-// the 128-byte-swizzled K-major shared-memory image.
+// W tiles for the MMA B operand: W[a][b] = U[b][j0 + a] (projection) or
+// U[j0 + a][b] (expansion), cut into the three fixed-point slices on the
+// scale 2^8 (|U| <= 1) and laid out per K tile exactly as the
+// 128-byte-swizzled K-major shared-memory image: [slice][kt][apad][64].
 template <bool BF16>
-__global__ void ttm_prep_b(const double* __restrict__ u, int A, int Bdim, int expand, int apad, int nkt, float uscale,
-                           uint8_t* __restrict__ bh, uint8_t* __restrict__ bl) {
+__global__ void ttm_prep_b(const double* __restrict__ u, int A, int64_t Atot, int64_t j0, int Bdim, int expand,
+                           int apad, int nkt, uint8_t* __restrict__ bw) {
   const int64_t total = (int64_t)nkt * apad * 64;
+  const size_t slice_bytes = (size_t)nkt * apad * 128;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
     const int il = (int)(idx & 63);
     const int64_t rest = idx >> 6;
@@ -310,57 +380,57 @@ __global__ void ttm_prep_b(const double* __restrict__ u, int A, int Bdim, int ex
     const int kt = (int)(rest / apad);
     const int b = kt * 64 + il;
     double w = 0.0;
-    if (j < A && b < Bdim) w = expand ? u[(int64_t)j * Bdim + b] : u[(int64_t)b * A + j];
-    const float wf = (float)(w * (double)uscale);
-    uint16_t h, l;
-    if (BF16) {
-      const __nv_bfloat16 hh = __float2bfloat16_rn(wf);
-      const float rem = (float)(w * (double)uscale - (double)__bfloat162float(hh));
-      h = __bfloat16_as_ushort(hh);
-      l = __bfloat16_as_ushort(__float2bfloat16_rn(rem));
-    } else {
-      const __half hh = __float2half_rn(wf);
-      const float rem = (float)(w * (double)uscale - (double)__half2float(hh));
-      h = __half_as_ushort(hh);
-      l = __half_as_ushort(__float2half_rn(rem));
-    }
+    if (j < A && b < Bdim) w = expand ? u[(j0 + j) * (int64_t)Bdim + b] : u[(int64_t)b * Atot + j0 + j];
+    // integer slices of v = 256 w in FP64 (exact steps, one final rounding)
+    const double v = w * 256.0;
+    const double a0 = rint(v);
+    const double t = (v - a0) * 256.0;
+    const double a1 = rint(t);
+    const double a2 = rint((t - a1) * 256.0);
     const size_t off = (size_t)kt * apad * 128 + tc::sw128_off((uint32_t)j, (uint32_t)il);
-    *reinterpret_cast<uint16_t*>(bh + off) = h;
-    *reinterpret_cast<uint16_t*>(bl + off) = l;
+    *reinterpret_cast<uint16_t*>(bw + off) = tc::Pack<BF16>::one((float)a0);
+    *reinterpret_cast<uint16_t*>(bw + slice_bytes + off) = tc::Pack<BF16>::one((float)a1);
+    *reinterpret_cast<uint16_t*>(bw + 2 * slice_bytes + off) = tc::Pack<BF16>::one((float)a2);
   }
 }
 
-template <typename T>
-__global__ void ttm_xscale_kernel(const T* __restrict__ x, int64_t N, unsigned* __restrict__ mx_bits) {
-  float m = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf((float)x[i]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(mx_bits, __float_as_uint(m));
-}
-__global__ void ttm_xscale_finish(const unsigned* __restrict__ mx_bits, float* __restrict__ scale) {
-  const float m = __uint_as_float(*mx_bits);
-  int e = 0;
-  if (m > 0.f) frexpf(m, &e);
-  *scale = (m > 0.f) ? ldexpf(1.0f, 14 - e) : 1.0f;
-}
-
-template <typename TX, bool BF16, bool GEN>
+template <typename TX, bool BF16, bool GEN, bool RES, typename TR>
 int ttm_launch_t(const TtmArgs& a, int grid, int smem, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    ATC_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<TX, BF16, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 197 * 1024));
+    ATC_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<TX, BF16, GEN, RES, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      225 * 1024));
     attr = true;
   }
-  ttm_tc_kernel<TX, BF16, GEN><<<grid, kThreads, smem, s>>>(a);
+  ttm_tc_kernel<TX, BF16, GEN, RES, TR><<<grid, kThreads, smem, s>>>(a);
   ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
 template <typename TX, bool BF16>
 int ttm_launch_g(const TtmArgs& a, bool gen, int grid, int smem, cudaStream_t s) {
-  return gen ? ttm_launch_t<TX, BF16, true>(a, grid, smem, s) : ttm_launch_t<TX, BF16, false>(a, grid, smem, s);
+  return gen ? ttm_launch_t<TX, BF16, true, false, float>(a, grid, smem, s)
+             : ttm_launch_t<TX, BF16, false, false, float>(a, grid, smem, s);
+}
+
+template <typename TR>
+int ttm_launch_res(const TtmArgs& a, bool gen, int grid, int smem, cudaStream_t s) {
+  return gen ? ttm_launch_t<float, true, true, true, TR>(a, grid, smem, s)
+             : ttm_launch_t<float, true, false, true, TR>(a, grid, smem, s);
+}
+
+// fixed-order sum of the residual partials
+__global__ void sum_res_partials(const double* __restrict__ p, int np, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < np; i += 256) v += p[i];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
 }
 
 int g_nsm_ttm = 0;
@@ -369,75 +439,109 @@ int g_nsm_ttm = 0;
 
 int tc_error_flag(int** flag);
 
-int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
-                     int expand, int precision, void* y, int ydtype, cudaStream_t s) {
-  const int64_t A = expand ? n : r;
+namespace {
+
+// Shared driver of the projection / expansion (res == nullptr) and of the
+// residual energy sum ||xres - U ._k X||^2 (res != nullptr, expansion only).
+int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r, int expand,
+            int precision, void* y, cudaStream_t s, const SliceScale* xs, const void* xres, int xres_dtype,
+            double* res) {
+  const int64_t Atot = expand ? n : r;
   const int64_t Bdim = expand ? r : n;
-  if (A > 256) return fail(ATC_EUNSUP, "split-precision TTM supports output mode <= 256 (got %lld)", (long long)A);
-  if (ydtype != ATC_F32) return fail(ATC_EUNSUP, "split-precision TTM writes FP32 output");
+  if (Bdim > 1024) return fail(ATC_EUNSUP, "split-precision TTM supports contraction length <= 1024 (got %lld)",
+                               (long long)Bdim);
   if (g_nsm_ttm == 0) {
     int dev = 0;
     ATC_CUDA_TRY(cudaGetDevice(&dev));
     ATC_CUDA_TRY(cudaDeviceGetAttribute(&g_nsm_ttm, cudaDevAttrMultiProcessorCount, dev));
   }
   const bool bf16 = (precision == ATC_PREC_SPLIT_BF16);
-  TtmArgs a;
-  a.x = x;
-  a.L = L;
-  a.Bdim = Bdim;
-  a.R = R;
-  a.A = (int)A;
-  a.apad = (int)((A + 15) / 16 * 16);
-  a.nkt = (int)((Bdim + KT - 1) / KT);
-  a.mtiles = (L * R + 127) / 128;
-  a.y = y;
-  a.uscale = bf16 ? 1.0f : 8192.0f;
-  a.rowmode = (Bdim % 8 == 0) ? TM_ROWVEC : TM_ROW;
-  const uint32_t bbytes = (uint32_t)a.apad * 128u;
-  const uint32_t stage = 2u * 128u * 128u + ((2u * bbytes + 1023u) & ~1023u);
-  a.nstage = (int)((192u * 1024u) / stage);
-  if (a.nstage > 4) a.nstage = 4;
-  if (a.nstage < 2) return fail(ATC_EUNSUP, "TTM stage does not fit in shared memory");
-  const int smem = (int)(a.nstage * stage + 1024);
-  uint8_t* bw = nullptr;
-  const size_t wb = (size_t)a.nkt * bbytes;
-  ATC_TRY(Scratch::get(SLOT_TTM_U, 2 * wb + 256, (void**)&bw));
-  a.bh = bw;
-  a.bl = bw + wb;
+  if (!xs) ATC_TRY(slice_scale(x, xdtype, L * Bdim * R, s, &xs));
   int* err = nullptr;
   ATC_TRY(tc_error_flag(&err));
-  a.err = err;
-  a.xscale = nullptr;
-  if (!bf16) {
-    unsigned* mx = reinterpret_cast<unsigned*>(err + 8);
-    float* scale = reinterpret_cast<float*>(err + 9);
-    ATC_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned), s));
-    const int64_t N = L * Bdim * R;
-    const int blocks = (int)((N + 255) / 256 < 1216 ? (N + 255) / 256 : 1216);
-    if (xdtype == ATC_F32) ttm_xscale_kernel<float><<<blocks, 256, 0, s>>>((const float*)x, N, mx);
-    else ttm_xscale_kernel<double><<<blocks, 256, 0, s>>>((const double*)x, N, mx);
-    ttm_xscale_finish<<<1, 1, 0, s>>>(mx, scale);
-    ATC_LAUNCHED(2);
-    a.xscale = scale;
+  const int nkt = (int)((Bdim + KT - 1) / KT);
+  const int64_t mtiles = (L * R + 127) / 128;
+  // the output indices in chunks of at most kMaxN (two TMEM buffers of five orders)
+  const int nchunk = (int)((Atot + kMaxN - 1) / kMaxN);
+  const int64_t csz = (Atot + nchunk - 1) / nchunk;
+  const int apad_max = (int)((csz + 15) / 16 * 16);
+  const size_t wb = (size_t)3 * nkt * apad_max * 128;
+  const int grid = (int)(mtiles < g_nsm_ttm ? mtiles : g_nsm_ttm);
+  uint8_t* bw = nullptr;
+  ATC_TRY(Scratch::get(SLOT_TTM_U, wb * nchunk + (size_t)8 * nchunk * (grid + 1) + 256, (void**)&bw));
+  double* part = reinterpret_cast<double*>(bw + wb * nchunk);
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int64_t j0 = ch * csz;
+    const int64_t A = std::min<int64_t>(csz, Atot - j0);
+    if (A <= 0) break;
+    TtmArgs a;
+    a.x = x;
+    a.L = L;
+    a.Bdim = Bdim;
+    a.R = R;
+    a.A = (int)A;
+    a.apad = (int)((A + 15) / 16 * 16);
+    a.Atot = Atot;
+    a.j0 = j0;
+    a.nkt = nkt;
+    a.mtiles = mtiles;
+    a.y = y;
+    a.xs = xs;
+    a.err = err;
+    a.rowmode = (Bdim % 8 == 0) ? TM_ROWVEC : TM_ROW;
+    a.xres = xres;
+    a.res_part = part + (size_t)ch * grid;
+    const uint32_t bbytes = (uint32_t)a.apad * 128u;
+    const uint32_t stage = 3u * 128u * 128u + ((3u * bbytes + 1023u) & ~1023u);
+    a.nstage = (int)((224u * 1024u) / stage);
+    if (a.nstage > 4) a.nstage = 4;
+    if (a.nstage < 2) return fail(ATC_EUNSUP, "TTM stage does not fit in shared memory");
+    const int smem = (int)(a.nstage * stage + 1024);
+    uint8_t* bwc = bw + wb * ch;
+    a.bw = bwc;
+    {
+      const int64_t tot = (int64_t)nkt * a.apad * 64;
+      const int blocks = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
+      if (bf16 || res) ttm_prep_b<true><<<blocks, 256, 0, s>>>(u, a.A, Atot, j0, (int)Bdim, expand, a.apad, nkt, bwc);
+      else ttm_prep_b<false><<<blocks, 256, 0, s>>>(u, a.A, Atot, j0, (int)Bdim, expand, a.apad, nkt, bwc);
+      ATC_LAUNCHED(1);
+    }
+    if (mtiles == 0) continue;
+    const bool gen = (R != 1);
+    if (res) {
+      if (xdtype != ATC_F32) return fail(ATC_EUNSUP, "residual mode expects an FP32 projected tensor");
+      if (xres_dtype == ATC_F32) ATC_TRY(ttm_launch_res<float>(a, gen, grid, smem, s));
+      else ATC_TRY(ttm_launch_res<double>(a, gen, grid, smem, s));
+    } else if (xdtype == ATC_F32) {
+      if (bf16) ATC_TRY((ttm_launch_g<float, true>(a, gen, grid, smem, s)));
+      else ATC_TRY((ttm_launch_g<float, false>(a, gen, grid, smem, s)));
+    } else {
+      if (bf16) ATC_TRY((ttm_launch_g<double, true>(a, gen, grid, smem, s)));
+      else ATC_TRY((ttm_launch_g<double, false>(a, gen, grid, smem, s)));
+    }
   }
-  {
-    const int64_t tot = (int64_t)a.nkt * a.apad * 64;
-    const int blocks = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
-    if (bf16) ttm_prep_b<true><<<blocks, 256, 0, s>>>(u, a.A, (int)Bdim, expand, a.apad, a.nkt, a.uscale, bw, bw + wb);
-    else ttm_prep_b<false><<<blocks, 256, 0, s>>>(u, a.A, (int)Bdim, expand, a.apad, a.nkt, a.uscale, bw, bw + wb);
-    ATC_LAUNCHED(1);
-  }
-  if (a.mtiles == 0) return ATC_OK;
-  const int grid = (int)(a.mtiles < g_nsm_ttm ? a.mtiles : g_nsm_ttm);
-  const bool gen = (R != 1);
-  if (xdtype == ATC_F32) {
-    if (bf16) ATC_TRY((ttm_launch_g<float, true>(a, gen, grid, smem, s)));
-    else ATC_TRY((ttm_launch_g<float, false>(a, gen, grid, smem, s)));
-  } else {
-    if (bf16) ATC_TRY((ttm_launch_g<double, true>(a, gen, grid, smem, s)));
-    else ATC_TRY((ttm_launch_g<double, false>(a, gen, grid, smem, s)));
+  if (res) {
+    if (mtiles == 0) {
+      ATC_CUDA_TRY(cudaMemsetAsync(res, 0, sizeof(double), s));
+    } else {
+      sum_res_partials<<<1, 256, 0, s>>>(part, nchunk * grid, res);
+      ATC_LAUNCHED(1);
+    }
   }
   return ATC_OK;
+}
+
+}  // namespace
+
+int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
+                     int expand, int precision, void* y, int ydtype, cudaStream_t s, const SliceScale* xs) {
+  if (ydtype != ATC_F32) return fail(ATC_EUNSUP, "split-precision TTM writes FP32 output");
+  return ttm_run(x, xdtype, L, n, R, u, r, expand, precision, y, s, xs, nullptr, 0, nullptr);
+}
+
+int launch_ttm_residual(const float* y, int64_t L, int64_t r, int64_t R, const double* u, int64_t n, const void* x,
+                        int xdtype, double* rho, cudaStream_t s) {
+  return ttm_run(y, ATC_F32, L, n, R, u, r, 1, ATC_PREC_SPLIT_BF16, nullptr, s, nullptr, x, xdtype, rho);
 }
 
 }  // namespace atc

@@ -148,40 +148,58 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
       : "memory");
 }
 
-// split x into hi + lo halves of a 16-bit type, packed in pairs
+// Fixed-point slices (error-free splitting in the manner of Ozaki et al.,
+// as used for tensor-core GEMMs by Mukunoki et al., ICCS 2020).  With one
+// power-of-two scale per operand, v = x * 2^shift and |v| < 256:
+//   v ~ a0 + a1 2^-8 + a2 2^-16,  a0, a1, a2 integers, |a0| <= 256, |a1|, |a2| <= 128
+// (round to nearest at each step, so |v - ...| <= 2^-17).  Every slice is an
+// integer exact in bf16 and fp16, every product of two slices is exact, and
+// a sum of such products is exact in FP32 while its magnitude stays below 2^24:
+// the tensor-core FP32 accumulation then performs no rounding at all, whatever
+// its internal rounding mode.  The products are grouped by order s + t (the
+// scale 2^-8(s+t)) into five accumulators and combined outside the tensor core.
+__device__ __forceinline__ void slice3i(float v, float& a0, float& a1, float& a2) {
+  a0 = rintf(v);
+  const float t = (v - a0) * 256.0f;  // exact
+  a1 = rintf(t);
+  a2 = rintf((t - a1) * 256.0f);
+}
+
+// acc0 + 2^-8 acc1 + 2^-16 acc2 + 2^-24 acc3 + 2^-32 acc4 as an unevaluated
+// sum s + t (s carries the leading 24 bits; the exact orders 0 and 1 enter
+// through an error-free two-sum, the rest with round-to-nearest)
+__device__ __forceinline__ void combine_orders(float c0, float c1, float c2, float c3, float c4, float& s, float& t) {
+  const float b = c1 * 0.00390625f;
+  s = c0 + b;
+  const float bp = s - c0;
+  const float e = (c0 - (s - bp)) + (b - bp);
+  t = e + fmaf(c2, 1.52587890625e-05f, fmaf(c3, 5.9604644775390625e-08f, c4 * 2.3283064365386963e-10f));
+}
+
 template <bool BF16>
-struct Split;
+struct Pack;
 template <>
-struct Split<true> {
-  static __device__ __forceinline__ void run(float a, float b, uint32_t& hi, uint32_t& lo, float lo_mul) {
-    __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-    __nv_bfloat16 la = __float2bfloat16_rn((a - __bfloat162float(ha)) * lo_mul);
-    __nv_bfloat16 lb = __float2bfloat16_rn((b - __bfloat162float(hb)) * lo_mul);
-    hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-    lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+struct Pack<true> {
+  static __device__ __forceinline__ uint32_t two(float a, float b) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
   }
-  // 2x each packed half (exact: exponent + 1)
-  static __device__ __forceinline__ uint32_t twice(uint32_t v) {
-    __nv_bfloat162 t = *reinterpret_cast<__nv_bfloat162*>(&v);
-    t = __hmul2(t, __floats2bfloat162_rn(2.0f, 2.0f));
-    return *reinterpret_cast<uint32_t*>(&t);
-  }
+  static __device__ __forceinline__ uint16_t one(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
 };
 template <>
-struct Split<false> {
-  static __device__ __forceinline__ void run(float a, float b, uint32_t& hi, uint32_t& lo, float lo_mul) {
-    __half ha = __float2half_rn(a), hb = __float2half_rn(b);
-    __half la = __float2half_rn((a - __half2float(ha)) * lo_mul);
-    __half lb = __float2half_rn((b - __half2float(hb)) * lo_mul);
-    hi = (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
-    lo = (uint32_t)__half_as_ushort(la) | ((uint32_t)__half_as_ushort(lb) << 16);
+struct Pack<false> {
+  static __device__ __forceinline__ uint32_t two(float a, float b) {
+    return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
   }
-  static __device__ __forceinline__ uint32_t twice(uint32_t v) {
-    __half2 t = *reinterpret_cast<__half2*>(&v);
-    t = __hmul2(t, __floats2half2_rn(2.0f, 2.0f));
-    return *reinterpret_cast<uint32_t*>(&t);
-  }
+  static __device__ __forceinline__ uint16_t one(float a) { return __half_as_ushort(__float2half_rn(a)); }
 };
+
+// error-free sum of two floats: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
 
 }  // namespace tc
 }  // namespace atc

@@ -2,15 +2,18 @@
 FP64 oracle, through the C ABI.
 
 Error model (written out so the tolerances are derivable):
-* x = h + l + rho with h, l 16-bit halves.  bf16: |rho| <= 2^-17 |x| and the
-  dropped l*l' term <= 2^-16 |x y|; fp16 (pre-scaled, 11-bit halves): 2^-23 and
-  2^-22.  So one split product is within c * 2^-15 |x y| (bf16) or
-  c * 2^-21 |x y| (fp16) of x*y, c <= 2.
-* Accumulation in FP32 inside one CTA adds about 2^-24 * sqrt(K_chunk) of
-  the sum of |products|; partial sums are combined in FP64.
-Hence for the Gram matrix |G - G_ref|_ij <= tol * sqrt(G_ii G_jj) with
-tol = 2^-13 (bf16) or 2^-18 (fp16), and for the projection
-|Y - Y_ref| <= tol * ||x_gamma|| per output column.
+* Each element is read as v = x 2^shift (one power-of-two scale per tensor,
+  |v| < 256, 2^-shift * 256 = 2^E <= 2 max|x|) and cut into three integer
+  slices, v ~ a0 + a1 2^-8 + a2 2^-16, rounded to nearest: |x - x~| <= 2^(E-25)
+  <= 2^-24 M with M = max|x|.  Factors (|U| <= 1) are sliced on the scale 2^8:
+  |u - u~| <= 2^-25.
+* The tensor cores form all nine slice products, grouped by order into five
+  accumulators that stay integers below 2^24, so nothing rounds there; the
+  orders are combined in double-float / FP64.
+Hence |G - G_ref|_ij <= 2^-24 M sqrt(K) (||x_i|| + ||x_j||) + K 2^-48 M^2, and
+for the projection |y - y_ref| <= 2^-24 (M sqrt(n) + sqrt(n) ||x_gamma|| + |y|);
+the tests use these bounds with a factor 4.  Exactness tests use data whose
+slices are exact: there the results must equal the exact values.
 """
 import numpy as np
 import pytest
@@ -22,8 +25,9 @@ pytestmark = pytest.mark.gpu
 import synth  # noqa: E402
 from oracle import sthosvd as O  # noqa: E402
 
-TOL = {1: 2.0 ** -13, 2: 2.0 ** -18}
-
+def ttm_bound(M, K, colnorm, y):
+    """|y - y_ref| bound of the error model, for contraction length K."""
+    return 4 * 2.0 ** -24 * (M * np.sqrt(K) + np.sqrt(K) * colnorm + np.abs(y))
 
 @pytest.fixture(scope="module")
 def P():
@@ -53,9 +57,10 @@ def test_gram_split(P, dims, mode, dtype, prec):
     L = int(np.prod(dims[:mode])); n = dims[mode]; R = int(np.prod(dims[mode + 1:]))
     g = P.atc_gram(cuda(x), L, n, R, prec).cpu().numpy()
     ref = O.mode_gram(x, mode)
-    d = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
-    err = np.abs(g - ref) / np.maximum(d, 1e-300)
-    assert err.max() <= TOL[prec], err.max()
+    M = float(np.abs(x).max()); K = L * R
+    rn = np.sqrt(np.diag(ref))
+    bound = 2.0 ** -24 * M * np.sqrt(K) * (rn[:, None] + rn[None, :]) + K * 2.0 ** -48 * M * M
+    assert np.all(np.abs(g - ref) <= 4 * bound), (np.abs(g - ref) / bound).max()
     assert np.array_equal(g, g.T)
 
 
@@ -75,8 +80,10 @@ def test_ttm_split(P, dims, mode, r, dtype, prec):
     y = P.atc_ttm(cuda(x), L, n, R, cuda(u), r, expand=False, precision=prec, out_dtype=torch.float32).cpu().numpy()
     ref = O.ttm_project(x.astype(np.float64), u, mode)
     colnorm = np.sqrt(np.sum(np.moveaxis(x.astype(np.float64), mode, 0) ** 2, axis=0))  # ||x_gamma||
-    err = np.abs(np.moveaxis(y.reshape(ref.shape), mode, 0) - np.moveaxis(ref, mode, 0)) / np.maximum(colnorm, 1e-300)
-    assert err.max() <= TOL[prec], err.max()
+    yr = np.moveaxis(ref, mode, 0)
+    err = np.abs(np.moveaxis(y.reshape(ref.shape), mode, 0) - yr)
+    bound = ttm_bound(float(np.abs(x).max()), dims[mode], colnorm[None], yr)
+    assert np.all(err <= bound), (err / bound).max()
 
 
 @pytest.mark.parametrize("prec", [1, 2])
@@ -88,8 +95,60 @@ def test_ttm_split_expand(P, prec):
     y = P.atc_ttm(cuda(x), 20, 90, 30, cuda(u), 12, expand=True, precision=prec, out_dtype=torch.float32).cpu().numpy()
     ref = O.ttm_expand(x.astype(np.float64), u, 1)
     scale = np.sqrt(np.sum(x.astype(np.float64) ** 2, axis=1))  # per (l, c) column norm of the input
-    err = np.abs(y.reshape(ref.shape) - ref) / np.maximum(scale[:, None, :], 1e-300)
-    assert err.max() <= TOL[prec], err.max()
+    err = np.abs(y.reshape(ref.shape) - ref)
+    bound = ttm_bound(float(np.abs(x).max()), 12, scale[:, None, :], ref)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+EXACT_CASES = [((64, 64, 64), 0), ((64, 64, 64), 2), ((3, 256, 700), 1), ((37, 129, 5), 1), ((1, 200, 1000), 1),
+               ((700, 224), 1), ((5, 300, 33), 1)]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("dims,mode", EXACT_CASES)
+def test_gram_split_exact_integer(P, dims, mode, prec):
+    """Values on an 8-bit grid: one slice each, so every product and every
+    partial sum is an integer below 2^24 and the tensor-core Gram must equal
+    the exact FP64 Gram bit for bit (no truncation anywhere)."""
+    rng = np.random.default_rng(11)
+    x = (rng.integers(-255, 256, size=dims) * 0.125).astype(np.float32)
+    x.flat[0] = 255 * 0.125  # max|x| = 31.875 -> shift 3, v = 8 x integer
+    L = int(np.prod(dims[:mode])); n = dims[mode]; R = int(np.prod(dims[mode + 1:]))
+    g = P.atc_gram(cuda(x), L, n, R, prec).cpu().numpy()
+    ref = O.mode_gram(x.astype(np.float64), mode)
+    assert np.array_equal(g, ref), np.abs(g - ref).max()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("dims,mode", [((64, 64, 64), 1), ((3, 256, 700), 1), ((700, 224), 1), ((2, 300, 5000), 1)])
+def test_gram_split_exact_24bit(P, dims, mode, prec):
+    """24-bit data (|x| < 8 on a 2^-20 grid): the three slices represent every
+    element exactly and all nine slice products are formed without rounding.
+    What rounds is the combination of the orders after each 128-product
+    window: the orders >= 2 are added in FP32 (round to nearest, <= 2^-40 of
+    the window's largest entry), the rest in double-float and FP64."""
+    rng = np.random.default_rng(12)
+    x = (rng.integers(-(2 ** 23) + 1, 2 ** 23, size=dims) * 2.0 ** -20).astype(np.float32)
+    L = int(np.prod(dims[:mode])); n = dims[mode]; R = int(np.prod(dims[mode + 1:]))
+    g = P.atc_gram(cuda(x), L, n, R, prec).cpu().numpy()
+    ref = O.mode_gram(x.astype(np.float64), mode)
+    assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("dims,mode,r", [((64, 64, 64), 1, 40), ((3, 256, 700), 1, 130), ((700, 224), 1, 16)])
+def test_ttm_split_exact_integer(P, dims, mode, r, prec):
+    """x on an 8-bit grid and factor entries k/256 with |k| < 256: single
+    slices, all partial sums integers below 2^24, so Y must equal the exact
+    product rounded once to FP32."""
+    rng = np.random.default_rng(13)
+    x = (rng.integers(-255, 256, size=dims) * 0.125).astype(np.float32)
+    x.flat[0] = 255 * 0.125
+    u = rng.integers(-255, 256, size=(dims[mode], r)) / 256.0
+    L = int(np.prod(dims[:mode])); n = dims[mode]; R = int(np.prod(dims[mode + 1:]))
+    y = P.atc_ttm(cuda(x), L, n, R, cuda(u), r, expand=False, precision=prec, out_dtype=torch.float32).cpu().numpy()
+    ref = O.ttm_project(x.astype(np.float64), u, mode).astype(np.float32)
+    assert np.array_equal(y.reshape(ref.shape), ref)
 
 
 def test_split_rejects_unsupported(P):
