@@ -6,12 +6,15 @@
 // GB300 has a small FP64 rate (about 2 DFMA lanes per clock per SM), so the
 // solver keeps FP64 work proportional to n^3 only where unavoidable and spreads
 // it over many SMs:
-//   1. Householder tridiagonalisation T = Q^T G Q: one cooperative kernel, rows
-//      dealt cyclically to the CTAs; each step re-forms the next reflector
-//      redundantly in every CTA and fuses the two-sided update of step s-1 with
-//      the matrix-vector product of step s, so a step costs ONE grid barrier.
-//      The barrier spin is bounded: on time-out an error flag is raised and
-//      every CTA returns.
+//   1. Householder tridiagonalisation T = Q^T G Q: rows dealt cyclically to the
+//      CTAs; each step re-forms the next reflector redundantly in every CTA and
+//      fuses the two-sided update of step s-1 with the matrix-vector product of
+//      step s, so a step costs ONE barrier.  For n <= 512 the CTAs form one
+//      thread-block cluster (16, else 8): the rows live in shared memory, row s
+//      and the vector p are read from the owners through distributed shared
+//      memory, and the barrier is the hardware cluster barrier.  Larger n use a
+//      cooperative grid with the rows in global memory and a bounded software
+//      grid barrier (on time-out an error flag is raised and every CTA returns).
 //   2. Eigenvalues of T by bisection on Sturm counts; the count uses the
 //      three-term recurrence of the leading principal minors (one dependent
 //      FMA per row) with power-of-two rescaling instead of a division per row.
@@ -21,11 +24,16 @@
 //   4. Back-transformation X = Q Z, a warp per column, then the sign
 //      convention (largest-magnitude entry positive).
 #include <math.h>
+#include <stdio.h>
 #include <stdint.h>
+
+#include <cooperative_groups.h>
 
 #include <vector>
 
 #include "atc_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace atc {
 namespace {
@@ -212,6 +220,152 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(EigState st) {
   }
 }
 
+// Same iteration as tridiag_kernel, on one cluster of C CTAs with the rows in
+// shared memory: CTA b owns rows i == b (mod C), stored at local index i / C.
+// Thread t handles index j = s + t of the step's vectors, so the gathered p,
+// w and row s never need a barrier of their own; a step has two block
+// reductions, one block barrier and one cluster barrier.  Every CTA runs the
+// same number of cluster barriers (no early exit).
+constexpr int kTriCThreads = 512;  // launch uses 256 for n <= 256 (one thread per index)
+
+// sum over the CTA, identical in every thread: warp sums, then warp 0 sums the
+// partials (fixed tree) and publishes the total.  Warps whose lanes all carry
+// zero skip their FP64 work (the FP64 pipe is the scarce resource).
+__device__ __forceinline__ double block_reduce(double v, double* red, bool warp_active) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (warp_active) v = warp_sum(v);
+  if (lane == 0) red[warp] = warp_active ? v : 0.0;
+  __syncthreads();
+  if (warp == 0) {
+    double t = (lane < nw) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[16] = t;
+  }
+  __syncthreads();
+  return red[16];
+}
+
+template <int NPER>
+__global__ void __launch_bounds__(kTriCThreads) tridiag_cluster_kernel(EigState st, const double* __restrict__ g) {
+  extern __shared__ double sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int n = st.n;
+  const int C = (int)cl.num_blocks(), b = (int)cl.block_rank();
+  const int rows = (n + C - 1) / C;
+  double* vprev = sm;           // v_{s-1}
+  double* vcur = sm + n;        // v_s
+  double* wv = sm + 2 * n;      // w_{s-1}
+  double* red1 = sm + 3 * n;    // 16 partials + total
+  double* red2 = red1 + 24;     // 16 partials + total
+  double* sx = red2 + 24;       // [0] row_s[s+1], [1] row_s[s]
+  double* pfull = sx + 16;      // [2][n] p_s, written into every CTA by the row owners
+  double* A = pfull + 2 * n;    // [rows][n]
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  for (int li = 0; li < rows; ++li) {
+    const int i = li * C + b;
+    for (int j = tid; j < n; j += blockDim.x) A[(int64_t)li * n + j] = (i < n) ? g[(int64_t)i * n + j] : 0.0;
+  }
+  for (int i = tid; i < n; i += blockDim.x) {
+    vprev[i] = 0.0; vcur[i] = 0.0; wv[i] = 0.0; pfull[i] = 0.0; pfull[n + i] = 0.0;
+  }
+  double tau_prev = 0.0;
+  cl.sync();
+  for (int s = 0; s <= n - 2; ++s) {
+    const int j = s + tid;
+    const bool has = j < n;
+    const bool wact = s + (tid & ~31) < n;  // some lane of this warp has j < n
+    // w_{s-1} = p_{s-1} - K v_{s-1}, K = (tau_{s-1} / 2) p_{s-1} . v_{s-1}
+    double pj = 0.0, ps = 0.0, K = 0.0;
+    const double vj = has ? vprev[j] : 0.0, vs = vprev[s];
+    if (s >= 1) {
+      const double* pb = pfull + ((s - 1) & 1) * n;
+      if (has) pj = pb[j];
+      ps = pb[s];
+      K = 0.5 * tau_prev * block_reduce(pj * vj, red1, wact);
+    }
+    const double wj = pj - K * vj, ws = ps - K * vs;
+    // row s of A^(s), entries j >= s, read from the owner of row s
+    double rowj = 0.0;
+    if (has) rowj = *cl.map_shared_rank(A + (int64_t)(s / C) * n + j, s % C) - vs * wj - ws * vj;
+    if (s <= n - 3) {
+      if (tid == 1) sx[0] = rowj;
+      if (tid == 0) sx[1] = rowj;
+      const double sig2 = block_reduce((j >= s + 2 && has) ? rowj * rowj : 0.0, red2, wact);
+      const double x0 = sx[0], ds = sx[1];
+      double alpha, tau, scal;
+      if (sig2 == 0.0) {
+        tau = 0.0; alpha = x0; scal = 0.0;
+      } else {
+        const double nrm = sqrt(x0 * x0 + sig2);
+        alpha = (x0 >= 0.0) ? -nrm : nrm;
+        tau = (alpha - x0) / alpha;
+        scal = 1.0 / (x0 - alpha);
+      }
+      if (has) {
+        wv[j] = wj;
+        vcur[j] = (j == s + 1) ? 1.0 : ((j > s + 1) ? rowj * scal : 0.0);
+      }
+      __syncthreads();
+      if (b == 0) {
+        for (int q = tid; q < n; q += blockDim.x) st.hv[(int64_t)s * n + q] = (q > s) ? vcur[q] : 0.0;
+        if (tid == 0) { st.d[s] = ds; st.e[s] = alpha; st.tau[s] = tau; }
+      }
+      // fused update of the owned rows >= s+1 and p_s, a warp per row, the
+      // lane's slice of the vectors in registers
+      double vp[NPER], wq[NPER], vc[NPER];
+#pragma unroll
+      for (int q = 0; q < NPER; ++q) {
+        const int jj = s + 1 + lane + 32 * q;
+        const bool ok = jj < n;
+        vp[q] = ok ? vprev[jj] : 0.0;
+        wq[q] = ok ? wv[jj] : 0.0;
+        vc[q] = ok ? vcur[jj] : 0.0;
+      }
+      double* pout = pfull + (s & 1) * n;
+      const int li0 = (s + 1 - b + C - 1) / C;  // first local row with global index >= s+1
+      for (int li = li0 + warp; li < rows; li += nwarp) {
+        const int i = li * C + b;
+        if (i >= n) break;
+        const double vi = vprev[i], wi = wv[i];
+        double* arow = A + (int64_t)li * n + s + 1 + lane;
+        double a[NPER];
+#pragma unroll
+        for (int q = 0; q < NPER; ++q) a[q] = (s + 1 + lane + 32 * q < n) ? arow[32 * q] : 0.0;
+#pragma unroll
+        for (int q = 0; q < NPER; ++q) {
+          a[q] = fma(-vi, wq[q], fma(-wi, vp[q], a[q]));
+          if (s + 1 + lane + 32 * q < n) arow[32 * q] = a[q];
+          a[q] *= vc[q];
+        }
+#pragma unroll
+        for (int w = 1; w < NPER; w <<= 1)
+#pragma unroll
+          for (int q = 0; q + w < NPER; q += 2 * w) a[q] += a[q + w];
+        const double acc = warp_sum(a[0]);
+        // p_s[i] into every CTA of the cluster (remote stores, visible after the barrier)
+        if (lane < C) *cl.map_shared_rank(pout + i, lane) = tau * acc;
+      }
+      cl.sync();
+      double* t = vprev;
+      vprev = vcur;
+      vcur = t;
+      tau_prev = tau;
+    } else {
+      // s == n-2: the last 2 x 2 block
+      if (b == 0 && tid == 0) { st.d[s] = rowj; st.tau[s] = 0.0; }
+      if (b == 0 && tid == 1) {
+        st.e[s] = rowj;
+        const double a11 = *cl.map_shared_rank(A + (int64_t)((n - 1) / C) * n + (n - 1), (n - 1) % C);
+        st.d[n - 1] = a11 - 2.0 * vj * wj;
+      }
+    }
+  }
+  // no CTA may leave while another can still read its shared memory
+  cl.sync();
+}
+
 __global__ void tridiag_small_kernel(EigState st) {
   // n == 1
   if (threadIdx.x == 0) { st.d[0] = st.a[0]; st.e[0] = 0.0; }
@@ -248,25 +402,38 @@ __global__ void scale_kernel(EigState st) {
 }
 
 // Number of eigenvalues of T (scaled, |entries| <= 1) smaller than sigma: sign
-// changes of the leading principal minors p_0 = 1, p_1, ..., p_n.
+// changes of the leading principal minors p_0 = 1, p_1, ..., p_n.  The
+// recurrence p_i = (d_i - sigma) p_{i-1} - e_{i-1}^2 p_{i-2} is one dependent
+// FMA per row (e^2 p_{i-2} and d_i - sigma are ready a step early); the
+// power-of-two rescaling only selects, so it adds no FP64 latency.
 __device__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n, double sigma) {
   double pp = 1.0, p = d[0] - sigma;
   const double tiny = 0x1p-900;
   if (p == 0.0) p = -tiny;
   int cnt = (p < 0.0);
-  for (int i = 1; i < n; ++i) {
-    double q = fma(d[i] - sigma, p, -e2[i - 1] * pp);
-    if (q == 0.0) q = (p < 0.0) ? tiny : -tiny;
-    cnt += ((q < 0.0) != (p < 0.0));
-    pp = p;
-    p = q;
-    // rescale by 2^-512 / 2^512 when the pair leaves [2^-480, 2^480]
-    int ex = (__double2hiint(p) >> 20) & 0x7ff;
-    if (ex > 1023 + 480) { p *= 0x1p-512; pp *= 0x1p-512; }
-    else if (ex < 1023 - 480) {
-      int ex2 = (__double2hiint(pp) >> 20) & 0x7ff;
-      if (ex2 < 1023 - 480) { p *= 0x1p512; pp *= 0x1p512; }
+  int i = 1;
+  while (i < n) {
+    const int i1 = min(n, i + 4);
+    for (; i < i1; ++i) {
+      const double t = e2[i - 1] * pp;
+      const double dm = d[i] - sigma;
+      double q = fma(dm, p, -t);
+      const long long qb = __double_as_longlong(q), pb = __double_as_longlong(p);
+      // an exact zero continues with the sign opposite to p (a sign change)
+      if ((qb & 0x7fffffffffffffffll) == 0) q = (pb < 0) ? tiny : -tiny;
+      cnt += (int)(((unsigned long long)(__double_as_longlong(q) ^ pb)) >> 63);
+      pp = p;
+      p = q;
     }
+    // rescale by 2^-500 / 2^500 when max(|p|, |pp|) leaves [2^-500, 2^500]: a
+    // row grows the pair at most 3-fold (|entries| <= 1) and shrinks it at most
+    // by e^2 >= 2^-120 (the floor applied when e2 is built), so between checks
+    // it stays within [2^-980, 2^507]
+    const int ex = (__double2hiint(p) >> 20) & 0x7ff;
+    const int ex2 = (__double2hiint(pp) >> 20) & 0x7ff;
+    const int mx = max(ex, ex2);
+    if (mx > 1023 + 500) { p *= 0x1p-500; pp *= 0x1p-500; }
+    else if (mx < 1023 - 500) { p *= 0x1p500; pp *= 0x1p500; }
   }
   return cnt;
 }
@@ -278,7 +445,7 @@ __global__ void bisect_kernel(EigState st) {
   double* e2 = sm + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     d[i] = st.d[i];
-    e2[i] = (i < n - 1) ? st.e[i] * st.e[i] : 0.0;
+    e2[i] = (i < n - 1) ? fmax(st.e[i] * st.e[i], 0x1p-120) : 0.0;
   }
   __syncthreads();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;  // j-th largest
@@ -391,35 +558,49 @@ __global__ void invit_kernel(EigState st, const int* __restrict__ grp_start, con
 
 // X = H_0 H_1 ... H_{n-3} Z, one warp per column; then the sign convention and
 // the transpose into v (n x nvec row-major).
+template <int NPER>
 __global__ void backtransform_kernel(EigState st, int nvec, double* __restrict__ v) {
   const int n = st.n;
   const int lane = threadIdx.x & 31;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col >= nvec) return;
-  constexpr int MAXPER = 32;  // n <= 1024
-  double z[MAXPER];
+  constexpr int MAXPER = NPER;  // n <= 32 * NPER
+  double z[MAXPER], h[MAXPER];
   const double* zc = st.z + (int64_t)col * n;
 #pragma unroll
   for (int q = 0; q < MAXPER; ++q) {
     int i = lane + 32 * q;
     z[q] = (i < n) ? zc[i] : 0.0;
   }
+  // reflector s acts on entries i > s; the next one is prefetched while the
+  // current one is applied (the loop is a chain of dependent reductions)
+  auto load_h = [&](int s) {
+    const double* hv = st.hv + (int64_t)s * n;
+#pragma unroll
+    for (int q = 0; q < MAXPER; ++q) {
+      const int i = lane + 32 * q;
+      h[q] = (i > s && i < n) ? __ldg(hv + i) : 0.0;
+    }
+  };
+  if (n >= 3) load_h(n - 3);
   for (int s = n - 3; s >= 0; --s) {
     const double t = st.tau[s];
+    double hc[MAXPER];
+#pragma unroll
+    for (int q = 0; q < MAXPER; ++q) hc[q] = h[q];
+    if (s > 0) load_h(s - 1);
     if (t == 0.0) continue;
-    const double* hv = st.hv + (int64_t)s * n;
-    double part = 0.0;
+    // pairwise dot product (tree depth log2(MAXPER)) and warp reduction
+    double pr[MAXPER];
 #pragma unroll
-    for (int q = 0; q < MAXPER; ++q) {
-      int i = lane + 32 * q;
-      if (i > s && i < n) part = fma(__ldg(hv + i), z[q], part);
-    }
-    double dot = warp_sum(part) * t;
+    for (int q = 0; q < MAXPER; ++q) pr[q] = hc[q] * z[q];
 #pragma unroll
-    for (int q = 0; q < MAXPER; ++q) {
-      int i = lane + 32 * q;
-      if (i > s && i < n) z[q] -= dot * __ldg(hv + i);
-    }
+    for (int w = 1; w < MAXPER; w <<= 1)
+#pragma unroll
+      for (int q = 0; q + w < MAXPER; q += 2 * w) pr[q] += pr[q + w];
+    const double dot = warp_sum(pr[0]) * t;
+#pragma unroll
+    for (int q = 0; q < MAXPER; ++q) z[q] = fma(-dot, hc[q], z[q]);
   }
   // sign: entry of largest magnitude (first on ties) positive
   double best = -1.0;
@@ -472,40 +653,46 @@ __global__ void group_kernel(EigState st, int nvec, int* grp_start, int* ngrp) {
 // lane evaluates a Sturm count at one of 32 interior points per round, so a
 // round narrows the bracket 33-fold (5 bits).  One warp per CTA spreads the
 // FP64 work over many SMs.
-__global__ void __launch_bounds__(32) msect_kernel(EigState st, int K) {
+// Multisection: kMsThreads Sturm counts per round at equally spaced points of
+// the current bracket of eigenvalue j (descending order), one CTA per
+// eigenvalue; every thread derives the new bracket from the same ballots.
+constexpr int kMsThreads = 64;
+__global__ void __launch_bounds__(kMsThreads) msect_kernel(EigState st, int K) {
   const int j = blockIdx.x;
   if (j >= K) return;
   const int n = st.n;
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   extern __shared__ double smd[];
+  __shared__ unsigned masks[kMsThreads / 32];
   double* d = smd;
   double* e2 = smd + n;
-  for (int i = lane; i < n; i += 32) {
+  for (int i = tid; i < n; i += kMsThreads) {
     d[i] = st.d[i];
-    e2[i] = (i < n - 1) ? st.e[i] * st.e[i] : 0.0;
+    // floor 2^-120 on e^2 (changes eigenvalues by <= 2^-60): bounds the decay of the recurrence
+    e2[i] = (i < n - 1) ? fmax(st.e[i] * st.e[i], 0x1p-120) : 0.0;
   }
-  __syncwarp();
+  __syncthreads();
   const int m = n - 1 - j;
-  double lo = -1.0, hi = 1.0;  // Gershgorin radius <= 1 after scaling
-  for (int round = 0; round < 14; ++round) {
-    const double p = lo + (hi - lo) * (double)(lane + 1) * (1.0 / 33.0);
+  const double inv = 1.0 / (double)(kMsThreads + 1);
+  double lo = -1.0, hi = 1.0;  // Gershgorin radius < 1 after scaling
+  for (int round = 0; round < 16; ++round) {
+    const double p = lo + (hi - lo) * (double)(tid + 1) * inv;
     const int c = sturm_count(d, e2, n, p);
     const unsigned above = __ballot_sync(0xffffffffu, c > m);
-    double nlo, nhi;
-    if (above == 0u) {
-      nlo = __shfl_sync(0xffffffffu, p, 31);
-      nhi = hi;
-    } else {
-      const int f = __ffs(above) - 1;
-      nhi = __shfl_sync(0xffffffffu, p, f);
-      const double pf = __shfl_sync(0xffffffffu, p, f > 0 ? f - 1 : 0);
-      nlo = (f == 0) ? lo : pf;
-    }
+    if (lane == 0) masks[warp] = above;
+    __syncthreads();
+    int f = kMsThreads;  // first point above eigenvalue j
+    for (int w = 0; w < kMsThreads / 32; ++w)
+      if (masks[w]) { f = 32 * w + __ffs(masks[w]) - 1; break; }
+    const double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f * inv;
+    const double nhi = (f == kMsThreads) ? hi : lo + (hi - lo) * (double)(f + 1) * inv;
     lo = nlo;
     hi = nhi;
-    if (hi - lo <= 0x1p-53 * fmax(fabs(lo), fabs(hi)) + 0x1p-60) break;
+    __syncthreads();
+    // stop at (about) one ulp: adjacent doubles satisfy the relative test
+    if (hi - lo <= 0x1p-52 * fmax(fabs(lo), fabs(hi)) + 0x1p-60) break;
   }
-  if (lane == 0) st.lam[j] = 0.5 * (lo + hi);
+  if (tid == 0) st.lam[j] = 0.5 * (lo + hi);
 }
 
 __device__ __forceinline__ double hash_start(uint32_t a, uint32_t b) {
@@ -520,67 +707,85 @@ __device__ __forceinline__ double hash_start(uint32_t a, uint32_t b) {
 
 // Inverse iteration for every requested eigenvalue in parallel (one thread per
 // vector, one vector per CTA to spread the FP64 recurrences over the SMs);
-// deterministic pseudo-random start vectors, three solves.  Close eigenvalues
-// are re-orthogonalised afterwards by mgs_group_kernel.
+// deterministic pseudo-random start vectors, three solves.  The LU factors and
+// the iterate live in shared memory: the recurrences are sequential, so every
+// access sits on the critical path.  Close eigenvalues are re-orthogonalised
+// afterwards by mgs_group_kernel.
 __global__ void __launch_bounds__(32) invit_par_kernel(EigState st, int nvec) {
+  extern __shared__ double smi[];
   const int j = blockIdx.x;
-  if (j >= nvec || threadIdx.x != 0) return;
+  if (j >= nvec) return;
   const int n = st.n;
-  double* x = st.z + (int64_t)j * n;
-  double* fl = st.lu + (int64_t)j * 5 * n;
+  double* fl = smi;
   double* fd = fl + n;
   double* fu = fd + n;
   double* fu2 = fu + n;
   double* fp = fu2 + n;
+  double* x = fp + n;
   const double lam = st.lam[j];
-  const double eps_piv = 0x1p-52;
-  for (int i = 0; i < n; ++i) {
+  for (int i = threadIdx.x; i < n; i += 32) {
     fd[i] = st.d[i] - lam;
     fl[i] = (i < n - 1) ? st.e[i] : 0.0;
     fu[i] = (i < n - 1) ? st.e[i] : 0.0;
     fu2[i] = 0.0;
     fp[i] = 0.0;
+    x[i] = hash_start((uint32_t)j, (uint32_t)i);
   }
-  for (int i = 0; i < n - 1; ++i) {
-    if (fabs(fd[i]) >= fabs(fl[i])) {
-      double piv = fd[i];
-      if (fabs(piv) < eps_piv) { piv = (piv < 0.0) ? -eps_piv : eps_piv; fd[i] = piv; }
-      const double l = fl[i] / piv;
-      fl[i] = l;
-      fd[i + 1] -= l * fu[i];
-    } else {
-      const double l = fd[i] / fl[i];
-      fd[i] = fl[i];
-      fl[i] = l;
-      const double t = fu[i];
-      fu[i] = fd[i + 1];
-      fd[i + 1] = t - l * fd[i + 1];
-      if (i < n - 2) { fu2[i] = fu[i + 1]; fu[i + 1] = -l * fu[i + 1]; }
-      fp[i] = 1.0;
-    }
-  }
-  for (int i = 0; i < n; ++i)
-    if (fabs(fd[i]) < eps_piv) fd[i] = (fd[i] < 0.0) ? -eps_piv : eps_piv;
-  for (int i = 0; i < n; ++i) fu2[i] = (i + 2 < n) ? fu2[i] : 0.0;
-  // reciprocal pivots once: the solves then multiply
-  for (int i = 0; i < n; ++i) fd[i] = 1.0 / fd[i];
-  for (int i = 0; i < n; ++i) x[i] = hash_start((uint32_t)j, (uint32_t)i);
-  for (int it = 0; it < 3; ++it) {
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    const double eps_piv = 0x1p-52;
     for (int i = 0; i < n - 1; ++i) {
-      if (fp[i] != 0.0) { const double t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
-      x[i + 1] -= fl[i] * x[i];
+      if (fabs(fd[i]) >= fabs(fl[i])) {
+        double piv = fd[i];
+        if (fabs(piv) < eps_piv) { piv = (piv < 0.0) ? -eps_piv : eps_piv; fd[i] = piv; }
+        const double l = fl[i] / piv;
+        fl[i] = l;
+        fd[i + 1] -= l * fu[i];
+      } else {
+        const double l = fd[i] / fl[i];
+        fd[i] = fl[i];
+        fl[i] = l;
+        const double t = fu[i];
+        fu[i] = fd[i + 1];
+        fd[i + 1] = t - l * fd[i + 1];
+        if (i < n - 2) { fu2[i] = fu[i + 1]; fu[i + 1] = -l * fu[i + 1]; }
+        fp[i] = 1.0;
+      }
     }
-    for (int i = n - 1; i >= 0; --i) {
-      double v = x[i];
-      if (i + 1 < n) v -= fu[i] * x[i + 1];
-      if (i + 2 < n) v -= fu2[i] * x[i + 2];
-      x[i] = v * fd[i];
-    }
-    double mx = 0.0;
-    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(x[i]));
-    const double inv = (mx > 0.0) ? 1.0 / mx : 1.0;
-    for (int i = 0; i < n; ++i) x[i] *= inv;
   }
+  __syncwarp();
+  // pivot clamp and reciprocals: independent per entry, done by the whole warp
+  for (int i = threadIdx.x; i < n; i += 32) {
+    double v = fd[i];
+    if (fabs(v) < 0x1p-52) v = (v < 0.0) ? -0x1p-52 : 0x1p-52;
+    fd[i] = 1.0 / v;
+    if (i + 2 >= n) fu2[i] = 0.0;
+  }
+  __syncwarp();
+  for (int it = 0; it < 3; ++it) {
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < n - 1; ++i) {
+        if (fp[i] != 0.0) { const double t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+        x[i + 1] -= fl[i] * x[i];
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double v = x[i];
+        if (i + 1 < n) v -= fu[i] * x[i + 1];
+        if (i + 2 < n) v -= fu2[i] * x[i + 2];
+        x[i] = v * fd[i];
+      }
+    }
+    __syncwarp();
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) mx = fmax(mx, fabs(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const double inv = (mx > 0.0) ? 1.0 / mx : 1.0;
+    for (int i = threadIdx.x; i < n; i += 32) x[i] *= inv;
+    __syncwarp();
+  }
+  double* xo = st.z + (int64_t)j * n;
+  for (int i = threadIdx.x; i < n; i += 32) xo[i] = x[i];
 }
 
 // Modified Gram-Schmidt (two passes) inside every group of size > 1, then
@@ -662,6 +867,66 @@ int setup_state(int n, int nvec_max) {
 
 }  // namespace
 
+constexpr int kClusterMaxN = 512;
+
+size_t tri_cluster_smem(int n, int C) {
+  const int rows = (n + C - 1) / C;
+  return sizeof(double) * ((size_t)5 * n + 64 + (size_t)rows * n);
+}
+
+template <int NPER>
+int tri_cluster_attr() {
+  if (cudaFuncSetAttribute(tridiag_cluster_kernel<NPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(tridiag_cluster_kernel<NPER>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return 1;
+}
+
+// Cluster size of the shared-memory tridiagonalisation for this n (16 if the
+// device schedules such clusters with this much shared memory, else 8), or 0.
+int cluster_size_for(int n) {
+  static int attr_ok = -1;
+  static int last_n = -1, last_c = 0;
+  if (n == last_n) return last_c;
+  if (attr_ok < 0) attr_ok = tri_cluster_attr<8>() && tri_cluster_attr<16>();
+  int found = 0;
+  for (int C : {16, 8}) {
+    if (!attr_ok) break;
+    const size_t smem = tri_cluster_smem(n, C);
+    if (smem > 200 * 1024) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(n <= 256 ? 256 : kTriCThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    const cudaError_t oe = (n <= 256) ? cudaOccupancyMaxActiveClusters(&nclusters, tridiag_cluster_kernel<8>, &cfg)
+                                      : cudaOccupancyMaxActiveClusters(&nclusters, tridiag_cluster_kernel<16>, &cfg);
+    if (trace_enabled())
+      fprintf(stderr, "[atc] tridiag cluster n=%d C=%d smem=%zu: %s, %d clusters\n", n, C, smem, cudaGetErrorString(oe),
+              nclusters);
+    if (oe == cudaSuccess && nclusters > 0) {
+      found = C;
+      break;
+    }
+    cudaGetLastError();
+  }
+  if (trace_enabled() && !attr_ok) fprintf(stderr, "[atc] tridiag cluster attributes rejected\n");
+  last_n = n;
+  last_c = found;
+  return found;
+}
+
 int launch_eig_values_impl(const double* g, int n, cudaStream_t s) {
   if (n < 1 || n > 1024) return fail(ATC_EUNSUP, "eigensolver supports 1 <= n <= 1024 (n = %d)", n);
   ATC_TRY(setup_state(n, n));
@@ -671,6 +936,27 @@ int launch_eig_values_impl(const double* g, int n, cudaStream_t s) {
   ATC_CUDA_TRY(cudaMemsetAsync(st.d, 0, sizeof(double) * 3 * n, s));
   if (n == 1) {
     tridiag_small_kernel<<<1, 32, 0, s>>>(st);
+    ATC_LAUNCHED(1);
+  } else if (n <= kClusterMaxN && cluster_size_for(n) > 0) {
+    const int C = cluster_size_for(n);
+    const int rows = (n + C - 1) / C;
+    const size_t smem = tri_cluster_smem(n, C);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(n <= 256 ? 256 : kTriCThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (n <= 256)
+      ATC_CUDA_TRY(cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel<8>, st, g));
+    else
+      ATC_CUDA_TRY(cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel<16>, st, g));
     ATC_LAUNCHED(1);
   } else {
     static int max_blocks = -1;
@@ -712,7 +998,7 @@ int launch_eig_more(int n, int K, double* lam, cudaStream_t s) {
   if (g_state.n != n) return fail(ATC_EINVAL, "eigenvalues requested without a tridiagonal matrix");
   if (K > n) K = n;
   EigState st = g_state;
-  msect_kernel<<<K, 32, sizeof(double) * 2 * n, s>>>(st, K);
+  msect_kernel<<<K, kMsThreads, sizeof(double) * 2 * n, s>>>(st, K);
   ATC_LAUNCHED(1);
   if (lam) {
     unscale_kernel<<<(K + 255) / 256, 256, 0, s>>>(st, lam, K);
@@ -739,11 +1025,13 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
   int* ngrp = grp + nvec + 2;
   group_kernel<<<1, 32, 0, s>>>(st, nvec, grp, ngrp);
   ATC_LAUNCHED(1);
-  invit_par_kernel<<<nvec, 32, 0, s>>>(st, nvec);
+  invit_par_kernel<<<nvec, 32, sizeof(double) * 6 * n, s>>>(st, nvec);
   ATC_LAUNCHED(1);
   mgs_group_kernel<<<nvec, 128, 0, s>>>(st, grp, ngrp);
   ATC_LAUNCHED(1);
-  backtransform_kernel<<<nvec, 32, 0, s>>>(st, nvec, v);
+  if (n <= 256) backtransform_kernel<8><<<nvec, 32, 0, s>>>(st, nvec, v);
+  else if (n <= 512) backtransform_kernel<16><<<nvec, 32, 0, s>>>(st, nvec, v);
+  else backtransform_kernel<32><<<nvec, 32, 0, s>>>(st, nvec, v);
   ATC_LAUNCHED(1);
   return ATC_OK;
 }
