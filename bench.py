@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp16", choices=list(PRECISIONS))
+    ap.add_argument("--precision", default="bf16", choices=list(PRECISIONS))
     ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -291,42 +291,71 @@ def run_ours(args, world, rank, local):
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_per = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world)
 
-    # roofline of the dominant phase's main kernel
+    # rooflines.  Per step the phases are timed by CUDA events on the library's
+    # stream; the unit of each roofline is the phase (its kernels are listed).
     hbm, bf16, bf16s, peak_src = load_peaks()
+    gram_tflops_issued = 0.0  # tensor-core FLOPs issued: 9 slice products per 128 x 64 tile entry
+    ttm_tflops_issued = 0.0   # 9 slice products per 128 x N(chunk, padded to 16) tile entry
+    ttm_bytes = 0.0
+    cur3 = list(dims)
+    for m in order:
+        S = float(np.prod(cur3))
+        n = cur3[m]
+        K = S / n
+        nt128, nc64 = -(-n // 128), -(-n // 64)
+        ntile = sum(nc64 - 2 * t for t in range(nt128))
+        gram_tflops_issued += 9 * 2.0 * 128 * 64 * K * ntile
+        r = ranks[m]
+        nch = -(-r // 32)
+        csz = -(-r // nch)
+        apad = -(-csz // 16) * 16
+        ttm_tflops_issued += 9 * 2.0 * (-(-K // 128) * 128) * apad * nch * n
+        ttm_bytes += S * 4.0 + K * r * 4.0
+        cur3[m] = r
+
+    def roof_of(name, kernels, ms, alg_bytes, issued_flops):
+        gbs = alg_bytes / (ms * 1e-3) / 1e9
+        tfs = issued_flops / (ms * 1e-3) / 1e12 if issued_flops else 0.0
+        fr_h, fr_t = gbs / hbm, (tfs / bf16s if issued_flops else 0.0)
+        bound = "tensor" if fr_t > fr_h else "hbm"
+        d = {"kernel": name, "kernels": kernels, "bound": bound,
+             "achieved": tfs if bound == "tensor" else gbs, "peak": bf16s if bound == "tensor" else hbm,
+             "unit": "TFLOP/s" if bound == "tensor" else "GB/s", "frac": fr_t if bound == "tensor" else fr_h,
+             "traffic": None, "hbm_gbs": gbs, "hbm_frac": fr_h, "tensor_tflops_issued": tfs, "tensor_frac": fr_t,
+             "ms_per_step": ms, "peak_source": peak_src + " (sustained bf16 for the tensor view)"}
+        return d
+
+    roof_gram = roof_of("gram phase", "absmax_kernel, gram_tc_kernel, gram_tc_assemble", phases["ms_gram"],
+                        gram_bytes, gram_tflops_issued)
+    roof_ttm = roof_of("projection + certification phase", "ttm_prep_b, ttm_tc_kernel (projection and residual), "
+                       "row_energy, compact, eigenvectors", phases["ms_ttm"], ttm_bytes, ttm_tflops_issued)
     ph_share = {"gram": phases["ms_gram"], "eig": phases["ms_eig"], "ttm": phases["ms_ttm"],
                 "quant+encode": phases["ms_quant"] + phases["ms_encode"]}
     dom = max(ph_share, key=ph_share.get)
     if dom == "gram":
-        ach = gram_bytes / (phases["ms_gram"] * 1e-3) / 1e9
-        roof = {"kernel": "gram_tc_kernel (+split-K reduce)", "bound": "hbm", "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "traffic": None}
+        roof = dict(roof_gram)
     elif dom == "ttm":
-        ttm_bytes = 0.0
-        cur2 = list(dims)
-        for m in order:
-            S = float(np.prod(cur2))
-            ttm_bytes += S * 4.0 + S / cur2[m] * ranks[m] * 4.0
-            cur2[m] = ranks[m]
-        ach = ttm_bytes / (phases["ms_ttm"] * 1e-3) / 1e9
-        roof = {"kernel": "ttm_tc_kernel", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None}
+        roof = dict(roof_ttm)
     elif dom == "eig":
         # FP64 work of the eigensolver: tridiagonalisation 4/3 n^3 + back-transformation 2 n^2 r per mode
         fl = sum(4.0 / 3.0 * dims[m] ** 3 + 2.0 * dims[m] ** 2 * ranks[m] for m in order)
         ach = fl / (phases["ms_eig"] * 1e-3) / 1e12
-        fp64_peak = 1.1  # TFLOP/s, torch float64 matmul measured on this machine's GB300 (no FP64 entry in the peaks file)
-        roof = {"kernel": "eigensolver (tridiag_kernel dominant)", "bound": "alu", "achieved": ach,
-                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None}
+        fp64_peak = 1.1  # TFLOP/s: torch float64 matmul on this machine's GB300 (no FP64 entry in the peaks file)
+        roof = {"kernel": "eigensolver phase", "kernels": "tridiag_cluster_kernel, msect_kernel, invit_par_kernel, "
+                "mgs_group_kernel, backtransform_kernel", "bound": "alu", "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s (FP64)", "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "measured FP64 DGEMM rate (torch float64 matmul), not in the peaks file"}
     else:
         roof = {"kernel": "quantizer/encoder", "bound": "alu", "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None}
-    roof["peak_source"] = peak_src
     roof["share_of_step"] = ph_share[dom] / per_ms
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp16": "fp16x2-split/f32-acc/f64-eig", "bf16": "bf16x2-split/f32-acc/f64-eig",
-                                          "fp64": "f64"}[args.precision],
+            "vs_baseline": None, "dtype": {"fp16": "fp16", "bf16": "bf16", "fp64": "f64"}[args.precision],
+            "dtype_detail": "tensor-core operands: three integer slices per value (exact in bf16/fp16), FP32 "
+                            "accumulation that never rounds, FP64 eigensolve and FP64 rank sums"
+            if args.precision != "fp64" else "FP64 throughout",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "rel_eps": args.eps, "precision": args.precision,
                        "step": "atc_compress + atc_decompress", "l2": "flushed (256 MB write) before each timed step",
@@ -334,7 +363,8 @@ def run_ours(args, world, rank, local):
             "ranks": ranks, "achieved_rel_err": re, "stream_bytes": len(s),
             "sthosvd_gbs": nbytes / (sthosvd_ms * 1e-3) / 1e9, "sthosvd_tflops": tflops,
             "phases_ms": phases, "fp64_plain": fp64,
-            "roofline": roof, "clocks": clk, "gpu_launches": launches,
+            "roofline": roof, "roofline_gram": roof_gram, "roofline_ttm": roof_ttm,
+            "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": world * nbytes / (e2e_per * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes + len(s), "ms_per_step": e2e_per}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

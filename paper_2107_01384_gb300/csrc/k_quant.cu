@@ -793,6 +793,177 @@ __global__ void decode_kernel(DecParams D) {
   }
 }
 
+// Block-parallel decoder (blocks of at most kDecMax coefficients): one CTA per
+// block, the block's magnitudes and signs in shared memory.  Per plane the
+// run-length symbols are decoded by one thread - there is one symbol per new
+// significant coefficient (plus a final run), not one step per coefficient -
+// and two block-wide scans place the new leading bits (rank among the
+// insignificant coefficients -> index) and the raw bits (trailing bits of
+// significant coefficients and signs of new ones, in coefficient order).  The
+// result is identical to the sequential walk of the encoder's order.
+constexpr int kDecThreads = 256;
+constexpr int kDecMax = 4096;
+constexpr int kDecPer = kDecMax / kDecThreads;  // 16 consecutive coefficients per thread
+
+// exclusive prefix over the CTA of a per-thread count; *total receives the sum
+__device__ __forceinline__ int64_t dec_scan(int64_t v, int64_t* sh, int64_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int64_t t = (lane < kDecThreads / 32) ? sh[lane] : 0;
+    int64_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t u = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += u;
+    }
+    if (lane < kDecThreads / 32) sh[8 + lane] = ti - t;  // exclusive warp offsets
+    if (lane == kDecThreads / 32 - 1) sh[16] = ti;
+  }
+  __syncthreads();
+  const int64_t r = sh[8 + w] + inc - v;
+  *total = sh[16];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) {
+  __shared__ unsigned long long qs[kDecMax];
+  __shared__ uint8_t ss[kDecMax];
+  __shared__ uint32_t newbm[kDecMax / 32];
+  __shared__ int64_t scan_sh[24];
+  __shared__ int s_err;
+  __shared__ uint32_t s_rl, s_wl;
+  const int64_t b = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
+  for (int i = tid; i < kDecMax; i += kDecThreads) { qs[i] = 0; ss[i] = 0; }
+  if (tid == 0) s_err = (*D.err != 0) ? -1 : 0;
+  __syncthreads();
+  if (s_err) return;
+  uint64_t pos = D.boff[b];
+  const uint8_t* ftab = D.sec + 48;
+  const int64_t j0 = lo + (int64_t)tid * kDecPer;  // this thread's first coefficient
+  for (int pi = 0; pi < D.nplanes; ++pi) {
+    const int p = 63 - pi;
+    int64_t hi = hi_all;
+    if (p == D.p_star && hi > D.i_star + 1) hi = max(lo, D.i_star + 1);
+    for (int i = tid; i < kDecMax / 32; i += kDecThreads) newbm[i] = 0u;
+    if (tid == 0) {
+      const uint8_t* t = D.sec + D.tab + (b * D.nplanes + pi) * 8;
+      s_rl = rd32(t);
+      s_wl = rd32(t + 4);
+      if (pos + s_rl + s_wl > (uint64_t)D.nbytes) s_err = 2;
+      else if (s_rl && s_rl < 4) s_err = 3;
+    }
+    // 1. rank of every insignificant coefficient among the insignificant ones
+    uint32_t sigm = 0, actm = 0;
+    for (int u = 0; u < kDecPer; ++u) {
+      const int64_t j = j0 + u;
+      if (j < hi) {
+        actm |= 1u << u;
+        if (qs[j - lo] != 0) sigm |= 1u << u;
+      }
+    }
+    int64_t n_insig = 0;
+    const int64_t rank0 = dec_scan(__popc(actm & ~sigm), scan_sh, &n_insig);  // (barriers inside)
+    // 2. run-length symbols of this plane: one thread
+    if (tid == 0 && s_err == 0 && n_insig > 0) {
+      const uint32_t rl = s_rl;
+      if (!rl) s_err = 5;
+      const uint8_t* rp = D.sec + pos;
+      const uint8_t* rend = rp + rl;
+      uint32_t f[kNsym], cum[kNsym];
+      uint32_t ca = 0;
+      for (int i = 0; i < kNsym; ++i) {
+        f[i] = (uint32_t)ftab[2 * (pi * kNsym + i)] | ((uint32_t)ftab[2 * (pi * kNsym + i) + 1] << 8);
+        cum[i] = ca;
+        ca += f[i];
+      }
+      uint32_t x = 0;
+      if (s_err == 0) { x = rd32(rp); rp += 4; }
+      int64_t q = 0;
+      while (s_err == 0 && q < n_insig) {
+        const uint32_t slot = x & (kM - 1);
+        int sb = -1;
+        for (int i = 0; i < kNsym; ++i)
+          if (f[i] && slot >= cum[i] && slot < cum[i] + f[i]) { sb = i; break; }
+        if (sb < 0) { s_err = 6; break; }
+        x = f[sb] * (x >> kScaleBits) + slot - cum[sb];
+        while (x < kRansL) { if (rp >= rend) { s_err = 7; break; } x = (x << 8) | *rp++; }
+        if (s_err) break;
+        uint32_t extra = 0;
+        if (sb > 0) {
+          extra = x & ((1u << sb) - 1u);
+          x >>= sb;
+          while (x < kRansL) { if (rp >= rend) { s_err = 8; break; } x = (x << 8) | *rp++; }
+          if (s_err) break;
+        }
+        q += (int64_t)((1u << sb) - 1u + extra);
+        if (q < n_insig) {
+          newbm[q >> 5] |= 1u << (q & 31);
+          ++q;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_err) break;
+    // 3. raw bits: one per significant coefficient (a trailing bit) and one per
+    //    new significant coefficient (its sign), in coefficient order
+    uint32_t newm = 0;
+    {
+      int64_t r = rank0;
+      for (int u = 0; u < kDecPer; ++u)
+        if ((actm >> u & 1u) && !(sigm >> u & 1u)) {
+          if (newbm[r >> 5] >> (r & 31) & 1u) newm |= 1u << u;
+          ++r;
+        }
+    }
+    const uint32_t consm = sigm | newm;
+    int64_t ncons = 0;
+    const int64_t rb0 = dec_scan(__popc(consm), scan_sh, &ncons);
+    const uint64_t rcap = (uint64_t)s_wl * 8;
+    if ((uint64_t)ncons > rcap) {
+      if (tid == 0) s_err = 4;
+    } else {
+      const uint8_t* raw = D.sec + pos + s_rl;
+      int64_t rbit = rb0;
+      for (int u = 0; u < kDecPer; ++u) {
+        if (!(consm >> u & 1u)) continue;
+        const uint32_t bit = (__ldg(raw + (rbit >> 3)) >> (rbit & 7)) & 1u;
+        ++rbit;
+        const int64_t jj = j0 + u - lo;
+        if (sigm >> u & 1u) qs[jj] |= (unsigned long long)bit << p;
+        else { qs[jj] |= 1ull << p; ss[jj] = (uint8_t)bit; }
+      }
+    }
+    pos += s_rl + s_wl;
+    __syncthreads();
+    if (s_err) break;
+  }
+  if (s_err) {
+    if (tid == 0 && s_err > 0) atomicExch(D.err, s_err);
+    return;
+  }
+  for (int u = 0; u < kDecPer; ++u) {
+    const int64_t j = j0 + u;
+    if (j >= hi_all) break;
+    const uint64_t a = qs[j - lo];
+    if (a == 0) { D.out[j] = 0.0; continue; }
+    const int pj = (j <= D.i_star) ? D.p_star : D.p_star + 1;
+    const uint64_t v = a + ((pj >= 1) ? (1ull << (pj - 1)) : 0ull);
+    const double m = mul_pow2(__ull2double_rn(v), -D.k);
+    D.out[j] = ss[j - lo] ? -m : m;
+  }
+}
+
 static void put32(uint8_t* p, uint32_t v) { for (int i = 0; i < 4; ++i) p[i] = (uint8_t)(v >> (8 * i)); }
 static void put64(uint8_t* p, uint64_t v) { for (int i = 0; i < 8; ++i) p[i] = (uint8_t)(v >> (8 * i)); }
 static uint32_t get32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i); return v; }
@@ -995,7 +1166,8 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
   D.sec = dsec; D.qt = qt; D.sg = sg; D.out = core; D.err = err; D.boff = boff;
   block_offsets_kernel<<<1, 32, 0, s>>>(D, boff);
   ATC_LAUNCHED(1);
-  decode_kernel<<<(unsigned)((D.nblocks + 63) / 64), 64, 0, s>>>(D);
+  if (D.block_size <= kDecMax) decode_block_kernel<<<(unsigned)D.nblocks, kDecThreads, 0, s>>>(D);
+  else decode_kernel<<<(unsigned)((D.nblocks + 63) / 64), 64, 0, s>>>(D);
   ATC_LAUNCHED(1);
   int herr = 0;
   ATC_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
