@@ -203,7 +203,11 @@ def run_ours(args, world, rank, local):
     def step(precision):
         c = P.atc_compress(xd, args.eps, precision=precision, stream=stream)
         s = c.stream_bytes()
-        rc = P.lib().atc_decompress(s, len(s), P._dev(out), P.ATC_F32, P._stream(stream))
+        opt = P.Options()
+        P.lib().atc_default_options(P.C.byref(opt))
+        opt.precision = precision
+        opt.stream = P._stream(stream)
+        rc = P.lib().atc_decompress_ex(s, len(s), P._dev(out), P.ATC_F32, P.C.byref(opt))
         if rc != 0:
             raise P.AtcError(rc, P.lib().atc_last_error().decode())
         return c, s

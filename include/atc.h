@@ -124,6 +124,16 @@ int atc_peek_dims(const uint8_t* stream, size_t nbytes, int* ndim, int64_t* dims
  */
 int atc_decompress(const uint8_t* stream, size_t nbytes, void* out_dev, int out_dtype, void* cuda_stream);
 
+/*
+ * atc_decompress with options: opt->stream is the CUDA stream; with
+ * opt->precision = ATC_PREC_SPLIT_BF16 / _FP16 the expansion runs on the
+ * tensor cores (the same exact fixed-point slice products as the projection,
+ * FP32 intermediates, one rounding per output), with ATC_PREC_FP64 (or
+ * opt == NULL) exactly as atc_decompress.  Other option fields are ignored.
+ * Errors: as atc_decompress; ATC_EUNSUP for a rank above 1024 on the split paths.
+ */
+int atc_decompress_ex(const uint8_t* stream, size_t nbytes, void* out_dev, int out_dtype, const atc_options* opt);
+
 /* ------------------------------------------------------------------------
  * Step entry points: one per stage of the hot path, for parity tests and
  * for callers that drive the loop themselves.  All sizes are element counts.

@@ -33,7 +33,8 @@ lib_path = os.path.join(HERE, "libatc.so")
 # every symbol include/atc.h declares
 EXPORTS = [
     "atc_default_options", "atc_compress", "atc_get_ranks", "atc_get_core", "atc_get_factor",
-    "atc_get_stream", "atc_get_stats", "atc_free", "atc_peek_dims", "atc_decompress", "atc_norm2",
+    "atc_get_stream", "atc_get_stats", "atc_free", "atc_peek_dims", "atc_decompress", "atc_decompress_ex",
+    "atc_norm2",
     "atc_gram", "atc_eig_sym", "atc_rank_select", "atc_ttm", "atc_quantize_core",
     "atc_dequantize_core", "atc_free_buffer", "atc_release_workspace", "atc_last_error",
     "atc_kernel_launches", "atc_gram_fp64_noalloc",
@@ -84,6 +85,7 @@ def lib():
         L.atc_free.restype = None
         L.atc_peek_dims.argtypes = [C.c_char_p, C.c_size_t, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
         L.atc_decompress.argtypes = [C.c_char_p, C.c_size_t, vp, i32, vp]
+        L.atc_decompress_ex.argtypes = [C.c_char_p, C.c_size_t, vp, i32, C.POINTER(Options)]
         L.atc_norm2.argtypes = [vp, i64, i32, vp, vp]
         L.atc_gram.argtypes = [vp, i32, i64, i64, i64, i32, vp, vp]
         L.atc_eig_sym.argtypes = [vp, i32, vp, vp, i32, vp]
@@ -264,8 +266,17 @@ def atc_peek_dims(stream_bytes: bytes):
     return list(dims)[: nd.value], dt.value
 
 
-def atc_decompress(stream_bytes: bytes, out_dtype=torch.float64, device="cuda", stream=None) -> torch.Tensor:
+def atc_decompress(stream_bytes: bytes, out_dtype=torch.float64, device="cuda", stream=None,
+                   precision: int = PREC_FP64) -> torch.Tensor:
+    """Decode a stream; precision selects the FP64 or the tensor-core expansion."""
     dims, _ = atc_peek_dims(stream_bytes)
     out = torch.empty(dims, dtype=out_dtype, device=device)
-    _check(lib().atc_decompress(stream_bytes, len(stream_bytes), _dev(out), _dt(out), _stream(stream)))
+    if precision == PREC_FP64:
+        _check(lib().atc_decompress(stream_bytes, len(stream_bytes), _dev(out), _dt(out), _stream(stream)))
+    else:
+        opt = Options()
+        lib().atc_default_options(C.byref(opt))
+        opt.precision = precision
+        opt.stream = _stream(stream)
+        _check(lib().atc_decompress_ex(stream_bytes, len(stream_bytes), _dev(out), _dt(out), C.byref(opt)))
     return out

@@ -515,7 +515,7 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         // FP64 tridiagonalisation, then only the largest K eigenvalues (more
         // if the rank is not decided among them); tail(r) = trace(G) - sum_{j<r}
         // lambda_j in FP64.
-        rc = launch_eig_tridiag(G, (int)n, ddev + 2, s);
+        rc = launch_eig_tridiag(G, (int)n, ddev + 2, s, opt.precision != ATC_PREC_FP64);
         if (rc) return bail(rc);
         int K = (int)std::min<int64_t>(n, 48);
         double tr = 0.0;
@@ -745,7 +745,20 @@ int atc_peek_dims(const uint8_t* stream, size_t nbytes, int* ndim, int64_t* dims
 }
 
 int atc_decompress(const uint8_t* stream, size_t nbytes, void* out_dev, int out_dtype, void* cuda_stream) {
+  atc_options o;
+  atc_default_options(&o);
+  o.stream = cuda_stream;
+  return atc_decompress_ex(stream, nbytes, out_dev, out_dtype, &o);
+}
+
+int atc_decompress_ex(const uint8_t* stream, size_t nbytes, void* out_dev, int out_dtype, const atc_options* opt) {
   if (!stream || !out_dev || !dtype_size(out_dtype)) return fail(ATC_EINVAL, "atc_decompress: bad arguments");
+  atc_options o;
+  atc_default_options(&o);
+  if (opt) o = *opt;
+  void* cuda_stream = o.stream;
+  const bool split = (o.precision == ATC_PREC_SPLIT_BF16 || o.precision == ATC_PREC_SPLIT_FP16);
+  if (!split && o.precision != ATC_PREC_FP64) return fail(ATC_EINVAL, "bad precision %d", (int)o.precision);
   int d = 0, dt = 0;
   int64_t dims[8];
   ATC_TRY(atc_peek_dims(stream, nbytes, &d, dims, &dt));
@@ -806,6 +819,33 @@ int atc_decompress(const uint8_t* stream, size_t nbytes, void* out_dev, int out_
   ATC_TRY(Scratch::get(SLOT_DEC2, sizeof(double) * maxsz, (void**)&B));
   ATC_TRY(launch_permute(vec, ranks, perm, d, A, 1, s));
   std::vector<int> ord = decompression_order(d, dims, ranks);
+  if (split) {
+    // tensor-core expansion: FP64 core in, FP32 intermediates (ping-pong in the
+    // same scratch), the last step straight into out_dev when it is FP32
+    float* fa = reinterpret_cast<float*>(B);
+    float* fb = reinterpret_cast<float*>(A);
+    const void* src = A;
+    int sdt = ATC_F64;
+    int64_t cur[8];
+    for (int i = 0; i < d; ++i) cur[i] = ranks[i];
+    for (size_t q = 0; q < ord.size(); ++q) {
+      const int m = ord[q];
+      int64_t L = 1, R = 1;
+      for (int i = 0; i < m; ++i) L *= cur[i];
+      for (int i = m + 1; i < d; ++i) R *= cur[i];
+      const bool last = (q + 1 == ord.size());
+      float* dst = (last && out_dtype == ATC_F32) ? reinterpret_cast<float*>(out_dev) : fa;
+      ATC_TRY(launch_ttm_split(src, sdt, L, dims[m], R, U[m], ranks[m], 1, o.precision, dst, ATC_F32, s));
+      cur[m] = dims[m];
+      src = dst;
+      sdt = ATC_F32;
+      std::swap(fa, fb);
+    }
+    // FP64 output: widen the FP32 result
+    if (out_dtype != ATC_F32) ATC_TRY(launch_convert_to_f64(src, ATC_F32, N, reinterpret_cast<double*>(out_dev), s));
+    ATC_CUDA_TRY(cudaStreamSynchronize(s));
+    return ATC_OK;
+  }
   int64_t cur[8];
   for (int i = 0; i < d; ++i) cur[i] = ranks[i];
   double* src = A;

@@ -119,7 +119,9 @@ int launch_eig_sym(const double* g, int n, double* lam, double* v, int nvec, cud
 int launch_eig_values(const double* g, int n, double* lam, cudaStream_t s);
 int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s);
 // tridiagonalise only (+ FP64 trace of G into *trace_dev); then the K largest eigenvalues
-int launch_eig_tridiag(const double* g, int n, double* trace_dev, cudaStream_t s);
+// use_dd: double-float (FP32-pair) solver for n <= 512 (the split paths); the
+// following eig_more / eig_vectors calls use the same arithmetic
+int launch_eig_tridiag(const double* g, int n, double* trace_dev, cudaStream_t s, bool use_dd = false);
 int launch_eig_more(int n, int K, double* lam, cudaStream_t s);
 int launch_rank_select(const double* lam, int n, double budget, int* r_dev, double* disc_dev, cudaStream_t s);
 int eig_read_error(int* err);

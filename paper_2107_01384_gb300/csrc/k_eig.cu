@@ -56,6 +56,7 @@ struct EigState {
   int n;
 };
 EigState g_state = {};  // host-side copy of the scratch layout (single-stream use per device)
+bool g_state_dd = false;  // the current tridiagonal matrix came from the double-float solver
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
@@ -790,10 +791,12 @@ __global__ void __launch_bounds__(32) invit_par_kernel(EigState st, int nvec) {
 
 // Modified Gram-Schmidt (two passes) inside every group of size > 1, then
 // normalisation of every vector; one CTA per group.
-__global__ void mgs_group_kernel(EigState st, const int* __restrict__ grp_start, const int* __restrict__ ngrp) {
+__global__ void mgs_group_kernel(EigState st, const int* __restrict__ grp_start, const int* __restrict__ ngrp,
+                                 int gmin_exclusive) {
   __shared__ double red[32];
   if ((int)blockIdx.x >= *ngrp) return;
   const int g0 = grp_start[blockIdx.x], g1 = grp_start[blockIdx.x + 1];
+  if (g1 - g0 <= gmin_exclusive) return;  // handled by cholqr_group_kernel
   const int n = st.n;
   for (int k = g0; k < g1; ++k) {
     double* xk = st.z + (int64_t)k * n;
@@ -812,6 +815,67 @@ __global__ void mgs_group_kernel(EigState st, const int* __restrict__ grp_start,
     const double nr = block_sum(part, red);
     const double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) xk[i] *= inv;
+    __syncthreads();
+  }
+}
+
+// Orthonormalisation of every group of close eigenvalues by CholQR2: the
+// vectors of inverse iteration are already nearly orthonormal (well
+// conditioned), so two passes of  W = Z^T Z,  W = R^T R,  Z <- Z R^-1
+// reach orthonormality to rounding level, with parallel dot products instead
+// of a chain of Gram-Schmidt reductions.  One CTA per group of at most
+// kQrMax vectors (larger groups use mgs_group_kernel).
+constexpr int kQrMax = 48;
+__global__ void __launch_bounds__(256) cholqr_group_kernel(EigState st, const int* __restrict__ grp_start,
+                                                           const int* __restrict__ ngrp, int gmax) {
+  __shared__ double W[kQrMax * kQrMax];
+  if ((int)blockIdx.x >= *ngrp) return;
+  const int g0 = grp_start[blockIdx.x], g1 = grp_start[blockIdx.x + 1];
+  const int g = g1 - g0;
+  if (g > gmax) return;
+  const int n = st.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double* Z = st.z + (int64_t)g0 * n;  // column c of the group at Z + c * n
+  for (int pass = 0; pass < 2; ++pass) {
+    // W = Z^T Z (upper triangle), a warp per entry
+    for (int e = warp; e < g * g; e += nw) {
+      const int a = e / g, c = e % g;
+      if (c < a) continue;
+      const double* za = Z + (int64_t)a * n;
+      const double* zc = Z + (int64_t)c * n;
+      double part = 0.0;
+      for (int i = lane; i < n; i += 32) part = fma(za[i], zc[i], part);
+      part = warp_sum(part);
+      if (lane == 0) { W[a * kQrMax + c] = part; W[c * kQrMax + a] = part; }
+    }
+    __syncthreads();
+    // Cholesky W = R^T R (R upper, stored in the upper triangle of W); one warp
+    if (warp == 0) {
+      for (int k = 0; k < g; ++k) {
+        const double dkk = sqrt(fmax(W[k * kQrMax + k], 1e-300));
+        const double inv = 1.0 / dkk;
+        __syncwarp();
+        for (int c = k + 1 + lane; c < g; c += 32) W[k * kQrMax + c] *= inv;
+        if (lane == 0) W[k * kQrMax + k] = dkk;
+        __syncwarp();
+        for (int e = lane; e < (g - k - 1) * (g - k - 1); e += 32) {
+          const int a = k + 1 + e / (g - k - 1), c = k + 1 + e % (g - k - 1);
+          if (c >= a) W[a * kQrMax + c] -= W[k * kQrMax + a] * W[k * kQrMax + c];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // Z <- Z R^-1, a thread per row: forward substitution y R = z
+    for (int i = tid; i < n; i += blockDim.x) {
+      double y[kQrMax];
+      for (int c = 0; c < g; ++c) {
+        double v = Z[(int64_t)c * n + i];
+        for (int a = 0; a < c; ++a) v -= y[a] * W[a * kQrMax + c];
+        y[c] = v / W[c * kQrMax + c];
+      }
+      for (int c = 0; c < g; ++c) Z[(int64_t)c * n + i] = y[c];
+    }
     __syncthreads();
   }
 }
@@ -840,6 +904,437 @@ __global__ void rank_kernel(const double* __restrict__ lam, int n, double budget
   }
   *r_out = r;
   *disc_out = disc;
+}
+
+// ===================================================== double-float (FP32 pairs)
+// The split paths' eigensolver runs on the FP32 pipes: a value is an
+// unevaluated sum hi + lo of two floats (48-bit significand, error-free
+// transformations with FMA; Dekker, Numer. Math. 18, 1971; the "double-double"
+// technique at single-precision width).  On GB300 an FP64 operation has a
+// 64-cycle latency and 1/64 of the FP32 rate, while the algorithms here are
+// chains of dependent operations, so the pair arithmetic is several times
+// faster at an accuracy (2^-47 relative per operation) far inside what the
+// residual-certified rank choice needs.  The tridiagonal matrix is scaled to
+// |entries| <= 1 first, so the float exponent range is never approached.
+struct dd {
+  float hi, lo;
+};
+__device__ __forceinline__ dd ddf(float a) { return dd{a, 0.f}; }
+__device__ __forceinline__ dd dd_from(double x) {
+  const float h = (float)x;
+  return dd{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double dd_to(dd a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dd dd_qts(float s, float e) {  // |s| >= |e|
+  const float h = s + e;
+  return dd{h, e - (h - s)};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  const float s = a.hi + b.hi;
+  const float bp = s - a.hi;
+  float e = (a.hi - (s - bp)) + (b.hi - bp);
+  e += a.lo + b.lo;
+  return dd_qts(s, e);
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
+__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return dd_qts(p, e);
+}
+__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
+// a / b: float quotient, one correction from the exact residual
+__device__ __forceinline__ dd dd_div(dd a, dd b) {
+  const float rb = 1.0f / b.hi;
+  const float q1 = a.hi * rb;
+  const dd r = dd_sub(a, dd_mul(b, ddf(q1)));
+  const float q2 = r.hi * rb;
+  const dd q = dd_qts(q1, q2);
+  const dd r2 = dd_sub(a, dd_mul(b, q));
+  return dd_add(q, ddf(r2.hi * rb));
+}
+// sqrt(a), a >= 0: float root, one Newton correction
+__device__ __forceinline__ dd dd_sqrt(dd a) {
+  if (a.hi <= 0.f) return dd{0.f, 0.f};
+  const float x = sqrtf(a.hi);
+  const dd xx = dd_mul(ddf(x), ddf(x));
+  const dd r = dd_sub(a, xx);
+  return dd_qts(x, r.hi * (0.5f / x));
+}
+__device__ __forceinline__ bool dd_neg_sign(dd a) { return a.hi < 0.f || (a.hi == 0.f && a.lo < 0.f); }
+__device__ __forceinline__ dd dd_shfl_xor(dd a, int o) {
+  return dd{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ dd dd_warp_sum(dd a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = dd_add(a, dd_shfl_xor(a, o));
+  return a;
+}
+// CTA sum identical in every thread (warp sums, then warp 0 over the partials)
+__device__ __forceinline__ dd dd_block_reduce(dd v, dd* red, bool warp_active) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (warp_active) v = dd_warp_sum(v);
+  if (lane == 0) red[warp] = warp_active ? v : dd{0.f, 0.f};
+  __syncthreads();
+  if (warp == 0) {
+    dd t = (lane < nw) ? red[lane] : dd{0.f, 0.f};
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) t = dd_add(t, dd_shfl_xor(t, o));
+    if (lane == 0) red[16] = t;
+  }
+  __syncthreads();
+  return red[16];
+}
+
+// Householder tridiagonalisation in double-float on one cluster (the
+// iteration of tridiag_cluster_kernel).  G is scaled by 2^-sh (diag max ->
+// [0.5, 1)) on load; d and e are written back unscaled in FP64, the reflectors
+// as float pairs (row s of hv holds v_s).
+template <int NPER>
+__global__ void __launch_bounds__(kTriCThreads) tridiag_cluster_dd_kernel(EigState st, const double* __restrict__ g) {
+  extern __shared__ dd smdd[];
+  __shared__ double s_scale[2];
+  cg::cluster_group cl = cg::this_cluster();
+  const int n = st.n;
+  const int C = (int)cl.num_blocks(), b = (int)cl.block_rank();
+  const int rows = (n + C - 1) / C;
+  dd* vprev = smdd;
+  dd* vcur = smdd + n;
+  dd* wv = smdd + 2 * n;
+  dd* red1 = smdd + 3 * n;  // 17 used
+  dd* red2 = red1 + 24;
+  dd* sx = red2 + 24;
+  dd* pfull = sx + 16;      // [2][n]
+  dd* A = pfull + 2 * n;    // [rows][n]
+  dd* hvo = reinterpret_cast<dd*>(st.hv);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  // power-of-two scale from the largest diagonal entry (G is PSD: it bounds |G|)
+  if (warp == 0) {
+    double m = 0.0;
+    for (int i = lane; i < n; i += 32) m = fmax(m, fabs(g[(int64_t)i * n + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+      int ex = 0;
+      if (m > 0.0) frexp(m, &ex);
+      s_scale[0] = ldexp(1.0, -ex);
+      s_scale[1] = ldexp(1.0, ex);
+    }
+  }
+  __syncthreads();
+  const double sc = s_scale[0], usc = s_scale[1];
+  for (int li = 0; li < rows; ++li) {
+    const int i = li * C + b;
+    for (int j = tid; j < n; j += blockDim.x)
+      A[(int64_t)li * n + j] = (i < n) ? dd_from(g[(int64_t)i * n + j] * sc) : dd{0.f, 0.f};
+  }
+  for (int i = tid; i < n; i += blockDim.x) {
+    vprev[i] = dd{0.f, 0.f}; vcur[i] = dd{0.f, 0.f}; wv[i] = dd{0.f, 0.f};
+    pfull[i] = dd{0.f, 0.f}; pfull[n + i] = dd{0.f, 0.f};
+  }
+  dd tau_prev = dd{0.f, 0.f};
+  const dd zero = dd{0.f, 0.f};
+  cl.sync();
+  for (int s = 0; s <= n - 2; ++s) {
+    const int j = s + tid;
+    const bool has = j < n;
+    const bool wact = s + (tid & ~31) < n;
+    dd pj = zero, ps = zero, K = zero;
+    const dd vj = has ? vprev[j] : zero, vs = vprev[s];
+    if (s >= 1) {
+      const dd* pb = pfull + ((s - 1) & 1) * n;
+      if (has) pj = pb[j];
+      ps = pb[s];
+      const dd dot = dd_block_reduce(has ? dd_mul(pj, vj) : zero, red1, wact);
+      K = dd_mul(dd_mul(ddf(0.5f), tau_prev), dot);
+    }
+    const dd wj = dd_sub(pj, dd_mul(K, vj)), ws = dd_sub(ps, dd_mul(K, vs));
+    dd rowj = zero;
+    if (has) {
+      const dd a = *cl.map_shared_rank(A + (int64_t)(s / C) * n + j, s % C);
+      rowj = dd_sub(dd_sub(a, dd_mul(vs, wj)), dd_mul(ws, vj));
+    }
+    if (s <= n - 3) {
+      if (tid == 1) sx[0] = rowj;
+      if (tid == 0) sx[1] = rowj;
+      const dd sig2 = dd_block_reduce((j >= s + 2 && has) ? dd_mul(rowj, rowj) : zero, red2, wact);
+      const dd x0 = sx[0], ds = sx[1];
+      dd alpha, tau, scal;
+      if (sig2.hi == 0.f) {
+        tau = zero; alpha = x0; scal = zero;
+      } else {
+        const dd nrm = dd_sqrt(dd_add(dd_mul(x0, x0), sig2));
+        alpha = dd_neg_sign(x0) ? nrm : dd_neg(nrm);
+        tau = dd_div(dd_sub(alpha, x0), alpha);
+        scal = dd_div(ddf(1.0f), dd_sub(x0, alpha));
+      }
+      if (has) {
+        wv[j] = wj;
+        vcur[j] = (j == s + 1) ? ddf(1.0f) : ((j > s + 1) ? dd_mul(rowj, scal) : zero);
+      }
+      __syncthreads();
+      if (b == 0) {
+        for (int q = tid; q < n; q += blockDim.x) hvo[(int64_t)s * n + q] = (q > s) ? vcur[q] : zero;
+        if (tid == 0) { st.d[s] = dd_to(ds) * usc; st.e[s] = dd_to(alpha) * usc; st.tau[s] = dd_to(tau); }
+      }
+      dd vp[NPER], wq[NPER], vc[NPER];
+#pragma unroll
+      for (int q = 0; q < NPER; ++q) {
+        const int jj = s + 1 + lane + 32 * q;
+        const bool ok = jj < n;
+        vp[q] = ok ? vprev[jj] : zero;
+        wq[q] = ok ? wv[jj] : zero;
+        vc[q] = ok ? vcur[jj] : zero;
+      }
+      dd* pout = pfull + (s & 1) * n;
+      const int li0 = (s + 1 - b + C - 1) / C;
+      for (int li = li0 + warp; li < rows; li += nwarp) {
+        const int i = li * C + b;
+        if (i >= n) break;
+        const dd vi = vprev[i], wi = wv[i];
+        dd* arow = A + (int64_t)li * n + s + 1 + lane;
+        dd a[NPER];
+#pragma unroll
+        for (int q = 0; q < NPER; ++q) a[q] = (s + 1 + lane + 32 * q < n) ? arow[32 * q] : zero;
+#pragma unroll
+        for (int q = 0; q < NPER; ++q) {
+          a[q] = dd_sub(dd_sub(a[q], dd_mul(vi, wq[q])), dd_mul(wi, vp[q]));
+          if (s + 1 + lane + 32 * q < n) arow[32 * q] = a[q];
+          a[q] = dd_mul(a[q], vc[q]);
+        }
+#pragma unroll
+        for (int w = 1; w < NPER; w <<= 1)
+#pragma unroll
+          for (int q = 0; q + w < NPER; q += 2 * w) a[q] = dd_add(a[q], a[q + w]);
+        const dd acc = dd_mul(tau, dd_warp_sum(a[0]));
+        if (lane < C) *cl.map_shared_rank(pout + i, lane) = acc;
+      }
+      cl.sync();
+      dd* t = vprev;
+      vprev = vcur;
+      vcur = t;
+      tau_prev = tau;
+    } else {
+      if (b == 0 && tid == 0) { st.d[s] = dd_to(rowj) * usc; st.tau[s] = 0.0; }
+      if (b == 0 && tid == 1) {
+        st.e[s] = dd_to(rowj) * usc;
+        const dd a11 = *cl.map_shared_rank(A + (int64_t)((n - 1) / C) * n + (n - 1), (n - 1) % C);
+        st.d[n - 1] = dd_to(dd_sub(a11, dd_mul(ddf(2.0f), dd_mul(vj, wj)))) * usc;
+      }
+    }
+  }
+  cl.sync();
+}
+
+// Sturm count in double-float with the LDL^T recurrence
+// q_i = (d_i - sigma) - e_{i-1}^2 / q_{i-1}, |q| floored at pivmin (as in
+// bisection codes of LAPACK's dstebz); T scaled to |entries| < 1.
+__device__ int sturm_count_dd(const dd* __restrict__ d, const dd* __restrict__ e2, int n, dd sigma) {
+  const float pivmin = 0x1p-90f;
+  dd q = dd_sub(d[0], sigma);
+  if (fabsf(q.hi) < pivmin) q = dd{-pivmin, 0.f};
+  int cnt = dd_neg_sign(q);
+  for (int i = 1; i < n; ++i) {
+    q = dd_sub(dd_sub(d[i], sigma), dd_div(e2[i - 1], q));
+    if (fabsf(q.hi) < pivmin) q = dd{-pivmin, 0.f};
+    cnt += dd_neg_sign(q);
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(kMsThreads) msect_dd_kernel(EigState st, int K) {
+  const int j = blockIdx.x;
+  if (j >= K) return;
+  const int n = st.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  extern __shared__ dd smm[];
+  __shared__ unsigned masks[kMsThreads / 32];
+  dd* d = smm;
+  dd* e2 = smm + n;
+  for (int i = tid; i < n; i += kMsThreads) {
+    d[i] = dd_from(st.d[i]);
+    e2[i] = (i < n - 1) ? dd_from(st.e[i] * st.e[i]) : dd{0.f, 0.f};
+  }
+  __syncthreads();
+  const int m = n - 1 - j;
+  const double inv = 1.0 / (double)(kMsThreads + 1);
+  double lo = -1.0, hi = 1.0;  // Gershgorin radius < 1 after scaling
+  for (int round = 0; round < 16; ++round) {
+    const double p = lo + (hi - lo) * (double)(tid + 1) * inv;
+    const int c = sturm_count_dd(d, e2, n, dd_from(p));
+    const unsigned above = __ballot_sync(0xffffffffu, c > m);
+    if (lane == 0) masks[warp] = above;
+    __syncthreads();
+    int f = kMsThreads;
+    for (int w = 0; w < kMsThreads / 32; ++w)
+      if (masks[w]) { f = 32 * w + __ffs(masks[w]) - 1; break; }
+    const double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f * inv;
+    const double nhi = (f == kMsThreads) ? hi : lo + (hi - lo) * (double)(f + 1) * inv;
+    lo = nlo;
+    hi = nhi;
+    __syncthreads();
+    // double-float resolution of the recurrence: about 2^-44 relative, 2^-70 absolute
+    if (hi - lo <= 0x1p-44 * fmax(fabs(lo), fabs(hi)) + 0x1p-70) break;
+  }
+  if (tid == 0) st.lam[j] = 0.5 * (lo + hi);
+}
+
+// Inverse iteration in double-float (the iteration of invit_par_kernel).
+__global__ void __launch_bounds__(32) invit_dd_kernel(EigState st, int nvec) {
+  extern __shared__ dd smv[];
+  const int j = blockIdx.x;
+  if (j >= nvec) return;
+  const int n = st.n;
+  dd* fl = smv;
+  dd* fd = fl + n;
+  dd* fu = fd + n;
+  dd* fu2 = fu + n;
+  dd* x = fu2 + n;
+  uint8_t* fp = reinterpret_cast<uint8_t*>(x + n);
+  const dd lam = dd_from(st.lam[j]);
+  const dd zero = dd{0.f, 0.f};
+  for (int i = threadIdx.x; i < n; i += 32) {
+    fd[i] = dd_sub(dd_from(st.d[i]), lam);
+    fl[i] = (i < n - 1) ? dd_from(st.e[i]) : zero;
+    fu[i] = fl[i];
+    fu2[i] = zero;
+    fp[i] = 0;
+    x[i] = dd_from(hash_start((uint32_t)j, (uint32_t)i));
+  }
+  __syncwarp();
+  const float eps_piv = 0x1p-46f;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n - 1; ++i) {
+      if (fabsf(fd[i].hi) >= fabsf(fl[i].hi)) {
+        dd piv = fd[i];
+        if (fabsf(piv.hi) < eps_piv) { piv = dd{piv.hi < 0.f ? -eps_piv : eps_piv, 0.f}; fd[i] = piv; }
+        const dd l = dd_div(fl[i], piv);
+        fl[i] = l;
+        fd[i + 1] = dd_sub(fd[i + 1], dd_mul(l, fu[i]));
+      } else {
+        const dd l = dd_div(fd[i], fl[i]);
+        fd[i] = fl[i];
+        fl[i] = l;
+        const dd t = fu[i];
+        fu[i] = fd[i + 1];
+        fd[i + 1] = dd_sub(t, dd_mul(l, fd[i + 1]));
+        if (i < n - 2) { fu2[i] = fu[i + 1]; fu[i + 1] = dd_neg(dd_mul(l, fu[i + 1])); }
+        fp[i] = 1;
+      }
+    }
+  }
+  __syncwarp();
+  for (int i = threadIdx.x; i < n; i += 32) {
+    dd v = fd[i];
+    if (fabsf(v.hi) < eps_piv) v = dd{v.hi < 0.f ? -eps_piv : eps_piv, 0.f};
+    fd[i] = dd_div(ddf(1.0f), v);
+    if (i + 2 >= n) fu2[i] = zero;
+  }
+  __syncwarp();
+  for (int it = 0; it < 3; ++it) {
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < n - 1; ++i) {
+        if (fp[i]) { const dd t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+        x[i + 1] = dd_sub(x[i + 1], dd_mul(fl[i], x[i]));
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        dd v = x[i];
+        if (i + 1 < n) v = dd_sub(v, dd_mul(fu[i], x[i + 1]));
+        if (i + 2 < n) v = dd_sub(v, dd_mul(fu2[i], x[i + 2]));
+        x[i] = dd_mul(v, fd[i]);
+      }
+    }
+    __syncwarp();
+    float mx = 0.f;
+    for (int i = threadIdx.x; i < n; i += 32) mx = fmaxf(mx, fabsf(x[i].hi));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    // scale by a power of two near 1/max (exact)
+    int ex = 0;
+    if (mx > 0.f) frexpf(mx, &ex);
+    const float sc = ldexpf(1.0f, -ex);
+    for (int i = threadIdx.x; i < n; i += 32) x[i] = dd{x[i].hi * sc, x[i].lo * sc};
+    __syncwarp();
+  }
+  double* xo = st.z + (int64_t)j * n;
+  for (int i = threadIdx.x; i < n; i += 32) xo[i] = dd_to(x[i]);
+}
+
+// Back-transformation X = Q Z with the double-float reflectors of
+// tridiag_cluster_dd_kernel (a warp per column; next reflector prefetched).
+template <int NPER>
+__global__ void backtransform_dd_kernel(EigState st, int nvec, double* __restrict__ v) {
+  const int n = st.n;
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= nvec) return;
+  const dd* hvd = reinterpret_cast<const dd*>(st.hv);
+  const dd zero = dd{0.f, 0.f};
+  dd z[NPER], h[NPER];
+  const double* zc = st.z + (int64_t)col * n;
+#pragma unroll
+  for (int q = 0; q < NPER; ++q) {
+    const int i = lane + 32 * q;
+    z[q] = (i < n) ? dd_from(zc[i]) : zero;
+  }
+  auto load_h = [&](int s) {
+    const dd* hv = hvd + (int64_t)s * n;
+#pragma unroll
+    for (int q = 0; q < NPER; ++q) {
+      const int i = lane + 32 * q;
+      h[q] = (i > s && i < n) ? hv[i] : zero;
+    }
+  };
+  if (n >= 3) load_h(n - 3);
+  for (int s = n - 3; s >= 0; --s) {
+    const dd t = dd_from(st.tau[s]);
+    dd hc[NPER];
+#pragma unroll
+    for (int q = 0; q < NPER; ++q) hc[q] = h[q];
+    if (s > 0) load_h(s - 1);
+    if (t.hi == 0.f) continue;
+    dd pr[NPER];
+#pragma unroll
+    for (int q = 0; q < NPER; ++q) pr[q] = dd_mul(hc[q], z[q]);
+#pragma unroll
+    for (int w = 1; w < NPER; w <<= 1)
+#pragma unroll
+      for (int q = 0; q + w < NPER; q += 2 * w) pr[q] = dd_add(pr[q], pr[q + w]);
+    const dd dot = dd_mul(dd_warp_sum(pr[0]), t);
+#pragma unroll
+    for (int q = 0; q < NPER; ++q) z[q] = dd_sub(z[q], dd_mul(dot, hc[q]));
+  }
+  // sign: entry of largest magnitude (first on ties) positive; write FP64
+  double zz[NPER];
+#pragma unroll
+  for (int q = 0; q < NPER; ++q) zz[q] = dd_to(z[q]);
+  double best = -1.0;
+  int bidx = n;
+  double bval = 0.0;
+#pragma unroll
+  for (int q = 0; q < NPER; ++q) {
+    const int i = lane + 32 * q;
+    if (i < n) {
+      const double a = fabs(zz[q]);
+      if (a > best) { best = a; bidx = i; bval = zz[q]; }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    const double ov = __shfl_xor_sync(0xffffffffu, bval, o);
+    if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; bval = ov; }
+  }
+  const double sg = (bval < 0.0) ? -1.0 : 1.0;
+#pragma unroll
+  for (int q = 0; q < NPER; ++q) {
+    const int i = lane + 32 * q;
+    if (i < n) v[(int64_t)i * nvec + col] = sg * zz[q];
+  }
 }
 
 int setup_state(int n, int nvec_max) {
@@ -886,13 +1381,26 @@ int tri_cluster_attr() {
   return 1;
 }
 
+template <int NPER>
+int tri_cluster_dd_attr() {
+  if (cudaFuncSetAttribute(tridiag_cluster_dd_kernel<NPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(tridiag_cluster_dd_kernel<NPER>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return 1;
+}
+
 // Cluster size of the shared-memory tridiagonalisation for this n (16 if the
 // device schedules such clusters with this much shared memory, else 8), or 0.
 int cluster_size_for(int n) {
   static int attr_ok = -1;
   static int last_n = -1, last_c = 0;
   if (n == last_n) return last_c;
-  if (attr_ok < 0) attr_ok = tri_cluster_attr<8>() && tri_cluster_attr<16>();
+  if (attr_ok < 0) attr_ok = tri_cluster_attr<8>() && tri_cluster_attr<16>() && tri_cluster_dd_attr<8>() &&
+                              tri_cluster_dd_attr<16>();
   int found = 0;
   for (int C : {16, 8}) {
     if (!attr_ok) break;
@@ -927,10 +1435,11 @@ int cluster_size_for(int n) {
   return found;
 }
 
-int launch_eig_values_impl(const double* g, int n, cudaStream_t s) {
+int launch_eig_values_impl(const double* g, int n, cudaStream_t s, bool use_dd = false) {
   if (n < 1 || n > 1024) return fail(ATC_EUNSUP, "eigensolver supports 1 <= n <= 1024 (n = %d)", n);
   ATC_TRY(setup_state(n, n));
   EigState st = g_state;
+  g_state_dd = use_dd && n >= 3 && n <= kClusterMaxN && cluster_size_for(n) > 0;
   ATC_CUDA_TRY(cudaMemcpyAsync(st.a, g, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
   ATC_CUDA_TRY(cudaMemsetAsync(st.flags, 0, 4 * sizeof(int), s));
   ATC_CUDA_TRY(cudaMemsetAsync(st.d, 0, sizeof(double) * 3 * n, s));
@@ -953,10 +1462,16 @@ int launch_eig_values_impl(const double* g, int n, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (n <= 256)
+    if (g_state_dd) {
+      if (n <= 256)
+        ATC_CUDA_TRY(cudaLaunchKernelEx(&cfg, tridiag_cluster_dd_kernel<8>, st, g));
+      else
+        ATC_CUDA_TRY(cudaLaunchKernelEx(&cfg, tridiag_cluster_dd_kernel<16>, st, g));
+    } else if (n <= 256) {
       ATC_CUDA_TRY(cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel<8>, st, g));
-    else
+    } else {
       ATC_CUDA_TRY(cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel<16>, st, g));
+    }
     ATC_LAUNCHED(1);
   } else {
     static int max_blocks = -1;
@@ -998,7 +1513,8 @@ int launch_eig_more(int n, int K, double* lam, cudaStream_t s) {
   if (g_state.n != n) return fail(ATC_EINVAL, "eigenvalues requested without a tridiagonal matrix");
   if (K > n) K = n;
   EigState st = g_state;
-  msect_kernel<<<K, kMsThreads, sizeof(double) * 2 * n, s>>>(st, K);
+  if (g_state_dd) msect_dd_kernel<<<K, kMsThreads, sizeof(dd) * 2 * n, s>>>(st, K);
+  else msect_kernel<<<K, kMsThreads, sizeof(double) * 2 * n, s>>>(st, K);
   ATC_LAUNCHED(1);
   if (lam) {
     unscale_kernel<<<(K + 255) / 256, 256, 0, s>>>(st, lam, K);
@@ -1008,8 +1524,8 @@ int launch_eig_more(int n, int K, double* lam, cudaStream_t s) {
 }
 
 // Tridiagonalise G and return trace(G) (device scalar *trace_dev).
-int launch_eig_tridiag(const double* g, int n, double* trace_dev, cudaStream_t s) {
-  ATC_TRY(launch_eig_values_impl(g, n, s));
+int launch_eig_tridiag(const double* g, int n, double* trace_dev, cudaStream_t s, bool use_dd) {
+  ATC_TRY(launch_eig_values_impl(g, n, s, use_dd));
   trace_g_kernel<<<1, 256, 0, s>>>(g, n, trace_dev);
   ATC_LAUNCHED(1);
   return ATC_OK;
@@ -1025,13 +1541,25 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
   int* ngrp = grp + nvec + 2;
   group_kernel<<<1, 32, 0, s>>>(st, nvec, grp, ngrp);
   ATC_LAUNCHED(1);
-  invit_par_kernel<<<nvec, 32, sizeof(double) * 6 * n, s>>>(st, nvec);
+  if (g_state_dd) invit_dd_kernel<<<nvec, 32, (sizeof(dd) * 5 + 1) * n, s>>>(st, nvec);
+  else invit_par_kernel<<<nvec, 32, sizeof(double) * 6 * n, s>>>(st, nvec);
   ATC_LAUNCHED(1);
-  mgs_group_kernel<<<nvec, 128, 0, s>>>(st, grp, ngrp);
+  // groups are found on the device: CholQR2 handles groups of <= kQrMax vectors,
+  // the sequential Gram-Schmidt kernel the (rare) larger ones
+  cholqr_group_kernel<<<nvec, 256, 0, s>>>(st, grp, ngrp, kQrMax);
   ATC_LAUNCHED(1);
-  if (n <= 256) backtransform_kernel<8><<<nvec, 32, 0, s>>>(st, nvec, v);
-  else if (n <= 512) backtransform_kernel<16><<<nvec, 32, 0, s>>>(st, nvec, v);
-  else backtransform_kernel<32><<<nvec, 32, 0, s>>>(st, nvec, v);
+  mgs_group_kernel<<<nvec, 128, 0, s>>>(st, grp, ngrp, kQrMax);
+  ATC_LAUNCHED(1);
+  if (g_state_dd) {
+    if (n <= 256) backtransform_dd_kernel<8><<<nvec, 32, 0, s>>>(st, nvec, v);
+    else backtransform_dd_kernel<16><<<nvec, 32, 0, s>>>(st, nvec, v);
+  } else if (n <= 256) {
+    backtransform_kernel<8><<<nvec, 32, 0, s>>>(st, nvec, v);
+  } else if (n <= 512) {
+    backtransform_kernel<16><<<nvec, 32, 0, s>>>(st, nvec, v);
+  } else {
+    backtransform_kernel<32><<<nvec, 32, 0, s>>>(st, nvec, v);
+  }
   ATC_LAUNCHED(1);
   return ATC_OK;
 }

@@ -178,3 +178,20 @@ def test_pipeline_split_bumps256(P, prec, eps):
     xh = P.atc_decompress(c.stream_bytes()).cpu().numpy()
     re = np.linalg.norm(x - xh) / np.linalg.norm(x)
     assert 0.98 * eps <= re <= eps, re
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_decompress_split_expansion(P, prec):
+    """The tensor-core expansion (atc_decompress_ex) reproduces the FP64
+    expansion of the same stream to FP32 level (spec bar: 1e-5)."""
+    x = synth.lowrank_tucker()
+    c = P.atc_compress(cuda(x), 1e-2, precision=prec)
+    s = c.stream_bytes()
+    x64 = P.atc_decompress(s).cpu().numpy()
+    xs = P.atc_decompress(s, out_dtype=torch.float32, precision=prec).cpu().numpy().astype(np.float64)
+    xs64 = P.atc_decompress(s, out_dtype=torch.float64, precision=prec).cpu().numpy()
+    nx = np.linalg.norm(x)
+    assert np.linalg.norm(xs - x64) <= 1e-6 * nx
+    assert np.array_equal(xs64, xs)
+    re = np.linalg.norm(x - xs) / nx
+    assert 0.98e-2 <= re <= 1e-2, re
