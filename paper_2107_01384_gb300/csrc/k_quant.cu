@@ -834,6 +834,7 @@ __device__ __forceinline__ int64_t dec_scan(int64_t v, int64_t* sh, int64_t* tot
   return r;
 }
 
+constexpr int kDecBytes = 16384;  // rANS bytes of one (block, plane) staged in shared memory
 __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) {
   __shared__ unsigned long long qs[kDecMax];
   __shared__ uint8_t ss[kDecMax];
@@ -841,6 +842,9 @@ __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) 
   __shared__ int64_t scan_sh[24];
   __shared__ int s_err;
   __shared__ uint32_t s_rl, s_wl;
+  extern __shared__ uint8_t dyn[];
+  uint8_t* sym_of = dyn;               // [kM] slot -> symbol of this plane's table
+  uint8_t* rbytes = dyn + kM;          // [kDecBytes] this plane's rANS bytes
   const int64_t b = blockIdx.x;
   const int tid = threadIdx.x;
   const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
@@ -874,27 +878,41 @@ __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) 
     }
     int64_t n_insig = 0;
     const int64_t rank0 = dec_scan(__popc(actm & ~sigm), scan_sh, &n_insig);  // (barriers inside)
-    // 2. run-length symbols of this plane: one thread
-    if (tid == 0 && s_err == 0 && n_insig > 0) {
-      const uint32_t rl = s_rl;
-      if (!rl) s_err = 5;
-      const uint8_t* rp = D.sec + pos;
-      const uint8_t* rend = rp + rl;
-      uint32_t f[kNsym], cum[kNsym];
+    // stage the plane's symbol table (slot -> symbol, 0xff = unused slot) and,
+    // when they fit, its rANS bytes in shared memory
+    uint32_t f[kNsym], cum[kNsym];
+    {
       uint32_t ca = 0;
       for (int i = 0; i < kNsym; ++i) {
         f[i] = (uint32_t)ftab[2 * (pi * kNsym + i)] | ((uint32_t)ftab[2 * (pi * kNsym + i) + 1] << 8);
         cum[i] = ca;
         ca += f[i];
       }
+    }
+    const bool staged = s_err == 0 && n_insig > 0 && s_rl <= (uint32_t)kDecBytes;
+    if (s_err == 0 && n_insig > 0) {
+      for (int sl = tid; sl < (int)kM; sl += kDecThreads) {
+        uint8_t sb = 0xff;
+        for (int i = 0; i < kNsym; ++i)
+          if (f[i] && (uint32_t)sl >= cum[i] && (uint32_t)sl < cum[i] + f[i]) { sb = (uint8_t)i; break; }
+        sym_of[sl] = sb;
+      }
+      if (staged)
+        for (uint32_t i = tid; i < s_rl; i += kDecThreads) rbytes[i] = __ldg(D.sec + pos + i);
+    }
+    __syncthreads();
+    // 2. run-length symbols of this plane: one thread
+    if (tid == 0 && s_err == 0 && n_insig > 0) {
+      const uint32_t rl = s_rl;
+      if (!rl) s_err = 5;
+      const uint8_t* rp = staged ? rbytes : D.sec + pos;
+      const uint8_t* rend = rp + rl;
       uint32_t x = 0;
       if (s_err == 0) { x = rd32(rp); rp += 4; }
       int64_t q = 0;
       while (s_err == 0 && q < n_insig) {
         const uint32_t slot = x & (kM - 1);
-        int sb = -1;
-        for (int i = 0; i < kNsym; ++i)
-          if (f[i] && slot >= cum[i] && slot < cum[i] + f[i]) { sb = i; break; }
+        const int sb = (sym_of[slot] == 0xff) ? -1 : (int)sym_of[slot];
         if (sb < 0) { s_err = 6; break; }
         x = f[sb] * (x >> kScaleBits) + slot - cum[sb];
         while (x < kRansL) { if (rp >= rend) { s_err = 7; break; } x = (x << 8) | *rp++; }
@@ -1166,7 +1184,12 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
   D.sec = dsec; D.qt = qt; D.sg = sg; D.out = core; D.err = err; D.boff = boff;
   block_offsets_kernel<<<1, 32, 0, s>>>(D, boff);
   ATC_LAUNCHED(1);
-  if (D.block_size <= kDecMax) decode_block_kernel<<<(unsigned)D.nblocks, kDecThreads, 0, s>>>(D);
+  static bool dec_attr = false;
+  if (!dec_attr) {
+    ATC_CUDA_TRY(cudaFuncSetAttribute(decode_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kM + kDecBytes));
+    dec_attr = true;
+  }
+  if (D.block_size <= kDecMax) decode_block_kernel<<<(unsigned)D.nblocks, kDecThreads, kM + kDecBytes, s>>>(D);
   else decode_kernel<<<(unsigned)((D.nblocks + 63) / 64), 64, 0, s>>>(D);
   ATC_LAUNCHED(1);
   int herr = 0;
