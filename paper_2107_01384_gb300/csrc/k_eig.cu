@@ -1162,8 +1162,12 @@ __global__ void __launch_bounds__(kMsThreads) msect_dd_kernel(EigState st, int K
   const int m = n - 1 - j;
   const double inv = 1.0 / (double)(kMsThreads + 1);
   double lo = -1.0, hi = 1.0;  // Gershgorin radius < 1 after scaling
+  // round 0 is geometric: points 0 and 2^-62 .. 2^0 (increasing), so that the
+  // bracket of a small eigenvalue (T comes from a PSD Gram matrix) is within a
+  // factor two after one round; later rounds are linear
   for (int round = 0; round < 16; ++round) {
-    const double p = lo + (hi - lo) * (double)(tid + 1) * inv;
+    const double p = (round == 0) ? ((tid == 0) ? 0.0 : ldexp(1.0, tid - (kMsThreads - 1)))
+                                  : lo + (hi - lo) * (double)(tid + 1) * inv;
     const int c = sturm_count_dd(d, e2, n, dd_from(p));
     const unsigned above = __ballot_sync(0xffffffffu, c > m);
     if (lane == 0) masks[warp] = above;
@@ -1171,8 +1175,16 @@ __global__ void __launch_bounds__(kMsThreads) msect_dd_kernel(EigState st, int K
     int f = kMsThreads;
     for (int w = 0; w < kMsThreads / 32; ++w)
       if (masks[w]) { f = 32 * w + __ffs(masks[w]) - 1; break; }
-    const double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f * inv;
-    const double nhi = (f == kMsThreads) ? hi : lo + (hi - lo) * (double)(f + 1) * inv;
+    double nlo, nhi;
+    if (round == 0) {
+      // point t is 0 (t = 0) or 2^(t-63); kMsThreads points, the last is 1
+      auto pt = [&](int t) { return (t == 0) ? 0.0 : ldexp(1.0, t - (kMsThreads - 1)); };
+      nlo = (f == 0) ? lo : pt(f - 1);
+      nhi = (f == kMsThreads) ? hi : pt(f);
+    } else {
+      nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f * inv;
+      nhi = (f == kMsThreads) ? hi : lo + (hi - lo) * (double)(f + 1) * inv;
+    }
     lo = nlo;
     hi = nhi;
     __syncthreads();
@@ -1234,7 +1246,8 @@ __global__ void __launch_bounds__(32) invit_dd_kernel(EigState st, int nvec) {
     if (i + 2 >= n) fu2[i] = zero;
   }
   __syncwarp();
-  for (int it = 0; it < 3; ++it) {
+  // two solves: the shifts come from multisection to ~2^-44 relative
+  for (int it = 0; it < 2; ++it) {
     if (threadIdx.x == 0) {
       for (int i = 0; i < n - 1; ++i) {
         if (fp[i]) { const dd t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
@@ -1408,7 +1421,7 @@ int cluster_size_for(int n) {
     if (smem > 200 * 1024) continue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
-    cfg.blockDim = dim3(n <= 256 ? 256 : kTriCThreads);
+    cfg.blockDim = dim3(kTriCThreads);  // the larger of the two launch shapes
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
