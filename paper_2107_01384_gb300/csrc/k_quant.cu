@@ -835,6 +835,7 @@ __device__ __forceinline__ int64_t dec_scan(int64_t v, int64_t* sh, int64_t* tot
 }
 
 constexpr int kDecBytes = 16384;  // rANS bytes of one (block, plane) staged in shared memory
+constexpr int kDecDyn = 4 * kM + 4 * kDecMax + kDecBytes;
 __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) {
   __shared__ unsigned long long qs[kDecMax];
   __shared__ uint8_t ss[kDecMax];
@@ -842,9 +843,12 @@ __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) 
   __shared__ int64_t scan_sh[24];
   __shared__ int s_err;
   __shared__ uint32_t s_rl, s_wl;
-  extern __shared__ uint8_t dyn[];
-  uint8_t* sym_of = dyn;               // [kM] slot -> symbol of this plane's table
-  uint8_t* rbytes = dyn + kM;          // [kDecBytes] this plane's rANS bytes
+  extern __shared__ uint32_t dyn32[];
+  // [kM] slot -> (symbol << 25) | (frequency << 12) | (slot - cumulative), or ~0u for an unused slot
+  uint32_t* slot_tab = dyn32;
+  int32_t* newpos = reinterpret_cast<int32_t*>(dyn32 + kM);      // [kDecMax] ranks of new leading bits
+  uint8_t* rbytes = reinterpret_cast<uint8_t*>(newpos + kDecMax);  // [kDecBytes] this plane's rANS bytes
+  __shared__ int s_nnew;
   const int64_t b = blockIdx.x;
   const int tid = threadIdx.x;
   const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
@@ -892,14 +896,18 @@ __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) 
     const bool staged = s_err == 0 && n_insig > 0 && s_rl <= (uint32_t)kDecBytes;
     if (s_err == 0 && n_insig > 0) {
       for (int sl = tid; sl < (int)kM; sl += kDecThreads) {
-        uint8_t sb = 0xff;
+        uint32_t e = ~0u;
         for (int i = 0; i < kNsym; ++i)
-          if (f[i] && (uint32_t)sl >= cum[i] && (uint32_t)sl < cum[i] + f[i]) { sb = (uint8_t)i; break; }
-        sym_of[sl] = sb;
+          if (f[i] && (uint32_t)sl >= cum[i] && (uint32_t)sl < cum[i] + f[i]) {
+            e = ((uint32_t)i << 25) | (f[i] << 12) | ((uint32_t)sl - cum[i]);
+            break;
+          }
+        slot_tab[sl] = e;
       }
       if (staged)
         for (uint32_t i = tid; i < s_rl; i += kDecThreads) rbytes[i] = __ldg(D.sec + pos + i);
     }
+    if (tid == 0) s_nnew = 0;
     __syncthreads();
     // 2. run-length symbols of this plane: one thread
     if (tid == 0 && s_err == 0 && n_insig > 0) {
@@ -910,31 +918,250 @@ __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) 
       uint32_t x = 0;
       if (s_err == 0) { x = rd32(rp); rp += 4; }
       int64_t q = 0;
-      while (s_err == 0 && q < n_insig) {
-        const uint32_t slot = x & (kM - 1);
-        const int sb = (sym_of[slot] == 0xff) ? -1 : (int)sym_of[slot];
-        if (sb < 0) { s_err = 6; break; }
-        x = f[sb] * (x >> kScaleBits) + slot - cum[sb];
-        while (x < kRansL) { if (rp >= rend) { s_err = 7; break; } x = (x << 8) | *rp++; }
-        if (s_err) break;
+      int nnew = 0;
+      int err = s_err;
+      // the next stream bytes wait in a register queue (low byte first), refilled
+      // ahead of use so that renormalisation does not wait on memory
+      uint64_t bq = 0;
+      int bn = 0;
+      while (err == 0 && q < n_insig) {
+        while (bn <= 4 && rp < rend) { bq |= (uint64_t)(*rp++) << (8 * bn); ++bn; }
+        const uint32_t e = slot_tab[x & (kM - 1)];
+        if (e == ~0u) { err = 6; break; }
+        const int sb = (int)(e >> 25);
+        x = ((e >> 12) & 0x1fffu) * (x >> kScaleBits) + (e & 0xfffu);
+        while (x < kRansL) {
+          if (bn == 0) { err = 7; break; }
+          x = (x << 8) | (uint32_t)(bq & 0xffu);
+          bq >>= 8;
+          --bn;
+        }
+        if (err) break;
         uint32_t extra = 0;
         if (sb > 0) {
           extra = x & ((1u << sb) - 1u);
           x >>= sb;
-          while (x < kRansL) { if (rp >= rend) { s_err = 8; break; } x = (x << 8) | *rp++; }
-          if (s_err) break;
+          while (x < kRansL) {
+            if (bn == 0) { err = 8; break; }
+            x = (x << 8) | (uint32_t)(bq & 0xffu);
+            bq >>= 8;
+            --bn;
+          }
+          if (err) break;
         }
         q += (int64_t)((1u << sb) - 1u + extra);
         if (q < n_insig) {
-          newbm[q >> 5] |= 1u << (q & 31);
+          newpos[nnew++] = (int32_t)q;
           ++q;
         }
       }
+      s_err = err;
+      s_nnew = nnew;
+    }
+    __syncthreads();
+    for (int k = tid; k < s_nnew; k += kDecThreads) {
+      const int32_t qq = newpos[k];
+      atomicOr(&newbm[qq >> 5], 1u << (qq & 31));
     }
     __syncthreads();
     if (s_err) break;
     // 3. raw bits: one per significant coefficient (a trailing bit) and one per
     //    new significant coefficient (its sign), in coefficient order
+    uint32_t newm = 0;
+    {
+      int64_t r = rank0;
+      for (int u = 0; u < kDecPer; ++u)
+        if ((actm >> u & 1u) && !(sigm >> u & 1u)) {
+          if (newbm[r >> 5] >> (r & 31) & 1u) newm |= 1u << u;
+          ++r;
+        }
+    }
+    const uint32_t consm = sigm | newm;
+    int64_t ncons = 0;
+    const int64_t rb0 = dec_scan(__popc(consm), scan_sh, &ncons);
+    const uint64_t rcap = (uint64_t)s_wl * 8;
+    if ((uint64_t)ncons > rcap) {
+      if (tid == 0) s_err = 4;
+    } else {
+      const uint8_t* raw = D.sec + pos + s_rl;
+      int64_t rbit = rb0;
+      for (int u = 0; u < kDecPer; ++u) {
+        if (!(consm >> u & 1u)) continue;
+        const uint32_t bit = (__ldg(raw + (rbit >> 3)) >> (rbit & 7)) & 1u;
+        ++rbit;
+        const int64_t jj = j0 + u - lo;
+        if (sigm >> u & 1u) qs[jj] |= (unsigned long long)bit << p;
+        else { qs[jj] |= 1ull << p; ss[jj] = (uint8_t)bit; }
+      }
+    }
+    pos += s_rl + s_wl;
+    __syncthreads();
+    if (s_err) break;
+  }
+  if (s_err) {
+    if (tid == 0 && s_err > 0) atomicExch(D.err, s_err);
+    return;
+  }
+  for (int u = 0; u < kDecPer; ++u) {
+    const int64_t j = j0 + u;
+    if (j >= hi_all) break;
+    const uint64_t a = qs[j - lo];
+    if (a == 0) { D.out[j] = 0.0; continue; }
+    const int pj = (j <= D.i_star) ? D.p_star : D.p_star + 1;
+    const uint64_t v = a + ((pj >= 1) ? (1ull << (pj - 1)) : 0ull);
+    const double m = mul_pow2(__ull2double_rn(v), -D.k);
+    D.out[j] = ss[j - lo] ? -m : m;
+  }
+}
+
+// Two-phase decoder.  The run-length symbols of a (block, plane) chunk do not
+// depend on any other chunk - only their placement does - and a rANS decoder
+// ends exactly in the encoder's initial state kRansL with every byte used.
+// Phase A (decode_runs_kernel) therefore decodes every chunk's runs in
+// parallel, one thread per chunk, until that end state; a plane whose table
+// holds a single bucket of probability one with no extra bits carries no
+// information and is marked implicit (every remaining run is 0).  Phase B
+// (decode_place_kernel, one CTA per block, planes in order) turns the runs
+// into positions with a block scan and places the leading and raw bits.
+constexpr int kRunsImplicit = -1;
+
+struct RunParams {
+  const uint8_t* sec;
+  int64_t nbytes, tab;
+  int nplanes;
+  int64_t nblocks;
+  int block_size;
+  const uint64_t* boff;
+  uint32_t* runs;  // [chunk][block_size + 2]
+  int* nruns;      // [chunk]
+  int* err;
+};
+
+__global__ void decode_runs_kernel(RunParams P) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= P.nblocks * P.nplanes) return;
+  const int64_t b = c / P.nplanes;
+  const int pi = (int)(c % P.nplanes);
+  const int cap = P.block_size + 2;
+  // byte offset of this chunk: the block's payload start plus its earlier planes
+  uint64_t pos = P.boff[b];
+  for (int q = 0; q < pi; ++q) {
+    const uint8_t* t = P.sec + P.tab + (b * P.nplanes + q) * 8;
+    pos += (uint64_t)rd32(t) + rd32(t + 4);
+  }
+  const uint8_t* t = P.sec + P.tab + (b * P.nplanes + pi) * 8;
+  const uint32_t rl = rd32(t), wl = rd32(t + 4);
+  int* nr = P.nruns + c;
+  if (pos + rl + wl > (uint64_t)P.nbytes) { atomicExch(P.err, 2); *nr = 0; return; }
+  if (rl == 0) { *nr = 0; return; }
+  if (rl < 4) { atomicExch(P.err, 3); *nr = 0; return; }
+  const uint8_t* ftab = P.sec + 48 + 2 * pi * kNsym;
+  uint32_t f[kNsym], cum[kNsym];
+  uint32_t ca = 0;
+  int single = -1;
+#pragma unroll
+  for (int i = 0; i < kNsym; ++i) {
+    f[i] = (uint32_t)ftab[2 * i] | ((uint32_t)ftab[2 * i + 1] << 8);
+    cum[i] = ca;
+    ca += f[i];
+    if (f[i] == kM) single = i;
+  }
+  if (single == 0) { *nr = kRunsImplicit; return; }
+  const uint8_t* rp = P.sec + pos;
+  const uint8_t* rend = rp + rl;
+  uint32_t x = rd32(rp);
+  rp += 4;
+  uint32_t* out = P.runs + c * (int64_t)cap;
+  int k = 0;
+  while (!(x == kRansL && rp == rend)) {
+    const uint32_t slot = x & (kM - 1);
+    uint32_t fs = 0, cs = 0;
+    int sb = -1;
+#pragma unroll
+    for (int i = 0; i < kNsym; ++i)
+      if (f[i] && slot >= cum[i] && slot < cum[i] + f[i]) { fs = f[i]; cs = cum[i]; sb = i; }
+    if (sb < 0) { atomicExch(P.err, 6); break; }
+    x = fs * (x >> kScaleBits) + slot - cs;
+    bool bad = false;
+    while (x < kRansL) { if (rp >= rend) { bad = true; break; } x = (x << 8) | *rp++; }
+    if (bad) { atomicExch(P.err, 7); break; }
+    uint32_t extra = 0;
+    if (sb > 0) {
+      extra = x & ((1u << sb) - 1u);
+      x >>= sb;
+      while (x < kRansL) { if (rp >= rend) { bad = true; break; } x = (x << 8) | *rp++; }
+      if (bad) { atomicExch(P.err, 8); break; }
+    }
+    if (k >= cap) { atomicExch(P.err, 10); break; }
+    out[k++] = (1u << sb) - 1u + extra;
+  }
+  *nr = k;
+}
+
+__global__ void __launch_bounds__(kDecThreads) decode_place_kernel(DecParams D, const uint32_t* __restrict__ runs,
+                                                                   const int* __restrict__ nruns) {
+  __shared__ unsigned long long qs[kDecMax];
+  __shared__ uint8_t ss[kDecMax];
+  __shared__ uint32_t newbm[kDecMax / 32];
+  __shared__ int64_t scan_sh[24];
+  __shared__ int s_err;
+  __shared__ uint32_t s_rl, s_wl;
+  constexpr int kRunPer = (kDecMax + 2 + kDecThreads - 1) / kDecThreads;  // runs per thread (17)
+  const int64_t b = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
+  const int cap = D.block_size + 2;
+  for (int i = tid; i < kDecMax; i += kDecThreads) { qs[i] = 0; ss[i] = 0; }
+  if (tid == 0) s_err = (*D.err != 0) ? -1 : 0;
+  __syncthreads();
+  if (s_err) return;
+  uint64_t pos = D.boff[b];
+  const int64_t j0 = lo + (int64_t)tid * kDecPer;
+  for (int pi = 0; pi < D.nplanes; ++pi) {
+    const int p = 63 - pi;
+    int64_t hi = hi_all;
+    if (p == D.p_star && hi > D.i_star + 1) hi = max(lo, D.i_star + 1);
+    for (int i = tid; i < kDecMax / 32; i += kDecThreads) newbm[i] = 0u;
+    if (tid == 0) {
+      const uint8_t* t = D.sec + D.tab + (b * D.nplanes + pi) * 8;
+      s_rl = rd32(t);
+      s_wl = rd32(t + 4);
+    }
+    uint32_t sigm = 0, actm = 0;
+    for (int u = 0; u < kDecPer; ++u) {
+      const int64_t j = j0 + u;
+      if (j < hi) {
+        actm |= 1u << u;
+        if (qs[j - lo] != 0) sigm |= 1u << u;
+      }
+    }
+    int64_t n_insig = 0;
+    const int64_t rank0 = dec_scan(__popc(actm & ~sigm), scan_sh, &n_insig);  // (barriers inside)
+    // runs -> ranks of the new leading bits
+    const int64_t chunk = b * D.nplanes + pi;
+    const int nr = nruns[chunk];
+    if (nr == kRunsImplicit) {
+      for (int64_t r = tid; r < n_insig; r += kDecThreads) atomicOr(&newbm[r >> 5], 1u << (r & 31));
+    } else {
+      const uint32_t* rr = runs + chunk * (int64_t)cap;
+      const int k0 = tid * kRunPer;
+      int64_t loc = 0;
+      for (int u = 0; u < kRunPer; ++u)
+        if (k0 + u < nr) loc += (int64_t)rr[k0 + u] + 1;
+      int64_t total = 0;
+      int64_t q = dec_scan(loc, scan_sh, &total);
+      for (int u = 0; u < kRunPer; ++u) {
+        const int k = k0 + u;
+        if (k >= nr) break;
+        const int64_t at = q + rr[k];  // rank of this run's 1
+        if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rr[k] + 1)) s_err = 11;  // symbol count
+        if (at < n_insig) atomicOr(&newbm[at >> 5], 1u << (at & 31));
+        q += (int64_t)rr[k] + 1;
+      }
+      if (tid == 0 && nr == 0 && n_insig > 0) s_err = 5;
+    }
+    __syncthreads();
+    if (s_err) break;
     uint32_t newm = 0;
     {
       int64_t r = rank0;
@@ -1184,14 +1411,32 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
   D.sec = dsec; D.qt = qt; D.sg = sg; D.out = core; D.err = err; D.boff = boff;
   block_offsets_kernel<<<1, 32, 0, s>>>(D, boff);
   ATC_LAUNCHED(1);
-  static bool dec_attr = false;
-  if (!dec_attr) {
-    ATC_CUDA_TRY(cudaFuncSetAttribute(decode_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kM + kDecBytes));
-    dec_attr = true;
+  if (D.block_size <= kDecMax && D.nplanes > 0) {
+    // phase A: every (block, plane) chunk's runs in parallel; phase B: placement
+    RunParams RP;
+    RP.sec = dsec; RP.nbytes = D.nbytes; RP.tab = D.tab; RP.nplanes = D.nplanes; RP.nblocks = D.nblocks;
+    RP.block_size = D.block_size; RP.boff = boff; RP.err = err;
+    const int64_t nchunk = D.nblocks * D.nplanes;
+    uint8_t* rbuf = nullptr;
+    ATC_TRY(Scratch::get(SLOT_DEC_RUNS, sizeof(uint32_t) * (size_t)nchunk * (D.block_size + 2) +
+                                            sizeof(int) * (size_t)nchunk + 256, (void**)&rbuf));
+    RP.runs = reinterpret_cast<uint32_t*>(rbuf);
+    RP.nruns = reinterpret_cast<int*>(rbuf + sizeof(uint32_t) * (size_t)nchunk * (D.block_size + 2));
+    decode_runs_kernel<<<(unsigned)((nchunk + 63) / 64), 64, 0, s>>>(RP);
+    decode_place_kernel<<<(unsigned)D.nblocks, kDecThreads, 0, s>>>(D, RP.runs, RP.nruns);
+    ATC_LAUNCHED(2);
+  } else if (D.block_size <= kDecMax) {
+    static bool dec_attr = false;
+    if (!dec_attr) {
+      ATC_CUDA_TRY(cudaFuncSetAttribute(decode_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecDyn));
+      dec_attr = true;
+    }
+    decode_block_kernel<<<(unsigned)D.nblocks, kDecThreads, kDecDyn, s>>>(D);
+    ATC_LAUNCHED(1);
+  } else {
+    decode_kernel<<<(unsigned)((D.nblocks + 63) / 64), 64, 0, s>>>(D);
+    ATC_LAUNCHED(1);
   }
-  if (D.block_size <= kDecMax) decode_block_kernel<<<(unsigned)D.nblocks, kDecThreads, kM + kDecBytes, s>>>(D);
-  else decode_kernel<<<(unsigned)((D.nblocks + 63) / 64), 64, 0, s>>>(D);
-  ATC_LAUNCHED(1);
   int herr = 0;
   ATC_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   ATC_CUDA_TRY(cudaStreamSynchronize(s));
