@@ -329,7 +329,7 @@ def run_ours(args, world, rank, local):
              "ms_per_step": ms, "peak_source": peak_src + " (sustained bf16 for the tensor view)"}
         return d
 
-    roof_gram = roof_of("gram phase", "absmax_kernel, gram_tc_kernel, gram_tc_assemble", phases["ms_gram"],
+    roof_gram = roof_of("gram phase", "absmax_kernel, slice_planes_kernel, gram_tma_kernel, gram_tc_assemble", phases["ms_gram"],
                         gram_bytes, gram_tflops_issued)
     roof_ttm = roof_of("projection + certification phase", "ttm_prep_b, ttm_tc_kernel (projection and residual), "
                        "row_energy, compact, eigenvectors", phases["ms_ttm"], ttm_bytes, ttm_tflops_issued)

@@ -74,6 +74,7 @@ enum ScratchSlot {
   SLOT_TEN_C,          // third tensor buffer (compaction target)
   SLOT_CAND,           // candidate factor of the residual-certified rank choice
   SLOT_DEC_RUNS,       // decoded run lengths per (block, plane)
+  SLOT_SLICES,         // integer slice planes of the Gram input
   SLOT_COUNT
 };
 

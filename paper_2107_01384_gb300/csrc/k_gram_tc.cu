@@ -34,6 +34,7 @@
 // Every wait is bounded (2 s); on time-out the CTA raises an error flag, waits
 // for its own MMAs, frees its TMEM and returns.
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "atc_internal.cuh"
 #include "tc_common.cuh"
@@ -362,6 +363,259 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a) {
   if (tid == 0 && abort_flag) atomicExch(a.err, 1);
 }
 
+// ------------------------------------------------ pre-sliced, TMA-fed variant
+// The slices are formed once per mode by slice_planes_kernel (an HBM-bound
+// pass) into three 16-bit planes in the unfolded (n, Kp) layout, Kp = K rounded
+// up to 64 with zero padding; the Gram CTAs then pull 128 x 64 (A rows) and
+// 64 x 64 (B rows) tiles of every plane with TMA (128-byte swizzle, the smem
+// image the MMA descriptors expect), so no warp re-slices a row block per
+// tile.  Warp 0 issues the copies, warp 1 the MMAs (the same nine products
+// into five orders), warps 2-5 flush each exact window into a double-float
+// running sum kept in their registers.
+constexpr int kTmaThreads = 192;
+constexpr int TNS = 3;                      // pipeline stages
+constexpr int T_STAGE = 3 * SLOT_A + 3 * SLOT_B;
+
+struct GramTmaArgs {
+  int64_t kchunk;  // multiple of KT
+  int64_t Kp;
+  int nsplit, nc64, npair;
+  double* part;
+  int* err;
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+    gram_tma_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                    const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
+                    const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
+                    GramTmaArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full_bar[TNS], empty_bar[TNS], accf_bar, acce_bar, done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  volatile int* abort = &abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int pair = blockIdx.x / a.nsplit, split = blockIdx.x % a.nsplit;
+  int ti, cj;
+  tile_of(pair, a.nc64, ti, cj);
+  const int64_t kb = (int64_t)split * a.kchunk;
+  const int64_t ke = min(a.Kp, kb + a.kchunk);
+  const int ntiles = (ke > kb) ? (int)((ke - kb) / KT) : 0;
+  const int ngroups = (ntiles + FLUSH - 1) / FLUSH;
+  if (tid == 0) {
+    for (int s = 0; s < TNS; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&accf_bar, 1);
+    mbar_init(&acce_bar, 128);
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int t = 0; t < ntiles; ++t) {
+        const int s = t % TNS;
+        if (!mbar_wait(&empty_bar[s], ((uint32_t)(t / TNS) & 1u) ^ 1u, abort)) break;
+        uint8_t* st = smem + s * T_STAGE;
+        mbar_arrive_expect_tx(&full_bar[s], (uint32_t)T_STAGE);
+        const int k0 = (int)(kb + (int64_t)t * KT);
+        tma_load_2d(st, &mA0, &full_bar[s], k0, ti * TM);
+        tma_load_2d(st + SLOT_A, &mA1, &full_bar[s], k0, ti * TM);
+        tma_load_2d(st + 2 * SLOT_A, &mA2, &full_bar[s], k0, ti * TM);
+        tma_load_2d(st + 3 * SLOT_A, &mB0, &full_bar[s], k0, cj * TN);
+        tma_load_2d(st + 3 * SLOT_A + SLOT_B, &mB1, &full_bar[s], k0, cj * TN);
+        tma_load_2d(st + 3 * SLOT_A + 2 * SLOT_B, &mB2, &full_bar[s], k0, cj * TN);
+        issued = t + 1;
+      }
+      // every issued copy must land before the CTA may exit
+      for (int t = (issued > TNS ? issued - TNS : 0); t < issued; ++t)
+        mbar_wait_drain(&full_bar[t % TNS], (uint32_t)(t / TNS) & 1u);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16(BF16 ? 1 : 0, TM, TN);
+      bool ok = true;
+      for (int g = 0; g < ngroups && ok; ++g) {
+        if (!mbar_wait(&acce_bar, ((uint32_t)g & 1u) ^ 1u, abort)) break;
+        tc_fence_after();
+        const int t1 = min(ntiles, (g + 1) * FLUSH);
+        for (int t = g * FLUSH; t < t1; ++t) {
+          const int s = t % TNS;
+          if (!mbar_wait(&full_bar[s], (uint32_t)(t / TNS) & 1u, abort)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * T_STAGE), sb = sa + 3 * SLOT_A;
+#pragma unroll
+          for (int j = 0; j < KT / 16; ++j) {
+            const uint32_t acc = (t == g * FLUSH && j == 0) ? 0u : 1u;
+            const uint32_t o = 32u * j;
+            const uint64_t A0 = desc_k128(sa + o), A1 = desc_k128(sa + SLOT_A + o), A2 = desc_k128(sa + 2 * SLOT_A + o);
+            const uint64_t B0 = desc_k128(sb + o), B1 = desc_k128(sb + SLOT_B + o), B2 = desc_k128(sb + 2 * SLOT_B + o);
+            umma_f16(tmem + 0u, A0, B0, idesc, acc);
+            umma_f16(tmem + 64u, A0, B1, idesc, acc);
+            umma_f16(tmem + 64u, A1, B0, idesc, 1u);
+            umma_f16(tmem + 128u, A0, B2, idesc, acc);
+            umma_f16(tmem + 128u, A1, B1, idesc, 1u);
+            umma_f16(tmem + 128u, A2, B0, idesc, 1u);
+            umma_f16(tmem + 192u, A1, B2, idesc, acc);
+            umma_f16(tmem + 192u, A2, B1, idesc, 1u);
+            umma_f16(tmem + 256u, A2, B2, idesc, acc);
+          }
+          umma_commit(&empty_bar[s]);
+        }
+        if (ok) umma_commit(&accf_bar);
+      }
+      umma_commit(&done_bar);
+      mbar_wait_drain(&done_bar, 0);
+    }
+  } else {
+    // --------------------------------- flush into registers and epilogue
+    const int w = warp & 3;  // TMEM lane quarter of this warp
+    const uint32_t tl = tmem + ((uint32_t)(32 * w) << 16);
+    float hi[TN], lo[TN];
+#pragma unroll
+    for (int c = 0; c < TN; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+    bool ok = true;
+    for (int g = 0; g < ngroups; ++g) {
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(&accf_bar, (uint32_t)g & 1u, abort) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      __syncwarp();
+      if (!okw) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int c0 = 0; c0 < TN; c0 += 16) {
+        uint32_t r0[16], r1[16], r2[16], r3[16], r4[16];
+        tmem_ld16(tl + c0, r0);
+        tmem_ld16(tl + 64u + c0, r1);
+        tmem_ld16(tl + 128u + c0, r2);
+        tmem_ld16(tl + 192u + c0, r3);
+        tmem_ld16(tl + 256u + c0, r4);
+        tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          float sv, tv, s1, e1;
+          combine_orders(__uint_as_float(r0[e]), __uint_as_float(r1[e]), __uint_as_float(r2[e]),
+                         __uint_as_float(r3[e]), __uint_as_float(r4[e]), sv, tv);
+          two_sum(hi[c0 + e], sv, s1, e1);
+          e1 += lo[c0 + e] + tv;
+          const float h2 = s1 + e1;
+          lo[c0 + e] = e1 - (h2 - s1);
+          hi[c0 + e] = h2;
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acce_bar);
+    }
+    ok = ok && !abort_flag;
+    double* out = a.part + ((int64_t)split * a.npair + pair) * (TM * TN);
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      const double v = (double)hi[c] + (double)lo[c];
+      out[(int64_t)c * TM + 32 * w + lane] = ok ? v : 0.0;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+  if (tid == 0 && abort_flag) atomicExch(a.err, 1);
+}
+
+// Slices of the (L, n, R) tensor into three 16-bit planes laid out (n, Kp):
+// plane[i][k] for k = l R + r (zero for k >= K).  For R = 1 the reads along k
+// are strided by n, so that case goes through a 32 x 32 shared-memory transpose.
+template <typename T, bool BF16>
+__global__ void slice_planes_kernel(const T* __restrict__ x, int64_t n, int64_t R, int64_t K, int64_t Kp,
+                                    const SliceScale* __restrict__ xs, uint16_t* __restrict__ p0,
+                                    uint16_t* __restrict__ p1, uint16_t* __restrict__ p2) {
+  const float sc = ldexpf(1.0f, xs->shift);
+  const int64_t total = n * Kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / Kp, k = idx - i * Kp;
+    float v = 0.f;
+    if (k < K) {
+      const int64_t l = k / R, r = k - l * R;
+      v = (float)__ldg(x + (l * n + i) * R + r) * sc;
+    }
+    float a0, a1, a2;
+    slice3i(v, a0, a1, a2);
+    p0[idx] = Pack<BF16>::one(a0);
+    p1[idx] = Pack<BF16>::one(a1);
+    p2[idx] = Pack<BF16>::one(a2);
+  }
+}
+template <typename T, bool BF16>
+__global__ void slice_planes_t_kernel(const T* __restrict__ x, int64_t n, int64_t K, int64_t Kp,
+                                      const SliceScale* __restrict__ xs, uint16_t* __restrict__ p0,
+                                      uint16_t* __restrict__ p1, uint16_t* __restrict__ p2) {
+  // R == 1: x[k][i] (k = l), tile of 32 k x 32 i through shared memory
+  __shared__ float tile[32][33];
+  const float sc = ldexpf(1.0f, xs->shift);
+  const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t k = k0 + yy, i = i0 + threadIdx.x;
+    tile[yy][threadIdx.x] = (k < K && i < n) ? (float)__ldg(x + k * n + i) * sc : 0.f;
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t i = i0 + yy, k = k0 + threadIdx.x;
+    if (i < n && k < Kp) {
+      float a0, a1, a2;
+      slice3i(tile[threadIdx.x][yy], a0, a1, a2);
+      const int64_t idx = i * Kp + k;
+      p0[idx] = Pack<BF16>::one(a0);
+      p1[idx] = Pack<BF16>::one(a1);
+      p2[idx] = Pack<BF16>::one(a2);
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2D map over a (rows, Kp) plane of 16-bit values, box (64 k, box_rows rows), 128-byte swizzle
+int make_map(CUtensorMap* m, void* base, int64_t rows, int64_t Kp, int box_rows, bool bf16) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(ATC_EUNSUP, "cuTensorMapEncodeTiled unavailable");
+  const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ATC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return ATC_OK;
+}
+
 // G[i][j] from the split partials, summed in FP64 in split order and scaled
 // by 2^(-2 shift); (i, j) is read from the tile of (min, max), which covers it.
 __global__ void gram_tc_assemble(const double* __restrict__ part, int nsplit, int npair, int nc64, int64_t n,
@@ -420,6 +674,16 @@ int launch_t(const GramArgs& a, int grid, cudaStream_t s) {
 int g_nsm = 0;
 int g_scale_rot = 0;
 
+// ATC_GRAM_CONVERT=1 selects the converter-warp kernel (the TMA-fed one is the default)
+bool gram_tma_off() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("ATC_GRAM_CONVERT");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
 }  // namespace
 
 // layout of the SLOT_TC_ERR scratch: error word at byte 0, slice scales from byte 64
@@ -466,6 +730,76 @@ int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R,
   int nsplit = (int)((ktiles + tpc - 1) / tpc);
   if (nsplit < 1) nsplit = 1;
   if (!xs) ATC_TRY(slice_scale(x, dtype, K * n, s, &xs));
+  const bool bf16 = (precision == ATC_PREC_SPLIT_BF16);
+  if (encode_fn() && !gram_tma_off()) {
+    // pre-sliced planes + TMA-fed tensor-core Gram
+    const int64_t Kp = ktiles * KT;
+    uint16_t* planes = nullptr;
+    ATC_TRY(Scratch::get(SLOT_SLICES, (size_t)3 * n * Kp * 2 + 1024, (void**)&planes));
+    uint16_t* p0 = planes;
+    uint16_t* p1 = planes + n * Kp;
+    uint16_t* p2 = planes + 2 * n * Kp;
+    if (R == 1) {
+      const dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)((n + 31) / 32));
+      const dim3 blk(32, 8);
+      if (dtype == ATC_F32)
+        bf16 ? slice_planes_t_kernel<float, true><<<grid, blk, 0, s>>>((const float*)x, n, K, Kp, xs, p0, p1, p2)
+             : slice_planes_t_kernel<float, false><<<grid, blk, 0, s>>>((const float*)x, n, K, Kp, xs, p0, p1, p2);
+      else
+        bf16 ? slice_planes_t_kernel<double, true><<<grid, blk, 0, s>>>((const double*)x, n, K, Kp, xs, p0, p1, p2)
+             : slice_planes_t_kernel<double, false><<<grid, blk, 0, s>>>((const double*)x, n, K, Kp, xs, p0, p1, p2);
+    } else {
+      const int64_t tot = n * Kp;
+      const int blocks = (int)((tot + 255) / 256 < 4 * 1216 ? (tot + 255) / 256 : 4 * 1216);
+      if (dtype == ATC_F32)
+        bf16 ? slice_planes_kernel<float, true><<<blocks, 256, 0, s>>>((const float*)x, n, R, K, Kp, xs, p0, p1, p2)
+             : slice_planes_kernel<float, false><<<blocks, 256, 0, s>>>((const float*)x, n, R, K, Kp, xs, p0, p1, p2);
+      else
+        bf16 ? slice_planes_kernel<double, true><<<blocks, 256, 0, s>>>((const double*)x, n, R, K, Kp, xs, p0, p1, p2)
+             : slice_planes_kernel<double, false><<<blocks, 256, 0, s>>>((const double*)x, n, R, K, Kp, xs, p0, p1, p2);
+    }
+    ATC_LAUNCHED(1);
+    CUtensorMap mA[3], mB[3];
+    uint16_t* pl[3] = {p0, p1, p2};
+    for (int q = 0; q < 3; ++q) {
+      ATC_TRY(make_map(&mA[q], pl[q], n, Kp, TM, bf16));
+      ATC_TRY(make_map(&mB[q], pl[q], n, Kp, TN, bf16));
+    }
+    GramTmaArgs ta;
+    ta.kchunk = tpc * KT;
+    ta.Kp = Kp;
+    ta.nsplit = nsplit;
+    ta.nc64 = nc64;
+    ta.npair = npair;
+    const size_t part_elems = (size_t)nsplit * npair * TM * TN;
+    ATC_TRY(Scratch::get(SLOT_GRAM_PART, part_elems * 8 + 1024, (void**)&ta.part));
+    int* err = nullptr;
+    ATC_TRY(tc_error_flag(&err));
+    ta.err = err;
+    const int smem = TNS * T_STAGE + 1024;
+    const int grid = npair * nsplit;
+    if (bf16) {
+      static bool attr = false;
+      if (!attr) {
+        ATC_CUDA_TRY(cudaFuncSetAttribute(gram_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+      }
+      gram_tma_kernel<true><<<grid, kTmaThreads, smem, s>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], ta);
+    } else {
+      static bool attr = false;
+      if (!attr) {
+        ATC_CUDA_TRY(cudaFuncSetAttribute(gram_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+      }
+      gram_tma_kernel<false><<<grid, kTmaThreads, smem, s>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], ta);
+    }
+    ATC_LAUNCHED(1);
+    const int64_t tot = n * n;
+    const int rb = (int)((tot + 255) / 256 < 2048 ? (tot + 255) / 256 : 2048);
+    gram_tc_assemble<<<rb, 256, 0, s>>>(ta.part, nsplit, npair, nc64, n, xs, g);
+    ATC_LAUNCHED(1);
+    return ATC_OK;
+  }
   GramArgs a;
   a.x = x;
   a.n = n;
@@ -483,7 +817,6 @@ int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R,
   int* err = nullptr;
   ATC_TRY(tc_error_flag(&err));
   a.err = err;
-  const bool bf16 = (precision == ATC_PREC_SPLIT_BF16);
   const int grid = npair * nsplit;
   if (dtype == ATC_F32) {
     if (bf16) ATC_TRY((launch_t<float, true>(a, grid, s)));
