@@ -134,6 +134,33 @@ int atc_decompress(const uint8_t* stream, size_t nbytes, void* out_dev, int out_
  */
 int atc_decompress_ex(const uint8_t* stream, size_t nbytes, void* out_dev, int out_dtype, const atc_options* opt);
 
+/*
+ * Tucker expansion X_hat = G x_1 U_1 ... x_d U_d (the reconstruction of
+ * Section 4.1.1 / 4.3, Algorithm 1's model) from DEVICE data, and its adjoint.
+ *   core_dev   G, row-major (r_1..r_d), ATC_F32 or ATC_F64
+ *   factors_dev[k]  U_k, n_k x r_k row-major FP64 (any matrices; orthonormality not assumed)
+ *   dims       n_1..n_d (1 <= d <= 8, r_k <= n_k)
+ *   out_dev    X_hat, row-major (n_1..n_d), out_dtype
+ * opt->precision: ATC_PREC_FP64 (FP64 SIMT products) or a split precision
+ * (tensor-core products with the exact slices, FP32 intermediates); opt->stream.
+ * Errors: ATC_EINVAL, ATC_ENOMEM, ATC_ECUDA.
+ */
+int atc_tucker_expand(const void* core_dev, int core_dtype, const int64_t* ranks, int ndim,
+                      const double* const* factors_dev, const int64_t* dims, void* out_dev, int out_dtype,
+                      const atc_options* opt);
+
+/*
+ * Adjoint of atc_tucker_expand for a cotangent dY = dL/dX_hat (device, (n_1..n_d), F32/F64):
+ *   dcore_dev     dL/dG = dY x_1 U_1^T ... x_d U_d^T          (r_1..r_d, FP64; may be NULL)
+ *   dfactors_dev[k]  dL/dU_k = dY_(k) (G x_{j!=k} U_j)_(k)^T   (n_k x r_k, FP64; array or entries may be NULL)
+ * The per-mode intermediates G x_{j!=k} U_j are recomputed for every k, never
+ * stored together.  The paper has no adjoint; this extends its reconstruction.
+ * Errors: as atc_tucker_expand.
+ */
+int atc_tucker_expand_adjoint(const void* dy_dev, int dy_dtype, const void* core_dev, int core_dtype,
+                              const int64_t* ranks, int ndim, const double* const* factors_dev, const int64_t* dims,
+                              double* dcore_dev, double* const* dfactors_dev, const atc_options* opt);
+
 /* ------------------------------------------------------------------------
  * Step entry points: one per stage of the hot path, for parity tests and
  * for callers that drive the loop themselves.  All sizes are element counts.

@@ -20,7 +20,8 @@ __all__ = [
     "RANK_STATIC", "RANK_ADAPTIVE", "AtcError", "lib", "lib_path",
     "atc_norm2", "atc_gram", "atc_gram_fp64_noalloc", "atc_eig_sym", "atc_rank_select", "atc_ttm",
     "atc_quantize_core", "atc_dequantize_core", "atc_compress", "atc_decompress",
-    "atc_peek_dims", "Compressed", "EXPORTS",
+    "atc_peek_dims", "Compressed", "EXPORTS", "atc_tucker_expand", "atc_tucker_expand_adjoint",
+    "TuckerExpand", "tucker_expand",
 ]
 
 ATC_F32, ATC_F64 = 1, 2
@@ -34,7 +35,7 @@ lib_path = os.path.join(HERE, "libatc.so")
 EXPORTS = [
     "atc_default_options", "atc_compress", "atc_get_ranks", "atc_get_core", "atc_get_factor",
     "atc_get_stream", "atc_get_stats", "atc_free", "atc_peek_dims", "atc_decompress", "atc_decompress_ex",
-    "atc_norm2",
+    "atc_tucker_expand", "atc_tucker_expand_adjoint", "atc_norm2",
     "atc_gram", "atc_eig_sym", "atc_rank_select", "atc_ttm", "atc_quantize_core",
     "atc_dequantize_core", "atc_free_buffer", "atc_release_workspace", "atc_last_error",
     "atc_kernel_launches", "atc_gram_fp64_noalloc",
@@ -86,6 +87,10 @@ def lib():
         L.atc_peek_dims.argtypes = [C.c_char_p, C.c_size_t, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
         L.atc_decompress.argtypes = [C.c_char_p, C.c_size_t, vp, i32, vp]
         L.atc_decompress_ex.argtypes = [C.c_char_p, C.c_size_t, vp, i32, C.POINTER(Options)]
+        L.atc_tucker_expand.argtypes = [vp, i32, C.POINTER(i64), i32, C.POINTER(vp), C.POINTER(i64), vp, i32,
+                                        C.POINTER(Options)]
+        L.atc_tucker_expand_adjoint.argtypes = [vp, i32, vp, i32, C.POINTER(i64), i32, C.POINTER(vp), C.POINTER(i64),
+                                                vp, C.POINTER(vp), C.POINTER(Options)]
         L.atc_norm2.argtypes = [vp, i64, i32, vp, vp]
         L.atc_gram.argtypes = [vp, i32, i64, i64, i64, i32, vp, vp]
         L.atc_eig_sym.argtypes = [vp, i32, vp, vp, i32, vp]
@@ -280,3 +285,69 @@ def atc_decompress(stream_bytes: bytes, out_dtype=torch.float64, device="cuda", 
         opt.stream = _stream(stream)
         _check(lib().atc_decompress_ex(stream_bytes, len(stream_bytes), _dev(out), _dt(out), C.byref(opt)))
     return out
+
+
+def _opts(precision, stream):
+    opt = Options()
+    lib().atc_default_options(C.byref(opt))
+    opt.precision = precision
+    opt.stream = _stream(stream)
+    return opt
+
+
+def atc_tucker_expand(core: torch.Tensor, factors, out_dtype=None, precision: int = PREC_FP64,
+                      stream=None) -> torch.Tensor:
+    """X_hat = G x_1 U_1 ... x_d U_d on the GPU (factors n_k x r_k, any dtype; used as FP64)."""
+    d = core.dim()
+    us = [f.to(torch.float64).contiguous() for f in factors]
+    dims = [u.shape[0] for u in us]
+    out = torch.empty(dims, dtype=out_dtype or core.dtype, device=core.device)
+    core = core.contiguous()
+    ranks = (C.c_int64 * d)(*core.shape)
+    dd = (C.c_int64 * d)(*dims)
+    fp = (C.c_void_p * d)(*[u.data_ptr() for u in us])
+    opt = _opts(precision, stream)
+    _check(lib().atc_tucker_expand(_dev(core), _dt(core), ranks, d, fp, dd, _dev(out), _dt(out), C.byref(opt)))
+    return out
+
+
+def atc_tucker_expand_adjoint(dy: torch.Tensor, core: torch.Tensor, factors, precision: int = PREC_FP64,
+                              stream=None):
+    """(dL/dG, [dL/dU_k]) in FP64 for the cotangent dy of atc_tucker_expand."""
+    d = core.dim()
+    us = [f.to(torch.float64).contiguous() for f in factors]
+    dims = [u.shape[0] for u in us]
+    dy = dy.contiguous()
+    core = core.contiguous()
+    dcore = torch.empty(core.shape, dtype=torch.float64, device=core.device)
+    dfac = [torch.empty(u.shape, dtype=torch.float64, device=core.device) for u in us]
+    ranks = (C.c_int64 * d)(*core.shape)
+    dd = (C.c_int64 * d)(*dims)
+    fp = (C.c_void_p * d)(*[u.data_ptr() for u in us])
+    dfp = (C.c_void_p * d)(*[t.data_ptr() for t in dfac])
+    opt = _opts(precision, stream)
+    _check(lib().atc_tucker_expand_adjoint(_dev(dy), _dt(dy), _dev(core), _dt(core), ranks, d, fp, dd,
+                                           _dev(dcore), dfp, C.byref(opt)))
+    return dcore, dfac
+
+
+class TuckerExpand(torch.autograd.Function):
+    """Differentiable Tucker expansion: forward atc_tucker_expand, backward the
+    hand-written adjoint (gradients to the core and to every factor)."""
+
+    @staticmethod
+    def forward(ctx, precision, core, *factors):
+        ctx.precision = precision
+        ctx.save_for_backward(core, *factors)
+        return atc_tucker_expand(core, factors, out_dtype=core.dtype, precision=precision)
+
+    @staticmethod
+    def backward(ctx, dy):
+        core, *factors = ctx.saved_tensors
+        dcore, dfac = atc_tucker_expand_adjoint(dy, core, factors, precision=ctx.precision)
+        return (None, dcore.to(core.dtype)) + tuple(g.to(f.dtype) for g, f in zip(dfac, factors))
+
+
+def tucker_expand(core: torch.Tensor, factors, precision: int = PREC_FP64) -> torch.Tensor:
+    return TuckerExpand.apply(precision, core, *factors)
+

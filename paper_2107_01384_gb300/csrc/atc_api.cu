@@ -252,6 +252,54 @@ void free_compressed(atc_compressed* c) {
 
 }  // namespace
 
+// Expands the modes listed in `modes` (in that order) of the tensor `src`
+// (current sizes cur[], dtype sdt) with the factors U (n_m x r_m, FP64):
+// mode m goes from r_m to dims[m].  FP64 intermediates on the plain path, FP32
+// (tensor cores) on the split paths; ping-pong in bufA / bufB.  On return
+// *res / *rdt is the result (one of the buffers, or src if no mode was given).
+int expand_modes(const void* src, int sdt, int64_t* cur, int d, const double* const* U, const int64_t* dims,
+                 const std::vector<int>& modes, int precision, void* bufA, void* bufB, cudaStream_t s,
+                 const void** res, int* rdt) {
+  const bool split = precision != ATC_PREC_FP64;
+  const int odt = split ? ATC_F32 : ATC_F64;
+  void* dst = bufA;
+  for (int m : modes) {
+    int64_t L = 1, R = 1;
+    for (int i = 0; i < m; ++i) L *= cur[i];
+    for (int i = m + 1; i < d; ++i) R *= cur[i];
+    ATC_TRY(ttm_dispatch(src, sdt, L, dims[m], R, U[m], cur[m], 1, precision, dst, odt, s));
+    cur[m] = dims[m];
+    src = dst;
+    sdt = odt;
+    dst = (dst == bufA) ? bufB : bufA;
+  }
+  *res = src;
+  *rdt = sdt;
+  return ATC_OK;
+}
+
+// expansion order for a subset of modes: smallest growth n_m / r_m first
+std::vector<int> growth_order(const std::vector<int>& ms, const int64_t* dims, const int64_t* ranks) {
+  std::vector<int> o = ms;
+  std::stable_sort(o.begin(), o.end(), [&](int a, int b) {
+    return (double)dims[a] / (double)ranks[a] < (double)dims[b] / (double)ranks[b];
+  });
+  return o;
+}
+
+int tucker_args(const void* core, int cdt, const int64_t* ranks, int d, const double* const* U, const int64_t* dims,
+                int precision, int64_t* N) {
+  if (!core || !ranks || !U || !dims || d < 1 || d > 8 || !dtype_size(cdt))
+    return fail(ATC_EINVAL, "tucker expansion: bad arguments");
+  if (precision < 0 || precision > 2) return fail(ATC_EINVAL, "tucker expansion: bad precision");
+  ATC_TRY(check_dims(dims, d, N));
+  for (int i = 0; i < d; ++i) {
+    if (!U[i]) return fail(ATC_EINVAL, "tucker expansion: factor %d is NULL", i);
+    if (ranks[i] < 1 || ranks[i] > dims[i]) return fail(ATC_EINVAL, "tucker expansion: rank %d out of range", i);
+  }
+  return ATC_OK;
+}
+
 extern "C" {
 
 void atc_default_options(atc_options* opt) {
@@ -860,6 +908,102 @@ int atc_decompress_ex(const uint8_t* stream, size_t nbytes, void* out_dev, int o
   }
   ATC_TRY(launch_convert_f64_to(src, N, out_dev, out_dtype, s));
   ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  return ATC_OK;
+}
+
+int atc_tucker_expand(const void* core_dev, int core_dtype, const int64_t* ranks, int ndim,
+                      const double* const* factors_dev, const int64_t* dims, void* out_dev, int out_dtype,
+                      const atc_options* opt) {
+  atc_options o;
+  atc_default_options(&o);
+  if (opt) o = *opt;
+  int64_t N = 0;
+  ATC_TRY(tucker_args(core_dev, core_dtype, ranks, ndim, factors_dev, dims, o.precision, &N));
+  if (!out_dev || !dtype_size(out_dtype)) return fail(ATC_EINVAL, "atc_tucker_expand: bad output");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  void *A = nullptr, *B = nullptr;
+  ATC_TRY(Scratch::get(SLOT_ADJ_A, sizeof(double) * (size_t)N, &A));
+  ATC_TRY(Scratch::get(SLOT_ADJ_B, sizeof(double) * (size_t)N, &B));
+  int64_t cur[8];
+  for (int i = 0; i < ndim; ++i) cur[i] = ranks[i];
+  std::vector<int> all(ndim);
+  for (int i = 0; i < ndim; ++i) all[i] = i;
+  const void* res = nullptr;
+  int rdt = 0;
+  ATC_TRY(expand_modes(core_dev, core_dtype, cur, ndim, factors_dev, dims, growth_order(all, dims, ranks), o.precision,
+                       A, B, s, &res, &rdt));
+  if (rdt == out_dtype)
+    ATC_CUDA_TRY(cudaMemcpyAsync(out_dev, res, (size_t)N * dtype_size(out_dtype), cudaMemcpyDeviceToDevice, s));
+  else if (rdt == ATC_F64)
+    ATC_TRY(launch_convert_f64_to((const double*)res, N, out_dev, out_dtype, s));
+  else
+    ATC_TRY(launch_convert_to_f64(res, rdt, N, (double*)out_dev, s));
+  return ATC_OK;
+}
+
+int atc_tucker_expand_adjoint(const void* dy_dev, int dy_dtype, const void* core_dev, int core_dtype,
+                              const int64_t* ranks, int ndim, const double* const* factors_dev, const int64_t* dims,
+                              double* dcore_dev, double* const* dfactors_dev, const atc_options* opt) {
+  atc_options o;
+  atc_default_options(&o);
+  if (opt) o = *opt;
+  int64_t N = 0;
+  ATC_TRY(tucker_args(core_dev, core_dtype, ranks, ndim, factors_dev, dims, o.precision, &N));
+  if (!dy_dev || !dtype_size(dy_dtype)) return fail(ATC_EINVAL, "atc_tucker_expand_adjoint: bad dY");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  void *A = nullptr, *B = nullptr;
+  ATC_TRY(Scratch::get(SLOT_ADJ_A, sizeof(double) * (size_t)N, &A));
+  ATC_TRY(Scratch::get(SLOT_ADJ_B, sizeof(double) * (size_t)N, &B));
+  int64_t ncore = 1;
+  for (int i = 0; i < ndim; ++i) ncore *= ranks[i];
+  // dG = dY x_1 U_1^T ... x_d U_d^T: project every mode, largest shrink first
+  if (dcore_dev) {
+    std::vector<int> ord(ndim);
+    for (int i = 0; i < ndim; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+      return (double)dims[a] / (double)ranks[a] > (double)dims[b] / (double)ranks[b];
+    });
+    const bool split = o.precision != ATC_PREC_FP64;
+    const int odt = split ? ATC_F32 : ATC_F64;
+    int64_t cur[8];
+    for (int i = 0; i < ndim; ++i) cur[i] = dims[i];
+    const void* src = dy_dev;
+    int sdt = dy_dtype;
+    void* dst = A;
+    for (int m : ord) {
+      int64_t L = 1, R = 1;
+      for (int i = 0; i < m; ++i) L *= cur[i];
+      for (int i = m + 1; i < ndim; ++i) R *= cur[i];
+      ATC_TRY(ttm_dispatch(src, sdt, L, dims[m], R, factors_dev[m], ranks[m], 0, o.precision, dst, odt, s));
+      cur[m] = ranks[m];
+      src = dst;
+      sdt = odt;
+      dst = (dst == A) ? B : A;
+    }
+    if (sdt == ATC_F64)
+      ATC_CUDA_TRY(cudaMemcpyAsync(dcore_dev, src, sizeof(double) * (size_t)ncore, cudaMemcpyDeviceToDevice, s));
+    else
+      ATC_TRY(launch_convert_to_f64(src, sdt, ncore, dcore_dev, s));
+  }
+  // dU_i = unfold_i(dY) unfold_i(Z_i)^T with Z_i = G x_{j != i} U_j, recomputed per mode
+  if (dfactors_dev) {
+    for (int i = 0; i < ndim; ++i) {
+      if (!dfactors_dev[i]) continue;
+      int64_t cur[8];
+      for (int q = 0; q < ndim; ++q) cur[q] = ranks[q];
+      std::vector<int> others;
+      for (int q = 0; q < ndim; ++q)
+        if (q != i) others.push_back(q);
+      const void* z = nullptr;
+      int zdt = 0;
+      ATC_TRY(expand_modes(core_dev, core_dtype, cur, ndim, factors_dev, dims, growth_order(others, dims, ranks),
+                           o.precision, A, B, s, &z, &zdt));
+      int64_t L = 1, R = 1;
+      for (int q = 0; q < i; ++q) L *= dims[q];
+      for (int q = i + 1; q < ndim; ++q) R *= dims[q];
+      ATC_TRY(launch_cross_gram_fp64(dy_dev, dy_dtype, z, zdt, L, dims[i], ranks[i], R, dfactors_dev[i], s));
+    }
+  }
   return ATC_OK;
 }
 

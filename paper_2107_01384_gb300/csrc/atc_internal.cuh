@@ -75,6 +75,8 @@ enum ScratchSlot {
   SLOT_CAND,           // candidate factor of the residual-certified rank choice
   SLOT_DEC_RUNS,       // decoded run lengths per (block, plane)
   SLOT_SLICES,         // integer slice planes of the Gram input
+  SLOT_ADJ_A,          // adjoint / expansion chains
+  SLOT_ADJ_B,
   SLOT_COUNT
 };
 
@@ -94,6 +96,9 @@ int launch_permute(const double* x, const int64_t* dims, const int* perm, int nd
 int launch_gram_fp64(const void* x, int dtype, int64_t L, int64_t n, int64_t R, double* g, cudaStream_t s);
 int launch_ttm_fp64(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
                     int expand, void* y, int ydtype, cudaStream_t s);
+// C[i][j] = sum_{l,c} A[l][i][c] B[l][j][c] for A (L, n, R) and B (L, m, R), FP64 accumulation
+int launch_cross_gram_fp64(const void* a, int adt, const void* b, int bdt, int64_t L, int64_t n, int64_t m,
+                           int64_t R, double* c, cudaStream_t s);
 
 // split-precision tensor-core contractions (k_gram_tc.cu, k_ttm_tc.cu)
 // Common power-of-two scale of a tensor's fixed-point slices: the kernels read

@@ -164,6 +164,76 @@ __global__ void __launch_bounds__(kThreads) ttm_fp64_kernel(const TX* __restrict
   }
 }
 
+// Cross Gram of two tensors that share all modes but one:
+//   C[i][j] = sum_{l,c} A[l][i][c] B[l][j][c],   A viewed (L, n, R), B viewed (L, m, R)
+// (the factor gradient of the Tucker expansion).  Full n x m tiling, split-K
+// partials in part[split][n][m], FP64 accumulation.
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(kThreads) cross_gram_fp64_kernel(const TA* __restrict__ a, const TB* __restrict__ b,
+                                                                   int64_t n, int64_t m, int64_t R, int64_t K,
+                                                                   int64_t kchunk, int ntm, double* __restrict__ part) {
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+  const int ti = blockIdx.x / ntm, tj = blockIdx.x % ntm;
+  const int64_t i0 = (int64_t)ti * TM, j0 = (int64_t)tj * TN;
+  const int64_t k_begin = (int64_t)blockIdx.y * kchunk;
+  const int64_t k_end = min(K, k_begin + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0.0;
+  const bool kfast = R >= TK;
+  for (int64_t k0 = k_begin; k0 < k_end; k0 += TK) {
+#pragma unroll
+    for (int e = 0; e < (TM * TK) / kThreads; ++e) {
+      const int idx = threadIdx.x + e * kThreads;
+      int rr, kk;
+      if (kfast) { kk = idx % TK; rr = idx / TK; } else { rr = idx % TM; kk = idx / TM; }
+      const int64_t kappa = k0 + kk;
+      double va = 0.0, vb = 0.0;
+      if (kappa < k_end) {
+        if (i0 + rr < n) va = ld(a + unfold_off(i0 + rr, kappa, n, R));
+        if (j0 + rr < m) vb = ld(b + unfold_off(j0 + rr, kappa, m, R));
+      }
+      As[kk][rr] = va;
+      Bs[kk][rr] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { av[q] = As[kk][ty + 16 * q]; bv[q] = Bs[kk][tx + 16 * q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(av[p], bv[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.y * n * m;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int64_t i = i0 + ty + 16 * p;
+    if (i >= n) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t j = j0 + tx + 16 * q;
+      if (j < m) out[i * m + j] = acc[p][q];
+    }
+  }
+}
+
+__global__ void sum_splits_kernel(const double* __restrict__ part, int nsplit, int64_t total, double* __restrict__ c) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < nsplit; ++s) acc += part[(int64_t)s * total + idx];
+    c[idx] = acc;
+  }
+}
+
 }  // namespace
 
 int launch_gram_fp64(const void* x, int dtype, int64_t L, int64_t n, int64_t R, double* g, cudaStream_t s) {
@@ -193,6 +263,42 @@ int launch_gram_fp64(const void* x, int dtype, int64_t L, int64_t n, int64_t R, 
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   gram_reduce_kernel<<<blocks, 256, 0, s>>>(part, (int)nsplit, n, g);
+  ATC_LAUNCHED(1);
+  return ATC_OK;
+}
+
+int launch_cross_gram_fp64(const void* a, int adt, const void* b, int bdt, int64_t L, int64_t n, int64_t m,
+                           int64_t R, double* c, cudaStream_t s) {
+  const int64_t K = L * R;
+  const int ntn = (int)((n + TM - 1) / TM), ntm = (int)((m + TN - 1) / TN);
+  const int ntiles = ntn * ntm;
+  int64_t nsplit = (4 * 152 + ntiles - 1) / ntiles;
+  const int64_t maxsplit = (K + 255) / 256;
+  if (nsplit > maxsplit) nsplit = maxsplit;
+  while (nsplit > 1 && nsplit * n * m * 8 > (64ll << 20)) nsplit--;
+  if (nsplit < 1) nsplit = 1;
+  int64_t kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = (kchunk + TK - 1) / TK * TK;
+  if (kchunk < TK) kchunk = TK;
+  nsplit = (K + kchunk - 1) / kchunk;
+  if (nsplit < 1) nsplit = 1;
+  double* part = nullptr;
+  ATC_TRY(Scratch::get(SLOT_GRAM_PART, sizeof(double) * nsplit * n * m + 64, (void**)&part));
+  const dim3 grid((unsigned)ntiles, (unsigned)nsplit);
+  if (adt == ATC_F32 && bdt == ATC_F32)
+    cross_gram_fp64_kernel<float, float><<<grid, kThreads, 0, s>>>((const float*)a, (const float*)b, n, m, R, K, kchunk, ntm, part);
+  else if (adt == ATC_F32)
+    cross_gram_fp64_kernel<float, double><<<grid, kThreads, 0, s>>>((const float*)a, (const double*)b, n, m, R, K, kchunk, ntm, part);
+  else if (bdt == ATC_F32)
+    cross_gram_fp64_kernel<double, float><<<grid, kThreads, 0, s>>>((const double*)a, (const float*)b, n, m, R, K, kchunk, ntm, part);
+  else
+    cross_gram_fp64_kernel<double, double><<<grid, kThreads, 0, s>>>((const double*)a, (const double*)b, n, m, R, K, kchunk, ntm, part);
+  ATC_LAUNCHED(1);
+  const int64_t tot = n * m;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  sum_splits_kernel<<<blocks, 256, 0, s>>>(part, (int)nsplit, tot, c);
   ATC_LAUNCHED(1);
   return ATC_OK;
 }
