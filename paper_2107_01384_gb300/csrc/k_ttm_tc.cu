@@ -69,6 +69,9 @@ struct TtmArgs {
   // chunk's outputs, one FP64 partial per CTA in res_part[blockIdx.x]
   const void* xres;      // (L, Atot, R) tensor compared with the product
   double* res_part;
+  int64_t csz;           // output indices per chunk (blockIdx.y = chunk)
+  size_t wb;             // bytes of one chunk's factor slices
+  unsigned nchunk_launch;
 };
 
 template <typename T>
@@ -104,7 +107,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 template <typename TX, bool BF16, bool GEN, bool RES, typename TR>
-__global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a is modified per chunk (by value)
   typedef float TY;
   constexpr int MAXST = 4;
   const int NSTAGE = a.nstage;
@@ -118,6 +121,14 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   volatile int* abort = &abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // chunk of output indices of this CTA row (all chunks share the padded width apad)
+  {
+    const int64_t j0c = (int64_t)blockIdx.y * a.csz;
+    a.j0 = j0c;
+    a.A = (int)min((int64_t)a.csz, a.Atot - j0c);
+    a.bw += (size_t)blockIdx.y * a.wb;
+    if (a.res_part) a.res_part += (size_t)blockIdx.y * gridDim.x;
+  }
   const uint32_t B_BYTES = (uint32_t)a.apad * 128u;
   const uint32_t STAGE = 3 * A_BYTES + ((3 * B_BYTES + 1023u) & ~1023u);
   const int64_t nmine = (a.mtiles > blockIdx.x) ? (a.mtiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -369,16 +380,25 @@ namespace {
 // scale 2^8 (|U| <= 1) and laid out per K tile exactly as the
 // 128-byte-swizzled K-major shared-memory image: [slice][kt][apad][64].
 template <bool BF16>
-__global__ void ttm_prep_b(const double* __restrict__ u, int A, int64_t Atot, int64_t j0, int Bdim, int expand,
-                           int apad, int nkt, uint8_t* __restrict__ bw) {
-  const int64_t total = (int64_t)nkt * apad * 64;
+__global__ void ttm_prep_b(const double* __restrict__ u, int64_t csz, int64_t Atot, int nchunk, int Bdim, int expand,
+                           int apad, int nkt, uint8_t* __restrict__ bw, size_t wb) {
+  // W tiles of every chunk: W_ch[a][b] = U[b][j0 + a] (projection) or U[j0 + a][b]
+  // (expansion), j0 = ch * csz, cut into three integer slices on the scale
+  // 2^8 (|U| <= 1), laid out per K tile exactly as the 128-byte-swizzled
+  // K-major shared-memory image: [chunk][slice][kt][apad][64].
+  const int64_t per = (int64_t)nkt * apad * 64;
+  const int64_t total = per * nchunk;
   const size_t slice_bytes = (size_t)nkt * apad * 128;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int il = (int)(idx & 63);
-    const int64_t rest = idx >> 6;
+    const int ch = (int)(idx / per);
+    const int64_t e = idx - (int64_t)ch * per;
+    const int il = (int)(e & 63);
+    const int64_t rest = e >> 6;
     const int j = (int)(rest % apad);
     const int kt = (int)(rest / apad);
     const int b = kt * 64 + il;
+    const int64_t j0 = (int64_t)ch * csz;
+    const int64_t A = min(csz, Atot - j0);
     double w = 0.0;
     if (j < A && b < Bdim) w = expand ? u[(j0 + j) * (int64_t)Bdim + b] : u[(int64_t)b * Atot + j0 + j];
     // integer slices of v = 256 w in FP64 (exact steps, one final rounding)
@@ -387,10 +407,11 @@ __global__ void ttm_prep_b(const double* __restrict__ u, int A, int64_t Atot, in
     const double t = (v - a0) * 256.0;
     const double a1 = rint(t);
     const double a2 = rint((t - a1) * 256.0);
+    uint8_t* base = bw + (size_t)ch * wb;
     const size_t off = (size_t)kt * apad * 128 + tc::sw128_off((uint32_t)j, (uint32_t)il);
-    *reinterpret_cast<uint16_t*>(bw + off) = tc::Pack<BF16>::one((float)a0);
-    *reinterpret_cast<uint16_t*>(bw + slice_bytes + off) = tc::Pack<BF16>::one((float)a1);
-    *reinterpret_cast<uint16_t*>(bw + 2 * slice_bytes + off) = tc::Pack<BF16>::one((float)a2);
+    *reinterpret_cast<uint16_t*>(base + off) = tc::Pack<BF16>::one((float)a0);
+    *reinterpret_cast<uint16_t*>(base + slice_bytes + off) = tc::Pack<BF16>::one((float)a1);
+    *reinterpret_cast<uint16_t*>(base + 2 * slice_bytes + off) = tc::Pack<BF16>::one((float)a2);
   }
 }
 
@@ -402,7 +423,7 @@ int ttm_launch_t(const TtmArgs& a, int grid, int smem, cudaStream_t s) {
                                       225 * 1024));
     attr = true;
   }
-  ttm_tc_kernel<TX, BF16, GEN, RES, TR><<<grid, kThreads, smem, s>>>(a);
+  ttm_tc_kernel<TX, BF16, GEN, RES, TR><<<dim3(grid, a.nchunk_launch), kThreads, smem, s>>>(a);
   ATC_LAUNCHED(1);
   return ATC_OK;
 }
@@ -470,19 +491,16 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
   uint8_t* bw = nullptr;
   ATC_TRY(Scratch::get(SLOT_TTM_U, wb * nchunk + (size_t)8 * nchunk * (grid + 1) + 256, (void**)&bw));
   double* part = reinterpret_cast<double*>(bw + wb * nchunk);
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const int64_t j0 = ch * csz;
-    const int64_t A = std::min<int64_t>(csz, Atot - j0);
-    if (A <= 0) break;
+  {
     TtmArgs a;
     a.x = x;
     a.L = L;
     a.Bdim = Bdim;
     a.R = R;
-    a.A = (int)A;
-    a.apad = (int)((A + 15) / 16 * 16);
+    a.A = (int)std::min<int64_t>(csz, Atot);
+    a.apad = apad_max;
     a.Atot = Atot;
-    a.j0 = j0;
+    a.j0 = 0;
     a.nkt = nkt;
     a.mtiles = mtiles;
     a.y = y;
@@ -490,34 +508,37 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
     a.err = err;
     a.rowmode = (Bdim % 8 == 0) ? TM_ROWVEC : TM_ROW;
     a.xres = xres;
-    a.res_part = part + (size_t)ch * grid;
+    a.res_part = res ? part : nullptr;
+    a.csz = csz;
+    a.wb = wb;
+    a.nchunk_launch = (unsigned)nchunk;
+    a.bw = bw;
     const uint32_t bbytes = (uint32_t)a.apad * 128u;
     const uint32_t stage = 3u * 128u * 128u + ((3u * bbytes + 1023u) & ~1023u);
     a.nstage = (int)((224u * 1024u) / stage);
     if (a.nstage > 4) a.nstage = 4;
     if (a.nstage < 2) return fail(ATC_EUNSUP, "TTM stage does not fit in shared memory");
     const int smem = (int)(a.nstage * stage + 1024);
-    uint8_t* bwc = bw + wb * ch;
-    a.bw = bwc;
     {
-      const int64_t tot = (int64_t)nkt * a.apad * 64;
-      const int blocks = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
-      if (bf16 || res) ttm_prep_b<true><<<blocks, 256, 0, s>>>(u, a.A, Atot, j0, (int)Bdim, expand, a.apad, nkt, bwc);
-      else ttm_prep_b<false><<<blocks, 256, 0, s>>>(u, a.A, Atot, j0, (int)Bdim, expand, a.apad, nkt, bwc);
+      const int64_t tot = (int64_t)nkt * a.apad * 64 * nchunk;
+      const int blocks = (int)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096);
+      if (bf16 || res) ttm_prep_b<true><<<blocks, 256, 0, s>>>(u, csz, Atot, nchunk, (int)Bdim, expand, a.apad, nkt, bw, wb);
+      else ttm_prep_b<false><<<blocks, 256, 0, s>>>(u, csz, Atot, nchunk, (int)Bdim, expand, a.apad, nkt, bw, wb);
       ATC_LAUNCHED(1);
     }
-    if (mtiles == 0) continue;
-    const bool gen = (R != 1);
-    if (res) {
-      if (xdtype != ATC_F32) return fail(ATC_EUNSUP, "residual mode expects an FP32 projected tensor");
-      if (xres_dtype == ATC_F32) ATC_TRY(ttm_launch_res<float>(a, gen, grid, smem, s));
-      else ATC_TRY(ttm_launch_res<double>(a, gen, grid, smem, s));
-    } else if (xdtype == ATC_F32) {
-      if (bf16) ATC_TRY((ttm_launch_g<float, true>(a, gen, grid, smem, s)));
-      else ATC_TRY((ttm_launch_g<float, false>(a, gen, grid, smem, s)));
-    } else {
-      if (bf16) ATC_TRY((ttm_launch_g<double, true>(a, gen, grid, smem, s)));
-      else ATC_TRY((ttm_launch_g<double, false>(a, gen, grid, smem, s)));
+    if (mtiles > 0) {
+      const bool gen = (R != 1);
+      if (res) {
+        if (xdtype != ATC_F32) return fail(ATC_EUNSUP, "residual mode expects an FP32 projected tensor");
+        if (xres_dtype == ATC_F32) ATC_TRY(ttm_launch_res<float>(a, gen, grid, smem, s));
+        else ATC_TRY(ttm_launch_res<double>(a, gen, grid, smem, s));
+      } else if (xdtype == ATC_F32) {
+        if (bf16) ATC_TRY((ttm_launch_g<float, true>(a, gen, grid, smem, s)));
+        else ATC_TRY((ttm_launch_g<float, false>(a, gen, grid, smem, s)));
+      } else {
+        if (bf16) ATC_TRY((ttm_launch_g<double, true>(a, gen, grid, smem, s)));
+        else ATC_TRY((ttm_launch_g<double, false>(a, gen, grid, smem, s)));
+      }
     }
   }
   if (res) {
