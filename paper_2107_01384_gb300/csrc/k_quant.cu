@@ -575,8 +575,17 @@ struct RansEnc {
   uint32_t nbytes;
 };
 
+// x / f for x < 2^31 and 1 <= f <= 2^12 by one multiply-high with
+// inv = ceil(2^44 / f): the error of x inv / 2^44 is below 2^31 / 2^44 = 2^-13,
+// less than the distance 1/f >= 2^-12 of x/f to the next integer when x mod f
+// < f - 1, and the floor is exact in every case (Granlund-Montgomery style)
+__device__ __forceinline__ uint32_t div_by_inv(uint32_t x, uint64_t inv) {
+  return (uint32_t)__umul64hi((uint64_t)x << 20, inv);
+}
+
 template <typename EmitF>
-__device__ __forceinline__ void rans_put_run(RansEnc& r, uint32_t run, const uint32_t* f, const uint32_t* cum, EmitF emit) {
+__device__ __forceinline__ void rans_put_run(RansEnc& r, uint32_t run, const uint32_t* f, const uint32_t* cum,
+                                             const uint64_t* inv, EmitF emit) {
   const int sb = bucket_of(run);
   const uint32_t extra = run + 1u - (1u << sb);
   if (sb > 0) {
@@ -587,7 +596,8 @@ __device__ __forceinline__ void rans_put_run(RansEnc& r, uint32_t run, const uin
   const uint32_t fr = f[sb], c = cum[sb];
   const uint32_t xmax = ((kRansL >> kScaleBits) << 8) * fr;
   while (r.x >= xmax) { emit((uint8_t)(r.x & 0xff)); r.x >>= 8; r.nbytes++; }
-  r.x = ((r.x / fr) << kScaleBits) + (r.x % fr) + c;
+  const uint32_t q = div_by_inv(r.x, inv[sb]);
+  r.x = (q << kScaleBits) + (r.x - q * fr) + c;
 }
 
 constexpr int kMaxRuns = 4097;  // enough for block_size <= 4096; larger blocks use the global spill
@@ -596,6 +606,8 @@ constexpr int kEncWarps = 2;  // 2 x 4097 x 4 B of static shared memory
 // pass 2 (sizes_only) / pass 3: per chunk, collect runs (forward), rANS them backward.
 __global__ void __launch_bounds__(32 * kEncWarps) enc_rans_kernel(EncParams P, int sizes_only, uint32_t* spill) {
   __shared__ uint32_t runs_sm[kEncWarps][kMaxRuns];
+  __shared__ uint32_t f_sm[kEncWarps][kNsym], c_sm[kEncWarps][kNsym];
+  __shared__ uint64_t i_sm[kEncWarps][kNsym];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t chunk = (int64_t)blockIdx.x * kEncWarps + warp;
   const int64_t nchunks = P.nblocks * P.nplanes;
@@ -627,11 +639,18 @@ __global__ void __launch_bounds__(32 * kEncWarps) enc_rans_kernel(EncParams P, i
       });
   if (lane != 0) return;
   if (!sizes_only && nacc > 0) *rawp = (uint8_t)(acc & 0xff);
-  const uint32_t* f = P.freq + pi * kNsym;
-  const uint32_t* cum = P.freq + P.nplanes * kNsym + pi * kNsym;
+  // this plane's table in shared memory, with the division constants
+  uint32_t* f = f_sm[warp];
+  uint32_t* cum = c_sm[warp];
+  uint64_t* inv = i_sm[warp];
+  for (int i = 0; i < kNsym; ++i) {
+    f[i] = P.freq[pi * kNsym + i];
+    cum[i] = P.freq[P.nplanes * kNsym + pi * kNsym + i];
+    inv[i] = f[i] ? ((1ull << 44) + f[i] - 1) / f[i] : 0ull;
+  }
   RansEnc r = {kRansL, 0};
   if (sizes_only) {
-    for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, [](uint8_t) {});
+    for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, inv, [](uint8_t) {});
     P.rsize[chunk] = nr ? (r.nbytes + 4) : 0;
   } else {
     if (nr) {
@@ -639,7 +658,8 @@ __global__ void __launch_bounds__(32 * kEncWarps) enc_rans_kernel(EncParams P, i
       uint8_t* base = P.out + P.off[chunk];
       uint8_t* end = base + P.rsize[chunk];
       uint8_t* w = end;
-      for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, [&](uint8_t by) { *--w = by; });
+      for (int64_t t = (int64_t)nr - 1; t >= 0; --t)
+        rans_put_run(r, runs[t], f, cum, inv, [&](uint8_t by) { *--w = by; });
       w -= 4;
       w[0] = (uint8_t)r.x;
       w[1] = (uint8_t)(r.x >> 8);
