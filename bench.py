@@ -153,7 +153,7 @@ def time_oracle_step(x, eps):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(x, eps, budget_s=12.0, max_reps=5):
+def cpu_baseline(x, eps, budget_s=12.0, max_reps=1000):
     reps, total = 0, 0.0
     while reps < max_reps and (total < budget_s or reps == 0):
         total += time_oracle_step(x, eps)
@@ -345,10 +345,13 @@ def run_ours(args, world, rank, local):
         fl = sum(4.0 / 3.0 * dims[m] ** 3 + 2.0 * dims[m] ** 2 * ranks[m] for m in order)
         ach = fl / (phases["ms_eig"] * 1e-3) / 1e12
         fp64_peak = 1.1  # TFLOP/s: torch float64 matmul on this machine's GB300 (no FP64 entry in the peaks file)
-        roof = {"kernel": "eigensolver phase", "kernels": "tridiag_cluster_kernel, msect_kernel, invit_par_kernel, "
-                "mgs_group_kernel, backtransform_kernel", "bound": "alu", "achieved": ach, "peak": fp64_peak,
-                "unit": "TFLOP/s (FP64)", "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "measured FP64 DGEMM rate (torch float64 matmul), not in the peaks file"}
+        kern = ("tridiag_cluster_dd_kernel, msect_dd_kernel, invit_dd_kernel, cholqr_group_kernel, "
+                "backtransform_dd_kernel (double-float on the FP32 pipes)") if prec != 0 else \
+               ("tridiag_cluster_kernel, msect_kernel, invit_par_kernel, cholqr_group_kernel, backtransform_kernel")
+        roof = {"kernel": "eigensolver phase", "kernels": kern, "bound": "alu", "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s (FP64-class: 4/3 n^3 + 2 n^2 r per mode)", "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "measured FP64 DGEMM rate (torch float64 matmul), not in the peaks file; the phase "
+                               "is a chain of n - 2 dependent Householder steps (latency-bound)"}
     else:
         roof = {"kernel": "quantizer/encoder", "bound": "alu", "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None}
