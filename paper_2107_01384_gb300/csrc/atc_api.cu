@@ -567,13 +567,15 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         if (rc) return bail(rc);
         int K = (int)std::min<int64_t>(n, 48);
         double tr = 0.0;
+        int he = 0;  // tensor-core wait flag, read with the eigenvalues (one host sync)
         std::vector<double> lh;
         for (;;) {
           rc = launch_eig_more((int)n, K, lam, s);
           if (rc) return bail(rc);
           lh.resize(K);
           if (cudaMemcpyAsync(lh.data(), lam, sizeof(double) * K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-              cudaMemcpyAsync(&tr, ddev + 2, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+              cudaMemcpyAsync(&tr, ddev + 2, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              (tc_err && cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess))
             return bail(fail(ATC_ECUDA, "eigenvalue readback failed"));
           rc = eig_check(s);
           if (rc) return bail(rc);
@@ -589,19 +591,14 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
           if (K == n) { r = (int)n; disc = 0.0; break; }
           K = (int)n;
         }
-        if (tc_err) {
-          int he = 0;
-          if (cudaMemcpy(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-            return bail(fail(ATC_ECUDA, "error flag readback failed"));
-          if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
-        }
+        if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
         if (r < 1 || r > n) return bail(fail(ATC_ENUMERIC, "rank selection failed (r = %d)", r));
         if (opt.precision != ATC_PREC_FP64 && r < n) {
           clk.mark(PH_EIG);
-          // Split paths: the eigenvalues of the sliced Gram carry a small
-          // systematic shift (the dropped low-order slice products are
-          // correlated for smooth data), far below what moves the eigenvectors
-          // but not always below the distance of the tail from the budget.
+          // Split paths: the sliced Gram is that of X rounded to 24-bit fixed
+          // point, summed in FP32 orders; its eigenvalues carry a small shift,
+          // far below what moves the eigenvectors but not always below the
+          // distance of the tail from the budget.
           // So the rank is certified on the tensor itself: with U the leading
           // rh eigenvectors and Y = U^T ._m X (tensor cores),
           //   tail(r) = ||X - U ._m Y||^2 + sum_{j >= r} ||Y_j||^2   (U orthonormal),
@@ -623,10 +620,12 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
             if (!rc) rc = launch_row_energy((const float*)next, L, rh, R, edev, s);
             if (rc) return bail(rc);
             std::vector<double> eh((size_t)rh + 1), t((size_t)rh + 1);
-            if (cudaMemcpyAsync(eh.data(), edev, sizeof(double) * (rh + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            if (cudaMemcpyAsync(eh.data(), edev, sizeof(double) * (rh + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
               return bail(fail(ATC_ECUDA, "residual readback failed"));
             rc = eig_check(s);
             if (rc) return bail(rc);
+            if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
             t[rh] = (rh == n) ? 0.0 : eh[rh];
             for (int j = rh - 1; j >= 0; --j) t[j] = t[j + 1] + eh[j];
             int rn = -1;
@@ -732,7 +731,11 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   put64(S, (uint64_t)section.size());
   S.append(section);
   clk.mark(PH_OTHER);
+  int he_end = 0;
+  if (tc_err && cudaMemcpyAsync(&he_end, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return bail(fail(ATC_ECUDA, "error flag readback failed"));
   if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ATC_ECUDA, "stream synchronisation failed"));
+  if (he_end) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
   {
     double ph[PH_COUNT];
     clk.sum(ph, PH_COUNT);

@@ -1188,8 +1188,10 @@ __global__ void __launch_bounds__(kMsThreads) msect_dd_kernel(EigState st, int K
     lo = nlo;
     hi = nhi;
     __syncthreads();
-    // double-float resolution of the recurrence: about 2^-44 relative, 2^-70 absolute
-    if (hi - lo <= 0x1p-44 * fmax(fabs(lo), fabs(hi)) + 0x1p-70) break;
+    // the split paths use these values for inverse-iteration shifts and a
+    // provisional rank only (ranks are certified from residuals): 2^-30
+    // relative (or 2^-70 absolute) is ample
+    if (hi - lo <= 0x1p-30 * fmax(fabs(lo), fabs(hi)) + 0x1p-70) break;
   }
   if (tid == 0) st.lam[j] = 0.5 * (lo + hi);
 }
