@@ -162,6 +162,54 @@ int atc_tucker_expand_adjoint(const void* dy_dev, int dy_dtype, const void* core
                               double* dcore_dev, double* const* dfactors_dev, const atc_options* opt);
 
 /* ------------------------------------------------------------------------
+ * Batched ST-HOSVD.  `count` float32 tensors of one order d (1..8), each with
+ * its own shape (every mode length <= 112) and rel_eps, go through Algorithm 1
+ * (Section 4.1.3 error budget and rank rule, Section 4.1.1 mode order) in ONE
+ * persistent kernel launch that is captured once in a CUDA graph and replayed
+ * by atc_batch_run.  Arithmetic: exact float products summed in double-float
+ * with FP64 flushes (Gram), double-float Jacobi eigensolve, FP64 tails for the
+ * rank choice, double-float projection (FP32 intermediates, FP64 core).
+ * opt->precision is ignored; opt->rtmss, rank_rule and mode_order apply to
+ * every tensor.  Quantization and encoding of the cores are not part of it.
+ * ------------------------------------------------------------------------ */
+typedef struct atc_batch atc_batch; /* opaque, library-owned until atc_batch_free() */
+
+/*
+ * Plan a batch: dims is a host array of count * ndim sizes (tensor t's modes
+ * at dims[t * ndim ...]), rel_eps a host array of count values in (0, 1],
+ * dtype must be ATC_F32.  Allocates the outputs (cores, factors), the per-CTA
+ * scratch and the graph.  The first plan of a process also measures the Gram
+ * register tile per mode length on the device (atc_batch_tune; set the
+ * environment variable ATC_BATCH_TUNE=0 to use the built-in table instead).
+ * Errors: ATC_EINVAL, ATC_EUNSUP (dtype, a mode longer than 112), ATC_ENOMEM, ATC_ECUDA.
+ */
+int atc_batch_create(int count, int ndim, const int64_t* dims, int dtype, const double* rel_eps,
+                     const atc_options* opt, atc_batch** out);
+/*
+ * Run the planned batch on `count` device tensors (host array of device
+ * pointers, tensor t row-major with the planned shape; read only) on `stream`,
+ * then wait for it.  Results stay valid until the next run or atc_batch_free.
+ * Errors: ATC_EINVAL, ATC_ECUDA, ATC_ENUMERIC (NaN / Inf in an input).
+ */
+int atc_batch_run(atc_batch* b, const void* const* tensors_dev, void* stream);
+/* ranks[ndim] (host) of tensor `index`, original mode order. */
+int atc_batch_get_ranks(const atc_batch* b, int index, int64_t* ranks);
+/* Borrowed device pointer to tensor index's FP64 core, shape (r_1..r_d) row-major. */
+int atc_batch_get_core(const atc_batch* b, int index, const double** core_dev);
+/* Borrowed device pointer to factor U_mode of tensor index, FP64 (n_mode x r_mode) row-major. */
+int atc_batch_get_factor(const atc_batch* b, int index, int mode, const double** u_dev);
+/* Host statistics of tensor index: ||X||^2, the discarded energy, the Jacobi
+ * sweeps per mode (negative: the sweep limit was hit) and a status word
+ * (0 ok, 2 a Jacobi solve hit its sweep limit).  Any pointer may be NULL. */
+int atc_batch_get_stats(const atc_batch* b, int index, double* norm2, double* sse_trunc, int* sweeps,
+                        int* status);
+/* Device time of the last atc_batch_run, graph launch to completion, in ms. */
+float atc_batch_last_ms(const atc_batch* b);
+/* Measure the Gram tile table now (table_out: NULL or 113 ints, the tile edge per mode length). */
+int atc_batch_tune(void* stream, int* table_out);
+void atc_batch_free(atc_batch* b);
+
+/* ------------------------------------------------------------------------
  * Step entry points: one per stage of the hot path, for parity tests and
  * for callers that drive the loop themselves.  All sizes are element counts.
  * ------------------------------------------------------------------------ */

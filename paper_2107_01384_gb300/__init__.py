@@ -21,7 +21,7 @@ __all__ = [
     "atc_norm2", "atc_gram", "atc_gram_fp64_noalloc", "atc_eig_sym", "atc_rank_select", "atc_ttm",
     "atc_quantize_core", "atc_dequantize_core", "atc_compress", "atc_decompress",
     "atc_peek_dims", "Compressed", "EXPORTS", "atc_tucker_expand", "atc_tucker_expand_adjoint",
-    "TuckerExpand", "tucker_expand",
+    "TuckerExpand", "tucker_expand", "Batch", "atc_batch_tune",
 ]
 
 ATC_F32, ATC_F64 = 1, 2
@@ -39,6 +39,8 @@ EXPORTS = [
     "atc_gram", "atc_eig_sym", "atc_rank_select", "atc_ttm", "atc_quantize_core",
     "atc_dequantize_core", "atc_free_buffer", "atc_release_workspace", "atc_last_error",
     "atc_kernel_launches", "atc_gram_fp64_noalloc",
+    "atc_batch_create", "atc_batch_run", "atc_batch_get_ranks", "atc_batch_get_core", "atc_batch_get_factor",
+    "atc_batch_get_stats", "atc_batch_last_ms", "atc_batch_tune", "atc_batch_free",
 ]
 
 
@@ -104,6 +106,18 @@ def lib():
         L.atc_release_workspace.argtypes = []
         L.atc_kernel_launches.argtypes = []
         L.atc_kernel_launches.restype = C.c_longlong
+        L.atc_batch_create.argtypes = [i32, i32, C.POINTER(i64), i32, C.POINTER(dbl), C.POINTER(Options),
+                                       C.POINTER(vp)]
+        L.atc_batch_run.argtypes = [vp, C.POINTER(vp), vp]
+        L.atc_batch_get_ranks.argtypes = [vp, i32, C.POINTER(i64)]
+        L.atc_batch_get_core.argtypes = [vp, i32, C.POINTER(vp)]
+        L.atc_batch_get_factor.argtypes = [vp, i32, i32, C.POINTER(vp)]
+        L.atc_batch_get_stats.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(i32), C.POINTER(i32)]
+        L.atc_batch_last_ms.argtypes = [vp]
+        L.atc_batch_last_ms.restype = C.c_float
+        L.atc_batch_tune.argtypes = [vp, C.POINTER(i32)]
+        L.atc_batch_free.argtypes = [vp]
+        L.atc_batch_free.restype = None
         _lib = L
     return _lib
 
@@ -351,3 +365,89 @@ class TuckerExpand(torch.autograd.Function):
 def tucker_expand(core: torch.Tensor, factors, precision: int = PREC_FP64) -> torch.Tensor:
     return TuckerExpand.apply(precision, core, *factors)
 
+
+
+def _borrowed(ptr, shape):
+    """Copy of a library-owned FP64 device buffer as a torch tensor."""
+    class _View:
+        pass
+    v = _View()
+    v.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": "<f8",
+                                  "data": (ptr.value, False), "version": 3, "strides": None}
+    return torch.as_tensor(v, device="cuda").clone()
+
+
+class Batch:
+    """Batched ST-HOSVD plan (atc_batch_*): many float32 tensors of one order,
+    uneven shapes and per-tensor rel_eps, in one persistent graph-replayed launch."""
+
+    def __init__(self, shapes, rel_eps, rtmss: float = 0.5, rank_rule: int = RANK_STATIC, mode_order=None,
+                 stream=None):
+        shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        if not shapes:
+            raise ValueError("empty batch")
+        d = len(shapes[0])
+        if any(len(sh) != d for sh in shapes):
+            raise ValueError("all tensors of a batch must have the same order")
+        if len(rel_eps) != len(shapes):
+            raise ValueError("one rel_eps per tensor")
+        self.shapes, self.ndim, self.count = shapes, d, len(shapes)
+        opt = Options()
+        lib().atc_default_options(C.byref(opt))
+        opt.rtmss = rtmss
+        opt.rank_rule = rank_rule
+        opt.stream = _stream(stream)
+        self._order = None
+        if mode_order is not None:
+            self._order = (C.c_int * d)(*mode_order)
+            opt.mode_order = self._order
+        dims = (C.c_int64 * (d * self.count))(*[v for sh in shapes for v in sh])
+        eps = (C.c_double * self.count)(*[float(e) for e in rel_eps])
+        h = C.c_void_p()
+        _check(lib().atc_batch_create(self.count, d, dims, ATC_F32, eps, C.byref(opt), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().atc_batch_free(self._h)
+            self._h = None
+
+    def run(self, tensors, stream=None) -> float:
+        """Compress the device tensors (float32, the planned shapes); returns the device ms."""
+        if len(tensors) != self.count:
+            raise ValueError("one tensor per planned shape")
+        for t, sh in zip(tensors, self.shapes):
+            if t.dtype != torch.float32 or tuple(t.shape) != sh:
+                raise ValueError(f"expected a float32 tensor of shape {sh}")
+        ptrs = (C.c_void_p * self.count)(*[_dev(t).value for t in tensors])
+        _check(lib().atc_batch_run(self._h, ptrs, _stream(stream)))
+        return float(lib().atc_batch_last_ms(self._h))
+
+    def ranks(self, i: int):
+        r = (C.c_int64 * self.ndim)()
+        _check(lib().atc_batch_get_ranks(self._h, i, r))
+        return list(r)
+
+    def stats(self, i: int) -> dict:
+        n2, sse = C.c_double(0), C.c_double(0)
+        sw = (C.c_int * self.ndim)()
+        st = C.c_int(0)
+        _check(lib().atc_batch_get_stats(self._h, i, C.byref(n2), C.byref(sse), sw, C.byref(st)))
+        return dict(norm2=n2.value, sse_trunc=sse.value, sweeps=list(sw), status=st.value)
+
+    def core(self, i: int) -> torch.Tensor:
+        p = C.c_void_p()
+        _check(lib().atc_batch_get_core(self._h, i, C.byref(p)))
+        return _borrowed(p, self.ranks(i))
+
+    def factor(self, i: int, mode: int) -> torch.Tensor:
+        p = C.c_void_p()
+        _check(lib().atc_batch_get_factor(self._h, i, mode, C.byref(p)))
+        return _borrowed(p, [self.shapes[i][mode], self.ranks(i)[mode]])
+
+
+def atc_batch_tune(stream=None):
+    """Measure the batched Gram tile table now; returns the tile edge per mode length."""
+    tab = (C.c_int * 113)()
+    _check(lib().atc_batch_tune(_stream(stream), tab))
+    return list(tab)

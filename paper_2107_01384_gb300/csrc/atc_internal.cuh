@@ -77,6 +77,7 @@ enum ScratchSlot {
   SLOT_SLICES,         // integer slice planes of the Gram input
   SLOT_ADJ_A,          // adjoint / expansion chains
   SLOT_ADJ_B,
+  SLOT_BATCH_TUNE,     // batched-path tile probe input
   SLOT_COUNT
 };
 

@@ -78,3 +78,23 @@ def test_stream_header_checks_on_host(lib):
     assert lib.atc_peek_dims(hdr + b"\0" * 64, len(hdr) + 64, C.byref(nd), dims, C.byref(dt)) == 0
     assert nd.value == 3 and list(dims)[:3] == [5, 6, 7] and dt.value == 1
     assert lib.atc_peek_dims(hdr[:20], 20, C.byref(nd), dims, C.byref(dt)) == -4
+
+
+def test_batch_create_rejects_bad_arguments_on_the_host(lib):
+    """atc_batch_create validates shapes, dtype and rel_eps before touching the device."""
+    import ctypes as C
+    h = C.c_void_p()
+    dims = (C.c_int64 * 6)(16, 20, 24, 30, 31, 32)
+    eps = (C.c_double * 2)(1e-2, 1e-3)
+    assert lib.atc_batch_create(0, 3, dims, 1, eps, None, C.byref(h)) == -1
+    assert lib.atc_batch_create(2, 9, dims, 1, eps, None, C.byref(h)) == -1
+    assert lib.atc_batch_create(2, 3, None, 1, eps, None, C.byref(h)) == -1
+    assert lib.atc_batch_create(2, 3, dims, 2, eps, None, C.byref(h)) == -5   # float64: unsupported
+    big = (C.c_int64 * 6)(16, 20, 113, 30, 31, 32)
+    assert lib.atc_batch_create(2, 3, big, 1, eps, None, C.byref(h)) == -5    # mode > 112
+    zero = (C.c_int64 * 6)(16, 0, 24, 30, 31, 32)
+    assert lib.atc_batch_create(2, 3, zero, 1, eps, None, C.byref(h)) == -1
+    for bad in (0.0, 1.5, float("nan")):
+        e2 = (C.c_double * 2)(1e-2, bad)
+        assert lib.atc_batch_create(2, 3, dims, 1, e2, None, C.byref(h)) == -1
+    assert not h.value
