@@ -203,6 +203,10 @@ int atc_batch_get_factor(const atc_batch* b, int index, int mode, const double**
  * (0 ok, 2 a Jacobi solve hit its sweep limit).  Any pointer may be NULL. */
 int atc_batch_get_stats(const atc_batch* b, int index, double* norm2, double* sse_trunc, int* sweeps,
                         int* status);
+/* SM clock cycles the CTA that took tensor index spent in its phases
+ * (cycles[4]: power-of-two scale + Gram, Jacobi, rank choice + factor output,
+ * projection) and rounds[ndim]: the Jacobi rounds that rotated, per mode.  Either pointer may be NULL. */
+int atc_batch_get_profile(const atc_batch* b, int index, int64_t* cycles, int* rounds);
 /* Device time of the last atc_batch_run, graph launch to completion, in ms. */
 float atc_batch_last_ms(const atc_batch* b);
 /* Measure the Gram tile table now (table_out: NULL or 113 ints, the tile edge per mode length). */

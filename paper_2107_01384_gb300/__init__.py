@@ -40,7 +40,7 @@ EXPORTS = [
     "atc_dequantize_core", "atc_free_buffer", "atc_release_workspace", "atc_last_error",
     "atc_kernel_launches", "atc_gram_fp64_noalloc",
     "atc_batch_create", "atc_batch_run", "atc_batch_get_ranks", "atc_batch_get_core", "atc_batch_get_factor",
-    "atc_batch_get_stats", "atc_batch_last_ms", "atc_batch_tune", "atc_batch_free",
+    "atc_batch_get_stats", "atc_batch_get_profile", "atc_batch_last_ms", "atc_batch_tune", "atc_batch_free",
 ]
 
 
@@ -113,6 +113,7 @@ def lib():
         L.atc_batch_get_core.argtypes = [vp, i32, C.POINTER(vp)]
         L.atc_batch_get_factor.argtypes = [vp, i32, i32, C.POINTER(vp)]
         L.atc_batch_get_stats.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(i32), C.POINTER(i32)]
+        L.atc_batch_get_profile.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i32)]
         L.atc_batch_last_ms.argtypes = [vp]
         L.atc_batch_last_ms.restype = C.c_float
         L.atc_batch_tune.argtypes = [vp, C.POINTER(i32)]
@@ -434,6 +435,13 @@ class Batch:
         st = C.c_int(0)
         _check(lib().atc_batch_get_stats(self._h, i, C.byref(n2), C.byref(sse), sw, C.byref(st)))
         return dict(norm2=n2.value, sse_trunc=sse.value, sweeps=list(sw), status=st.value)
+
+    def profile(self, i: int) -> dict:
+        """SM cycles per phase (gram, jacobi, rank, ttm) and rotating Jacobi rounds per mode of tensor i."""
+        cyc = (C.c_int64 * 4)()
+        rounds = (C.c_int * self.ndim)()
+        _check(lib().atc_batch_get_profile(self._h, i, cyc, rounds))
+        return dict(gram=cyc[0], jacobi=cyc[1], rank=cyc[2], ttm=cyc[3], rounds=list(rounds))
 
     def core(self, i: int) -> torch.Tensor:
         p = C.c_void_p()

@@ -65,7 +65,8 @@ struct BatchOut {
   double norm2;
   double sse_trunc;
   int status;                 // 0 ok, 1 NaN/Inf in the input, 2 Jacobi did not converge
-  int pad;
+  int rounds[kBMaxD];         // Jacobi rounds that rotated, per mode
+  long long cycles[4];        // SM clocks in scale+Gram, Jacobi, rank+factor, projection
 };
 
 struct BatchArgs {
@@ -309,7 +310,8 @@ struct JacobiShared {
 // |a_pq| <= 2^-40 sqrt(|a_pp a_qq|) or |a_pq| <= 2^-44 trace(A); the sweeps
 // stop after one with no rotation.  Returns the sweeps run (negative if the
 // limit was hit).
-__device__ int batch_jacobi(dd* __restrict__ A, dd* __restrict__ V, int n, JacobiShared& js, float trace) {
+__device__ int batch_jacobi(dd* __restrict__ A, dd* __restrict__ V, int n, JacobiShared& js, float trace,
+                            int* nrounds) {
   const int tid = threadIdx.x;
   const int m = n + (n & 1);
   const int np = m / 2;
@@ -360,6 +362,7 @@ __device__ int batch_jacobi(dd* __restrict__ A, dd* __restrict__ V, int n, Jacob
       }
       if (!__syncthreads_or(flag)) continue;
       rotated = 1;
+      ++*nrounds;
       // A <- J^T A J over the 2x2 blocks (ki <= kj; the mirror is written too)
       for (int b = tid; b < nblk; b += blockDim.x) {
         const int ki = js.blk[b] >> 8, kj = js.blk[b] & 0xff;
@@ -565,6 +568,8 @@ __global__ void __launch_bounds__(kBThreads) batch_sthosvd_kernel(BatchArgs a) {
     float src_scl = scl;
     double norm2 = 0.0, used = 0.0, budget_total = 0.0;
     int status = 0;
+    long long cyc[4] = {0, 0, 0, 0};
+    long long t0 = clock64();
     for (int step = 0; step < d; ++step) {
       const int m = T.order[step];
       int64_t L = 1, R = 1;
@@ -598,7 +603,14 @@ __global__ void __launch_bounds__(kBThreads) batch_sthosvd_kernel(BatchArgs a) {
         V[e] = ddf(i == j ? 1.f : 0.f);
       }
       __syncthreads();
-      const int sw = batch_jacobi(A, V, n, js, (float)trace);
+      long long t1 = clock64();
+      cyc[0] += t1 - t0;
+      t0 = t1;
+      int nrounds = 0;
+      const int sw = batch_jacobi(A, V, n, js, (float)trace, &nrounds);
+      t1 = clock64();
+      cyc[1] += t1 - t0;
+      t0 = t1;
       if (sw < 0) status = 2;
       // eigenvalues (clamped at 0, unscaled), descending order, ties by index
       for (int i = tid; i < n; i += blockDim.x) s_lam[i] = fmax(dd_to(A[i * n + i]), 0.0) * unscale2;
@@ -630,6 +642,7 @@ __global__ void __launch_bounds__(kBThreads) batch_sthosvd_kernel(BatchArgs a) {
         s_r = r;
         O->ranks[m] = r;
         O->sweeps[m] = sw;
+        O->rounds[m] = nrounds;
         O->discarded[m] = s_tail[r];
       }
       __syncthreads();
@@ -681,8 +694,14 @@ __global__ void __launch_bounds__(kBThreads) batch_sthosvd_kernel(BatchArgs a) {
       float* dst32 = (step & 1) ? buf1 : buf0;
       double* dst64 = last ? a.core_pool + T.core_off : nullptr;
       const int cap = (int)((size_t)8 * kBMaxN * kBMaxN / sizeof(float));
+      t1 = clock64();
+      cyc[2] += t1 - t0;
+      t0 = t1;
       batch_ttm(src, src_scl, L, n, R, Us, r, rp, stage, cap, dst32, dst64, unscale);
       __syncthreads();
+      t1 = clock64();
+      cyc[3] += t1 - t0;
+      t0 = t1;
       src = dst32;
       src_scl = 1.f;
       cur[m] = r;
@@ -691,6 +710,7 @@ __global__ void __launch_bounds__(kBThreads) batch_sthosvd_kernel(BatchArgs a) {
       O->norm2 = norm2;
       O->sse_trunc = used;
       O->status = status;
+      for (int i = 0; i < 4; ++i) O->cycles[i] = cyc[i];
     }
     __syncthreads();
   }
@@ -1051,6 +1071,16 @@ extern "C" int atc_batch_get_stats(const atc_batch* b, int index, double* norm2,
   if (sweeps)
     for (int i = 0; i < b->d; ++i) sweeps[i] = o.sweeps[i];
   if (status) *status = o.status;
+  return ATC_OK;
+}
+
+extern "C" int atc_batch_get_profile(const atc_batch* b, int index, int64_t* cycles, int* rounds) {
+  if (!b || index < 0 || index >= b->count) return fail(ATC_EINVAL, "atc_batch_get_profile: bad arguments");
+  const BatchOut& o = b->hout[index];
+  if (cycles)
+    for (int i = 0; i < 4; ++i) cycles[i] = o.cycles[i];
+  if (rounds)
+    for (int i = 0; i < b->d; ++i) rounds[i] = o.rounds[i];
   return ATC_OK;
 }
 
