@@ -38,7 +38,7 @@ namespace atc {
 
 namespace {
 
-constexpr int kBThreads = 256;
+constexpr int kBThreads = 512;
 constexpr int kBMaxN = 112;        // 16 n^2 bytes of shared memory (G and V in double-float)
 constexpr int kBMaxD = 8;
 constexpr int kGramKC = 64;        // staged columns per Gram chunk
@@ -181,10 +181,14 @@ __device__ void batch_gram(const float* __restrict__ src, float scl, int64_t L, 
                            double* __restrict__ Ad, float* __restrict__ stage) {
   const int T = (n + TM - 1) / TM;
   const int U = T * (T + 1) / 2;
-  int KS = (int)blockDim.x / U;
-  if (KS < 1) KS = 1;
-  if (KS > 16) KS = 16;
   const int SP = T * TM;  // stage row stride (rows >= n stay zero)
+  // k-split groups: as many as the CTA has threads for, at most 16, and as
+  // many as their FP64 partials fit beside the stage in the second region
+  int KS = (int)blockDim.x / U;
+  const int room = (int)(((size_t)8 * kBMaxN * kBMaxN - (size_t)4 * (kGramKC * SP + 2)) / ((size_t)8 * U * TM * TM));
+  if (KS > room) KS = room;
+  if (KS > 16) KS = 16;
+  if (KS < 1) KS = 1;
   const int tid = threadIdx.x;
   for (int e = tid; e < n * n; e += blockDim.x) Ad[e] = 0.0;
   for (int e = tid; e < kGramKC * SP; e += blockDim.x) stage[e] = 0.f;
@@ -285,12 +289,11 @@ __host__ __device__ __forceinline__ bool gram_tm_fits(int tm, int n, int threads
 
 __device__ void batch_gram_dispatch(int tm, const float* src, float scl, int64_t L, int n, int64_t R, double* Ad,
                                     float* stage) {
-  while (tm < 6 && !gram_tm_fits(tm, n, blockDim.x)) ++tm;
+  while (tm < 5 && !gram_tm_fits(tm, n, blockDim.x)) ++tm;
   switch (tm) {
     case 2: batch_gram<2>(src, scl, L, n, R, Ad, stage); break;
     case 3: batch_gram<3>(src, scl, L, n, R, Ad, stage); break;
     case 5: batch_gram<5>(src, scl, L, n, R, Ad, stage); break;
-    case 6: batch_gram<6>(src, scl, L, n, R, Ad, stage); break;
     default: batch_gram<4>(src, scl, L, n, R, Ad, stage); break;
   }
 }
@@ -781,7 +784,7 @@ int batch_tune(cudaStream_t s, int* table_out) {
   for (int nb = 16; nb <= kBMaxN; nb += 8) {
     float best = 1e30f;
     int bt = tab[nb];
-    for (int tm : {2, 3, 4, 5, 6}) {
+    for (int tm : {2, 3, 4, 5}) {
       if (!gram_tm_fits(tm, nb, kBThreads)) continue;
       float ms = 0.f;
       int rc = ATC_OK;
@@ -789,8 +792,7 @@ int batch_tune(cudaStream_t s, int* table_out) {
         case 2: rc = probe_one<2>(x, nb, K, sink, grid, s, &ms); break;
         case 3: rc = probe_one<3>(x, nb, K, sink, grid, s, &ms); break;
         case 4: rc = probe_one<4>(x, nb, K, sink, grid, s, &ms); break;
-        case 5: rc = probe_one<5>(x, nb, K, sink, grid, s, &ms); break;
-        default: rc = probe_one<6>(x, nb, K, sink, grid, s, &ms); break;
+        default: rc = probe_one<5>(x, nb, K, sink, grid, s, &ms); break;
       }
       if (rc) return rc;
       if (ms < best) {

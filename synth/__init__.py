@@ -17,6 +17,11 @@ Isotropic-PT/V, ...), none of which is available here:
   mixed by spatially smooth abundance maps (softmax of low-passed Gaussian
   noise), plus 1% Gaussian noise (a Moffett-Field-shaped cube).
 * ``batched_lowrank`` -- many small uneven tensors built like ``lowrank_tucker``.
+* ``turbulence``      -- n^3 float32 turbulence-like field: every wavevector
+  k != 0 of the grid with amplitude |k|^(-5/3) and a uniform random phase,
+  made real through the half spectrum (irfftn), normalised to RMS 1 (stands in
+  for the Isotropic-PT/V fields).  Built with torch on a CUDA device for the
+  1024^3 size (seeded Philox), with NumPy for small sizes.
 
 Every generator uses ``numpy.random.default_rng(seed)`` (PCG64), so the same
 seed gives the same bytes on x86 and on Arm.
@@ -31,6 +36,7 @@ __all__ = [
     "hyperspectral",
     "batched_lowrank",
     "random_core",
+    "turbulence",
     "WORKLOADS",
 ]
 
@@ -127,6 +133,43 @@ def random_core(shape, decay=0.25, seed=7, dtype=np.float64) -> np.ndarray:
     rng = np.random.default_rng(seed)
     idx = np.indices(shape).sum(axis=0).astype(np.float64)
     return np.ascontiguousarray(rng.standard_normal(shape) * np.power(2.0, -decay * idx), dtype=dtype)
+
+
+def _turbulence_spectrum_np(n, rng):
+    k = np.fft.fftfreq(n) * n
+    kr = np.fft.rfftfreq(n) * n
+    kk = np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + kr[None, None, :] ** 2)
+    amp = np.zeros_like(kk)
+    nz = kk > 0
+    amp[nz] = kk[nz] ** (-5.0 / 3.0)
+    phase = rng.uniform(0.0, 2.0 * np.pi, size=kk.shape)
+    return amp * np.exp(1j * phase)
+
+
+def turbulence(n=1024, seed=1004, device=None, dtype=np.float32):
+    """Real n^3 field with an |k|^(-5/3) amplitude spectrum and random phases,
+    RMS 1.  device=None: NumPy (small n, returns an ndarray); a torch CUDA
+    device: built there with a seeded generator (returns a torch tensor)."""
+    if device is None:
+        rng = np.random.default_rng(seed)
+        x = np.fft.irfftn(_turbulence_spectrum_np(n, rng), s=(n, n, n))
+        x /= np.sqrt(np.mean(x * x))
+        return np.ascontiguousarray(x, dtype=dtype)
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    k = torch.fft.fftfreq(n, device=device) * n
+    kr = torch.fft.rfftfreq(n, device=device) * n
+    kk = torch.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + kr[None, None, :] ** 2)
+    amp = torch.where(kk > 0, kk.clamp_min(1e-30) ** (-5.0 / 3.0), torch.zeros_like(kk))
+    del kk
+    phase = torch.rand(amp.shape, generator=g, device=device) * (2.0 * np.pi)
+    spec = torch.polar(amp, phase)
+    del amp, phase
+    x = torch.fft.irfftn(spec, s=(n, n, n))
+    del spec
+    x /= torch.sqrt(torch.mean(x.double() * x.double())).float()
+    return x.contiguous()
 
 
 WORKLOADS = {
