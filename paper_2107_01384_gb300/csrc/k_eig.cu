@@ -712,7 +712,7 @@ __device__ __forceinline__ double hash_start(uint32_t a, uint32_t b) {
 // deterministic pseudo-random start vectors, three solves.  The LU factors and
 // the iterate live in shared memory: the recurrences are sequential, so every
 // access sits on the critical path.  Close eigenvalues are re-orthogonalised
-// afterwards by mgs_group_kernel.
+// afterwards (CholQR2 per group, block Gram-Schmidt for large groups).
 __global__ void __launch_bounds__(32) invit_par_kernel(EigState st, int nvec) {
   extern __shared__ double smi[];
   const int j = blockIdx.x;
@@ -790,53 +790,18 @@ __global__ void __launch_bounds__(32) invit_par_kernel(EigState st, int nvec) {
   for (int i = threadIdx.x; i < n; i += 32) xo[i] = x[i];
 }
 
-// Modified Gram-Schmidt (two passes) inside every group of size > 1, then
-// normalisation of every vector; one CTA per group.
-__global__ void mgs_group_kernel(EigState st, const int* __restrict__ grp_start, const int* __restrict__ ngrp,
-                                 int gmin_exclusive) {
-  __shared__ double red[32];
-  if ((int)blockIdx.x >= *ngrp) return;
-  const int g0 = grp_start[blockIdx.x], g1 = grp_start[blockIdx.x + 1];
-  if (g1 - g0 <= gmin_exclusive) return;  // handled by cholqr_group_kernel
-  const int n = st.n;
-  for (int k = g0; k < g1; ++k) {
-    double* xk = st.z + (int64_t)k * n;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int i0 = g0; i0 < k; ++i0) {
-        const double* y = st.z + (int64_t)i0 * n;
-        double part = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) part += y[i] * xk[i];
-        const double dot = block_sum(part, red);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) xk[i] -= dot * y[i];
-        __syncthreads();
-      }
-    }
-    double part = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) part += xk[i] * xk[i];
-    const double nr = block_sum(part, red);
-    const double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) xk[i] *= inv;
-    __syncthreads();
-  }
-}
-
 // Orthonormalisation of every group of close eigenvalues by CholQR2: the
 // vectors of inverse iteration are already nearly orthonormal (well
 // conditioned), so two passes of  W = Z^T Z,  W = R^T R,  Z <- Z R^-1
 // reach orthonormality to rounding level, with parallel dot products instead
 // of a chain of Gram-Schmidt reductions.  One CTA per group of at most
-// kQrMax vectors (larger groups use mgs_group_kernel).
+// kQrMax vectors; larger groups are cut into blocks of kQrMax that are
+// orthonormalised in turn (block classical Gram-Schmidt, two passes, against
+// the earlier blocks, then CholQR2 inside the block: cholqr_range_kernel).
 constexpr int kQrMax = 48;
-__global__ void __launch_bounds__(256) cholqr_group_kernel(EigState st, const int* __restrict__ grp_start,
-                                                           const int* __restrict__ ngrp, int gmax) {
-  __shared__ double W[kQrMax * kQrMax];
-  if ((int)blockIdx.x >= *ngrp) return;
-  const int g0 = grp_start[blockIdx.x], g1 = grp_start[blockIdx.x + 1];
-  const int g = g1 - g0;
-  if (g > gmax) return;
-  const int n = st.n;
+// CholQR2 of the g <= kQrMax vectors Z + c * n (c < g), one CTA.
+__device__ void cholqr_block(double* __restrict__ Z, int g, int n, double* __restrict__ W) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  double* Z = st.z + (int64_t)g0 * n;  // column c of the group at Z + c * n
   for (int pass = 0; pass < 2; ++pass) {
     // W = Z^T Z (upper triangle), a warp per entry
     for (int e = warp; e < g * g; e += nw) {
@@ -879,6 +844,49 @@ __global__ void __launch_bounds__(256) cholqr_group_kernel(EigState st, const in
     }
     __syncthreads();
   }
+}
+
+// One CTA per group of at most gmax vectors.
+__global__ void __launch_bounds__(256) cholqr_group_kernel(EigState st, const int* __restrict__ grp_start,
+                                                           const int* __restrict__ ngrp, int gmax) {
+  __shared__ double W[kQrMax * kQrMax];
+  if ((int)blockIdx.x >= *ngrp) return;
+  const int g0 = grp_start[blockIdx.x], g1 = grp_start[blockIdx.x + 1];
+  const int g = g1 - g0;
+  if (g > gmax) return;
+  cholqr_block(st.z + (int64_t)g0 * st.n, g, st.n, W);
+}
+
+// CholQR2 of vectors k0 .. k1-1 (k1 - k0 <= kQrMax), one CTA.
+__global__ void __launch_bounds__(256) cholqr_range_kernel(EigState st, int k0, int k1) {
+  __shared__ double W[kQrMax * kQrMax];
+  cholqr_block(st.z + (int64_t)k0 * st.n, k1 - k0, st.n, W);
+}
+
+// Block Gram-Schmidt step against the earlier vectors g0 .. g0+np-1 of a group:
+// W[p][b] = <z_{g0+p}, z_{k0+b}> (a warp per entry, FP64) ...
+__global__ void __launch_bounds__(256) blk_dot_kernel(const double* __restrict__ z, int n, int g0, int np, int k0,
+                                                      int nb, double* __restrict__ W) {
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (e >= np * nb) return;
+  const int p = e / nb, b = e - p * nb;
+  const double* zp = z + (int64_t)(g0 + p) * n;
+  const double* zb = z + (int64_t)(k0 + b) * n;
+  double part = 0.0;
+  for (int i = lane; i < n; i += 32) part = fma(zp[i], zb[i], part);
+  part = warp_sum(part);
+  if (lane == 0) W[e] = part;
+}
+// ... then z_{k0+b} -= sum_p z_{g0+p} W[p][b] (a thread per entry of the block).
+__global__ void __launch_bounds__(256) blk_update_kernel(double* __restrict__ z, int n, int g0, int np, int k0,
+                                                         int nb, const double* __restrict__ W) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nb * n) return;
+  const int b = (int)(idx / n), i = (int)(idx - (int64_t)b * n);
+  double acc = z[(int64_t)(k0 + b) * n + i];
+  for (int p = 0; p < np; ++p) acc = fma(-z[(int64_t)(g0 + p) * n + i], W[p * nb + b], acc);
+  z[(int64_t)(k0 + b) * n + i] = acc;
 }
 
 __global__ void trace_g_kernel(const double* __restrict__ G, int n, double* __restrict__ out) {
@@ -1500,15 +1508,35 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
   int* ngrp = grp + nvec + 2;
   group_kernel<<<1, 32, 0, s>>>(st, nvec, grp, ngrp);
   ATC_LAUNCHED(1);
+  std::vector<int> hg((size_t)nvec + 2);
+  ATC_CUDA_TRY(cudaMemcpyAsync(hg.data(), grp, sizeof(int) * (nvec + 2), cudaMemcpyDeviceToHost, s));
   if (g_state_dd) invit_dd_kernel<<<nvec, 32, (sizeof(dd) * 5 + 1) * n, s>>>(st, nvec);
   else invit_par_kernel<<<nvec, 32, sizeof(double) * 6 * n, s>>>(st, nvec);
   ATC_LAUNCHED(1);
-  // groups are found on the device: CholQR2 handles groups of <= kQrMax vectors,
-  // the sequential Gram-Schmidt kernel the (rare) larger ones
+  // CholQR2 for the groups of <= kQrMax vectors (one CTA each) ...
   cholqr_group_kernel<<<nvec, 256, 0, s>>>(st, grp, ngrp, kQrMax);
   ATC_LAUNCHED(1);
-  mgs_group_kernel<<<nvec, 128, 0, s>>>(st, grp, ngrp, kQrMax);
-  ATC_LAUNCHED(1);
+  // ... and block Gram-Schmidt (two passes) + CholQR2 per block for the larger ones
+  int hn = 0;
+  ATC_CUDA_TRY(cudaMemcpyAsync(&hn, ngrp, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  double* W = st.lu;  // the LU scratch of inverse iteration is free again (stream order)
+  for (int q = 0; q < hn && q < nvec; ++q) {
+    const int g0 = hg[q], g1 = hg[q + 1];
+    if (g1 - g0 <= kQrMax) continue;
+    for (int k0 = g0; k0 < g1; k0 += kQrMax) {
+      const int nb = std::min(kQrMax, g1 - k0), np = k0 - g0;
+      for (int pass = 0; pass < 2; ++pass) {
+        if (np > 0) {
+          blk_dot_kernel<<<(np * nb + 7) / 8, 256, 0, s>>>(st.z, n, g0, np, k0, nb, W);
+          blk_update_kernel<<<(int)(((int64_t)nb * n + 255) / 256), 256, 0, s>>>(st.z, n, g0, np, k0, nb, W);
+          ATC_LAUNCHED(2);
+        }
+        cholqr_range_kernel<<<1, 256, 0, s>>>(st, k0, k0 + nb);
+        ATC_LAUNCHED(1);
+      }
+    }
+  }
   if (g_state_dd) {
     if (n <= 256) backtransform_dd_kernel<8><<<nvec, 32, 0, s>>>(st, nvec, v);
     else backtransform_dd_kernel<16><<<nvec, 32, 0, s>>>(st, nvec, v);
