@@ -107,3 +107,65 @@ def test_split_precision_adjoint(P, prec):
     assert np.abs(dG.cpu().numpy() - rG).max() <= 1e-5 * np.abs(rG).max()
     for a, b in zip(dU, rU):
         assert np.abs(a.cpu().numpy() - b).max() <= 1e-5 * np.abs(b).max()
+
+
+def _decoded_point(P, n):
+    """Core and factors decoded from a compressed stream of the turbulence-like
+    field at rel_eps 1e-3: the point where a decompression is differentiated
+    (residual ~ rel_eps ||X||)."""
+    import synth
+    from oracle import pipeline as OP
+    x = synth.turbulence(n, device=torch.device("cuda"))
+    c = P.atc_compress(x, 1e-3, precision=P.PREC_SPLIT_BF16)
+    h = OP.parse(c.stream_bytes())
+    ranks, perm = h["ranks"], h["perm"]
+    vec = P.atc_dequantize_core(h["core_stream"], int(np.prod(ranks)))
+    core = torch.permute(vec.reshape([ranks[p] for p in perm]), tuple(int(i) for i in np.argsort(perm))).contiguous()
+    facs = [torch.from_numpy(np.ascontiguousarray(u)).cuda() for u in h["factors"]]
+    return x, core.float(), [u.float() for u in facs]
+
+
+def _torch_expand(G, Us, skip=None):
+    y = G
+    for m in range(len(Us)):
+        if m != skip:
+            y = torch.movedim(torch.tensordot(Us[m], y, dims=([1], [m])), 0, m)
+    return y
+
+
+def test_decompression_gradient_turbulence(P):
+    """L = ||X_hat - X||^2 at the decoded point of a 128^3 turbulence-like field
+    (full multilinear rank): FP32 parameters, FP64 products (precision FP64):
+    gradients against the FP64 definitions.  X_hat is returned in FP32, so dY =
+    2 (X_hat - X) carries a rounding of ~2^-24 ||X|| against a residual of
+    ~1e-3 ||X||: relative gradient error ~1e-4 at most."""
+    x, core, facs = _decoded_point(P, 128)
+    G64, U64 = core.double(), [u.double() for u in facs]
+    dY = 2.0 * (_torch_expand(G64, U64) - x.double())
+    rG = dY
+    for m in range(3):
+        rG = torch.movedim(torch.tensordot(U64[m].t(), rG, dims=([1], [m])), 0, m)
+    rU = []
+    for k in range(3):
+        Z = _torch_expand(G64, U64, skip=k)
+        rU.append(torch.movedim(dY, k, 0).reshape(dY.shape[k], -1) @ torch.movedim(Z, k, 0).reshape(Z.shape[k], -1).t())
+    g = core.clone().requires_grad_(True)
+    us = [u.clone().requires_grad_(True) for u in facs]
+    loss = torch.sum((P.tucker_expand(g, us, precision=P.PREC_FP64) - x).double() ** 2)
+    loss.backward()
+    rel = lambda a, b: float(torch.linalg.vector_norm(a.double() - b) / torch.linalg.vector_norm(b))
+    assert rel(g.grad, rG) <= 1e-4
+    for u, r in zip(us, rU):
+        assert rel(u.grad, r) <= 1e-4
+    # central difference of the FP64 loss along a random direction against the FP64 gradient
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    vG = torch.randn(G64.shape, generator=gen, device="cuda", dtype=torch.float64)
+    vU = [torch.randn(u.shape, generator=gen, device="cuda", dtype=torch.float64) for u in U64]
+
+    def L(h):
+        return float(((_torch_expand(G64 + h * vG, [u + h * v for u, v in zip(U64, vU)]) - x.double()) ** 2).sum())
+    h = 1e-6 * float(torch.linalg.vector_norm(G64)) / float(torch.linalg.vector_norm(vG))
+    fd = (L(h) - L(-h)) / (2 * h)
+    an = float((rG * vG).sum()) + sum(float((r * v).sum()) for r, v in zip(rU, vU))
+    assert abs(fd - an) <= 1e-2 * abs(fd)
