@@ -78,6 +78,7 @@ enum ScratchSlot {
   SLOT_ADJ_A,          // adjoint / expansion chains
   SLOT_ADJ_B,
   SLOT_BATCH_TUNE,     // batched-path tile probe input
+  SLOT_COLSHIFT,       // per-column scale exponents of the split expansions
   SLOT_COUNT
 };
 

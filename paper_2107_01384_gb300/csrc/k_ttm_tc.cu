@@ -7,7 +7,9 @@
 // K = n.  The same kernel runs the expansion Y = U ._k X with B[a][b] = U[a][b],
 // and, in residual mode, sums (X' - U ._k Y)^2 instead of writing the product.
 // Both operands are cut into three integer slices (tc::slice3i): X on the
-// tensor's power-of-two scale, the factor on the scale 2^8 (|U| <= 1).  The
+// tensor's power-of-two scale (projections) or on one power of two per column
+// gamma (expansions: a row of the MMA sums inside one column, so the column's
+// scale factors out exactly), the factor on the scale 2^8 (|U| <= 1).  The
 // nine slice products go, by order s + t, into five TMEM accumulators.  By
 // Cauchy-Schwarz every partial sum of an order is below 2^16 sqrt(n) (a factor
 // column or row has norm <= 1), so for the sizes here the FP32 tensor-core
@@ -62,6 +64,7 @@ struct TtmArgs {
   const uint8_t* bw;     // [3 slices][nkt][apad][128 B] pre-swizzled
   void* y;               // (L, Atot, R)
   const SliceScale* xs;  // slice scale of x
+  const signed char* cshift;  // per-column (gamma) scale exponents, or nullptr: xs for every column
   int* err;
   int nstage;            // pipeline depth (<= 4)
   int rowmode;           // TM_ROW / TM_ROWVEC when R == 1
@@ -207,12 +210,17 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
         const int g = ct + kConvThreads * u;
         int m, q;
         if (MODE == TM_GEN) { m = g & 127; q = g >> 7; } else { m = g >> 3; q = g & 7; }
+        float scu = sc;
+        if (a.cshift) {
+          const int64_t gam = ((int64_t)blockIdx.x + (it / a.nkt) * gridDim.x) * 128 + m;
+          scu = (gam < LR) ? ldexpf(1.0f, (int)__ldg(a.cshift + gam)) : 0.f;
+        }
         uint32_t p0[4], p1[4], p2[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           float a0x, a1x, a2x, a0y, a1y, a2y;
-          slice3i(buf[u][2 * e] * sc, a0x, a1x, a2x);
-          slice3i(buf[u][2 * e + 1] * sc, a0y, a1y, a2y);
+          slice3i(buf[u][2 * e] * scu, a0x, a1x, a2x);
+          slice3i(buf[u][2 * e + 1] * scu, a0y, a1y, a2y);
           p0[e] = Pack<BF16>::two(a0x, a0y);
           p1[e] = Pack<BF16>::two(a1x, a1y);
           p2[e] = Pack<BF16>::two(a2x, a2y);
@@ -300,8 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
   } else {
     // ------------------------------------------------------------- epilogue
     // y = (sum_o 2^-8o acc_o) 2^-(shift + 8): one rounding, then exact power-of-two scaling
-    const int e_out = -(shift + 8);
-    const float f1 = ldexpf(1.0f, e_out / 2), f2 = ldexpf(1.0f, e_out - e_out / 2);
+    const int e_glob = -(shift + 8);
     TY* __restrict__ y = reinterpret_cast<TY*>(a.y);
     const TR* __restrict__ xr = reinterpret_cast<const TR*>(a.xres);
     float racc = 0.f;  // residual mode: this thread's sum of squares
@@ -318,6 +325,8 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
       const int64_t gam = mt * 128 + 32 * warp + lane;
       const bool valid = gam < LR;
       const int64_t l = valid ? gam / a.R : 0, c = valid ? gam - l * a.R : 0;
+      const int e_out = (a.cshift && valid) ? -((int)__ldg(a.cshift + gam) + 8) : e_glob;
+      const float f1 = ldexpf(1.0f, e_out / 2), f2 = ldexpf(1.0f, e_out - e_out / 2);
       TY* yo = y + (l * a.Atot + a.j0) * a.R + c;
       const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)ab * 256u;
 #pragma unroll 1
@@ -374,6 +383,45 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
 
 namespace atc {
 namespace {
+
+// Per-column scale exponents of the (L, K, R) input: column gamma = (l, c)
+// gets shift_gamma = 8 - E with max_i |x[l][i][c]| < 2^E, so that its values
+// times 2^shift_gamma stay below 2^8 (the slice range).  The sum of every MMA
+// row runs over i inside one column, so the column's power of two factors out
+// exactly; the epilogue removes it.  A zero column gets 0.
+__device__ __forceinline__ signed char col_shift_of(float m) {
+  if (!(m > 0.f)) return 0;
+  int E = 0;
+  frexpf(m, &E);  // m = f 2^E, f in [0.5, 1)
+  int sh = 8 - E;
+  sh = sh < -120 ? -120 : (sh > 120 ? 120 : sh);
+  return (signed char)sh;
+}
+template <typename TX>
+__global__ void col_shift_rows_kernel(const TX* __restrict__ x, int64_t L, int64_t K, signed char* __restrict__ cs) {
+  // R == 1: a warp per row l (contiguous)
+  const int lane = threadIdx.x & 31;
+  for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < L;
+       l += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    float m = 0.f;
+    for (int64_t i = lane; i < K; i += 32) m = fmaxf(m, fabsf((float)__ldg(x + l * K + i)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) cs[l] = col_shift_of(m);
+  }
+}
+template <typename TX>
+__global__ void col_shift_cols_kernel(const TX* __restrict__ x, int64_t L, int64_t K, int64_t R,
+                                      signed char* __restrict__ cs) {
+  // R > 1: a thread per column, consecutive threads on consecutive c (coalesced)
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L * R; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = g / R, c = g - l * R;
+    const TX* p = x + l * K * R + c;
+    float m = 0.f;
+    for (int64_t i = 0; i < K; ++i) m = fmaxf(m, fabsf((float)__ldg(p + i * R)));
+    cs[g] = col_shift_of(m);
+  }
+}
 
 // W tiles for the MMA B operand: W[a][b] = U[b][j0 + a] (projection) or
 // U[j0 + a][b] (expansion), cut into the three fixed-point slices on the
@@ -464,9 +512,12 @@ namespace {
 
 // Shared driver of the projection / expansion (res == nullptr) and of the
 // residual energy sum ||xres - U ._k X||^2 (res != nullptr, expansion only).
+// percol: per-column scale exponents for the data operand (expansions, whose
+// inputs -- cores and partly expanded cores -- span many orders of magnitude
+// across columns); otherwise one power of two for the whole tensor.
 int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r, int expand,
             int precision, void* y, cudaStream_t s, const SliceScale* xs, const void* xres, int xres_dtype,
-            double* res) {
+            double* res, bool percol) {
   const int64_t Atot = expand ? n : r;
   const int64_t Bdim = expand ? r : n;
   if (Bdim > 1024) return fail(ATC_EUNSUP, "split-precision TTM supports contraction length <= 1024 (got %lld)",
@@ -491,6 +542,19 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
   uint8_t* bw = nullptr;
   ATC_TRY(Scratch::get(SLOT_TTM_U, wb * nchunk + (size_t)8 * nchunk * (grid + 1) + 256, (void**)&bw));
   double* part = reinterpret_cast<double*>(bw + wb * nchunk);
+  signed char* cshift = nullptr;
+  if (percol && L * R > 0) {
+    ATC_TRY(Scratch::get(SLOT_COLSHIFT, (size_t)(L * R) + 256, (void**)&cshift));
+    const int blocks = 4 * g_nsm_ttm;
+    if (R == 1) {
+      if (xdtype == ATC_F32) col_shift_rows_kernel<float><<<blocks, 256, 0, s>>>((const float*)x, L, Bdim, cshift);
+      else col_shift_rows_kernel<double><<<blocks, 256, 0, s>>>((const double*)x, L, Bdim, cshift);
+    } else {
+      if (xdtype == ATC_F32) col_shift_cols_kernel<float><<<blocks, 256, 0, s>>>((const float*)x, L, Bdim, R, cshift);
+      else col_shift_cols_kernel<double><<<blocks, 256, 0, s>>>((const double*)x, L, Bdim, R, cshift);
+    }
+    ATC_LAUNCHED(1);
+  }
   {
     TtmArgs a;
     a.x = x;
@@ -505,6 +569,7 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
     a.mtiles = mtiles;
     a.y = y;
     a.xs = xs;
+    a.cshift = cshift;
     a.err = err;
     a.rowmode = (Bdim % 8 == 0) ? TM_ROWVEC : TM_ROW;
     a.xres = xres;
@@ -557,12 +622,12 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
 int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
                      int expand, int precision, void* y, int ydtype, cudaStream_t s, const SliceScale* xs) {
   if (ydtype != ATC_F32) return fail(ATC_EUNSUP, "split-precision TTM writes FP32 output");
-  return ttm_run(x, xdtype, L, n, R, u, r, expand, precision, y, s, xs, nullptr, 0, nullptr);
+  return ttm_run(x, xdtype, L, n, R, u, r, expand, precision, y, s, xs, nullptr, 0, nullptr, expand != 0);
 }
 
 int launch_ttm_residual(const float* y, int64_t L, int64_t r, int64_t R, const double* u, int64_t n, const void* x,
                         int xdtype, double* rho, cudaStream_t s) {
-  return ttm_run(y, ATC_F32, L, n, R, u, r, 1, ATC_PREC_SPLIT_BF16, nullptr, s, nullptr, x, xdtype, rho);
+  return ttm_run(y, ATC_F32, L, n, R, u, r, 1, ATC_PREC_SPLIT_BF16, nullptr, s, nullptr, x, xdtype, rho, true);
 }
 
 }  // namespace atc
