@@ -83,6 +83,7 @@ typedef struct {
   int64_t i_star;         /* breakpoint coefficient: 0..i_star carry planes >= p_star, the rest >= p_star+1 */
   int escalated_modes;    /* modes whose Gram was recomputed in FP64 by the precision check */
   double ms_norm, ms_gram, ms_eig, ms_ttm, ms_quant, ms_encode, ms_total; /* device time per phase (CUDA events) */
+  int subspace_modes;     /* split paths: modes whose eigenvectors came from subspace iteration + Rayleigh-Ritz */
 } atc_stats;
 
 typedef struct atc_compressed atc_compressed; /* opaque, library-owned until atc_free() */

@@ -17,8 +17,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "atc_internal.cuh"
@@ -201,6 +203,18 @@ int check_dims(const int64_t* dims, int ndim, int64_t* total) {
 // extra eigenvectors beyond the provisional rank of a split path, from which
 // the certified rank is chosen
 constexpr int kCertExtra = 4;
+// subspace iteration for the leading eigenvectors on the split paths
+constexpr int kSubK = 48;      // block columns
+constexpr int kSubIters = 1;   // iterations before Rayleigh-Ritz
+constexpr int kSubMargin = 4;  // columns kept beyond the largest certified candidate count
+bool subspace_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("ATC_SUBSPACE");
+    on = (e && e[0] == '0') ? 0 : 1;
+  }
+  return on == 1;
+}
 
 int gram_dispatch(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g, cudaStream_t s,
                   const SliceScale* xs = nullptr) {
@@ -560,14 +574,120 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
                               cudaMemcpyDeviceToDevice, s) != cudaSuccess)
           return bail(fail(ATC_ECUDA, "factor copy failed"));
       } else {
-        // FP64 tridiagonalisation, then only the largest K eigenvalues (more
-        // if the rank is not decided among them); tail(r) = trace(G) - sum_{j<r}
+        // Split paths: the sliced Gram is that of X rounded to 24-bit fixed
+        // point, summed in FP32 orders; its eigenvalues carry a small shift,
+        // far below what moves the eigenvectors but not always below the
+        // distance of the tail from the budget.  So the rank is certified on
+        // the tensor itself: with U the leading rh eigenvectors and
+        // Y = U^T ._m X (tensor cores),
+        //   tail(r) = ||X - U ._m Y||^2 + sum_{j >= r} ||Y_j||^2   (U orthonormal),
+        // which is second order in the rounding errors of Y and U.
+        // certify(): 1 = rank and factor set, 0 = it needs more than rh_cap
+        // candidate vectors, < 0 = error.
+        int he = 0;  // tensor-core wait flag, read with the host readbacks
+        auto certify = [&](int rh, int rh_cap, const std::function<int(int, double*)>& get_cand) -> int {
+          for (;;) {
+            double* cand = nullptr;
+            int rc2 = Scratch::get(SLOT_CAND, sizeof(double) * ((size_t)n * rh + rh + 8), (void**)&cand);
+            if (rc2) return rc2;
+            double* edev = cand + (size_t)n * rh;  // e[0..rh), then rho
+            rc2 = get_cand(rh, cand);
+            if (!rc2) rc2 = ttm_dispatch(curp, curdt, L, n, R, cand, rh, 0, opt.precision, next, idt, s, xs);
+            if (!rc2) rc2 = launch_ttm_residual((const float*)next, L, rh, R, cand, n, curp, curdt, edev + rh, s);
+            if (!rc2) rc2 = launch_row_energy((const float*)next, L, rh, R, edev, s);
+            if (rc2) return rc2;
+            std::vector<double> eh((size_t)rh + 1), t((size_t)rh + 1);
+            if (cudaMemcpyAsync(eh.data(), edev, sizeof(double) * (rh + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+              return fail(ATC_ECUDA, "residual readback failed");
+            rc2 = eig_check(s);
+            if (rc2) return rc2;
+            if (he) return fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)");
+            t[rh] = (rh == n) ? 0.0 : eh[rh];
+            for (int j = rh - 1; j >= 0; --j) t[j] = t[j + 1] + eh[j];
+            int rn = -1;
+            for (int rr = 1; rr <= rh; ++rr)
+              if (t[rr] <= budget) { rn = rr; break; }
+            if (rn < 0 && rh < n) {
+              const int nrh = (int)std::min<int64_t>(n, 2 * (int64_t)rh);
+              if (nrh > rh_cap) return 0;
+              rh = nrh;
+              continue;
+            }
+            if (rn < 0) rn = (int)n;
+            r = rn;
+            disc = t[rn];
+            if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
+              return fail(ATC_ENOMEM, "factor allocation failed");
+            if (cudaMemcpy2DAsync(c->factors[m], sizeof(double) * r, cand, sizeof(double) * rh, sizeof(double) * r, n,
+                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+              return fail(ATC_ECUDA, "factor copy failed");
+            if (r < rh && L > 1) {
+              // keep the leading r of the rh projected rows (for L == 1 they already form the prefix)
+              void* tgt = other(next, curp);
+              rc2 = launch_compact((const float*)next, L, rh, R, r, (float*)tgt, s);
+              if (rc2) return rc2;
+              next = tgt;
+            }
+            have_y = true;
+            return 1;
+          }
+        };
+        bool done = false;
+        // Split paths, n >= 64: the leading eigenvectors by subspace iteration
+        // (48 columns, 2 iterations, Rayleigh-Ritz) when the Ritz values show
+        // it has converged for the provisional rank; else the full solver.
+        if (opt.precision != ATC_PREC_FP64 && n >= 64 && subspace_enabled() &&
+            subspace_supported((int)n, (int)std::min<int64_t>(n, kSubK))) {
+          const int Ks = (int)std::min<int64_t>(n, kSubK), Ts = kSubIters;
+          std::vector<double> th((size_t)Ks);
+          double trs = 0.0;
+          rc = subspace_values(G, (int)n, Ks, Ts, th.data(), &trs, s);
+          if (rc) return bail(rc);
+          if (tc_err && cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return bail(fail(ATC_ECUDA, "error flag readback failed"));
+          rc = eig_check(s);
+          if (rc) return bail(rc);
+          if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
+          int rp = -1;
+          double acc = 0.0;
+          for (int rr = 1; rr <= Ks; ++rr) {
+            acc += th[rr - 1];
+            const double t = std::max(0.0, trs - acc);
+            if (t <= budget) { rp = rr; break; }
+          }
+          // the top-rp subspace has converged to about (|theta_K| / theta_rp)^T
+          const int nv = rp + kCertExtra;
+          if (rp >= 1 && rp < n && nv <= Ks - kSubMargin && th[rp - 1] > 0.0 &&
+              std::pow(std::fabs(th[Ks - 1]) / th[rp - 1], (double)Ts) <= 1e-6) {
+            double* Usub = nullptr;
+            rc = Scratch::get(SLOT_SUB_U, sizeof(double) * (size_t)n * nv, (void**)&Usub);
+            if (!rc) rc = subspace_vectors((int)n, Ks, nv, Usub, s);
+            if (rc) return bail(rc);
+            clk.mark(PH_EIG);
+            auto from_ritz = [&](int rh, double* cand) -> int {
+              if (cudaMemcpy2DAsync(cand, sizeof(double) * rh, Usub, sizeof(double) * nv, sizeof(double) * rh, n,
+                                    cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return fail(ATC_ECUDA, "candidate copy failed");
+              return ATC_OK;
+            };
+            rc = certify(nv, nv, from_ritz);
+            if (rc < 0) return bail(rc);
+            if (rc == 1) {
+              done = true;
+              ++st.subspace_modes;
+              clk.mark(PH_TTM);
+            }
+          }
+        }
+        if (!done) {
+        // tridiagonalisation, then only the largest K eigenvalues (more if
+        // the rank is not decided among them); tail(r) = trace(G) - sum_{j<r}
         // lambda_j in FP64.
         rc = launch_eig_tridiag(G, (int)n, ddev + 2, s, opt.precision != ATC_PREC_FP64);
         if (rc) return bail(rc);
         int K = (int)std::min<int64_t>(n, 48);
         double tr = 0.0;
-        int he = 0;  // tensor-core wait flag, read with the eigenvalues (one host sync)
         std::vector<double> lh;
         for (;;) {
           rc = launch_eig_more((int)n, K, lam, s);
@@ -595,70 +715,23 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         if (r < 1 || r > n) return bail(fail(ATC_ENUMERIC, "rank selection failed (r = %d)", r));
         if (opt.precision != ATC_PREC_FP64 && r < n) {
           clk.mark(PH_EIG);
-          // Split paths: the sliced Gram is that of X rounded to 24-bit fixed
-          // point, summed in FP32 orders; its eigenvalues carry a small shift,
-          // far below what moves the eigenvectors but not always below the
-          // distance of the tail from the budget.
-          // So the rank is certified on the tensor itself: with U the leading
-          // rh eigenvectors and Y = U^T ._m X (tensor cores),
-          //   tail(r) = ||X - U ._m Y||^2 + sum_{j >= r} ||Y_j||^2   (U orthonormal),
-          // which is second order in the rounding errors of Y and U.
-          int rh = (int)std::min<int64_t>(n, (int64_t)r + kCertExtra);
-          for (;;) {
+          auto from_eig = [&](int rh, double* cand) -> int {
             if (rh > K) {
-              rc = launch_eig_more((int)n, rh, lam, s);
-              if (rc) return bail(rc);
+              const int rc3 = launch_eig_more((int)n, rh, lam, s);
+              if (rc3) return rc3;
               K = rh;
             }
-            double* cand = nullptr;
-            rc = Scratch::get(SLOT_CAND, sizeof(double) * ((size_t)n * rh + rh + 8), (void**)&cand);
-            if (rc) return bail(rc);
-            double* edev = cand + (size_t)n * rh;  // e[0..rh), then rho
-            rc = launch_eig_vectors((int)n, rh, cand, s);
-            if (!rc) rc = ttm_dispatch(curp, curdt, L, n, R, cand, rh, 0, opt.precision, next, idt, s, xs);
-            if (!rc) rc = launch_ttm_residual((const float*)next, L, rh, R, cand, n, curp, curdt, edev + rh, s);
-            if (!rc) rc = launch_row_energy((const float*)next, L, rh, R, edev, s);
-            if (rc) return bail(rc);
-            std::vector<double> eh((size_t)rh + 1), t((size_t)rh + 1);
-            if (cudaMemcpyAsync(eh.data(), edev, sizeof(double) * (rh + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-              return bail(fail(ATC_ECUDA, "residual readback failed"));
-            rc = eig_check(s);
-            if (rc) return bail(rc);
-            if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
-            t[rh] = (rh == n) ? 0.0 : eh[rh];
-            for (int j = rh - 1; j >= 0; --j) t[j] = t[j + 1] + eh[j];
-            int rn = -1;
-            for (int rr = 1; rr <= rh; ++rr)
-              if (t[rr] <= budget) { rn = rr; break; }
-            if (rn < 0 && rh < n) {
-              rh = (int)std::min<int64_t>(n, 2 * (int64_t)rh);
-              continue;
-            }
-            if (rn < 0) rn = (int)n;
-            r = rn;
-            disc = t[rn];
-            if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
-              return bail(fail(ATC_ENOMEM, "factor allocation failed"));
-            if (cudaMemcpy2DAsync(c->factors[m], sizeof(double) * r, cand, sizeof(double) * rh, sizeof(double) * r, n,
-                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-              return bail(fail(ATC_ECUDA, "factor copy failed"));
-            if (r < rh && L > 1) {
-              // keep the leading r of the rh projected rows (for L == 1 they already form the prefix)
-              void* tgt = other(next, curp);
-              rc = launch_compact((const float*)next, L, rh, R, r, (float*)tgt, s);
-              if (rc) return bail(rc);
-              next = tgt;
-            }
-            have_y = true;
-            clk.mark(PH_TTM);
-            break;
-          }
+            return launch_eig_vectors((int)n, rh, cand, s);
+          };
+          rc = certify((int)std::min<int64_t>(n, (int64_t)r + kCertExtra), (int)n, from_eig);
+          if (rc < 0) return bail(rc);
+          clk.mark(PH_TTM);
         } else {
           if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
             return bail(fail(ATC_ENOMEM, "factor allocation failed"));
           rc = launch_eig_vectors((int)n, r, c->factors[m], s);
           if (rc) return bail(rc);
+        }
         }
       }
       clk.mark(PH_EIG);

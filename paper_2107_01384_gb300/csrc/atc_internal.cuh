@@ -79,6 +79,8 @@ enum ScratchSlot {
   SLOT_ADJ_B,
   SLOT_BATCH_TUNE,     // batched-path tile probe input
   SLOT_COLSHIFT,       // per-column scale exponents of the split expansions
+  SLOT_SUBSPACE,       // subspace-iteration blocks
+  SLOT_SUB_U,          // subspace-iteration Ritz vectors
   SLOT_COUNT
 };
 
@@ -139,6 +141,15 @@ bool eig32_supported(int n);
 bool eig32_enabled();
 int eig32_values(const double* G, int n, std::vector<double>* lam_host, double* trace, cudaStream_t s);
 int eig32_refine(int m, double* lam_dev, double* v_dev, int nvec, std::vector<double>* lam_top, cudaStream_t s);
+// Leading eigenpairs of a symmetric PSD n x n FP64 matrix by subspace iteration
+// (T iterations of a K-column block, K <= min(64, n), n K doubles in shared
+// memory) and Rayleigh-Ritz.  subspace_values: theta_host[K] <- Ritz values
+// (descending), *trace_host <- trace(G), valid once the stream is synchronised;
+// subspace_vectors (next call of the eigensolver): U_dev (n x nvec row-major)
+// <- the leading nvec Ritz vectors.
+bool subspace_supported(int n, int K);
+int subspace_values(const double* G, int n, int K, int T, double* theta_host, double* trace_host, cudaStream_t s);
+int subspace_vectors(int n, int K, int nvec, double* U_dev, cudaStream_t s);
 int tc_error_flag(int** flag);  // device error word of the tensor-core kernels (zeroed by the caller)
 
 // quantizer / encoder (k_quant.cu)
