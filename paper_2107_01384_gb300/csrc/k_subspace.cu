@@ -155,14 +155,16 @@ __device__ dd dd_block_sum(dd v, dd* red) {
 }
 // sum_{i >= i0} a[i] b[i] over a warp, two interleaved accumulators
 __device__ __forceinline__ dd dd_dot_from(const dd* __restrict__ a, const dd* __restrict__ b, int i0, int n, int lane) {
-  dd d0 = dd{0.f, 0.f}, d1 = dd{0.f, 0.f};
+  dd d0 = dd{0.f, 0.f}, d1 = dd{0.f, 0.f}, d2 = dd{0.f, 0.f}, d3 = dd{0.f, 0.f};
   int i = i0 + lane;
-  for (; i + 32 < n; i += 64) {
+  for (; i + 96 < n; i += 128) {
     d0 = dd_add(d0, dd_mul(a[i], b[i]));
     d1 = dd_add(d1, dd_mul(a[i + 32], b[i + 32]));
+    d2 = dd_add(d2, dd_mul(a[i + 64], b[i + 64]));
+    d3 = dd_add(d3, dd_mul(a[i + 96], b[i + 96]));
   }
-  if (i < n) d0 = dd_add(d0, dd_mul(a[i], b[i]));
-  return dd_warp_sum_l(dd_add(d0, d1));
+  for (; i < n; i += 32) d0 = dd_add(d0, dd_mul(a[i], b[i]));
+  return dd_warp_sum_l(dd_add(dd_add(d0, d1), dd_add(d2, d3)));
 }
 // c[i] -= d * v[i] for i > j, c[j] -= d (v_j = 1)
 __device__ __forceinline__ void dd_reflect(dd* __restrict__ c, const dd* __restrict__ v, dd d, int j, int n, int lane) {
