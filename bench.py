@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=list(PRECISIONS))
     ap.add_argument("--eps", type=float, default=1e-3)
+    ap.add_argument("--block-size", type=int, default=0,
+                    help="encoder block size (0 = automatic: >= 16 blocks, 512..4096 coefficients)")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
@@ -206,7 +208,7 @@ def run_ours(args, world, rank, local):
     out = torch.empty_like(xd)
 
     def step(precision):
-        c = P.atc_compress(xd, args.eps, precision=precision, stream=stream)
+        c = P.atc_compress(xd, args.eps, precision=precision, block_size=args.block_size, stream=stream)
         s = c.stream_bytes()
         opt = P.Options()
         P.lib().atc_default_options(P.C.byref(opt))
@@ -387,6 +389,7 @@ def run_ours(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "rel_eps": args.eps, "precision": args.precision,
                        "step": "atc_compress + atc_decompress", "l2": "flushed (256 MB write) before each timed step",
+                       "block_size": stats[-1].get("block_size"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "ranks": ranks, "achieved_rel_err": re, "stream_bytes": len(s),
             "subspace_modes": stats[-1].get("subspace_modes", 0),

@@ -63,7 +63,8 @@ typedef struct {
   int precision;         /* atc_precision; default ATC_PREC_FP64 */
   int rank_rule;         /* atc_rank_rule; default ATC_RANK_STATIC */
   const int* mode_order; /* processing order (permutation of 0..ndim-1) or NULL = increasing length (Section 4.1.1) */
-  int block_size;        /* coefficients per encoder block (Section 4.2); multiple of 32 in [32, 65535]; default 4096 */
+  int block_size;        /* coefficients per encoder block (Section 4.2); multiple of 32 in [32, 65535], or 0 = automatic
+                            (a multiple of 32 giving >= 16 blocks, within [512, 4096]); default 4096 */
   void* stream;          /* cudaStream_t or NULL */
 } atc_options;
 
@@ -84,6 +85,7 @@ typedef struct {
   int escalated_modes;    /* modes whose Gram was recomputed in FP64 by the precision check */
   double ms_norm, ms_gram, ms_eig, ms_ttm, ms_quant, ms_encode, ms_total; /* device time per phase (CUDA events) */
   int subspace_modes;     /* split paths: modes whose eigenvectors came from subspace iteration + Rayleigh-Ritz */
+  int block_size;         /* encoder block size used */
 } atc_stats;
 
 typedef struct atc_compressed atc_compressed; /* opaque, library-owned until atc_free() */

@@ -61,7 +61,7 @@ class Stats(C.Structure):
                 ("k", C.c_int), ("p_star", C.c_int), ("i_star", C.c_int64), ("escalated_modes", C.c_int),
                 ("ms_norm", C.c_double), ("ms_gram", C.c_double), ("ms_eig", C.c_double),
                 ("ms_ttm", C.c_double), ("ms_quant", C.c_double), ("ms_encode", C.c_double),
-                ("ms_total", C.c_double), ("subspace_modes", C.c_int)]
+                ("ms_total", C.c_double), ("subspace_modes", C.c_int), ("block_size", C.c_int)]
 
 
 _lib = None

@@ -419,7 +419,8 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   if (!(opt.rtmss >= 0.0 && opt.rtmss <= 1.0)) return fail(ATC_EINVAL, "rtmss must lie in [0, 1]");
   if (opt.precision < 0 || opt.precision > 2) return fail(ATC_EINVAL, "bad precision");
   if (opt.rank_rule != ATC_RANK_STATIC && opt.rank_rule != ATC_RANK_ADAPTIVE) return fail(ATC_EINVAL, "bad rank rule");
-  if (opt.block_size < 32 || opt.block_size > 65535 || (opt.block_size % 32)) return fail(ATC_EINVAL, "bad block_size");
+  if (opt.block_size != 0 && (opt.block_size < 32 || opt.block_size > 65535 || (opt.block_size % 32)))
+    return fail(ATC_EINVAL, "bad block_size");
   const int d = ndim;
   std::vector<int> order(d);
   if (opt.mode_order) {
@@ -773,7 +774,15 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   // with FP32-accumulation and split-residual perturbations; half a percent of
   // the target is held back from the quantizer so the total stays <= rel_eps.
   const double margin = (opt.precision == ATC_PREC_FP64) ? 0.0 : 0.005 * st.target_sse;
-  rc = quantize_encode(vec, ncore, st.target_sse - used - margin, opt.block_size, s, &section, &qr, &msq, &mse);
+  // block_size 0: enough blocks for the GPU's independent (block, plane) streams (Section 4.2 asks for
+  // at least as many blocks as workers): a multiple of 32 giving >= 16 blocks, within [512, 4096]
+  int bsz = opt.block_size;
+  if (bsz == 0) {
+    const int64_t want = ((ncore + 15) / 16 + 31) / 32 * 32;
+    bsz = (int)std::min<int64_t>(4096, std::max<int64_t>(512, want));
+  }
+  st.block_size = bsz;
+  rc = quantize_encode(vec, ncore, st.target_sse - used - margin, bsz, s, &section, &qr, &msq, &mse);
   if (rc) return bail(rc);
   clk.mark(PH_QUANT);
   st.ms_quant = msq;

@@ -261,3 +261,24 @@ def test_pipeline_hyperspectral_split(P, cube, prec):
     xh = P.atc_decompress(c.stream_bytes(), out_dtype=torch.float32, precision=prec).cpu().numpy()
     re = np.linalg.norm(cube.astype(np.float64) - xh) / np.linalg.norm(cube.astype(np.float64))
     assert 0.98e-2 <= re <= 1e-2, re
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pipeline_automatic_block_size(P, prec):
+    """block_size 0: a multiple of 32 giving >= 16 blocks within [512, 4096]; the
+    core section is byte-identical to the oracle's at that block size."""
+    x = synth.gaussian_bumps(n=128, nbumps=16, seed=31)
+    c = P.atc_compress(cuda(x), 1e-3, precision=prec, block_size=0)
+    st = c.stats()
+    ncore = int(np.prod(c.ranks()))
+    want = ((ncore + 15) // 16 + 31) // 32 * 32
+    assert st["block_size"] == min(4096, max(512, want))
+    core = c.core().cpu().numpy()
+    vec = np.ascontiguousarray(np.transpose(core, st["storage_order"])).ravel()
+    stream = c.stream_bytes()
+    margin = 0.0 if prec == 0 else 0.005 * st["target_sse"]
+    sec, _ = OQ.compress_core(vec, st["target_sse"] - st["sse_trunc"] - margin, st["block_size"])
+    assert OP.parse(stream)["core_stream"] == sec
+    xo = OP.decompress(stream)
+    xh = P.atc_decompress(stream).cpu().numpy()
+    assert np.linalg.norm(xo - xh) <= 1e-9 * np.linalg.norm(x)
