@@ -356,9 +356,9 @@ def run_ours(args, world, rank, local):
             K = 40
             fl = sum(2 * 2.0 * dims[m] ** 2 * K + 6.0 * dims[m] * K * K + 4.0 / 3.0 * K ** 3
                      + 2.0 * dims[m] * K * (ranks[m] + 4) for m in order)
-            kern = ("sub_gemm_kernel, sub_hqr_kernel (double-float Householder QR), sub_proj_kernel, "
-                    "tridiag_cluster_dd_kernel / msect_dd_kernel / invit_dd_kernel / cholqr_group_kernel / "
-                    "backtransform_dd_kernel on the 40 x 40 Rayleigh-Ritz matrix, sub_rotate_kernel")
+            kern = ("sub_gemm_kernel, sub_qr_kernel (blocked double-float Householder QR), sub_qform_kernel, "
+                    "sub_proj_kernel, rr_kernel (one-CTA double-float Rayleigh-Ritz on the 40 x 40 matrix: "
+                    "tridiagonalisation, Sturm multisection, provisional rank, inverse iteration), sub_rotate_kernel")
             unit = "TFLOP/s (FP64-class: subspace iteration + Rayleigh-Ritz, formula in bench.py)"
             why = "a chain of dependent QR and tridiagonalisation steps on small matrices (latency-bound)"
         else:

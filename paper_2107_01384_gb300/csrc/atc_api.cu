@@ -21,6 +21,7 @@
 #include <mutex>
 #include <string>
 #include <functional>
+#include <chrono>
 #include <vector>
 
 #include "atc_internal.cuh"
@@ -36,13 +37,23 @@ int trace_enabled() {
   static int v = -1;
   if (v < 0) {
     const char* e = getenv("ATC_TRACE");
-    v = (e && e[0] == '1') ? 1 : 0;
+    v = (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 0;
   }
   return v;
 }
+// ATC_TRACE=1: synchronise and report the status after every launch site;
+// ATC_TRACE=2: also the host time since the previous trace point (kernel time
+// plus launch overhead, for locating slow launches)
 int trace_point(const char* file, int line) {
+  static auto last = std::chrono::steady_clock::now();
   cudaError_t e = cudaDeviceSynchronize();
-  fprintf(stderr, "[atc trace] %s:%d -> %s\n", file, line, cudaGetErrorString(e));
+  const auto now = std::chrono::steady_clock::now();
+  if (trace_enabled() == 2)
+    fprintf(stderr, "[atc trace] %s:%d -> %s %.1f us\n", file, line, cudaGetErrorString(e),
+            std::chrono::duration<double, std::micro>(now - last).count());
+  else
+    fprintf(stderr, "[atc trace] %s:%d -> %s\n", file, line, cudaGetErrorString(e));
+  last = std::chrono::steady_clock::now();
   fflush(stderr);
   if (e != cudaSuccess) return fail(ATC_ECUDA, "trace %s:%d: %s", file, line, cudaGetErrorString(e));
   return ATC_OK;
@@ -636,35 +647,27 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         };
         bool done = false;
         // Split paths, n >= 64: the leading eigenvectors by subspace iteration
-        // (48 columns, 2 iterations, Rayleigh-Ritz) when the Ritz values show
-        // it has converged for the provisional rank; else the full solver.
+        // (40 columns, 1 iteration, Rayleigh-Ritz); the Rayleigh-Ritz kernel
+        // takes the provisional rank and passes the subspace when the Ritz
+        // values show convergence for it; else the full solver.
         if (opt.precision != ATC_PREC_FP64 && n >= 64 && subspace_enabled() &&
             subspace_supported((int)n, (int)std::min<int64_t>(n, kSubK))) {
           const int Ks = (int)std::min<int64_t>(n, kSubK), Ts = kSubIters;
+          const int nmax = Ks - kSubMargin;
           std::vector<double> th((size_t)Ks);
           double trs = 0.0;
-          rc = subspace_values(G, (int)n, Ks, Ts, th.data(), &trs, s);
+          int dec[3] = {0, 0, 0};
+          double* Usub = nullptr;
+          rc = Scratch::get(SLOT_SUB_U, sizeof(double) * (size_t)n * nmax, (void**)&Usub);
+          if (!rc) rc = subspace_solve(G, (int)n, Ks, Ts, budget, kCertExtra, nmax, 1e-6, Usub, th.data(), &trs, dec, s);
           if (rc) return bail(rc);
           if (tc_err && cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return bail(fail(ATC_ECUDA, "error flag readback failed"));
           rc = eig_check(s);
           if (rc) return bail(rc);
           if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
-          int rp = -1;
-          double acc = 0.0;
-          for (int rr = 1; rr <= Ks; ++rr) {
-            acc += th[rr - 1];
-            const double t = std::max(0.0, trs - acc);
-            if (t <= budget) { rp = rr; break; }
-          }
-          // the top-rp subspace has converged to about (|theta_K| / theta_rp)^T
-          const int nv = rp + kCertExtra;
-          if (rp >= 1 && rp < n && nv <= Ks - kSubMargin && th[rp - 1] > 0.0 &&
-              std::pow(std::fabs(th[Ks - 1]) / th[rp - 1], (double)Ts) <= 1e-6) {
-            double* Usub = nullptr;
-            rc = Scratch::get(SLOT_SUB_U, sizeof(double) * (size_t)n * nv, (void**)&Usub);
-            if (!rc) rc = subspace_vectors((int)n, Ks, nv, Usub, s);
-            if (rc) return bail(rc);
+          if (dec[2] && dec[1] >= 1 && dec[1] <= nmax) {
+            const int nv = dec[1];
             clk.mark(PH_EIG);
             auto from_ritz = [&](int rh, double* cand) -> int {
               if (cudaMemcpy2DAsync(cand, sizeof(double) * rh, Usub, sizeof(double) * nv, sizeof(double) * rh, n,

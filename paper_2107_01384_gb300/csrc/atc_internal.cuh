@@ -142,14 +142,21 @@ bool eig32_enabled();
 int eig32_values(const double* G, int n, std::vector<double>* lam_host, double* trace, cudaStream_t s);
 int eig32_refine(int m, double* lam_dev, double* v_dev, int nvec, std::vector<double>* lam_top, cudaStream_t s);
 // Leading eigenpairs of a symmetric PSD n x n FP64 matrix by subspace iteration
-// (T iterations of a K-column block, K <= min(64, n), n K doubles in shared
-// memory) and Rayleigh-Ritz.  subspace_values: theta_host[K] <- Ritz values
-// (descending), *trace_host <- trace(G), valid once the stream is synchronised;
-// subspace_vectors (next call of the eigensolver): U_dev (n x nvec row-major)
-// <- the leading nvec Ritz vectors.
+// (T iterations of a K-column block, K <= min(64, n), n K double-floats in
+// shared memory) and Rayleigh-Ritz (k_subspace.cu, k_rr.cu).  Once the stream
+// is synchronised: theta_host[K] = Ritz values (descending), *trace_host =
+// trace(G), decision_host = {rp, nv, passed}: rp the smallest rank whose tail
+// trace(G) - sum_{j<rp} theta_j is <= budget, passed = 1 when rp >= 1,
+// rp < n, nv = rp + extra <= nmax and (|theta_K| / theta_rp)^T <= conv; then
+// U_dev (n x nv row-major, capacity n x nmax) holds the leading nv Ritz vectors.
 bool subspace_supported(int n, int K);
-int subspace_values(const double* G, int n, int K, int T, double* theta_host, double* trace_host, cudaStream_t s);
-int subspace_vectors(int n, int K, int nvec, double* U_dev, cudaStream_t s);
+int subspace_solve(const double* G, int n, int K, int T, double budget, int extra, int nmax, double conv,
+                   double* U_dev, double* theta_host, double* trace_host, int* decision_host, cudaStream_t s);
+// the Rayleigh-Ritz kernel alone (k_rr.cu): B K x K FP64, trace_dev a device
+// scalar; theta_dev (K), decision_dev (3 ints) and Y_dev (K x nv) on the device
+size_t rr_smem_bytes(int K, int nmax);  // dynamic shared memory of the Rayleigh-Ritz kernel
+int launch_rr_small(const double* B, int K, int n, const double* trace_dev, double budget, int extra, int nmax,
+                    double conv, int T, double* theta_dev, int* decision_dev, double* Y_dev, cudaStream_t s);
 int tc_error_flag(int** flag);  // device error word of the tensor-core kernels (zeroed by the caller)
 
 // quantizer / encoder (k_quant.cu)
