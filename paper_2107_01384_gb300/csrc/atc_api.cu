@@ -88,6 +88,8 @@ std::mutex g_arena_mu;
 std::vector<DevArena> g_arenas;
 }  // namespace
 
+long long g_scratch_serial = 0;  // bumped whenever any scratch slot is allocated or freed
+
 int Scratch::get(int slot, size_t bytes, void** out) {
   if (slot < 0 || slot >= SLOT_COUNT) return fail(ATC_EINVAL, "bad scratch slot");
   int dev = 0;
@@ -104,6 +106,7 @@ int Scratch::get(int slot, size_t bytes, void** out) {
       cudaFree(a.ptr[slot]);
       a.ptr[slot] = nullptr;
       a.cap[slot] = 0;
+      ++g_scratch_serial;
     }
     size_t want = bytes + bytes / 8;
     want = (want + 255) & ~(size_t)255;
@@ -115,6 +118,7 @@ int Scratch::get(int slot, size_t bytes, void** out) {
     }
     a.ptr[slot] = p;
     a.cap[slot] = want;
+    ++g_scratch_serial;
   }
   *out = a.ptr[slot];
   return ATC_OK;
@@ -132,6 +136,7 @@ int Scratch::release_all() {
     a.ptr[i] = nullptr;
     a.cap[i] = 0;
   }
+  ++g_scratch_serial;
   return ATC_OK;
 }
 
@@ -239,11 +244,47 @@ int ttm_dispatch(const void* x, int xdt, int64_t L, int64_t n, int64_t R, const 
   return launch_ttm_split(x, xdt, L, n, R, u, r, expand, precision, y, ydt, s, xs);
 }
 
+// Pinned host memory for the small per-mode readbacks (norm, decisions,
+// residual tails, error words): copies into it are truly asynchronous, so a
+// mode needs one stream synchronisation instead of one per pageable copy.
+// Layout: ints [0, 16) (0: grid-barrier flag, 1: tensor-core flag, 2..5: the
+// subspace decision), doubles from byte 64.
+struct PinnedReadback {
+  int* ints = nullptr;
+  double* dbl = nullptr;
+  size_t ndbl = 0;
+};
+int pinned_readback(size_t ndbl, PinnedReadback* out) {
+  static std::mutex mu;
+  static void* buf = nullptr;
+  static size_t cap = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  const size_t want = 64 + sizeof(double) * (ndbl < 64 ? 64 : ndbl);
+  if (cap < want) {
+    if (buf) {
+      ATC_CUDA_TRY(cudaDeviceSynchronize());
+      cudaFreeHost(buf);
+      buf = nullptr;
+      cap = 0;
+    }
+    ATC_CUDA_TRY(cudaHostAlloc(&buf, want, cudaHostAllocPortable));
+    cap = want;
+  }
+  out->ints = static_cast<int*>(buf);
+  out->dbl = reinterpret_cast<double*>(static_cast<char*>(buf) + 64);
+  out->ndbl = (cap - 64) / sizeof(double);
+  return ATC_OK;
+}
+
+// Synchronise the stream and check the grid-barrier flag of the FP64
+// tridiagonalisation (copied asynchronously into the pinned buffer first).
 int eig_check(cudaStream_t s) {
-  int err = 0;
+  PinnedReadback pb;
+  ATC_TRY(pinned_readback(0, &pb));
+  int* fl = eig_error_flag_dev();
+  if (fl) ATC_CUDA_TRY(cudaMemcpyAsync(&pb.ints[0], fl, sizeof(int), cudaMemcpyDeviceToHost, s));
   ATC_CUDA_TRY(cudaStreamSynchronize(s));
-  ATC_TRY(eig_read_error(&err));
-  if (err) return fail(ATC_ETIMEOUT, "grid barrier of the tridiagonalisation timed out");
+  if (fl && pb.ints[0]) return fail(ATC_ETIMEOUT, "grid barrier of the tridiagonalisation timed out");
   return ATC_OK;
 }
 
@@ -471,11 +512,13 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
     rc = launch_norm2(x_dev, dtype, N, dnorm, s);
     if (rc) return bail(rc);
     clk.mark(PH_NORM);
-    double h = 0.0;
-    if (cudaMemcpyAsync(&h, dnorm, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    PinnedReadback pb;
+    rc = pinned_readback(1, &pb);
+    if (rc) return bail(rc);
+    if (cudaMemcpyAsync(pb.dbl, dnorm, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return bail(fail(ATC_ECUDA, "norm readback failed"));
-    st.norm2 = h;
+    st.norm2 = pb.dbl[0];
     clk.mark(PH_OTHER);
   }
   if (!(st.norm2 == st.norm2) || st.norm2 > 1.7e308) return bail(fail(ATC_ENUMERIC, "input contains NaN or Inf"));
@@ -608,12 +651,17 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
             if (!rc2) rc2 = launch_ttm_residual((const float*)next, L, rh, R, cand, n, curp, curdt, edev + rh, s);
             if (!rc2) rc2 = launch_row_energy((const float*)next, L, rh, R, edev, s);
             if (rc2) return rc2;
-            std::vector<double> eh((size_t)rh + 1), t((size_t)rh + 1);
-            if (cudaMemcpyAsync(eh.data(), edev, sizeof(double) * (rh + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            std::vector<double> t((size_t)rh + 1);
+            PinnedReadback pb;
+            rc2 = pinned_readback((size_t)rh + 1, &pb);
+            if (rc2) return rc2;
+            const double* eh = pb.dbl;
+            if (cudaMemcpyAsync(pb.dbl, edev, sizeof(double) * (rh + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(&pb.ints[1], tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
               return fail(ATC_ECUDA, "residual readback failed");
             rc2 = eig_check(s);
             if (rc2) return rc2;
+            he = pb.ints[1];
             if (he) return fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)");
             t[rh] = (rh == n) ? 0.0 : eh[rh];
             for (int j = rh - 1; j >= 0; --j) t[j] = t[j + 1] + eh[j];
@@ -654,17 +702,16 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
             subspace_supported((int)n, (int)std::min<int64_t>(n, kSubK))) {
           const int Ks = (int)std::min<int64_t>(n, kSubK), Ts = kSubIters;
           const int nmax = Ks - kSubMargin;
-          std::vector<double> th((size_t)Ks);
-          double trs = 0.0;
-          int dec[3] = {0, 0, 0};
           double* Usub = nullptr;
+          PinnedReadback pb;
           rc = Scratch::get(SLOT_SUB_U, sizeof(double) * (size_t)n * nmax, (void**)&Usub);
-          if (!rc) rc = subspace_solve(G, (int)n, Ks, Ts, budget, kCertExtra, nmax, 1e-6, Usub, th.data(), &trs, dec, s);
+          if (!rc) rc = pinned_readback(0, &pb);
+          // decision {rp, nv, passed, tensor-core error word} lands in pb.ints[2..5]
+          if (!rc) rc = subspace_solve(G, (int)n, Ks, Ts, budget, kCertExtra, nmax, 1e-6, tc_err, Usub, &pb.ints[2], s);
           if (rc) return bail(rc);
-          if (tc_err && cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-            return bail(fail(ATC_ECUDA, "error flag readback failed"));
-          rc = eig_check(s);
-          if (rc) return bail(rc);
+          if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ATC_ECUDA, "stream synchronisation failed"));
+          const int dec[4] = {pb.ints[2], pb.ints[3], pb.ints[4], pb.ints[5]};
+          he = dec[3];
           if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
           if (dec[2] && dec[1] >= 1 && dec[1] <= nmax) {
             const int nv = dec[1];

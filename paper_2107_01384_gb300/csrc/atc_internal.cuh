@@ -42,6 +42,7 @@ int trace_point(const char* file, int line);
   } while (0)
 
 // Device scratch: a grow-only cached arena per device (cudaMalloc).
+extern long long g_scratch_serial;  // changes whenever scratch memory is allocated or freed
 struct Scratch {
   // Returns a device pointer to at least `bytes` bytes of slot `slot`, 256-B aligned.
   static int get(int slot, size_t bytes, void** ptr);
@@ -81,6 +82,7 @@ enum ScratchSlot {
   SLOT_COLSHIFT,       // per-column scale exponents of the split expansions
   SLOT_SUBSPACE,       // subspace-iteration blocks
   SLOT_SUB_U,          // subspace-iteration Ritz vectors
+  SLOT_SUB_V0,         // subspace-iteration start frame (kept while n and K stay the same)
   SLOT_COUNT
 };
 
@@ -136,6 +138,7 @@ int launch_eig_tridiag(const double* g, int n, double* trace_dev, cudaStream_t s
 int launch_eig_more(int n, int K, double* lam, cudaStream_t s);
 int launch_rank_select(const double* lam, int n, double budget, int* r_dev, double* disc_dev, cudaStream_t s);
 int eig_read_error(int* err);
+int* eig_error_flag_dev();  // device word of the grid-barrier time-out flag, or nullptr
 // FP32-stage + FP64-refinement eigensolver (k_eig32.cu), n <= 256
 bool eig32_supported(int n);
 bool eig32_enabled();
@@ -143,20 +146,21 @@ int eig32_values(const double* G, int n, std::vector<double>* lam_host, double* 
 int eig32_refine(int m, double* lam_dev, double* v_dev, int nvec, std::vector<double>* lam_top, cudaStream_t s);
 // Leading eigenpairs of a symmetric PSD n x n FP64 matrix by subspace iteration
 // (T iterations of a K-column block, K <= min(64, n), n K double-floats in
-// shared memory) and Rayleigh-Ritz (k_subspace.cu, k_rr.cu).  Once the stream
-// is synchronised: theta_host[K] = Ritz values (descending), *trace_host =
-// trace(G), decision_host = {rp, nv, passed}: rp the smallest rank whose tail
-// trace(G) - sum_{j<rp} theta_j is <= budget, passed = 1 when rp >= 1,
-// rp < n, nv = rp + extra <= nmax and (|theta_K| / theta_rp)^T <= conv; then
-// U_dev (n x nv row-major, capacity n x nmax) holds the leading nv Ritz vectors.
+// shared memory) and Rayleigh-Ritz (k_subspace.cu, k_rr.cu).  Enqueues the
+// copy of decision_host[0..4) = {rp, nv, passed, *tc_err} (pinned host memory;
+// valid once the stream is synchronised): rp the smallest rank whose tail
+// trace(G) - sum_{j<rp} theta_j is <= budget, passed = 1 when rp >= 1, rp < n,
+// nv = rp + extra <= nmax and (|theta_K| / theta_rp)^T <= conv; then U_dev
+// (n x nv row-major, capacity n x nmax) holds the leading nv Ritz vectors.
 bool subspace_supported(int n, int K);
 int subspace_solve(const double* G, int n, int K, int T, double budget, int extra, int nmax, double conv,
-                   double* U_dev, double* theta_host, double* trace_host, int* decision_host, cudaStream_t s);
+                   const int* tc_err, double* U_dev, int* decision_host, cudaStream_t s);
 // the Rayleigh-Ritz kernel alone (k_rr.cu): B K x K FP64, trace_dev a device
-// scalar; theta_dev (K), decision_dev (3 ints) and Y_dev (K x nv) on the device
+// scalar; theta_dev (K), decision_dev (4 ints) and Y_dev (K x nv) on the device
 size_t rr_smem_bytes(int K, int nmax);  // dynamic shared memory of the Rayleigh-Ritz kernel
 int launch_rr_small(const double* B, int K, int n, const double* trace_dev, double budget, int extra, int nmax,
-                    double conv, int T, double* theta_dev, int* decision_dev, double* Y_dev, cudaStream_t s);
+                    double conv, int T, const int* tc_err, double* theta_dev, int* decision_dev, double* Y_dev,
+                    cudaStream_t s);
 int tc_error_flag(int** flag);  // device error word of the tensor-core kernels (zeroed by the caller)
 
 // quantizer / encoder (k_quant.cu)

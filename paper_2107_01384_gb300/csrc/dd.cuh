@@ -14,7 +14,8 @@ namespace atc {
 // faster at an accuracy of about 2^-47 relative per operation.  Callers scale
 // their data by powers of two so that the float exponent range is never
 // approached.
-struct dd {
+// (8-byte aligned: a pair moves with one 64-bit load or store)
+struct __align__(8) dd {
   float hi, lo;
 };
 __device__ __forceinline__ dd ddf(float a) { return dd{a, 0.f}; }

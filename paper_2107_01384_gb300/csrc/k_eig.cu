@@ -1571,6 +1571,8 @@ int launch_rank_select(const double* lam, int n, double budget, int* r_dev, doub
   return ATC_OK;
 }
 
+int* eig_error_flag_dev() { return g_state.flags ? g_state.flags + 2 : nullptr; }
+
 int eig_read_error(int* err) {
   *err = 0;
   if (!g_state.flags) return ATC_OK;  // the FP64 tridiagonalisation has not run on this device

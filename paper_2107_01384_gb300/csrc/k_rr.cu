@@ -213,10 +213,39 @@ __device__ void rr_invit(const dd* __restrict__ d, const dd* __restrict__ e, int
   }
 }
 
+// One reflector of the back-transformation on this lane's rows (i0, i0 + 2, ...)
+// of vector z; the partner lane (lane ^ 16) holds the other rows.  Restrict-
+// qualified: the reflector rows and the vectors are disjoint parts of one
+// shared array.
+__device__ __forceinline__ void rr_bt_apply(const dd* __restrict__ hs, dd* __restrict__ z, int i0, int K, dd t,
+                                            bool act) {
+  const dd zero = dd{0.f, 0.f};
+  dd a0 = zero, a1 = zero;
+  int i = i0;
+  for (; i + 2 < K; i += 4) {
+    a0 = dd_add(a0, dd_mul(hs[i], z[i]));
+    a1 = dd_add(a1, dd_mul(hs[i + 2], z[i + 2]));
+  }
+  if (i < K) a0 = dd_add(a0, dd_mul(hs[i], z[i]));
+  dd dt = dd_add(a0, a1);
+  dt = dd_add(dt, rr_shfl(dt, 16));
+  const dd f = dd_mul(t, dt);
+  if (act) {
+    int i2 = i0;
+    for (; i2 + 2 < K; i2 += 4) {
+      const dd x0 = z[i2], x1 = z[i2 + 2], h0 = hs[i2], h1 = hs[i2 + 2];
+      z[i2] = dd_sub(x0, dd_mul(f, h0));
+      z[i2 + 2] = dd_sub(x1, dd_mul(f, h1));
+    }
+    if (i2 < K) z[i2] = dd_sub(z[i2], dd_mul(f, hs[i2]));
+  }
+}
+
 __global__ void __launch_bounds__(kRrThreads) rr_kernel(const double* __restrict__ B, int K, int n,
                                                         const double* __restrict__ trace_g, double budget, int extra,
-                                                        int nmax, double conv, int T, double* __restrict__ theta_out,
-                                                        int* __restrict__ decision, double* __restrict__ Y) {
+                                                        int nmax, double conv, int T, const int* __restrict__ tc_err,
+                                                        double* __restrict__ theta_out, int* __restrict__ decision,
+                                                        double* __restrict__ Y) {
   extern __shared__ dd sm[];
   const int P = K | 1;                          // odd pitches: row- and column-wise access are conflict-free
   dd* A = sm;                                   // K x P, lower triangle used
@@ -306,9 +335,10 @@ __global__ void __launch_bounds__(kRrThreads) rr_kernel(const double* __restrict
           s_d[c] = A[c * P + c];
           s_e[c] = A[(c + 1) * P + c];
         }
-      } else if (warp <= 8) {
-        // rows i >= s+2, columns s+2 .. i
-        for (int i = s + 2 + (warp - 1); i < K; i += 8) {
+      } else if ((warp & 3) != 0 && warp < 12) {
+        // rows i >= s+2, columns s+2 .. i: warps 1-3, 5-7, 9-11 (warp 0 keeps its SM sub-partition)
+        const int u = warp - 1 - (warp >> 2);
+        for (int i = s + 2 + u; i < K; i += 9) {
           const dd vi = v[i], wi = dd_sub(s_p[i], dd_mul(kc, vi));
           for (int k = s + 2 + lane; k <= i; k += 32) {
             const dd wk = dd_sub(s_p[k], dd_mul(kc, v[k]));
@@ -437,6 +467,7 @@ __global__ void __launch_bounds__(kRrThreads) rr_kernel(const double* __restrict
       decision[0] = rp;
       decision[1] = ok ? nv : 0;
       decision[2] = ok;
+      decision[3] = tc_err ? *tc_err : 0;
       s_nv = ok ? nv : 0;
     }
   }
@@ -498,20 +529,7 @@ __global__ void __launch_bounds__(kRrThreads) rr_kernel(const double* __restrict
       for (int s = K - 3; s >= 0; --s) {
         const dd t = s_tau[s];
         if (t.hi == 0.f) continue;
-        const dd* hs = H + s * K;
-        const int i0 = s + 1 + ((s + 1 + h) & 1);  // first row > s of this lane's parity
-        dd a0 = zero, a1 = zero;
-        int i = i0;
-        for (; i + 2 < K; i += 4) {
-          a0 = dd_add(a0, dd_mul(hs[i], z[i]));
-          a1 = dd_add(a1, dd_mul(hs[i + 2], z[i + 2]));
-        }
-        if (i < K) a0 = dd_add(a0, dd_mul(hs[i], z[i]));
-        dd dt = dd_add(a0, a1);
-        dt = dd_add(dt, rr_shfl(dt, 16));
-        const dd f = dd_mul(t, dt);
-        if (act)
-          for (int i2 = i0; i2 < K; i2 += 2) z[i2] = dd_sub(z[i2], dd_mul(f, hs[i2]));
+        rr_bt_apply(H + s * K, z, s + 1 + ((s + 1 + h) & 1), K, t, act);
       }
       // normalise, largest entry positive, write FP64
       dd q = zero;
@@ -549,7 +567,8 @@ size_t rr_smem_bytes(int K, int nmax) {
 }
 
 int launch_rr_small(const double* B, int K, int n, const double* trace_dev, double budget, int extra, int nmax,
-                    double conv, int T, double* theta_dev, int* decision_dev, double* Y_dev, cudaStream_t s) {
+                    double conv, int T, const int* tc_err, double* theta_dev, int* decision_dev, double* Y_dev,
+                    cudaStream_t s) {
   if (K < 1 || K > kRrMaxK || nmax < 1 || nmax > K || nmax > 32 * kRrVecWarps)
     return fail(ATC_EINVAL, "Rayleigh-Ritz solver: K = %d, nmax = %d unsupported", K, nmax);
   const size_t smem = rr_smem_bytes(K, nmax);
@@ -559,8 +578,8 @@ int launch_rr_small(const double* B, int K, int n, const double* trace_dev, doub
     ATC_CUDA_TRY(cudaFuncSetAttribute(rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024));
     attr = true;
   }
-  rr_kernel<<<1, kRrThreads, smem, s>>>(B, K, n, trace_dev, budget, extra, nmax, conv, T, theta_dev, decision_dev,
-                                        Y_dev);
+  rr_kernel<<<1, kRrThreads, smem, s>>>(B, K, n, trace_dev, budget, extra, nmax, conv, T, tc_err, theta_dev,
+                                        decision_dev, Y_dev);
   ATC_LAUNCHED(1);
   return ATC_OK;
 }

@@ -51,50 +51,66 @@ __global__ void sub_init_kernel(double* __restrict__ V, int n, int K) {
   }
 }
 
-// *ex = the exponent e with max_i G[i][i] * 2^-e in [0.5, 1) (G is PSD, so it
-// bounds |G|; 0 for a zero matrix): the scale of the double-float copy of G V
-__global__ void sub_scale_kernel(const double* __restrict__ G, int n, int* __restrict__ ex) {
-  double m = 0.0;
-  for (int i = threadIdx.x; i < n; i += 32) m = fmax(m, fabs(G[(int64_t)i * n + i]));
+// From the diagonal of G, one warp: *trace = trace(G) and *ex = the exponent e
+// with max_i G[i][i] * 2^-e in [0.5, 1) (G is PSD, so its diagonal bounds |G|;
+// 0 for a zero matrix), the scale of the double-float copy of G V.
+__global__ void sub_diag_kernel(const double* __restrict__ G, int n, double* __restrict__ trace, int* __restrict__ ex) {
+  double m = 0.0, t = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) {
+    const double g = G[(int64_t)i * n + i];
+    m = fmax(m, fabs(g));
+    t += g;
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
   if (threadIdx.x == 0) {
     int e = 0;
     if (m > 0.0) frexp(m, &e);
     *ex = e;
+    *trace = t;
   }
 }
 
-// W[c][i] = sum_k G[i][k] V[c][k]: a warp per (i, group of 8 columns c).
-// Wd != nullptr: written as double-floats scaled by 2^-(*ex) (|W| <= sqrt(n)
-// then, since |G| <= max diag and V has orthonormal columns) for the QR,
-// which so needs no FP64 arithmetic; else FP64 into W.
-__global__ void __launch_bounds__(256) sub_gemm_kernel(const double* __restrict__ G, int n,
-                                                       const double* __restrict__ V, int K, double* __restrict__ W,
-                                                       dd* __restrict__ Wd, const int* __restrict__ ex) {
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int ngrp = (K + 7) / 8;
-  if (gw >= n * ngrp) return;
-  const int i = gw / ngrp, c0 = (gw - i * ngrp) * 8;
-  double acc[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-  const double* gi = G + (int64_t)i * n;
-  for (int k = lane; k < n; k += 32) {
-    const double g = gi[k];
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (c0 + q < K) acc[q] = fma(g, V[(int64_t)(c0 + q) * n + k], acc[q]);
+// Partial products P[z][c][i] = sum_{k in split z} G[k][i] V[c][k] (= (G V)[i][c]
+// for symmetric G): a thread per (i, c, z); G is read column-wise by the 32
+// lanes of a warp (consecutive i, coalesced), V[c][k] is a warp broadcast, four
+// independent FP64 accumulators.  Grid (ceil(n/32), ceil(K/8), kSubSplit),
+// 8 warps per CTA (one column c each).
+constexpr int kSubSplit = 4;
+__global__ void __launch_bounds__(256) sub_gemm_part_kernel(const double* __restrict__ G, int n,
+                                                            const double* __restrict__ V, int K,
+                                                            double* __restrict__ part) {
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int c = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (i >= n || c >= K) return;
+  const int k0 = (int)((int64_t)n * blockIdx.z / kSubSplit), k1 = (int)((int64_t)n * (blockIdx.z + 1) / kSubSplit);
+  const double* vc = V + (int64_t)c * n;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int k = k0;
+  for (; k + 3 < k1; k += 4) {
+    a0 = fma(G[(int64_t)k * n + i], vc[k], a0);
+    a1 = fma(G[(int64_t)(k + 1) * n + i], vc[k + 1], a1);
+    a2 = fma(G[(int64_t)(k + 2) * n + i], vc[k + 2], a2);
+    a3 = fma(G[(int64_t)(k + 3) * n + i], vc[k + 3], a3);
   }
-  const double sc = Wd ? ldexp(1.0, -*ex) : 1.0;
+  for (; k < k1; ++k) a0 = fma(G[(int64_t)k * n + i], vc[k], a0);
+  part[((int64_t)blockIdx.z * K + c) * n + i] = (a0 + a1) + (a2 + a3);
+}
+// W[c][i] = sum_z P[z][c][i] in a fixed order; Wd != nullptr: as double-floats
+// scaled by 2^-(*ex) (|W| <= sqrt(n) then, since |G| <= max diag and V has
+// orthonormal columns), so that the QR needs no FP64 arithmetic; else FP64.
+__global__ void sub_gemm_sum_kernel(const double* __restrict__ part, int n, int K, double* __restrict__ W,
+                                    dd* __restrict__ Wd, const int* __restrict__ ex) {
+  const int64_t nk = (int64_t)n * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = part[e];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const double v = warp_sum_d(acc[q]);
-    if (lane == q && c0 + q < K) {
-      if (Wd) Wd[(int64_t)(c0 + q) * n + i] = dd_from(v * sc);
-      else W[(int64_t)(c0 + q) * n + i] = v;
-    }
+    for (int z = 1; z < kSubSplit; ++z) v += part[z * nk + e];
+    if (Wd) Wd[e] = dd_from(v * ldexp(1.0, -*ex));
+    else W[e] = v;
   }
 }
 
@@ -134,12 +150,6 @@ __global__ void sub_rotate_kernel(const double* __restrict__ V, int n, int K, co
   }
 }
 
-__global__ void sub_trace_kernel(const double* __restrict__ G, int n, double* __restrict__ out) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += 32) s += G[(int64_t)i * n + i];
-  s = warp_sum_d(s);
-  if (threadIdx.x == 0) *out = s;
-}
 
 // Blocked Householder QR of the K columns of W (n x K, column c at W + c n,
 // K <= 64 <= ... n), one CTA, in double-float (FP64 issues at 2 lanes per
@@ -201,6 +211,83 @@ __device__ __forceinline__ void qr_finalize(dd* __restrict__ aj, int j, int n, d
     aj[i] = (i < j) ? zero : ((i == j) ? dd{1.f, 0.f} : ((tau.hi != 0.f) ? dd_mul(aj[i], inv) : zero));
 }
 
+// Inner loops of the QR as helpers with restrict-qualified operands (the
+// reflector columns and the columns they update are disjoint parts of one
+// shared array, which the compiler cannot see through the offsets).
+// d = tau (c[j] + inv sum_{i>j} a[i] c[i]), four accumulators, warp-summed
+__device__ __forceinline__ dd qr_pivot_dot(const dd* __restrict__ a, const dd* __restrict__ c, int j, int n,
+                                           int lane) {
+  const dd zero = dd{0.f, 0.f};
+  dd s0 = zero, s1 = zero, s2 = zero, s3 = zero;
+  int i = j + 1 + lane;
+  for (; i + 96 < n; i += 128) {
+    s0 = dd_add(s0, dd_mul(a[i], c[i]));
+    s1 = dd_add(s1, dd_mul(a[i + 32], c[i + 32]));
+    s2 = dd_add(s2, dd_mul(a[i + 64], c[i + 64]));
+    s3 = dd_add(s3, dd_mul(a[i + 96], c[i + 96]));
+  }
+  for (; i < n; i += 32) s0 = dd_add(s0, dd_mul(a[i], c[i]));
+  return dd_warp_sum_l(dd_add(dd_add(s0, s1), dd_add(s2, s3)));
+}
+// c[i] -= dv a[i] for i > j; returns the lane's sum of the new c[i]^2 for i > j + 1
+__device__ __forceinline__ dd qr_pivot_update(const dd* __restrict__ a, dd* __restrict__ c, dd dv, int j, int n,
+                                              int lane) {
+  const dd zero = dd{0.f, 0.f};
+  dd q0 = zero, q1 = zero;
+  int i = j + 1 + lane;
+  for (; i + 32 < n; i += 64) {
+    const dd x0 = c[i], x1 = c[i + 32], y0 = a[i], y1 = a[i + 32];
+    const dd v0 = dd_sub(x0, dd_mul(dv, y0)), v1 = dd_sub(x1, dd_mul(dv, y1));
+    c[i] = v0;
+    c[i + 32] = v1;
+    if (i > j + 1) q0 = dd_add(q0, dd_mul(v0, v0));
+    q1 = dd_add(q1, dd_mul(v1, v1));
+  }
+  if (i < n) {
+    const dd v0 = dd_sub(c[i], dd_mul(dv, a[i]));
+    c[i] = v0;
+    if (i > j + 1) q0 = dd_add(q0, dd_mul(v0, v0));
+  }
+  return dd_add(q0, q1);
+}
+// trailing column c <- c - V (T^T (V^T c)) for the panel's reflectors V (column a at V + a n)
+__device__ __forceinline__ void qr_trailing(const dd* __restrict__ V, dd* __restrict__ c, const dd* __restrict__ T,
+                                            int p0, int n, int nb, int lane) {
+  const dd zero = dd{0.f, 0.f};
+  dd y[kQrNb];
+#pragma unroll
+  for (int a = 0; a < kQrNb; ++a) y[a] = zero;
+  for (int i = p0 + lane; i < n; i += 32) {
+    const dd x = c[i];
+#pragma unroll
+    for (int a = 0; a < kQrNb; ++a)
+      if (a < nb) y[a] = dd_add(y[a], dd_mul(V[(size_t)a * n + i], x));
+  }
+#pragma unroll
+  for (int a = 0; a < kQrNb; ++a) y[a] = dd_warp_sum_l(y[a]);
+  // z = T^T y: lane a < kQrNb forms z_a, then every lane takes all of them
+  dd za = zero;
+#pragma unroll
+  for (int b = 0; b < kQrNb; ++b)
+    if (b <= lane) za = dd_add(za, dd_mul(T[b * kQrNb + (lane & (kQrNb - 1))], y[b]));
+  dd z[kQrNb];
+#pragma unroll
+  for (int a = 0; a < kQrNb; ++a) z[a] = dd{__shfl_sync(0xffffffffu, za.hi, a), __shfl_sync(0xffffffffu, za.lo, a)};
+  __syncwarp();
+  for (int i = p0 + lane; i < n; i += 32) {
+    dd x = c[i];
+#pragma unroll
+    for (int a = 0; a < kQrNb; ++a)
+      if (a < nb) x = dd_sub(x, dd_mul(V[(size_t)a * n + i], z[a]));
+    c[i] = x;
+  }
+}
+// warp that takes panel column offset o = c - j - 1 (0 .. kQrNb-2): the critical
+// column (o = 0) gets warp 0 alone on its SM sub-partition (warp % 4 == 0);
+// the others go to warps of the other three sub-partitions
+__device__ __forceinline__ int qr_col_warp(int o) { return o == 0 ? 0 : o + (o - 1) / 3; }
+constexpr int kQrFinWarp = 9;  // finalises the previous reflector column
+
 __global__ void __launch_bounds__(kQrThreads) sub_qr_kernel(const dd* __restrict__ W, int n, int K,
                                                             dd* __restrict__ Vg, dd* __restrict__ Tg) {
   extern __shared__ dd A[];
@@ -240,9 +327,12 @@ __global__ void __launch_bounds__(kQrThreads) sub_qr_kernel(const dd* __restrict
       __syncthreads();
     }
     for (int j = p0; j < p1; ++j) {
-      // only the warps that use the reflector form it (warp 0 stores tau and 1/v0)
-      const int c = j + 1 + warp;
-      const bool uses = c < p1 || warp == 0 || warp == nw - 1;
+      // the panel column this warp updates (if any); only those warps form the reflector
+      int o = -1;
+      for (int t = 0; t < p1 - j - 1; ++t)
+        if (qr_col_warp(t) == warp) o = t;
+      const int c = j + 1 + o;
+      const bool uses = o >= 0 || warp == 0;
       const dd sig = s_sig[j & 1], x0 = s_x0[j & 1];
       dd tj = zero, inv = one;
       if (uses && sig.hi != 0.f) {
@@ -255,36 +345,21 @@ __global__ void __launch_bounds__(kQrThreads) sub_qr_kernel(const dd* __restrict
       }
       if (tid == 0) { s_tau[j] = tj; s_inv[j] = inv; }
       const dd* aj = A + (size_t)j * n;
-      if (c < p1) {
+      if (o >= 0) {
         dd* ac = A + (size_t)c * n;
         if (tj.hi != 0.f) {
-          // d = tau (a_c[j] + sum_{i>j} v_i a_c[i]) with v_i = inv a_j[i]
-          dd s0 = zero, s1 = zero, s2 = zero, s3 = zero;
-          int i = j + 1 + lane;
-          for (; i + 96 < n; i += 128) {
-            s0 = dd_add(s0, dd_mul(aj[i], ac[i]));
-            s1 = dd_add(s1, dd_mul(aj[i + 32], ac[i + 32]));
-            s2 = dd_add(s2, dd_mul(aj[i + 64], ac[i + 64]));
-            s3 = dd_add(s3, dd_mul(aj[i + 96], ac[i + 96]));
-          }
-          for (; i < n; i += 32) s0 = dd_add(s0, dd_mul(aj[i], ac[i]));
-          const dd sdot = dd_warp_sum_l(dd_add(dd_add(s0, s1), dd_add(s2, s3)));
+          const dd sdot = qr_pivot_dot(aj, ac, j, n, lane);
           const dd acj = ac[j];
           const dd d = dd_mul(tj, dd_add(acj, dd_mul(inv, sdot)));
           const dd dv = dd_mul(d, inv);
           __syncwarp();
           if (lane == 0) ac[j] = dd_sub(acj, d);
-          dd q = zero;
-          for (int i2 = j + 1 + lane; i2 < n; i2 += 32) {
-            const dd v = dd_sub(ac[i2], dd_mul(dv, aj[i2]));
-            ac[i2] = v;
-            if (i2 > j + 1) q = dd_add(q, dd_mul(v, v));
-          }
-          if (c == j + 1) {
+          dd q = qr_pivot_update(aj, ac, dv, j, n, lane);
+          if (o == 0) {
             q = dd_warp_sum_l(q);
             if (lane == 0) { s_sig[(j + 1) & 1] = q; s_x0[(j + 1) & 1] = ac[j + 1]; }
           }
-        } else if (c == j + 1) {
+        } else if (o == 0) {
           dd q = zero;
           for (int i2 = j + 2 + lane; i2 < n; i2 += 32) q = dd_add(q, dd_mul(ac[i2], ac[i2]));
           q = dd_warp_sum_l(q);
@@ -292,10 +367,11 @@ __global__ void __launch_bounds__(kQrThreads) sub_qr_kernel(const dd* __restrict
         }
       }
       // column j-1 is no longer read by the panel: scale it into its reflector
-      if (warp == nw - 1 && j > p0) qr_finalize(A + (size_t)(j - 1) * n, j - 1, n, s_inv[j - 1], s_tau[j - 1], lane);
+      if (warp == kQrFinWarp && j > p0)
+        qr_finalize(A + (size_t)(j - 1) * n, j - 1, n, s_inv[j - 1], s_tau[j - 1], lane);
       __syncthreads();
     }
-    if (warp == nw - 1) qr_finalize(A + (size_t)(p1 - 1) * n, p1 - 1, n, s_inv[p1 - 1], s_tau[p1 - 1], lane);
+    if (warp == kQrFinWarp) qr_finalize(A + (size_t)(p1 - 1) * n, p1 - 1, n, s_inv[p1 - 1], s_tau[p1 - 1], lane);
     __syncthreads();
     // S[a][b] = v_a . v_b for a < b (v_b is 0 above row p0 + b)
     for (int e = warp; e < nb * nb; e += nw) {
@@ -325,115 +401,95 @@ __global__ void __launch_bounds__(kQrThreads) sub_qr_kernel(const dd* __restrict
     __syncthreads();
     for (int e = tid; e < kQrNb * kQrNb; e += blockDim.x) Tg[(size_t)(p0 / kQrNb) * kQrNb * kQrNb + e] = s_T[e];
     // trailing columns: a_c -= V (T^T (V^T a_c)), a warp per column
-    for (int c = p1 + warp; c < K; c += nw) {
-      dd* ac = A + (size_t)c * n;
-      dd y[kQrNb];
-#pragma unroll
-      for (int a = 0; a < kQrNb; ++a) y[a] = zero;
-      for (int i = p0 + lane; i < n; i += 32) {
-        const dd x = ac[i];
-#pragma unroll
-        for (int a = 0; a < kQrNb; ++a)
-          if (a < nb) y[a] = dd_add(y[a], dd_mul(A[(size_t)(p0 + a) * n + i], x));
-      }
-#pragma unroll
-      for (int a = 0; a < kQrNb; ++a) y[a] = dd_warp_sum_l(y[a]);
-      // z = T^T y: lane a < kQrNb forms z_a, then every lane takes all of them
-      dd za = zero;
-#pragma unroll
-      for (int b = 0; b < kQrNb; ++b)
-        if (b <= lane) za = dd_add(za, dd_mul(s_T[b * kQrNb + (lane & (kQrNb - 1))], y[b]));
-      dd z[kQrNb];
-#pragma unroll
-      for (int a = 0; a < kQrNb; ++a)
-        z[a] = dd{__shfl_sync(0xffffffffu, za.hi, a), __shfl_sync(0xffffffffu, za.lo, a)};
-      __syncwarp();
-      for (int i = p0 + lane; i < n; i += 32) {
-        dd x = ac[i];
-#pragma unroll
-        for (int a = 0; a < kQrNb; ++a)
-          if (a < nb) x = dd_sub(x, dd_mul(A[(size_t)(p0 + a) * n + i], z[a]));
-        ac[i] = x;
-      }
-    }
+    for (int c = p1 + warp; c < K; c += nw) qr_trailing(A + (size_t)p0 * n, A + (size_t)c * n, s_T, p0, n, nb, lane);
     __syncthreads();
   }
   for (int e = tid; e < n * K; e += blockDim.x) Vg[e] = A[e];
 }
 
-// Q = H_0 H_1 ... H_{K-1} [I_K; 0] from the panels' WY blocks, a warp per
-// column c: q = e_c, then q <- q - V_p (T_p (V_p^T q)) for the panels p from
-// the one holding c down to the first (later panels leave e_c unchanged).  A
-// CTA holds the kQrNb columns of one panel, so its warps walk the same panels:
-// each panel's reflectors and T are staged in shared memory once per CTA.
-constexpr int kQfWarps = kQrNb;
-__global__ void __launch_bounds__(kQfWarps * 32) sub_qform_kernel(const dd* __restrict__ Vg, const dd* __restrict__ Tg,
-                                                                  int n, int K, double* __restrict__ Q) {
-  extern __shared__ dd qs[];
-  __shared__ dd sT[kQrNb * kQrNb];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int c = blockIdx.x * kQfWarps + w;
-  const bool active = c < K;
+// Q = H_0 H_1 ... H_{K-1} [I_K; 0] from the panels' WY blocks, one CTA per
+// column c (threads over rows): q = e_c, then q <- q - V_p (T_p (V_p^T q)) for
+// the panels p from the one holding c down to the first (later panels leave
+// e_c unchanged); per panel one CTA reduction of the kQrNb dot products, z = T y
+// in warp 0, and the update of the thread's rows.
+constexpr int kQfThreads = 256;
+constexpr int kQfRows = 3;  // rows per thread: n <= 768
+__global__ void __launch_bounds__(kQfThreads) sub_qform_kernel(const dd* __restrict__ Vg, const dd* __restrict__ Tg,
+                                                               int n, int K, double* __restrict__ Q) {
+  __shared__ dd part[kQfThreads / 32][kQrNb];
+  __shared__ dd zs[kQrNb];
+  const int c = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const dd zero = dd{0.f, 0.f};
-  dd* Vs = qs;                            // kQrNb x n
-  dd* q = qs + (size_t)(kQrNb + w) * n;   // this warp's column
-  for (int i = lane; i < n; i += 32) q[i] = (i == c) ? dd{1.f, 0.f} : zero;
-  for (int p = (int)blockIdx.x; p >= 0; --p) {
+  dd q[kQfRows];
+#pragma unroll
+  for (int r = 0; r < kQfRows; ++r) q[r] = (tid + r * kQfThreads == c) ? dd{1.f, 0.f} : zero;
+  for (int p = c / kQrNb; p >= 0; --p) {
     const int p0 = p * kQrNb, nb = min(kQrNb, K - p0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * n; e += blockDim.x) Vs[e] = Vg[(size_t)p0 * n + e];
-    for (int e = threadIdx.x; e < kQrNb * kQrNb; e += blockDim.x) sT[e] = Tg[(size_t)p * kQrNb * kQrNb + e];
-    __syncthreads();
-    if (!active) continue;
+    const dd* V = Vg + (size_t)p0 * n;
+    const dd* T = Tg + (size_t)p * kQrNb * kQrNb;
     dd y[kQrNb];
 #pragma unroll
     for (int a = 0; a < kQrNb; ++a) y[a] = zero;
-    for (int i = p0 + lane; i < n; i += 32) {
-      const dd x = q[i];
 #pragma unroll
-      for (int a = 0; a < kQrNb; ++a)
-        if (a < nb) y[a] = dd_add(y[a], dd_mul(Vs[(size_t)a * n + i], x));
+    for (int r = 0; r < kQfRows; ++r) {
+      const int i = tid + r * kQfThreads;
+      if (i >= p0 && i < n)
+#pragma unroll
+        for (int a = 0; a < kQrNb; ++a)
+          if (a < nb) y[a] = dd_add(y[a], dd_mul(V[(size_t)a * n + i], q[r]));
     }
 #pragma unroll
     for (int a = 0; a < kQrNb; ++a) y[a] = dd_warp_sum_l(y[a]);
-    dd z[kQrNb];
+    if (lane == 0)
 #pragma unroll
-    for (int a = 0; a < kQrNb; ++a) {
-      dd t = zero;
+      for (int a = 0; a < kQrNb; ++a) part[warp][a] = y[a];
+    __syncthreads();
+    if (warp == 0) {
+      dd ya = zero;
+      if (lane < kQrNb)
+        for (int w = 0; w < kQfThreads / 32; ++w) ya = dd_add(ya, part[w][lane]);
+      dd za = zero;
 #pragma unroll
-      for (int b = a; b < kQrNb; ++b)
-        if (b < nb) t = dd_add(t, dd_mul(sT[a * kQrNb + b], y[b]));
-      z[a] = t;
+      for (int b = 0; b < kQrNb; ++b) {
+        const dd yb = dd{__shfl_sync(0xffffffffu, ya.hi, b), __shfl_sync(0xffffffffu, ya.lo, b)};
+        if (lane < nb && b >= lane && b < nb) za = dd_add(za, dd_mul(T[lane * kQrNb + b], yb));
+      }
+      if (lane < kQrNb) zs[lane] = za;
     }
-    __syncwarp();
-    for (int i = p0 + lane; i < n; i += 32) {
-      dd x = q[i];
+    __syncthreads();
 #pragma unroll
-      for (int a = 0; a < kQrNb; ++a)
-        if (a < nb) x = dd_sub(x, dd_mul(Vs[(size_t)a * n + i], z[a]));
-      q[i] = x;
+    for (int r = 0; r < kQfRows; ++r) {
+      const int i = tid + r * kQfThreads;
+      if (i >= p0 && i < n)
+#pragma unroll
+        for (int a = 0; a < kQrNb; ++a)
+          if (a < nb) q[r] = dd_sub(q[r], dd_mul(V[(size_t)a * n + i], zs[a]));
     }
-    __syncwarp();
   }
-  if (active)
-    for (int i = lane; i < n; i += 32) Q[(size_t)c * n + i] = dd_to(q[i]);
+#pragma unroll
+  for (int r = 0; r < kQfRows; ++r) {
+    const int i = tid + r * kQfThreads;
+    if (i < n) Q[(size_t)c * n + i] = dd_to(q[r]);
+  }
 }
 
 }  // namespace
 
 bool subspace_supported(int n, int K) {
-  return K >= 5 && K <= 64 && K <= n && (size_t)n * K * sizeof(dd) <= 200 * 1024 &&
-         (size_t)2 * kQrNb * n * sizeof(dd) <= 200 * 1024 && rr_smem_bytes(K, K - 4) <= 180 * 1024;
+  return K >= 5 && K <= 64 && K <= n && n <= kQfThreads * kQfRows && (size_t)n * K * sizeof(dd) <= 200 * 1024 &&
+         rr_smem_bytes(K, K - 4) <= 180 * 1024;
 }
 
 int subspace_solve(const double* G, int n, int K, int T, double budget, int extra, int nmax, double conv,
-                   double* U_dev, double* theta_host, double* trace_host, int* decision_host, cudaStream_t s) {
+                   const int* tc_err, double* U_dev, int* decision_host, cudaStream_t s) {
   if (!subspace_supported(n, K)) return fail(ATC_EINVAL, "subspace_solve: unsupported n = %d, K = %d", n, K);
   if (nmax < 1 || nmax > K || T < 1) return fail(ATC_EINVAL, "subspace_solve: nmax = %d, T = %d", nmax, T);
   const size_t nk = (size_t)n * K;
   const int npan = (K + kQrNb - 1) / kQrNb;
-  const size_t nd = 2 * nk + (size_t)K * K + K + 8 + nk + (size_t)npan * kQrNb * kQrNb + (size_t)K * nmax + 8;
-  // (the last 8 doubles: decision ints and the scale exponent)
+  // V, W, B, theta, trace (8), Vg, Tg, Y, decision + exponent (8), split-K partials
+  const size_t nd = 2 * nk + (size_t)K * K + K + 8 + nk + (size_t)npan * kQrNb * kQrNb + (size_t)K * nmax + 8 +
+                    (size_t)kSubSplit * nk;
   double* base = nullptr;
   ATC_TRY(Scratch::get(SLOT_SUBSPACE, sizeof(double) * nd, (void**)&base));
   double* V = base;
@@ -446,41 +502,55 @@ int subspace_solve(const double* G, int n, int K, int T, double budget, int extr
   double* Y = reinterpret_cast<double*>(Tg + (size_t)npan * kQrNb * kQrNb);
   int* dec = reinterpret_cast<int*>(Y + (size_t)K * nmax);
   int* gex = dec + 4;
+  double* part = Y + (size_t)K * nmax + 8;
   dd* Wd = reinterpret_cast<dd*>(W);  // the double-float copy of G V reuses the FP64 block
-  const size_t qsm = sizeof(dd) * nk;
-  const size_t fsm = sizeof(dd) * 2 * kQrNb * (size_t)n;
+  // the start frame depends on (n, K) only: kept in its own slot per device
+  double* V0 = nullptr;
+  ATC_TRY(Scratch::get(SLOT_SUB_V0, sizeof(double) * nk, (void**)&V0));
+  {
+    static int c_dev = -1, c_n = -1, c_K = -1;
+    static long long c_serial = -1;
+    int dev = 0;
+    ATC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != c_dev || n != c_n || K != c_K || g_scratch_serial != c_serial) {
+      const int blocks = (int)((nk + 255) / 256 < 1024 ? (nk + 255) / 256 : 1024);
+      sub_init_kernel<<<blocks, 256, 0, s>>>(V0, n, K);
+      ATC_LAUNCHED(1);
+      c_dev = dev;
+      c_n = n;
+      c_K = K;
+      c_serial = g_scratch_serial;
+    }
+  }
   static bool attr = false;
   if (!attr) {
     ATC_CUDA_TRY(cudaFuncSetAttribute(sub_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    ATC_CUDA_TRY(cudaFuncSetAttribute(sub_qform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
-  const int blocks = (int)((nk + 255) / 256 < 1024 ? (nk + 255) / 256 : 1024);
-  sub_init_kernel<<<blocks, 256, 0, s>>>(V, n, K);
-  sub_scale_kernel<<<1, 32, 0, s>>>(G, n, gex);
-  ATC_LAUNCHED(2);
-  const int gemm_blocks = (int)(((int64_t)n * ((K + 7) / 8) * 32 + 255) / 256);
+  sub_diag_kernel<<<1, 32, 0, s>>>(G, n, tr, gex);
+  ATC_LAUNCHED(1);
+  const dim3 ggrid((n + 31) / 32, (K + 7) / 8, kSubSplit);
+  const int sblocks = (int)((nk + 255) / 256 < 1024 ? (nk + 255) / 256 : 1024);
   for (int t = 0; t < T; ++t) {
-    sub_gemm_kernel<<<gemm_blocks, 256, 0, s>>>(G, n, V, K, nullptr, Wd, gex);
+    sub_gemm_part_kernel<<<ggrid, 256, 0, s>>>(G, n, t == 0 ? V0 : V, K, part);
+    sub_gemm_sum_kernel<<<sblocks, 256, 0, s>>>(part, n, K, nullptr, Wd, gex);
+    ATC_LAUNCHED(2);
+    sub_qr_kernel<<<1, kQrThreads, sizeof(dd) * nk, s>>>(Wd, n, K, Vg, Tg);
     ATC_LAUNCHED(1);
-    sub_qr_kernel<<<1, kQrThreads, qsm, s>>>(Wd, n, K, Vg, Tg);
-    ATC_LAUNCHED(1);
-    sub_qform_kernel<<<(K + kQfWarps - 1) / kQfWarps, kQfWarps * 32, fsm, s>>>(Vg, Tg, n, K, V);
+    sub_qform_kernel<<<K, kQfThreads, 0, s>>>(Vg, Tg, n, K, V);
     ATC_LAUNCHED(1);
   }
-  sub_gemm_kernel<<<gemm_blocks, 256, 0, s>>>(G, n, V, K, W, nullptr, gex);
-  ATC_LAUNCHED(1);
-  sub_proj_kernel<<<(K * K * 32 + 255) / 256, 256, 0, s>>>(V, W, n, K, B);
-  sub_trace_kernel<<<1, 32, 0, s>>>(G, n, tr);
+  sub_gemm_part_kernel<<<ggrid, 256, 0, s>>>(G, n, V, K, part);
+  sub_gemm_sum_kernel<<<sblocks, 256, 0, s>>>(part, n, K, W, nullptr, gex);
   ATC_LAUNCHED(2);
+  sub_proj_kernel<<<(K * K * 32 + 255) / 256, 256, 0, s>>>(V, W, n, K, B);
+  ATC_LAUNCHED(1);
   // Rayleigh-Ritz on the K x K matrix B (one CTA), provisional rank and vector count on the device
-  ATC_TRY(launch_rr_small(B, K, n, tr, budget, extra, nmax, conv, T, th, dec, Y, s));
+  ATC_TRY(launch_rr_small(B, K, n, tr, budget, extra, nmax, conv, T, tc_err, th, dec, Y, s));
   const int rblocks = (int)(((size_t)n * nmax + 255) / 256 < 1024 ? ((size_t)n * nmax + 255) / 256 : 1024);
   sub_rotate_kernel<<<rblocks, 256, 0, s>>>(V, n, K, Y, dec + 1, U_dev);
   ATC_LAUNCHED(1);
-  ATC_CUDA_TRY(cudaMemcpyAsync(theta_host, th, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
-  ATC_CUDA_TRY(cudaMemcpyAsync(trace_host, tr, sizeof(double), cudaMemcpyDeviceToHost, s));
-  ATC_CUDA_TRY(cudaMemcpyAsync(decision_host, dec, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+  ATC_CUDA_TRY(cudaMemcpyAsync(decision_host, dec, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
   return ATC_OK;
 }
 
