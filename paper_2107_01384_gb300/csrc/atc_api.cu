@@ -220,7 +220,7 @@ int check_dims(const int64_t* dims, int ndim, int64_t* total) {
 // the certified rank is chosen
 constexpr int kCertExtra = 4;
 // subspace iteration for the leading eigenvectors on the split paths
-constexpr int kSubK = 40;      // block columns
+constexpr int kSubK = 32;      // block columns
 constexpr int kSubIters = 1;   // iterations before Rayleigh-Ritz
 constexpr int kSubMargin = 4;  // columns kept beyond the largest certified candidate count
 bool subspace_enabled() {

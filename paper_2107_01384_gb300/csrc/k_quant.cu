@@ -33,6 +33,7 @@
 #include <string.h>
 
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "atc_internal.cuh"
@@ -1241,6 +1242,28 @@ double i192_to_double(const I192& v) {
 
 }  // namespace
 
+// Pinned host staging for the tracker state and the encoder's small tables:
+// copies into it are asynchronous, so each readback costs one stream
+// synchronisation and no pageable staging (grow-only, process-wide).
+static int quant_pinned(size_t bytes, void** p) {
+  static std::mutex mu;
+  static void* buf = nullptr;
+  static size_t cap = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cap < bytes) {
+    if (buf) {
+      ATC_CUDA_TRY(cudaDeviceSynchronize());
+      cudaFreeHost(buf);
+      buf = nullptr;
+      cap = 0;
+    }
+    ATC_CUDA_TRY(cudaHostAlloc(&buf, bytes, cudaHostAllocPortable));
+    cap = bytes;
+  }
+  *p = buf;
+  return ATC_OK;
+}
+
 int quantize_encode(const double* core, int64_t n, double target, int block_size, cudaStream_t s, std::string* out,
                     QuantResult* res, float* ms_quant, float* ms_encode) {
   if (n < 1) return fail(ATC_EINVAL, "empty core");
@@ -1274,7 +1297,9 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
   ATC_LAUNCHED(1);
   quantize_kernel<<<grid, 256, 0, s>>>(core, n, &st->k, q, sg);
   ATC_LAUNCHED(1);
-  TrackState hst;
+  TrackState* hstp = nullptr;
+  ATC_TRY(quant_pinned(sizeof(TrackState) + 16 + sizeof(uint32_t) * 2 * 64 * kNsym, (void**)&hstp));
+  TrackState& hst = *hstp;
   int phi = 63;
   bool first = true;
   for (;;) {
@@ -1349,11 +1374,12 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     ATC_LAUNCHED(1);
     scan_kernel<<<1, 1024, 0, s>>>(rsize, wsize, nchunks, off);
     ATC_LAUNCHED(1);
-    uint64_t total = 0;
-    ATC_CUDA_TRY(cudaMemcpyAsync(&total, off + nchunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    std::vector<uint32_t> hfc(2 * nplanes * kNsym);
-    ATC_CUDA_TRY(cudaMemcpyAsync(hfc.data(), fc, sizeof(uint32_t) * nplanes * kNsym, cudaMemcpyDeviceToHost, s));
+    uint64_t* ptotal = reinterpret_cast<uint64_t*>(hstp + 1);
+    uint32_t* hfc = reinterpret_cast<uint32_t*>(ptotal + 2);
+    ATC_CUDA_TRY(cudaMemcpyAsync(ptotal, off + nchunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    ATC_CUDA_TRY(cudaMemcpyAsync(hfc, fc, sizeof(uint32_t) * nplanes * kNsym, cudaMemcpyDeviceToHost, s));
     ATC_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint64_t total = *ptotal;
     for (int i = 0; i < nplanes * kNsym; ++i) {
       head[48 + 2 * i] = (uint8_t)hfc[i];
       head[48 + 2 * i + 1] = (uint8_t)(hfc[i] >> 8);

@@ -39,14 +39,26 @@ __global__ void __launch_bounds__(kNormThreads) norm2_partial(const T* __restric
   double acc = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (sizeof(T) == 4 && ((uintptr_t)x & 15) == 0) {
+    // FP32 input: every square is exact as a float pair (v*v, fma(v, v, -v*v));
+    // four of them are summed as a double-float on the FP32 pipes and each
+    // group of four is added into the FP64 accumulator (GB300 issues FP64 at
+    // 1/64 of the FP32 rate, which would otherwise bound this HBM pass).
     const int64_t n4 = n / 4;
     const float4* x4 = reinterpret_cast<const float4*>(x);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += stride) {
-      float4 v = __ldg(x4 + i);
-      acc = fma((double)v.x, (double)v.x, acc);
-      acc = fma((double)v.y, (double)v.y, acc);
-      acc = fma((double)v.z, (double)v.z, acc);
-      acc = fma((double)v.w, (double)v.w, acc);
+      const float4 v = __ldg(x4 + i);
+      const float q[4] = {v.x, v.y, v.z, v.w};
+      float hi = 0.f, lo = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float p = q[k] * q[k];
+        const float e = fmaf(q[k], q[k], -p);
+        const float s = hi + p;
+        const float bp = s - hi;
+        lo += ((hi - (s - bp)) + (p - bp)) + e;
+        hi = s;
+      }
+      acc += (double)hi + (double)lo;
     }
     for (int64_t i = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
       double v = (double)x[i];
