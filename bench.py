@@ -350,14 +350,14 @@ def run_ours(args, world, rank, local):
     elif dom == "eig":
         sub = stats[-1].get("subspace_modes", 0) == len(order)
         if sub:
-            # subspace iteration per mode (K = 40 columns, 1 iteration): two G V products 2 n^2 K each,
+            # subspace iteration per mode (K = 32 columns, 1 iteration): two G V products 2 n^2 K each,
             # Householder QR + explicit Q 4 n K^2, V^T (G V) 2 n K^2, the K x K eigensolve 4/3 K^3,
             # Ritz vectors 2 n K (r + 4)
-            K = 40
+            K = 32
             fl = sum(2 * 2.0 * dims[m] ** 2 * K + 6.0 * dims[m] * K * K + 4.0 / 3.0 * K ** 3
                      + 2.0 * dims[m] * K * (ranks[m] + 4) for m in order)
             kern = ("sub_gemm_kernel, sub_qr_kernel (blocked double-float Householder QR), sub_qform_kernel, "
-                    "sub_proj_kernel, rr_kernel (one-CTA double-float Rayleigh-Ritz on the 40 x 40 matrix: "
+                    "sub_proj_kernel, rr_kernel (one-CTA double-float Rayleigh-Ritz on the 32 x 32 matrix: "
                     "tridiagonalisation, Sturm multisection, provisional rank, inverse iteration), sub_rotate_kernel")
             unit = "TFLOP/s (FP64-class: subspace iteration + Rayleigh-Ritz, formula in bench.py)"
             why = "a chain of dependent QR and tridiagonalisation steps on small matrices (latency-bound)"
