@@ -83,12 +83,17 @@ enum ScratchSlot {
   SLOT_SUBSPACE,       // subspace-iteration blocks
   SLOT_SUB_U,          // subspace-iteration Ritz vectors
   SLOT_SUB_V0,         // subspace-iteration start frame (kept while n and K stay the same)
+  SLOT_TTM_AIMG,       // pre-sliced data operand of single-K-tile products
+  SLOT_RES_TMP,        // reproduction U ._k Y of the certification residual
+  SLOT_RES_PART,       // its partial sums
   SLOT_COUNT
 };
 
 // ---------------------------------------------------------------- kernels
 // norm / reductions (k_reduce.cu)
 int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s);
+// *out = sum (x - z)^2 over n elements, x FP32/FP64 (dtype), z FP32; FP64 result
+int launch_diff_norm2(const void* x, int dtype, const float* z, int64_t n, double* out, cudaStream_t s);
 int launch_convert_to_f64(const void* x, int dtype, int64_t n, double* y, cudaStream_t s);
 int launch_convert_f64_to(const double* x, int64_t n, void* y, int dtype, cudaStream_t s);
 // e[j] = sum over (l, c) of y[(l r + j) R + c]^2 in FP64 (fixed order)

@@ -74,6 +74,51 @@ __global__ void __launch_bounds__(kNormThreads) norm2_partial(const T* __restric
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+// sum_i (x_i - z_i)^2 for the tensor x (FP32 or FP64) and its reproduction z
+// (FP32): each difference is taken in the precision of x and rounded to FP32,
+// its square is an exact float pair, four squares are summed as a double-float
+// and added into the FP64 accumulator (the FP32 pipes carry the work; GB300
+// issues FP64 at 1/64 of their rate).  Fixed grid and reduction tree.
+__device__ __forceinline__ void dd_acc_sq(float d, float& hi, float& lo) {
+  const float p = d * d;
+  const float e = fmaf(d, d, -p);
+  const float s = hi + p;
+  const float bp = s - hi;
+  lo += ((hi - (s - bp)) + (p - bp)) + e;
+  hi = s;
+}
+template <typename T>
+__global__ void __launch_bounds__(kNormThreads) diff2_partial(const T* __restrict__ x, const float* __restrict__ z,
+                                                               int64_t n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t done = 0;
+  if (sizeof(T) == 4 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)z & 15) == 0) {
+    const int64_t n4 = n / 4;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    for (int64_t i = t0; i < n4; i += stride) {
+      const float4 a = __ldg(x4 + i), b = __ldg(z4 + i);
+      float hi = 0.f, lo = 0.f;
+      dd_acc_sq(a.x - b.x, hi, lo);
+      dd_acc_sq(a.y - b.y, hi, lo);
+      dd_acc_sq(a.z - b.z, hi, lo);
+      dd_acc_sq(a.w - b.w, hi, lo);
+      acc += (double)hi + (double)lo;
+    }
+    done = n4 * 4;
+  }
+  for (int64_t i = done + t0; i < n; i += stride) {
+    float hi = 0.f, lo = 0.f;
+    dd_acc_sq((float)((double)x[i] - (double)z[i]), hi, lo);
+    acc += (double)hi + (double)lo;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
 __global__ void __launch_bounds__(kNormThreads) sum_partials(const double* __restrict__ part, int np,
                                                              double* __restrict__ out) {
   __shared__ double sh[32];
@@ -185,6 +230,19 @@ int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t 
     norm2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, n, part);
   else
     norm2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, n, part);
+  ATC_LAUNCHED(1);
+  sum_partials<<<1, kNormThreads, 0, s>>>(part, kNormBlocks, out);
+  ATC_LAUNCHED(1);
+  return ATC_OK;
+}
+
+int launch_diff_norm2(const void* x, int dtype, const float* z, int64_t n, double* out, cudaStream_t s) {
+  double* part = nullptr;
+  ATC_TRY(Scratch::get(SLOT_RES_PART, sizeof(double) * (kNormBlocks + 64), (void**)&part));
+  if (dtype == ATC_F32)
+    diff2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, z, n, part);
+  else
+    diff2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, z, n, part);
   ATC_LAUNCHED(1);
   sum_partials<<<1, kNormThreads, 0, s>>>(part, kNormBlocks, out);
   ATC_LAUNCHED(1);

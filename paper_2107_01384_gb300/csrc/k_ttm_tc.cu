@@ -75,6 +75,10 @@ struct TtmArgs {
   int64_t csz;           // output indices per chunk (blockIdx.y = chunk)
   size_t wb;             // bytes of one chunk's factor slices
   unsigned nchunk_launch;
+  // single-K-tile products with several output chunks: the data operand
+  // already sliced into the converters' shared-memory image, one 3 x 16 KB
+  // block per M tile (ttm_preslice_a); nullptr: the converter warps slice it
+  const uint8_t* aimg;
 };
 
 template <typename T>
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(&full_bar[s], kConvThreads);
+      mbar_init(&full_bar[s], a.aimg ? 1 : kConvThreads);
       mbar_init(&bfull_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -159,7 +163,24 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp >= kEpiWarps && warp < kMmaWarp) {
+  if (warp >= kEpiWarps && warp < kMmaWarp && a.aimg) {
+    // --------------------------------------- pre-sliced data operand (bulk copies)
+    if (tid == kEpiWarps * 32) {
+      int64_t issued = 0;
+      for (int64_t it = 0; it < iters; ++it) {
+        const int s = (int)(it % NSTAGE);
+        const int64_t mt = blockIdx.x + (it / a.nkt) * gridDim.x;
+        if (!mbar_wait(&empty_bar[s], ((uint32_t)(it / NSTAGE) & 1u) ^ 1u, abort)) break;
+        mbar_arrive_expect_tx(&full_bar[s], 3 * A_BYTES);
+        bulk_g2s(smem + (size_t)s * STAGE, a.aimg + (size_t)mt * 3 * A_BYTES, 3 * A_BYTES, &full_bar[s]);
+        issued = it + 1;
+      }
+      // drain: every issued copy must land before the CTA may exit
+      const int64_t first = issued > NSTAGE ? issued - NSTAGE : 0;
+      for (int64_t it = first; it < issued; ++it)
+        mbar_wait_drain(&full_bar[it % NSTAGE], (uint32_t)(it / NSTAGE) & 1u);
+    }
+  } else if (warp >= kEpiWarps && warp < kMmaWarp) {
     // ------------------------------------------------------------ converters
     const int ct = tid - kEpiWarps * 32;
     const float sc = ldexpf(1.0f, shift);
@@ -463,6 +484,61 @@ __global__ void ttm_prep_b(const double* __restrict__ u, int64_t csz, int64_t At
   }
 }
 
+// The data operand of a single-K-tile product (contraction <= 64) sliced once
+// into the converter warps' shared-memory image: per M tile, three 128 x 64
+// 16-bit slices in the 128-byte-swizzled K-major layout, [m tile][slice][16 KB].
+// The output chunks (blockIdx.y of the product) then copy it with the bulk
+// engine instead of each re-slicing it.  Same loads, scales and slicing as the
+// converter warps, one thread per (m tile, row, group of 8 K values).
+template <typename TX, bool GEN, bool BF16>
+__global__ void ttm_preslice_a(TtmArgs a, uint8_t* __restrict__ img) {
+  constexpr uint32_t A_BYTES = 128 * 128;
+  const int MODE = GEN ? TM_GEN : a.rowmode;
+  const float sc = ldexpf(1.0f, a.xs->shift);
+  const TX* __restrict__ x = reinterpret_cast<const TX*>(a.x);
+  const int64_t LR = a.L * a.R;
+  const int64_t total = a.mtiles * 1024;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t mt = idx >> 10;
+    const int g = (int)(idx & 1023);
+    int m, q;
+    if (MODE == TM_GEN) { m = g & 127; q = g >> 7; } else { m = g >> 3; q = g & 7; }
+    const int64_t gam = mt * 128 + m;
+    float buf[8];
+    if (MODE == TM_GEN) {
+      const int64_t l = gam / a.R, c = gam - l * a.R;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int64_t i = 8 * q + e;
+        buf[e] = (gam < LR && i < a.Bdim) ? (float)__ldg(x + (l * a.Bdim + i) * a.R + c) : 0.f;
+      }
+    } else if (MODE == TM_ROWVEC && gam < LR && 8 * q < a.Bdim) {
+      ld8<TX>(x + gam * a.Bdim + 8 * q, buf);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        buf[e] = (gam < LR && 8 * q + e < a.Bdim) ? (float)__ldg(x + gam * a.Bdim + 8 * q + e) : 0.f;
+    }
+    float scu = sc;
+    if (a.cshift) scu = (gam < LR) ? ldexpf(1.0f, (int)__ldg(a.cshift + gam)) : 0.f;
+    uint32_t p0[4], p1[4], p2[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float a0x, a1x, a2x, a0y, a1y, a2y;
+      slice3i(buf[2 * e] * scu, a0x, a1x, a2x);
+      slice3i(buf[2 * e + 1] * scu, a0y, a1y, a2y);
+      p0[e] = Pack<BF16>::two(a0x, a0y);
+      p1[e] = Pack<BF16>::two(a1x, a1y);
+      p2[e] = Pack<BF16>::two(a2x, a2y);
+    }
+    uint8_t* base = img + (size_t)mt * 3 * A_BYTES + sw128_off((uint32_t)m, (uint32_t)(8 * q));
+    *reinterpret_cast<uint4*>(base) = make_uint4(p0[0], p0[1], p0[2], p0[3]);
+    *reinterpret_cast<uint4*>(base + A_BYTES) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
+    *reinterpret_cast<uint4*>(base + 2 * A_BYTES) = make_uint4(p2[0], p2[1], p2[2], p2[3]);
+  }
+}
+
 template <typename TX, bool BF16, bool GEN, bool RES, typename TR>
 int ttm_launch_t(const TtmArgs& a, int grid, int smem, cudaStream_t s) {
   static bool attr = false;
@@ -578,6 +654,7 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
     a.wb = wb;
     a.nchunk_launch = (unsigned)nchunk;
     a.bw = bw;
+    a.aimg = nullptr;
     const uint32_t bbytes = (uint32_t)a.apad * 128u;
     const uint32_t stage = 3u * 128u * 128u + ((3u * bbytes + 1023u) & ~1023u);
     a.nstage = (int)((224u * 1024u) / stage);
@@ -590,6 +667,34 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
       if (bf16 || res) ttm_prep_b<true><<<blocks, 256, 0, s>>>(u, csz, Atot, nchunk, (int)Bdim, expand, a.apad, nkt, bw, wb);
       else ttm_prep_b<false><<<blocks, 256, 0, s>>>(u, csz, Atot, nchunk, (int)Bdim, expand, a.apad, nkt, bw, wb);
       ATC_LAUNCHED(1);
+    }
+    // one K tile and several output chunks: slice the data operand once (the
+    // image stays in L2 when it is at most 64 MB) instead of once per chunk
+    if (mtiles > 0 && nkt == 1 && nchunk > 1 && (size_t)mtiles * 3 * 128 * 128 <= ((size_t)64 << 20)) {
+      uint8_t* img = nullptr;
+      ATC_TRY(Scratch::get(SLOT_TTM_AIMG, (size_t)mtiles * 3 * 128 * 128, (void**)&img));
+      const int64_t tot = mtiles * 1024;
+      const int blocks = (int)((tot + 255) / 256 < 8 * g_nsm_ttm ? (tot + 255) / 256 : 8 * g_nsm_ttm);
+      const bool gen = (R != 1), pb = bf16 || res;
+      if (xdtype == ATC_F32) {
+        if (gen) {
+          if (pb) ttm_preslice_a<float, true, true><<<blocks, 256, 0, s>>>(a, img);
+          else ttm_preslice_a<float, true, false><<<blocks, 256, 0, s>>>(a, img);
+        } else {
+          if (pb) ttm_preslice_a<float, false, true><<<blocks, 256, 0, s>>>(a, img);
+          else ttm_preslice_a<float, false, false><<<blocks, 256, 0, s>>>(a, img);
+        }
+      } else {
+        if (gen) {
+          if (pb) ttm_preslice_a<double, true, true><<<blocks, 256, 0, s>>>(a, img);
+          else ttm_preslice_a<double, true, false><<<blocks, 256, 0, s>>>(a, img);
+        } else {
+          if (pb) ttm_preslice_a<double, false, true><<<blocks, 256, 0, s>>>(a, img);
+          else ttm_preslice_a<double, false, false><<<blocks, 256, 0, s>>>(a, img);
+        }
+      }
+      ATC_LAUNCHED(1);
+      a.aimg = img;
     }
     if (mtiles > 0) {
       const bool gen = (R != 1);
@@ -625,9 +730,17 @@ int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R,
   return ttm_run(x, xdtype, L, n, R, u, r, expand, precision, y, s, xs, nullptr, 0, nullptr, expand != 0);
 }
 
+// The residual ||x - U ._k y||^2 as the tensor-core expansion into a scratch
+// tensor (the epilogue's stores do not stall it) followed by one streaming pass
+// over x and the expansion; the differences and their rounding are those of the
+// fused residual epilogue of ttm_tc_kernel (res != nullptr), whose dependent
+// loads of x left HBM mostly idle.
 int launch_ttm_residual(const float* y, int64_t L, int64_t r, int64_t R, const double* u, int64_t n, const void* x,
                         int xdtype, double* rho, cudaStream_t s) {
-  return ttm_run(y, ATC_F32, L, n, R, u, r, 1, ATC_PREC_SPLIT_BF16, nullptr, s, nullptr, x, xdtype, rho, true);
+  float* z = nullptr;
+  ATC_TRY(Scratch::get(SLOT_RES_TMP, sizeof(float) * (size_t)(L * n * R) + 256, (void**)&z));
+  ATC_TRY(ttm_run(y, ATC_F32, L, n, R, u, r, 1, ATC_PREC_SPLIT_BF16, z, s, nullptr, nullptr, 0, nullptr, true));
+  return launch_diff_norm2(x, xdtype, z, L * n * R, rho, s);
 }
 
 }  // namespace atc
