@@ -28,6 +28,7 @@
 // Run r >= 0 -> symbol s = floor(log2(r+1)) coded with the plane's table, then
 // s extra bits (r + 1 - 2^s) coded as a uniform symbol; 32-bit rANS state,
 // L = 2^23, byte-wise renormalisation, 12-bit frequencies.
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -352,40 +353,81 @@ __global__ void __launch_bounds__(32 * kPlaneChunk) plane_scan_kernel(const Seg*
 
 // Exact position of the breakpoint inside plane p_star: one CTA walks the
 // segment summaries, then re-scans the segment that holds it.
-__global__ void __launch_bounds__(kSegThreads) istar_kernel(const uint64_t* __restrict__ q, int64_t n, int64_t seg_len,
-                                                             const Seg* __restrict__ segs, int nseg, int phi,
-                                                             TrackState* st) {
-  __shared__ Seg tsum[kSegThreads];
-  __shared__ int s_seg;
+// Block-wide exclusive prefix sum of one I192 per thread (two's-complement
+// sums mod 2^192, so any grouping gives the sequential result); *total gets the
+// sum over the block.  Three barriers.
+constexpr int kIstarThreads = 512;  // >= kSegBlocks: one segment per thread
+__device__ I192 i192_block_exscan(I192 v, I192* sh, I192* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  I192 inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    I192 u;
+    u.w0 = __shfl_up_sync(0xffffffffu, inc.w0, o);
+    u.w1 = __shfl_up_sync(0xffffffffu, inc.w1, o);
+    u.w2 = __shfl_up_sync(0xffffffffu, inc.w2, o);
+    if (lane >= o) inc = i192_add(inc, u);
+  }
+  __syncthreads();
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    I192 x = (lane < nw) ? sh[lane] : i192_zero();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      I192 u;
+      u.w0 = __shfl_up_sync(0xffffffffu, x.w0, o);
+      u.w1 = __shfl_up_sync(0xffffffffu, x.w1, o);
+      u.w2 = __shfl_up_sync(0xffffffffu, x.w2, o);
+      if (lane >= o) x = i192_add(x, u);
+    }
+    if (lane < nw) sh[lane] = x;  // inclusive prefix over the warps
+  }
+  __syncthreads();
+  const I192 warp_pre = (w > 0) ? sh[w - 1] : i192_zero();
+  *total = sh[nw - 1];
+  return i192_add(warp_pre, i192_sub(inc, v));
+}
+
+// i* (the breakpoint inside plane p*): the first coefficient, in vectorised
+// order, at which the tracked error falls to the target.  Three ordered
+// first-passage searches, each an exclusive prefix sum over the block, a
+// per-entry test and a minimum: over the plane's segment summaries, over the
+// per-thread summaries inside the hit segment, then element by element inside
+// the hit thread's range.
+__global__ void __launch_bounds__(kIstarThreads) istar_kernel(const uint64_t* __restrict__ q, int64_t n, int64_t seg_len,
+                                                              const Seg* __restrict__ segs, int nseg, int phi,
+                                                              TrackState* st) {
+  __shared__ I192 sh[32];
+  __shared__ int s_first;
   __shared__ I192 s_pre;
-  __shared__ int64_t s_hit;
   const int p = st->p_star;
   if (p >= 64) return;
   const I192 T = st->t_int;
   const I192 E1 = st->e_plane;
   if (!st->reachable) return;  // i_star stays -1 (everything encoded)
-  if (threadIdx.x == 0) {
-    I192 pre = i192_zero();
-    int found = -1;
-    for (int b = 0; b < nseg; ++b) {
-      const Seg& sgm = segs[(int64_t)(phi - p) * nseg + b];
-      if (!sgm.empty) {
-        I192 low = i192_sub(E1, i192_add(pre, sgm.m));
-        if (i192_le(low, T)) { found = b; break; }
-        pre = i192_add(pre, sgm.s);
-      }
-    }
-    s_seg = found;
-    s_pre = pre;
-    s_hit = INT64_MAX;
-  }
+  const int tid = threadIdx.x;
+  I192 tot;
+  // 1. the first segment whose largest prefix reaches the target
+  Seg sg;
+  sg.empty = 1;
+  sg.s = sg.m = i192_zero();
+  if (tid < nseg) sg = segs[(int64_t)(phi - p) * nseg + tid];
+  const I192 pre = i192_block_exscan(sg.empty ? i192_zero() : sg.s, sh, &tot);
+  if (tid == 0) s_first = INT_MAX;
   __syncthreads();
-  const int b = s_seg;
-  if (b < 0) return;  // cannot happen when p_star came from plane_scan_kernel
+  if (tid < nseg && !sg.empty && i192_le(i192_sub(E1, i192_add(pre, sg.m)), T)) atomicMin(&s_first, tid);
+  __syncthreads();
+  const int b = s_first;
+  if (b == INT_MAX) return;  // cannot happen when p_star came from plane_scan_kernel
+  if (tid == b) s_pre = pre;
+  __syncthreads();
+  const I192 seg_pre = s_pre;
+  // 2. inside segment b: the first thread range that reaches it
   const int64_t s_lo = b * seg_len;
   const int64_t s_hi = min(n, s_lo + seg_len);
   const int64_t per = (seg_len + blockDim.x - 1) / blockDim.x;
-  const int64_t t_lo = min(s_hi, s_lo + threadIdx.x * per);
+  const int64_t t_lo = min(s_hi, s_lo + tid * per);
   const int64_t t_hi = min(s_hi, t_lo + per);
   Seg a;
   a.empty = 1;
@@ -400,32 +442,23 @@ __global__ void __launch_bounds__(kSegThreads) istar_kernel(const uint64_t* __re
       if (i192_lt(a.m, a.s)) a.m = a.s;
     }
   }
-  tsum[threadIdx.x] = a;
+  const I192 pre2 = i192_add(seg_pre, i192_block_exscan(a.empty ? i192_zero() : a.s, sh, &tot));
+  if (tid == 0) s_first = INT_MAX;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    // exclusive prefixes in thread order; first thread whose range reaches T
-    I192 pre = s_pre;
-    int hit_t = -1;
-    I192 hit_pre = pre;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      const Seg& x = tsum[t];
-      if (x.empty) continue;
-      if (i192_le(i192_sub(E1, i192_add(pre, x.m)), T)) { hit_t = t; hit_pre = pre; break; }
-      pre = i192_add(pre, x.s);
-    }
-    if (hit_t >= 0) {
-      const int64_t lo = min(s_hi, s_lo + hit_t * per), hi = min(s_hi, lo + per);
-      I192 run = i192_sub(E1, hit_pre);
-      for (int64_t i = lo; i < hi; ++i) {
-        const uint64_t v = q[i];
-        I192 d = i192_zero();
-        if ((v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
-        run = i192_sub(run, d);
-        if (i192_le(run, T)) {
-          st->i_star = i;
-          st->e_star = run;
-          break;
-        }
+  if (!a.empty && i192_le(i192_sub(E1, i192_add(pre2, a.m)), T)) atomicMin(&s_first, tid);
+  __syncthreads();
+  // 3. element by element inside the hit thread's range
+  if (tid == s_first) {
+    I192 run = i192_sub(E1, pre2);
+    for (int64_t i = t_lo; i < t_hi; ++i) {
+      const uint64_t v = q[i];
+      I192 d = i192_zero();
+      if ((v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+      run = i192_sub(run, d);
+      if (i192_le(run, T)) {
+        st->i_star = i;
+        st->e_star = run;
+        break;
       }
     }
   }
@@ -1318,7 +1351,7 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     if (phi < 0) return fail(ATC_ECUDA, "tracker did not terminate");
   }
   if (hst.p_star < 64 && hst.reachable) {
-    istar_kernel<<<1, kSegThreads, 0, s>>>(q, n, seg_len, segs, nseg, phi, st);
+    istar_kernel<<<1, kIstarThreads, 0, s>>>(q, n, seg_len, segs, nseg, phi, st);
     ATC_LAUNCHED(1);
     ATC_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
     ATC_CUDA_TRY(cudaStreamSynchronize(s));
