@@ -749,18 +749,54 @@ __device__ __forceinline__ uint32_t rd32(const uint8_t* p) {
   return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
 }
 
-__global__ void block_offsets_kernel(DecParams D, uint64_t* boff) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  uint64_t pos = D.tab + (uint64_t)D.nblocks * D.nplanes * 8;
-  for (int64_t b = 0; b < D.nblocks; ++b) {
-    boff[b] = pos;
+// Payload offset of every block: the sizes of its (block, plane) chunks from
+// the size table, summed per contiguous range of blocks by each thread, then a
+// block-wide exclusive scan (one CTA of kOffThreads).
+constexpr int kOffThreads = 1024;
+__global__ void __launch_bounds__(kOffThreads) block_offsets_kernel(DecParams D, uint64_t* boff) {
+  __shared__ unsigned long long sh[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t per = (D.nblocks + kOffThreads - 1) / kOffThreads;
+  const int64_t b0 = min((int64_t)tid * per, D.nblocks), b1 = min(D.nblocks, b0 + per);
+  auto block_bytes = [&](int64_t b) -> unsigned long long {
+    unsigned long long t = 0;
     for (int pi = 0; pi < D.nplanes; ++pi) {
-      const uint8_t* t = D.sec + D.tab + (b * D.nplanes + pi) * 8;
-      pos += (uint64_t)rd32(t) + rd32(t + 4);
+      const uint8_t* e = D.sec + D.tab + (b * D.nplanes + pi) * 8;
+      t += (unsigned long long)rd32(e) + rd32(e + 4);
     }
+    return t;
+  };
+  unsigned long long mine = 0;
+  for (int64_t b = b0; b < b1; ++b) mine += block_bytes(b);
+  unsigned long long inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
   }
-  boff[D.nblocks] = pos;
-  if (pos > (uint64_t)D.nbytes) atomicExch(D.err, 1);
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long x = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    sh[lane] = x;
+  }
+  __syncthreads();
+  const unsigned long long base = D.tab + (unsigned long long)D.nblocks * D.nplanes * 8;
+  unsigned long long pos = base + (w > 0 ? sh[w - 1] : 0ull) + (inc - mine);
+  for (int64_t b = b0; b < b1; ++b) {
+    boff[b] = pos;
+    pos += block_bytes(b);
+  }
+  if (tid == 0) {
+    const unsigned long long end = base + sh[31];
+    boff[D.nblocks] = end;
+    if (end > (unsigned long long)D.nbytes) atomicExch(D.err, 1);
+  }
 }
 
 // One thread per block: planes 63 .. p_star in order, then dequantize.
@@ -1488,7 +1524,7 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
   uint64_t* boff = reinterpret_cast<uint64_t*>(small + 64);
   ATC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   D.sec = dsec; D.qt = qt; D.sg = sg; D.out = core; D.err = err; D.boff = boff;
-  block_offsets_kernel<<<1, 32, 0, s>>>(D, boff);
+  block_offsets_kernel<<<1, kOffThreads, 0, s>>>(D, boff);
   ATC_LAUNCHED(1);
   if (D.block_size <= kDecMax && D.nplanes > 0) {
     // phase A: every (block, plane) chunk's runs in parallel; phase B: placement
