@@ -27,6 +27,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -138,6 +139,63 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlClocks:
+    """SM clock and throttle reasons sampled every ~2 ms in-process through the
+    NVML C library (read-only queries), so that even a timed region of a few tens
+    of milliseconds gets samples; the nvidia-smi sampler is the fallback."""
+    SW_POWER_CAP, HW_SLOWDOWN, SW_THERMAL, HW_THERMAL = 0x4, 0x8, 0x20, 0x40
+
+    def __init__(self, index):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.dev)) != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples, self.reasons = [], 0
+        self.stop_flag = threading.Event()
+        self.thread = None
+
+    def _loop(self):
+        C = self.C
+        clk, rs = C.c_uint(0), C.c_ulonglong(0)
+        while not self.stop_flag.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.dev, C.c_int(1), C.byref(clk)) == 0:  # NVML_CLOCK_SM
+                self.samples.append(clk.value)
+            if self.reasons_fn(self.dev, C.byref(rs)) == 0:
+                self.reasons |= rs.value
+            time.sleep(0.002)
+
+    def start(self):
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+        time.sleep(0.005)
+
+    def stop(self):
+        self.stop_flag.set()
+        self.thread.join(timeout=5)
+        C = self.C
+        mx = C.c_uint(0)
+        smax = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.dev, C.c_int(1), C.byref(mx)) == 0 else None
+        names = [(self.HW_SLOWDOWN, "hw_slowdown"), (self.HW_THERMAL, "hw_thermal_slowdown"),
+                 (self.SW_THERMAL, "sw_thermal_slowdown"), (self.SW_POWER_CAP, "sw_power_cap")]
+        reasons = sorted(n for bit, n in names if self.reasons & bit)
+        self.lib.nvmlShutdown()
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(self.samples), "sampler": "NVML, 2 ms, timed steps only"}
+
+
+def clock_sampler(index):
+    try:
+        return NvmlClocks(index)
+    except (OSError, AttributeError):
+        return Clocks(index)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -219,12 +277,14 @@ def run_ours(args, world, rank, local):
             raise P.AtcError(rc, P.lib().atc_last_error().decode())
         return c, s
 
-    def timed(precision, k, w):
+    def timed(precision, k, w, clocks=None):
         for _ in range(w):
             step(precision)
         torch.cuda.synchronize()
         barrier(world)
         ms, stats = [], []
+        if clocks is not None:
+            clocks.start()  # sampled over the timed steps only
         l0 = P.lib().atc_kernel_launches()
         for _ in range(k):
             flush.zero_()
@@ -237,14 +297,12 @@ def run_ours(args, world, rank, local):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
             stats.append(c.stats())
-        barrier(world)
         launches = P.lib().atc_kernel_launches() - l0
-        return ms, stats, c, s, launches
+        clk = clocks.stop() if clocks is not None else None
+        barrier(world)
+        return ms, stats, c, s, launches, clk
 
-    clocks = Clocks(local)
-    clocks.start()
-    ms, stats, c, s, launches = timed(prec, args.steps, args.warmup)
-    clk = clocks.stop()
+    ms, stats, c, s, launches, clk = timed(prec, args.steps, args.warmup, clock_sampler(local))
     per_ms = max_over_ranks(sum(ms) / len(ms), world)
     value = world * nbytes / (per_ms * 1e-3) / 1e9
 
@@ -276,7 +334,7 @@ def run_ours(args, world, rank, local):
     # plain FP64 path, same box
     fp64 = None
     if args.fp64_steps > 0 and prec != 0:
-        ms64, st64, c64, _, _ = timed(0, args.fp64_steps, 1)
+        ms64, st64, c64, _, _, _ = timed(0, args.fp64_steps, 1)
         per64 = sum(ms64) / len(ms64)
         sth64 = sum(st["ms_norm"] + st["ms_gram"] + st["ms_eig"] + st["ms_ttm"] for st in st64) / len(st64)
         fp64 = {"value": nbytes / (per64 * 1e-3) / 1e9, "ms_per_step": per64,
@@ -452,7 +510,7 @@ def run_batched(args, world, rank, local):
     plan = P.Batch([tuple(x.shape) for x in xs], eps, stream=stream)
     for _ in range(args.warmup):
         plan.run(xs, stream=stream)
-    clocks = Clocks(local)
+    clocks = clock_sampler(local)
     barrier(world)
     clocks.start()
     l0 = P.lib().atc_kernel_launches()
