@@ -168,6 +168,13 @@ def test_pipeline_split_lowrank64(P, prec):
     assert 0.98e-2 <= re <= 1e-2, re
 
 
+def _principal_angle(u, v):
+    qu, _ = np.linalg.qr(u)
+    qv, _ = np.linalg.qr(v)
+    s = np.linalg.svd(qu.T @ qv, compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("eps", [1e-3, 1e-4])
 def test_pipeline_split_bumps256(P, prec, eps):
@@ -180,6 +187,13 @@ def test_pipeline_split_bumps256(P, prec, eps):
     # block or too small a Ritz-ratio margin, and those modes take the full solver)
     if eps == 1e-3:
         assert c.stats()["subspace_modes"] == 3
+    for m in range(x.ndim):
+        u = c.factor(m).cpu().numpy()
+        assert np.abs(u.T @ u - np.eye(u.shape[1])).max() <= 1e-12
+        # the split Gram matrix is that of X on a 24-bit fixed-point grid, so the
+        # last kept directions are fixed only to about (slicing perturbation) /
+        # (eigenvalue gap at the cut): measured 4e-5 rad at 1e-3, 6e-4 at 1e-4
+        assert _principal_angle(u, ref["factors"][m]) <= 2e-3
     xh = P.atc_decompress(c.stream_bytes()).cpu().numpy()
     re = np.linalg.norm(x - xh) / np.linalg.norm(x)
     assert 0.98 * eps <= re <= eps, re
