@@ -30,6 +30,7 @@
 // All waits are bounded (2 s); on time-out the CTA raises an error flag,
 // waits for its own MMAs, frees TMEM and returns.
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -734,9 +735,13 @@ int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R,
 // tensor (the epilogue's stores do not stall it) followed by one streaming pass
 // over x and the expansion; the differences and their rounding are those of the
 // fused residual epilogue of ttm_tc_kernel (res != nullptr), whose dependent
-// loads of x left HBM mostly idle.
+// loads of x left HBM mostly idle.  ATC_RESIDUAL_FUSED=1 (read on every call)
+// selects the fused epilogue instead; it needs no scratch tensor.
 int launch_ttm_residual(const float* y, int64_t L, int64_t r, int64_t R, const double* u, int64_t n, const void* x,
                         int xdtype, double* rho, cudaStream_t s) {
+  const char* fused = getenv("ATC_RESIDUAL_FUSED");
+  if (fused && fused[0] == '1')
+    return ttm_run(y, ATC_F32, L, n, R, u, r, 1, ATC_PREC_SPLIT_BF16, nullptr, s, nullptr, x, xdtype, rho, true);
   float* z = nullptr;
   ATC_TRY(Scratch::get(SLOT_RES_TMP, sizeof(float) * (size_t)(L * n * R) + 256, (void**)&z));
   ATC_TRY(ttm_run(y, ATC_F32, L, n, R, u, r, 1, ATC_PREC_SPLIT_BF16, z, s, nullptr, nullptr, 0, nullptr, true));

@@ -214,3 +214,20 @@ def test_decompress_split_expansion(P, prec):
     assert np.array_equal(xs64, xs)
     re = np.linalg.norm(x - xs) / nx
     assert 0.98e-2 <= re <= 1e-2, re
+
+
+def test_residual_fused_and_streaming_agree(P, monkeypatch):
+    """The certification residual computed by the fused tensor-core epilogue
+    (ATC_RESIDUAL_FUSED=1) and by the expansion + streaming pass sums the same
+    FP32-rounded differences in different orders: the ranks, the certified
+    discarded energy and the stream agree."""
+    x = synth.gaussian_bumps()
+    out = []
+    for fused in ("1", "0"):
+        monkeypatch.setenv("ATC_RESIDUAL_FUSED", fused)
+        c = P.atc_compress(cuda(x), 1e-3, precision=1)
+        out.append((c.ranks(), c.stats()["sse_trunc"], c.stats()["norm2"]))
+    (r1, s1, n1), (r2, s2, n2) = out
+    assert r1 == r2
+    assert abs(s1 - s2) <= 1e-9 * n1
+
