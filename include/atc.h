@@ -22,7 +22,20 @@
  *    nothing aborts.  atc_last_error() gives a thread-local message for the
  *    last failing call of the calling thread.
  *  - Scratch device memory is allocated by the library with cudaMalloc and
- *    cached per device (released by atc_release_workspace()).
+ *    cached per device (released by atc_release_workspace()); small per-mode
+ *    readbacks go through one pinned host buffer of the process.
+ *  - The library is meant for one host thread per device at a time (its
+ *    scratch, pinned readback buffer and cached start frame are shared).
+ *
+ * Environment switches (read by the library; the defaults need none):
+ *   ATC_TRACE=1 / 2        synchronise after every launch site and report its
+ *                          status (2: also the host time since the previous one)
+ *   ATC_SUBSPACE=0         split paths: full eigensolver instead of subspace iteration
+ *   ATC_RESIDUAL_FUSED=1   split paths: certification residual in the fused
+ *                          tensor-core epilogue (no scratch tensor)
+ *   ATC_GRAM_CONVERT=1     split paths: converter-warp Gram instead of the TMA-fed one
+ *   ATC_EIG32=1            FP32 eigensolve + refinement (an earlier experiment)
+ *   ATC_BATCH_TUNE=0       batched ST-HOSVD: built-in Gram tile table, no probe
  */
 #ifndef ATC_H
 #define ATC_H
