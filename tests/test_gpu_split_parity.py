@@ -183,8 +183,8 @@ def test_pipeline_split_bumps256(P, prec, eps):
     c = P.atc_compress(cuda(x), eps, precision=prec)
     assert c.ranks() == ref["ranks"], (c.ranks(), ref["ranks"])
     # at 1e-3 every mode's leading eigenvectors come from the subspace iteration
-    # (at 1e-4 the ranks near 24 leave too few spare columns of the 32-column
-    # block or too small a Ritz-ratio margin, and those modes take the full solver)
+    # (at 1e-4, ranks near 24, a mode may also take the full solver; the ranks are
+    # certified either way)
     if eps == 1e-3:
         assert c.stats()["subspace_modes"] == 3
     for m in range(x.ndim):
