@@ -3,7 +3,7 @@
  *
  * The library computes the hot path of the ATC Tucker compressor (arXiv
  * 2107.01384) on one NVIDIA GB300 (sm_103a):
- *   ||X||^2 -> per mode: Gram SYRK -> FP64 eigensolve -> rank choice ->
+ *   ||X||^2 -> per mode: Gram SYRK -> eigensolve -> rank choice ->
  *   projection TTM (Algorithm 1, Section 4.1) -> core storage order ->
  *   scaling / rounding -> exact bit-plane tracking and breakpoint ->
  *   run-length + rANS block encoding (Sections 3.3, 4.2, 4.3, supplement S.6),
@@ -58,12 +58,20 @@ extern "C" {
 
 typedef enum { ATC_F32 = 1, ATC_F64 = 2 } atc_dtype;
 
-/* Arithmetic of the Gram and projection contractions.  The eigensolve and the
- * discarded-energy sums that choose ranks are FP64 in every mode. */
+/* Arithmetic of the contractions and of the eigensolver.  In every mode the
+ * discarded-energy sums that choose ranks are FP64.
+ *  FP64:  FP64 SIMT contractions and intermediates, FP64 eigensolver, ranks from
+ *         the eigenvalue tails.
+ *  SPLIT: tcgen05 contractions on three integer slices per value (each exact in
+ *         bf16 / fp16), all nine slice products accumulated in FP32 without
+ *         rounding, FP64 split-K sums; FP32 intermediates; leading eigenvectors
+ *         by double-float subspace iteration + Rayleigh-Ritz for mode lengths
+ *         64..768 (else a double-float tridiagonal solver); ranks certified from
+ *         the measured tails ||X - U ._k Y||^2 + sum_{j>=r} ||Y_j||^2. */
 typedef enum {
-  ATC_PREC_FP64 = 0,       /* plain FP64 SIMT contractions, FP64 intermediates */
-  ATC_PREC_SPLIT_BF16 = 1, /* x = hi + lo in bf16, 3 tcgen05 products, FP32 accumulate, FP64 split-K sum */
-  ATC_PREC_SPLIT_FP16 = 2  /* same with fp16 halves and a power-of-two pre-scale */
+  ATC_PREC_FP64 = 0,       /* plain FP64 */
+  ATC_PREC_SPLIT_BF16 = 1, /* split, bf16 slices */
+  ATC_PREC_SPLIT_FP16 = 2  /* split, fp16 slices */
 } atc_precision;
 
 typedef enum {
