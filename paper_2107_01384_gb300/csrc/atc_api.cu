@@ -700,7 +700,7 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         };
         bool done = false;
         // Split paths, n >= 64: the leading eigenvectors by subspace iteration
-        // (40 columns, 1 iteration, Rayleigh-Ritz); the Rayleigh-Ritz kernel
+        // (32 columns, 1 iteration, Rayleigh-Ritz); the Rayleigh-Ritz kernel
         // takes the provisional rank and passes the subspace when the Ritz
         // values show convergence for it; else the full solver.
         if (opt.precision != ATC_PREC_FP64 && n >= 64 && subspace_enabled() &&

@@ -4,28 +4,30 @@
 // arithmetic (pairs of FP32: GB300 issues FP64 at 1/64 of the FP32 rate and
 // every stage below is a chain of dependent steps), with the whole problem in
 // shared memory:
-//   1. Householder tridiagonalisation T = Q_T^T B Q_T (K - 2 steps, two CTA
-//      barriers a step: a warp per row forms p = tau A v; warp 0 updates the
-//      next row itself and builds the next reflector while the other warps
-//      apply the rank-2 update to the remaining rows).
+//   1. Householder tridiagonalisation T = Q_T^T B Q_T on the lower triangle
+//      (K - 2 steps, two CTA barriers a step: one thread per row forms
+//      p = tau A v; warp 0 updates column s+1 and builds the next reflector
+//      from it while warps of the other SM sub-partitions apply the rank-2
+//      update to the remaining columns).
 //   2. All K eigenvalues by Sturm counts (number of sign changes of the leading
-//      principal minors of T - x I, one dd multiply-add pair per row with
-//      power-of-two rescaling): one shared round of 1024 geometrically spaced
-//      points brackets every eigenvalue within a factor 1.09, then a group of
-//      16 lanes per eigenvalue narrows its bracket 17-fold per round to
-//      2^-30 relative.
+//      principal minors of T - x I, one double-float multiply-add pair per row
+//      with power-of-two rescaling): one shared round of 1024 geometrically
+//      spaced points brackets every eigenvalue within a factor 1.09, then a
+//      group of 8 lanes per eigenvalue narrows its bracket 9-fold per round to
+//      2^-30 relative (brackets in double-float, points in float).
 //   3. The provisional rank from the Ritz values, rp = the smallest r with
-//      trace(G) - sum_{j<r} theta_j <= budget, and the convergence test of the
-//      subspace, (|theta_K| / theta_rp)^T <= conv, on the device in FP64; the
+//      trace(G) - sum_{j<r} theta_j <= budget (FP64 warp prefix sum), and the
+//      convergence test of the subspace, (|theta_K| / theta_rp)^T <= conv; the
 //      vector count is nv = rp + extra (at most nmax).
-//   4. The leading nv eigenvectors of T by inverse iteration (one thread per
-//      vector: LU with partial pivoting of T - theta I, two solves), groups of
-//      eigenvalues closer than 2^-12 relative re-orthonormalised by classical
+//   4. The leading nv eigenvectors of T by inverse iteration (lane per vector:
+//      LU with partial pivoting of T - theta I as selects, two solves), groups
+//      of eigenvalues closer than 2^-12 relative re-orthonormalised by
 //      Gram-Schmidt applied twice (a warp per group), then the
-//      back-transformation Y = Q_T Z (a warp per vector), normalised, largest
-//      entry positive.
+//      back-transformation Y = Q_T Z (two lanes per vector), normalised,
+//      largest entry positive.
 // Outputs: theta (K, descending, FP64), decision = {rp, nv (0 unless the
-// subspace passed), passed}, Y (K x nv row-major, FP64).
+// subspace passed), passed, the tensor-core error word}, Y (K x nv row-major,
+// FP64).
 #include <math.h>
 #include <stdint.h>
 

@@ -6,7 +6,7 @@
 // r_h (+ margin) eigenvectors of the mode Gram matrix to moderate accuracy and
 // its eigenvalues only to pick a provisional rank.  For the smooth fields this
 // library targets the Gram spectrum falls by many orders of magnitude within
-// the first few dozen eigenvalues, and K = 40 columns of
+// the first few dozen eigenvalues, and K = 32 columns of
 //     V <- orth(G V)  (T times),  B = V^T G V = Y Theta Y^T,  U = V Y
 // reach the leading subspace to the angles the certification needs, with GEMM
 // work and short QR chains instead of the n - 2 dependent Householder steps of
