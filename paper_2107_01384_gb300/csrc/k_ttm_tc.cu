@@ -22,6 +22,9 @@
 //              overlapped with the next tile's MMAs (two TMEM buffers);
 //   warps 4-11 converters: coalesced loads of X (the unfolding is index
 //              arithmetic), slicing, K-major 128-byte-swizzled stores to smem;
+//              for single-K-tile products with several output chunks the
+//              operand is sliced once beforehand (ttm_preslice_a) and one
+//              thread of warp 4 bulk-copies each stage's image instead;
 //   warp 12    MMA issuer (one elected thread), 9 MMAs per K step;
 //   warp 13    B producer: bulk-async copies (cp.async.bulk, TMA engine) of the
 //              pre-sliced, pre-swizzled factor tiles, completing on the
