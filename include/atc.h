@@ -34,7 +34,6 @@
  *   ATC_RESIDUAL_FUSED=1   split paths: certification residual in the fused
  *                          tensor-core epilogue (no scratch tensor)
  *   ATC_GRAM_CONVERT=1     split paths: converter-warp Gram instead of the TMA-fed one
- *   ATC_EIG32=1            FP32 eigensolve + refinement (an earlier experiment)
  *   ATC_BATCH_TUNE=0       batched ST-HOSVD: built-in Gram tile table, no probe
  */
 #ifndef ATC_H
@@ -299,18 +298,24 @@ int atc_quantize_core(const double* core_dev, int64_t n, double target_sse, int 
 
 /*
  * atc_gram with precision ATC_PREC_FP64, for callers that cannot allocate
- * device memory (for example code running while somebody else builds a CUDA
- * graph around it, or a host that gives this library a fixed memory budget).
+ * device memory: real-time paths that must not block on the device allocator
+ * (cudaMalloc can synchronise the device), or a host that gives this library a
+ * fixed memory budget and accounts for every byte it may take.
  * The paper has no counterpart: it is an integration variant of the Gram step.
  *   Same arguments, layout and result as atc_gram (g_dev: n*n doubles, full
  *   symmetric).  It calls no cudaMalloc, cudaFree or allocating library
  *   routine: the split-K partial sums live in a 4 MiB array in this library's
  *   device memory, held by every GPU that loads the library until exit.
- *   Limit: n * n <= 524288 (n <= 724); larger n returns ATC_EINVAL.
+ *   Limit: n <= 724 (n * n <= 524288); larger n, or L * n * R beyond int64,
+ *   returns ATC_EINVAL before anything runs.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
- *   All calls share the one array: calls that overlap on the GPU (different
- *   streams or threads at the same time) race and give wrong results.
+ *   (cudaGetSymbolAddress) and keeps it; make that first call before any
+ *   stream capture.  After a device reset call atc_release_workspace() so that
+ *   the next call looks the address up again.
+ *   All calls share the one array and it keeps the last call's contents (every
+ *   entry a call reads is written by that call first): calls that overlap on
+ *   the GPU (different streams or threads at the same time) race and give
+ *   wrong results.
  */
 int atc_gram_fp64_noalloc(const void* x_dev, int dtype, int64_t L, int64_t n, int64_t R, double* g_dev,
                           void* stream);
@@ -321,7 +326,8 @@ int atc_dequantize_core(const uint8_t* bytes, size_t nbytes, double* core_dev, i
 void atc_free_buffer(void* p);
 /* Number of CUDA kernels this library has launched in this process (host counter). */
 long long atc_kernel_launches(void);
-/* Free the cached device scratch of the current device. */
+/* Free the cached device scratch of the current device (and forget the looked-up
+   address of the no-allocation Gram array there). */
 int atc_release_workspace(void);
 const char* atc_last_error(void);
 

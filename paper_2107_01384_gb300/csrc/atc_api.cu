@@ -228,13 +228,10 @@ constexpr int kSubMargin = 4;  // columns kept beyond the largest certified cand
 // tighter bound would reject converged subspaces whenever theta_rp < 1e-8
 // theta_1; the ranks are certified from measured tails either way
 constexpr double kSubConv = 1e-4;
+// ATC_SUBSPACE=0 (read on every call): the full eigensolver on every mode
 bool subspace_enabled() {
-  static int on = -1;
-  if (on < 0) {
-    const char* e = getenv("ATC_SUBSPACE");
-    on = (e && e[0] == '0') ? 0 : 1;
-  }
-  return on == 1;
+  const char* e = getenv("ATC_SUBSPACE");
+  return !(e && e[0] == '0');
 }
 
 int gram_dispatch(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g, cudaStream_t s,
@@ -387,7 +384,11 @@ const char* atc_last_error(void) { return g_err.c_str(); }
 
 void atc_free_buffer(void* p) { free(p); }
 
-int atc_release_workspace(void) { return Scratch::release_all(); }
+int atc_release_workspace(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) noalloc_forget(dev);
+  return Scratch::release_all();
+}
 
 long long atc_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED); }
 
@@ -408,10 +409,6 @@ int atc_eig_sym(const double* g_dev, int n, double* lam_dev, double* v_dev, int 
     return fail(ATC_EINVAL, "atc_eig_sym: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   ATC_TRY(launch_eig_sym(g_dev, n, lam_dev, v_dev, nvec, s));
-  if (eig32_enabled() && eig32_supported(n)) {
-    ATC_CUDA_TRY(cudaStreamSynchronize(s));
-    return ATC_OK;
-  }
   return eig_check(s);
 }
 
@@ -589,51 +586,7 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
     {
       const double budget =
           (opt.rank_rule == ATC_RANK_STATIC) ? budget_total / d : (budget_total - used) / (double)(d - step);
-      if (eig32_enabled() && eig32_supported((int)n)) {
-        // FP32 eigensolve + FP64 refinement of the top m eigenpairs; the rank
-        // rule reads tail(r) = trace(G) - sum_{j<r} lambda_j from the refined
-        // eigenvalues (FP64).
-        std::vector<double> l32, top;
-        double tr = 0.0;
-        rc = eig32_values(G, (int)n, &l32, &tr, s);
-        if (rc) return bail(rc);
-        auto pick = [&](const std::vector<double>& lv, int lim, double* dsc) -> int {
-          double acc = 0.0;
-          for (int rr = 1; rr <= lim; ++rr) {
-            acc += lv[rr - 1];
-            double t = tr - acc;
-            if (t < 0.0) t = 0.0;
-            if (t <= budget) { *dsc = t; return rr; }
-          }
-          return -1;
-        };
-        double d32 = 0.0;
-        int r32 = pick(l32, (int)n, &d32);
-        if (r32 < 1) r32 = (int)n;
-        int mref = std::min<int>((int)n, r32 + 4);
-        double* vtmp = nullptr;
-        rc = Scratch::get(SLOT_EIG_A, sizeof(double) * (size_t)n * n, (void**)&vtmp);
-        if (rc) return bail(rc);
-        for (;;) {
-          rc = eig32_refine(mref, lam, vtmp, mref, &top, s);
-          if (rc) return bail(rc);
-          r = pick(top, mref, &disc);
-          if (r >= 1 && (r < mref || mref == n)) break;
-          if (mref == n) { r = (int)n; disc = 0.0; break; }
-          mref = std::min<int>((int)n, 2 * mref);
-        }
-        if (tc_err) {
-          int he = 0;
-          if (cudaMemcpy(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-            return bail(fail(ATC_ECUDA, "error flag readback failed"));
-          if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
-        }
-        if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
-          return bail(fail(ATC_ENOMEM, "factor allocation failed"));
-        if (cudaMemcpy2DAsync(c->factors[m], sizeof(double) * r, vtmp, sizeof(double) * mref, sizeof(double) * r, n,
-                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-          return bail(fail(ATC_ECUDA, "factor copy failed"));
-      } else {
+      {
         // Split paths: the sliced Gram is that of X rounded to 24-bit fixed
         // point, summed in FP32 orders; its eigenvalues carry a small shift,
         // far below what moves the eigenvectors but not always below the

@@ -144,11 +144,6 @@ int launch_eig_more(int n, int K, double* lam, cudaStream_t s);
 int launch_rank_select(const double* lam, int n, double budget, int* r_dev, double* disc_dev, cudaStream_t s);
 int eig_read_error(int* err);
 int* eig_error_flag_dev();  // device word of the grid-barrier time-out flag, or nullptr
-// FP32-stage + FP64-refinement eigensolver (k_eig32.cu), n <= 256
-bool eig32_supported(int n);
-bool eig32_enabled();
-int eig32_values(const double* G, int n, std::vector<double>* lam_host, double* trace, cudaStream_t s);
-int eig32_refine(int m, double* lam_dev, double* v_dev, int nvec, std::vector<double>* lam_top, cudaStream_t s);
 // Leading eigenpairs of a symmetric PSD n x n FP64 matrix by subspace iteration
 // (T iterations of a K-column block, K <= min(64, n), n K double-floats in
 // shared memory) and Rayleigh-Ritz (k_subspace.cu, k_rr.cu).  Enqueues the
@@ -178,5 +173,8 @@ struct QuantResult {
 int quantize_encode(const double* core, int64_t n, double target, int block_size, cudaStream_t s,
                     std::string* out, QuantResult* res, float* ms_quant, float* ms_encode);
 int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t n, cudaStream_t s);
+
+// drop the cached device address of the no-allocation Gram array of `dev`
+void noalloc_forget(int dev);
 
 }  // namespace atc

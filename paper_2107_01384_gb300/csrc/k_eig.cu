@@ -1552,13 +1552,6 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
 }
 
 int launch_eig_sym(const double* g, int n, double* lam, double* v, int nvec, cudaStream_t s) {
-  if (eig32_enabled() && eig32_supported(n)) {
-    std::vector<double> lh, top;
-    double tr = 0.0;
-    ATC_TRY(eig32_values(g, n, &lh, &tr, s));
-    ATC_TRY(eig32_refine(n, lam, v, nvec, &top, s));
-    return ATC_OK;
-  }
   g_state.flags = nullptr;
   ATC_TRY(launch_eig_values(g, n, lam, s));
   ATC_TRY(launch_eig_vectors(n, nvec, v, s));

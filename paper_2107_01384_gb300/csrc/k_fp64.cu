@@ -329,19 +329,32 @@ int launch_ttm_fp64(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, 
 // ---------------------------------------------------------------------------
 // Gram matrix without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being built around it by someone else, real-time paths that must not block
-// on the allocator, or hosts that hand this library a fixed memory budget.
-// For them the split-K partial sums of the FP64 Gram kernel live in the
+// Some callers cannot call cudaMalloc: real-time paths that must not block on
+// the device allocator (cudaMalloc can synchronise the device), or hosts that
+// hand this library a fixed memory budget and account for every byte it may
+// take.  For them the split-K partial sums of the FP64 Gram kernel live in the
 // file-scope device array below instead of the cached scratch arena.  Every
 // GPU that loads this library holds the array (4 MiB) until the process exits.
 namespace {
 constexpr size_t kNoAllocDoubles = (size_t)1 << 19;  // 4 MiB of FP64 partial sums
+constexpr int64_t kNoAllocMaxN = 724;                // largest n with n * n <= kNoAllocDoubles
+static_assert(kNoAllocMaxN * kNoAllocMaxN <= (int64_t)kNoAllocDoubles &&
+                  (kNoAllocMaxN + 1) * (kNoAllocMaxN + 1) > (int64_t)kNoAllocDoubles,
+              "no-allocation limit");
 __device__ __align__(256) double g_noalloc_part[kNoAllocDoubles];
 constexpr int kMaxDevices = 64;
 double* g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_part, per device
 std::mutex g_noalloc_mu;
 }  // namespace
+
+// Forget the looked-up address of the no-allocation array on `dev` (called
+// where the library drops its per-device state: after a device reset the
+// module is loaded again and the array may sit at another address).
+void noalloc_forget(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  g_noalloc_ptr[dev] = nullptr;
+}
 
 }  // namespace atc
 
@@ -350,9 +363,13 @@ extern "C" int atc_gram_fp64_noalloc(const void* x_dev, int dtype, int64_t L, in
   using namespace atc;
   if (!x_dev || !g_dev || L < 1 || n < 1 || R < 1 || (dtype != ATC_F32 && dtype != ATC_F64))
     return fail(ATC_EINVAL, "atc_gram_fp64_noalloc: bad arguments");
-  if ((size_t)n * (size_t)n > kNoAllocDoubles)
-    return fail(ATC_EINVAL, "atc_gram_fp64_noalloc: n = %lld exceeds the no-allocation maximum (n*n <= %zu, n <= 724)",
-                (long long)n, kNoAllocDoubles);
+  // n is checked on its own before any product is formed (n * n could wrap)
+  if (n > kNoAllocMaxN)
+    return fail(ATC_EINVAL, "atc_gram_fp64_noalloc: n = %lld exceeds the no-allocation maximum (n <= %lld)",
+                (long long)n, (long long)kNoAllocMaxN);
+  // every element index l n R + i R + c must fit in int64
+  if (L > INT64_MAX / R || L * R > (INT64_MAX / 2) / n)
+    return fail(ATC_EINVAL, "atc_gram_fp64_noalloc: L * n * R overflows");
   int dev = 0;
   ATC_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(ATC_EUNSUP, "atc_gram_fp64_noalloc: device index %d", dev);

@@ -685,14 +685,11 @@ int launch_t(const GramArgs& a, int grid, cudaStream_t s) {
 int g_nsm = 0;
 int g_scale_rot = 0;
 
-// ATC_GRAM_CONVERT=1 selects the converter-warp kernel (the TMA-fed one is the default)
+// ATC_GRAM_CONVERT=1 (read on every call) selects the converter-warp kernel
+// (the TMA-fed one is the default)
 bool gram_tma_off() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("ATC_GRAM_CONVERT");
-    v = (e && e[0] == '1') ? 1 : 0;
-  }
-  return v == 1;
+  const char* e = getenv("ATC_GRAM_CONVERT");
+  return e && e[0] == '1';
 }
 
 }  // namespace

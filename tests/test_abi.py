@@ -66,6 +66,12 @@ def test_host_validation_rejects_bad_arguments(lib):
     opt.mode_order = order
     assert lib.atc_compress(fake, dims, 3, 1, 1e-2, C.byref(opt), C.byref(h)) == -1
     assert b"permutation" in lib.atc_last_error()
+    # the no-allocation Gram checks n before forming n * n (2^32 would wrap to 0)
+    # and refuses an index range beyond int64, before touching the device
+    assert lib.atc_gram_fp64_noalloc(fake, 1, 1, 2 ** 32, 1, fake, None) == -1
+    assert b"no-allocation maximum" in lib.atc_last_error()
+    assert lib.atc_gram_fp64_noalloc(fake, 1, 2 ** 40, 2, 2 ** 40, fake, None) == -1
+    assert b"overflows" in lib.atc_last_error()
 
 
 def test_stream_header_checks_on_host(lib):

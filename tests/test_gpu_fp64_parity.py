@@ -186,22 +186,30 @@ def _check_pipeline(P, x, eps, rtmss=0.5, mode_order=None, rank_rule=0):
     nx = np.linalg.norm(x)
     re = np.linalg.norm(x - xh) / nx
     assert re <= eps, re
-    if int(np.prod(c.ranks())) >= 1000:
-        # the breakpoint moves one bit at a time: with enough coefficients the
-        # error lands within 2% of the target (tiny cores step too coarsely)
-        assert re >= 0.98 * eps, re
     xo = OP.decompress(stream)   # the oracle decodes the GPU stream
     assert np.linalg.norm(xo - xh) <= 1e-9 * nx
     # the oracle's own compression reconstructs to the same tensor within 1e-5
-    s_ref, _ = OP.compress(x, eps, rtmss=rtmss, mode_order=mode_order,
-                           rank_rule="static" if rank_rule == 0 else "adaptive")
+    s_ref, info_ref = OP.compress(x, eps, rtmss=rtmss, mode_order=mode_order,
+                                  rank_rule="static" if rank_rule == 0 else "adaptive")
     xr = OP.decompress(s_ref)
     assert np.linalg.norm(xr - xh) <= 1e-5 * nx
     re_ref = np.linalg.norm(x - xr) / nx
     assert abs(re - re_ref) <= 1e-4 * eps
+    # within 2% of the target wherever the oracle itself lands there (a tiny
+    # core can step past it: the 50 x 33 matrix below reaches 0.921 eps in the
+    # oracle too, one quantization bit being a large share of the target)
+    if re_ref >= 0.98 * eps:
+        assert re >= 0.98 * eps, re
+    # storage order and every header field of the stream equal the oracle's
+    assert list(st["storage_order"]) == O.storage_order(ref["ranks"])
+    hg, hr = OP.parse(stream), OP.parse(s_ref)
+    for key in ("dims", "ranks", "perm", "dtype"):
+        assert hg[key] == hr[key], (key, hg[key], hr[key])
+    qg, qr = OQ.peek(hg["core_stream"]), OQ.peek(hr["core_stream"])
+    assert qg == qr, (qg, qr)
     # bit-exact quantizer on the GPU's own core
     core = c.core().cpu().numpy()
-    perm = st["storage_order"]
+    perm = O.storage_order(c.ranks())
     vec = np.ascontiguousarray(np.transpose(core, perm)).ravel()
     sec, _ = OQ.compress_core(vec, st["target_sse"] - st["sse_trunc"], 4096)
     assert OP.parse(stream)["core_stream"] == sec
@@ -261,6 +269,8 @@ def test_pipeline_hyperspectral_split(P, cube, prec):
     xh = P.atc_decompress(c.stream_bytes(), out_dtype=torch.float32, precision=prec).cpu().numpy()
     re = np.linalg.norm(cube.astype(np.float64) - xh) / np.linalg.norm(cube.astype(np.float64))
     assert 0.98e-2 <= re <= 1e-2, re
+    from test_gpu_split_parity import _check_split_against_oracle
+    _check_split_against_oracle(P, c, cube, 1e-2, ref)
 
 
 @pytest.mark.parametrize("prec", [0, 1])

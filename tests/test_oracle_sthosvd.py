@@ -157,3 +157,50 @@ def test_invalid_arguments():
             O.sthosvd(x, eps)
     with pytest.raises(ValueError):
         O.sthosvd(x, 0.1, rtmss=1.5)
+
+
+def test_storage_order_hand_worked_cases():
+    """Supplement S.2: the core's modes are stored in order of increasing size
+    (the shortest mode first, i.e. slowest-varying in the lexicographic
+    vectorisation), ties by lower index.  Worked by hand."""
+    assert O.storage_order([19, 18, 21]) == [1, 0, 2]
+    assert O.storage_order([8, 8, 8]) == [0, 1, 2]          # all equal: identity
+    assert O.storage_order([5, 3, 5]) == [1, 0, 2]          # tie between 0 and 2 keeps 0 first
+    assert O.storage_order([4, 4, 2]) == [2, 0, 1]
+    assert O.storage_order([7, 2, 7, 1]) == [3, 1, 0, 2]    # 4-D with a tie
+    assert O.storage_order([3, 3, 3, 3]) == [0, 1, 2, 3]
+    assert O.storage_order([9, 1]) == [1, 0]
+    assert O.storage_order([6]) == [0]
+    # decreasing sizes reverse completely
+    assert O.storage_order([40, 30, 20, 10]) == [3, 2, 1, 0]
+
+
+def test_storage_order_brute_force():
+    """Against brute force over all d! permutations: the storage order is the
+    lexicographically first permutation whose permuted sizes do not decrease
+    (a permutation search, not a sort)."""
+    rng = np.random.default_rng(23)
+    for _ in range(200):
+        d = int(rng.integers(1, 6))
+        ranks = [int(v) for v in rng.integers(1, 5, size=d)]
+        ok = [p for p in itertools.permutations(range(d))
+              if all(ranks[p[i]] <= ranks[p[i + 1]] for i in range(d - 1))]
+        assert O.storage_order(ranks) == list(min(ok))
+
+
+def test_vectorisation_in_storage_order_by_hand():
+    """The vectorised core in storage order, written out with explicit loops:
+    ranks (4, 2, 3) give storage order (1, 2, 0), i.e. the core is read as
+    b[a, b, c] at position b*12 + c*4 + a (Section 3.3 vectorisation,
+    lexicographic, last storage index fastest)."""
+    from oracle import pipeline as OP
+    core = np.arange(24, dtype=np.float64).reshape(4, 2, 3) * 1.5 - 7.0
+    perm = O.storage_order(list(core.shape))
+    assert perm == [1, 2, 0]
+    vec = OP.vectorize_core(core, perm)
+    for a in range(4):
+        for b in range(2):
+            for c in range(3):
+                assert vec[b * 12 + c * 4 + a] == core[a, b, c]
+    # and back
+    assert np.array_equal(OP.devectorize_core(vec, list(core.shape), perm), core)
