@@ -35,7 +35,6 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "ST-HOSVD input GB/s (mixed vs FP64 plain, same GB300) at rel err 1e-3; TFLOP/s"
-WORKLOAD = "gaussian_bumps_256x256x256_f32"
 PRECISIONS = {"fp16": 2, "bf16": 1, "fp64": 0}
 
 
@@ -53,9 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="batched512: skip the one-tensor-at-a-time comparison (for profiling runs)")
-    ap.add_argument("--workload", default="bumps256", choices=["bumps256", "batched512"],
-                    help="bumps256: the 256^3 single-tensor step (default); batched512: 512 uneven tensors "
-                         "in one persistent graph-replayed launch")
+    ap.add_argument("--workload", default="bumps256", choices=["bumps256", "turbulence1024", "batched512"],
+                    help="bumps256: the 256^3 single-tensor step (default); turbulence1024: the 1024^3 "
+                         "turbulence-like field (full ranks: the compute-bound case); batched512: 512 uneven "
+                         "tensors in one persistent graph-replayed launch")
     return ap.parse_args()
 
 
@@ -204,9 +204,29 @@ def load_peaks():
     return 6800.0, 1900.0, 1700.0, "fallback"
 
 
-def workload():
+WORKLOADS = {
+    "bumps256": "gaussian_bumps_256x256x256_f32",
+    "turbulence1024": "turbulence_1024x1024x1024_f32 (|k|^-5/3 spectrum, random phases, RMS 1)",
+}
+
+
+def workload(name="bumps256"):
     import synth
+    if name == "turbulence1024":
+        # the CPU-side stand-in (oracle sample): the 256^3 field of the same recipe
+        return synth.turbulence(n=256)
     return synth.gaussian_bumps()
+
+
+def workload_device(name, dev):
+    """The timed input on the device (and its host copy for the end-to-end leg)."""
+    import torch
+    import synth
+    if name == "turbulence1024":
+        xd = synth.turbulence(n=1024, device=dev)
+        return xd, xd.cpu().numpy()
+    x = synth.gaussian_bumps()
+    return torch.from_numpy(x).to(dev), x
 
 
 def time_oracle_step(x, eps):
@@ -218,21 +238,23 @@ def time_oracle_step(x, eps):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(x, eps, budget_s=12.0, max_reps=1000):
+def cpu_baseline(x, eps, name="bumps256", budget_s=12.0, max_reps=1000):
     reps, total = 0, 0.0
     while reps < max_reps and (total < budget_s or reps == 0):
         total += time_oracle_step(x, eps)
         reps += 1
     per = total / reps
+    what = (f"full {WORKLOADS[name]}" if name == "bumps256" else
+            f"the 256^3 field of the same recipe as {WORKLOADS[name]} (the 1024^3 one takes minutes on the host)")
     return {"value": x.nbytes / per / 1e9, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"full {WORKLOAD} (ST-HOSVD + quantize + encode + decode + expand), {reps} repetition(s), "
+            "sample": f"{what} (ST-HOSVD + quantize + encode + decode + expand), {reps} repetition(s), "
                       f"{per:.2f} s each; NumPy BLAS threads + single-threaded C quantizer"}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    x = workload()
+    x = workload(args.workload)
     for _ in range(args.warmup):
         time_oracle_step(x, args.eps)
     times = [time_oracle_step(x, args.eps) for _ in range(args.steps)]
@@ -241,11 +263,67 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rel_eps": args.eps, "l2": "input 67 MB; oracle runs on the host"},
+            "config": {"workload": WORKLOADS.get(args.workload, args.workload), "rel_eps": args.eps,
+                       "l2": "oracle runs on the host"},
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"each step = one full oracle compress + decompress of {WORKLOAD}"},
+                             "sample": ("each step = one full oracle compress + decompress of "
+                                        + (WORKLOADS["bumps256"] if args.workload == "bumps256" else
+                                           "the 256^3 field of the same recipe as " + WORKLOADS[args.workload]))},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+FP32_OPS_PER_CLK_SM = 128   # FP32 lanes per SM (4 SMSPs x 32)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal, dense; the profiling recipe's table)
+TENSOR_KERNELS = ("gram_tma_kernel", "ttm_tc_kernel")
+FP64_KERNELS = ("sub_gemm_part_kernel", "gram_fp64_kernel", "ttm_fp64_kernel")
+DD_KERNELS = ("qr_col_kernel", "sub_qr_kernel", "sub_qform_kernel", "rr_jacobi_kernel")
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# kernels as they stand, from the ncu captures summarised under profiles/
+# (file named per entry); a kernel changed since its capture has no entry.
+TRAFFIC = {}
+
+
+def roofline_of(name, d, hbm, bf16s, fp32_peak, fp64_peak, peak_src, sm_mhz, sms, args):
+    """Roofline entry of kernel `name` from its kernel-timer totals d (launches,
+    ms, algorithmic bytes / flops, issued tensor flops): achieved = algorithmic
+    work / device time, against the peak of the resource that bounds it."""
+    if not d or d["ms"] <= 0:
+        return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+    t = d["ms"] * 1e-3
+    gbs = d["bytes"] / t / 1e9
+    tf = d["flops"] / t / 1e12
+    ti = d["issued"] / t / 1e12
+    base = name.split("(")[0]
+    tr = TRAFFIC.get((name, args.workload))
+    out = {"kernel": name, "launches": d["launches"], "avg_launch_us": 1e3 * d["ms"] / d["launches"],
+           "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+           "algorithmic_flops_per_launch": d["flops"] / d["launches"],
+           "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None}
+    if base in TENSOR_KERNELS:
+        fh, ft = gbs / hbm, ti / bf16s
+        if ft >= fh:
+            out.update(bound="tensor", achieved=tf, peak=bf16s, unit="TFLOP/s", frac=tf / bf16s,
+                       issued_tflops=ti, issued_frac=ft, hbm_gbs=gbs, hbm_frac=fh,
+                       peak_source=peak_src + " sustained bf16 (MEASURED_PEAKS.json); achieved = the operation's "
+                       "FLOPs, issued = all slice products over the padded tiles")
+        else:
+            out.update(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=fh, issued_tflops=ti, issued_frac=ft,
+                       peak_source=peak_src + " HBM copy bandwidth (MEASURED_PEAKS.json)")
+    elif base in FP64_KERNELS:
+        out.update(bound="alu", achieved=tf, peak=fp64_peak, unit="TFLOP/s (FP64)", frac=tf / fp64_peak,
+                   hbm_gbs=gbs, peak_source="nominal GB300 FP64 1.25 TFLOP/s (not in MEASURED_PEAKS.json)")
+    elif base in DD_KERNELS:
+        out.update(bound="alu", achieved=tf, peak=fp32_peak, unit="TFLOP/s (double-float on the FP32 pipes)",
+                   frac=tf / fp32_peak,
+                   peak_source=f"FP32-pipe peak {sms} SMs x {FP32_OPS_PER_CLK_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                               "(median SM clock under load); the kernel runs on ONE CTA, so its own ceiling is "
+                               f"1/{sms} of this; achieved = the operation's FLOPs counted as FP64-class FLOPs")
+    else:
+        out.update(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=gbs / hbm,
+                   peak_source=peak_src + " HBM copy bandwidth (MEASURED_PEAKS.json)")
+    return out
 
 
 def run_ours(args, world, rank, local):
@@ -256,10 +334,9 @@ def run_ours(args, world, rank, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    x = workload()
+    xd, x = workload_device(args.workload, dev)
     N = x.size
     nbytes = x.nbytes
-    xd = torch.from_numpy(x).to(dev)
     prec = PRECISIONS[args.precision]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -277,7 +354,7 @@ def run_ours(args, world, rank, local):
             raise P.AtcError(rc, P.lib().atc_last_error().decode())
         return c, s
 
-    def timed(precision, k, w, clocks=None):
+    def timed(precision, k, w, clocks=None, ktimer=False):
         for _ in range(w):
             step(precision)
         torch.cuda.synchronize()
@@ -286,6 +363,8 @@ def run_ours(args, world, rank, local):
         if clocks is not None:
             clocks.start()  # sampled over the timed steps only
         l0 = P.lib().atc_kernel_launches()
+        if ktimer:
+            P.kernel_timing(True)
         for _ in range(k):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -298,11 +377,19 @@ def run_ours(args, world, rank, local):
             ms.append(e0.elapsed_time(e1))
             stats.append(c.stats())
         launches = P.lib().atc_kernel_launches() - l0
+        kt = None
+        if ktimer:
+            kt = P.kernel_times()
+            P.kernel_timing(False)
         clk = clocks.stop() if clocks is not None else None
         barrier(world)
-        return ms, stats, c, s, launches, clk
+        return ms, stats, c, s, launches, clk, kt
 
-    ms, stats, c, s, launches, clk = timed(prec, args.steps, args.warmup, clock_sampler(local))
+    ms, stats, c, s, launches, clk, _ = timed(prec, args.steps, args.warmup, clock_sampler(local))
+    # per-kernel device times: the same steps again with the library's kernel
+    # timer on (CUDA events around each launch on its stream; kept out of the
+    # headline timing because the event records add a little time per launch)
+    _, _, _, _, _, _, ktimes = timed(prec, args.steps, 0, ktimer=True)
     per_ms = max_over_ranks(sum(ms) / len(ms), world)
     value = world * nbytes / (per_ms * 1e-3) / 1e9
 
@@ -334,12 +421,21 @@ def run_ours(args, world, rank, local):
     # plain FP64 path, same box
     fp64 = None
     if args.fp64_steps > 0 and prec != 0:
-        ms64, st64, c64, _, _, _ = timed(0, args.fp64_steps, 1)
+        ms64, st64, c64, _, _, _, _ = timed(0, args.fp64_steps, 1)
         per64 = sum(ms64) / len(ms64)
         sth64 = sum(st["ms_norm"] + st["ms_gram"] + st["ms_eig"] + st["ms_ttm"] for st in st64) / len(st64)
+        ph64 = {k: sum(st[k] for st in st64) / len(st64) for k in phases}
+        # per-phase speed-ups: the Gram and projection phases compare the same operation in two
+        # precisions; the eigen phase also compares two algorithms (the plain path runs the full
+        # tridiagonal FP64 eigensolver, the split path subspace iteration + Rayleigh-Ritz)
         fp64 = {"value": nbytes / (per64 * 1e-3) / 1e9, "ms_per_step": per64,
-                "sthosvd_gbs": nbytes / (sth64 * 1e-3) / 1e9, "ranks": c64.ranks(),
-                "speedup_step": per64 / per_ms, "speedup_sthosvd": sth64 / sthosvd_ms}
+                "sthosvd_gbs": nbytes / (sth64 * 1e-3) / 1e9, "ranks": c64.ranks(), "phases_ms": ph64,
+                "speedup_step": per64 / per_ms, "speedup_sthosvd": sth64 / sthosvd_ms,
+                "speedup_per_phase": {k: (ph64[k] / phases[k] if phases[k] > 0 else None)
+                                      for k in ("ms_norm", "ms_gram", "ms_eig", "ms_ttm", "ms_quant", "ms_encode")},
+                "note": "ms_eig compares two algorithms as well as two precisions (full FP64 tridiagonal "
+                        "eigensolver vs double-float subspace iteration + Rayleigh-Ritz); ms_gram and ms_ttm "
+                        "compare the same operations"}
 
     # e2e through the public API with host buffers
     xh_pin = torch.from_numpy(x).pin_memory()
@@ -360,83 +456,26 @@ def run_ours(args, world, rank, local):
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_per = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world)
 
-    # rooflines.  Per step the phases are timed by CUDA events on the library's
-    # stream; the unit of each roofline is the phase (its kernels are listed).
+    # rooflines.  The library's kernel timer brackets every launch of its main
+    # kernels with CUDA events on the launching stream during the timed steps
+    # and records each launch's algorithmic work (include/atc.h); the dominant
+    # kernel is the one with the largest device time.
     hbm, bf16, bf16s, peak_src = load_peaks()
-    gram_tflops_issued = 0.0  # tensor-core FLOPs issued: 9 slice products per 128 x 64 tile entry
-    ttm_tflops_issued = 0.0   # 9 slice products per 128 x N(chunk, padded to 16) tile entry
-    ttm_bytes = 0.0
-    cur3 = list(dims)
-    for m in order:
-        S = float(np.prod(cur3))
-        n = cur3[m]
-        K = S / n
-        nt128, nc64 = -(-n // 128), -(-n // 64)
-        ntile = sum(nc64 - 2 * t for t in range(nt128))
-        gram_tflops_issued += 9 * 2.0 * 128 * 64 * K * ntile
-        r = ranks[m]
-        nch = -(-r // 32)
-        csz = -(-r // nch)
-        apad = -(-csz // 16) * 16
-        ttm_tflops_issued += 9 * 2.0 * (-(-K // 128) * 128) * apad * nch * n
-        ttm_bytes += S * 4.0 + K * r * 4.0
-        cur3[m] = r
-
-    def roof_of(name, kernels, ms, alg_bytes, issued_flops):
-        gbs = alg_bytes / (ms * 1e-3) / 1e9
-        tfs = issued_flops / (ms * 1e-3) / 1e12 if issued_flops else 0.0
-        fr_h, fr_t = gbs / hbm, (tfs / bf16s if issued_flops else 0.0)
-        bound = "tensor" if fr_t > fr_h else "hbm"
-        d = {"kernel": name, "kernels": kernels, "bound": bound,
-             "achieved": tfs if bound == "tensor" else gbs, "peak": bf16s if bound == "tensor" else hbm,
-             "unit": "TFLOP/s" if bound == "tensor" else "GB/s", "frac": fr_t if bound == "tensor" else fr_h,
-             "traffic": None, "hbm_gbs": gbs, "hbm_frac": fr_h, "tensor_tflops_issued": tfs, "tensor_frac": fr_t,
-             "ms_per_step": ms, "peak_source": peak_src + " (sustained bf16 for the tensor view)"}
-        return d
-
-    roof_gram = roof_of("gram phase", "absmax_kernel, slice_planes_kernel, gram_tma_kernel, gram_tc_assemble", phases["ms_gram"],
-                        gram_bytes, gram_tflops_issued)
-    roof_ttm = roof_of("projection + certification phase", "ttm_prep_b, ttm_tc_kernel (projection and residual), "
-                       "row_energy, compact, eigenvectors", phases["ms_ttm"], ttm_bytes, ttm_tflops_issued)
-    ph_share = {"gram": phases["ms_gram"], "eig": phases["ms_eig"], "ttm": phases["ms_ttm"],
-                "quant+encode": phases["ms_quant"] + phases["ms_encode"]}
-    dom = max(ph_share, key=ph_share.get)
-    if dom == "gram":
-        roof = dict(roof_gram)
-    elif dom == "ttm":
-        roof = dict(roof_ttm)
-    elif dom == "eig":
-        sub = stats[-1].get("subspace_modes", 0) == len(order)
-        if sub:
-            # subspace iteration per mode (K = 32 columns, 1 iteration): two G V products 2 n^2 K each,
-            # Householder QR + explicit Q 4 n K^2, V^T (G V) 2 n K^2, the K x K eigensolve 4/3 K^3,
-            # Ritz vectors 2 n K (r + 4)
-            K = 32
-            fl = sum(2 * 2.0 * dims[m] ** 2 * K + 6.0 * dims[m] * K * K + 4.0 / 3.0 * K ** 3
-                     + 2.0 * dims[m] * K * (ranks[m] + 4) for m in order)
-            kern = ("sub_gemm_kernel, sub_qr_kernel (blocked double-float Householder QR), sub_qform_kernel, "
-                    "sub_proj_kernel, rr_kernel (one-CTA double-float Rayleigh-Ritz on the 32 x 32 matrix: "
-                    "tridiagonalisation, Sturm multisection, provisional rank, inverse iteration), sub_rotate_kernel")
-            unit = "TFLOP/s (FP64-class: subspace iteration + Rayleigh-Ritz, formula in bench.py)"
-            why = "a chain of dependent QR and tridiagonalisation steps on small matrices (latency-bound)"
-        else:
-            # tridiagonalisation 4/3 n^3 + back-transformation 2 n^2 r per mode
-            fl = sum(4.0 / 3.0 * dims[m] ** 3 + 2.0 * dims[m] ** 2 * ranks[m] for m in order)
-            kern = ("tridiag_cluster_dd_kernel, msect_dd_kernel, invit_dd_kernel, cholqr_group_kernel, "
-                    "backtransform_dd_kernel (double-float on the FP32 pipes)") if prec != 0 else \
-                   ("tridiag_cluster_kernel, msect_kernel, invit_par_kernel, cholqr_group_kernel, backtransform_kernel")
-            unit = "TFLOP/s (FP64-class: 4/3 n^3 + 2 n^2 r per mode)"
-            why = "a chain of n - 2 dependent Householder steps (latency-bound)"
-        ach = fl / (phases["ms_eig"] * 1e-3) / 1e12
-        fp64_peak = 1.1  # TFLOP/s: torch float64 matmul on this machine's GB300 (no FP64 entry in the peaks file)
-        roof = {"kernel": "eigensolver phase", "kernels": kern, "bound": "alu", "achieved": ach, "peak": fp64_peak,
-                "unit": unit, "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "measured FP64 DGEMM rate (torch float64 matmul), not in the peaks file; the phase "
-                               "is " + why}
-    else:
-        roof = {"kernel": "quantizer/encoder", "bound": "alu", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None}
-    roof["share_of_step"] = ph_share[dom] / per_ms
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    fp32_peak = sms * FP32_OPS_PER_CLK_SM * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s, FMA = 2
+    fp64_peak = FP64_NOMINAL_TFLOPS
+    total_kt = sum(d["ms"] for d in ktimes.values()) or 1.0
+    kern_table = {k: {"launches_per_step": d["launches"] / args.steps, "ms_per_step": d["ms"] / args.steps,
+                      "avg_us": 1e3 * d["ms"] / d["launches"], "share_of_timed_kernels": d["ms"] / total_kt}
+                  for k, d in sorted(ktimes.items(), key=lambda kv: -kv[1]["ms"])}
+    dom = max(ktimes, key=lambda k: ktimes[k]["ms"]) if ktimes else None
+    roof = roofline_of(dom, ktimes.get(dom), hbm, bf16s, fp32_peak, fp64_peak, peak_src, sm_mhz, sms, args)
+    roof["share_of_step"] = (ktimes[dom]["ms"] / args.steps) / per_ms if dom else None
+    roof_gram = roofline_of("gram_tma_kernel", ktimes.get("gram_tma_kernel"), hbm, bf16s, fp32_peak, fp64_peak,
+                            peak_src, sm_mhz, sms, args)
+    roof_ttm = roofline_of("ttm_tc_kernel", ktimes.get("ttm_tc_kernel"), hbm, bf16s, fp32_peak, fp64_peak,
+                           peak_src, sm_mhz, sms, args)
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "weak",
@@ -445,26 +484,28 @@ def run_ours(args, world, rank, local):
                             "accumulation that never rounds, FP64 eigensolve and FP64 rank sums"
             if args.precision != "fp64" else "FP64 throughout",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rel_eps": args.eps, "precision": args.precision,
-                       "step": "atc_compress + atc_decompress", "l2": "flushed (256 MB write) before each timed step",
+            "config": {"workload": WORKLOADS[args.workload], "rel_eps": args.eps, "precision": args.precision,
+                       "step": "atc_compress + atc_decompress",
+                       "l2": ("flushed (256 MB write) before each timed step" if args.workload == "bumps256" else
+                              "input 4.3 GB > L2 (and flushed before each timed step)"),
                        "block_size": stats[-1].get("block_size"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "ranks": ranks, "achieved_rel_err": re, "stream_bytes": len(s),
             "subspace_modes": stats[-1].get("subspace_modes", 0),
             "sthosvd_gbs": nbytes / (sthosvd_ms * 1e-3) / 1e9, "sthosvd_tflops": tflops,
             "phases_ms": phases, "fp64_plain": fp64,
-            "roofline": roof, "roofline_gram": roof_gram, "roofline_ttm": roof_ttm,
+            "roofline": roof, "roofline_gram": roof_gram, "roofline_ttm": roof_ttm, "kernels": kern_table,
+            "escalated_modes": stats[-1].get("escalated_modes", 0),
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": world * nbytes / (e2e_per * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes + len(s), "ms_per_step": e2e_per}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(x, args.eps)
+        line["cpu_baseline"] = cpu_baseline(workload(args.workload), args.eps, args.workload)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 BATCH_WORKLOAD = "batched_lowrank_512_f32 (dims U{16..96}, ranks U{2..12}, rel_eps in {1e-2,1e-3,1e-4})"
-FP32_OPS_PER_CLK_SM = 128  # FP32 lanes per SM (4 SMSPs x 32)
 
 
 def batch_items():

@@ -72,6 +72,16 @@ typedef enum {
   ATC_PREC_SPLIT_BF16 = 1, /* split, bf16 slices */
   ATC_PREC_SPLIT_FP16 = 2  /* split, fp16 slices */
 } atc_precision;
+/* Flag OR-ed into a split precision (atc_gram, atc_options.precision): the
+ * Gram matrices use FOUR 8-bit slices (32-bit fixed point below max |x|, the
+ * thirteen slice products of order <= 4, still exact in FP32) instead of three.
+ * Without the flag a split compression starts every mode with three slices and
+ * recomputes a mode's Gram matrix with four when the estimated shift of its kept
+ * subspace from the 24-bit rounding, D = q/sqrt(12) sqrt(sum_{j<=r<k}
+ * ((l_j + l_k)/(l_j - l_k))^2) for the eigenvalues l and grid q, exceeds
+ * 1e-6 ||X|| (cuts inside dense spectra, e.g. noise floors); the count is
+ * atc_stats.escalated_modes. */
+#define ATC_PREC_WIDE 16
 
 typedef enum {
   ATC_RANK_STATIC = 0,   /* budget_k = rtmss * TargetSSE_total / d for every mode */
@@ -102,7 +112,7 @@ typedef struct {
   int k;                  /* quantization scale exponent: 2^63 <= 2^k max|b| < 2^64 */
   int p_star;             /* breakpoint plane (64 = nothing encoded) */
   int64_t i_star;         /* breakpoint coefficient: 0..i_star carry planes >= p_star, the rest >= p_star+1 */
-  int escalated_modes;    /* modes whose Gram was recomputed in FP64 by the precision check */
+  int escalated_modes;    /* split paths: modes whose Gram was recomputed with four slices (ATC_PREC_WIDE) */
   double ms_norm, ms_gram, ms_eig, ms_ttm, ms_quant, ms_encode, ms_total; /* device time per phase (CUDA events) */
   int subspace_modes;     /* split paths: modes whose eigenvectors came from subspace iteration + Rayleigh-Ritz */
   int block_size;         /* encoder block size used */
@@ -326,6 +336,20 @@ int atc_dequantize_core(const uint8_t* bytes, size_t nbytes, double* core_dev, i
 void atc_free_buffer(void* p);
 /* Number of CUDA kernels this library has launched in this process (host counter). */
 long long atc_kernel_launches(void);
+/* Kernel timer (measurement aid, not part of the paper's method).  enable != 0
+ * starts a new timing window (earlier records are dropped): from then on the
+ * library brackets every launch of its main kernels with two CUDA events on
+ * the launching stream (at most 65536 launches a window).  enable == 0 stops
+ * recording and drops the records.  Adds two event records per timed launch. */
+int atc_kernel_timing(int enable);
+/* Per-kernel totals of the current window, one line per kernel name:
+ * "<name>|<launches>|<total device ms>|<bytes>|<flops>|<issued flops>\n" into
+ * buf (host, cap bytes, NUL terminated), where bytes / flops are the
+ * algorithmic work of the timed launches (inputs read once, outputs written
+ * once; FLOPs of the operation computed) and issued flops the tensor-core work
+ * they issue (slice products, tile padding; 0 for other kernels); waits for the
+ * recorded events.  ATC_EINVAL if buf is too small. */
+int atc_kernel_times(char* buf, size_t cap);
 /* Free the cached device scratch of the current device (and forget the looked-up
    address of the no-allocation Gram array there). */
 int atc_release_workspace(void);

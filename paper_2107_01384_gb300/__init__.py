@@ -16,16 +16,17 @@ import os
 import torch
 
 __all__ = [
-    "ATC_F32", "ATC_F64", "PREC_FP64", "PREC_SPLIT_BF16", "PREC_SPLIT_FP16",
+    "ATC_F32", "ATC_F64", "PREC_FP64", "PREC_SPLIT_BF16", "PREC_SPLIT_FP16", "PREC_WIDE",
     "RANK_STATIC", "RANK_ADAPTIVE", "AtcError", "lib", "lib_path",
     "atc_norm2", "atc_gram", "atc_gram_fp64_noalloc", "atc_eig_sym", "atc_rank_select", "atc_ttm",
     "atc_quantize_core", "atc_dequantize_core", "atc_compress", "atc_decompress",
     "atc_peek_dims", "Compressed", "EXPORTS", "atc_tucker_expand", "atc_tucker_expand_adjoint",
-    "TuckerExpand", "tucker_expand", "Batch", "atc_batch_tune",
+    "TuckerExpand", "tucker_expand", "Batch", "atc_batch_tune", "kernel_timing", "kernel_times",
 ]
 
 ATC_F32, ATC_F64 = 1, 2
 PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_FP16 = 0, 1, 2
+PREC_WIDE = 16  # flag: split Grams with four slices (32-bit fixed point)
 RANK_STATIC, RANK_ADAPTIVE = 0, 1
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -38,7 +39,7 @@ EXPORTS = [
     "atc_tucker_expand", "atc_tucker_expand_adjoint", "atc_norm2",
     "atc_gram", "atc_eig_sym", "atc_rank_select", "atc_ttm", "atc_quantize_core",
     "atc_dequantize_core", "atc_free_buffer", "atc_release_workspace", "atc_last_error",
-    "atc_kernel_launches", "atc_gram_fp64_noalloc",
+    "atc_kernel_launches", "atc_kernel_timing", "atc_kernel_times", "atc_gram_fp64_noalloc",
     "atc_batch_create", "atc_batch_run", "atc_batch_get_ranks", "atc_batch_get_core", "atc_batch_get_factor",
     "atc_batch_get_stats", "atc_batch_get_profile", "atc_batch_last_ms", "atc_batch_tune", "atc_batch_free",
 ]
@@ -106,6 +107,8 @@ def lib():
         L.atc_release_workspace.argtypes = []
         L.atc_kernel_launches.argtypes = []
         L.atc_kernel_launches.restype = C.c_longlong
+        L.atc_kernel_timing.argtypes = [i32]
+        L.atc_kernel_times.argtypes = [C.c_char_p, C.c_size_t]
         L.atc_batch_create.argtypes = [i32, i32, C.POINTER(i64), i32, C.POINTER(dbl), C.POINTER(Options),
                                        C.POINTER(vp)]
         L.atc_batch_run.argtypes = [vp, C.POINTER(vp), vp]
@@ -459,3 +462,20 @@ def atc_batch_tune(stream=None):
     tab = (C.c_int * 113)()
     _check(lib().atc_batch_tune(_stream(stream), tab))
     return list(tab)
+
+
+def kernel_timing(enable: bool) -> None:
+    """Start (True) or stop (False) the library's kernel timer (include/atc.h)."""
+    _check(lib().atc_kernel_timing(1 if enable else 0))
+
+
+def kernel_times() -> dict:
+    """{kernel name: dict(launches, ms, bytes, flops, issued)} of the current
+    timing window (totals over its launches; see include/atc.h)."""
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().atc_kernel_times(buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms, by, fl, iss = line.split("|")
+        out[name] = dict(launches=int(cnt), ms=float(ms), bytes=float(by), flops=float(fl), issued=float(iss))
+    return out

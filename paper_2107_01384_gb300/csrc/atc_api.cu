@@ -90,6 +90,51 @@ std::vector<DevArena> g_arenas;
 
 long long g_scratch_serial = 0;  // bumped whenever any scratch slot is allocated or freed
 
+// ------------------------------------------------------------- kernel timer
+namespace {
+struct KRecord {
+  const char* name;
+  cudaEvent_t a, b;
+  double bytes, flops, issued;
+};
+std::mutex g_kt_mu;
+int g_kt_on = 0;
+std::vector<KRecord> g_kt_rec;   // records of the current timing window
+std::vector<cudaEvent_t> g_kt_pool;
+constexpr size_t kKtMax = 65536;  // records per window (later launches are not timed)
+cudaEvent_t kt_event() {
+  cudaEvent_t e = nullptr;
+  if (!g_kt_pool.empty()) {
+    e = g_kt_pool.back();
+    g_kt_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    e = nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+int ktimer_begin(cudaStream_t s, const char* name, double bytes, double flops, double issued) {
+  if (!__atomic_load_n(&g_kt_on, __ATOMIC_RELAXED)) return -1;
+  std::lock_guard<std::mutex> lk(g_kt_mu);
+  if (g_kt_rec.size() >= kKtMax) return -1;
+  KRecord r{name, kt_event(), kt_event(), bytes, flops, issued};
+  if (!r.a || !r.b || cudaEventRecord(r.a, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (r.a) g_kt_pool.push_back(r.a);
+    if (r.b) g_kt_pool.push_back(r.b);
+    return -1;
+  }
+  g_kt_rec.push_back(r);
+  return (int)g_kt_rec.size() - 1;
+}
+void ktimer_end(cudaStream_t s, int token) {
+  if (token < 0) return;
+  std::lock_guard<std::mutex> lk(g_kt_mu);
+  if (token < (int)g_kt_rec.size() && cudaEventRecord(g_kt_rec[token].b, s) != cudaSuccess) cudaGetLastError();
+}
+
 int Scratch::get(int slot, size_t bytes, void** out) {
   if (slot < 0 || slot >= SLOT_COUNT) return fail(ATC_EINVAL, "bad scratch slot");
   int dev = 0;
@@ -234,10 +279,45 @@ bool subspace_enabled() {
   return !(e && e[0] == '0');
 }
 
+// precision: an atc_precision, on the split paths optionally with ATC_PREC_WIDE
+// (four slices: 32-bit fixed point)
 int gram_dispatch(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g, cudaStream_t s,
                   const SliceScale* xs = nullptr) {
-  if (precision == ATC_PREC_FP64) return launch_gram_fp64(x, dtype, L, n, R, g, s);
-  return launch_gram_split(x, dtype, L, n, R, precision, g, s, xs);
+  const int base = precision & ~ATC_PREC_WIDE;
+  if (base == ATC_PREC_FP64) return launch_gram_fp64(x, dtype, L, n, R, g, s);
+  return launch_gram_split(x, dtype, L, n, R, base, g, s, xs, (precision & ATC_PREC_WIDE) ? 4 : 3);
+}
+bool valid_precision(int p, bool allow_wide) {
+  const int base = p & ~ATC_PREC_WIDE;
+  if (base < ATC_PREC_FP64 || base > ATC_PREC_SPLIT_FP16) return false;
+  if (p & ATC_PREC_WIDE) return allow_wide && base != ATC_PREC_FP64;
+  return true;
+}
+
+// Subspace perturbation check of the split paths.  The sliced Gram matrix is
+// that of X rounded to a fixed-point grid q (24 bits below max |x|): with
+// independent rounding errors of variance q^2 / 12 the coupling it adds between
+// eigen-directions j <= r < k is about sqrt(lambda_j + lambda_k) q / sqrt(12),
+// which turns the kept subspace by theta_jk ~ that / (lambda_j - lambda_k)
+// (first-order perturbation theory) and moves the projection of X by
+//   D^2 = sum_{j <= r < k} theta_jk^2 (lambda_j + lambda_k)
+//       = q^2 / 12 sum_{j <= r < k} ((lambda_j + lambda_k) / (lambda_j - lambda_k))^2.
+// Eigenvalues beyond the known ones add ~1 per pair.  When D exceeds
+// kWideTol ||X||, the Gram matrix is recomputed with four slices (q / 256).
+constexpr double kWideTol = 1e-6;
+double subspace_shift_estimate(const std::vector<double>& lam, int known, int r, int64_t n, double q) {
+  double sum = 0.0;
+  for (int j = 0; j < r && j < known; ++j) {
+    const double lj = std::max(lam[j], 0.0);
+    for (int k = r; k < known; ++k) {
+      const double lk = std::max(lam[k], 0.0);
+      const double gap = lj - lk;
+      const double t = (gap > 1e-300 * (lj + 1e-300)) ? (lj + lk) / gap : 1e150;
+      sum += t * t;
+    }
+  }
+  sum += (double)std::min<int64_t>(r, known) * (double)(n - std::max<int64_t>(r, known));
+  return std::sqrt(sum * q * q / 12.0);
 }
 
 int ttm_dispatch(const void* x, int xdt, int64_t L, int64_t n, int64_t R, const double* u, int64_t r, int expand,
@@ -392,6 +472,55 @@ int atc_release_workspace(void) {
 
 long long atc_kernel_launches(void) { return __atomic_load_n(&g_kernel_launches, __ATOMIC_RELAXED); }
 
+int atc_kernel_timing(int enable) {
+  std::lock_guard<std::mutex> lk(g_kt_mu);
+  for (auto& r : g_kt_rec) {
+    g_kt_pool.push_back(r.a);
+    g_kt_pool.push_back(r.b);
+  }
+  g_kt_rec.clear();
+  __atomic_store_n(&g_kt_on, enable ? 1 : 0, __ATOMIC_RELAXED);
+  return ATC_OK;
+}
+
+int atc_kernel_times(char* buf, size_t cap) {
+  if (!buf || cap == 0) return fail(ATC_EINVAL, "atc_kernel_times: bad arguments");
+  std::lock_guard<std::mutex> lk(g_kt_mu);
+  std::vector<std::string> names;
+  std::vector<double> tot, byt, flo, iss;
+  std::vector<long long> cnt;
+  for (auto& r : g_kt_rec) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return fail(ATC_ECUDA, "kernel timer: event synchronisation failed");
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return fail(ATC_ECUDA, "kernel timer: elapsed time failed");
+    size_t k = 0;
+    while (k < names.size() && names[k] != r.name) ++k;
+    if (k == names.size()) {
+      names.push_back(r.name);
+      tot.push_back(0.0);
+      byt.push_back(0.0);
+      flo.push_back(0.0);
+      iss.push_back(0.0);
+      cnt.push_back(0);
+    }
+    tot[k] += ms;
+    byt[k] += r.bytes;
+    flo[k] += r.flops;
+    iss[k] += r.issued;
+    cnt[k] += 1;
+  }
+  std::string out;
+  char line[320];
+  for (size_t k = 0; k < names.size(); ++k) {
+    snprintf(line, sizeof(line), "%s|%lld|%.6f|%.6e|%.6e|%.6e\n", names[k].c_str(), cnt[k], tot[k], byt[k], flo[k], iss[k]);
+    out += line;
+  }
+  if (out.size() + 1 > cap) return fail(ATC_EINVAL, "atc_kernel_times: buffer of %zu bytes too small (%zu needed)", cap,
+                                        out.size() + 1);
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return ATC_OK;
+}
+
 int atc_norm2(const void* x_dev, int64_t n, int dtype, double* out_dev, void* stream) {
   if (!x_dev || !out_dev || n < 0 || !dtype_size(dtype)) return fail(ATC_EINVAL, "atc_norm2: bad arguments");
   return launch_norm2(x_dev, dtype, n, out_dev, (cudaStream_t)stream);
@@ -400,7 +529,7 @@ int atc_norm2(const void* x_dev, int64_t n, int dtype, double* out_dev, void* st
 int atc_gram(const void* x_dev, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g_dev,
              void* stream) {
   if (!x_dev || !g_dev || L < 1 || n < 1 || R < 1 || !dtype_size(dtype)) return fail(ATC_EINVAL, "atc_gram: bad arguments");
-  if (precision < 0 || precision > 2) return fail(ATC_EINVAL, "atc_gram: bad precision");
+  if (!valid_precision(precision, true)) return fail(ATC_EINVAL, "atc_gram: bad precision");
   return gram_dispatch(x_dev, dtype, L, n, R, precision, g_dev, (cudaStream_t)stream);
 }
 
@@ -471,7 +600,10 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   atc_default_options(&opt);
   if (opt_in) opt = *opt_in;
   if (!(opt.rtmss >= 0.0 && opt.rtmss <= 1.0)) return fail(ATC_EINVAL, "rtmss must lie in [0, 1]");
-  if (opt.precision < 0 || opt.precision > 2) return fail(ATC_EINVAL, "bad precision");
+  if (!valid_precision(opt.precision, true)) return fail(ATC_EINVAL, "bad precision");
+  // every Gram with four slices (ATC_PREC_WIDE), else three with the perturbation check
+  const bool wide_all = (opt.precision & ATC_PREC_WIDE) != 0;
+  opt.precision &= ~ATC_PREC_WIDE;
   if (opt.rank_rule != ATC_RANK_STATIC && opt.rank_rule != ATC_RANK_ADAPTIVE) return fail(ATC_EINVAL, "bad rank rule");
   if (opt.block_size != 0 && (opt.block_size < 32 || opt.block_size > 65535 || (opt.block_size % 32)))
     return fail(ATC_EINVAL, "bad block_size");
@@ -576,8 +708,9 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
       rc = slice_scale(curp, curdt, L * n * R, s, &xs);
       if (rc) return bail(rc);
     }
+    bool wide = wide_all;
     {
-      rc = gram_dispatch(curp, curdt, L, n, R, opt.precision, G, s, xs);
+      rc = gram_dispatch(curp, curdt, L, n, R, opt.precision | (wide ? ATC_PREC_WIDE : 0), G, s, xs);
       if (rc) return bail(rc);
       clk.mark(PH_GRAM);
     }
@@ -693,32 +826,60 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         // tridiagonalisation, then only the largest K eigenvalues (more if
         // the rank is not decided among them); tail(r) = trace(G) - sum_{j<r}
         // lambda_j in FP64.
-        rc = launch_eig_tridiag(G, (int)n, ddev + 2, s, opt.precision != ATC_PREC_FP64);
-        if (rc) return bail(rc);
-        int K = (int)std::min<int64_t>(n, 48);
-        double tr = 0.0;
+        int K = 0;
         std::vector<double> lh;
-        for (;;) {
-          rc = launch_eig_more((int)n, K, lam, s);
-          if (rc) return bail(rc);
-          lh.resize(K);
-          if (cudaMemcpyAsync(lh.data(), lam, sizeof(double) * K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-              cudaMemcpyAsync(&tr, ddev + 2, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-              (tc_err && cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess))
-            return bail(fail(ATC_ECUDA, "eigenvalue readback failed"));
-          rc = eig_check(s);
-          if (rc) return bail(rc);
-          r = -1;
-          double acc = 0.0;
-          for (int rr = 1; rr <= K; ++rr) {
-            acc += lh[rr - 1];
-            double t = tr - acc;
-            if (t < 0.0) t = 0.0;
-            if (t <= budget) { r = rr; disc = t; break; }
+        auto eig_rank = [&]() -> int {
+          int rc3 = launch_eig_tridiag(G, (int)n, ddev + 2, s, opt.precision != ATC_PREC_FP64);
+          if (rc3) return rc3;
+          K = (int)std::min<int64_t>(n, 48);
+          double tr = 0.0;
+          for (;;) {
+            rc3 = launch_eig_more((int)n, K, lam, s);
+            if (rc3) return rc3;
+            lh.resize(K);
+            if (cudaMemcpyAsync(lh.data(), lam, sizeof(double) * K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(&tr, ddev + 2, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                (tc_err && cudaMemcpyAsync(&he, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess))
+              return fail(ATC_ECUDA, "eigenvalue readback failed");
+            rc3 = eig_check(s);
+            if (rc3) return rc3;
+            r = -1;
+            double acc = 0.0;
+            for (int rr = 1; rr <= K; ++rr) {
+              acc += lh[rr - 1];
+              double t = tr - acc;
+              if (t < 0.0) t = 0.0;
+              if (t <= budget) { r = rr; disc = t; break; }
+            }
+            if (r >= 1) break;
+            if (K == n) { r = (int)n; disc = 0.0; break; }
+            K = (int)n;
           }
-          if (r >= 1) break;
-          if (K == n) { r = (int)n; disc = 0.0; break; }
-          K = (int)n;
+          return ATC_OK;
+        };
+        rc = eig_rank();
+        if (rc) return bail(rc);
+        if (opt.precision != ATC_PREC_FP64 && !wide && r >= 1 && r < n && !he) {
+          // the subspace of a cut inside a dense part of the spectrum is sensitive to the
+          // 24-bit slicing of the Gram input: estimate the shift of the projection and,
+          // if it is not negligible, recompute this mode's Gram matrix with four slices
+          const SliceScale* sc = xs;
+          int shift = 0;
+          if (cudaMemcpyAsync(&shift, &sc->shift, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess)
+            return bail(fail(ATC_ECUDA, "slice scale readback failed"));
+          const double q = std::ldexp(1.0, -16 - shift);  // grid of three 8-bit slices
+          const double D = subspace_shift_estimate(lh, K, r, n, q);
+          if (D > kWideTol * std::sqrt(st.norm2)) {
+            wide = true;
+            ++st.escalated_modes;
+            clk.mark(PH_EIG);
+            rc = gram_dispatch(curp, curdt, L, n, R, opt.precision | ATC_PREC_WIDE, G, s, xs);
+            if (rc) return bail(rc);
+            clk.mark(PH_GRAM);
+            rc = eig_rank();
+            if (rc) return bail(rc);
+          }
         }
         if (he) return bail(fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)"));
         if (r < 1 || r > n) return bail(fail(ATC_ENUMERIC, "rank selection failed (r = %d)", r));
@@ -799,10 +960,24 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   st.p_star = qr.p_star;
   st.i_star = qr.i_star;
   st.sse_quant_pred = qr.sse_pred;
-  // stream: header, factors (raw FP64), core section
+  // core slices left without a significant coefficient: their factor columns
+  // are not stored (Section 3.3, the paragraph after Table 2)
+  int64_t rsum = 0;
+  for (int i = 0; i < d; ++i) rsum += c->ranks[i];
+  std::vector<uint8_t> kept((size_t)rsum, 0);
+  rc = core_kept_slices(ncore, c->ranks, perm.data(), d, qr.p_star, qr.i_star, kept.data(), s);
+  if (rc) return bail(rc);
+  // stream (version 2): header, kept-column maps, kept factor columns (raw FP64), core section
+  std::vector<std::vector<double>> hfac(d);
+  for (int i = 0; i < d; ++i) {
+    hfac[i].resize((size_t)dims[i] * c->ranks[i]);
+    if (cudaMemcpyAsync(hfac[i].data(), c->factors[i], hfac[i].size() * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return bail(fail(ATC_ECUDA, "factor readback failed"));
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ATC_ECUDA, "stream synchronisation failed"));
   std::string& S = c->stream;
   S.append("ATC1", 4);
-  put32(S, 1);
+  put32(S, 2);
   put32(S, (uint32_t)d);
   put32(S, (uint32_t)dtype);
   for (int i = 0; i < d; ++i) put64(S, (uint64_t)dims[i]);
@@ -811,12 +986,25 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   while (S.size() % 8) S.push_back('\0');
   putf64(S, st.norm2);
   putf64(S, st.sse_trunc);
-  for (int i = 0; i < d; ++i) {
-    const size_t cnt = (size_t)dims[i] * c->ranks[i];
-    const size_t at = S.size();
-    S.resize(at + cnt * 8);
-    if (cudaMemcpyAsync(&S[at], c->factors[i], cnt * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return bail(fail(ATC_ECUDA, "factor readback failed"));
+  {
+    int64_t o = 0;
+    for (int i = 0; i < d; ++i) {
+      for (int64_t b = 0; b < (c->ranks[i] + 7) / 8; ++b) {
+        uint8_t byte = 0;
+        for (int t = 0; t < 8 && 8 * b + t < c->ranks[i]; ++t) byte |= (uint8_t)(kept[(size_t)(o + 8 * b + t)] << t);
+        S.push_back((char)byte);
+      }
+      o += c->ranks[i];
+    }
+    while (S.size() % 8) S.push_back('\0');
+    o = 0;
+    for (int i = 0; i < d; ++i) {
+      const int64_t r = c->ranks[i];
+      for (int64_t row = 0; row < dims[i]; ++row)
+        for (int64_t col = 0; col < r; ++col)
+          if (kept[(size_t)(o + col)]) putf64(S, hfac[i][(size_t)(row * r + col)]);
+      o += r;
+    }
   }
   put64(S, (uint64_t)section.size());
   S.append(section);
@@ -874,7 +1062,7 @@ void atc_free(atc_compressed* c) { free_compressed(c); }
 
 int atc_peek_dims(const uint8_t* stream, size_t nbytes, int* ndim, int64_t* dims, int* dtype) {
   if (!stream || !ndim || !dims || !dtype) return fail(ATC_EINVAL, "atc_peek_dims: bad arguments");
-  if (nbytes < 16 || memcmp(stream, "ATC1", 4) != 0 || get32(stream + 4) != 1) return fail(ATC_ECORRUPT, "bad stream magic/version");
+  if (nbytes < 16 || memcmp(stream, "ATC1", 4) != 0 || get32(stream + 4) != 2) return fail(ATC_ECORRUPT, "bad stream magic/version");
   const int d = (int)get32(stream + 8);
   const int dt = (int)get32(stream + 12);
   if (d < 1 || d > 8 || !dtype_size(dt)) return fail(ATC_ECORRUPT, "bad stream header");
@@ -927,18 +1115,49 @@ int atc_decompress_ex(const uint8_t* stream, size_t nbytes, void* out_dev, int o
     N *= dims[i];
     maxn = std::max(maxn, dims[i]);
   }
-  size_t fac_total = 0;
-  for (int i = 0; i < d; ++i) fac_total += (size_t)dims[i] * ranks[i];
-  if (nbytes < off + fac_total * 8 + 8) return fail(ATC_ECORRUPT, "truncated factors");
+  // kept-column maps, then the kept columns of every factor; the dropped
+  // columns multiply all-zero core slices, so they are rebuilt as zeros
+  size_t map_bytes = 0, fac_total = 0, kept_total = 0;
+  for (int i = 0; i < d; ++i) map_bytes += (size_t)(ranks[i] + 7) / 8;
+  if (nbytes < off + map_bytes + 8) return fail(ATC_ECORRUPT, "truncated column maps");
+  std::vector<std::vector<uint8_t>> keep(d);
+  {
+    size_t mo = off;
+    for (int i = 0; i < d; ++i) {
+      keep[i].resize((size_t)ranks[i]);
+      for (int64_t col = 0; col < ranks[i]; ++col) {
+        keep[i][(size_t)col] = (stream[mo + col / 8] >> (col % 8)) & 1;
+        kept_total += (size_t)dims[i] * keep[i][(size_t)col];
+      }
+      mo += (size_t)(ranks[i] + 7) / 8;
+      fac_total += (size_t)dims[i] * ranks[i];
+    }
+  }
+  off += (map_bytes + 7) & ~(size_t)7;
+  if (nbytes < off + kept_total * 8 + 8) return fail(ATC_ECORRUPT, "truncated factors");
+  std::vector<double> hfac(fac_total, 0.0);
+  {
+    size_t at = off, acc = 0;
+    for (int i = 0; i < d; ++i) {
+      for (int64_t row = 0; row < dims[i]; ++row)
+        for (int64_t col = 0; col < ranks[i]; ++col)
+          if (keep[i][(size_t)col]) {
+            uint64_t u = get64(stream + at);
+            memcpy(&hfac[acc + (size_t)(row * ranks[i] + col)], &u, 8);
+            at += 8;
+          }
+      acc += (size_t)dims[i] * ranks[i];
+    }
+  }
   double* fac = nullptr;
   ATC_TRY(Scratch::get(SLOT_FAC, fac_total * 8 + 64, (void**)&fac));
-  ATC_CUDA_TRY(cudaMemcpyAsync(fac, stream + off, fac_total * 8, cudaMemcpyHostToDevice, s));
+  ATC_CUDA_TRY(cudaMemcpyAsync(fac, hfac.data(), fac_total * 8, cudaMemcpyHostToDevice, s));
   double* U[8];
   {
     size_t acc = 0;
     for (int i = 0; i < d; ++i) { U[i] = fac + acc; acc += (size_t)dims[i] * ranks[i]; }
   }
-  off += fac_total * 8;
+  off += kept_total * 8;
   const uint64_t cb = get64(stream + off);
   off += 8;
   if (cb > nbytes - off) return fail(ATC_ECORRUPT, "truncated core section");

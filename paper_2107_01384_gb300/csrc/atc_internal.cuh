@@ -86,6 +86,7 @@ enum ScratchSlot {
   SLOT_TTM_AIMG,       // pre-sliced data operand of single-K-tile products
   SLOT_RES_TMP,        // reproduction U ._k Y of the certification residual
   SLOT_RES_PART,       // its partial sums
+  SLOT_KEPT,           // per-slice significance flags of the quantized core
   SLOT_COUNT
 };
 
@@ -119,9 +120,10 @@ struct SliceScale {
   int shift;
 };
 int slice_scale(const void* x, int dtype, int64_t N, cudaStream_t s, const SliceScale** out);
-// xs: the input's slice scale from slice_scale(), or nullptr to compute it here
+// xs: the input's slice scale from slice_scale(), or nullptr to compute it here;
+// nslice: 3 (24-bit fixed point) or 4 (32-bit)
 int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g,
-                      cudaStream_t s, const SliceScale* xs = nullptr);
+                      cudaStream_t s, const SliceScale* xs = nullptr, int nslice = 3);
 int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
                      int expand, int precision, void* y, int ydtype, cudaStream_t s,
                      const SliceScale* xs = nullptr);
@@ -173,6 +175,27 @@ struct QuantResult {
 int quantize_encode(const double* core, int64_t n, double target, int block_size, cudaStream_t s,
                     std::string* out, QuantResult* res, float* ms_quant, float* ms_encode);
 int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t n, cudaStream_t s);
+// slices of the last quantized core holding a significant coefficient (k_quant.cu)
+int core_kept_slices(int64_t n, const int64_t* ranks, const int* perm, int d, int p_star, int64_t i_star,
+                     uint8_t* kept_host, cudaStream_t s);
+
+// Kernel timer (atc_kernel_timing): when enabled, the launch sites of the main
+// kernels bracket their launch with CUDA events recorded on the launching
+// stream; atc_kernel_times() reports launches and total device time per kernel.
+// Off by default (one relaxed load per launch site).
+// Each timed launch also records its algorithmic work: bytes the operation must
+// move (inputs read once, outputs written once) and FLOPs of the operation it
+// computes, plus the FLOPs the tensor cores issue for it (slice products and
+// tile padding), 0 where not applicable.
+int ktimer_begin(cudaStream_t s, const char* name, double bytes, double flops, double issued);  // token or -1
+void ktimer_end(cudaStream_t s, int token);
+struct KTimed {
+  cudaStream_t s;
+  int tok;
+  KTimed(cudaStream_t st, const char* name, double bytes = 0.0, double flops = 0.0, double issued = 0.0)
+      : s(st), tok(ktimer_begin(st, name, bytes, flops, issued)) {}
+  ~KTimed() { ktimer_end(s, tok); }
+};
 
 // drop the cached device address of the no-allocation Gram array of `dev`
 void noalloc_forget(int dev);

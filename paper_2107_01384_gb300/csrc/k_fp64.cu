@@ -254,10 +254,15 @@ int launch_gram_fp64(const void* x, int dtype, int64_t L, int64_t n, int64_t R, 
   double* part = nullptr;
   ATC_TRY(Scratch::get(SLOT_GRAM_PART, sizeof(double) * nsplit * n * n, (void**)&part));
   dim3 grid(npairs, (unsigned)nsplit);
-  if (dtype == ATC_F32)
-    gram_fp64_kernel<float><<<grid, kThreads, 0, s>>>((const float*)x, n, R, K, kchunk, ntile, part);
-  else
-    gram_fp64_kernel<double><<<grid, kThreads, 0, s>>>((const double*)x, n, R, K, kchunk, ntile, part);
+  {
+    KTimed kt_(s, "gram_fp64_kernel", (double)n * (double)K * (dtype == ATC_F32 ? 4.0 : 8.0) +
+                                          (double)nsplit * (double)n * (double)n * 8.0,
+               (double)n * (double)n * (double)K);
+    if (dtype == ATC_F32)
+      gram_fp64_kernel<float><<<grid, kThreads, 0, s>>>((const float*)x, n, R, K, kchunk, ntile, part);
+    else
+      gram_fp64_kernel<double><<<grid, kThreads, 0, s>>>((const double*)x, n, R, K, kchunk, ntile, part);
+  }
   ATC_LAUNCHED(1);
   int64_t tot = n * n;
   int blocks = (int)((tot + 255) / 256);
@@ -313,6 +318,10 @@ int launch_ttm_fp64(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, 
   if (N == 0 || A == 0) return ATC_OK;
   dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((A + TM - 1) / TM));
   if (grid.y > 65535) return fail(ATC_EUNSUP, "ttm: output mode too large");
+  KTimed kt_(s, "ttm_fp64_kernel",
+             (double)N * (double)B * (xdtype == ATC_F32 ? 4.0 : 8.0) + (double)N * (double)A * (ydtype == ATC_F32 ? 4.0 : 8.0) +
+                 (double)A * (double)B * 8.0,
+             2.0 * (double)N * (double)A * (double)B);
   if (xdtype == ATC_F32 && ydtype == ATC_F32)
     ttm_fp64_kernel<float, float><<<grid, kThreads, 0, s>>>((const float*)x, u, wsa, wsb, A, B, R, N, (float*)y);
   else if (xdtype == ATC_F32 && ydtype == ATC_F64)

@@ -365,16 +365,23 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramArgs a) {
 
 // ------------------------------------------------ pre-sliced, TMA-fed variant
 // The slices are formed once per mode by slice_planes_kernel (an HBM-bound
-// pass) into three 16-bit planes in the unfolded (n, Kp) layout, Kp = K rounded
-// up to 64 with zero padding; the Gram CTAs then pull 128 x 64 (A rows) and
-// 64 x 64 (B rows) tiles of every plane with TMA (128-byte swizzle, the smem
-// image the MMA descriptors expect), so no warp re-slices a row block per
-// tile.  Warp 0 issues the copies, warp 1 the MMAs (the same nine products
-// into five orders), warps 2-5 flush each exact window into a double-float
-// running sum kept in their registers.
+// pass) into NS = 3 (24-bit fixed point) or NS = 4 (32-bit) 16-bit planes in
+// the unfolded (n, Kp) layout, Kp = K rounded up to 64 with zero padding; the
+// Gram CTAs then pull 128 x 64 (A rows) and 64 x 64 (B rows) tiles of every
+// plane with TMA (128-byte swizzle, the smem image the MMA descriptors
+// expect), so no warp re-slices a row block per tile.  Warp 0 issues the
+// copies, warp 1 the MMAs (all slice products of order s + t <= 4 -- nine for
+// three slices, thirteen for four -- into five order accumulators), warps 2-5
+// flush each exact window into a double-float running sum kept in their
+// registers.  With four slices every partial sum of an order stays below
+// 3 * 2^22 < 2^24 in a window of 128 products (|a0| <= 256, other slices
+// <= 128), so the FP32 accumulation is still exact.
 constexpr int kTmaThreads = 192;
-constexpr int TNS = 3;                      // pipeline stages
-constexpr int T_STAGE = 3 * SLOT_A + 3 * SLOT_B;
+template <int NS>
+struct TmaCfg {
+  static constexpr int STAGES = (NS == 3) ? 3 : 2;  // 216 KB / 192 KB of stages
+  static constexpr int STAGE = NS * (SLOT_A + SLOT_B);
+};
 
 struct GramTmaArgs {
   int64_t kchunk;  // multiple of KT
@@ -384,12 +391,15 @@ struct GramTmaArgs {
   int* err;
 };
 
-template <bool BF16>
+struct GramMaps {
+  CUtensorMap a[4], b[4];  // per slice plane: 128-row and 64-row boxes
+};
+
+template <bool BF16, int NS>
 __global__ void __launch_bounds__(kTmaThreads, 1)
-    gram_tma_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-                    const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
-                    const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
-                    GramTmaArgs a) {
+    gram_tma_kernel(const __grid_constant__ GramMaps maps, GramTmaArgs a) {
+  constexpr int TNS = TmaCfg<NS>::STAGES;
+  constexpr int T_STAGE = TmaCfg<NS>::STAGE;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full_bar[TNS], empty_bar[TNS], accf_bar, acce_bar, done_bar;
   __shared__ uint32_t tmem_slot;
@@ -431,12 +441,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         uint8_t* st = smem + s * T_STAGE;
         mbar_arrive_expect_tx(&full_bar[s], (uint32_t)T_STAGE);
         const int k0 = (int)(kb + (int64_t)t * KT);
-        tma_load_2d(st, &mA0, &full_bar[s], k0, ti * TM);
-        tma_load_2d(st + SLOT_A, &mA1, &full_bar[s], k0, ti * TM);
-        tma_load_2d(st + 2 * SLOT_A, &mA2, &full_bar[s], k0, ti * TM);
-        tma_load_2d(st + 3 * SLOT_A, &mB0, &full_bar[s], k0, cj * TN);
-        tma_load_2d(st + 3 * SLOT_A + SLOT_B, &mB1, &full_bar[s], k0, cj * TN);
-        tma_load_2d(st + 3 * SLOT_A + 2 * SLOT_B, &mB2, &full_bar[s], k0, cj * TN);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          tma_load_2d(st + q * SLOT_A, &maps.a[q], &full_bar[s], k0, ti * TM);
+          tma_load_2d(st + NS * SLOT_A + q * SLOT_B, &maps.b[q], &full_bar[s], k0, cj * TN);
+        }
         issued = t + 1;
       }
       // every issued copy must land before the CTA may exit
@@ -456,22 +465,25 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
           const int s = t % TNS;
           if (!mbar_wait(&full_bar[s], (uint32_t)(t / TNS) & 1u, abort)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + s * T_STAGE), sb = sa + 3 * SLOT_A;
+          const uint32_t sa = smem_u32(smem + s * T_STAGE), sb = sa + NS * SLOT_A;
 #pragma unroll
           for (int j = 0; j < KT / 16; ++j) {
             const uint32_t acc = (t == g * FLUSH && j == 0) ? 0u : 1u;
             const uint32_t o = 32u * j;
-            const uint64_t A0 = desc_k128(sa + o), A1 = desc_k128(sa + SLOT_A + o), A2 = desc_k128(sa + 2 * SLOT_A + o);
-            const uint64_t B0 = desc_k128(sb + o), B1 = desc_k128(sb + SLOT_B + o), B2 = desc_k128(sb + 2 * SLOT_B + o);
-            umma_f16(tmem + 0u, A0, B0, idesc, acc);
-            umma_f16(tmem + 64u, A0, B1, idesc, acc);
-            umma_f16(tmem + 64u, A1, B0, idesc, 1u);
-            umma_f16(tmem + 128u, A0, B2, idesc, acc);
-            umma_f16(tmem + 128u, A1, B1, idesc, 1u);
-            umma_f16(tmem + 128u, A2, B0, idesc, 1u);
-            umma_f16(tmem + 192u, A1, B2, idesc, acc);
-            umma_f16(tmem + 192u, A2, B1, idesc, 1u);
-            umma_f16(tmem + 256u, A2, B2, idesc, acc);
+            // order o = s + t <= 4 into TMEM columns [64 o, 64 o + 64); the first
+            // product of an order in a window starts it (acc), the others add
+#pragma unroll
+            for (int od = 0; od <= 4; ++od) {
+              bool first = true;
+#pragma unroll
+              for (int sa_i = 0; sa_i < NS; ++sa_i) {
+                const int tb_i = od - sa_i;
+                if (tb_i < 0 || tb_i >= NS) continue;
+                umma_f16(tmem + 64u * od, desc_k128(sa + sa_i * SLOT_A + o), desc_k128(sb + tb_i * SLOT_B + o), idesc,
+                         first ? acc : 1u);
+                first = false;
+              }
+            }
           }
           umma_commit(&empty_bar[s]);
         }
@@ -537,48 +549,68 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 // Slices of the (L, n, R) tensor into three 16-bit planes laid out (n, Kp):
 // plane[i][k] for k = l R + r (zero for k >= K).  For R = 1 the reads along k
 // are strided by n, so that case goes through a 32 x 32 shared-memory transpose.
-template <typename T, bool BF16>
+struct Planes {
+  uint16_t* p[4];
+};
+template <bool BF16, int NS>
+__device__ __forceinline__ void put_slices(const Planes& pl, int64_t idx, float v) {
+  float a0, a1, a2, a3 = 0.f;
+  if (NS == 4) slice4i(v, a0, a1, a2, a3);
+  else slice3i(v, a0, a1, a2);
+  pl.p[0][idx] = Pack<BF16>::one(a0);
+  pl.p[1][idx] = Pack<BF16>::one(a1);
+  pl.p[2][idx] = Pack<BF16>::one(a2);
+  if (NS == 4) pl.p[3][idx] = Pack<BF16>::one(a3);
+}
+// FP64 input: the slices are cut from the double value v = x 2^shift (every
+// step exact in binary64 for |v| < 256); rounding x to float first would keep
+// only 24 significant bits, less than four slices resolve near max |x|
+template <bool BF16, int NS>
+__device__ __forceinline__ void put_slices_d(const Planes& pl, int64_t idx, double v) {
+  if (NS == 3) {
+    put_slices<BF16, NS>(pl, idx, (float)v);  // 24 bits below max |x|: float holds them
+    return;
+  }
+  const double a0 = rint(v), t = (v - a0) * 256.0, a1 = rint(t), t2 = (t - a1) * 256.0, a2 = rint(t2);
+  const double a3 = rint((t2 - a2) * 256.0);
+  pl.p[0][idx] = Pack<BF16>::one((float)a0);
+  pl.p[1][idx] = Pack<BF16>::one((float)a1);
+  pl.p[2][idx] = Pack<BF16>::one((float)a2);
+  pl.p[3][idx] = Pack<BF16>::one((float)a3);
+}
+
+template <typename T, bool BF16, int NS>
 __global__ void slice_planes_kernel(const T* __restrict__ x, int64_t n, int64_t R, int64_t K, int64_t Kp,
-                                    const SliceScale* __restrict__ xs, uint16_t* __restrict__ p0,
-                                    uint16_t* __restrict__ p1, uint16_t* __restrict__ p2) {
-  const float sc = ldexpf(1.0f, xs->shift);
+                                    const SliceScale* __restrict__ xs, Planes pl) {
   const int64_t total = n * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx / Kp, k = idx - i * Kp;
-    float v = 0.f;
+    T v = 0;
     if (k < K) {
       const int64_t l = k / R, r = k - l * R;
-      v = (float)__ldg(x + (l * n + i) * R + r) * sc;
+      v = __ldg(x + (l * n + i) * R + r);
     }
-    float a0, a1, a2;
-    slice3i(v, a0, a1, a2);
-    p0[idx] = Pack<BF16>::one(a0);
-    p1[idx] = Pack<BF16>::one(a1);
-    p2[idx] = Pack<BF16>::one(a2);
+    if (sizeof(T) == 8) put_slices_d<BF16, NS>(pl, idx, ldexp((double)v, xs->shift));
+    else put_slices<BF16, NS>(pl, idx, ldexpf((float)v, xs->shift));
   }
 }
-template <typename T, bool BF16>
+template <typename T, bool BF16, int NS>
 __global__ void slice_planes_t_kernel(const T* __restrict__ x, int64_t n, int64_t K, int64_t Kp,
-                                      const SliceScale* __restrict__ xs, uint16_t* __restrict__ p0,
-                                      uint16_t* __restrict__ p1, uint16_t* __restrict__ p2) {
+                                      const SliceScale* __restrict__ xs, Planes pl) {
   // R == 1: x[k][i] (k = l), tile of 32 k x 32 i through shared memory
-  __shared__ float tile[32][33];
-  const float sc = ldexpf(1.0f, xs->shift);
+  __shared__ T tile[32][33];
   const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
   for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
     const int64_t k = k0 + yy, i = i0 + threadIdx.x;
-    tile[yy][threadIdx.x] = (k < K && i < n) ? (float)__ldg(x + k * n + i) * sc : 0.f;
+    tile[yy][threadIdx.x] = (k < K && i < n) ? __ldg(x + k * n + i) : (T)0;
   }
   __syncthreads();
   for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
     const int64_t i = i0 + yy, k = k0 + threadIdx.x;
     if (i < n && k < Kp) {
-      float a0, a1, a2;
-      slice3i(tile[threadIdx.x][yy], a0, a1, a2);
-      const int64_t idx = i * Kp + k;
-      p0[idx] = Pack<BF16>::one(a0);
-      p1[idx] = Pack<BF16>::one(a1);
-      p2[idx] = Pack<BF16>::one(a2);
+      const T v = tile[threadIdx.x][yy];
+      if (sizeof(T) == 8) put_slices_d<BF16, NS>(pl, i * Kp + k, ldexp((double)v, xs->shift));
+      else put_slices<BF16, NS>(pl, i * Kp + k, ldexpf((float)v, xs->shift));
     }
   }
 }
@@ -705,6 +737,7 @@ int slice_scale(const void* x, int dtype, int64_t N, cudaStream_t s, const Slice
   ATC_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(SliceScale), s));
   if (N > 0) {
     const int blocks = (int)((N + 255) / 256 < 1216 ? (N + 255) / 256 : 1216);
+    KTimed kt_(s, "absmax_kernel", (double)N * (dtype == ATC_F32 ? 4.0 : 8.0));
     if (dtype == ATC_F32)
       absmax_kernel<float><<<blocks, 256, 0, s>>>((const float*)x, N, &sc->maxbits);
     else
@@ -717,9 +750,40 @@ int slice_scale(const void* x, int dtype, int64_t N, cudaStream_t s, const Slice
   return ATC_OK;
 }
 
+namespace {
+template <typename T, bool BF16, int NS>
+void launch_slices(const T* x, int64_t n, int64_t R, int64_t K, int64_t Kp, const SliceScale* xs, const Planes& pl,
+                   cudaStream_t s) {
+  KTimed kt_(s, NS == 3 ? "slice_planes_kernel" : "slice_planes_kernel(4 slices)",
+             (double)n * (double)K * sizeof(T) + (double)NS * 2.0 * (double)n * (double)Kp);
+  if (R == 1) {
+    const dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)((n + 31) / 32));
+    slice_planes_t_kernel<T, BF16, NS><<<grid, dim3(32, 8), 0, s>>>(x, n, K, Kp, xs, pl);
+  } else {
+    const int64_t tot = n * Kp;
+    const int blocks = (int)((tot + 255) / 256 < 4 * 1216 ? (tot + 255) / 256 : 4 * 1216);
+    slice_planes_kernel<T, BF16, NS><<<blocks, 256, 0, s>>>(x, n, R, K, Kp, xs, pl);
+  }
+}
+template <bool BF16, int NS>
+int launch_gram_tma(const GramMaps& maps, const GramTmaArgs& ta, int grid, cudaStream_t s, double bytes, double flops,
+                    double issued) {
+  const int smem = TmaCfg<NS>::STAGES * TmaCfg<NS>::STAGE + 1024;
+  static bool attr = false;
+  if (!attr) {
+    ATC_CUDA_TRY(cudaFuncSetAttribute(gram_tma_kernel<BF16, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  KTimed kt_(s, NS == 3 ? "gram_tma_kernel" : "gram_tma_kernel(4 slices)", bytes, flops, issued);
+  gram_tma_kernel<BF16, NS><<<grid, kTmaThreads, smem, s>>>(maps, ta);
+  return ATC_OK;
+}
+}  // namespace
+
 int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g,
-                      cudaStream_t s, const SliceScale* xs) {
+                      cudaStream_t s, const SliceScale* xs, int nslice) {
   if (n > 1024) return fail(ATC_EUNSUP, "split-precision Gram supports n <= 1024 (n = %lld)", (long long)n);
+  if (nslice != 3 && nslice != 4) return fail(ATC_EINVAL, "split-precision Gram: %d slices", nslice);
   if (g_nsm == 0) {
     int dev = 0;
     ATC_CUDA_TRY(cudaGetDevice(&dev));
@@ -739,39 +803,32 @@ int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R,
   if (nsplit < 1) nsplit = 1;
   if (!xs) ATC_TRY(slice_scale(x, dtype, K * n, s, &xs));
   const bool bf16 = (precision == ATC_PREC_SPLIT_BF16);
-  if (encode_fn() && !gram_tma_off()) {
+  if (!encode_fn() && nslice == 4) return fail(ATC_EUNSUP, "four-slice Gram needs cuTensorMapEncodeTiled");
+  if (encode_fn() && (!gram_tma_off() || nslice == 4)) {
     // pre-sliced planes + TMA-fed tensor-core Gram
     const int64_t Kp = ktiles * KT;
     uint16_t* planes = nullptr;
-    ATC_TRY(Scratch::get(SLOT_SLICES, (size_t)3 * n * Kp * 2 + 1024, (void**)&planes));
-    uint16_t* p0 = planes;
-    uint16_t* p1 = planes + n * Kp;
-    uint16_t* p2 = planes + 2 * n * Kp;
-    if (R == 1) {
-      const dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)((n + 31) / 32));
-      const dim3 blk(32, 8);
-      if (dtype == ATC_F32)
-        bf16 ? slice_planes_t_kernel<float, true><<<grid, blk, 0, s>>>((const float*)x, n, K, Kp, xs, p0, p1, p2)
-             : slice_planes_t_kernel<float, false><<<grid, blk, 0, s>>>((const float*)x, n, K, Kp, xs, p0, p1, p2);
-      else
-        bf16 ? slice_planes_t_kernel<double, true><<<grid, blk, 0, s>>>((const double*)x, n, K, Kp, xs, p0, p1, p2)
-             : slice_planes_t_kernel<double, false><<<grid, blk, 0, s>>>((const double*)x, n, K, Kp, xs, p0, p1, p2);
+    ATC_TRY(Scratch::get(SLOT_SLICES, (size_t)nslice * n * Kp * 2 + 1024, (void**)&planes));
+    Planes pl;
+    for (int q = 0; q < 4; ++q) pl.p[q] = planes + (q < nslice ? q : 0) * n * Kp;
+    if (dtype == ATC_F32) {
+      const float* xf = (const float*)x;
+      if (nslice == 3) bf16 ? launch_slices<float, true, 3>(xf, n, R, K, Kp, xs, pl, s)
+                            : launch_slices<float, false, 3>(xf, n, R, K, Kp, xs, pl, s);
+      else bf16 ? launch_slices<float, true, 4>(xf, n, R, K, Kp, xs, pl, s)
+                : launch_slices<float, false, 4>(xf, n, R, K, Kp, xs, pl, s);
     } else {
-      const int64_t tot = n * Kp;
-      const int blocks = (int)((tot + 255) / 256 < 4 * 1216 ? (tot + 255) / 256 : 4 * 1216);
-      if (dtype == ATC_F32)
-        bf16 ? slice_planes_kernel<float, true><<<blocks, 256, 0, s>>>((const float*)x, n, R, K, Kp, xs, p0, p1, p2)
-             : slice_planes_kernel<float, false><<<blocks, 256, 0, s>>>((const float*)x, n, R, K, Kp, xs, p0, p1, p2);
-      else
-        bf16 ? slice_planes_kernel<double, true><<<blocks, 256, 0, s>>>((const double*)x, n, R, K, Kp, xs, p0, p1, p2)
-             : slice_planes_kernel<double, false><<<blocks, 256, 0, s>>>((const double*)x, n, R, K, Kp, xs, p0, p1, p2);
+      const double* xd = (const double*)x;
+      if (nslice == 3) bf16 ? launch_slices<double, true, 3>(xd, n, R, K, Kp, xs, pl, s)
+                            : launch_slices<double, false, 3>(xd, n, R, K, Kp, xs, pl, s);
+      else bf16 ? launch_slices<double, true, 4>(xd, n, R, K, Kp, xs, pl, s)
+                : launch_slices<double, false, 4>(xd, n, R, K, Kp, xs, pl, s);
     }
     ATC_LAUNCHED(1);
-    CUtensorMap mA[3], mB[3];
-    uint16_t* pl[3] = {p0, p1, p2};
-    for (int q = 0; q < 3; ++q) {
-      ATC_TRY(make_map(&mA[q], pl[q], n, Kp, TM, bf16));
-      ATC_TRY(make_map(&mB[q], pl[q], n, Kp, TN, bf16));
+    GramMaps maps;
+    for (int q = 0; q < 4; ++q) {
+      ATC_TRY(make_map(&maps.a[q], pl.p[q], n, Kp, TM, bf16));
+      ATC_TRY(make_map(&maps.b[q], pl.p[q], n, Kp, TN, bf16));
     }
     GramTmaArgs ta;
     ta.kchunk = tpc * KT;
@@ -784,27 +841,24 @@ int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R,
     int* err = nullptr;
     ATC_TRY(tc_error_flag(&err));
     ta.err = err;
-    const int smem = TNS * T_STAGE + 1024;
     const int grid = npair * nsplit;
-    if (bf16) {
-      static bool attr = false;
-      if (!attr) {
-        ATC_CUDA_TRY(cudaFuncSetAttribute(gram_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr = true;
-      }
-      gram_tma_kernel<true><<<grid, kTmaThreads, smem, s>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], ta);
-    } else {
-      static bool attr = false;
-      if (!attr) {
-        ATC_CUDA_TRY(cudaFuncSetAttribute(gram_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr = true;
-      }
-      gram_tma_kernel<false><<<grid, kTmaThreads, smem, s>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], ta);
-    }
+    // algorithmic work of this kernel: every plane element read once, the
+    // split partials written once; the SYRK's n^2 K FLOPs (unique half, as
+    // multiply-adds); issued: all slice products over the 128 x 64 tiles
+    const double gb = (double)nslice * 2.0 * (double)n * (double)Kp + (double)part_elems * 8.0;
+    const double gf = (double)n * (double)n * (double)K;
+    const double gi = (nslice == 3 ? 9.0 : 13.0) * 2.0 * TM * TN * (double)Kp * (double)npair;
+    if (nslice == 3)
+      ATC_TRY((bf16 ? launch_gram_tma<true, 3>(maps, ta, grid, s, gb, gf, gi) : launch_gram_tma<false, 3>(maps, ta, grid, s, gb, gf, gi)));
+    else
+      ATC_TRY((bf16 ? launch_gram_tma<true, 4>(maps, ta, grid, s, gb, gf, gi) : launch_gram_tma<false, 4>(maps, ta, grid, s, gb, gf, gi)));
     ATC_LAUNCHED(1);
     const int64_t tot = n * n;
     const int rb = (int)((tot + 255) / 256 < 2048 ? (tot + 255) / 256 : 2048);
-    gram_tc_assemble<<<rb, 256, 0, s>>>(ta.part, nsplit, npair, nc64, n, xs, g);
+    {
+      KTimed kt_(s, "gram_tc_assemble", (double)part_elems * 8.0 + (double)n * (double)n * 8.0);
+      gram_tc_assemble<<<rb, 256, 0, s>>>(ta.part, nsplit, npair, nc64, n, xs, g);
+    }
     ATC_LAUNCHED(1);
     return ATC_OK;
   }

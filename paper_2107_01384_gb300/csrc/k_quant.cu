@@ -1364,7 +1364,10 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
   ATC_LAUNCHED(1);
   scale_exp_kernel<<<1, 32, 0, s>>>(mx, target, st);
   ATC_LAUNCHED(1);
-  quantize_kernel<<<grid, 256, 0, s>>>(core, n, &st->k, q, sg);
+  {
+    KTimed kt_(s, "quantize_kernel", (double)n * (8.0 + 8.0 + 1.0));
+    quantize_kernel<<<grid, 256, 0, s>>>(core, n, &st->k, q, sg);
+  }
   ATC_LAUNCHED(1);
   TrackState* hstp = nullptr;
   ATC_TRY(quant_pinned(sizeof(TrackState) + 16 + sizeof(uint32_t) * 2 * 64 * kNsym, (void**)&hstp));
@@ -1374,7 +1377,10 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
   for (;;) {
     int plo = phi - kPlaneChunk + 1;
     if (plo < 0) plo = 0;
-    plane_stats_kernel<<<nseg, kSegThreads, 0, s>>>(q, n, seg_len, plo, phi, first ? 1 : 0, segs, e64s);
+    {
+      KTimed kt_(s, "plane_stats_kernel", (double)n * 8.0);
+      plane_stats_kernel<<<nseg, kSegThreads, 0, s>>>(q, n, seg_len, plo, phi, first ? 1 : 0, segs, e64s);
+    }
     ATC_LAUNCHED(1);
     plane_scan_kernel<<<1, 32 * kPlaneChunk, 0, s>>>(segs, e64s, nseg, plo, phi, first ? 1 : 0, st);
     ATC_LAUNCHED(1);
@@ -1435,11 +1441,17 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     P.off = off; P.out = nullptr; P.table = nullptr;
     const int wpb = 4;
     const unsigned eg = (unsigned)((nchunks + wpb - 1) / wpb);
-    enc_hist_kernel<<<eg, 32 * wpb, 0, s>>>(P);
+    {
+      KTimed kt_(s, "enc_hist_kernel");
+      enc_hist_kernel<<<eg, 32 * wpb, 0, s>>>(P);
+    }
     ATC_LAUNCHED(1);
     freq_kernel<<<(nplanes + 63) / 64, 64, 0, s>>>(hist, nplanes, fc);
     ATC_LAUNCHED(1);
-    enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 1, spill);
+    {
+      KTimed kt_(s, "enc_rans_kernel(sizes)");
+      enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 1, spill);
+    }
     ATC_LAUNCHED(1);
     scan_kernel<<<1, 1024, 0, s>>>(rsize, wsize, nchunks, off);
     ATC_LAUNCHED(1);
@@ -1457,7 +1469,10 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     ATC_TRY(Scratch::get(SLOT_OUT, tabb + total + 64, (void**)&dout));
     P.table = reinterpret_cast<uint32_t*>(dout);
     P.out = dout + tabb;
-    enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 0, spill);
+    {
+      KTimed kt_(s, "enc_rans_kernel");
+      enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 0, spill);
+    }
     ATC_LAUNCHED(1);
     result.resize(hdr + tabb + total);
     memcpy(&result[0], head.data(), hdr);
@@ -1483,6 +1498,70 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     res->sse_pred = ldexp(i192_to_double(hst.e_star), -2 * k);
   }
   out->swap(result);
+  return ATC_OK;
+}
+
+namespace {
+// Slices of the core that keep a significant coefficient (Section 3.3, the
+// paragraph after Table 2): coefficient j of the vectorised core is significant
+// when one of its encoded bits is a 1 -- planes >= p_star for j <= i_star,
+// >= p_star + 1 after it; its storage-order index on axis a marks slice idx_a
+// of mode perm[a].  A flag is read before it is set, so a slice costs one
+// atomic however many significant coefficients it holds.
+struct KeptArgs {
+  int d;
+  int64_t dim[8];  // storage-order sizes (the vectorisation's row-major shape)
+  int off[8];      // first flag of storage axis a
+};
+__global__ void kept_slices_kernel(const uint64_t* __restrict__ q, int64_t n, int p_star, int64_t i_star, KeptArgs a,
+                                   unsigned* __restrict__ flags) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int lo = (j <= i_star) ? p_star : p_star + 1;
+    if (lo >= 64 || (q[j] >> lo) == 0ull) continue;
+    int64_t rem = j;
+    for (int ax = a.d - 1; ax >= 0; --ax) {
+      const int64_t idx = rem % a.dim[ax];
+      rem /= a.dim[ax];
+      unsigned* f = flags + a.off[ax] + idx;
+      if (*reinterpret_cast<volatile unsigned*>(f) == 0u) atomicOr(f, 1u);
+    }
+  }
+}
+}  // namespace
+
+// kept[i][c] (host, sum_i ranks[i] bytes, mode-major) for the core most recently
+// quantized by quantize_encode on this device (its magnitudes are still in the
+// quantizer scratch): 1 where slice c of mode i holds a significant coefficient.
+int core_kept_slices(int64_t n, const int64_t* ranks, const int* perm, int d, int p_star, int64_t i_star,
+                     uint8_t* kept_host, cudaStream_t s) {
+  if (d < 1 || d > 8) return fail(ATC_EINVAL, "core_kept_slices: ndim %d", d);
+  int total = 0, moff[8];
+  for (int i = 0; i < d; ++i) {
+    moff[i] = total;
+    total += (int)ranks[i];
+  }
+  uint64_t* q = nullptr;
+  ATC_TRY(Scratch::get(SLOT_Q, sizeof(uint64_t) * (size_t)n, (void**)&q));
+  unsigned* flags = nullptr;
+  ATC_TRY(Scratch::get(SLOT_KEPT, sizeof(unsigned) * (size_t)total + 64, (void**)&flags));
+  ATC_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)total, s));
+  KeptArgs a;
+  a.d = d;
+  for (int ax = 0; ax < d; ++ax) {
+    a.dim[ax] = ranks[perm[ax]];
+    a.off[ax] = moff[perm[ax]];
+  }
+  if (p_star < 64 && n > 0) {
+    const int64_t gb = (n + 255) / 256;
+    const int grid = (int)(gb < 152 * 16 ? gb : 152 * 16);
+    KTimed kt_(s, "kept_slices_kernel", (double)n * 8.0);
+    kept_slices_kernel<<<grid, 256, 0, s>>>(q, n, p_star, i_star, a, flags);
+  }
+  ATC_LAUNCHED(1);
+  std::vector<unsigned> h((size_t)total);
+  ATC_CUDA_TRY(cudaMemcpyAsync(h.data(), flags, sizeof(unsigned) * (size_t)total, cudaMemcpyDeviceToHost, s));
+  ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int t = 0; t < total; ++t) kept_host[t] = h[t] ? 1 : 0;
   return ATC_OK;
 }
 
@@ -1537,8 +1616,14 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
                                             sizeof(int) * (size_t)nchunk + 256, (void**)&rbuf));
     RP.runs = reinterpret_cast<uint32_t*>(rbuf);
     RP.nruns = reinterpret_cast<int*>(rbuf + sizeof(uint32_t) * (size_t)nchunk * (D.block_size + 2));
-    decode_runs_kernel<<<(unsigned)((nchunk + 63) / 64), 64, 0, s>>>(RP);
-    decode_place_kernel<<<(unsigned)D.nblocks, kDecThreads, 0, s>>>(D, RP.runs, RP.nruns);
+    {
+      KTimed kt_(s, "decode_runs_kernel");
+      decode_runs_kernel<<<(unsigned)((nchunk + 63) / 64), 64, 0, s>>>(RP);
+    }
+    {
+      KTimed kt_(s, "decode_place_kernel");
+      decode_place_kernel<<<(unsigned)D.nblocks, kDecThreads, 0, s>>>(D, RP.runs, RP.nruns);
+    }
     ATC_LAUNCHED(2);
   } else if (D.block_size <= kDecMax) {
     static bool dec_attr = false;

@@ -208,7 +208,10 @@ int launch_row_energy(const float* y, int64_t L, int64_t r, int64_t R, double* e
   if (r > 65535) return fail(ATC_EUNSUP, "row energy: too many rows");
   double* part = nullptr;
   ATC_TRY(Scratch::get(SLOT_ENERGY, sizeof(double) * (size_t)r * kEnChunks + 256, (void**)&part));
-  row_energy_partial<<<dim3(kEnChunks, (unsigned)r), kNormThreads, 0, s>>>(y, L * R, r, R, part);
+  {
+    KTimed kt_(s, "row_energy_partial", (double)L * (double)R * (double)r * 4.0);
+    row_energy_partial<<<dim3(kEnChunks, (unsigned)r), kNormThreads, 0, s>>>(y, L * R, r, R, part);
+  }
   row_energy_finish<<<(unsigned)((r + 255) / 256), 256, 0, s>>>(part, kEnChunks, r, e);
   ATC_LAUNCHED(2);
   return ATC_OK;
@@ -227,9 +230,9 @@ int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t 
   double* part = nullptr;
   ATC_TRY(Scratch::get(SLOT_SMALL, sizeof(double) * (kNormBlocks + 64), (void**)&part));
   if (dtype == ATC_F32)
-    norm2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, n, part);
+    { KTimed kt_(s, "norm2_partial", (double)n * 4.0); norm2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, n, part); }
   else
-    norm2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, n, part);
+    { KTimed kt_(s, "norm2_partial", (double)n * 8.0); norm2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, n, part); }
   ATC_LAUNCHED(1);
   sum_partials<<<1, kNormThreads, 0, s>>>(part, kNormBlocks, out);
   ATC_LAUNCHED(1);
@@ -240,9 +243,9 @@ int launch_diff_norm2(const void* x, int dtype, const float* z, int64_t n, doubl
   double* part = nullptr;
   ATC_TRY(Scratch::get(SLOT_RES_PART, sizeof(double) * (kNormBlocks + 64), (void**)&part));
   if (dtype == ATC_F32)
-    diff2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, z, n, part);
+    { KTimed kt_(s, "diff2_partial", (double)n * 8.0); diff2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, z, n, part); }
   else
-    diff2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, z, n, part);
+    { KTimed kt_(s, "diff2_partial", (double)n * 12.0); diff2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, z, n, part); }
   ATC_LAUNCHED(1);
   sum_partials<<<1, kNormThreads, 0, s>>>(part, kNormBlocks, out);
   ATC_LAUNCHED(1);

@@ -79,7 +79,7 @@ __global__ void sub_diag_kernel(const double* __restrict__ G, int n, double* __r
 // lanes of a warp (consecutive i, coalesced), V[c][k] is a warp broadcast, four
 // independent FP64 accumulators.  Grid (ceil(n/32), ceil(K/8), kSubSplit),
 // 8 warps per CTA (one column c each).
-constexpr int kSubSplit = 4;
+constexpr int kSubSplit = 16;  // k-split: enough warps in flight to hide the L2 latency of G
 __global__ void __launch_bounds__(256) sub_gemm_part_kernel(const double* __restrict__ G, int n,
                                                             const double* __restrict__ V, int K,
                                                             double* __restrict__ part) {
@@ -109,7 +109,7 @@ __global__ void sub_gemm_sum_kernel(const double* __restrict__ part, int n, int 
     double v = part[e];
 #pragma unroll
     for (int z = 1; z < kSubSplit; ++z) v += part[z * nk + e];
-    if (Wd) Wd[e] = dd_from(v * ldexp(1.0, -*ex));
+    if (Wd) Wd[e] = dd_from(v * __longlong_as_double((long long)(1023 - *ex) << 52));  // v 2^-ex
     else W[e] = v;
   }
 }
@@ -407,6 +407,151 @@ __global__ void __launch_bounds__(kQrThreads) sub_qr_kernel(const dd* __restrict
   for (int e = tid; e < n * K; e += blockDim.x) Vg[e] = A[e];
 }
 
+// Householder QR of the K <= 32 columns of W (n x K, n <= 256), one CTA of
+// 1024 threads in double-float, for the mode lengths of the smooth fields:
+// warp c owns column c with its n entries in registers (kQcRpl rows per lane,
+// row = lane + 32 t).  Pivot j: warp j sums the squares below the diagonal
+// (warp butterfly), forms the reflector H_j = I - tau v v^T (v_j = 1, tau =
+// 2 v0^2 / (v0^2 + sigma) from v itself, so H_j is orthogonal to working
+// precision) and publishes v in shared memory; after one CTA barrier every warp
+// c > j applies H_j to its column (dot product by butterfly, update in
+// registers).  Warp j + 1 then pivots at once while the others still apply
+// H_j, so each pivot costs one barrier and no CTA-wide reduction.  The panels'
+// compact-WY blocks T (kQrNb columns each) are formed at the end for
+// sub_qform_kernel; the outputs match sub_qr_kernel's.
+constexpr int kQcRpl = 8;          // rows per lane: n <= 32 * kQcRpl
+constexpr int kQcThreads = 1024;   // 32 warps, one per column
+
+__global__ void __launch_bounds__(kQcThreads, 1) qr_col_kernel(const dd* __restrict__ W, int n, int K,
+                                                                dd* __restrict__ Vg, dd* __restrict__ Tg) {
+  extern __shared__ dd Vs[];  // K x n: column j = reflector j
+  __shared__ dd s_tau[32];
+  __shared__ dd s_S[4][kQrNb * kQrNb], s_T[4][kQrNb * kQrNb];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const dd zero = dd{0.f, 0.f}, one = dd{1.f, 0.f};
+  dd a[kQcRpl];
+#pragma unroll
+  for (int t = 0; t < kQcRpl; ++t) {
+    const int row = lane + 32 * t;
+    a[t] = (warp < K && row < n) ? W[(size_t)warp * n + row] : zero;
+  }
+  // sigma_j = sum_{row > j} a_row^2 of the next pivot column, accumulated by
+  // its warp while it applies the previous reflector (column 0: here)
+  dd sig_next = zero;
+  if (warp == 0) {
+    dd q0 = zero, q1 = zero;
+#pragma unroll
+    for (int t = 0; t < kQcRpl; ++t) {
+      const int row = lane + 32 * t;
+      if (row > 0 && row < n) {
+        if (t & 1) q1 = dd_add(q1, dd_mul(a[t], a[t]));
+        else q0 = dd_add(q0, dd_mul(a[t], a[t]));
+      }
+    }
+    sig_next = dd_add(q0, q1);
+  }
+  for (int j = 0; j < K; ++j) {
+    if (warp == j) {
+      const dd sig = dd_warp_sum_l(sig_next);
+      // a at row j: lane j % 32, register group j / 32
+      dd xl = zero;
+#pragma unroll
+      for (int t = 0; t < kQcRpl; ++t)
+        if (t == (j >> 5)) xl = a[t];
+      const dd x0 = dd{__shfl_sync(0xffffffffu, xl.hi, j & 31), __shfl_sync(0xffffffffu, xl.lo, j & 31)};
+      dd tau = zero, inv = zero;
+      if (sig.hi != 0.f) {
+        const dd nrm = qr_sqrt(dd_add(dd_mul(x0, x0), sig));
+        const dd alpha = dd_neg_sign(x0) ? nrm : dd_neg(nrm);
+        const dd v0 = dd_sub(x0, alpha);
+        const dd v02 = dd_mul(v0, v0);
+        tau = qr_div(dd_add(v02, v02), dd_add(v02, sig));
+        inv = qr_div(one, v0);
+      }
+#pragma unroll
+      for (int t = 0; t < kQcRpl; ++t) {
+        const int row = lane + 32 * t;
+        if (row < n) Vs[(size_t)j * n + row] = (row < j) ? zero : ((row == j) ? one : dd_mul(a[t], inv));
+      }
+      if (lane == 0) s_tau[j] = tau;
+    }
+    __syncthreads();
+    if (warp > j && warp < K) {
+      const dd tau = s_tau[j];
+      const bool next = warp == j + 1;  // the next pivot: also sums its squares below row j + 1
+      if (tau.hi != 0.f) {
+        dd v[kQcRpl];
+        dd s0 = zero, s1 = zero;
+#pragma unroll
+        for (int t = 0; t < kQcRpl; ++t) {
+          const int row = lane + 32 * t;
+          v[t] = zero;
+          if (32 * t + 32 > j) {  // groups entirely above row j hold zeros of v
+            v[t] = (row < n) ? Vs[(size_t)j * n + row] : zero;
+            if (t & 1) s1 = dd_add(s1, dd_mul(v[t], a[t]));
+            else s0 = dd_add(s0, dd_mul(v[t], a[t]));
+          }
+        }
+        const dd dv = dd_mul(tau, dd_warp_sum_l(dd_add(s0, s1)));
+        dd q0 = zero, q1 = zero;
+#pragma unroll
+        for (int t = 0; t < kQcRpl; ++t) {
+          if (32 * t + 32 > j) a[t] = dd_sub(a[t], dd_mul(dv, v[t]));
+          if (next) {
+            const int row = lane + 32 * t;
+            if (row > j + 1 && row < n) {
+              if (t & 1) q1 = dd_add(q1, dd_mul(a[t], a[t]));
+              else q0 = dd_add(q0, dd_mul(a[t], a[t]));
+            }
+          }
+        }
+        if (next) sig_next = dd_add(q0, q1);
+      } else if (next) {
+        dd q0 = zero, q1 = zero;
+#pragma unroll
+        for (int t = 0; t < kQcRpl; ++t) {
+          const int row = lane + 32 * t;
+          if (row > j + 1 && row < n) {
+            if (t & 1) q1 = dd_add(q1, dd_mul(a[t], a[t]));
+            else q0 = dd_add(q0, dd_mul(a[t], a[t]));
+          }
+        }
+        sig_next = dd_add(q0, q1);
+      }
+    }
+  }
+  __syncthreads();
+  // reflectors out; S[a][b] = v_a . v_b (a < b) inside each panel, a warp per pair
+  for (int e = tid; e < K * n; e += kQcThreads) Vg[e] = Vs[e];
+  const int npan = (K + kQrNb - 1) / kQrNb;
+  for (int item = warp; item < npan * kQrNb * kQrNb; item += kQcThreads / 32) {
+    const int p = item / (kQrNb * kQrNb), ab = item - p * kQrNb * kQrNb, aa = ab / kQrNb, bb = ab - aa * kQrNb;
+    const int ca = p * kQrNb + aa, cb = p * kQrNb + bb;
+    if (aa >= bb || cb >= K) continue;
+    dd sp = zero;
+    for (int row = cb + lane; row < n; row += 32) sp = dd_add(sp, dd_mul(Vs[(size_t)ca * n + row], Vs[(size_t)cb * n + row]));
+    sp = dd_warp_sum_l(sp);
+    if (lane == 0) s_S[p][aa * kQrNb + bb] = sp;
+  }
+  for (int e = tid; e < 4 * kQrNb * kQrNb; e += kQcThreads) (&s_T[0][0])[e] = zero;
+  __syncthreads();
+  // T (upper triangular): T[b][b] = tau_b, T[0:b, b] = -tau_b T[0:b, 0:b] S[0:b, b]
+  if (warp < npan) {
+    const int p = warp, p0 = p * kQrNb, nb = min(kQrNb, K - p0);
+    for (int b = 0; b < nb; ++b) {
+      const dd tb = s_tau[p0 + b];
+      dd t = zero;
+      if (lane < b)
+        for (int c2 = lane; c2 < b; ++c2) t = dd_add(t, dd_mul(s_T[p][lane * kQrNb + c2], s_S[p][c2 * kQrNb + b]));
+      __syncwarp();
+      if (lane < b) s_T[p][lane * kQrNb + b] = dd_neg(dd_mul(tb, t));
+      if (lane == b) s_T[p][b * kQrNb + b] = tb;
+      __syncwarp();
+    }
+    for (int e = lane; e < kQrNb * kQrNb; e += 32) Tg[(size_t)p * kQrNb * kQrNb + e] = s_T[p][e];
+  }
+}
+
 // Q = H_0 H_1 ... H_{K-1} [I_K; 0] from the panels' WY blocks, one CTA per
 // column c (threads over rows): q = e_c, then q <- q - V_p (T_p (V_p^T q)) for
 // the panels p from the one holding c down to the first (later panels leave
@@ -525,30 +670,38 @@ int subspace_solve(const double* G, int n, int K, int T, double budget, int extr
   static bool attr = false;
   if (!attr) {
     ATC_CUDA_TRY(cudaFuncSetAttribute(sub_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    ATC_CUDA_TRY(cudaFuncSetAttribute(qr_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(dd) * 32 * 32 * kQcRpl)));
     attr = true;
   }
-  sub_diag_kernel<<<1, 32, 0, s>>>(G, n, tr, gex);
+  // column-owner QR for n <= 256 (K <= 32 warps), the blocked one-CTA QR above
+  const bool qr_col = n <= 32 * kQcRpl && K <= 32;
+  { KTimed kt_(s, "sub_diag_kernel"); sub_diag_kernel<<<1, 32, 0, s>>>(G, n, tr, gex); }
   ATC_LAUNCHED(1);
   const dim3 ggrid((n + 31) / 32, (K + 7) / 8, kSubSplit);
   const int sblocks = (int)((nk + 255) / 256 < 1024 ? (nk + 255) / 256 : 1024);
   for (int t = 0; t < T; ++t) {
-    sub_gemm_part_kernel<<<ggrid, 256, 0, s>>>(G, n, t == 0 ? V0 : V, K, part);
-    sub_gemm_sum_kernel<<<sblocks, 256, 0, s>>>(part, n, K, nullptr, Wd, gex);
+    { KTimed kt_(s, "sub_gemm_part_kernel", (double)n * n * 8.0 + 2.0 * (double)nk * 8.0, 2.0 * (double)n * n * K); sub_gemm_part_kernel<<<ggrid, 256, 0, s>>>(G, n, t == 0 ? V0 : V, K, part); }
+    { KTimed kt_(s, "sub_gemm_sum_kernel"); sub_gemm_sum_kernel<<<sblocks, 256, 0, s>>>(part, n, K, nullptr, Wd, gex); }
     ATC_LAUNCHED(2);
-    sub_qr_kernel<<<1, kQrThreads, sizeof(dd) * nk, s>>>(Wd, n, K, Vg, Tg);
+    {
+      KTimed kt_(s, qr_col ? "qr_col_kernel" : "sub_qr_kernel", 2.0 * (double)nk * 8.0, 2.0 * (double)n * K * K - 2.0 / 3.0 * (double)K * K * K);
+      if (qr_col) qr_col_kernel<<<1, kQcThreads, sizeof(dd) * nk, s>>>(Wd, n, K, Vg, Tg);
+      else sub_qr_kernel<<<1, kQrThreads, sizeof(dd) * nk, s>>>(Wd, n, K, Vg, Tg);
+    }
     ATC_LAUNCHED(1);
-    sub_qform_kernel<<<K, kQfThreads, 0, s>>>(Vg, Tg, n, K, V);
+    { KTimed kt_(s, "sub_qform_kernel", 2.0 * (double)nk * 8.0, 2.0 * (double)n * K * K); sub_qform_kernel<<<K, kQfThreads, 0, s>>>(Vg, Tg, n, K, V); }
     ATC_LAUNCHED(1);
   }
-  sub_gemm_part_kernel<<<ggrid, 256, 0, s>>>(G, n, V, K, part);
-  sub_gemm_sum_kernel<<<sblocks, 256, 0, s>>>(part, n, K, W, nullptr, gex);
+  { KTimed kt_(s, "sub_gemm_part_kernel", (double)n * n * 8.0 + 2.0 * (double)nk * 8.0, 2.0 * (double)n * n * K); sub_gemm_part_kernel<<<ggrid, 256, 0, s>>>(G, n, V, K, part); }
+  { KTimed kt_(s, "sub_gemm_sum_kernel"); sub_gemm_sum_kernel<<<sblocks, 256, 0, s>>>(part, n, K, W, nullptr, gex); }
   ATC_LAUNCHED(2);
-  sub_proj_kernel<<<(K * K * 32 + 255) / 256, 256, 0, s>>>(V, W, n, K, B);
+  { KTimed kt_(s, "sub_proj_kernel"); sub_proj_kernel<<<(K * K * 32 + 255) / 256, 256, 0, s>>>(V, W, n, K, B); }
   ATC_LAUNCHED(1);
   // Rayleigh-Ritz on the K x K matrix B (one CTA), provisional rank and vector count on the device
   ATC_TRY(launch_rr_small(B, K, n, tr, budget, extra, nmax, conv, T, tc_err, th, dec, Y, s));
   const int rblocks = (int)(((size_t)n * nmax + 255) / 256 < 1024 ? ((size_t)n * nmax + 255) / 256 : 1024);
-  sub_rotate_kernel<<<rblocks, 256, 0, s>>>(V, n, K, Y, dec + 1, U_dev);
+  { KTimed kt_(s, "sub_rotate_kernel"); sub_rotate_kernel<<<rblocks, 256, 0, s>>>(V, n, K, Y, dec + 1, U_dev); }
   ATC_LAUNCHED(1);
   ATC_CUDA_TRY(cudaMemcpyAsync(decision_host, dec, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
   return ATC_OK;

@@ -551,6 +551,16 @@ int ttm_launch_t(const TtmArgs& a, int grid, int smem, cudaStream_t s) {
                                       225 * 1024));
     attr = true;
   }
+  // algorithmic work: the data tensor read once, the output (or, with the
+  // fused residual, the compared tensor) once, the factor once; 2 Atot Bdim per
+  // output column; issued: nine slice products over the padded tiles
+  const double cols = (double)a.L * (double)a.R;
+  const double bytes = cols * (double)a.Bdim * sizeof(TX) + cols * (double)a.Atot * (RES ? sizeof(TR) : 4.0) +
+                       (double)a.Atot * (double)a.Bdim * 8.0;
+  const double flops = 2.0 * cols * (double)a.Atot * (double)a.Bdim;
+  const double issued = 9.0 * 2.0 * (double)a.mtiles * 128.0 * (double)a.apad * (double)a.nchunk_launch *
+                        (double)a.nkt * KT;
+  KTimed kt_(s, RES ? "ttm_tc_kernel(fused residual)" : "ttm_tc_kernel", bytes, flops, issued);
   ttm_tc_kernel<TX, BF16, GEN, RES, TR><<<dim3(grid, a.nchunk_launch), kThreads, smem, s>>>(a);
   ATC_LAUNCHED(1);
   return ATC_OK;

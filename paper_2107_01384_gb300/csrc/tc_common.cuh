@@ -165,6 +165,19 @@ __device__ __forceinline__ void slice3i(float v, float& a0, float& a1, float& a2
   a2 = rintf((t - a1) * 256.0f);
 }
 
+// Four slices (32-bit fixed point): v ~ a0 + a1 2^-8 + a2 2^-16 + a3 2^-24,
+// |a0| <= 256, |a1|, |a2|, |a3| <= 128, |v - ...| <= 2^-25.  The products of
+// order s + t >= 5 (scale <= 2^-40) are left out by the Gram kernels: they are
+// below the rounding of v itself.
+__device__ __forceinline__ void slice4i(float v, float& a0, float& a1, float& a2, float& a3) {
+  a0 = rintf(v);
+  const float t = (v - a0) * 256.0f;  // exact
+  a1 = rintf(t);
+  const float t2 = (t - a1) * 256.0f;  // exact
+  a2 = rintf(t2);
+  a3 = rintf((t2 - a2) * 256.0f);
+}
+
 // acc0 + 2^-8 acc1 + 2^-16 acc2 + 2^-24 acc3 + 2^-32 acc4 as an unevaluated
 // sum s + t (s carries the leading 24 bits; the exact orders 0 and 1 enter
 // through an error-free two-sum, the rest with round-to-nearest)

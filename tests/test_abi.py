@@ -80,10 +80,13 @@ def test_stream_header_checks_on_host(lib):
     dims = (C.c_int64 * 8)()
     assert lib.atc_peek_dims(b"XXXX" + b"\0" * 60, 64, C.byref(nd), dims, C.byref(dt)) == -4
     import struct
-    hdr = b"ATC1" + struct.pack("<III", 1, 3, 1) + struct.pack("<3Q", 5, 6, 7)
+    hdr = b"ATC1" + struct.pack("<III", 2, 3, 1) + struct.pack("<3Q", 5, 6, 7)
     assert lib.atc_peek_dims(hdr + b"\0" * 64, len(hdr) + 64, C.byref(nd), dims, C.byref(dt)) == 0
     assert nd.value == 3 and list(dims)[:3] == [5, 6, 7] and dt.value == 1
     assert lib.atc_peek_dims(hdr[:20], 20, C.byref(nd), dims, C.byref(dt)) == -4
+    # the version-1 layout (all factor columns, no column maps) is not read
+    old = b"ATC1" + struct.pack("<III", 1, 3, 1) + struct.pack("<3Q", 5, 6, 7)
+    assert lib.atc_peek_dims(old + b"\0" * 64, len(old) + 64, C.byref(nd), dims, C.byref(dt)) == -4
 
 
 def test_batch_create_rejects_bad_arguments_on_the_host(lib):

@@ -207,6 +207,9 @@ def _check_pipeline(P, x, eps, rtmss=0.5, mode_order=None, rank_rule=0):
         assert hg[key] == hr[key], (key, hg[key], hr[key])
     qg, qr = OQ.peek(hg["core_stream"]), OQ.peek(hr["core_stream"])
     assert qg == qr, (qg, qr)
+    # the same factor columns are dropped (core slices without a significant coefficient)
+    for kg, kr in zip(hg["kept"], hr["kept"]):
+        assert np.array_equal(kg, kr)
     # bit-exact quantizer on the GPU's own core
     core = c.core().cpu().numpy()
     perm = O.storage_order(c.ranks())
@@ -269,6 +272,9 @@ def test_pipeline_hyperspectral_split(P, cube, prec):
     xh = P.atc_decompress(c.stream_bytes(), out_dtype=torch.float32, precision=prec).cpu().numpy()
     re = np.linalg.norm(cube.astype(np.float64) - xh) / np.linalg.norm(cube.astype(np.float64))
     assert 0.98e-2 <= re <= 1e-2, re
+    # the cuts lie in the noise floor (dense spectrum): the subspace-shift estimate
+    # recomputes at least the last mode's Gram matrix with four slices
+    assert c.stats()["escalated_modes"] >= 1
     from test_gpu_split_parity import _check_split_against_oracle
     _check_split_against_oracle(P, c, cube, 1e-2, ref)
 
@@ -292,3 +298,16 @@ def test_pipeline_automatic_block_size(P, prec):
     xo = OP.decompress(stream)
     xh = P.atc_decompress(stream).cpu().numpy()
     assert np.linalg.norm(xo - xh) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_pipeline_drops_columns_of_zero_slices(P):
+    """Full ranks (RTMSS = 0: the whole budget goes to the quantizer) leave core
+    slices that hold only rounding-level coefficients; after bit-plane
+    truncation they are zero, and their factor columns are not stored (Section
+    3.3).  The GPU stream drops the same columns as the oracle's, the oracle
+    decodes it, and the stream is shorter than with every column stored."""
+    x = synth.lowrank_tucker((12, 10, 9), (6, 5, 4), noise=None, seed=9)
+    c, st = _check_pipeline(P, x, 1e-2, rtmss=0.0)
+    h = OP.parse(c.stream_bytes())
+    dropped = sum(int((~k).sum()) for k in h["kept"])
+    assert dropped >= 3, [k.astype(int).tolist() for k in h["kept"]]

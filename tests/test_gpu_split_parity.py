@@ -187,6 +187,8 @@ def test_pipeline_split_bumps256(P, prec, eps):
     # certified either way)
     if eps == 1e-3:
         assert c.stats()["subspace_modes"] == 3
+    # a smooth field's cut sits in a fast-falling spectrum: no mode needs four slices
+    assert c.stats()["escalated_modes"] == 0
     for m in range(x.ndim):
         u = c.factor(m).cpu().numpy()
         assert np.abs(u.T @ u - np.eye(u.shape[1])).max() <= 1e-12
@@ -225,6 +227,13 @@ def _check_split_against_oracle(P, c, x, eps, ref):
     qg, qr = OQ.peek(hg["core_stream"]), OQ.peek(hr["core_stream"])
     for key in ("n", "k", "block_size"):
         assert qg[key] == qr[key], (key, qg, qr)
+    # dropped factor columns: exactly the slices without a significant coefficient
+    # in the GPU's own quantized core (the quantizer is bit-exact on it)
+    vec = OP.vectorize_core(core, hg["perm"])
+    q, _ = OQ.quantize(vec, qg["k"])
+    kept = OP.kept_columns(OP.significant(q, qg["p_star"], qg["i_star"]), hg["ranks"], hg["perm"])
+    for kg, ke in zip(hg["kept"], kept):
+        assert np.array_equal(kg, ke)
     xh = P.atc_decompress(stream).cpu().numpy()
     xo = OP.decompress(stream)
     assert np.linalg.norm(xo - xh) <= 1e-9 * nx
@@ -301,3 +310,44 @@ def test_split_full_eigensolver_switch(P, monkeypatch):
     monkeypatch.setenv("ATC_SUBSPACE", "1")
     c2 = P.atc_compress(cuda(x), 1e-3, precision=1)
     assert c2.ranks() == ref["ranks"]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("dims,mode", [((6, 200, 70), 1), ((300, 96), 0), ((50, 224), 1)])
+def test_gram_wide_32bit(P, dims, mode, prec, dtype):
+    """ATC_PREC_WIDE: four 8-bit slices per value (32-bit fixed point below
+    max |x|).  On data that 32-bit fixed point holds exactly -- 31-bit integer
+    mantissas in FP64, or FP32 values whose magnitudes spread over 2^8 (as in a
+    projected tensor) -- the Gram matrix matches the FP64 one to the
+    double-float running sums and the dropped products of order >= 5 (~2^-39
+    relative), where three slices round the data to 24 bits below max |x|; R = 1
+    (the last mode) takes the transposing slicer."""
+    rng = np.random.default_rng(51)
+    if dtype == np.float64:
+        x = rng.integers(-(2 ** 31) + 1, 2 ** 31, size=dims) * 2.0 ** -28
+    else:
+        e = rng.integers(0, 9, size=dims)
+        x = (rng.integers(-(2 ** 23) + 1, 2 ** 23, size=dims) * 2.0 ** (-20 - e)).astype(np.float32)
+        x.flat[0] = (2 ** 23 - 1) * 2.0 ** -20
+    L = int(np.prod(dims[:mode])); n = dims[mode]; R = int(np.prod(dims[mode + 1:]))
+    ref = O.mode_gram(x.astype(np.float64), mode)
+    gw = P.atc_gram(cuda(x), L, n, R, prec | P.PREC_WIDE).cpu().numpy()
+    g3 = P.atc_gram(cuda(x), L, n, R, prec).cpu().numpy()
+    scale = np.abs(ref).max()
+    err_w = np.abs(gw - ref).max() / scale
+    err_3 = np.abs(g3 - ref).max() / scale
+    assert err_w <= 1e-11, err_w
+    assert err_w <= 1e-3 * err_3, (err_w, err_3)
+    assert np.array_equal(gw, gw.T)
+
+
+def test_pipeline_split_wide_bumps(P):
+    """A whole split compression with four-slice Grams in every mode (ranks,
+    error bound and the oracle comparisons as for three slices)."""
+    x = synth.gaussian_bumps(n=128, nbumps=16, seed=31)
+    ref = O.sthosvd(x, 1e-3)
+    c = P.atc_compress(cuda(x), 1e-3, precision=P.PREC_SPLIT_BF16 | P.PREC_WIDE)
+    assert c.ranks() == ref["ranks"]
+    assert c.stats()["escalated_modes"] == 0
+    _check_split_against_oracle(P, c, x, 1e-3, ref)
