@@ -61,7 +61,8 @@ __device__ __forceinline__ int jac_partner(int i, int r) {
 struct JacShared {
   float A[2][kJ][kJP];
   float Y[2][kJ][kJP];
-  float c[kJ], sg[kJ], t[kJ];  // per index: cos, signed coefficient of the partner, tan (0: no rotation)
+  float2 cs[kJ];               // per index: (cos, signed coefficient of the partner)
+  float t[kJ];                 // per index: signed tan (0: no rotation)
   dd Yd[kJ][kJ];               // refined vectors (column j = Ritz vector j, sorted)
   dd Md[kJ][kJ];               // Y^T Y, then B Y
   dd Bd[kJ][kJ];               // B scaled, double-float
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(kJThreads, 1)
   // need c^2 + s^2 = 1 to FP32 level, the vectors are re-orthonormalised below),
   // then every thread updates its entry of A and of Y.
   int buf = 0;
+  // this thread's column partner per round moves by a fixed rule: j' = 2r - j (mod 31) for j < 31
   for (int sweep = 0; sweep < kJSweeps; ++sweep) {
     if (tid == 0) S.rot[sweep & 1] = 0;
     __syncthreads();
@@ -133,28 +135,28 @@ __global__ void __launch_bounds__(kJThreads, 1)
           ss = tt * c;
           S.rot[sweep & 1] = 1;
         }
-        S.c[lo] = c;
-        S.c[hi] = c;
-        S.sg[lo] = -ss;
-        S.sg[hi] = ss;
-        S.t[lo] = tt;
+        // per index: (c, signed coefficient of the partner); t signed so that the
+        // diagonal update is a_ii + t_i a_{lo,hi} for both members of the pair
+        S.cs[lo] = make_float2(c, -ss);
+        S.cs[hi] = make_float2(c, ss);
+        S.t[lo] = -tt;
         S.t[hi] = tt;
       }
       __syncthreads();
       const int pi = jac_partner(i, r), pj = jac_partner(j, r);
-      const float ci = S.c[i], si = S.sg[i], cj = S.c[j], sj = S.sg[j], ti = S.t[i];
-      const float aij = S.A[buf][i][j], aipj = S.A[buf][i][pj], apij = S.A[buf][pi][j], apipj = S.A[buf][pi][pj];
-      float anew;
-      if (i == j && ti != 0.f) {
-        // a_pp - t a_pq, a_qq + t a_pq (p < q): the accurate diagonal update
-        anew = (i < pi) ? fmaf(-ti, aipj, aij) : fmaf(ti, apij, aij);
-      } else if (j == pi && ti != 0.f) {
-        anew = 0.f;
-      } else {
-        anew = ci * (cj * aij + sj * aipj) + si * (cj * apij + sj * apipj);
-      }
+      const float2 csi = S.cs[i], csj = S.cs[j];
+      const float ti = S.t[i];
+      const float(*Ab)[kJP] = S.A[buf];
+      const float aij = Ab[i][j], aipj = Ab[i][pj], apij = Ab[pi][j], apipj = Ab[pi][pj];
+      // general entry of J^T A J; the two entries of a rotated pair's 2 x 2 block
+      // on the diagonal take the accurate update a_ii + t_i a_lo,hi, the
+      // off-diagonal pair entries become 0 (branch-free selects)
+      const float gen = csi.x * (csj.x * aij + csj.y * aipj) + csi.y * (csj.x * apij + csj.y * apipj);
+      const float apq = (i < pi) ? aipj : apij;  // a_{lo,hi} of i's pair, used when i == j
+      float anew = (i == j) ? fmaf(ti, apq, aij) : gen;
+      anew = (j == pi && ti != 0.f) ? 0.f : anew;
       S.A[buf ^ 1][i][j] = anew;
-      S.Y[buf ^ 1][i][j] = fmaf(cj, S.Y[buf][i][j], sj * S.Y[buf][i][pj]);
+      S.Y[buf ^ 1][i][j] = fmaf(csj.x, S.Y[buf][i][j], csj.y * S.Y[buf][i][pj]);
       buf ^= 1;
       __syncthreads();
     }
