@@ -110,8 +110,10 @@ typedef struct {
   int order[8];           /* processing order used */
   int storage_order[8];   /* core mode storage order before vectorisation (supplement S.2) */
   int k;                  /* quantization scale exponent: 2^63 <= 2^k max|b| < 2^64 */
-  int p_star;             /* breakpoint plane (64 = nothing encoded) */
-  int64_t i_star;         /* breakpoint coefficient: 0..i_star carry planes >= p_star, the rest >= p_star+1 */
+  int p_star;             /* last encoded plane (64 = nothing encoded) */
+  int64_t i_lead;         /* plane p_star: leading bits (not yet significant) encoded for 0..i_lead (-1: none) */
+  int64_t i_trail;        /* plane p_star: trailing bits (significant above) encoded for 0..i_trail (-1: none) */
+  int prio;               /* split truncation (supplement S.3): 0 leading bits first, 1 trailing first */
   int escalated_modes;    /* split paths: modes whose Gram was recomputed with four slices (ATC_PREC_WIDE) */
   double ms_norm, ms_gram, ms_eig, ms_ttm, ms_quant, ms_encode, ms_total; /* device time per phase (CUDA events) */
   int subspace_modes;     /* split paths: modes whose eigenvectors came from subspace iteration + Rayleigh-Ritz */
@@ -295,12 +297,17 @@ int atc_ttm(const void* x_dev, int xdtype, int64_t L, int64_t n, int64_t R, cons
             int expand, int precision, void* y_dev, int ydtype, void* stream);
 
 /*
- * Quantize and encode a vectorised FP64 core (Sections 3.3, 4.2, 4.3, S.6).
+ * Quantize and encode a vectorised FP64 core (Sections 3.3, 4.2, 4.3, S.6),
+ * with split bit-plane truncation of the last plane (supplement S.3): the
+ * breakpoint plane p_star comes from the walk in coefficient order; on it the
+ * category (leading or trailing bits) with the higher efficiency on plane
+ * p_star + 1 is walked first, then the other, up to the first bit whose
+ * tracked error meets the target.
  *   core_dev   : n doubles (device), already in storage order.
  *   target_sse : quantization error budget in core units (may be <= 0: encode all).
  *   *bytes     : receives a library-allocated HOST buffer (free with
  *                atc_free_buffer) holding the "ATCQ" section, *nbytes its size.
- *   info       : optional host int64[4] <- {k, p_star, i_star, 0}.
+ *   info       : optional host int64[5] <- {k, p_star, prio, i_lead, i_trail}.
  * The bytes are identical to the plain C reference for the same core and target.
  */
 int atc_quantize_core(const double* core_dev, int64_t n, double target_sse, int block_size, void* stream,

@@ -12,8 +12,9 @@ path).
   4. Core slices left without a significant coefficient (Section 3.3, the
      paragraph after Table 2): after bit-plane truncation such a slice is all
      zero in the decoded core, so the matching factor column is not stored.
-     A coefficient is significant when one of its encoded bits is a 1: planes
-     >= p_star for vectorised positions <= i_star, >= p_star + 1 after it.
+     A coefficient is significant when one of its encoded bits is a 1: a 1
+     above the last plane p_star, or its leading 1 on p_star where that
+     plane's leading bits are encoded (positions <= i_lead).
 
 Full stream layout ("ATC1", little-endian):
   char[4] "ATC1" | u32 version=2 | u32 ndim | u32 dtype (1 f32, 2 f64) |
@@ -48,21 +49,20 @@ def devectorize_core(vec, ranks, perm):
     return np.ascontiguousarray(np.transpose(t, inv))
 
 
-def significant(q, p_star, i_star):
+def significant(q, p_star, i_lead):
     """Significance of each vectorised coefficient after bit-plane truncation
-    (Section 3.3): one of its encoded bits is a 1, the encoded planes being
-    >= p_star up to position i_star and >= p_star + 1 after it."""
+    (Section 3.3): one of its encoded bits is a 1 -- a 1 above plane p_star, or
+    its leading 1 on plane p_star where the leading bits are encoded (positions
+    <= i_lead; Supplement S.3 splits the last plane's breakpoint by category)."""
     q = np.asarray(q, dtype=np.uint64)
     n = q.size
     sig = np.zeros(n, dtype=bool)
     if p_star >= 64:
         return sig
+    if p_star < 63:
+        sig |= (q >> np.uint64(p_star + 1)) != 0
     j = np.arange(n)
-    lo = np.where(j <= i_star, p_star, p_star + 1)
-    for p in (p_star, p_star + 1):
-        m = lo == p
-        if p < 64:
-            sig[m] = (q[m] >> np.uint64(p)) != 0
+    sig |= ((q >> np.uint64(p_star)) != 0) & (j <= i_lead)
     return sig
 
 
@@ -92,7 +92,7 @@ def compress(x, rel_eps, rtmss=0.5, mode_order=None, block_size=4096, rank_rule=
     target_q = res["target_sse"] - res["sse_trunc"]
     core_stream, qinfo = quant.compress_core(vec, target_q, block_size)
     q, _ = quant.quantize(vec, qinfo["k"])
-    kept = kept_columns(significant(q, qinfo["p_star"], qinfo["i_star"]), ranks, perm)
+    kept = kept_columns(significant(q, qinfo["p_star"], qinfo["i_lead"]), ranks, perm)
     d = x.ndim
     hdr = b"ATC1" + struct.pack("<III", 2, d, DTYPE_CODE[np.dtype(x.dtype)])
     hdr += struct.pack(f"<{d}Q", *x.shape) + struct.pack(f"<{d}Q", *ranks) + struct.pack(f"<{d}I", *perm)

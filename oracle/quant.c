@@ -23,9 +23,19 @@
  * breakpoint does not depend on summation order (this replaces the floating
  * point tracking and recalibration of supplement S.4).
  *
+ *  - Supplement S.3 (split bit plane truncation): on the last plane p_star
+ *    the leading bits (of coefficients not yet significant) and the trailing
+ *    bits (of significant ones) get separate breakpoints i_lead and i_trail.
+ *    The category that was encoded more efficiently on plane p_star + 1 (exact
+ *    SSE reduction per encoded bit: rANS bytes x 8 + sign bits for the leading
+ *    bits, one raw bit per trailing bit) goes first: the plane is walked as its
+ *    first category's bits in coefficient order, then the other's, and the
+ *    first position whose tracked error reaches the target splits it.
+ *
  * Stream layout of one encoded core ("ATCQ" section, little-endian):
- *   char[4] "ATCQ" | u32 version=1 | u64 n | i32 k | u32 block_size |
- *   i32 p_star | u32 0 | u64 i_star | u32 nplanes | u32 nsym=17 |
+ *   char[4] "ATCQ" | u32 version=2 | u64 n | i32 k | u32 block_size |
+ *   i32 p_star | u32 priority (0 leading first, 1 trailing first) |
+ *   u64 i_lead | u64 i_trail | u32 nplanes | u32 nsym=17 |
  *   u16 freq[nplanes][17] | u32 sizes[nblocks][nplanes][2] | payload
  * Planes are listed from 63 down to p_star.  Payload: for each block, for each
  * plane, the rANS bytes then the raw-bit bytes of that (block, plane) chunk.
@@ -56,7 +66,7 @@ static u192 u192_add(u192 a, u192 b) {
   r.w[2] = a.w[2] + b.w[2] + (uint64_t)(s >> 64);
   return r;
 }
-static u192 u192_sub(u192 a, u192 b) { /* requires a >= b */
+static u192 u192_sub(u192 a, u192 b) { /* a - b mod 2^192 (the borrow propagates) */
   u192 r; uint64_t br = 0;
   for (int i = 0; i < 3; ++i) {
     uint64_t t = a.w[i] - b.w[i];
@@ -179,13 +189,17 @@ static int run_bucket(uint32_t v) { /* floor(log2(v + 1)) */
  * raw bit and, if cat != NULL, records the category of each visited bit. */
 typedef struct { uint32_t* runs; int64_t nruns; int64_t cap; } runlist;
 
-static int chunk_walk(const uint64_t* q, const uint8_t* s, int64_t lo, int64_t hi, int p,
+/* hl / ht: end (exclusive) of the coefficients whose leading / trailing bit of
+ * plane p is encoded (both the block end except on the last plane). */
+static int chunk_walk(const uint64_t* q, const uint8_t* s, int64_t lo, int64_t hl, int64_t ht, int p,
                       runlist* rl, bitbuf* raw, char* cat) {
   uint32_t run = 0;
   rl->nruns = 0;
+  int64_t hi = hl > ht ? hl : ht;
   for (int64_t j = lo; j < hi; ++j) {
     int bit = (int)((q[j] >> p) & 1u);
     int sig_before = (p == 63) ? 0 : ((q[j] >> (p + 1)) != 0);
+    if (sig_before ? (j >= ht) : (j >= hl)) continue;   /* this category stops earlier here */
     if (sig_before) {                       /* trailing bit, raw */
       if (raw && bb_put(raw, bit)) return -1;
       if (cat) cat[j * 64 + (63 - p)] = 'T';
@@ -252,18 +266,102 @@ static void put_u64(uint8_t* p, uint64_t v) { for (int i = 0; i < 8; ++i) p[i] =
 static uint32_t get_u32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i); return v; }
 static uint64_t get_u64(const uint8_t* p) { uint64_t v = 0; for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i); return v; }
 
-#define ORC_HDR 48
+#define ORC_HDR 56
 
 static int64_t chunk_hi(int64_t lo, int64_t hi, int p, int p_star, int64_t i_star) {
   if (p == p_star && hi > i_star + 1) hi = i_star + 1;
   return hi < lo ? lo : hi;
 }
 
+/* rANS bytes of the runs of one full plane p over every block (its own
+ * normalised table): the leading-bit encoding cost of that plane. */
+int64_t orc_plane_rans_bytes(const uint64_t* q, const uint8_t* s, int64_t n, int block_size, int p) {
+  if (block_size < 32 || n < 0 || p < 0 || p > 63) return -1;
+  int64_t nblocks = (n + block_size - 1) / block_size;
+  uint64_t hist[ORC_NSYM] = {0};
+  runlist rl; rl.cap = block_size + 1; rl.runs = malloc(sizeof(uint32_t) * (size_t)rl.cap);
+  if (!rl.runs) return -1;
+  for (int64_t b = 0; b < nblocks; ++b) {
+    int64_t lo = b * block_size, hi = lo + block_size; if (hi > n) hi = n;
+    chunk_walk(q, s, lo, hi, hi, p, &rl, NULL, NULL);
+    for (int64_t r = 0; r < rl.nruns; ++r) hist[run_bucket(rl.runs[r])]++;
+  }
+  uint16_t f[ORC_NSYM]; uint32_t cum[ORC_NSYM];
+  normalize_freq(hist, f);
+  uint32_t c = 0;
+  for (int i = 0; i < ORC_NSYM; ++i) { cum[i] = c; c += f[i]; }
+  int64_t cap = (int64_t)block_size * 8 + 64, total = 0;
+  uint8_t* buf = malloc((size_t)cap);
+  if (!buf) { free(rl.runs); return -1; }
+  for (int64_t b = 0; b < nblocks; ++b) {
+    int64_t lo = b * block_size, hi = lo + block_size; if (hi > n) hi = n;
+    chunk_walk(q, s, lo, hi, hi, p, &rl, NULL, NULL);
+    int64_t len = rans_encode(rl.runs, rl.nruns, f, cum, buf, cap);
+    if (len < 0) { total = -1; break; }
+    total += len;
+  }
+  free(buf); free(rl.runs);
+  return total;
+}
+
+/* Exact statistics of plane p as one would encode it whole: the SSE
+ * reductions of its leading bits (dl) and trailing bits (dt) as signed 192-bit
+ * two's-complement limbs, and the counts of leading ones (= signs) and of
+ * trailing bits. */
+void orc_plane_stats(const uint64_t* q, int64_t n, int p, uint64_t* dl, uint64_t* dt, int64_t* n_ones, int64_t* n_trail) {
+  u192 l = {{0, 0, 0}}, t = {{0, 0, 0}};
+  int64_t ones = 0, trail = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    if ((q[j] >> p) == 0) continue;                 /* insignificant through plane p: D = 0 */
+    u128 before = coef_err(q[j], p + 1), after = coef_err(q[j], p);
+    int sig_before = (p == 63) ? 0 : ((q[j] >> (p + 1)) != 0);
+    /* D = before - after, accumulated mod 2^192 (two's complement; u192_sub
+     * propagates the borrow, so it is exact modular subtraction) */
+    if (sig_before) { t = u192_sub(u192_add(t, u192_from128(before)), u192_from128(after)); ++trail; }
+    else { l = u192_sub(u192_add(l, u192_from128(before)), u192_from128(after)); ++ones; }
+  }
+  memcpy(dl, l.w, sizeof(l.w)); memcpy(dt, t.w, sizeof(t.w));
+  *n_ones = ones; *n_trail = trail;
+}
+
+/* The split walk of plane p (Supplement S.3): starting from the tracked error
+ * after every plane above p, the bits of category `first` (0 leading, 1
+ * trailing) in coefficient order, then those of the other category; the first
+ * position whose error is <= the target gives (i_lead, i_trail): the first
+ * category encoded up to that coefficient and the other not at all, or the
+ * first whole and the second up to it.  Returns 1 if the target is reached on
+ * the plane, 0 if not (err_out: tracked error at the split point). */
+int orc_split_walk(const uint64_t* q, int64_t n, int p, int first, double target, int k,
+                   int64_t* i_lead, int64_t* i_trail, uint64_t* err_out) {
+  u192 tint; int reachable = target_scaled(target, k, &tint);
+  u192 run = {{0, 0, 0}};
+  for (int64_t j = 0; j < n; ++j) run = u192_add(run, u192_from128(coef_err(q[j], p + 1)));
+  for (int pass = 0; pass < 2; ++pass) {
+    int cat = pass == 0 ? first : 1 - first;          /* 0 leading, 1 trailing */
+    for (int64_t j = 0; j < n; ++j) {
+      int sig_before = (p == 63) ? 0 : ((q[j] >> (p + 1)) != 0);
+      if (sig_before != cat) continue;
+      u128 before = coef_err(q[j], p + 1), after = coef_err(q[j], p);
+      run = u192_sub(u192_add(run, u192_from128(after)), u192_from128(before));
+      if (reachable && u192_le(run, tint)) {
+        int64_t* ifirst = (first == 0) ? i_lead : i_trail;
+        int64_t* isecond = (first == 0) ? i_trail : i_lead;
+        if (pass == 0) { *ifirst = j; *isecond = -1; }
+        else { *ifirst = n - 1; *isecond = j; }
+        memcpy(err_out, run.w, sizeof(run.w));
+        return 1;
+      }
+    }
+  }
+  memcpy(err_out, run.w, sizeof(run.w));
+  return 0;
+}
+
 /* Encode the quantized core (q, s) given k and the breakpoint.  Returns the
  * stream size, or -(needed) if cap is too small / -1 on bad arguments.
  * cat (optional, n*64 chars, plane 63 first) receives 'L' / 'T' per encoded bit. */
-int64_t orc_encode(const uint64_t* q, const uint8_t* s, int64_t n, int k, int p_star, int64_t i_star,
-                   int block_size, uint8_t* out, int64_t cap, char* cat) {
+int64_t orc_encode(const uint64_t* q, const uint8_t* s, int64_t n, int k, int p_star, int prio, int64_t i_lead,
+                   int64_t i_trail, int block_size, uint8_t* out, int64_t cap, char* cat) {
   if (block_size < 32 || block_size > 65535 || (block_size % 32) || n < 0) return -1;
   int nplanes = (p_star >= 64) ? 0 : 64 - p_star;
   int64_t nblocks = (n + block_size - 1) / block_size;
@@ -278,8 +376,7 @@ int64_t orc_encode(const uint64_t* q, const uint8_t* s, int64_t n, int k, int p_
     int p = 63 - pi;
     for (int64_t b = 0; b < nblocks; ++b) {
       int64_t lo = b * block_size, hi = lo + block_size; if (hi > n) hi = n;
-      hi = chunk_hi(lo, hi, p, p_star, i_star);
-      chunk_walk(q, s, lo, hi, p, &rl, NULL, cat);
+      chunk_walk(q, s, lo, chunk_hi(lo, hi, p, p_star, i_lead), chunk_hi(lo, hi, p, p_star, i_trail), p, &rl, NULL, cat);
       for (int64_t r = 0; r < rl.nruns; ++r) hist[pi * ORC_NSYM + run_bucket(rl.runs[r])]++;
     }
   }
@@ -300,9 +397,9 @@ int64_t orc_encode(const uint64_t* q, const uint8_t* s, int64_t n, int k, int p_
     for (int pi = 0; pi < nplanes; ++pi) {
       int p = 63 - pi;
       int64_t lo = b * block_size, hi = lo + block_size; if (hi > n) hi = n;
-      hi = chunk_hi(lo, hi, p, p_star, i_star);
       bitbuf raw = {wbuf, 0, scratch_cap};
-      if (chunk_walk(q, s, lo, hi, p, &rl, &raw, NULL)) { ok = 0; break; }
+      if (chunk_walk(q, s, lo, chunk_hi(lo, hi, p, p_star, i_lead), chunk_hi(lo, hi, p, p_star, i_trail), p, &rl, &raw,
+                     NULL)) { ok = 0; break; }
       int64_t rlen = rans_encode(rl.runs, rl.nruns, freq + pi * ORC_NSYM, cum + pi * ORC_NSYM, rbuf, scratch_cap);
       if (rlen < 0) { ok = 0; break; }
       int64_t wlen = (raw.nbits + 7) >> 3;
@@ -319,15 +416,16 @@ int64_t orc_encode(const uint64_t* q, const uint8_t* s, int64_t n, int k, int p_
   if (!ok) { free(freq); free(cum); return -1; }
   if (pos > cap) { free(freq); free(cum); return -pos; }
   memcpy(out, "ATCQ", 4);
-  put_u32(out + 4, 1);
+  put_u32(out + 4, 2);
   put_u64(out + 8, (uint64_t)n);
   put_u32(out + 16, (uint32_t)k);
   put_u32(out + 20, (uint32_t)block_size);
   put_u32(out + 24, (uint32_t)p_star);
-  put_u32(out + 28, 0);
-  put_u64(out + 32, (uint64_t)i_star);
-  put_u32(out + 40, (uint32_t)nplanes);
-  put_u32(out + 44, ORC_NSYM);
+  put_u32(out + 28, (uint32_t)prio);
+  put_u64(out + 32, (uint64_t)i_lead);
+  put_u64(out + 40, (uint64_t)i_trail);
+  put_u32(out + 48, (uint32_t)nplanes);
+  put_u32(out + 52, ORC_NSYM);
   for (int i = 0; i < nplanes * ORC_NSYM; ++i) { out[ORC_HDR + 2 * i] = (uint8_t)freq[i]; out[ORC_HDR + 2 * i + 1] = (uint8_t)(freq[i] >> 8); }
   free(freq); free(cum);
   return pos;
@@ -353,21 +451,23 @@ static int rd_run(rdec* d, const uint16_t* f, const uint32_t* cum, uint32_t* v) 
 }
 
 /* Parse an ATCQ section; returns 0 and fills the header fields. */
-int orc_peek(const uint8_t* in, int64_t nbytes, int64_t* n, int* k, int* block_size, int* p_star, int64_t* i_star) {
-  if (nbytes < ORC_HDR || memcmp(in, "ATCQ", 4) || get_u32(in + 4) != 1) return -1;
+int orc_peek(const uint8_t* in, int64_t nbytes, int64_t* n, int* k, int* block_size, int* p_star, int* prio,
+             int64_t* i_lead, int64_t* i_trail) {
+  if (nbytes < ORC_HDR || memcmp(in, "ATCQ", 4) || get_u32(in + 4) != 2) return -1;
   *n = (int64_t)get_u64(in + 8); *k = (int)get_u32(in + 16); *block_size = (int)get_u32(in + 20);
-  *p_star = (int)get_u32(in + 24); *i_star = (int64_t)get_u64(in + 32);
+  *p_star = (int)get_u32(in + 24); *prio = (int)get_u32(in + 28);
+  *i_lead = (int64_t)get_u64(in + 32); *i_trail = (int64_t)get_u64(in + 40);
   return 0;
 }
 
 /* Decode to the integer magnitudes q~ (bits of the encoded planes only), the
  * signs and the dequantized doubles (Section 4.3 reconstruction). */
 int orc_decode(const uint8_t* in, int64_t nbytes, uint64_t* qt, uint8_t* sg, double* b_out, int64_t n_expect) {
-  int64_t n; int k, bs, p_star; int64_t i_star;
-  if (orc_peek(in, nbytes, &n, &k, &bs, &p_star, &i_star)) return -1;
+  int64_t n; int k, bs, p_star, prio; int64_t i_lead, i_trail;
+  if (orc_peek(in, nbytes, &n, &k, &bs, &p_star, &prio, &i_lead, &i_trail)) return -1;
   if (n != n_expect || bs < 32 || bs > 65535) return -2;
-  int nplanes = (int)get_u32(in + 40);
-  if (get_u32(in + 44) != ORC_NSYM || nplanes != ((p_star >= 64) ? 0 : 64 - p_star) || nplanes < 0) return -3;
+  int nplanes = (int)get_u32(in + 48);
+  if (get_u32(in + 52) != ORC_NSYM || nplanes != ((p_star >= 64) ? 0 : 64 - p_star) || nplanes < 0) return -3;
   int64_t nblocks = (n + bs - 1) / bs;
   int64_t tab = ORC_HDR + (int64_t)nplanes * ORC_NSYM * 2;
   int64_t pos = tab + nblocks * nplanes * 8;
@@ -391,9 +491,11 @@ int orc_decode(const uint8_t* in, int64_t nbytes, uint64_t* qt, uint8_t* sg, dou
       if (rl) { if (rl < 4) return -7; d.x = get_u32(d.p); d.p += 4; }
       const uint8_t* raw = in + pos + rl; int64_t rbit = 0, rcap = (int64_t)wl * 8;
       int64_t lo = b * bs, hi = lo + bs; if (hi > n) hi = n;
-      hi = chunk_hi(lo, hi, p, p_star, i_star);
+      const int64_t hl = chunk_hi(lo, hi, p, p_star, i_lead), ht = chunk_hi(lo, hi, p, p_star, i_trail);
+      hi = hl > ht ? hl : ht;
       int need = 1; uint32_t left = 0;
       for (int64_t j = lo; j < hi; ++j) {
+        if (qt[j] != 0 ? (j >= ht) : (j >= hl)) continue;
         if (qt[j] != 0) {
           if (rbit >= rcap) return -8;
           uint64_t bit = (raw[rbit >> 3] >> (rbit & 7)) & 1u; rbit++;
@@ -414,7 +516,11 @@ int orc_decode(const uint8_t* in, int64_t nbytes, uint64_t* qt, uint8_t* sg, dou
   }
   for (int64_t j = 0; j < n; ++j) {
     if (qt[j] == 0) { b_out[j] = 0.0; continue; }
-    int pj = (j <= i_star) ? p_star : p_star + 1;
+    /* lowest encoded plane: p_star for a coefficient that became significant
+     * on p_star (its leading 1 is there) or whose trailing bit of p_star is
+     * encoded (j <= i_trail); p_star + 1 otherwise */
+    int sig_above = (p_star >= 63) ? 0 : ((qt[j] >> (p_star + 1)) != 0);
+    int pj = (!sig_above || j <= i_trail) ? p_star : p_star + 1;
     uint64_t v = qt[j] + ((pj >= 1) ? (1ull << (pj - 1)) : 0);
     double a = ldexp((double)v, -k);
     b_out[j] = sg[j] ? -a : a;

@@ -59,7 +59,8 @@ class Options(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("norm2", C.c_double), ("target_sse", C.c_double), ("sse_trunc", C.c_double),
                 ("sse_quant_pred", C.c_double), ("order", C.c_int * 8), ("storage_order", C.c_int * 8),
-                ("k", C.c_int), ("p_star", C.c_int), ("i_star", C.c_int64), ("escalated_modes", C.c_int),
+                ("k", C.c_int), ("p_star", C.c_int), ("i_lead", C.c_int64), ("i_trail", C.c_int64),
+                ("prio", C.c_int), ("escalated_modes", C.c_int),
                 ("ms_norm", C.c_double), ("ms_gram", C.c_double), ("ms_eig", C.c_double),
                 ("ms_ttm", C.c_double), ("ms_quant", C.c_double), ("ms_encode", C.c_double),
                 ("ms_total", C.c_double), ("subspace_modes", C.c_int), ("block_size", C.c_int)]
@@ -197,12 +198,12 @@ def atc_ttm(x: torch.Tensor, L: int, n: int, R: int, u: torch.Tensor, r: int, ex
 
 def atc_quantize_core(core: torch.Tensor, target_sse: float, block_size: int = 4096, stream=None):
     ptr, nb = C.c_void_p(), C.c_size_t(0)
-    info = (C.c_int64 * 4)()
+    info = (C.c_int64 * 5)()
     _check(lib().atc_quantize_core(_dev(core), core.numel(), float(target_sse), block_size, _stream(stream),
                                    C.byref(ptr), C.byref(nb), info))
     data = C.string_at(ptr, nb.value)
     lib().atc_free_buffer(ptr)
-    return data, dict(k=info[0], p_star=info[1], i_star=info[2])
+    return data, dict(k=info[0], p_star=info[1], prio=info[2], i_lead=info[3], i_trail=info[4])
 
 
 def atc_dequantize_core(section: bytes, n: int, device="cuda", stream=None) -> torch.Tensor:

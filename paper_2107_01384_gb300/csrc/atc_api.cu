@@ -576,8 +576,9 @@ int atc_quantize_core(const double* core_dev, int64_t n, double target_sse, int 
   if (info) {
     info[0] = qr.k;
     info[1] = qr.p_star;
-    info[2] = qr.i_star;
-    info[3] = 0;
+    info[2] = qr.prio;
+    info[3] = qr.i_lead;
+    info[4] = qr.i_trail;
   }
   return ATC_OK;
 }
@@ -958,14 +959,16 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   st.ms_encode = mse;
   st.k = qr.k;
   st.p_star = qr.p_star;
-  st.i_star = qr.i_star;
+  st.prio = qr.prio;
+  st.i_lead = qr.i_lead;
+  st.i_trail = qr.i_trail;
   st.sse_quant_pred = qr.sse_pred;
   // core slices left without a significant coefficient: their factor columns
   // are not stored (Section 3.3, the paragraph after Table 2)
   int64_t rsum = 0;
   for (int i = 0; i < d; ++i) rsum += c->ranks[i];
   std::vector<uint8_t> kept((size_t)rsum, 0);
-  rc = core_kept_slices(ncore, c->ranks, perm.data(), d, qr.p_star, qr.i_star, kept.data(), s);
+  rc = core_kept_slices(ncore, c->ranks, perm.data(), d, qr.p_star, qr.i_lead, kept.data(), s);
   if (rc) return bail(rc);
   // stream (version 2): header, kept-column maps, kept factor columns (raw FP64), core section
   std::vector<std::vector<double>> hfac(d);

@@ -169,14 +169,16 @@ int tc_error_flag(int** flag);  // device error word of the tensor-core kernels 
 struct QuantResult {
   int k;
   int p_star;
-  int64_t i_star;
+  int prio;        // split truncation of plane p_star: 0 leading bits first, 1 trailing first
+  int64_t i_lead;  // last leading bit of plane p_star encoded (-1: none)
+  int64_t i_trail; // last trailing bit of plane p_star encoded (-1: none)
   double sse_pred;
 };
 int quantize_encode(const double* core, int64_t n, double target, int block_size, cudaStream_t s,
                     std::string* out, QuantResult* res, float* ms_quant, float* ms_encode);
 int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t n, cudaStream_t s);
 // slices of the last quantized core holding a significant coefficient (k_quant.cu)
-int core_kept_slices(int64_t n, const int64_t* ranks, const int* perm, int d, int p_star, int64_t i_star,
+int core_kept_slices(int64_t n, const int64_t* ranks, const int* perm, int d, int p_star, int64_t i_lead,
                      uint8_t* kept_host, cudaStream_t s);
 
 // Kernel timer (atc_kernel_timing): when enabled, the launch sites of the main

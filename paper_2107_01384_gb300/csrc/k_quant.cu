@@ -20,9 +20,20 @@
 // (order-preserving) reduction.  The first plane with E(p+1) - M_p <= T holds
 // the breakpoint.
 //
+// Supplement S.3 (split bit-plane truncation): on the last plane p_star the
+//   leading bits (coefficients not yet significant) and the trailing bits
+//   (significant ones) get breakpoints of their own, i_lead and i_trail.  The
+//   category with the higher efficiency (exact SSE reduction / encoded bits)
+//   on plane p_star + 1 goes first: the walk takes its bits in coefficient
+//   order, then those of the other category, and stops at the first bit whose
+//   tracked error is <= the target.  p_star itself comes from the walk in
+//   coefficient order; when the split walk does not reach the target on that
+//   plane, i_lead = i_trail = i_star.
+//
 // Stream section "ATCQ" (little-endian):
-//   char[4] "ATCQ" | u32 1 | u64 n | i32 k | u32 block_size | i32 p_star | u32 0 |
-//   u64 i_star | u32 nplanes | u32 17 | u16 freq[nplanes][17] |
+//   char[4] "ATCQ" | u32 2 | u64 n | i32 k | u32 block_size | i32 p_star |
+//   u32 priority (0 leading first, 1 trailing first) | u64 i_lead | u64 i_trail |
+//   u32 nplanes | u32 17 | u16 freq[nplanes][17] |
 //   u32 sizes[nblocks][nplanes][2] (rANS bytes, raw bytes) | payload
 //   (per block, per plane 63 .. p_star: rANS bytes then raw bytes).
 // Run r >= 0 -> symbol s = floor(log2(r+1)) coded with the plane's table, then
@@ -48,8 +59,10 @@ constexpr int kScaleBits = 12;
 constexpr uint32_t kM = 1u << kScaleBits;
 constexpr uint32_t kRansL = 1u << 23;
 constexpr int kPlaneChunk = 16;       // planes per tracker pass
+constexpr int kPlaneGroup = 8;        // planes per load of each magnitude
 constexpr int kSegBlocks = 304;       // 2 x 152 SMs
 constexpr int kSegThreads = 256;
+constexpr int kQHdr = 56;             // fixed part of the ATCQ header
 
 // ------------------------------------------------------------ 192-bit signed
 struct I192 {
@@ -175,6 +188,9 @@ struct TrackState {
   I192 e64;
   I192 e_star;    // tracked error at the breakpoint
   I192 e_plane;   // E(p_star + 1)
+  int prio;       // split truncation of plane p_star: 0 leading first, 1 trailing first
+  int split_hit;  // the split walk reached the target on plane p_star
+  int64_t i_lead, i_trail;
 };
 
 __global__ void scale_exp_kernel(const unsigned long long* __restrict__ mx, double target, TrackState* st) {
@@ -251,30 +267,41 @@ __global__ void __launch_bounds__(kSegThreads) plane_stats_kernel(const uint64_t
     }
     __syncthreads();
   }
-  for (int p = phi; p >= plo; --p) {
-    Seg a;
-    a.s = i192_zero();
-    a.m = i192_zero();
-    a.empty = 1;
+  // kPlaneGroup planes per load of each magnitude (the per-plane summaries are
+  // independent, so the order of the element loop is unchanged)
+  for (int pg = phi; pg >= plo; pg -= kPlaneGroup) {
+    Seg a[kPlaneGroup];
+#pragma unroll
+    for (int k = 0; k < kPlaneGroup; ++k) {
+      a[k].s = i192_zero();
+      a[k].m = i192_zero();
+      a[k].empty = (t_lo >= t_hi);
+    }
     for (int64_t i = t_lo; i < t_hi; ++i) {
       const uint64_t v = q[i];
-      I192 d = i192_zero();
-      if ((v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
-      if (a.empty) { a.s = d; a.m = d; a.empty = 0; }
-      else {
-        a.s = i192_add(a.s, d);
-        if (i192_lt(a.m, a.s)) a.m = a.s;
+#pragma unroll
+      for (int k = 0; k < kPlaneGroup; ++k) {
+        const int p = pg - k;
+        I192 d = i192_zero();
+        if (p >= plo && (v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+        a[k].s = i192_add(a[k].s, d);
+        if (i192_lt(a[k].m, a[k].s) || i == t_lo) a[k].m = a[k].s;
       }
     }
-    Seg r = warp_seg_reduce(a);
-    if (lane == 0) wsum[warp] = r;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      Seg t = wsum[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = seg_combine(t, wsum[w]);
-      out[(int64_t)(phi - p) * gridDim.x + blockIdx.x] = t;
+#pragma unroll
+    for (int k = 0; k < kPlaneGroup; ++k) {
+      const int p = pg - k;
+      if (p < plo) break;
+      Seg r = warp_seg_reduce(a[k]);
+      if (lane == 0) wsum[warp] = r;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        Seg t = wsum[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = seg_combine(t, wsum[w]);
+        out[(int64_t)(phi - p) * gridDim.x + blockIdx.x] = t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -328,7 +355,7 @@ __global__ void __launch_bounds__(32 * kPlaneChunk) plane_scan_kernel(const Seg*
       return;
     }
   }
-  I192 e_next = st->e_next;
+  I192 e_next = st->e_next, e_prev = e_next;
   for (int q = phi; q >= plo; --q) {
     Seg t = plane_sum[phi - q];
     if (t.empty) { t.s = t.m = i192_zero(); }
@@ -339,15 +366,16 @@ __global__ void __launch_bounds__(32 * kPlaneChunk) plane_scan_kernel(const Seg*
       st->e_plane = e_next;
       return;
     }
+    e_prev = e_next;
     e_next = i192_sub(e_next, t.s);
   }
   st->e_next = e_next;
-  if (plo == 0) {  // target unreachable: everything encoded
+  if (plo == 0) {  // target not reached in coefficient order: everything encoded
     st->found = 1;
     st->p_star = 0;
     st->i_star = -1;
     st->e_star = e_next;
-    st->e_plane = e_next;
+    st->e_plane = e_prev;  // E(1): the split walk of plane 0 starts there
   }
 }
 
@@ -464,14 +492,300 @@ __global__ void __launch_bounds__(kIstarThreads) istar_kernel(const uint64_t* __
   }
 }
 
+// ------------------------------------------------ split truncation (S.3)
+// Reduction D_i(p) of the bit of coefficient v on plane p when it belongs to
+// category cat of that plane (0 leading: not significant above p, 1 trailing:
+// significant above p); zero for the other category and for a coefficient
+// still zero through plane p.
+__device__ __forceinline__ I192 cat_reduction(uint64_t v, int p, int cat) {
+  if ((v >> p) == 0) return i192_zero();
+  const int sig = (p == 63) ? 0 : ((v >> (p + 1)) != 0 ? 1 : 0);
+  if (sig != cat) return i192_zero();
+  return i192_diff(coef_err(v, p + 1), coef_err(v, p));
+}
+
+// Per segment of the tracker's segmentation: the ordered summaries of the
+// reductions of plane p restricted to each category (prefix maxima taken over
+// every prefix, the empty one included: a prefix value at a segment start is
+// the running error already tested there), and for the priority the
+// order-free totals of plane p + 1 -- the SSE reductions of its leading and
+// trailing bits and their counts (leading ones, trailing bits).
+struct SplitSeg {
+  Seg c[2];
+  I192 d[2];
+  unsigned long long cnt[2];
+};
+
+__device__ Seg block_seg_reduce(Seg a, Seg* wsum) {
+  Seg r = warp_seg_reduce(a);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) wsum[warp] = r;
+  __syncthreads();
+  Seg t = wsum[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = seg_combine(t, wsum[w]);
+  return t;  // valid in every thread
+}
+
+__device__ I192 warp_i192_sum(I192 e) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    I192 o;
+    o.w0 = __shfl_down_sync(0xffffffffu, e.w0, off);
+    o.w1 = __shfl_down_sync(0xffffffffu, e.w1, off);
+    o.w2 = __shfl_down_sync(0xffffffffu, e.w2, off);
+    e = i192_add(e, o);
+  }
+  return e;  // lane 0 holds the sum (other lanes: partial sums, mod 2^192)
+}
+
+__global__ void __launch_bounds__(kSegThreads) split_stats_kernel(const uint64_t* __restrict__ q, int64_t n,
+                                                                   int64_t seg_len, int p, SplitSeg* __restrict__ out) {
+  __shared__ Seg wsum[kSegThreads / 32];
+  __shared__ I192 wd[2][kSegThreads / 32];
+  __shared__ unsigned long long wc[2][kSegThreads / 32];
+  const int64_t s_lo = blockIdx.x * seg_len;
+  const int64_t s_hi = min(n, s_lo + seg_len);
+  const int64_t per = (seg_len + blockDim.x - 1) / blockDim.x;
+  const int64_t t_lo = min(s_hi, s_lo + threadIdx.x * per);
+  const int64_t t_hi = min(s_hi, t_lo + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Seg a[2];
+  I192 d[2] = {i192_zero(), i192_zero()};
+  unsigned long long c[2] = {0ull, 0ull};
+  for (int k = 0; k < 2; ++k) { a[k].s = a[k].m = i192_zero(); a[k].empty = 0; }
+  const bool above = p <= 62;
+  for (int64_t i = t_lo; i < t_hi; ++i) {
+    const uint64_t v = q[i];
+    if ((v >> p) != 0) {
+      const int sig = (p == 63) ? 0 : ((v >> (p + 1)) != 0 ? 1 : 0);
+      const I192 r = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+      // only the category the bit belongs to moves; the other keeps its prefix
+      if (sig) {
+        a[1].s = i192_add(a[1].s, r);
+        if (i192_lt(a[1].m, a[1].s)) a[1].m = a[1].s;
+      } else {
+        a[0].s = i192_add(a[0].s, r);
+        if (i192_lt(a[0].m, a[0].s)) a[0].m = a[0].s;
+      }
+      if (above && (v >> (p + 1)) != 0) {
+        const int sig1 = (p + 1 == 63) ? 0 : ((v >> (p + 2)) != 0 ? 1 : 0);
+        const I192 r1 = i192_diff(coef_err(v, p + 2), coef_err(v, p + 1));
+        if (sig1) { d[1] = i192_add(d[1], r1); ++c[1]; }
+        else { d[0] = i192_add(d[0], r1); ++c[0]; }
+      }
+    }
+  }
+  const Seg l = block_seg_reduce(a[0], wsum);
+  const Seg t = block_seg_reduce(a[1], wsum);
+  for (int k = 0; k < 2; ++k) {
+    const I192 e = warp_i192_sum(d[k]);
+    unsigned long long cc = c[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cc += __shfl_down_sync(0xffffffffu, cc, off);
+    if (lane == 0) { wd[k][warp] = e; wc[k][warp] = cc; }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    SplitSeg o;
+    o.c[0] = l;
+    o.c[1] = t;
+    for (int k = 0; k < 2; ++k) {
+      I192 e = i192_zero();
+      unsigned long long cc = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { e = i192_add(e, wd[k][w]); cc += wc[k][w]; }
+      o.d[k] = e;
+      o.cnt[k] = cc;
+    }
+    out[blockIdx.x] = o;
+  }
+}
+
+// 256-bit two's complement: (signed 192-bit) x (unsigned 64-bit), signed compare
+struct I256 {
+  uint64_t w[4];
+};
+__device__ I256 i256_mul(I192 a, uint64_t b) {
+  const bool neg = (int64_t)a.w2 < 0;
+  if (neg) a = i192_neg(a);
+  I256 r;
+  u128 t = (u128)a.w0 * b;
+  r.w[0] = (uint64_t)t;
+  t = (u128)a.w1 * b + (uint64_t)(t >> 64);
+  r.w[1] = (uint64_t)t;
+  t = (u128)a.w2 * b + (uint64_t)(t >> 64);
+  r.w[2] = (uint64_t)t;
+  r.w[3] = (uint64_t)(t >> 64);
+  if (neg) {
+    uint64_t carry = 1;
+    for (int k = 0; k < 4; ++k) {
+      const u128 x = (u128)(~r.w[k]) + carry;
+      r.w[k] = (uint64_t)x;
+      carry = (uint64_t)(x >> 64);
+    }
+  }
+  return r;
+}
+__device__ bool i256_ge(const I256& a, const I256& b) {
+  if (a.w[3] != b.w[3]) return (int64_t)a.w[3] > (int64_t)b.w[3];
+  for (int k = 2; k >= 0; --k)
+    if (a.w[k] != b.w[k]) return a.w[k] > b.w[k];
+  return true;
+}
+
+struct SplitShared {
+  I192 sh[32];
+  I192 pre;
+  int first;
+  int hit;
+  long long j;
+  I192 run;
+};
+
+// First bit of category cat of plane p, in coefficient order, at which the
+// running error (start minus the reductions so far) is <= T; returns its index
+// or -1.  Three ordered first-passage searches as for i_star: over the
+// segments' category summaries, over per-thread summaries inside the hit
+// segment, then element by element.  *total: the category's whole reduction.
+// Every thread of the block calls it.
+__device__ int64_t split_first_passage(const uint64_t* __restrict__ q, int64_t n, int64_t seg_len,
+                                       const SplitSeg* __restrict__ segs, int nseg, int p, int cat, I192 start, I192 T,
+                                       SplitShared* S, I192* err_at, I192* total) {
+  const int tid = threadIdx.x;
+  Seg g;
+  g.empty = 0;
+  g.s = g.m = i192_zero();
+  if (tid < nseg) g = segs[tid].c[cat];
+  I192 tot;
+  const I192 pre = i192_block_exscan(g.s, S->sh, &tot);
+  *total = tot;
+  if (tid == 0) { S->first = INT_MAX; S->hit = 0; }
+  __syncthreads();
+  if (tid < nseg && i192_le(i192_sub(start, i192_add(pre, g.m)), T)) atomicMin(&S->first, tid);
+  __syncthreads();
+  const int b = S->first;
+  if (b == INT_MAX) return -1;
+  if (tid == b) S->pre = pre;
+  __syncthreads();
+  const I192 seg_pre = S->pre;
+  const int64_t s_lo = b * seg_len;
+  const int64_t s_hi = min(n, s_lo + seg_len);
+  const int64_t per = (seg_len + blockDim.x - 1) / blockDim.x;
+  const int64_t t_lo = min(s_hi, s_lo + tid * per);
+  const int64_t t_hi = min(s_hi, t_lo + per);
+  Seg a;
+  a.empty = 0;
+  a.s = a.m = i192_zero();
+  for (int64_t i = t_lo; i < t_hi; ++i) {
+    const I192 d = cat_reduction(q[i], p, cat);
+    a.s = i192_add(a.s, d);
+    if (i192_lt(a.m, a.s)) a.m = a.s;
+  }
+  I192 tot2;
+  const I192 pre2 = i192_add(seg_pre, i192_block_exscan(a.s, S->sh, &tot2));
+  if (tid == 0) S->first = INT_MAX;
+  __syncthreads();
+  if (i192_le(i192_sub(start, i192_add(pre2, a.m)), T)) atomicMin(&S->first, tid);
+  __syncthreads();
+  if (tid == S->first) {
+    I192 run = i192_sub(start, pre2);
+    for (int64_t i = t_lo; i < t_hi; ++i) {
+      run = i192_sub(run, cat_reduction(q[i], p, cat));
+      if (i192_le(run, T)) {
+        S->j = i;
+        S->run = run;
+        S->hit = 1;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (!S->hit) return -1;  // cannot happen: the hit thread holds the passage
+  *err_at = S->run;
+  return S->j;
+}
+
+// Priority and breakpoints of the last plane (one CTA of kIstarThreads):
+// plane p + 1's efficiencies decide which category goes first (exact:
+// d_lead * cost_trail >= d_trail * cost_lead, ties and empty categories leading
+// first; cost_lead = 8 x its rANS bytes + one sign bit per leading 1,
+// cost_trail = one bit per trailing bit); then the walk of the first
+// category, and if it does not reach the target, the second one from the end
+// of the first.  cost_rs: the rANS bytes of plane p + 1 per block.
+__global__ void __launch_bounds__(kIstarThreads) split_kernel(const uint64_t* __restrict__ q, int64_t n, int64_t seg_len,
+                                                              const SplitSeg* __restrict__ segs, int nseg, int p,
+                                                              const uint32_t* __restrict__ cost_rs, int64_t ncost,
+                                                              TrackState* st) {
+  __shared__ SplitShared S;
+  __shared__ unsigned long long s_rb;
+  __shared__ int s_prio;
+  const int tid = threadIdx.x;
+  if (tid == 0) { s_rb = 0; s_prio = 0; }
+  __syncthreads();
+  if (p <= 62) {
+    unsigned long long rb = 0;
+    for (int64_t i = tid; i < ncost; i += blockDim.x) rb += cost_rs[i];
+    atomicAdd(&s_rb, rb);
+    I192 dl = i192_zero(), dt = i192_zero();
+    unsigned long long ones = 0, trail = 0;
+    if (tid < nseg) { dl = segs[tid].d[0]; dt = segs[tid].d[1]; ones = segs[tid].cnt[0]; trail = segs[tid].cnt[1]; }
+    I192 tl, tt, tmp;
+    i192_block_exscan(dl, S.sh, &tl);
+    i192_block_exscan(dt, S.sh, &tt);
+    i192_block_exscan({ones, 0, 0}, S.sh, &tmp);
+    ones = tmp.w0;
+    i192_block_exscan({trail, 0, 0}, S.sh, &tmp);
+    trail = tmp.w0;
+    __syncthreads();
+    if (tid == 0) {
+      const uint64_t cost_lead = 8ull * s_rb + ones, cost_trail = trail;
+      s_prio = i256_ge(i256_mul(tl, cost_trail), i256_mul(tt, cost_lead)) ? 0 : 1;
+    }
+  }
+  __syncthreads();
+  const int first = s_prio;
+  const int64_t i_std = (st->i_star < 0) ? n - 1 : st->i_star;
+  int64_t il = i_std, it = i_std;
+  int hit = 0;
+  I192 err = st->e_star;
+  if (st->reachable) {
+    const I192 T = st->t_int, E1 = st->e_plane;
+    I192 tot, e;
+    const int64_t j1 = split_first_passage(q, n, seg_len, segs, nseg, p, first, E1, T, &S, &e, &tot);
+    if (j1 >= 0) {
+      hit = 1;
+      err = e;
+      il = first == 0 ? j1 : -1;
+      it = first == 0 ? -1 : j1;
+    } else {
+      I192 tot2;
+      const int64_t j2 = split_first_passage(q, n, seg_len, segs, nseg, p, 1 - first, i192_sub(E1, tot), T, &S, &e, &tot2);
+      if (j2 >= 0) {
+        hit = 1;
+        err = e;
+        il = first == 0 ? n - 1 : j2;
+        it = first == 0 ? j2 : n - 1;
+      }
+    }
+  }
+  if (tid == 0) {
+    st->prio = first;
+    st->split_hit = hit;
+    st->i_lead = il;
+    st->i_trail = it;
+    st->e_star = err;
+  }
+}
+
 // -------------------------------------------------------------------- encoder
 struct EncParams {
   const uint64_t* q;
   const uint8_t* sg;
   int64_t n;
   int block_size;
-  int p_star;
-  int64_t i_star;
+  int p_top;                 // first plane (63, or p_star + 1 for the cost of that plane alone)
+  int p_star;                // last plane: leading bits up to i_lead, trailing bits up to i_trail
+  int64_t i_lead, i_trail;
   int nplanes;
   int64_t nblocks;
   unsigned long long* hist;  // nplanes x 17
@@ -485,13 +799,16 @@ struct EncParams {
 
 __device__ __forceinline__ int bucket_of(uint32_t v) { return 31 - __clz(v + 1u); }
 
-// Warp walk of one (block, plane) chunk.  For every run (in order) calls
+// Warp walk of one (block, plane) chunk: leading bits of coefficients before
+// hl, trailing bits of those before ht.  For every run (in order) calls
 // on_run(run); raw bits are reported per 32-coefficient group as
 // (packed value, count).  Returns via the callbacks only.
 template <typename RunF, typename RawF>
-__device__ __forceinline__ void chunk_walk(const EncParams& P, int64_t lo, int64_t hi, int p, RunF on_run, RawF on_raw) {
+__device__ __forceinline__ void chunk_walk(const EncParams& P, int64_t lo, int64_t hl, int64_t ht, int p, RunF on_run,
+                                           RawF on_raw) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
+  const int64_t hi = max(hl, ht);
   uint32_t carry = 0;  // zeros since the last 1 (leading subsequence)
   for (int64_t g = lo; g < hi; g += 32) {
     const int64_t j = g + lane;
@@ -499,10 +816,11 @@ __device__ __forceinline__ void chunk_walk(const EncParams& P, int64_t lo, int64
     uint64_t v = in ? P.q[j] : 0;
     const bool bit = (v >> p) & 1ull;
     const bool sigb = (p == 63) ? false : ((v >> (p + 1)) != 0ull);
-    const bool lead = in && !sigb;
+    const bool lead = in && !sigb && j < hl;
+    const bool trail = in && sigb && j < ht;
     const bool one = lead && bit;
-    const bool rawp = in && (sigb || one);
-    const bool rawv = sigb ? bit : (one ? (P.sg[j] != 0) : false);
+    const bool rawp = trail || one;
+    const bool rawv = trail ? bit : (one ? (P.sg[j] != 0) : false);
     const unsigned lead_m = __ballot_sync(0xffffffffu, lead);
     const unsigned one_m = __ballot_sync(0xffffffffu, one);
     const unsigned raw_m = __ballot_sync(0xffffffffu, rawp);
@@ -541,11 +859,18 @@ __device__ __forceinline__ void chunk_walk(const EncParams& P, int64_t lo, int64
   if (carry > 0) on_run(carry);
 }
 
-__device__ __forceinline__ void chunk_range(const EncParams& P, int64_t blk, int p, int64_t* lo, int64_t* hi) {
-  int64_t a = blk * P.block_size, b = min(P.n, a + P.block_size);
-  if (p == P.p_star && b > P.i_star + 1) b = max(a, P.i_star + 1);
+// end (exclusive) of the coefficients whose bit of plane p is encoded, for a
+// breakpoint i of the last plane
+__device__ __host__ __forceinline__ int64_t cat_end(int64_t lo, int64_t hi, int p, int p_star, int64_t i) {
+  if (p == p_star && hi > i + 1) hi = i + 1;
+  return hi < lo ? lo : hi;
+}
+__device__ __forceinline__ void chunk_range(const EncParams& P, int64_t blk, int p, int64_t* lo, int64_t* hl,
+                                            int64_t* ht) {
+  const int64_t a = blk * P.block_size, b = min(P.n, a + P.block_size);
   *lo = a;
-  *hi = b;
+  *hl = cat_end(a, b, p, P.p_star, P.i_lead);
+  *ht = cat_end(a, b, p, P.p_star, P.i_trail);
 }
 
 // pass 1: per-plane histograms of run symbols and raw byte counts
@@ -555,14 +880,14 @@ __global__ void enc_hist_kernel(EncParams P) {
   if (chunk >= nchunks) return;
   const int64_t blk = chunk / P.nplanes;
   const int pi = (int)(chunk % P.nplanes);
-  const int p = 63 - pi;
-  int64_t lo, hi;
-  chunk_range(P, blk, p, &lo, &hi);
+  const int p = P.p_top - pi;
+  int64_t lo, hl, ht;
+  chunk_range(P, blk, p, &lo, &hl, &ht);
   const int lane = threadIdx.x & 31;
   uint64_t rawbits = 0;
   unsigned long long* h = P.hist + pi * kNsym;
   chunk_walk(
-      P, lo, hi, p,
+      P, lo, hl, ht, p,
       [&](uint32_t run) {
         if (lane == 0) atomicAdd(h + bucket_of(run), 1ull);
       },
@@ -648,9 +973,9 @@ __global__ void __launch_bounds__(32 * kEncWarps) enc_rans_kernel(EncParams P, i
   if (chunk >= nchunks) return;
   const int64_t blk = chunk / P.nplanes;
   const int pi = (int)(chunk % P.nplanes);
-  const int p = 63 - pi;
-  int64_t lo, hi;
-  chunk_range(P, blk, p, &lo, &hi);
+  const int p = P.p_top - pi;
+  int64_t lo, hl, ht;
+  chunk_range(P, blk, p, &lo, &hl, &ht);
   uint32_t* runs = (P.block_size < kMaxRuns) ? runs_sm[warp] : (spill + chunk * (int64_t)(P.block_size + 1));
   uint32_t nr = 0;
   // raw writer state (lane 0)
@@ -659,7 +984,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) enc_rans_kernel(EncParams P, i
   uint8_t* rawp = nullptr;
   if (!sizes_only) rawp = P.out + P.off[chunk] + P.rsize[chunk];
   chunk_walk(
-      P, lo, hi, p,
+      P, lo, hl, ht, p,
       [&](uint32_t run) {
         if (lane == 0) runs[nr] = run;
         nr++;
@@ -705,6 +1030,281 @@ __global__ void __launch_bounds__(32 * kEncWarps) enc_rans_kernel(EncParams P, i
   }
 }
 
+// ------------------------------------------- block-parallel encoder (n large)
+// For blocks of at most kEncBlockMax coefficients.  Pass 1 (enc_block_kernel):
+// one CTA per block stages the block's magnitudes and signs in shared memory
+// once; the leading-bit position m_j of every coefficient gives each plane's
+// run and raw-bit counts (for plane p: a leading 1 is m_j == p, a trailing bit
+// m_j > p, a leading zero m_j < p, and a final run exists when a leading zero
+// follows the plane's last leading 1), hence the offsets of every (block,
+// plane) chunk inside the block's run and raw slots; then each warp walks its
+// planes from shared memory (the walk of chunk_walk), writing the runs and the
+// packed raw bits and counting the run symbols per plane.  Pass 2
+// (enc_rans_thread_kernel): one THREAD per chunk runs rANS over the chunk's
+// stored runs -- sizes first, then, after the offset scan, the bytes at their
+// final place together with the chunk's raw bytes and its table entry.
+constexpr int kEncBlockMax = 4096;
+constexpr int kEncBlockThreads = 256;
+
+struct BlockEncParams {
+  const uint64_t* q;
+  const uint8_t* sg;
+  int64_t n;
+  int block_size;
+  int p_top;       // first plane walked (63, or p_star + 1 for the cost pass of that plane alone)
+  int p_star;      // last plane (its leading bits up to i_lead, trailing bits up to i_trail)
+  int64_t i_lead, i_trail;
+  int nplanes;
+  int64_t nblocks;
+  int64_t run_slot;            // u32 run slots per block (block_size + nplanes)
+  int64_t raw_slot;            // raw bytes per block (nplanes * (block_size / 8 + 1))
+  uint32_t* runs;              // nblocks * run_slot
+  uint8_t* raw;                // nblocks * raw_slot
+  uint32_t* nruns;             // nchunks
+  uint32_t* run_off;           // nchunks: first run of the chunk inside its block slot
+  uint32_t* raw_off;           // nchunks: first raw byte of the chunk inside its block slot
+  uint32_t* wsize;             // nchunks: raw bytes
+  unsigned long long* hist;    // nplanes x 17
+};
+
+__global__ void __launch_bounds__(kEncBlockThreads) enc_block_kernel(BlockEncParams P) {
+  __shared__ unsigned long long qs[kEncBlockMax];
+  __shared__ uint8_t ss[kEncBlockMax];
+  __shared__ signed char ms[kEncBlockMax];   // leading-bit position, -1 for zero
+  __shared__ uint32_t s_cnt[65], s_hpos[65];  // per leading-bit position m + 1: count, last index + 1
+  __shared__ uint32_t s_low[64];
+  __shared__ uint32_t s_lastones[2], s_lastlow[2], s_cnt_last[2];  // last plane: [leading 1s/last 1, ...]
+  __shared__ uint32_t s_roff[64], s_woff[64];
+  __shared__ unsigned s_hist[64 * kNsym];
+  const int64_t b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t lo = b * P.block_size, hi_all = min(P.n, lo + P.block_size);
+  const int len = (int)(hi_all - lo);
+  const int np = P.nplanes;
+  // the last plane's category bounds inside this block (exclusive, relative to lo)
+  const int hl = (int)max((int64_t)0, min((int64_t)len, P.i_lead + 1 - lo));
+  const int ht = (int)max((int64_t)0, min((int64_t)len, P.i_trail + 1 - lo));
+  for (int i = tid; i < 65; i += kEncBlockThreads) { s_cnt[i] = 0; s_hpos[i] = 0; }
+  if (tid < 2) { s_lastones[tid] = 0; s_lastlow[tid] = 0; s_cnt_last[tid] = 0; }
+  for (int i = tid; i < 64 * kNsym; i += kEncBlockThreads) s_hist[i] = 0;
+  __syncthreads();
+  const int plast = P.p_top - (np - 1);   // == p_star unless this is the single-plane cost pass
+  const bool last_split = (plast == P.p_star);
+  for (int g = 0; g < len; g += kEncBlockThreads) {
+    const int i = g + tid;
+    const bool valid = i < len;
+    const uint64_t v = valid ? P.q[lo + i] : 0ull;
+    const int m = valid ? (v ? 63 - __clzll((long long)v) : -1) : -2;
+    if (valid) {
+      qs[i] = v;
+      ss[i] = P.sg[lo + i];
+      ms[i] = (signed char)m;
+    }
+    // whole planes: a histogram over the leading-bit positions, one atomic pair
+    // per distinct position in the warp (count, last index + 1)
+    const unsigned peers = __match_any_sync(0xffffffffu, m);
+    if (valid && lane == __ffs(peers) - 1) {
+      atomicAdd(&s_cnt[m + 1], (uint32_t)__popc(peers));
+      atomicMax(&s_hpos[m + 1], (uint32_t)(g + warp * 32 + (31 - __clz(peers)) + 1));
+    }
+  }
+  __syncthreads();
+  // the last plane (its category bounds): leading ones and trailing bits in range,
+  // the last leading one and the last leading zero in range (warp-aggregated)
+  if (last_split) {
+    const int p = plast;
+    uint32_t n1 = 0, nt = 0, l1 = 0, l0 = 0;
+    for (int i = tid; i < len; i += kEncBlockThreads) {
+      const int m = ms[i];
+      if (m > p && i < ht) ++nt;
+      if (m == p && i < hl) { ++n1; l1 = max(l1, (uint32_t)(i + 1)); }
+      if (m < p && i < hl) l0 = max(l0, (uint32_t)(i + 1));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+      nt += __shfl_xor_sync(0xffffffffu, nt, o);
+      l1 = max(l1, __shfl_xor_sync(0xffffffffu, l1, o));
+      l0 = max(l0, __shfl_xor_sync(0xffffffffu, l0, o));
+    }
+    if (lane == 0) {
+      atomicAdd(&s_cnt_last[0], n1);
+      atomicAdd(&s_cnt_last[1], nt);
+      atomicMax(&s_lastones[0], l1);
+      atomicMax(&s_lastlow[0], l0);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // whole plane p: runs = leading ones (m == p) + a final run when a leading
+    // zero (m < p) follows the last leading one; raw bits = ones (signs) + trailing (m > p)
+    uint32_t ro = 0, wo = 0;
+    uint32_t above = 0;                     // coefficients with m > p
+    for (int m = 63; m > P.p_top; --m) above += s_cnt[m + 1];
+    uint32_t low = s_hpos[0];               // s_low[p]: last index + 1 of a coefficient with m < p
+    for (int m = 0; m <= 63; ++m) {
+      s_low[m] = low;
+      low = max(low, s_hpos[m + 1]);
+    }
+    for (int pi = 0; pi < np; ++pi) {
+      const int p = P.p_top - pi;
+      uint32_t ones, trail, endrun;
+      if (pi == np - 1 && last_split) {
+        ones = s_cnt_last[0];
+        trail = s_cnt_last[1];
+        endrun = (s_lastlow[0] > s_lastones[0]) ? 1u : 0u;
+      } else {
+        ones = s_cnt[p + 1];
+        trail = above;
+        endrun = (s_low[p] > s_hpos[p + 1]) ? 1u : 0u;
+      }
+      above += s_cnt[p + 1];
+      s_roff[pi] = ro;
+      s_woff[pi] = wo;
+      const uint32_t nr = ones + endrun;
+      const uint32_t wb = (ones + trail + 7) / 8;
+      const int64_t chunk = b * np + pi;
+      P.nruns[chunk] = nr;
+      P.run_off[chunk] = ro;
+      P.raw_off[chunk] = wo;
+      P.wsize[chunk] = wb;
+      ro += nr;
+      wo += wb;
+    }
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int pi = warp; pi < np; pi += kEncBlockThreads / 32) {
+    const int p = P.p_top - pi;
+    const bool lastp = (pi == np - 1) && last_split;
+    const int cl = lastp ? hl : len, ct = lastp ? ht : len;  // category bounds of this chunk
+    const int clen = max(cl, ct);
+    uint32_t* runs = P.runs + b * P.run_slot + s_roff[pi];
+    uint8_t* rawp = P.raw + b * P.raw_slot + s_woff[pi];
+    unsigned* h = s_hist + pi * kNsym;
+    uint32_t nr = 0, carry = 0;
+    uint64_t acc = 0;
+    int nacc = 0;
+    for (int g = 0; g < clen; g += 32) {
+      const int i = g + lane;
+      const int m = (i < clen) ? ms[i] : -1;
+      const bool sig_in = i < ct && m > p;          // an encoded trailing bit
+      const bool lead = i < cl && m <= p;            // an encoded leading bit
+      const bool one = lead && m == p;
+      const bool rawp_b = sig_in || one;
+      const bool rawv = sig_in ? ((qs[i] >> p) & 1ull) : (one ? (ss[i] != 0) : false);
+      const unsigned lead_m = __ballot_sync(0xffffffffu, lead);
+      const unsigned one_m = __ballot_sync(0xffffffffu, one);
+      const unsigned raw_m = __ballot_sync(0xffffffffu, rawp_b);
+      const int rank = __popc(raw_m & lt);
+      const unsigned packed = __reduce_or_sync(0xffffffffu, (rawp_b && rawv) ? (1u << rank) : 0u);
+      const int cnt = __popc(raw_m);
+      // runs: lane l holding a leading 1 emits the zeros since the previous leading 1
+      const unsigned zero_m = lead_m & ~one_m;
+      if (one) {
+        const unsigned prevmask = one_m & lt;
+        uint32_t run;
+        if (prevmask) {
+          const int pl = 31 - __clz(prevmask);
+          const unsigned from = (pl == 31) ? 0u : ~((2u << pl) - 1u);
+          run = __popc(zero_m & lt & from);
+        } else {
+          run = carry + __popc(zero_m & lt);
+        }
+        runs[nr + __popc(one_m & lt)] = run;
+        atomicAdd(&h[bucket_of(run)], 1u);
+      }
+      nr += __popc(one_m);
+      if (one_m) {
+        const int ll = 31 - __clz(one_m);
+        const unsigned above_m = (ll == 31) ? 0u : ~((2u << ll) - 1u);
+        carry = __popc(zero_m & above_m);
+      } else {
+        carry += __popc(zero_m);
+      }
+      if (lane == 0 && cnt > 0) {
+        acc |= (uint64_t)packed << nacc;
+        nacc += cnt;
+        while (nacc >= 8) { *rawp++ = (uint8_t)(acc & 0xff); acc >>= 8; nacc -= 8; }
+      }
+    }
+    if (lane == 0) {
+      if (nacc > 0) *rawp = (uint8_t)(acc & 0xff);
+      if (carry > 0) {
+        runs[nr] = carry;
+        atomicAdd(&h[bucket_of(carry)], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < np * kNsym; i += kEncBlockThreads)
+    if (s_hist[i]) atomicAdd(&P.hist[i], (unsigned long long)s_hist[i]);
+}
+
+struct RansThreadParams {
+  const uint32_t* runs;
+  const uint8_t* raw;
+  int64_t run_slot, raw_slot;
+  const uint32_t* nruns;
+  const uint32_t* run_off;
+  const uint32_t* raw_off;
+  const uint32_t* wsize;
+  const uint32_t* freq;   // nplanes x 17, then cum
+  int nplanes;
+  int64_t nchunks;
+  uint32_t* rsize;        // nchunks
+  const uint64_t* off;    // nchunks + 1 (payload offsets), write pass only
+  uint8_t* out;           // payload base, write pass only
+  uint32_t* table;        // size table, write pass only
+};
+
+// one thread per (block, plane) chunk: rANS of its runs, backwards (the
+// sizes pass emits nothing; the write pass writes the bytes before the end of
+// the chunk's rANS area, the 4-byte state first, then copies the raw bytes)
+__global__ void enc_rans_thread_kernel(RansThreadParams P, int write) {
+  __shared__ uint32_t f_sm[64 * kNsym], c_sm[64 * kNsym];
+  __shared__ uint64_t i_sm[64 * kNsym];
+  for (int i = threadIdx.x; i < P.nplanes * kNsym; i += blockDim.x) {
+    const uint32_t f = P.freq[i];
+    f_sm[i] = f;
+    c_sm[i] = P.freq[P.nplanes * kNsym + i];
+    i_sm[i] = f ? ((1ull << 44) + f - 1) / f : 0ull;
+  }
+  __syncthreads();
+  const int64_t chunk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (chunk >= P.nchunks) return;
+  const int64_t blk = chunk / P.nplanes;
+  const int pi = (int)(chunk - blk * P.nplanes);
+  const uint32_t nr = P.nruns[chunk];
+  const uint32_t* runs = P.runs + blk * P.run_slot + P.run_off[chunk];
+  const uint32_t* f = f_sm + pi * kNsym;
+  const uint32_t* cum = c_sm + pi * kNsym;
+  const uint64_t* inv = i_sm + pi * kNsym;
+  RansEnc r = {kRansL, 0};
+  if (!write) {
+    for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, inv, [](uint8_t) {});
+    P.rsize[chunk] = nr ? (r.nbytes + 4) : 0;
+    return;
+  }
+  uint8_t* base = P.out + P.off[chunk];
+  const uint32_t rs = P.rsize[chunk];
+  if (nr) {
+    uint8_t* w = base + rs;
+    for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, inv, [&](uint8_t by) { *--w = by; });
+    w -= 4;
+    w[0] = (uint8_t)r.x;
+    w[1] = (uint8_t)(r.x >> 8);
+    w[2] = (uint8_t)(r.x >> 16);
+    w[3] = (uint8_t)(r.x >> 24);
+  }
+  const uint32_t ws = P.wsize[chunk];
+  const uint8_t* src = P.raw + blk * P.raw_slot + P.raw_off[chunk];
+  uint8_t* dst = base + rs;
+  for (uint32_t k = 0; k < ws; ++k) dst[k] = src[k];
+  P.table[2 * chunk] = rs;
+  P.table[2 * chunk + 1] = ws;
+}
+
 // exclusive scan of rsize + wsize in chunk order (single CTA, sequential per thread slice)
 __global__ void scan_kernel(const uint32_t* __restrict__ rs, const uint32_t* __restrict__ ws, int64_t nchunks,
                             uint64_t* __restrict__ off) {
@@ -734,7 +1334,7 @@ struct DecParams {
   int k;
   int block_size;
   int p_star;
-  int64_t i_star;
+  int64_t i_lead, i_trail;  // last plane: leading bits up to i_lead, trailing bits up to i_trail
   int nplanes;
   int64_t nblocks;
   int64_t tab;          // offset of the size table
@@ -744,6 +1344,14 @@ struct DecParams {
   double* out;
   int* err;
 };
+
+// Lowest encoded plane of a decoded coefficient a~ != 0 at index j: p_star when
+// it became significant there (its leading 1 is on p_star) or when its trailing
+// bit of p_star is encoded (j <= i_trail); p_star + 1 otherwise.
+__device__ __forceinline__ int lowest_plane(uint64_t a, int64_t j, int p_star, int64_t i_trail) {
+  const bool sig_above = (p_star >= 63) ? false : ((a >> (p_star + 1)) != 0ull);
+  return (!sig_above || j <= i_trail) ? p_star : p_star + 1;
+}
 
 __device__ __forceinline__ uint32_t rd32(const uint8_t* p) {
   return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
@@ -807,7 +1415,7 @@ __global__ void decode_kernel(DecParams D) {
   const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
   for (int64_t j = lo; j < hi_all; ++j) { D.qt[j] = 0; D.sg[j] = 0; }
   uint64_t pos = D.boff[b];
-  const uint8_t* ftab = D.sec + 48;
+  const uint8_t* ftab = D.sec + kQHdr;
   for (int pi = 0; pi < D.nplanes; ++pi) {
     const int p = 63 - pi;
     const uint8_t* t = D.sec + D.tab + (b * D.nplanes + pi) * 8;
@@ -831,11 +1439,12 @@ __global__ void decode_kernel(DecParams D) {
       cum[i] = ca;
       ca += f[i];
     }
-    int64_t hi = hi_all;
-    if (p == D.p_star && hi > D.i_star + 1) hi = max(lo, D.i_star + 1);
+    const int64_t hl = cat_end(lo, hi_all, p, D.p_star, D.i_lead), ht = cat_end(lo, hi_all, p, D.p_star, D.i_trail);
+    const int64_t hi = max(hl, ht);
     bool need = true;
     uint32_t left = 0;
     for (int64_t j = lo; j < hi; ++j) {
+      if (D.qt[j] != 0 ? (j >= ht) : (j >= hl)) continue;  // this category stops earlier
       if (D.qt[j] != 0) {
         if (rbit >= rcap) { atomicExch(D.err, 4); return; }
         const uint64_t bit = (raw[rbit >> 3] >> (rbit & 7)) & 1u;
@@ -876,7 +1485,7 @@ __global__ void decode_kernel(DecParams D) {
   for (int64_t j = lo; j < hi_all; ++j) {
     const uint64_t a = D.qt[j];
     if (a == 0) { D.out[j] = 0.0; continue; }
-    const int pj = (j <= D.i_star) ? D.p_star : D.p_star + 1;
+    const int pj = lowest_plane(a, j, D.p_star, D.i_trail);
     const uint64_t v = a + ((pj >= 1) ? (1ull << (pj - 1)) : 0ull);
     const double m = mul_pow2(__ull2double_rn(v), -D.k);
     D.out[j] = D.sg[j] ? -m : m;
@@ -947,12 +1556,11 @@ __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) 
   __syncthreads();
   if (s_err) return;
   uint64_t pos = D.boff[b];
-  const uint8_t* ftab = D.sec + 48;
+  const uint8_t* ftab = D.sec + kQHdr;
   const int64_t j0 = lo + (int64_t)tid * kDecPer;  // this thread's first coefficient
   for (int pi = 0; pi < D.nplanes; ++pi) {
     const int p = 63 - pi;
-    int64_t hi = hi_all;
-    if (p == D.p_star && hi > D.i_star + 1) hi = max(lo, D.i_star + 1);
+    const int64_t hl = cat_end(lo, hi_all, p, D.p_star, D.i_lead), ht = cat_end(lo, hi_all, p, D.p_star, D.i_trail);
     for (int i = tid; i < kDecMax / 32; i += kDecThreads) newbm[i] = 0u;
     if (tid == 0) {
       const uint8_t* t = D.sec + D.tab + (b * D.nplanes + pi) * 8;
@@ -962,12 +1570,17 @@ __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) 
       else if (s_rl && s_rl < 4) s_err = 3;
     }
     // 1. rank of every insignificant coefficient among the insignificant ones
+    // active: a significant coefficient before ht (trailing bit), an
+    // insignificant one before hl (leading bit)
     uint32_t sigm = 0, actm = 0;
     for (int u = 0; u < kDecPer; ++u) {
       const int64_t j = j0 + u;
-      if (j < hi) {
-        actm |= 1u << u;
-        if (qs[j - lo] != 0) sigm |= 1u << u;
+      if (j < hi_all) {
+        const bool sg_ = qs[j - lo] != 0;
+        if (sg_ ? j < ht : j < hl) {
+          actm |= 1u << u;
+          if (sg_) sigm |= 1u << u;
+        }
       }
     }
     int64_t n_insig = 0;
@@ -1097,7 +1710,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) 
     if (j >= hi_all) break;
     const uint64_t a = qs[j - lo];
     if (a == 0) { D.out[j] = 0.0; continue; }
-    const int pj = (j <= D.i_star) ? D.p_star : D.p_star + 1;
+    const int pj = lowest_plane(a, j, D.p_star, D.i_trail);
     const uint64_t v = a + ((pj >= 1) ? (1ull << (pj - 1)) : 0ull);
     const double m = mul_pow2(__ull2double_rn(v), -D.k);
     D.out[j] = ss[j - lo] ? -m : m;
@@ -1145,7 +1758,7 @@ __global__ void decode_runs_kernel(RunParams P) {
   if (pos + rl + wl > (uint64_t)P.nbytes) { atomicExch(P.err, 2); *nr = 0; return; }
   if (rl == 0) { *nr = 0; return; }
   if (rl < 4) { atomicExch(P.err, 3); *nr = 0; return; }
-  const uint8_t* ftab = P.sec + 48 + 2 * pi * kNsym;
+  const uint8_t* ftab = P.sec + kQHdr + 2 * pi * kNsym;
   uint32_t f[kNsym], cum[kNsym];
   uint32_t ca = 0;
   int single = -1;
@@ -1209,20 +1822,24 @@ __global__ void __launch_bounds__(kDecThreads) decode_place_kernel(DecParams D, 
   const int64_t j0 = lo + (int64_t)tid * kDecPer;
   for (int pi = 0; pi < D.nplanes; ++pi) {
     const int p = 63 - pi;
-    int64_t hi = hi_all;
-    if (p == D.p_star && hi > D.i_star + 1) hi = max(lo, D.i_star + 1);
+    const int64_t hl = cat_end(lo, hi_all, p, D.p_star, D.i_lead), ht = cat_end(lo, hi_all, p, D.p_star, D.i_trail);
     for (int i = tid; i < kDecMax / 32; i += kDecThreads) newbm[i] = 0u;
     if (tid == 0) {
       const uint8_t* t = D.sec + D.tab + (b * D.nplanes + pi) * 8;
       s_rl = rd32(t);
       s_wl = rd32(t + 4);
     }
+    // active: a significant coefficient before ht (trailing bit), an
+    // insignificant one before hl (leading bit)
     uint32_t sigm = 0, actm = 0;
     for (int u = 0; u < kDecPer; ++u) {
       const int64_t j = j0 + u;
-      if (j < hi) {
-        actm |= 1u << u;
-        if (qs[j - lo] != 0) sigm |= 1u << u;
+      if (j < hi_all) {
+        const bool sg_ = qs[j - lo] != 0;
+        if (sg_ ? j < ht : j < hl) {
+          actm |= 1u << u;
+          if (sg_) sigm |= 1u << u;
+        }
       }
     }
     int64_t n_insig = 0;
@@ -1292,7 +1909,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_place_kernel(DecParams D, 
     if (j >= hi_all) break;
     const uint64_t a = qs[j - lo];
     if (a == 0) { D.out[j] = 0.0; continue; }
-    const int pj = (j <= D.i_star) ? D.p_star : D.p_star + 1;
+    const int pj = lowest_plane(a, j, D.p_star, D.i_trail);
     const uint64_t v = a + ((pj >= 1) ? (1ull << (pj - 1)) : 0ull);
     const double m = mul_pow2(__ull2double_rn(v), -D.k);
     D.out[j] = ss[j - lo] ? -m : m;
@@ -1351,12 +1968,14 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
   const int nseg = (int)((n + seg_len - 1) / seg_len);
   uint8_t* small = nullptr;
   const size_t seg_bytes = sizeof(Seg) * (size_t)nseg * kPlaneChunk;
-  const size_t small_bytes = 4096 + seg_bytes + sizeof(I192) * nseg + 256;
+  const size_t ss_off = (4096 + seg_bytes + sizeof(I192) * nseg + 255) & ~(size_t)255;
+  const size_t small_bytes = ss_off + sizeof(SplitSeg) * nseg + 256;
   ATC_TRY(Scratch::get(SLOT_QPART, small_bytes, (void**)&small));
   TrackState* st = reinterpret_cast<TrackState*>(small);
   unsigned long long* mx = reinterpret_cast<unsigned long long*>(small + 1024);
   Seg* segs = reinterpret_cast<Seg*>(small + 4096);
   I192* e64s = reinterpret_cast<I192*>(small + 4096 + seg_bytes);
+  SplitSeg* sseg = reinterpret_cast<SplitSeg*>(small + ss_off);
   ATC_CUDA_TRY(cudaMemsetAsync(small, 0, 4096, s));
   const int64_t gb = (n + 255) / 256;
   const int grid = (int)(gb < 152 * 8 ? gb : 152 * 8);
@@ -1395,64 +2014,141 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
   if (hst.p_star < 64 && hst.reachable) {
     istar_kernel<<<1, kIstarThreads, 0, s>>>(q, n, seg_len, segs, nseg, phi, st);
     ATC_LAUNCHED(1);
-    ATC_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
-    ATC_CUDA_TRY(cudaStreamSynchronize(s));
   }
   const int k = hst.k;
   const int p_star = hst.p_star;
-  int64_t i_star = hst.i_star;
-  if (i_star < 0) i_star = n - 1;
-  ATC_CUDA_TRY(cudaEventRecord(e1, s));
-  // ------------------------------------------------ encoding
   const int nplanes = (p_star >= 64) ? 0 : 64 - p_star;
   const int64_t nblocks = (n + block_size - 1) / block_size;
   const int64_t nchunks = nblocks * nplanes;
-  const size_t hdr = 48 + (size_t)nplanes * kNsym * 2;
-  const size_t tabb = (size_t)nchunks * 8;
-  std::vector<uint8_t> head(hdr, 0);
-  memcpy(head.data(), "ATCQ", 4);
-  put32(head.data() + 4, 1);
-  put64(head.data() + 8, (uint64_t)n);
-  put32(head.data() + 16, (uint32_t)k);
-  put32(head.data() + 20, (uint32_t)block_size);
-  put32(head.data() + 24, (uint32_t)p_star);
-  put32(head.data() + 28, 0);
-  put64(head.data() + 32, (uint64_t)i_star);
-  put32(head.data() + 40, (uint32_t)nplanes);
-  put32(head.data() + 44, kNsym);
-  std::string result;
+  const bool block_path = block_size <= kEncBlockMax;
+  // encoder scratch for planes 63 .. p_star (the cost pass of plane p_star + 1
+  // alone, which sets the split priority, runs in the same buffers first)
+  unsigned long long* hist = nullptr;
+  uint32_t *fc = nullptr, *rsize = nullptr, *wsize = nullptr;
+  uint64_t* off = nullptr;
+  uint32_t* spill = nullptr;
+  BlockEncParams B;
+  RansThreadParams R;
+  EncParams P;
+  memset(&B, 0, sizeof(B));
+  memset(&R, 0, sizeof(R));
+  memset(&P, 0, sizeof(P));
   if (nplanes > 0) {
     uint8_t* enc = nullptr;
     const size_t enc_small = sizeof(unsigned long long) * nplanes * kNsym + sizeof(uint32_t) * 2 * nplanes * kNsym +
                              sizeof(uint32_t) * 2 * nchunks + sizeof(uint64_t) * (nchunks + 1) + 1024;
     ATC_TRY(Scratch::get(SLOT_ENC, enc_small, (void**)&enc));
-    unsigned long long* hist = reinterpret_cast<unsigned long long*>(enc);
-    uint32_t* fc = reinterpret_cast<uint32_t*>(hist + nplanes * kNsym);
-    uint32_t* rsize = fc + 2 * nplanes * kNsym;
-    uint32_t* wsize = rsize + nchunks;
-    uint64_t* off = reinterpret_cast<uint64_t*>(((uintptr_t)(wsize + nchunks) + 7) & ~(uintptr_t)7);
-    ATC_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nplanes * kNsym, s));
-    uint32_t* spill = nullptr;
-    if (block_size >= kMaxRuns)
-      ATC_TRY(Scratch::get(SLOT_SPILL, sizeof(uint32_t) * (size_t)nchunks * (block_size + 1), (void**)&spill));
-    EncParams P;
-    P.q = q; P.sg = sg; P.n = n; P.block_size = block_size; P.p_star = p_star; P.i_star = i_star;
-    P.nplanes = nplanes; P.nblocks = nblocks; P.hist = hist; P.freq = fc; P.rsize = rsize; P.wsize = wsize;
-    P.off = off; P.out = nullptr; P.table = nullptr;
-    const int wpb = 4;
-    const unsigned eg = (unsigned)((nchunks + wpb - 1) / wpb);
-    {
-      KTimed kt_(s, "enc_hist_kernel");
-      enc_hist_kernel<<<eg, 32 * wpb, 0, s>>>(P);
+    hist = reinterpret_cast<unsigned long long*>(enc);
+    fc = reinterpret_cast<uint32_t*>(hist + nplanes * kNsym);
+    rsize = fc + 2 * nplanes * kNsym;
+    wsize = rsize + nchunks;
+    off = reinterpret_cast<uint64_t*>(((uintptr_t)(wsize + nchunks) + 7) & ~(uintptr_t)7);
+    if (block_path) {
+      B.q = q; B.sg = sg; B.n = n; B.block_size = block_size; B.p_star = p_star;
+      B.nblocks = nblocks;
+      B.run_slot = (int64_t)block_size + nplanes;
+      B.raw_slot = (int64_t)nplanes * (block_size / 8 + 1);
+      uint8_t* work = nullptr;
+      const size_t runs_b = sizeof(uint32_t) * (size_t)nblocks * (size_t)B.run_slot;
+      const size_t raw_b = ((size_t)nblocks * (size_t)B.raw_slot + 255) & ~(size_t)255;
+      const size_t meta_b = sizeof(uint32_t) * 4 * (size_t)nchunks + 256;
+      ATC_TRY(Scratch::get(SLOT_SPILL, runs_b + raw_b + meta_b, (void**)&work));
+      B.runs = reinterpret_cast<uint32_t*>(work);
+      B.raw = work + runs_b;
+      B.nruns = reinterpret_cast<uint32_t*>(work + runs_b + raw_b);
+      B.run_off = B.nruns + nchunks;
+      B.raw_off = B.run_off + nchunks;
+      B.wsize = wsize;
+      B.hist = hist;
+      R.runs = B.runs; R.raw = B.raw; R.run_slot = B.run_slot; R.raw_slot = B.raw_slot;
+      R.nruns = B.nruns; R.run_off = B.run_off; R.raw_off = B.raw_off; R.wsize = wsize;
+      R.freq = fc; R.rsize = rsize; R.off = off;
+    } else {
+      if (block_size >= kMaxRuns)
+        ATC_TRY(Scratch::get(SLOT_SPILL, sizeof(uint32_t) * (size_t)nchunks * (block_size + 1), (void**)&spill));
+      P.q = q; P.sg = sg; P.n = n; P.block_size = block_size; P.p_star = p_star;
+      P.nblocks = nblocks; P.hist = hist; P.freq = fc; P.rsize = rsize; P.wsize = wsize; P.off = off;
     }
-    ATC_LAUNCHED(1);
-    freq_kernel<<<(nplanes + 63) / 64, 64, 0, s>>>(hist, nplanes, fc);
-    ATC_LAUNCHED(1);
-    {
+  }
+  // passes over `np` planes from p_top: histograms, tables, rANS sizes
+  auto size_pass = [&](int p_top, int np, int64_t il, int64_t it) -> int {
+    const int64_t nch = nblocks * np;
+    ATC_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * np * kNsym, s));
+    if (block_path) {
+      B.p_top = p_top; B.nplanes = np; B.i_lead = il; B.i_trail = it;
+      {
+        KTimed kt_(s, "enc_block_kernel", (double)n * 9.0 + (double)nblocks * (double)B.run_slot * 4.0 * np / nplanes);
+        enc_block_kernel<<<(unsigned)nblocks, kEncBlockThreads, 0, s>>>(B);
+      }
+      ATC_LAUNCHED(1);
+      freq_kernel<<<(np + 63) / 64, 64, 0, s>>>(hist, np, fc);
+      ATC_LAUNCHED(1);
+      R.nplanes = np;
+      R.nchunks = nch;
+      KTimed kt_(s, "enc_rans_thread_kernel(sizes)");
+      enc_rans_thread_kernel<<<(unsigned)((nch + 127) / 128), 128, 0, s>>>(R, 0);
+    } else {
+      P.p_top = p_top; P.nplanes = np; P.i_lead = il; P.i_trail = it;
+      const int wpb = 4;
+      {
+        KTimed kt_(s, "enc_hist_kernel");
+        enc_hist_kernel<<<(unsigned)((nch + wpb - 1) / wpb), 32 * wpb, 0, s>>>(P);
+      }
+      ATC_LAUNCHED(1);
+      freq_kernel<<<(np + 63) / 64, 64, 0, s>>>(hist, np, fc);
+      ATC_LAUNCHED(1);
       KTimed kt_(s, "enc_rans_kernel(sizes)");
-      enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 1, spill);
+      enc_rans_kernel<<<(unsigned)((nch + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 1, spill);
     }
     ATC_LAUNCHED(1);
+    return ATC_OK;
+  };
+  // split truncation of plane p_star (Supplement S.3)
+  if (nplanes > 0) {
+    {
+      KTimed kt_(s, "split_stats_kernel", (double)n * 8.0);
+      split_stats_kernel<<<nseg, kSegThreads, 0, s>>>(q, n, seg_len, p_star, sseg);
+    }
+    ATC_LAUNCHED(1);
+    int64_t ncost = 0;
+    if (p_star <= 62) {
+      ATC_TRY(size_pass(p_star + 1, 1, -1, -1));
+      ncost = nblocks;
+    }
+    {
+      KTimed kt_(s, "split_kernel");
+      split_kernel<<<1, kIstarThreads, 0, s>>>(q, n, seg_len, sseg, nseg, p_star, rsize, ncost, st);
+    }
+    ATC_LAUNCHED(1);
+  }
+  ATC_CUDA_TRY(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+  ATC_CUDA_TRY(cudaStreamSynchronize(s));
+  int prio = 0;
+  int64_t i_lead = n - 1, i_trail = n - 1;
+  if (nplanes > 0) {
+    prio = hst.prio;
+    i_lead = hst.i_lead;
+    i_trail = hst.i_trail;
+  }
+  ATC_CUDA_TRY(cudaEventRecord(e1, s));
+  // ------------------------------------------------ encoding
+  const size_t hdr = kQHdr + (size_t)nplanes * kNsym * 2;
+  const size_t tabb = (size_t)nchunks * 8;
+  std::vector<uint8_t> head(hdr, 0);
+  memcpy(head.data(), "ATCQ", 4);
+  put32(head.data() + 4, 2);
+  put64(head.data() + 8, (uint64_t)n);
+  put32(head.data() + 16, (uint32_t)k);
+  put32(head.data() + 20, (uint32_t)block_size);
+  put32(head.data() + 24, (uint32_t)p_star);
+  put32(head.data() + 28, (uint32_t)prio);
+  put64(head.data() + 32, (uint64_t)i_lead);
+  put64(head.data() + 40, (uint64_t)i_trail);
+  put32(head.data() + 48, (uint32_t)nplanes);
+  put32(head.data() + 52, kNsym);
+  std::string result;
+  if (nplanes > 0) {
+    ATC_TRY(size_pass(63, nplanes, i_lead, i_trail));
     scan_kernel<<<1, 1024, 0, s>>>(rsize, wsize, nchunks, off);
     ATC_LAUNCHED(1);
     uint64_t* ptotal = reinterpret_cast<uint64_t*>(hstp + 1);
@@ -1462,14 +2158,19 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     ATC_CUDA_TRY(cudaStreamSynchronize(s));
     const uint64_t total = *ptotal;
     for (int i = 0; i < nplanes * kNsym; ++i) {
-      head[48 + 2 * i] = (uint8_t)hfc[i];
-      head[48 + 2 * i + 1] = (uint8_t)(hfc[i] >> 8);
+      head[kQHdr + 2 * i] = (uint8_t)hfc[i];
+      head[kQHdr + 2 * i + 1] = (uint8_t)(hfc[i] >> 8);
     }
     uint8_t* dout = nullptr;
     ATC_TRY(Scratch::get(SLOT_OUT, tabb + total + 64, (void**)&dout));
-    P.table = reinterpret_cast<uint32_t*>(dout);
-    P.out = dout + tabb;
-    {
+    if (block_path) {
+      R.table = reinterpret_cast<uint32_t*>(dout);
+      R.out = dout + tabb;
+      KTimed kt_(s, "enc_rans_thread_kernel");
+      enc_rans_thread_kernel<<<(unsigned)((nchunks + 127) / 128), 128, 0, s>>>(R, 1);
+    } else {
+      P.table = reinterpret_cast<uint32_t*>(dout);
+      P.out = dout + tabb;
       KTimed kt_(s, "enc_rans_kernel");
       enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 0, spill);
     }
@@ -1494,7 +2195,9 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
   if (res) {
     res->k = k;
     res->p_star = p_star;
-    res->i_star = i_star;
+    res->prio = prio;
+    res->i_lead = i_lead;
+    res->i_trail = i_trail;
     res->sse_pred = ldexp(i192_to_double(hst.e_star), -2 * k);
   }
   out->swap(result);
@@ -1504,19 +2207,19 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
 namespace {
 // Slices of the core that keep a significant coefficient (Section 3.3, the
 // paragraph after Table 2): coefficient j of the vectorised core is significant
-// when one of its encoded bits is a 1 -- planes >= p_star for j <= i_star,
-// >= p_star + 1 after it; its storage-order index on axis a marks slice idx_a
-// of mode perm[a].  A flag is read before it is set, so a slice costs one
+// when one of its encoded bits is a 1 -- its leading 1 lies above p_star, or on
+// p_star with the leading bits of plane p_star encoded through j (j <= i_lead);
+// its storage-order index on axis a marks slice idx_a of mode perm[a].  A flag is read before it is set, so a slice costs one
 // atomic however many significant coefficients it holds.
 struct KeptArgs {
   int d;
   int64_t dim[8];  // storage-order sizes (the vectorisation's row-major shape)
   int off[8];      // first flag of storage axis a
 };
-__global__ void kept_slices_kernel(const uint64_t* __restrict__ q, int64_t n, int p_star, int64_t i_star, KeptArgs a,
+__global__ void kept_slices_kernel(const uint64_t* __restrict__ q, int64_t n, int p_star, int64_t i_lead, KeptArgs a,
                                    unsigned* __restrict__ flags) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    const int lo = (j <= i_star) ? p_star : p_star + 1;
+    const int lo = (j <= i_lead) ? p_star : p_star + 1;
     if (lo >= 64 || (q[j] >> lo) == 0ull) continue;
     int64_t rem = j;
     for (int ax = a.d - 1; ax >= 0; --ax) {
@@ -1532,7 +2235,7 @@ __global__ void kept_slices_kernel(const uint64_t* __restrict__ q, int64_t n, in
 // kept[i][c] (host, sum_i ranks[i] bytes, mode-major) for the core most recently
 // quantized by quantize_encode on this device (its magnitudes are still in the
 // quantizer scratch): 1 where slice c of mode i holds a significant coefficient.
-int core_kept_slices(int64_t n, const int64_t* ranks, const int* perm, int d, int p_star, int64_t i_star,
+int core_kept_slices(int64_t n, const int64_t* ranks, const int* perm, int d, int p_star, int64_t i_lead,
                      uint8_t* kept_host, cudaStream_t s) {
   if (d < 1 || d > 8) return fail(ATC_EINVAL, "core_kept_slices: ndim %d", d);
   int total = 0, moff[8];
@@ -1555,7 +2258,7 @@ int core_kept_slices(int64_t n, const int64_t* ranks, const int* perm, int d, in
     const int64_t gb = (n + 255) / 256;
     const int grid = (int)(gb < 152 * 16 ? gb : 152 * 16);
     KTimed kt_(s, "kept_slices_kernel", (double)n * 8.0);
-    kept_slices_kernel<<<grid, 256, 0, s>>>(q, n, p_star, i_star, a, flags);
+    kept_slices_kernel<<<grid, 256, 0, s>>>(q, n, p_star, i_lead, a, flags);
   }
   ATC_LAUNCHED(1);
   std::vector<unsigned> h((size_t)total);
@@ -1566,27 +2269,33 @@ int core_kept_slices(int64_t n, const int64_t* ranks, const int* perm, int d, in
 }
 
 int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t n, cudaStream_t s) {
-  if (!bytes || nbytes < 48) return fail(ATC_ECORRUPT, "core section too short");
-  if (memcmp(bytes, "ATCQ", 4) != 0 || get32(bytes + 4) != 1) return fail(ATC_ECORRUPT, "bad core section magic/version");
+  if (!bytes || nbytes < (size_t)kQHdr) return fail(ATC_ECORRUPT, "core section too short");
+  if (memcmp(bytes, "ATCQ", 4) != 0 || get32(bytes + 4) != 2) return fail(ATC_ECORRUPT, "bad core section magic/version");
   DecParams D;
   D.n = (int64_t)get64(bytes + 8);
   D.k = (int)get32(bytes + 16);
   D.block_size = (int)get32(bytes + 20);
   D.p_star = (int)get32(bytes + 24);
-  D.i_star = (int64_t)get64(bytes + 32);
-  D.nplanes = (int)get32(bytes + 40);
+  const uint32_t prio = get32(bytes + 28);
+  D.i_lead = (int64_t)get64(bytes + 32);
+  D.i_trail = (int64_t)get64(bytes + 40);
+  D.nplanes = (int)get32(bytes + 48);
   if (D.n != n) return fail(ATC_ECORRUPT, "core size mismatch (%lld vs %lld)", (long long)D.n, (long long)n);
   if (D.block_size < 32 || D.block_size > 65535 || (D.block_size % 32)) return fail(ATC_ECORRUPT, "bad block size");
-  if (get32(bytes + 44) != kNsym) return fail(ATC_ECORRUPT, "bad alphabet size");
+  if (get32(bytes + 52) != kNsym) return fail(ATC_ECORRUPT, "bad alphabet size");
   if (D.p_star < 0 || D.p_star > 64 || D.nplanes != (D.p_star >= 64 ? 0 : 64 - D.p_star))
     return fail(ATC_ECORRUPT, "bad breakpoint plane");
-  if (D.i_star < 0 || D.i_star >= n) return fail(ATC_ECORRUPT, "bad breakpoint index");
+  if (prio > 1) return fail(ATC_ECORRUPT, "bad split priority");
+  // a breakpoint is -1 (nothing of its category on the last plane) .. n - 1
+  if (D.i_lead < -1 || D.i_lead >= n || D.i_trail < -1 || D.i_trail >= n)
+    return fail(ATC_ECORRUPT, "bad breakpoint index");
   D.nblocks = (n + D.block_size - 1) / D.block_size;
-  D.tab = 48 + (int64_t)D.nplanes * kNsym * 2;
+  D.tab = kQHdr + (int64_t)D.nplanes * kNsym * 2;
   if ((uint64_t)D.tab + (uint64_t)D.nblocks * D.nplanes * 8 > nbytes) return fail(ATC_ECORRUPT, "truncated size table");
   for (int pi = 0; pi < D.nplanes; ++pi) {
     uint32_t sum = 0;
-    for (int i = 0; i < kNsym; ++i) sum += (uint32_t)bytes[48 + 2 * (pi * kNsym + i)] | ((uint32_t)bytes[48 + 2 * (pi * kNsym + i) + 1] << 8);
+    for (int i = 0; i < kNsym; ++i)
+      sum += (uint32_t)bytes[kQHdr + 2 * (pi * kNsym + i)] | ((uint32_t)bytes[kQHdr + 2 * (pi * kNsym + i) + 1] << 8);
     if (sum != 0 && sum != kM) return fail(ATC_ECORRUPT, "bad frequency table");
   }
   D.nbytes = (int64_t)nbytes;

@@ -149,7 +149,8 @@ def test_quantizer_bytes_identical(P, n, bs, frac, seed):
     t = frac * float(np.dot(b, b))
     data_gpu, info = P.atc_quantize_core(cuda(b), t, bs)
     data_ref, rinfo = OQ.compress_core(b, t, bs)
-    assert (info["k"], info["p_star"], info["i_star"]) == (rinfo["k"], rinfo["p_star"], rinfo["i_star"])
+    keys = ("k", "p_star", "prio", "i_lead", "i_trail")
+    assert tuple(info[x] for x in keys) == tuple(rinfo[x] for x in keys)
     assert data_gpu == data_ref
     deq = P.atc_dequantize_core(data_ref, n).cpu().numpy()
     _, _, deq_ref = OQ.decode(data_ref)

@@ -231,7 +231,7 @@ def _check_split_against_oracle(P, c, x, eps, ref):
     # in the GPU's own quantized core (the quantizer is bit-exact on it)
     vec = OP.vectorize_core(core, hg["perm"])
     q, _ = OQ.quantize(vec, qg["k"])
-    kept = OP.kept_columns(OP.significant(q, qg["p_star"], qg["i_star"]), hg["ranks"], hg["perm"])
+    kept = OP.kept_columns(OP.significant(q, qg["p_star"], qg["i_lead"]), hg["ranks"], hg["perm"])
     for kg, ke in zip(hg["kept"], kept):
         assert np.array_equal(kg, ke)
     xh = P.atc_decompress(stream).cpu().numpy()

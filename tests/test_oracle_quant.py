@@ -152,10 +152,14 @@ def test_round_trip_and_predicted_error(n, bs, frac):
     qt, sg, deq = Q.decode(data)
     k = info["k"]
     q, s = Q.quantize(b, k)
-    ps, ist = info["p_star"], info["i_star"]
+    ps, il, it = info["p_star"], info["i_lead"], info["i_trail"]
     err = 0
     for i in range(n):
-        p_i = ps if i <= ist else ps + 1
+        # the lowest encoded plane, from the definition: planes above p_star
+        # all; p_star for a significant-above coefficient up to i_trail, for a
+        # not-yet-significant one up to i_lead (Section 3.3, Supplement S.3)
+        above = ps < 63 and (int(q[i]) >> (ps + 1)) != 0
+        p_i = ps if (above and i <= it) or (not above and i <= il) else ps + 1
         keep = 0 if p_i >= 64 else (int(q[i]) >> p_i) << p_i
         assert int(qt[i]) == keep
         if keep:
@@ -173,9 +177,9 @@ def test_round_trip_and_predicted_error(n, bs, frac):
 def test_frequency_tables_are_normalised():
     b = synth.random_core((20, 30, 40), seed=3).ravel()
     data, info = Q.compress_core(b, 1e-6 * float(np.dot(b, b)), 256)
-    nplanes = int.from_bytes(data[40:44], "little")
+    nplanes = int.from_bytes(data[48:52], "little")
     assert nplanes == 64 - info["p_star"]
-    f = np.frombuffer(data, "<u2", nplanes * 17, 48).reshape(nplanes, 17)
+    f = np.frombuffer(data, "<u2", nplanes * 17, 56).reshape(nplanes, 17)
     for row in f:
         assert row.sum() in (0, 4096)
 

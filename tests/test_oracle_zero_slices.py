@@ -4,8 +4,8 @@ coefficients are all insignificant is zero in the decoded core, so the matching
 factor column is not stored.
 
 * significance against a literal bit-by-bit walk of each coefficient's encoded
-  bits (planes 63 down to its lowest encoded plane: p_star up to i_star,
-  p_star + 1 after it);
+  bits (planes 63 down to p_star, the last plane's leading bits up to i_lead
+  and trailing bits up to i_trail);
 * the kept-column maps against brute force over the devectorised core;
 * a hand-built core whose last slices are negligible: those columns are
   dropped and the stream is shorter by exactly 8 n_i bytes per dropped column;
@@ -23,15 +23,18 @@ from oracle import quant as Q
 from oracle import sthosvd as O
 
 
-def _bit_walk_significant(q, p_star, i_star):
+def _bit_walk_significant(q, p_star, i_lead, i_trail):
+    """Walk each coefficient's encoded bits from plane 63 down: planes above
+    p_star all, plane p_star as a leading bit (not yet significant) where
+    j <= i_lead, as a trailing bit where j <= i_trail; significant = a 1 seen."""
     out = []
     for j, v in enumerate(int(x) for x in q):
-        lowest = p_star if j <= i_star else p_star + 1
         sig = False
-        for p in range(63, lowest - 1, -1):
-            if p < 64 and (v >> p) & 1:
-                sig = True
+        for p in range(63, p_star - 1, -1):
+            if p == p_star and not ((sig and j <= i_trail) or (not sig and j <= i_lead)):
                 break
+            if (v >> p) & 1:
+                sig = True
         out.append(sig)
     return np.array(out, dtype=bool)
 
@@ -44,8 +47,8 @@ def test_significance_matches_bit_walk():
         frac = float(10 ** rng.uniform(-9, 0.5))
         _, info = Q.compress_core(b, frac * float(np.dot(b, b)), 64)
         q, _ = Q.quantize(b, info["k"])
-        got = P.significant(q, info["p_star"], info["i_star"])
-        ref = _bit_walk_significant(q, info["p_star"], info["i_star"])
+        got = P.significant(q, info["p_star"], info["i_lead"])
+        ref = _bit_walk_significant(q, info["p_star"], info["i_lead"], info["i_trail"])
         assert np.array_equal(got, ref), trial
 
 
