@@ -275,7 +275,7 @@ def run_reference(args, world, rank):
 
 FP32_OPS_PER_CLK_SM = 128   # FP32 lanes per SM (4 SMSPs x 32)
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal, dense; the profiling recipe's table)
-TENSOR_KERNELS = ("gram_tma_kernel", "ttm_tc_kernel")
+TENSOR_KERNELS = ("gram_raw_kernel", "gram_tma_kernel", "ttm_tc_kernel")
 FP64_KERNELS = ("sub_gemm_part_kernel", "gram_fp64_kernel", "ttm_fp64_kernel")
 DD_KERNELS = ("qr_col_kernel", "sub_qr_kernel", "sub_qform_kernel", "rr_jacobi_kernel")
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
@@ -472,8 +472,8 @@ def run_ours(args, world, rank, local):
     dom = max(ktimes, key=lambda k: ktimes[k]["ms"]) if ktimes else None
     roof = roofline_of(dom, ktimes.get(dom), hbm, bf16s, fp32_peak, fp64_peak, peak_src, sm_mhz, sms, args)
     roof["share_of_step"] = (ktimes[dom]["ms"] / args.steps) / per_ms if dom else None
-    roof_gram = roofline_of("gram_tma_kernel", ktimes.get("gram_tma_kernel"), hbm, bf16s, fp32_peak, fp64_peak,
-                            peak_src, sm_mhz, sms, args)
+    gram_k = next((k for k in ("gram_raw_kernel", "gram_tma_kernel") if k in ktimes), "gram_raw_kernel")
+    roof_gram = roofline_of(gram_k, ktimes.get(gram_k), hbm, bf16s, fp32_peak, fp64_peak, peak_src, sm_mhz, sms, args)
     roof_ttm = roofline_of("ttm_tc_kernel", ktimes.get("ttm_tc_kernel"), hbm, bf16s, fp32_peak, fp64_peak,
                            peak_src, sm_mhz, sms, args)
 

@@ -31,9 +31,8 @@
  *   ATC_TRACE=1 / 2        synchronise after every launch site and report its
  *                          status (2: also the host time since the previous one)
  *   ATC_SUBSPACE=0         split paths: full eigensolver instead of subspace iteration
- *   ATC_RESIDUAL_FUSED=1   split paths: certification residual in the fused
- *                          tensor-core epilogue (no scratch tensor)
- *   ATC_GRAM_CONVERT=1     split paths: converter-warp Gram instead of the TMA-fed one
+ *   ATC_GRAM_CONVERT=1     split paths: converter-warp Gram (global loads) instead of
+ *                          the TMA-fed ones
  *   ATC_BATCH_TUNE=0       batched ST-HOSVD: built-in Gram tile table, no probe
  */
 #ifndef ATC_H

@@ -667,13 +667,11 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   // the largest projected tensor is after the first mode: N * r / n <= N
   void* bufA = nullptr;
   void* bufB = nullptr;
-  void* bufC = nullptr;
   int64_t maxn = 1;
   for (int i = 0; i < d; ++i) maxn = std::max(maxn, dims[i]);
   double *G = nullptr, *lam = nullptr;
   rc = Scratch::get(SLOT_TEN_A, ibytes * (size_t)N, &bufA);
   if (!rc) rc = Scratch::get(SLOT_TEN_B, ibytes * (size_t)N, &bufB);
-  if (!rc && opt.precision != ATC_PREC_FP64) rc = Scratch::get(SLOT_TEN_C, ibytes * (size_t)N, &bufC);
   if (!rc) rc = Scratch::get(SLOT_LAM, sizeof(double) * (size_t)(maxn * maxn + maxn + 64), (void**)&lam);
   if (rc) return bail(rc);
   G = lam + maxn + 16;
@@ -688,9 +686,9 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   const void* curp = x_dev;
   int curdt = dtype;
   void* next = bufA;
-  // a work buffer that is neither `a` nor `b` (three exist on the split paths)
+  // a work buffer that is neither `a` nor `b`
   auto other = [&](const void* a, const void* b) -> void* {
-    for (void* q : {bufA, bufB, bufC})
+    for (void* q : {bufA, bufB})
       if (q && q != a && q != b) return q;
     return nullptr;
   };
@@ -721,14 +719,15 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
       const double budget =
           (opt.rank_rule == ATC_RANK_STATIC) ? budget_total / d : (budget_total - used) / (double)(d - step);
       {
-        // Split paths: the sliced Gram is that of X rounded to 24-bit fixed
-        // point, summed in FP32 orders; its eigenvalues carry a small shift,
-        // far below what moves the eigenvectors but not always below the
-        // distance of the tail from the budget.  So the rank is certified on
-        // the tensor itself: with U the leading rh eigenvectors and
-        // Y = U^T ._m X (tensor cores),
-        //   tail(r) = ||X - U ._m Y||^2 + sum_{j >= r} ||Y_j||^2   (U orthonormal),
-        // which is second order in the rounding errors of Y and U.
+        // Split paths: the rank is certified from the candidate factor itself.
+        // With U the leading rh eigenvector estimates (orthonormal to ~1e-15)
+        // and G the tensor-core Gram matrix of X on its 24-bit grid X~,
+        //   tail(r) = ||X~||^2 - ||U_r^T X~||^2 = trace(G) - sum_{j<r} u_j^T G u_j
+        // (FP64), exact for whatever subspace U spans: no eigenvalue of G is
+        // trusted, and the difference to the tail of X itself is second order in
+        // the 24-bit rounding (its cross term with the residual scales with the
+        // square root of the tail).  Then the factor is the leading r columns and
+        // the projection runs once with exactly r outputs.
         // certify(): 1 = rank and factor set, 0 = it needs more than rh_cap
         // candidate vectors, < 0 = error.
         int he = 0;  // tensor-core wait flag, read with the host readbacks
@@ -737,50 +736,49 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
             double* cand = nullptr;
             int rc2 = Scratch::get(SLOT_CAND, sizeof(double) * ((size_t)n * rh + rh + 8), (void**)&cand);
             if (rc2) return rc2;
-            double* edev = cand + (size_t)n * rh;  // e[0..rh), then rho
+            double* edev = cand + (size_t)n * rh;  // rho[0..rh), then trace(G)
             rc2 = get_cand(rh, cand);
-            if (!rc2) rc2 = ttm_dispatch(curp, curdt, L, n, R, cand, rh, 0, opt.precision, next, idt, s, xs);
-            if (!rc2) rc2 = launch_ttm_residual((const float*)next, L, rh, R, cand, n, curp, curdt, edev + rh, s);
-            if (!rc2) rc2 = launch_row_energy((const float*)next, L, rh, R, edev, s);
+            if (!rc2) rc2 = launch_rayleigh(G, n, cand, rh, edev, s);
             if (rc2) return rc2;
-            std::vector<double> t((size_t)rh + 1);
             PinnedReadback pb;
             rc2 = pinned_readback((size_t)rh + 1, &pb);
             if (rc2) return rc2;
             const double* eh = pb.dbl;
             if (cudaMemcpyAsync(pb.dbl, edev, sizeof(double) * (rh + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                 cudaMemcpyAsync(&pb.ints[1], tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-              return fail(ATC_ECUDA, "residual readback failed");
+              return fail(ATC_ECUDA, "Rayleigh quotient readback failed");
             rc2 = eig_check(s);
             if (rc2) return rc2;
             he = pb.ints[1];
             if (he) return fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)");
-            t[rh] = (rh == n) ? 0.0 : eh[rh];
-            for (int j = rh - 1; j >= 0; --j) t[j] = t[j + 1] + eh[j];
+            const double tr = eh[rh];
             int rn = -1;
-            for (int rr = 1; rr <= rh; ++rr)
-              if (t[rr] <= budget) { rn = rr; break; }
+            double tail = 0.0, acc = 0.0;
+            for (int rr = 1; rr <= rh; ++rr) {
+              acc += eh[rr - 1];
+              double t = tr - acc;
+              if (t < 0.0) t = 0.0;
+              if (t <= budget) { rn = rr; tail = t; break; }
+            }
             if (rn < 0 && rh < n) {
               const int nrh = (int)std::min<int64_t>(n, 2 * (int64_t)rh);
               if (nrh > rh_cap) return 0;
               rh = nrh;
               continue;
             }
-            if (rn < 0) rn = (int)n;
+            if (rn < 0) {
+              rn = (int)n;
+              tail = std::max(0.0, tr - acc);
+            }
             r = rn;
-            disc = t[rn];
+            disc = tail;
             if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
               return fail(ATC_ENOMEM, "factor allocation failed");
             if (cudaMemcpy2DAsync(c->factors[m], sizeof(double) * r, cand, sizeof(double) * rh, sizeof(double) * r, n,
                                   cudaMemcpyDeviceToDevice, s) != cudaSuccess)
               return fail(ATC_ECUDA, "factor copy failed");
-            if (r < rh && L > 1) {
-              // keep the leading r of the rh projected rows (for L == 1 they already form the prefix)
-              void* tgt = other(next, curp);
-              rc2 = launch_compact((const float*)next, L, rh, R, r, (float*)tgt, s);
-              if (rc2) return rc2;
-              next = tgt;
-            }
+            rc2 = ttm_dispatch(curp, curdt, L, n, R, c->factors[m], r, 0, opt.precision, next, idt, s, xs);
+            if (rc2) return rc2;
             have_y = true;
             return 1;
           }

@@ -71,9 +71,7 @@ enum ScratchSlot {
   SLOT_DEC2,
   SLOT_FAC,            // uploaded factors
   SLOT_TC_ERR,         // tensor-core kernels' error word + pre-scales
-  SLOT_ENERGY,         // row-energy partials
-  SLOT_TEN_C,          // third tensor buffer (compaction target)
-  SLOT_CAND,           // candidate factor of the residual-certified rank choice
+  SLOT_CAND,           // candidate factor of the certified rank choice + its Rayleigh quotients
   SLOT_DEC_RUNS,       // decoded run lengths per (block, plane)
   SLOT_SLICES,         // integer slice planes of the Gram input
   SLOT_ADJ_A,          // adjoint / expansion chains
@@ -83,9 +81,7 @@ enum ScratchSlot {
   SLOT_SUBSPACE,       // subspace-iteration blocks
   SLOT_SUB_U,          // subspace-iteration Ritz vectors
   SLOT_SUB_V0,         // subspace-iteration start frame (kept while n and K stay the same)
-  SLOT_TTM_AIMG,       // pre-sliced data operand of single-K-tile products
-  SLOT_RES_TMP,        // reproduction U ._k Y of the certification residual
-  SLOT_RES_PART,       // its partial sums
+  SLOT_TTM_AIMG,       // pre-sliced data operand of products with several output chunks
   SLOT_KEPT,           // per-slice significance flags of the quantized core
   SLOT_COUNT
 };
@@ -94,13 +90,12 @@ enum ScratchSlot {
 // norm / reductions (k_reduce.cu)
 int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s);
 // *out = sum (x - z)^2 over n elements, x FP32/FP64 (dtype), z FP32; FP64 result
-int launch_diff_norm2(const void* x, int dtype, const float* z, int64_t n, double* out, cudaStream_t s);
 int launch_convert_to_f64(const void* x, int dtype, int64_t n, double* y, cudaStream_t s);
 int launch_convert_f64_to(const double* x, int64_t n, void* y, int dtype, cudaStream_t s);
 // e[j] = sum over (l, c) of y[(l r + j) R + c]^2 in FP64 (fixed order)
-int launch_row_energy(const float* y, int64_t L, int64_t r, int64_t R, double* e, cudaStream_t s);
+// out[j] = u_j^T G u_j for the rh columns of U (n x rh row-major, FP64), out[rh] = trace(G); n <= 1024
+int launch_rayleigh(const double* G, int64_t n, const double* U, int rh, double* out, cudaStream_t s);
 // (L, rh, R) -> (L, r, R): the leading r of every rh rows
-int launch_compact(const float* y, int64_t L, int64_t rh, int64_t R, int64_t r, float* out, cudaStream_t s);
 int launch_permute(const double* x, const int64_t* dims, const int* perm, int ndim, double* y, int inverse,
                    cudaStream_t s);
 
@@ -127,11 +122,6 @@ int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R,
 int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
                      int expand, int precision, void* y, int ydtype, cudaStream_t s,
                      const SliceScale* xs = nullptr);
-// *rho = sum (x - U ._k y)^2 over the (L, n, R) tensor x (FP32 or FP64), with
-// y the (L, r, R) FP32 projection and U the n x r FP64 factor, on the tensor
-// cores (expansion with fixed-point slices, residual fused into the epilogue)
-int launch_ttm_residual(const float* y, int64_t L, int64_t r, int64_t R, const double* u, int64_t n, const void* x,
-                        int xdtype, double* rho, cudaStream_t s);
 
 // eigensolver (k_eig.cu)
 int launch_eig_sym(const double* g, int n, double* lam, double* v, int nvec, cudaStream_t s);

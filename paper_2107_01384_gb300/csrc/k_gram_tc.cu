@@ -546,6 +546,277 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   if (tid == 0 && abort_flag) atomicExch(a.err, 1);
 }
 
+// --------------------------- in-kernel unfolding: raw tiles by TMA, sliced here
+// FP32 input whose mode-k unfolding tiles are boxes of a tensor map: R = 1
+// (X is (L, n), a K tile is 32 consecutive rows l, the box {128 i, 32 l}) or
+// R a multiple of 64 (a K tile of 32 lies inside one l: the box {32 r, 128 i,
+// 1 l} over (R, n, L)).  Warp 0 streams raw A (128 rows) and B (64 rows)
+// tiles of 32 K values into a ring of shared-memory buffers with TMA tensor
+// copies -- the unfolding is the box geometry, nothing is transposed or
+// written back to HBM; warps 6-21 cut two raw halves at a time into the three
+// 16-bit slice planes of a K-major 128-byte-swizzled stage (tc::slice3i, the
+// tensor's power-of-two scale; sixteen warps, so that the dependent
+// add/multiply chains of the slicing overlap); warp 1 issues the nine slice
+// products per K step into the five order accumulators; warps 2-5 and 22-25
+// (two per TMEM lane quarter, 32 columns each) flush each exact window into a
+// double-float sum kept in TMEM columns [320, 448).
+constexpr int kRawConvWarps = 16;
+constexpr int kRawConvThreads = kRawConvWarps * 32;
+constexpr int kRawFlushThreads = 256;
+constexpr int kRawThreads = (6 + kRawConvWarps + 4) * 32;  // 832
+constexpr int kRawHalf = 32;                            // K values per raw tile
+constexpr int kRawStages = 3;
+constexpr uint32_t kRawA = TM * kRawHalf * 4, kRawB = TN * kRawHalf * 4;  // 16 KB, 8 KB
+constexpr int kRawConvStages = 2;
+constexpr int kRawStage = 3 * (SLOT_A + SLOT_B);  // 72 KB of slices
+constexpr int kRawSmem = kRawConvStages * kRawStage + kRawStages * (int)(kRawA + kRawB) + 1024;
+constexpr int kRawUnits = ROWS * 8 / kRawConvThreads;  // 3
+static_assert(ROWS * 8 == kRawUnits * kRawConvThreads, "unit split");
+
+struct GramRawArgs {
+  int64_t R;        // 1, or a multiple of 64
+  int64_t kchunk;   // K elements per CTA (multiple of KT)
+  int64_t Kp;       // K rounded up to KT
+  int nsplit, nc64, npair;
+  double* part;
+  const SliceScale* xs;
+  int* err;
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(kRawThreads, 1)
+    gram_raw_kernel(const __grid_constant__ CUtensorMap mapa, const __grid_constant__ CUtensorMap mapb, GramRawArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full_bar[kRawConvStages], empty_bar[kRawConvStages], raw_full[kRawStages], raw_empty[kRawStages];
+  __shared__ uint64_t accf_bar, acce_bar, done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* rawbuf = smem + kRawConvStages * kRawStage;
+  volatile int* abort = &abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int pair = blockIdx.x / a.nsplit, split = blockIdx.x % a.nsplit;
+  int ti, cj;
+  tile_of(pair, a.nc64, ti, cj);
+  const int64_t kb = (int64_t)split * a.kchunk;
+  const int64_t ke = min(a.Kp, kb + a.kchunk);
+  const int ntiles = (ke > kb) ? (int)((ke - kb) / KT) : 0;
+  const int nhalves = 2 * ntiles;
+  const int ngroups = (ntiles + FLUSH - 1) / FLUSH;
+  if (tid == 0) {
+    for (int s = 0; s < kRawConvStages; ++s) {
+      mbar_init(&full_bar[s], kRawConvThreads);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int s = 0; s < kRawStages; ++s) {
+      mbar_init(&raw_full[s], 1);
+      mbar_init(&raw_empty[s], kRawConvThreads);
+    }
+    mbar_init(&accf_bar, 1);
+    mbar_init(&acce_bar, kRawFlushThreads);
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------- raw-tile producer (TMA)
+    if (lane == 0) {
+      int issued = 0;
+      for (int h = 0; h < nhalves; ++h) {
+        const int rs = h % kRawStages;
+        if (!mbar_wait(&raw_empty[rs], ((uint32_t)(h / kRawStages) & 1u) ^ 1u, abort)) break;
+        uint8_t* dst = rawbuf + (size_t)rs * (kRawA + kRawB);
+        mbar_arrive_expect_tx(&raw_full[rs], kRawA + kRawB);
+        const int64_t k0 = kb + (int64_t)h * kRawHalf;
+        if (a.R == 1) {
+          tma_load_2d(dst, &mapa, &raw_full[rs], ti * TM, (int)k0);
+          tma_load_2d(dst + kRawA, &mapb, &raw_full[rs], cj * TN, (int)k0);
+        } else {
+          const int64_t l = k0 / a.R, r0 = k0 - l * a.R;
+          tma_load_3d(dst, &mapa, &raw_full[rs], (int)r0, ti * TM, (int)l);
+          tma_load_3d(dst + kRawA, &mapb, &raw_full[rs], (int)r0, cj * TN, (int)l);
+        }
+        issued = h + 1;
+      }
+      for (int h = (issued > kRawStages ? issued - kRawStages : 0); h < issued; ++h)
+        mbar_wait_drain(&raw_full[h % kRawStages], (uint32_t)(h / kRawStages) & 1u);
+    }
+  } else if (warp >= 6 && warp < 6 + kRawConvWarps) {
+    // ---------------------------------------------------------- converters
+    const int ct = tid - 6 * 32;
+    const float sc = ldexpf(1.0f, a.xs->shift);
+    const bool rows_k = a.R != 1;  // raw tiles [row][k] (else [k][row])
+    for (int t = 0; t < ntiles; ++t) {
+      const int h0 = 2 * t, h1 = 2 * t + 1;
+      const int r0s = h0 % kRawStages, r1s = h1 % kRawStages;
+      if (!mbar_wait(&raw_full[r0s], (uint32_t)(h0 / kRawStages) & 1u, abort)) break;
+      if (!mbar_wait(&raw_full[r1s], (uint32_t)(h1 / kRawStages) & 1u, abort)) break;
+      const int s = t % kRawConvStages;
+      if (!mbar_wait(&empty_bar[s], ((uint32_t)(t / kRawConvStages) & 1u) ^ 1u, abort)) break;
+      const float* raw0 = reinterpret_cast<const float*>(rawbuf + (size_t)r0s * (kRawA + kRawB));
+      const float* raw1 = reinterpret_cast<const float*>(rawbuf + (size_t)r1s * (kRawA + kRawB));
+      uint8_t* st = smem + (size_t)s * kRawStage;
+#pragma unroll
+      for (int u = 0; u < kRawUnits; ++u) {
+        const int g = ct + kRawConvThreads * u;
+        // unit = (row of the A and B blocks stacked, group q of 8 K values);
+        // q < 4 from the first raw half, q >= 4 from the second
+        int row, q;
+        if (rows_k) { row = g >> 3; q = g & 7; } else { row = g % ROWS; q = g / ROWS; }
+        const bool isb = row >= TM;
+        const int rr = isb ? row - TM : row;
+        const float* hb = (q < 4) ? raw0 : raw1;
+        const float* tile = isb ? hb + kRawA / 4 : hb;
+        const int kk = 8 * (q & 3);
+        float v[8];
+        if (rows_k) {
+          const float4* p4 = reinterpret_cast<const float4*>(tile + rr * kRawHalf + kk);
+          const float4 x0 = p4[0], x1 = p4[1];
+          v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+          v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+        } else {
+          const int ld = isb ? TN : TM;  // raw [k][row], rows contiguous
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = tile[(kk + e) * ld + rr];
+        }
+        uint32_t p0[4], p1[4], p2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float a0x, a1x, a2x, a0y, a1y, a2y;
+          slice3i(v[2 * e] * sc, a0x, a1x, a2x);
+          slice3i(v[2 * e + 1] * sc, a0y, a1y, a2y);
+          p0[e] = Pack<BF16>::two(a0x, a0y);
+          p1[e] = Pack<BF16>::two(a1x, a1y);
+          p2[e] = Pack<BF16>::two(a2x, a2y);
+        }
+        uint8_t* base = isb ? st + 3 * SLOT_A : st;
+        const uint32_t slot = isb ? SLOT_B : SLOT_A;
+        const uint32_t off = sw128_off((uint32_t)rr, (uint32_t)(8 * q));
+        *reinterpret_cast<uint4*>(base + off) = make_uint4(p0[0], p0[1], p0[2], p0[3]);
+        *reinterpret_cast<uint4*>(base + slot + off) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
+        *reinterpret_cast<uint4*>(base + 2 * slot + off) = make_uint4(p2[0], p2[1], p2[2], p2[3]);
+      }
+      mbar_arrive(&raw_empty[r0s]);
+      mbar_arrive(&raw_empty[r1s]);
+      fence_proxy_async_smem();
+      mbar_arrive(&full_bar[s]);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16(BF16 ? 1 : 0, TM, TN);
+      bool ok = true;
+      for (int g = 0; g < ngroups && ok; ++g) {
+        if (!mbar_wait(&acce_bar, ((uint32_t)g & 1u) ^ 1u, abort)) break;
+        tc_fence_after();
+        const int t1 = min(ntiles, (g + 1) * FLUSH);
+        for (int t = g * FLUSH; t < t1; ++t) {
+          const int s = t % kRawConvStages;
+          if (!mbar_wait(&full_bar[s], (uint32_t)(t / kRawConvStages) & 1u, abort)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + (size_t)s * kRawStage), sb = sa + 3 * SLOT_A;
+#pragma unroll
+          for (int j = 0; j < KT / 16; ++j) {
+            const uint32_t acc = (t == g * FLUSH && j == 0) ? 0u : 1u;
+            const uint32_t o = 32u * j;
+#pragma unroll
+            for (int od = 0; od <= 4; ++od) {
+              bool first = true;
+#pragma unroll
+              for (int sa_i = 0; sa_i < 3; ++sa_i) {
+                const int tb_i = od - sa_i;
+                if (tb_i < 0 || tb_i >= 3) continue;
+                umma_f16(tmem + 64u * od, desc_k128(sa + sa_i * SLOT_A + o), desc_k128(sb + tb_i * SLOT_B + o), idesc,
+                         first ? acc : 1u);
+                first = false;
+              }
+            }
+          }
+          umma_commit(&empty_bar[s]);
+        }
+        if (ok) umma_commit(&accf_bar);
+      }
+      umma_commit(&done_bar);
+      mbar_wait_drain(&done_bar, 0);
+    }
+  } else {
+    // ------------------------- flush into the TMEM (hi, lo) pair and epilogue
+    // (the running double-float sum lives in TMEM columns [320, 448): the
+    // converter warps leave too few registers to hold it)
+    const int w = warp & 3;                             // TMEM lane quarter of this warp
+    const uint32_t cb = (warp >= 6 + kRawConvWarps) ? 32u : 0u;  // this warp's 32 columns
+    const uint32_t tl = tmem + ((uint32_t)(32 * w) << 16) + cb;
+    const uint32_t thi = tl + 320u, tlo = tl + 384u;
+    bool ok = true;
+    for (int g = 0; g < ngroups; ++g) {
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(&accf_bar, (uint32_t)g & 1u, abort) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      __syncwarp();
+      if (!okw) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll 1
+      for (int c0 = 0; c0 < 32; c0 += 8) {
+        uint32_t r0[8], r1[8], r2[8], r3[8], r4[8], rh[8], rl[8];
+        tmem_ld8(tl + c0, r0);
+        tmem_ld8(tl + 64u + c0, r1);
+        tmem_ld8(tl + 128u + c0, r2);
+        tmem_ld8(tl + 192u + c0, r3);
+        tmem_ld8(tl + 256u + c0, r4);
+        if (g > 0) {
+          tmem_ld8(thi + c0, rh);
+          tmem_ld8(tlo + c0, rl);
+        }
+        tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          float sv, tv, s1, e1;
+          combine_orders(__uint_as_float(r0[e]), __uint_as_float(r1[e]), __uint_as_float(r2[e]),
+                         __uint_as_float(r3[e]), __uint_as_float(r4[e]), sv, tv);
+          const float h0 = (g > 0) ? __uint_as_float(rh[e]) : 0.f, l0 = (g > 0) ? __uint_as_float(rl[e]) : 0.f;
+          two_sum(h0, sv, s1, e1);
+          e1 += l0 + tv;
+          const float h2 = s1 + e1;
+          rh[e] = __float_as_uint(h2);
+          rl[e] = __float_as_uint(e1 - (h2 - s1));
+        }
+        tmem_st8(thi + c0, rh);
+        tmem_st8(tlo + c0, rl);
+      }
+      tmem_st_wait();
+      tc_fence_before();
+      mbar_arrive(&acce_bar);
+    }
+    ok = ok && !abort_flag && ngroups > 0;
+    double* out = a.part + ((int64_t)split * a.npair + pair) * (TM * TN) + (int64_t)cb * TM;
+#pragma unroll 1
+    for (int c0 = 0; c0 < 32; c0 += 8) {
+      uint32_t rh[8], rl[8];
+      if (ok) {
+        tmem_ld8(thi + c0, rh);
+        tmem_ld8(tlo + c0, rl);
+        tmem_ld_wait();
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const double v = ok ? (double)__uint_as_float(rh[e]) + (double)__uint_as_float(rl[e]) : 0.0;
+        out[(int64_t)(c0 + e) * TM + 32 * w + lane] = v;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+  if (tid == 0 && abort_flag) atomicExch(a.err, 1);
+}
+
 // Slices of the (L, n, R) tensor into three 16-bit planes laid out (n, Kp):
 // plane[i][k] for k = l R + r (zero for k >= K).  For R = 1 the reads along k
 // are strided by n, so that case goes through a 32 x 32 shared-memory transpose.
@@ -729,6 +1000,29 @@ bool gram_tma_off() {
 // layout of the SLOT_TC_ERR scratch: error word at byte 0, slice scales from byte 64
 int tc_error_flag(int** flag) { return Scratch::get(SLOT_TC_ERR, 1024, (void**)flag); }
 
+// Map over FP32 data of `rank` dimensions (innermost first: dims[0] elements
+// contiguous, strides[d - 1] bytes between consecutive indices of dimension
+// d), no swizzle, out-of-range elements read as zero.
+int make_raw_map_f32(CUtensorMap* m, const void* base, int rank, const int64_t* dims, const int64_t* strides,
+                     const uint32_t* box) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(ATC_EUNSUP, "cuTensorMapEncodeTiled unavailable");
+  if (rank < 1 || rank > 5) return fail(ATC_EINVAL, "bad tensor map rank %d", rank);
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = (cuuint64_t)dims[i];
+    bx[i] = box[i];
+    es[i] = 1u;
+    if (i > 0) st[i - 1] = (cuuint64_t)strides[i - 1];
+  }
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base), d, st, bx, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ATC_ECUDA, "cuTensorMapEncodeTiled (raw FP32) failed (%d)", (int)r);
+  return ATC_OK;
+}
+
 int slice_scale(const void* x, int dtype, int64_t N, cudaStream_t s, const SliceScale** out) {
   int* base = nullptr;
   ATC_TRY(tc_error_flag(&base));
@@ -795,8 +1089,9 @@ int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R,
   for (int ti = 0; ti < nt128; ++ti) npair += nc64 - 2 * ti;
   const int mode = (R == 1) ? LM_IC1 : ((R % 8 == 0) ? LM_KC8 : LM_GEN);
   const int64_t ktiles = (K + KT - 1) / KT;
-  // about one CTA per SM over all tiles, at least two windows per CTA
-  int64_t want = (g_nsm + npair - 1) / npair;
+  // at most one CTA per SM over all tiles (one wave), at least two windows per CTA
+  int64_t want = g_nsm / npair;
+  if (want < 1) want = 1;
   int64_t tpc = (ktiles + want - 1) / want;
   if (tpc < 2 * FLUSH) tpc = 2 * FLUSH;
   int nsplit = (int)((ktiles + tpc - 1) / tpc);
@@ -804,6 +1099,67 @@ int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R,
   if (!xs) ATC_TRY(slice_scale(x, dtype, K * n, s, &xs));
   const bool bf16 = (precision == ATC_PREC_SPLIT_BF16);
   if (!encode_fn() && nslice == 4) return fail(ATC_EUNSUP, "four-slice Gram needs cuTensorMapEncodeTiled");
+  // FP32, three slices, tensor-map geometry: the unfolding tiles come straight
+  // from the tensor by TMA and are sliced in the kernel
+  if (encode_fn() && !gram_tma_off() && nslice == 3 && dtype == ATC_F32 && ((uintptr_t)x & 15u) == 0 &&
+      ((R == 1 && n % 4 == 0) || (R > 1 && R % kRawHalf == 0))) {
+    CUtensorMap ma, mb;
+    int rc = ATC_OK;
+    if (R == 1) {
+      const int64_t dims[2] = {n, L}, strides[1] = {n * 4};
+      const uint32_t boxa[2] = {(uint32_t)TM, (uint32_t)kRawHalf}, boxb[2] = {(uint32_t)TN, (uint32_t)kRawHalf};
+      rc = make_raw_map_f32(&ma, x, 2, dims, strides, boxa);
+      if (!rc) rc = make_raw_map_f32(&mb, x, 2, dims, strides, boxb);
+    } else {
+      const int64_t dims[3] = {R, n, L}, strides[2] = {R * 4, R * n * 4};
+      const uint32_t boxa[3] = {(uint32_t)kRawHalf, (uint32_t)TM, 1u}, boxb[3] = {(uint32_t)kRawHalf, (uint32_t)TN, 1u};
+      rc = make_raw_map_f32(&ma, x, 3, dims, strides, boxa);
+      if (!rc) rc = make_raw_map_f32(&mb, x, 3, dims, strides, boxb);
+    }
+    if (rc == ATC_OK) {
+      GramRawArgs ra;
+      ra.R = R;
+      ra.kchunk = tpc * KT;
+      ra.Kp = ktiles * KT;
+      ra.nsplit = nsplit;
+      ra.nc64 = nc64;
+      ra.npair = npair;
+      ra.xs = xs;
+      const size_t part_elems = (size_t)nsplit * npair * TM * TN;
+      ATC_TRY(Scratch::get(SLOT_GRAM_PART, part_elems * 8 + 1024, (void**)&ra.part));
+      int* err = nullptr;
+      ATC_TRY(tc_error_flag(&err));
+      ra.err = err;
+      const int grid = npair * nsplit;
+      static bool attr_b = false, attr_h = false;
+      bool& attr = bf16 ? attr_b : attr_h;
+      if (!attr) {
+        ATC_CUDA_TRY(cudaFuncSetAttribute(bf16 ? gram_raw_kernel<true> : gram_raw_kernel<false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kRawSmem));
+        attr = true;
+      }
+      // algorithmic work: the tensor read once, the split partials written
+      // once, n^2 K multiply-adds; issued: nine slice products per 128 x 64 tile
+      const double gb = 4.0 * (double)n * (double)K + (double)part_elems * 8.0;
+      const double gf = (double)n * (double)n * (double)K;
+      const double gi = 9.0 * 2.0 * TM * TN * (double)ra.Kp * (double)npair;
+      {
+        KTimed kt_(s, "gram_raw_kernel", gb, gf, gi);
+        if (bf16) gram_raw_kernel<true><<<grid, kRawThreads, kRawSmem, s>>>(ma, mb, ra);
+        else gram_raw_kernel<false><<<grid, kRawThreads, kRawSmem, s>>>(ma, mb, ra);
+      }
+      ATC_LAUNCHED(1);
+      const int64_t tot = n * n;
+      const int rb = (int)((tot + 255) / 256 < 2048 ? (tot + 255) / 256 : 2048);
+      {
+        KTimed kt_(s, "gram_tc_assemble", (double)part_elems * 8.0 + (double)n * (double)n * 8.0);
+        gram_tc_assemble<<<rb, 256, 0, s>>>(ra.part, nsplit, npair, nc64, n, xs, g);
+      }
+      ATC_LAUNCHED(1);
+      return ATC_OK;
+    }
+    cudaGetLastError();  // no map: the pre-sliced path below
+  }
   if (encode_fn() && (!gram_tma_off() || nslice == 4)) {
     // pre-sliced planes + TMA-fed tensor-core Gram
     const int64_t Kp = ktiles * KT;

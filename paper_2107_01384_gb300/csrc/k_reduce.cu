@@ -74,51 +74,6 @@ __global__ void __launch_bounds__(kNormThreads) norm2_partial(const T* __restric
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// sum_i (x_i - z_i)^2 for the tensor x (FP32 or FP64) and its reproduction z
-// (FP32): each difference is taken in the precision of x and rounded to FP32,
-// its square is an exact float pair, four squares are summed as a double-float
-// and added into the FP64 accumulator (the FP32 pipes carry the work; GB300
-// issues FP64 at 1/64 of their rate).  Fixed grid and reduction tree.
-__device__ __forceinline__ void dd_acc_sq(float d, float& hi, float& lo) {
-  const float p = d * d;
-  const float e = fmaf(d, d, -p);
-  const float s = hi + p;
-  const float bp = s - hi;
-  lo += ((hi - (s - bp)) + (p - bp)) + e;
-  hi = s;
-}
-template <typename T>
-__global__ void __launch_bounds__(kNormThreads) diff2_partial(const T* __restrict__ x, const float* __restrict__ z,
-                                                               int64_t n, double* __restrict__ part) {
-  __shared__ double sh[32];
-  double acc = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t done = 0;
-  if (sizeof(T) == 4 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)z & 15) == 0) {
-    const int64_t n4 = n / 4;
-    const float4* x4 = reinterpret_cast<const float4*>(x);
-    const float4* z4 = reinterpret_cast<const float4*>(z);
-    for (int64_t i = t0; i < n4; i += stride) {
-      const float4 a = __ldg(x4 + i), b = __ldg(z4 + i);
-      float hi = 0.f, lo = 0.f;
-      dd_acc_sq(a.x - b.x, hi, lo);
-      dd_acc_sq(a.y - b.y, hi, lo);
-      dd_acc_sq(a.z - b.z, hi, lo);
-      dd_acc_sq(a.w - b.w, hi, lo);
-      acc += (double)hi + (double)lo;
-    }
-    done = n4 * 4;
-  }
-  for (int64_t i = done + t0; i < n; i += stride) {
-    float hi = 0.f, lo = 0.f;
-    dd_acc_sq((float)((double)x[i] - (double)z[i]), hi, lo);
-    acc += (double)hi + (double)lo;
-  }
-  double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
 __global__ void __launch_bounds__(kNormThreads) sum_partials(const double* __restrict__ part, int np,
                                                              double* __restrict__ out) {
   __shared__ double sh[32];
@@ -166,62 +121,57 @@ int grid_for(int64_t n, int threads) {
   return (int)b;
 }
 
-// e[j] partials: block (ch, j) sums y[(l r + j) R + c]^2 over its share of
-// the (l, c) fibers; the partials are then summed in chunk order.
-constexpr int kEnChunks = 64;
-__global__ void __launch_bounds__(kNormThreads) row_energy_partial(const float* __restrict__ y, int64_t LR, int64_t r,
-                                                                   int64_t R, double* __restrict__ part) {
+// Rayleigh quotients rho_j = u_j^T G u_j of the columns of U (n x rh,
+// row-major) and, in out[rh], trace(G): one CTA per column j stages u_j in
+// shared memory; a warp forms (G u_j)_i for one row i at a time (lanes over
+// the contiguous row, a fixed butterfly), then a fixed-order block sum.  FP64
+// throughout, the same order on every run.
+constexpr int kRayThreads = 512;
+constexpr int kRayMaxN = 1024;
+__global__ void __launch_bounds__(kRayThreads) rayleigh_kernel(const double* __restrict__ G, int n,
+                                                               const double* __restrict__ U, int rh,
+                                                               double* __restrict__ out) {
+  __shared__ double uj[kRayMaxN];
   __shared__ double sh[32];
-  const int64_t j = blockIdx.y;
-  const int64_t per = (LR + gridDim.x - 1) / gridDim.x;
-  const int64_t g0 = (int64_t)blockIdx.x * per, g1 = min(LR, g0 + per);
-  double v = 0.0;
-  for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-    const int64_t l = g / R, c = g - l * R;
-    const double t = (double)y[(l * r + j) * R + c];
-    v = fma(t, t, v);
+  const int j = blockIdx.x;
+  if (j > rh) return;
+  double acc = 0.0;
+  if (j == rh) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += G[(int64_t)i * n + i];
+  } else {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) uj[i] = U[(int64_t)i * rh + j];
+    __syncthreads();
+    // four rows per warp at a time: independent FMA chains hide the FP64
+    // latency (GB300 issues FP64 at a low rate with a long pipeline)
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i0 = 4 * (threadIdx.x >> 5); i0 < n; i0 += 4 * nw) {
+      double w[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int k = lane; k < n; k += 32) {
+        const double u = uj[k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (i0 + q < n) w[q] = fma(G[(int64_t)(i0 + q) * n + k], u, w[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double t = warp_sum(w[q]);
+        if (lane == 0 && i0 + q < n) acc = fma(uj[i0 + q], t, acc);
+      }
+    }
   }
-  v = block_sum(v, sh);
-  if (threadIdx.x == 0) part[j * gridDim.x + blockIdx.x] = v;
-}
-__global__ void row_energy_finish(const double* __restrict__ part, int nch, int64_t r, double* __restrict__ e) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < r; j += (int64_t)gridDim.x * blockDim.x) {
-    double v = 0.0;
-    for (int c = 0; c < nch; ++c) v += part[j * nch + c];
-    e[j] = v;
-  }
-}
-// (L, rh, R) -> (L, r, R), r <= rh: keep the leading r rows of every slab
-__global__ void compact_kernel(const float* __restrict__ y, int64_t L, int64_t rh, int64_t R, int64_t r,
-                               float* __restrict__ out) {
-  const int64_t total = L * r * R;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = i % R, t = i / R, j = t % r, l = t / r;
-    out[i] = y[(l * rh + j) * R + c];
-  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[j] = t;
 }
 
 }  // namespace
 
-int launch_row_energy(const float* y, int64_t L, int64_t r, int64_t R, double* e, cudaStream_t s) {
-  if (r <= 0) return ATC_OK;
-  if (r > 65535) return fail(ATC_EUNSUP, "row energy: too many rows");
-  double* part = nullptr;
-  ATC_TRY(Scratch::get(SLOT_ENERGY, sizeof(double) * (size_t)r * kEnChunks + 256, (void**)&part));
+int launch_rayleigh(const double* G, int64_t n, const double* U, int rh, double* out, cudaStream_t s) {
+  if (n < 1 || n > kRayMaxN || rh < 0) return fail(ATC_EINVAL, "launch_rayleigh: bad sizes");
   {
-    KTimed kt_(s, "row_energy_partial", (double)L * (double)R * (double)r * 4.0);
-    row_energy_partial<<<dim3(kEnChunks, (unsigned)r), kNormThreads, 0, s>>>(y, L * R, r, R, part);
+    KTimed kt_(s, "rayleigh_kernel", (double)n * (double)n * 8.0 + (double)n * rh * 8.0,
+               2.0 * (double)n * (double)n * rh);
+    rayleigh_kernel<<<rh + 1, kRayThreads, 0, s>>>(G, (int)n, U, rh, out);
   }
-  row_energy_finish<<<(unsigned)((r + 255) / 256), 256, 0, s>>>(part, kEnChunks, r, e);
-  ATC_LAUNCHED(2);
-  return ATC_OK;
-}
-
-int launch_compact(const float* y, int64_t L, int64_t rh, int64_t R, int64_t r, float* out, cudaStream_t s) {
-  const int64_t total = L * r * R;
-  if (total <= 0) return ATC_OK;
-  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-  compact_kernel<<<blocks, 256, 0, s>>>(y, L, rh, R, r, out);
   ATC_LAUNCHED(1);
   return ATC_OK;
 }
@@ -233,19 +183,6 @@ int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t 
     { KTimed kt_(s, "norm2_partial", (double)n * 4.0); norm2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, n, part); }
   else
     { KTimed kt_(s, "norm2_partial", (double)n * 8.0); norm2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, n, part); }
-  ATC_LAUNCHED(1);
-  sum_partials<<<1, kNormThreads, 0, s>>>(part, kNormBlocks, out);
-  ATC_LAUNCHED(1);
-  return ATC_OK;
-}
-
-int launch_diff_norm2(const void* x, int dtype, const float* z, int64_t n, double* out, cudaStream_t s) {
-  double* part = nullptr;
-  ATC_TRY(Scratch::get(SLOT_RES_PART, sizeof(double) * (kNormBlocks + 64), (void**)&part));
-  if (dtype == ATC_F32)
-    { KTimed kt_(s, "diff2_partial", (double)n * 8.0); diff2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, z, n, part); }
-  else
-    { KTimed kt_(s, "diff2_partial", (double)n * 12.0); diff2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, z, n, part); }
   ATC_LAUNCHED(1);
   sum_partials<<<1, kNormThreads, 0, s>>>(part, kNormBlocks, out);
   ATC_LAUNCHED(1);

@@ -4,8 +4,7 @@
 // every "column" gamma = (l, c) of the (L, n, R) view, y_gamma = U^T x_gamma.
 // As a GEMM: D[gamma][j] = sum_i A[gamma][i] B[j][i] with M = gamma (128 per
 // tile, any L and R), N = a chunk of <= 32 output indices j (padded to 16),
-// K = n.  The same kernel runs the expansion Y = U ._k X with B[a][b] = U[a][b],
-// and, in residual mode, sums (X' - U ._k Y)^2 instead of writing the product.
+// K = n.  The same kernel runs the expansion Y = U ._k X with B[a][b] = U[a][b].
 // Both operands are cut into three integer slices (tc::slice3i): X on the
 // tensor's power-of-two scale (projections) or on one power of two per column
 // gamma (expansions: a row of the MMA sums inside one column, so the column's
@@ -17,18 +16,26 @@
 // combined orders once: the output carries an unbiased round-to-nearest
 // error instead of the one-signed drift of truncating FP32 accumulation.
 //
-// Warp roles (448 threads):
+// Warp roles (480 threads):
 //   warps 0-3  epilogue: tcgen05.ld of a finished accumulator set -> Y (FP32),
 //              overlapped with the next tile's MMAs (two TMEM buffers);
-//   warps 4-11 converters: coalesced loads of X (the unfolding is index
-//              arithmetic), slicing, K-major 128-byte-swizzled stores to smem;
-//              for single-K-tile products with several output chunks the
-//              operand is sliced once beforehand (ttm_preslice_a) and one
-//              thread of warp 4 bulk-copies each stage's image instead;
+//   warps 4-11 converters: slicing into K-major 128-byte-swizzled stages.
+//              FP32 data whose unfolding tiles are boxes of a tensor map
+//              (R = 1, R a multiple of 128, or R a power of two below 128)
+//              arrive as raw tiles in a ring of shared-memory buffers filled
+//              by warp 14 with TMA tensor copies -- the mode-k unfolding is
+//              the box geometry, no transpose is written anywhere -- and the
+//              converters slice from shared memory; other data is loaded
+//              with coalesced global loads (the unfolding is index
+//              arithmetic).  With several output chunks the operand is sliced
+//              once beforehand (ttm_preslice_a) and one thread of warp 4
+//              bulk-copies each stage's image instead, the chunks of one M
+//              tile running side by side so that the image is read from L2;
 //   warp 12    MMA issuer (one elected thread), 9 MMAs per K step;
 //   warp 13    B producer: bulk-async copies (cp.async.bulk, TMA engine) of the
 //              pre-sliced, pre-swizzled factor tiles, completing on the
-//              stage's mbarrier.
+//              stage's mbarrier;
+//   warp 14    raw-tile producer (TMA tensor copies, see above).
 // TMEM: buffer b at column 256 b, order o at +32 o.
 // All waits are bounded (2 s); on time-out the CTA raises an error flag,
 // waits for its own MMAs, frees TMEM and returns.
@@ -49,7 +56,10 @@ constexpr int kConvWarps = 8;
 constexpr int kConvThreads = kConvWarps * 32;
 constexpr int kMmaWarp = kEpiWarps + kConvWarps;  // 12
 constexpr int kProdWarp = kMmaWarp + 1;           // 13
-constexpr int kThreads = (kProdWarp + 1) * 32;    // 448
+constexpr int kRawWarp = kProdWarp + 1;           // 14
+constexpr int kThreads = (kRawWarp + 1) * 32;     // 480
+constexpr int kMaxRaw = 3;                        // raw-tile ring depth
+constexpr uint32_t kRawBytes = 128 * 64 * 4;      // one raw FP32 tile: 128 columns x 64 K
 constexpr int KT = 64;
 constexpr int UNITS = 128 * 8 / kConvThreads;     // 4
 constexpr int kMaxN = 32;                         // output indices per launch
@@ -60,9 +70,8 @@ enum { TM_ROW = 0, TM_ROWVEC = 1, TM_GEN = 2 };
 struct TtmArgs {
   const void* x;
   int64_t L, Bdim, R;    // input view (L, Bdim, R); K = Bdim
-  int A;                 // output indices in this chunk (N of the MMA, <= kMaxN)
-  int apad;              // A padded to 16
-  int64_t Atot, j0;      // output mode size and this chunk's first index
+  int apad;              // output indices per chunk padded to 16 (N of the MMA, <= kMaxN)
+  int64_t Atot;          // output mode size
   int nkt;               // K tiles
   int64_t mtiles;        // ceil(L*R / 128)
   const uint8_t* bw;     // [3 slices][nkt][apad][128 B] pre-swizzled
@@ -72,17 +81,23 @@ struct TtmArgs {
   int* err;
   int nstage;            // pipeline depth (<= 4)
   int rowmode;           // TM_ROW / TM_ROWVEC when R == 1
-  // residual mode: instead of writing Y, accumulate sum (xres - Y)^2 over this
-  // chunk's outputs, one FP64 partial per CTA in res_part[blockIdx.x]
-  const void* xres;      // (L, Atot, R) tensor compared with the product
-  double* res_part;
-  int64_t csz;           // output indices per chunk (blockIdx.y = chunk)
+  int64_t csz;           // output indices per chunk
   size_t wb;             // bytes of one chunk's factor slices
   unsigned nchunk_launch;
-  // single-K-tile products with several output chunks: the data operand
-  // already sliced into the converters' shared-memory image, one 3 x 16 KB
-  // block per M tile (ttm_preslice_a); nullptr: the converter warps slice it
+  // products with several output chunks: the data operand already sliced into
+  // the converters' shared-memory image, one 3 x 16 KB block per (M tile,
+  // K tile) (ttm_preslice_a); nullptr: the converter warps slice it
   const uint8_t* aimg;
+  // raw FP32 tiles by TMA (the kernel's tensor map): box {rb, 64, 128 / rb}
+  // over (R, K, L) when R > 1 (rb = min(R, 128), a power of two), {64, 128}
+  // over (K, L) when R == 1
+  int tma;
+  int rb_log2;
+  int nraw;
+  // work items: chunk_fast -> item w = (M tile w / nchunk, chunk w % nchunk),
+  // so that the chunks of one M tile run side by side, CTA blockIdx.x taking
+  // items blockIdx.x + t gridDim.x; else item = M tile, chunk = blockIdx.y
+  int chunk_fast;
 };
 
 template <typename T>
@@ -117,32 +132,41 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-template <typename TX, bool BF16, bool GEN, bool RES, typename TR>
-__global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a is modified per chunk (by value)
+template <typename TX, bool BF16, bool GEN>
+__global__ void __launch_bounds__(kThreads, 1)
+    ttm_tc_kernel(TtmArgs a, const __grid_constant__ CUtensorMap xmap) {
   typedef float TY;
   constexpr int MAXST = 4;
   const int NSTAGE = a.nstage;
+  const int NRAW = a.nraw;
   const int MODE = GEN ? TM_GEN : a.rowmode;
   constexpr uint32_t A_BYTES = 128 * 128;  // 128 rows x 64 16-bit
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full_bar[MAXST], bfull_bar[MAXST], empty_bar[MAXST], accf_bar[2], acce_bar[2], done_bar;
+  __shared__ uint64_t raw_full[kMaxRaw], raw_empty[kMaxRaw];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
-  __shared__ double res_smem[kEpiWarps];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   volatile int* abort = &abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // chunk of output indices of this CTA row (all chunks share the padded width apad)
-  {
-    const int64_t j0c = (int64_t)blockIdx.y * a.csz;
-    a.j0 = j0c;
-    a.A = (int)min((int64_t)a.csz, a.Atot - j0c);
-    a.bw += (size_t)blockIdx.y * a.wb;
-    if (a.res_part) a.res_part += (size_t)blockIdx.y * gridDim.x;
-  }
+  // this CTA's work items t = 0 .. nmine-1: (M tile, output chunk) -- all
+  // chunks share the padded width apad
+  const bool cf = a.chunk_fast != 0;
+  const int64_t nch = cf ? (int64_t)a.nchunk_launch : 1;
+  const int64_t nwork = a.mtiles * nch;
+  const int64_t wb0 = blockIdx.x, wst = gridDim.x;
+  auto tile_mt = [&](int64_t t) -> int64_t {
+    const int64_t w = wb0 + t * wst;
+    return cf ? w / nch : w;
+  };
+  auto tile_ch = [&](int64_t t) -> int64_t {
+    const int64_t w = wb0 + t * wst;
+    return cf ? w - (w / nch) * nch : (int64_t)blockIdx.y;
+  };
   const uint32_t B_BYTES = (uint32_t)a.apad * 128u;
   const uint32_t STAGE = 3 * A_BYTES + ((3 * B_BYTES + 1023u) & ~1023u);
-  const int64_t nmine = (a.mtiles > blockIdx.x) ? (a.mtiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  uint8_t* rawbuf = smem + (size_t)NSTAGE * STAGE;  // raw-tile ring (TMA path)
+  const int64_t nmine = (nwork > wb0) ? (nwork - 1 - wb0) / wst + 1 : 0;
   const int64_t iters = nmine * a.nkt;
   const int64_t LR = a.L * a.R;
   const int shift = a.xs->shift;
@@ -152,6 +176,10 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
       mbar_init(&full_bar[s], a.aimg ? 1 : kConvThreads);
       mbar_init(&bfull_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
+    }
+    for (int s = 0; s < NRAW; ++s) {
+      mbar_init(&raw_full[s], 1);
+      mbar_init(&raw_empty[s], kConvThreads);
     }
     mbar_init(&done_bar, 1);
     for (int b = 0; b < 2; ++b) {
@@ -173,16 +201,76 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
       int64_t issued = 0;
       for (int64_t it = 0; it < iters; ++it) {
         const int s = (int)(it % NSTAGE);
-        const int64_t mt = blockIdx.x + (it / a.nkt) * gridDim.x;
+        const int64_t mt = tile_mt(it / a.nkt);
+        const int kt = (int)(it % a.nkt);
         if (!mbar_wait(&empty_bar[s], ((uint32_t)(it / NSTAGE) & 1u) ^ 1u, abort)) break;
         mbar_arrive_expect_tx(&full_bar[s], 3 * A_BYTES);
-        bulk_g2s(smem + (size_t)s * STAGE, a.aimg + (size_t)mt * 3 * A_BYTES, 3 * A_BYTES, &full_bar[s]);
+        bulk_g2s(smem + (size_t)s * STAGE, a.aimg + ((size_t)mt * a.nkt + kt) * 3 * A_BYTES, 3 * A_BYTES, &full_bar[s]);
         issued = it + 1;
       }
       // drain: every issued copy must land before the CTA may exit
       const int64_t first = issued > NSTAGE ? issued - NSTAGE : 0;
       for (int64_t it = first; it < issued; ++it)
         mbar_wait_drain(&full_bar[it % NSTAGE], (uint32_t)(it / NSTAGE) & 1u);
+    }
+  } else if (warp >= kEpiWarps && warp < kMmaWarp && a.tma) {
+    // ------------------------------ converters on raw tiles from the TMA ring
+    const int ct = tid - kEpiWarps * 32;
+    const float sc = ldexpf(1.0f, shift);
+    const int rbl = a.rb_log2;
+    const uint32_t rbm = (1u << rbl) - 1u;
+    for (int64_t it = 0; it < iters; ++it) {
+      const int rs = (int)(it % NRAW);
+      if (!mbar_wait(&raw_full[rs], (uint32_t)(it / NRAW) & 1u, abort)) break;
+      const int s = (int)(it % NSTAGE);
+      if (!mbar_wait(&empty_bar[s], ((uint32_t)(it / NSTAGE) & 1u) ^ 1u, abort)) break;
+      const float* raw = reinterpret_cast<const float*>(rawbuf + (size_t)rs * kRawBytes);
+      uint8_t* a0s = smem + (size_t)s * STAGE;
+      const int64_t g0 = tile_mt(it / a.nkt) * 128;
+#pragma unroll
+      for (int u = 0; u < UNITS; ++u) {
+        const int g = ct + kConvThreads * u;
+        int m, q;
+        float v[8];
+        if (MODE == TM_GEN) {
+          // raw tile [l][k][c] (c fastest), row m = l * rb + c
+          m = g & 127;
+          q = g >> 7;
+          const uint32_t base = ((((uint32_t)m >> rbl) * 64u + 8u * (uint32_t)q) << rbl) + ((uint32_t)m & rbm);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = raw[base + ((uint32_t)e << rbl)];
+        } else {
+          // raw tile [m][k]
+          m = g >> 3;
+          q = g & 7;
+          const float4* r4 = reinterpret_cast<const float4*>(raw + m * 64 + 8 * q);
+          const float4 x0 = r4[0], x1 = r4[1];
+          v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+          v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+        }
+        float scu = sc;
+        if (a.cshift) {
+          const int64_t gam = g0 + m;
+          scu = (gam < LR) ? ldexpf(1.0f, (int)__ldg(a.cshift + gam)) : 0.f;
+        }
+        uint32_t p0[4], p1[4], p2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float a0x, a1x, a2x, a0y, a1y, a2y;
+          slice3i(v[2 * e] * scu, a0x, a1x, a2x);
+          slice3i(v[2 * e + 1] * scu, a0y, a1y, a2y);
+          p0[e] = Pack<BF16>::two(a0x, a0y);
+          p1[e] = Pack<BF16>::two(a1x, a1y);
+          p2[e] = Pack<BF16>::two(a2x, a2y);
+        }
+        const uint32_t off = sw128_off((uint32_t)m, (uint32_t)(8 * q));
+        *reinterpret_cast<uint4*>(a0s + off) = make_uint4(p0[0], p0[1], p0[2], p0[3]);
+        *reinterpret_cast<uint4*>(a0s + A_BYTES + off) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
+        *reinterpret_cast<uint4*>(a0s + 2 * A_BYTES + off) = make_uint4(p2[0], p2[1], p2[2], p2[3]);
+      }
+      mbar_arrive(&raw_empty[rs]);  // the raw tile is consumed
+      fence_proxy_async_smem();
+      mbar_arrive(&full_bar[s]);
     }
   } else if (warp >= kEpiWarps && warp < kMmaWarp) {
     // ------------------------------------------------------------ converters
@@ -191,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
     const TX* __restrict__ x = reinterpret_cast<const TX*>(a.x);
     float bufA[UNITS][8], bufB[UNITS][8];
     auto load = [&](float (&buf)[UNITS][8], int64_t it) {
-      const int64_t mt = blockIdx.x + (it / a.nkt) * gridDim.x;
+      const int64_t mt = tile_mt(it / a.nkt);
       const int kt = (int)(it % a.nkt);
       const int64_t g0 = mt * 128;
 #pragma unroll
@@ -237,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
         if (MODE == TM_GEN) { m = g & 127; q = g >> 7; } else { m = g >> 3; q = g & 7; }
         float scu = sc;
         if (a.cshift) {
-          const int64_t gam = ((int64_t)blockIdx.x + (it / a.nkt) * gridDim.x) * 128 + m;
+          const int64_t gam = tile_mt(it / a.nkt) * 128 + m;
           scu = (gam < LR) ? ldexpf(1.0f, (int)__ldg(a.cshift + gam)) : 0.f;
         }
         uint32_t p0[4], p1[4], p2[4];
@@ -278,16 +366,41 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
         const int kt = (int)(it % a.nkt);
         if (!mbar_wait(&empty_bar[s], ((uint32_t)(it / NSTAGE) & 1u) ^ 1u, abort)) break;
         uint8_t* bb = smem + (size_t)s * STAGE + 3 * A_BYTES;
+        const uint8_t* bwc = a.bw + (size_t)tile_ch(it / a.nkt) * a.wb;
         mbar_arrive_expect_tx(&bfull_bar[s], 3 * B_BYTES);
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-          bulk_g2s(bb + q * B_BYTES, a.bw + q * slice_bytes + (size_t)kt * B_BYTES, B_BYTES, &bfull_bar[s]);
+          bulk_g2s(bb + q * B_BYTES, bwc + q * slice_bytes + (size_t)kt * B_BYTES, B_BYTES, &bfull_bar[s]);
         issued = it + 1;
       }
       // drain: every issued copy must land before the CTA may exit
       const int64_t first = issued > NSTAGE ? issued - NSTAGE : 0;
       for (int64_t it = first; it < issued; ++it)
         mbar_wait_drain(&bfull_bar[it % NSTAGE], (uint32_t)(it / NSTAGE) & 1u);
+    }
+  } else if (warp == kRawWarp) {
+    // ---------------------------------------------- raw-tile producer (TMA)
+    if (lane == 0 && a.tma && !a.aimg) {
+      int64_t issued = 0;
+      for (int64_t it = 0; it < iters; ++it) {
+        const int rs = (int)(it % NRAW);
+        if (!mbar_wait(&raw_empty[rs], ((uint32_t)(it / NRAW) & 1u) ^ 1u, abort)) break;
+        const int64_t g0 = tile_mt(it / a.nkt) * 128;
+        const int kt = (int)(it % a.nkt);
+        mbar_arrive_expect_tx(&raw_full[rs], kRawBytes);
+        void* dst = rawbuf + (size_t)rs * kRawBytes;
+        if (GEN) {
+          const int64_t l = g0 / a.R, c0 = g0 - l * a.R;
+          tma_load_3d(dst, &xmap, &raw_full[rs], (int)c0, kt * KT, (int)l);
+        } else {
+          tma_load_2d(dst, &xmap, &raw_full[rs], kt * KT, (int)g0);
+        }
+        issued = it + 1;
+      }
+      // drain: every issued copy must land before the CTA may exit
+      const int64_t first = issued > NRAW ? issued - NRAW : 0;
+      for (int64_t it = first; it < issued; ++it)
+        mbar_wait_drain(&raw_full[it % NRAW], (uint32_t)(it / NRAW) & 1u);
     }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
@@ -335,8 +448,6 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
     // y = (sum_o 2^-8o acc_o) 2^-(shift + 8): one rounding, then exact power-of-two scaling
     const int e_glob = -(shift + 8);
     TY* __restrict__ y = reinterpret_cast<TY*>(a.y);
-    const TR* __restrict__ xr = reinterpret_cast<const TR*>(a.xres);
-    float racc = 0.f;  // residual mode: this thread's sum of squares
     for (int64_t t = 0; t < nmine; ++t) {
       const int ab = (int)(t & 1);
       // warp-uniform wait: the tcgen05.ld below is .sync.aligned
@@ -346,13 +457,15 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
       __syncwarp();
       if (!okw) break;
       tc_fence_after();
-      const int64_t mt = blockIdx.x + t * gridDim.x;
+      const int64_t mt = tile_mt(t);
+      const int64_t j0 = tile_ch(t) * a.csz;
+      const int Ach = (int)min(a.csz, a.Atot - j0);
       const int64_t gam = mt * 128 + 32 * warp + lane;
       const bool valid = gam < LR;
       const int64_t l = valid ? gam / a.R : 0, c = valid ? gam - l * a.R : 0;
       const int e_out = (a.cshift && valid) ? -((int)__ldg(a.cshift + gam) + 8) : e_glob;
       const float f1 = ldexpf(1.0f, e_out / 2), f2 = ldexpf(1.0f, e_out - e_out / 2);
-      TY* yo = y + (l * a.Atot + a.j0) * a.R + c;
+      TY* yo = y + (l * a.Atot + j0) * a.R + c;
       const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)ab * 256u;
 #pragma unroll 1
       for (int c0 = 0; c0 < a.apad; c0 += 8) {
@@ -364,36 +477,20 @@ __global__ void __launch_bounds__(kThreads, 1) ttm_tc_kernel(TtmArgs a) {  // a 
         tmem_ld8(tb + 4 * kOrdStride + (uint32_t)c0, r4);
         tmem_ld_wait();
         if (valid) {
-          const TR* xo = RES ? xr + (l * a.Atot + a.j0) * a.R + c : nullptr;
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int j = c0 + e;
-            if (j < a.A) {
+            if (j < Ach) {
               float sv, tv;
               combine_orders(__uint_as_float(r0[e]), __uint_as_float(r1[e]), __uint_as_float(r2[e]),
                              __uint_as_float(r3[e]), __uint_as_float(r4[e]), sv, tv);
-              const float z = ((sv + tv) * f1) * f2;
-              if (RES) {
-                const float dd = (float)(__ldg(xo + (int64_t)j * a.R) - (TR)z);
-                racc = fmaf(dd, dd, racc);
-              } else {
-                yo[(int64_t)j * a.R] = (TY)z;
-              }
+              yo[(int64_t)j * a.R] = (TY)(((sv + tv) * f1) * f2);
             }
           }
         }
       }
       tc_fence_before();
       mbar_arrive(&acce_bar[ab]);
-    }
-    if (RES) {
-      // fixed-order FP64 reduction over the 128 epilogue threads
-      double v = (double)racc;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) res_smem[warp] = v;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (tid == 0) a.res_part[blockIdx.x] = ((res_smem[0] + res_smem[1]) + (res_smem[2] + res_smem[3]));
     }
   }
   tc_fence_before();
@@ -488,12 +585,13 @@ __global__ void ttm_prep_b(const double* __restrict__ u, int64_t csz, int64_t At
   }
 }
 
-// The data operand of a single-K-tile product (contraction <= 64) sliced once
-// into the converter warps' shared-memory image: per M tile, three 128 x 64
-// 16-bit slices in the 128-byte-swizzled K-major layout, [m tile][slice][16 KB].
-// The output chunks (blockIdx.y of the product) then copy it with the bulk
-// engine instead of each re-slicing it.  Same loads, scales and slicing as the
-// converter warps, one thread per (m tile, row, group of 8 K values).
+// The data operand of a product with several output chunks sliced once into
+// the converter warps' shared-memory image: per (M tile, K tile), three
+// 128 x 64 16-bit slices in the 128-byte-swizzled K-major layout,
+// [m tile][k tile][slice][16 KB].  The output chunks then copy it with the
+// bulk engine instead of each re-slicing it.  Same loads, scales and slicing
+// as the converter warps, one thread per (m tile, k tile, row, group of 8 K
+// values).
 template <typename TX, bool GEN, bool BF16>
 __global__ void ttm_preslice_a(TtmArgs a, uint8_t* __restrict__ img) {
   constexpr uint32_t A_BYTES = 128 * 128;
@@ -501,10 +599,12 @@ __global__ void ttm_preslice_a(TtmArgs a, uint8_t* __restrict__ img) {
   const float sc = ldexpf(1.0f, a.xs->shift);
   const TX* __restrict__ x = reinterpret_cast<const TX*>(a.x);
   const int64_t LR = a.L * a.R;
-  const int64_t total = a.mtiles * 1024;
+  const int64_t total = a.mtiles * a.nkt * 1024;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t mt = idx >> 10;
+    const int64_t tile = idx >> 10;  // mt * nkt + kt
+    const int64_t mt = tile / a.nkt;
+    const int64_t k0 = (tile - mt * a.nkt) * KT;
     const int g = (int)(idx & 1023);
     int m, q;
     if (MODE == TM_GEN) { m = g & 127; q = g >> 7; } else { m = g >> 3; q = g & 7; }
@@ -514,15 +614,15 @@ __global__ void ttm_preslice_a(TtmArgs a, uint8_t* __restrict__ img) {
       const int64_t l = gam / a.R, c = gam - l * a.R;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const int64_t i = 8 * q + e;
+        const int64_t i = k0 + 8 * q + e;
         buf[e] = (gam < LR && i < a.Bdim) ? (float)__ldg(x + (l * a.Bdim + i) * a.R + c) : 0.f;
       }
-    } else if (MODE == TM_ROWVEC && gam < LR && 8 * q < a.Bdim) {
-      ld8<TX>(x + gam * a.Bdim + 8 * q, buf);
+    } else if (MODE == TM_ROWVEC && gam < LR && k0 + 8 * q < a.Bdim) {
+      ld8<TX>(x + gam * a.Bdim + k0 + 8 * q, buf);
     } else {
 #pragma unroll
       for (int e = 0; e < 8; ++e)
-        buf[e] = (gam < LR && 8 * q + e < a.Bdim) ? (float)__ldg(x + gam * a.Bdim + 8 * q + e) : 0.f;
+        buf[e] = (gam < LR && k0 + 8 * q + e < a.Bdim) ? (float)__ldg(x + gam * a.Bdim + k0 + 8 * q + e) : 0.f;
     }
     float scu = sc;
     if (a.cshift) scu = (gam < LR) ? ldexpf(1.0f, (int)__ldg(a.cshift + gam)) : 0.f;
@@ -536,63 +636,46 @@ __global__ void ttm_preslice_a(TtmArgs a, uint8_t* __restrict__ img) {
       p1[e] = Pack<BF16>::two(a1x, a1y);
       p2[e] = Pack<BF16>::two(a2x, a2y);
     }
-    uint8_t* base = img + (size_t)mt * 3 * A_BYTES + sw128_off((uint32_t)m, (uint32_t)(8 * q));
+    uint8_t* base = img + (size_t)tile * 3 * A_BYTES + sw128_off((uint32_t)m, (uint32_t)(8 * q));
     *reinterpret_cast<uint4*>(base) = make_uint4(p0[0], p0[1], p0[2], p0[3]);
     *reinterpret_cast<uint4*>(base + A_BYTES) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
     *reinterpret_cast<uint4*>(base + 2 * A_BYTES) = make_uint4(p2[0], p2[1], p2[2], p2[3]);
   }
 }
 
-template <typename TX, bool BF16, bool GEN, bool RES, typename TR>
-int ttm_launch_t(const TtmArgs& a, int grid, int smem, cudaStream_t s) {
+template <typename TX, bool BF16, bool GEN>
+int ttm_launch_t(const TtmArgs& a, const CUtensorMap& map, dim3 grid, int smem, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    ATC_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<TX, BF16, GEN, RES, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ATC_CUDA_TRY(cudaFuncSetAttribute(ttm_tc_kernel<TX, BF16, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       225 * 1024));
     attr = true;
   }
-  // algorithmic work: the data tensor read once, the output (or, with the
-  // fused residual, the compared tensor) once, the factor once; 2 Atot Bdim per
-  // output column; issued: nine slice products over the padded tiles
+  // algorithmic work: the data tensor read once, the output written once, the
+  // factor read once; 2 Atot Bdim per output column; issued: nine slice
+  // products over the padded tiles
   const double cols = (double)a.L * (double)a.R;
-  const double bytes = cols * (double)a.Bdim * sizeof(TX) + cols * (double)a.Atot * (RES ? sizeof(TR) : 4.0) +
+  const double bytes = cols * (double)a.Bdim * sizeof(TX) + cols * (double)a.Atot * 4.0 +
                        (double)a.Atot * (double)a.Bdim * 8.0;
   const double flops = 2.0 * cols * (double)a.Atot * (double)a.Bdim;
   const double issued = 9.0 * 2.0 * (double)a.mtiles * 128.0 * (double)a.apad * (double)a.nchunk_launch *
                         (double)a.nkt * KT;
-  KTimed kt_(s, RES ? "ttm_tc_kernel(fused residual)" : "ttm_tc_kernel", bytes, flops, issued);
-  ttm_tc_kernel<TX, BF16, GEN, RES, TR><<<dim3(grid, a.nchunk_launch), kThreads, smem, s>>>(a);
+  KTimed kt_(s, "ttm_tc_kernel", bytes, flops, issued);
+  ttm_tc_kernel<TX, BF16, GEN><<<grid, kThreads, smem, s>>>(a, map);
   ATC_LAUNCHED(1);
   return ATC_OK;
 }
 
 template <typename TX, bool BF16>
-int ttm_launch_g(const TtmArgs& a, bool gen, int grid, int smem, cudaStream_t s) {
-  return gen ? ttm_launch_t<TX, BF16, true, false, float>(a, grid, smem, s)
-             : ttm_launch_t<TX, BF16, false, false, float>(a, grid, smem, s);
-}
-
-template <typename TR>
-int ttm_launch_res(const TtmArgs& a, bool gen, int grid, int smem, cudaStream_t s) {
-  return gen ? ttm_launch_t<float, true, true, true, TR>(a, grid, smem, s)
-             : ttm_launch_t<float, true, false, true, TR>(a, grid, smem, s);
-}
-
-// fixed-order sum of the residual partials
-__global__ void sum_res_partials(const double* __restrict__ p, int np, double* __restrict__ out) {
-  __shared__ double sh[256];
-  double v = 0.0;
-  for (int i = threadIdx.x; i < np; i += 256) v += p[i];
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = sh[0];
+int ttm_launch_g(const TtmArgs& a, const CUtensorMap& map, bool gen, dim3 grid, int smem, cudaStream_t s) {
+  return gen ? ttm_launch_t<TX, BF16, true>(a, map, grid, smem, s) : ttm_launch_t<TX, BF16, false>(a, map, grid, smem, s);
 }
 
 int g_nsm_ttm = 0;
+// per-column scales replace the tensor's slice scale: a zero scale stands in
+__device__ SliceScale g_unit_scale;
+// largest pre-sliced data image (6 bytes per element of the data operand)
+constexpr size_t kMaxImageBytes = (size_t)16 << 30;
 
 }  // namespace
 
@@ -600,14 +683,11 @@ int tc_error_flag(int** flag);
 
 namespace {
 
-// Shared driver of the projection / expansion (res == nullptr) and of the
-// residual energy sum ||xres - U ._k X||^2 (res != nullptr, expansion only).
-// percol: per-column scale exponents for the data operand (expansions, whose
+// Driver of the projection / expansion.  percol: per-column scale exponents for the data operand (expansions, whose
 // inputs -- cores and partly expanded cores -- span many orders of magnitude
 // across columns); otherwise one power of two for the whole tensor.
 int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r, int expand,
-            int precision, void* y, cudaStream_t s, const SliceScale* xs, const void* xres, int xres_dtype,
-            double* res, bool percol) {
+            int precision, void* y, cudaStream_t s, const SliceScale* xs, bool percol) {
   const int64_t Atot = expand ? n : r;
   const int64_t Bdim = expand ? r : n;
   if (Bdim > 1024) return fail(ATC_EUNSUP, "split-precision TTM supports contraction length <= 1024 (got %lld)",
@@ -618,6 +698,13 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
     ATC_CUDA_TRY(cudaDeviceGetAttribute(&g_nsm_ttm, cudaDevAttrMultiProcessorCount, dev));
   }
   const bool bf16 = (precision == ATC_PREC_SPLIT_BF16);
+  if (!xs && percol) {
+    // every column carries its own power of two (cshift): the tensor-wide
+    // scale is never read, so no pass over the data computes it
+    void* p = nullptr;
+    ATC_CUDA_TRY(cudaGetSymbolAddress(&p, g_unit_scale));
+    xs = reinterpret_cast<const SliceScale*>(p);
+  }
   if (!xs) ATC_TRY(slice_scale(x, xdtype, L * Bdim * R, s, &xs));
   int* err = nullptr;
   ATC_TRY(tc_error_flag(&err));
@@ -628,10 +715,12 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
   const int64_t csz = (Atot + nchunk - 1) / nchunk;
   const int apad_max = (int)((csz + 15) / 16 * 16);
   const size_t wb = (size_t)3 * nkt * apad_max * 128;
-  const int grid = (int)(mtiles < g_nsm_ttm ? mtiles : g_nsm_ttm);
+  // work items (M tile, chunk), chunks of one M tile side by side; one
+  // persistent CTA per SM at most
+  const int64_t nwork = mtiles * nchunk;
+  const int grid = (int)(nwork < g_nsm_ttm ? nwork : g_nsm_ttm);
   uint8_t* bw = nullptr;
-  ATC_TRY(Scratch::get(SLOT_TTM_U, wb * nchunk + (size_t)8 * nchunk * (grid + 1) + 256, (void**)&bw));
-  double* part = reinterpret_cast<double*>(bw + wb * nchunk);
+  ATC_TRY(Scratch::get(SLOT_TTM_U, wb * nchunk + 256, (void**)&bw));
   signed char* cshift = nullptr;
   if (percol && L * R > 0) {
     ATC_TRY(Scratch::get(SLOT_COLSHIFT, (size_t)(L * R) + 256, (void**)&cshift));
@@ -651,10 +740,8 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
     a.L = L;
     a.Bdim = Bdim;
     a.R = R;
-    a.A = (int)std::min<int64_t>(csz, Atot);
     a.apad = apad_max;
     a.Atot = Atot;
-    a.j0 = 0;
     a.nkt = nkt;
     a.mtiles = mtiles;
     a.y = y;
@@ -662,34 +749,68 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
     a.cshift = cshift;
     a.err = err;
     a.rowmode = (Bdim % 8 == 0) ? TM_ROWVEC : TM_ROW;
-    a.xres = xres;
-    a.res_part = res ? part : nullptr;
     a.csz = csz;
     a.wb = wb;
     a.nchunk_launch = (unsigned)nchunk;
     a.bw = bw;
     a.aimg = nullptr;
+    a.tma = 0;
+    a.rb_log2 = 0;
+    a.nraw = 0;
+    a.chunk_fast = nchunk > 1 ? 1 : 0;
     const uint32_t bbytes = (uint32_t)a.apad * 128u;
     const uint32_t stage = 3u * 128u * 128u + ((3u * bbytes + 1023u) & ~1023u);
-    a.nstage = (int)((224u * 1024u) / stage);
+    // the data operand: pre-sliced image (several chunks), raw FP32 tiles by
+    // TMA (tensor-map geometry), or the converters' global loads
+    const size_t img_bytes = (size_t)mtiles * nkt * 3 * 128 * 128;
+    const bool use_img = mtiles > 0 && nchunk > 1 && img_bytes <= kMaxImageBytes;
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    if (!use_img && mtiles > 0 && xdtype == ATC_F32 && ((uintptr_t)x & 15u) == 0) {
+      bool ok = false;
+      int rbl = 0;
+      if (R == 1) {
+        if (Bdim % 4 == 0) {
+          const int64_t dims[2] = {Bdim, L}, strides[1] = {Bdim * 4};
+          const uint32_t box[2] = {(uint32_t)KT, 128u};
+          ok = make_raw_map_f32(&map, x, 2, dims, strides, box) == ATC_OK;
+        }
+      } else if (R % 128 == 0 || (R < 128 && R >= 4 && (128 % R) == 0)) {
+        const int64_t rb = R < 128 ? R : 128;
+        while ((1 << rbl) < rb) ++rbl;
+        const int64_t dims[3] = {R, Bdim, L}, strides[2] = {R * 4, R * Bdim * 4};
+        const uint32_t box[3] = {(uint32_t)rb, (uint32_t)KT, (uint32_t)(128 / rb)};
+        ok = make_raw_map_f32(&map, x, 3, dims, strides, box) == ATC_OK;
+      }
+      if (!ok) cudaGetLastError();
+      for (int nraw = kMaxRaw; ok && nraw >= 2 && !a.tma; --nraw) {
+        if ((size_t)224 * 1024 >= (size_t)nraw * kRawBytes + 2 * (size_t)stage) {
+          a.tma = 1;
+          a.nraw = nraw;
+          a.rb_log2 = rbl;
+        }
+      }
+    }
+    const size_t raw_bytes = (size_t)a.nraw * kRawBytes;
+    a.nstage = (int)(((size_t)224 * 1024 - raw_bytes) / stage);
     if (a.nstage > 4) a.nstage = 4;
     if (a.nstage < 2) return fail(ATC_EUNSUP, "TTM stage does not fit in shared memory");
-    const int smem = (int)(a.nstage * stage + 1024);
+    const int smem = (int)(a.nstage * stage + raw_bytes + 1024);
     {
       const int64_t tot = (int64_t)nkt * a.apad * 64 * nchunk;
       const int blocks = (int)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096);
-      if (bf16 || res) ttm_prep_b<true><<<blocks, 256, 0, s>>>(u, csz, Atot, nchunk, (int)Bdim, expand, a.apad, nkt, bw, wb);
+      if (bf16) ttm_prep_b<true><<<blocks, 256, 0, s>>>(u, csz, Atot, nchunk, (int)Bdim, expand, a.apad, nkt, bw, wb);
       else ttm_prep_b<false><<<blocks, 256, 0, s>>>(u, csz, Atot, nchunk, (int)Bdim, expand, a.apad, nkt, bw, wb);
       ATC_LAUNCHED(1);
     }
-    // one K tile and several output chunks: slice the data operand once (the
-    // image stays in L2 when it is at most 64 MB) instead of once per chunk
-    if (mtiles > 0 && nkt == 1 && nchunk > 1 && (size_t)mtiles * 3 * 128 * 128 <= ((size_t)64 << 20)) {
+    // several output chunks: slice the data operand once instead of once per
+    // chunk; the chunks of an M tile read its image while it sits in L2
+    if (use_img) {
       uint8_t* img = nullptr;
-      ATC_TRY(Scratch::get(SLOT_TTM_AIMG, (size_t)mtiles * 3 * 128 * 128, (void**)&img));
-      const int64_t tot = mtiles * 1024;
+      ATC_TRY(Scratch::get(SLOT_TTM_AIMG, img_bytes, (void**)&img));
+      const int64_t tot = mtiles * nkt * 1024;
       const int blocks = (int)((tot + 255) / 256 < 8 * g_nsm_ttm ? (tot + 255) / 256 : 8 * g_nsm_ttm);
-      const bool gen = (R != 1), pb = bf16 || res;
+      const bool gen = (R != 1), pb = bf16;
       if (xdtype == ATC_F32) {
         if (gen) {
           if (pb) ttm_preslice_a<float, true, true><<<blocks, 256, 0, s>>>(a, img);
@@ -712,25 +833,14 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
     }
     if (mtiles > 0) {
       const bool gen = (R != 1);
-      if (res) {
-        if (xdtype != ATC_F32) return fail(ATC_EUNSUP, "residual mode expects an FP32 projected tensor");
-        if (xres_dtype == ATC_F32) ATC_TRY(ttm_launch_res<float>(a, gen, grid, smem, s));
-        else ATC_TRY(ttm_launch_res<double>(a, gen, grid, smem, s));
-      } else if (xdtype == ATC_F32) {
-        if (bf16) ATC_TRY((ttm_launch_g<float, true>(a, gen, grid, smem, s)));
-        else ATC_TRY((ttm_launch_g<float, false>(a, gen, grid, smem, s)));
+      const dim3 g3((unsigned)grid, 1u);
+      if (xdtype == ATC_F32) {
+        if (bf16) ATC_TRY((ttm_launch_g<float, true>(a, map, gen, g3, smem, s)));
+        else ATC_TRY((ttm_launch_g<float, false>(a, map, gen, g3, smem, s)));
       } else {
-        if (bf16) ATC_TRY((ttm_launch_g<double, true>(a, gen, grid, smem, s)));
-        else ATC_TRY((ttm_launch_g<double, false>(a, gen, grid, smem, s)));
+        if (bf16) ATC_TRY((ttm_launch_g<double, true>(a, map, gen, g3, smem, s)));
+        else ATC_TRY((ttm_launch_g<double, false>(a, map, gen, g3, smem, s)));
       }
-    }
-  }
-  if (res) {
-    if (mtiles == 0) {
-      ATC_CUDA_TRY(cudaMemsetAsync(res, 0, sizeof(double), s));
-    } else {
-      sum_res_partials<<<1, 256, 0, s>>>(part, nchunk * grid, res);
-      ATC_LAUNCHED(1);
     }
   }
   return ATC_OK;
@@ -741,24 +851,7 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
 int launch_ttm_split(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const double* u, int64_t r,
                      int expand, int precision, void* y, int ydtype, cudaStream_t s, const SliceScale* xs) {
   if (ydtype != ATC_F32) return fail(ATC_EUNSUP, "split-precision TTM writes FP32 output");
-  return ttm_run(x, xdtype, L, n, R, u, r, expand, precision, y, s, xs, nullptr, 0, nullptr, expand != 0);
-}
-
-// The residual ||x - U ._k y||^2 as the tensor-core expansion into a scratch
-// tensor (the epilogue's stores do not stall it) followed by one streaming pass
-// over x and the expansion; the differences and their rounding are those of the
-// fused residual epilogue of ttm_tc_kernel (res != nullptr), whose dependent
-// loads of x left HBM mostly idle.  ATC_RESIDUAL_FUSED=1 (read on every call)
-// selects the fused epilogue instead; it needs no scratch tensor.
-int launch_ttm_residual(const float* y, int64_t L, int64_t r, int64_t R, const double* u, int64_t n, const void* x,
-                        int xdtype, double* rho, cudaStream_t s) {
-  const char* fused = getenv("ATC_RESIDUAL_FUSED");
-  if (fused && fused[0] == '1')
-    return ttm_run(y, ATC_F32, L, n, R, u, r, 1, ATC_PREC_SPLIT_BF16, nullptr, s, nullptr, x, xdtype, rho, true);
-  float* z = nullptr;
-  ATC_TRY(Scratch::get(SLOT_RES_TMP, sizeof(float) * (size_t)(L * n * R) + 256, (void**)&z));
-  ATC_TRY(ttm_run(y, ATC_F32, L, n, R, u, r, 1, ATC_PREC_SPLIT_BF16, z, s, nullptr, nullptr, 0, nullptr, true));
-  return launch_diff_norm2(x, xdtype, z, L * n * R, rho, s);
+  return ttm_run(x, xdtype, L, n, R, u, r, expand, precision, y, s, xs, expand != 0);
 }
 
 }  // namespace atc

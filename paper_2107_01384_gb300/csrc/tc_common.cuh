@@ -42,19 +42,31 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same test with a suspend-time hint: a thread whose phase is not
+// complete sleeps (up to `ns` nanoseconds, or until the phase completes)
+// instead of spinning, leaving the issue slots to the working warps.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+constexpr uint32_t kWaitSleepNs = 20000;  // 20 us per suspended try
+
 // Wait for the phase of parity `parity` to complete; gives up after the time
 // limit or when *abort becomes non-zero.  Returns false if it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
-  for (uint32_t it = 0;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 63) == 63) {
-      if (*abort) return false;
-      if (globaltimer() - t0 > kWaitLimitNs) {
-        *abort = 1;
-        return false;
-      }
+  for (;;) {
+    if (mbar_try_sleep(bar, parity, kWaitSleepNs)) return true;
+    if (*abort) return false;
+    if (globaltimer() - t0 > kWaitLimitNs) {
+      *abort = 1;
+      return false;
     }
   }
 }
@@ -63,9 +75,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
 // before freeing TMEM or leaving the CTA).
 __device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
   const uint64_t t0 = globaltimer();
-  for (uint32_t it = 0;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 63) == 63 && globaltimer() - t0 > kWaitLimitNs) return false;
+  for (;;) {
+    if (mbar_try_sleep(bar, parity, kWaitSleepNs)) return true;
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
   }
 }
 
@@ -148,6 +160,15 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(smem_u32(smem_dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
 // Fixed-point slices (error-free splitting in the manner of Ozaki et al.,
 // as used for tensor-core GEMMs by Mukunoki et al., ICCS 2020).  With one
 // power-of-two scale per operand, v = x * 2^shift and |v| < 256:
@@ -158,11 +179,20 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
 // the tensor-core FP32 accumulation then performs no rounding at all, whatever
 // its internal rounding mode.  The products are grouped by order s + t (the
 // scale 2^-8(s+t)) into five accumulators and combined outside the tensor core.
+// Round to the nearest integer, ties to even, for |v| < 2^22: adding 1.5 2^23
+// moves v into [2^23, 2^24), where the float spacing is 1, so the addition
+// itself rounds (round-to-nearest-even); subtracting the constant is exact.
+// Two FP32 additions on the full-rate pipe (the _rn intrinsics keep the
+// compiler from contracting or reassociating them).
+__device__ __forceinline__ float rint_small(float v) {
+  return __fsub_rn(__fadd_rn(v, 12582912.0f), 12582912.0f);
+}
+
 __device__ __forceinline__ void slice3i(float v, float& a0, float& a1, float& a2) {
-  a0 = rintf(v);
+  a0 = rint_small(v);
   const float t = (v - a0) * 256.0f;  // exact
-  a1 = rintf(t);
-  a2 = rintf((t - a1) * 256.0f);
+  a1 = rint_small(t);
+  a2 = rint_small((t - a1) * 256.0f);
 }
 
 // Four slices (32-bit fixed point): v ~ a0 + a1 2^-8 + a2 2^-16 + a3 2^-24,
@@ -170,12 +200,12 @@ __device__ __forceinline__ void slice3i(float v, float& a0, float& a1, float& a2
 // order s + t >= 5 (scale <= 2^-40) are left out by the Gram kernels: they are
 // below the rounding of v itself.
 __device__ __forceinline__ void slice4i(float v, float& a0, float& a1, float& a2, float& a3) {
-  a0 = rintf(v);
+  a0 = rint_small(v);
   const float t = (v - a0) * 256.0f;  // exact
-  a1 = rintf(t);
+  a1 = rint_small(t);
   const float t2 = (t - a1) * 256.0f;  // exact
-  a2 = rintf(t2);
-  a3 = rintf((t2 - a2) * 256.0f);
+  a2 = rint_small(t2);
+  a3 = rint_small((t2 - a2) * 256.0f);
 }
 
 // acc0 + 2^-8 acc1 + 2^-16 acc2 + 2^-24 acc3 + 2^-32 acc4 as an unevaluated
@@ -189,15 +219,17 @@ __device__ __forceinline__ void combine_orders(float c0, float c1, float c2, flo
   t = e + fmaf(c2, 1.52587890625e-05f, fmaf(c3, 5.9604644775390625e-08f, c4 * 2.3283064365386963e-10f));
 }
 
+// 16-bit images of slice integers (|a| <= 256, exact in bf16 and fp16).  For
+// bf16 the image is the upper half of the float's bits (an integer of at most
+// 8 significant bits leaves the lower 16 bits zero): one byte permute packs two.
 template <bool BF16>
 struct Pack;
 template <>
 struct Pack<true> {
   static __device__ __forceinline__ uint32_t two(float a, float b) {
-    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
   }
-  static __device__ __forceinline__ uint16_t one(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
+  static __device__ __forceinline__ uint16_t one(float a) { return (uint16_t)(__float_as_uint(a) >> 16); }
 };
 template <>
 struct Pack<false> {
@@ -215,4 +247,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 }  // namespace tc
+
+// Host: TMA map over FP32 data (k_gram_tc.cu): `rank` dimensions innermost
+// first, strides[d - 1] = bytes between consecutive indices of dimension d,
+// box extents per dimension, no swizzle, zero fill out of range.
+int make_raw_map_f32(CUtensorMap* m, const void* base, int rank, const int64_t* dims, const int64_t* strides,
+                     const uint32_t* box);
 }  // namespace atc
