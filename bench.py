@@ -52,9 +52,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="batched512: skip the one-tensor-at-a-time comparison (for profiling runs)")
-    ap.add_argument("--workload", default="bumps256", choices=["bumps256", "turbulence1024", "batched512"],
+    ap.add_argument("--workload", default="bumps256",
+                    choices=["bumps256", "turbulence1024", "turbulence256", "batched512"],
                     help="bumps256: the 256^3 single-tensor step (default); turbulence1024: the 1024^3 "
-                         "turbulence-like field (full ranks: the compute-bound case); batched512: 512 uneven "
+                         "turbulence-like field (full ranks: the compute-bound case); turbulence256: its recipe "
+                         "at 256^3 (the size its kernels are profiled at); batched512: 512 uneven "
                          "tensors in one persistent graph-replayed launch")
     return ap.parse_args()
 
@@ -207,12 +209,15 @@ def load_peaks():
 WORKLOADS = {
     "bumps256": "gaussian_bumps_256x256x256_f32",
     "turbulence1024": "turbulence_1024x1024x1024_f32 (|k|^-5/3 spectrum, random phases, RMS 1)",
+    # the 1024^3 recipe at 256^3 (full ranks too: a 2^24-coefficient core), the
+    # size at which the kernels of the 1024^3 step are profiled
+    "turbulence256": "turbulence_256x256x256_f32 (|k|^-5/3 spectrum, random phases, RMS 1)",
 }
 
 
 def workload(name="bumps256"):
     import synth
-    if name == "turbulence1024":
+    if name in ("turbulence1024", "turbulence256"):
         # the CPU-side stand-in (oracle sample): the 256^3 field of the same recipe
         return synth.turbulence(n=256)
     return synth.gaussian_bumps()
@@ -222,8 +227,8 @@ def workload_device(name, dev):
     """The timed input on the device (and its host copy for the end-to-end leg)."""
     import torch
     import synth
-    if name == "turbulence1024":
-        xd = synth.turbulence(n=1024, device=dev)
+    if name in ("turbulence1024", "turbulence256"):
+        xd = synth.turbulence(n=1024 if name == "turbulence1024" else 256, device=dev)
         return xd, xd.cpu().numpy()
     x = synth.gaussian_bumps()
     return torch.from_numpy(x).to(dev), x
@@ -486,8 +491,9 @@ def run_ours(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "rel_eps": args.eps, "precision": args.precision,
                        "step": "atc_compress + atc_decompress",
-                       "l2": ("flushed (256 MB write) before each timed step" if args.workload == "bumps256" else
-                              "input 4.3 GB > L2 (and flushed before each timed step)"),
+                       "l2": ("input 4.3 GB > L2 (and flushed before each timed step)"
+                              if args.workload == "turbulence1024" else
+                              "flushed (256 MB write) before each timed step"),
                        "block_size": stats[-1].get("block_size"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "ranks": ranks, "achieved_rel_err": re, "stream_bytes": len(s),

@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(32) invit_par_kernel(EigState st, int nvec) {
 // of a chain of Gram-Schmidt reductions.  One CTA per group of at most
 // kQrMax vectors; larger groups are cut into blocks of kQrMax that are
 // orthonormalised in turn (block classical Gram-Schmidt, two passes, against
-// the earlier blocks, then CholQR2 inside the block: cholqr_range_kernel).
+// the earlier blocks, then CholQR2 inside the block across the GPU).
 constexpr int kQrMax = 48;
 // CholQR2 of the g <= kQrMax vectors Z + c * n (c < g), one CTA.
 __device__ void cholqr_block(double* __restrict__ Z, int g, int n, double* __restrict__ W) {
@@ -857,10 +857,58 @@ __global__ void __launch_bounds__(256) cholqr_group_kernel(EigState st, const in
   cholqr_block(st.z + (int64_t)g0 * st.n, g, st.n, W);
 }
 
-// CholQR2 of vectors k0 .. k1-1 (k1 - k0 <= kQrMax), one CTA.
-__global__ void __launch_bounds__(256) cholqr_range_kernel(EigState st, int k0, int k1) {
+
+// The same CholQR2 of one block of a large group spread over the GPU (the
+// block Gram-Schmidt of a large cluster runs its blocks in turn, so a one-CTA
+// block leaves the other SMs idle through a long FP64 chain): W = Z^T Z by
+// blk_dot_kernel (a warp per entry), the Cholesky factor by one warp
+// (cholqr_chol_kernel), Z <- Z R^-1 a thread per row (cholqr_trsm_kernel).
+// Every value is formed as in cholqr_block, in the same order.
+__global__ void __launch_bounds__(32) cholqr_chol_kernel(const double* __restrict__ Wg, int g, double* __restrict__ Rg) {
   __shared__ double W[kQrMax * kQrMax];
-  cholqr_block(st.z + (int64_t)k0 * st.n, k1 - k0, st.n, W);
+  const int lane = threadIdx.x;
+  for (int e = lane; e < g * g; e += 32) W[(e / g) * kQrMax + (e % g)] = Wg[e];
+  __syncwarp();
+  for (int k = 0; k < g; ++k) {
+    const double dkk = sqrt(fmax(W[k * kQrMax + k], 1e-300));
+    const double inv = 1.0 / dkk;
+    __syncwarp();
+    for (int c = k + 1 + lane; c < g; c += 32) W[k * kQrMax + c] *= inv;
+    if (lane == 0) W[k * kQrMax + k] = dkk;
+    __syncwarp();
+    for (int e = lane; e < (g - k - 1) * (g - k - 1); e += 32) {
+      const int a = k + 1 + e / (g - k - 1), c = k + 1 + e % (g - k - 1);
+      if (c >= a) W[a * kQrMax + c] -= W[k * kQrMax + a] * W[k * kQrMax + c];
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < kQrMax * kQrMax; e += 32) Rg[e] = W[e];
+}
+constexpr int kTrsmThreads = 8;  // rows per CTA: the rows spread over the SMs (FP64 is slow per SM)
+__global__ void __launch_bounds__(kTrsmThreads) cholqr_trsm_kernel(double* __restrict__ Z, int g, int n,
+                                                                    const double* __restrict__ Rg) {
+  __shared__ double R[kQrMax * kQrMax];
+  for (int e = threadIdx.x; e < kQrMax * kQrMax; e += blockDim.x) R[e] = Rg[e];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // forward substitution y R = z, right-looking (for each y_d the terms are
+  // subtracted in the order a = 0, 1, ..., as in cholqr_block)
+  double y[kQrMax];
+#pragma unroll
+  for (int c = 0; c < kQrMax; ++c) y[c] = (c < g) ? Z[(int64_t)c * n + i] : 0.0;
+#pragma unroll
+  for (int c = 0; c < kQrMax; ++c) {
+    if (c < g) {
+      y[c] = y[c] / R[c * kQrMax + c];
+#pragma unroll
+      for (int d = c + 1; d < kQrMax; ++d)
+        if (d < g) y[d] -= y[c] * R[c * kQrMax + d];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kQrMax; ++c)
+    if (c < g) Z[(int64_t)c * n + i] = y[c];
 }
 
 // Block Gram-Schmidt step against the earlier vectors g0 .. g0+np-1 of a group:
@@ -1502,7 +1550,8 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
   if (nvec <= 0) return ATC_OK;
   if (g_state.n != n) return fail(ATC_EINVAL, "eigenvectors requested without matching eigenvalues");
   EigState st = g_state;
-  ATC_TRY(Scratch::get(SLOT_EIG_Z, sizeof(double) * ((size_t)n * nvec * 6 + 2 * (size_t)nvec + 64), (void**)&st.z));
+  const size_t zlen = (size_t)n * nvec * 6 + 2 * (size_t)nvec + 64;
+  ATC_TRY(Scratch::get(SLOT_EIG_Z, sizeof(double) * (zlen + 2 * kQrMax * kQrMax), (void**)&st.z));
   st.lu = st.z + (size_t)n * nvec;
   int* grp = reinterpret_cast<int*>(st.lu + (size_t)5 * n * nvec);
   int* ngrp = grp + nvec + 2;
@@ -1521,6 +1570,8 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
   ATC_CUDA_TRY(cudaMemcpyAsync(&hn, ngrp, sizeof(int), cudaMemcpyDeviceToHost, s));
   ATC_CUDA_TRY(cudaStreamSynchronize(s));
   double* W = st.lu;  // the LU scratch of inverse iteration is free again (stream order)
+  double* Wq = st.z + zlen;  // CholQR Gram and factor of one block
+  double* Rq = Wq + kQrMax * kQrMax;
   for (int q = 0; q < hn && q < nvec; ++q) {
     const int g0 = hg[q], g1 = hg[q + 1];
     if (g1 - g0 <= kQrMax) continue;
@@ -1532,8 +1583,14 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
           blk_update_kernel<<<(int)(((int64_t)nb * n + 255) / 256), 256, 0, s>>>(st.z, n, g0, np, k0, nb, W);
           ATC_LAUNCHED(2);
         }
-        cholqr_range_kernel<<<1, 256, 0, s>>>(st, k0, k0 + nb);
-        ATC_LAUNCHED(1);
+        // CholQR2 of the block across the GPU (two passes, as cholqr_block)
+        for (int cq = 0; cq < 2; ++cq) {
+          blk_dot_kernel<<<(nb * nb + 7) / 8, 256, 0, s>>>(st.z, n, k0, nb, k0, nb, Wq);
+          cholqr_chol_kernel<<<1, 32, 0, s>>>(Wq, nb, Rq);
+          cholqr_trsm_kernel<<<(n + kTrsmThreads - 1) / kTrsmThreads, kTrsmThreads, 0, s>>>(
+              st.z + (int64_t)k0 * n, nb, n, Rq);
+          ATC_LAUNCHED(3);
+        }
       }
     }
   }

@@ -119,8 +119,25 @@ __device__ __forceinline__ u128 coef_err(uint64_t q, int p) {
   return (u128)d * d;
 }
 
-__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
-  return __shfl_sync(0xffffffffu, v, src);
+// D(p) = e(p+1) - e(p): the error reduction of coefficient v's bit on plane p
+// (signed; zero while v is zero through plane p), without forming either
+// square.  With c = 2^(p-1) and r = v mod 2^p:
+//   leading bit (v < 2^(p+1)):  q^2 - (r - c)^2 = 3c (c + 2r)
+//   trailing bit 1:  r^2 - (r - c)^2      = c (2r - c)
+//   trailing bit 0:  (2c - r)^2 - (r - c)^2 = c (3c - 2r)
+// (the reconstruction of Section 4.3; plane 0, where c is not an integer,
+// takes the two squares).  |D| < 2^128 (leading), < 2^126 (trailing).
+__device__ __forceinline__ I192 plane_reduction(uint64_t v, int p) {
+  if ((v >> p) == 0) return i192_zero();
+  if (p == 0) return i192_diff(coef_err(v, 1), coef_err(v, 0));
+  const uint64_t c = 1ull << (p - 1);
+  const uint64_t r = v & ((c << 1) - 1ull);
+  const bool above = (p < 63) && ((v >> (p + 1)) != 0);
+  if (!above) return i192_from_u128(((u128)3 * ((u128)c + 2 * (u128)r)) << (p - 1));
+  const bool bit = (v >> p) & 1ull;
+  const __int128 base = bit ? (__int128)2 * r - (__int128)c : (__int128)3 * c - (__int128)2 * r;
+  const I192 m = i192_from_u128((u128)(base < 0 ? -base : base) << (p - 1));
+  return base < 0 ? i192_neg(m) : m;
 }
 __device__ __forceinline__ uint64_t shfl_down_u64(uint64_t v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
 
@@ -240,7 +257,7 @@ __global__ void scale_exp_kernel(const unsigned long long* __restrict__ mx, doub
 
 // Per segment (one CTA, contiguous coefficients) and plane p in [plo, plo+15]:
 // the ordered summary of D_i(p); plus sum q_i^2 when first_pass.
-__global__ void __launch_bounds__(kSegThreads) plane_stats_kernel(const uint64_t* __restrict__ q, int64_t n,
+__global__ void __launch_bounds__(kSegThreads, 2) plane_stats_kernel(const uint64_t* __restrict__ q, int64_t n,
                                                                    int64_t seg_len, int plo, int phi, int first_pass,
                                                                    Seg* __restrict__ out, I192* __restrict__ e64_out) {
   __shared__ Seg wsum[kSegThreads / 32];
@@ -277,13 +294,16 @@ __global__ void __launch_bounds__(kSegThreads) plane_stats_kernel(const uint64_t
       a[k].m = i192_zero();
       a[k].empty = (t_lo >= t_hi);
     }
+    const int pgl = max(plo, pg - kPlaneGroup + 1);  // lowest plane of this group
     for (int64_t i = t_lo; i < t_hi; ++i) {
       const uint64_t v = q[i];
+      // zero through every plane of the group: D = 0 there, and skipping it
+      // leaves both the sum and the largest prefix (which starts at 0) unchanged
+      if ((v >> pgl) == 0) continue;
 #pragma unroll
       for (int k = 0; k < kPlaneGroup; ++k) {
         const int p = pg - k;
-        I192 d = i192_zero();
-        if (p >= plo && (v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+        const I192 d = (p >= plo) ? plane_reduction(v, p) : i192_zero();
         a[k].s = i192_add(a[k].s, d);
         if (i192_lt(a[k].m, a[k].s) || i == t_lo) a[k].m = a[k].s;
       }
@@ -462,8 +482,7 @@ __global__ void __launch_bounds__(kIstarThreads) istar_kernel(const uint64_t* __
   a.s = a.m = i192_zero();
   for (int64_t i = t_lo; i < t_hi; ++i) {
     const uint64_t v = q[i];
-    I192 d = i192_zero();
-    if ((v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+    const I192 d = plane_reduction(v, p);
     if (a.empty) { a.s = d; a.m = d; a.empty = 0; }
     else {
       a.s = i192_add(a.s, d);
@@ -480,8 +499,7 @@ __global__ void __launch_bounds__(kIstarThreads) istar_kernel(const uint64_t* __
     I192 run = i192_sub(E1, pre2);
     for (int64_t i = t_lo; i < t_hi; ++i) {
       const uint64_t v = q[i];
-      I192 d = i192_zero();
-      if ((v >> p) != 0) d = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+      const I192 d = plane_reduction(v, p);
       run = i192_sub(run, d);
       if (i192_le(run, T)) {
         st->i_star = i;
@@ -501,7 +519,7 @@ __device__ __forceinline__ I192 cat_reduction(uint64_t v, int p, int cat) {
   if ((v >> p) == 0) return i192_zero();
   const int sig = (p == 63) ? 0 : ((v >> (p + 1)) != 0 ? 1 : 0);
   if (sig != cat) return i192_zero();
-  return i192_diff(coef_err(v, p + 1), coef_err(v, p));
+  return plane_reduction(v, p);
 }
 
 // Per segment of the tracker's segmentation: the ordered summaries of the
@@ -559,7 +577,7 @@ __global__ void __launch_bounds__(kSegThreads) split_stats_kernel(const uint64_t
     const uint64_t v = q[i];
     if ((v >> p) != 0) {
       const int sig = (p == 63) ? 0 : ((v >> (p + 1)) != 0 ? 1 : 0);
-      const I192 r = i192_diff(coef_err(v, p + 1), coef_err(v, p));
+      const I192 r = plane_reduction(v, p);
       // only the category the bit belongs to moves; the other keeps its prefix
       if (sig) {
         a[1].s = i192_add(a[1].s, r);
@@ -570,7 +588,7 @@ __global__ void __launch_bounds__(kSegThreads) split_stats_kernel(const uint64_t
       }
       if (above && (v >> (p + 1)) != 0) {
         const int sig1 = (p + 1 == 63) ? 0 : ((v >> (p + 2)) != 0 ? 1 : 0);
-        const I192 r1 = i192_diff(coef_err(v, p + 2), coef_err(v, p + 1));
+        const I192 r1 = plane_reduction(v, p + 1);
         if (sig1) { d[1] = i192_add(d[1], r1); ++c[1]; }
         else { d[0] = i192_add(d[0], r1); ++c[0]; }
       }
@@ -1916,6 +1934,194 @@ __global__ void __launch_bounds__(kDecThreads) decode_place_kernel(DecParams D, 
   }
 }
 
+// Blocks of at most 512 coefficients: one WARP per block (16 consecutive
+// coefficients a lane), the placement of decode_place_kernel with warp scans
+// instead of block scans, so a plane costs no CTA barrier.  The block's size
+// table entries, plane offsets and (when it fits) its whole payload are
+// staged in shared memory first, and the runs of plane p + 1 are loaded while
+// plane p is placed, so the plane loop waits on no global load.  Same result.
+constexpr int kWDecPer = 16;
+constexpr int kWDecMax = 32 * kWDecPer;
+constexpr int kWDecWarps = 4;    // blocks per CTA
+constexpr int kWDecStage = 5120; // payload bytes staged per block
+__device__ __forceinline__ int64_t warp_exscan64(int64_t v, int64_t* total) {
+  const int lane = threadIdx.x & 31;
+  int64_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  *total = __shfl_sync(0xffffffffu, inc, 31);
+  return inc - v;
+}
+
+__global__ void __launch_bounds__(32 * kWDecWarps) decode_place_warp_kernel(DecParams D,
+                                                                            const uint32_t* __restrict__ runs,
+                                                                            const int* __restrict__ nruns) {
+  __shared__ unsigned long long qs_all[kWDecWarps][kWDecMax];
+  __shared__ uint8_t ss_all[kWDecWarps][kWDecMax];
+  __shared__ uint32_t nb_all[kWDecWarps][kWDecMax / 32];
+  __shared__ uint32_t rl_all[kWDecWarps][64], wl_all[kWDecWarps][64], po_all[kWDecWarps][64];
+  __shared__ int nr_all[kWDecWarps][64];
+  __shared__ __align__(16) uint8_t pay_all[kWDecWarps][kWDecStage];
+  constexpr int kRunPerW = (kWDecMax + 2 + 31) / 32;  // runs per lane (17)
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * kWDecWarps + w;
+  if (b >= D.nblocks) return;  // the whole warp: nothing below synchronises the CTA
+  unsigned long long* qs = qs_all[w];
+  uint8_t* ss = ss_all[w];
+  uint32_t* newbm = nb_all[w];
+  uint32_t *rlp = rl_all[w], *wlp = wl_all[w], *pop = po_all[w];
+  int* nrp = nr_all[w];
+  uint8_t* pay = pay_all[w];
+  const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
+  const int cap = D.block_size + 2;
+  for (int i = lane; i < kWDecMax; i += 32) { qs[i] = 0; ss[i] = 0; }
+  int err = (*D.err != 0) ? -1 : 0;
+  err = __reduce_max_sync(0xffffffffu, err);
+  if (err) return;
+  // size table entries, run counts and payload offsets of this block's planes
+  const uint64_t base = D.boff[b];
+  uint64_t acc = 0;
+  for (int p0 = 0; p0 < D.nplanes; p0 += 32) {
+    const int pi = p0 + lane;
+    uint32_t rl = 0, wl = 0;
+    int nr = 0;
+    if (pi < D.nplanes) {
+      const uint8_t* te = D.sec + D.tab + (b * D.nplanes + pi) * 8;
+      rl = rd32(te);
+      wl = rd32(te + 4);
+      nr = nruns[b * D.nplanes + pi];
+    }
+    int64_t tot = 0;
+    const int64_t ex = warp_exscan64((int64_t)rl + wl, &tot);
+    if (pi < D.nplanes) {
+      rlp[pi] = rl;
+      wlp[pi] = wl;
+      nrp[pi] = nr;
+      pop[pi] = (uint32_t)(acc + (uint64_t)ex);
+    }
+    acc += (uint64_t)tot;
+  }
+  if (base + acc > (uint64_t)D.nbytes) err = 2;
+  const bool staged = acc <= (uint64_t)kWDecStage;
+  if (staged && !err)
+    for (uint32_t i = lane; i < (uint32_t)acc; i += 32) pay[i] = __ldg(D.sec + base + i);
+  __syncwarp();
+  if (err) {
+    if (lane == 0) atomicExch(D.err, err);
+    return;
+  }
+  const int64_t j0 = lo + (int64_t)lane * kWDecPer;
+  const int k0 = lane * kRunPerW;
+  uint32_t rcur[kRunPerW];
+  {
+    const int nr0 = D.nplanes > 0 ? nrp[0] : 0;
+    const uint32_t* rr = runs + (b * D.nplanes) * (int64_t)cap;
+#pragma unroll
+    for (int u = 0; u < kRunPerW; ++u) rcur[u] = (k0 + u < nr0) ? __ldg(rr + k0 + u) : 0u;
+  }
+  for (int pi = 0; pi < D.nplanes; ++pi) {
+    const int p = 63 - pi;
+    const int64_t hl = cat_end(lo, hi_all, p, D.p_star, D.i_lead), ht = cat_end(lo, hi_all, p, D.p_star, D.i_trail);
+    if (lane < kWDecMax / 32) newbm[lane] = 0u;
+    const uint32_t rl = rlp[pi], wl = wlp[pi];
+    const int nr = nrp[pi];
+    // the next plane's runs, loaded while this plane is placed
+    uint32_t rnext[kRunPerW];
+    {
+      const int nrn = (pi + 1 < D.nplanes) ? nrp[pi + 1] : 0;
+      const uint32_t* rr = runs + (b * D.nplanes + pi + 1) * (int64_t)cap;
+#pragma unroll
+      for (int u = 0; u < kRunPerW; ++u) rnext[u] = (k0 + u < nrn) ? __ldg(rr + k0 + u) : 0u;
+    }
+    uint32_t sigm = 0, actm = 0;
+#pragma unroll
+    for (int u = 0; u < kWDecPer; ++u) {
+      const int64_t j = j0 + u;
+      if (j < hi_all) {
+        const bool sg_ = qs[j - lo] != 0;
+        if (sg_ ? j < ht : j < hl) {
+          actm |= 1u << u;
+          if (sg_) sigm |= 1u << u;
+        }
+      }
+    }
+    int64_t n_insig = 0;
+    const int64_t rank0 = warp_exscan64(__popc(actm & ~sigm), &n_insig);
+    __syncwarp();
+    if (nr == kRunsImplicit) {
+      for (int64_t r = lane; r < n_insig; r += 32) atomicOr(&newbm[r >> 5], 1u << (r & 31));
+    } else {
+      int64_t loc = 0;
+#pragma unroll
+      for (int u = 0; u < kRunPerW; ++u)
+        if (k0 + u < nr) loc += (int64_t)rcur[u] + 1;
+      int64_t total = 0;
+      int64_t q = warp_exscan64(loc, &total);
+#pragma unroll
+      for (int u = 0; u < kRunPerW; ++u) {
+        const int k = k0 + u;
+        if (k < nr) {
+          const int64_t at = q + rcur[u];  // rank of this run's 1
+          if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rcur[u] + 1)) err = 11;  // symbol count
+          if (at < n_insig) atomicOr(&newbm[at >> 5], 1u << (at & 31));
+          q += (int64_t)rcur[u] + 1;
+        }
+      }
+      if (nr == 0 && n_insig > 0) err = 5;
+    }
+    err = __reduce_max_sync(0xffffffffu, err);
+    __syncwarp();
+    if (err) break;
+    uint32_t newm = 0;
+    {
+      int64_t r = rank0;
+      for (int u = 0; u < kWDecPer; ++u)
+        if ((actm >> u & 1u) && !(sigm >> u & 1u)) {
+          if (newbm[r >> 5] >> (r & 31) & 1u) newm |= 1u << u;
+          ++r;
+        }
+    }
+    const uint32_t consm = sigm | newm;
+    int64_t ncons = 0;
+    const int64_t rb0 = warp_exscan64(__popc(consm), &ncons);
+    if ((uint64_t)ncons > (uint64_t)wl * 8) {
+      err = 4;
+      break;
+    }
+    const uint32_t roff = pop[pi] + rl;  // raw bytes of this plane, relative to the block's payload
+    int64_t rbit = rb0;
+    for (int u = 0; u < kWDecPer; ++u) {
+      if (!(consm >> u & 1u)) continue;
+      const uint32_t byte = staged ? pay[roff + (uint32_t)(rbit >> 3)] : __ldg(D.sec + base + roff + (rbit >> 3));
+      const uint32_t bit = (byte >> (rbit & 7)) & 1u;
+      ++rbit;
+      const int64_t jj = j0 + u - lo;
+      if (sigm >> u & 1u) qs[jj] |= (unsigned long long)bit << p;
+      else { qs[jj] |= 1ull << p; ss[jj] = (uint8_t)bit; }
+    }
+#pragma unroll
+    for (int u = 0; u < kRunPerW; ++u) rcur[u] = rnext[u];
+    __syncwarp();
+  }
+  if (err) {
+    if (lane == 0 && err > 0) atomicExch(D.err, err);
+    return;
+  }
+  for (int u = 0; u < kWDecPer; ++u) {
+    const int64_t j = j0 + u;
+    if (j >= hi_all) break;
+    const uint64_t a = qs[j - lo];
+    if (a == 0) { D.out[j] = 0.0; continue; }
+    const int pj = lowest_plane(a, j, D.p_star, D.i_trail);
+    const uint64_t v = a + ((pj >= 1) ? (1ull << (pj - 1)) : 0ull);
+    const double m = mul_pow2(__ull2double_rn(v), -D.k);
+    D.out[j] = ss[j - lo] ? -m : m;
+  }
+}
+
 static void put32(uint8_t* p, uint32_t v) { for (int i = 0; i < 4; ++i) p[i] = (uint8_t)(v >> (8 * i)); }
 static void put64(uint8_t* p, uint64_t v) { for (int i = 0; i < 8; ++i) p[i] = (uint8_t)(v >> (8 * i)); }
 static uint32_t get32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i); return v; }
@@ -2329,7 +2535,11 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
       KTimed kt_(s, "decode_runs_kernel");
       decode_runs_kernel<<<(unsigned)((nchunk + 63) / 64), 64, 0, s>>>(RP);
     }
-    {
+    if (D.block_size <= kWDecMax) {
+      KTimed kt_(s, "decode_place_warp_kernel");
+      decode_place_warp_kernel<<<(unsigned)((D.nblocks + kWDecWarps - 1) / kWDecWarps), 32 * kWDecWarps, 0, s>>>(
+          D, RP.runs, RP.nruns);
+    } else {
       KTimed kt_(s, "decode_place_kernel");
       decode_place_kernel<<<(unsigned)D.nblocks, kDecThreads, 0, s>>>(D, RP.runs, RP.nruns);
     }
