@@ -196,7 +196,8 @@ struct atc_compressed {
   int64_t ranks[8] = {};
   double* core = nullptr;      // device, FP64, (r_1..r_d)
   double* factors[8] = {};     // device, FP64, n_i x r_i
-  std::string stream;          // host
+  uint8_t* stream = nullptr;   // host (malloc), stream_n bytes
+  size_t stream_n = 0;
   atc_stats stats = {};
 };
 
@@ -392,6 +393,7 @@ std::vector<int> decompression_order(int d, const int64_t* dims, const int64_t* 
 
 void free_compressed(atc_compressed* c) {
   if (!c) return;
+  free(c->stream);
   if (c->core) cudaFree(c->core);
   for (int i = 0; i < 8; ++i)
     if (c->factors[i]) cudaFree(c->factors[i]);
@@ -565,12 +567,19 @@ int atc_ttm(const void* x_dev, int xdtype, int64_t L, int64_t n, int64_t R, cons
 int atc_quantize_core(const double* core_dev, int64_t n, double target_sse, int block_size, void* stream,
                       uint8_t** bytes, size_t* nbytes, int64_t* info) {
   if (!core_dev || n < 1 || !bytes || !nbytes) return fail(ATC_EINVAL, "atc_quantize_core: bad arguments");
-  std::string out;
+  QuantSection out;
   QuantResult qr;
   ATC_TRY(quantize_encode(core_dev, n, target_sse, block_size, (cudaStream_t)stream, &out, &qr, nullptr, nullptr));
   uint8_t* buf = (uint8_t*)malloc(out.size() ? out.size() : 1);
   if (!buf) return fail(ATC_ENOMEM, "host allocation failed");
-  memcpy(buf, out.data(), out.size());
+  memcpy(buf, out.head.data(), out.head.size());
+  if (out.payload_bytes &&
+      (cudaMemcpyAsync(buf + out.head.size(), out.payload, out.payload_bytes, cudaMemcpyDeviceToHost,
+                       (cudaStream_t)stream) != cudaSuccess ||
+       cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)) {
+    free(buf);
+    return fail(ATC_ECUDA, "core section readback failed");
+  }
   *bytes = buf;
   *nbytes = out.size();
   if (info) {
@@ -934,7 +943,7 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   if (rc) return bail(rc);
   rc = launch_permute(c->core, c->ranks, perm.data(), d, vec, 0, s);
   if (rc) return bail(rc);
-  std::string section;
+  QuantSection section;
   QuantResult qr;
   float msq = 0.f, mse = 0.f;
   clk.mark(PH_OTHER);
@@ -976,7 +985,7 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
       return bail(fail(ATC_ECUDA, "factor readback failed"));
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ATC_ECUDA, "stream synchronisation failed"));
-  std::string& S = c->stream;
+  std::string S;  // everything before the core section
   S.append("ATC1", 4);
   put32(S, 2);
   put32(S, (uint32_t)d);
@@ -1008,7 +1017,18 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
     }
   }
   put64(S, (uint64_t)section.size());
-  S.append(section);
+  // one uninitialised host buffer; the core section's payload goes there
+  // straight from the device
+  c->stream_n = S.size() + section.size();
+  c->stream = (uint8_t*)malloc(c->stream_n);
+  if (!c->stream) return bail(fail(ATC_ENOMEM, "stream allocation failed"));
+  memcpy(c->stream, S.data(), S.size());
+  memcpy(c->stream + S.size(), section.head.data(), section.head.size());
+  if (section.payload_bytes &&
+      (cudaMemcpyAsync(c->stream + S.size() + section.head.size(), section.payload, section.payload_bytes,
+                       cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    return bail(fail(ATC_ECUDA, "core section readback failed"));
   clk.mark(PH_OTHER);
   int he_end = 0;
   if (tc_err && cudaMemcpyAsync(&he_end, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -1048,8 +1068,8 @@ int atc_get_factor(const atc_compressed* c, int mode, const double** u_dev) {
 
 int atc_get_stream(const atc_compressed* c, const uint8_t** bytes, size_t* nbytes) {
   if (!c || !bytes || !nbytes) return fail(ATC_EINVAL, "atc_get_stream: bad arguments");
-  *bytes = (const uint8_t*)c->stream.data();
-  *nbytes = c->stream.size();
+  *bytes = c->stream;
+  *nbytes = c->stream_n;
   return ATC_OK;
 }
 

@@ -83,6 +83,7 @@ enum ScratchSlot {
   SLOT_SUB_V0,         // subspace-iteration start frame (kept while n and K stay the same)
   SLOT_TTM_AIMG,       // pre-sliced data operand of products with several output chunks
   SLOT_KEPT,           // per-slice significance flags of the quantized core
+  SLOT_SCAN,           // range sums of the multi-CTA offset scans
   SLOT_COUNT
 };
 
@@ -164,8 +165,17 @@ struct QuantResult {
   int64_t i_trail; // last trailing bit of plane p_star encoded (-1: none)
   double sse_pred;
 };
+// The encoded "ATCQ" section: its fixed header and frequency tables on the
+// host, the rest (size table + chunk bytes) left on the device for the caller
+// to copy straight into its own buffer (valid until the next call on this device).
+struct QuantSection {
+  std::vector<uint8_t> head;
+  const uint8_t* payload = nullptr;
+  size_t payload_bytes = 0;
+  size_t size() const { return head.size() + payload_bytes; }
+};
 int quantize_encode(const double* core, int64_t n, double target, int block_size, cudaStream_t s,
-                    std::string* out, QuantResult* res, float* ms_quant, float* ms_encode);
+                    QuantSection* out, QuantResult* res, float* ms_quant, float* ms_encode);
 int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t n, cudaStream_t s);
 // slices of the last quantized core holding a significant coefficient (k_quant.cu)
 int core_kept_slices(int64_t n, const int64_t* ranks, const int* perm, int d, int p_star, int64_t i_lead,

@@ -1323,26 +1323,123 @@ __global__ void enc_rans_thread_kernel(RansThreadParams P, int write) {
   P.table[2 * chunk + 1] = ws;
 }
 
-// exclusive scan of rsize + wsize in chunk order (single CTA, sequential per thread slice)
-__global__ void scan_kernel(const uint32_t* __restrict__ rs, const uint32_t* __restrict__ ws, int64_t nchunks,
-                            uint64_t* __restrict__ off) {
-  __shared__ uint64_t part[1024];
-  const int t = threadIdx.x, T = blockDim.x;
-  const int64_t per = (nchunks + T - 1) / T;
-  const int64_t lo = min(nchunks, (int64_t)t * per), hi = min(nchunks, lo + per);
-  uint64_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += (uint64_t)rs[i] + ws[i];
-  part[t] = s;
-  __syncthreads();
-  if (t == 0) {
-    uint64_t a = 0;
-    for (int i = 0; i < T; ++i) { uint64_t v = part[i]; part[i] = a; a += v; }
-    off[nchunks] = a;
+// Exclusive prefix sums of item sizes f(i) over many CTAs (the payload
+// offsets of the encoder's chunks and of the decoder's blocks): each CTA sums
+// a contiguous range, one CTA scans the range sums, then each CTA writes the
+// offsets of its range (threads on contiguous sub-ranges, a block scan
+// between them).  Sums of u64 are exact, so the offsets equal the sequential ones.
+constexpr int kScanThreads = 1024;
+struct ChunkBytes {
+  const uint32_t* rs;
+  const uint32_t* ws;
+  __device__ unsigned long long operator()(int64_t i) const { return (unsigned long long)rs[i] + ws[i]; }
+};
+struct BlockBytes {
+  const uint8_t* tab;
+  int nplanes;
+  __device__ unsigned long long operator()(int64_t b) const {
+    unsigned long long t = 0;
+    for (int pi = 0; pi < nplanes; ++pi) {
+      const uint8_t* e = tab + (b * nplanes + pi) * 8;
+      t += (unsigned long long)(e[0] | (e[1] << 8) | (e[2] << 16) | ((uint32_t)e[3] << 24)) +
+           (unsigned long long)(e[4] | (e[5] << 8) | (e[6] << 16) | ((uint32_t)e[7] << 24));
+    }
+    return t;
+  }
+};
+__device__ __forceinline__ unsigned long long block_exscan_u64(unsigned long long v, unsigned long long* sh,
+                                                               unsigned long long* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
   }
   __syncthreads();
-  uint64_t a = part[t];
-  for (int64_t i = lo; i < hi; ++i) { off[i] = a; a += (uint64_t)rs[i] + ws[i]; }
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long x = (lane < nw) ? sh[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane < nw) sh[lane] = x;
+  }
+  __syncthreads();
+  *total = sh[nw - 1];
+  return (w > 0 ? sh[w - 1] : 0ull) + inc - v;
 }
+template <typename F>
+__global__ void __launch_bounds__(kScanThreads) range_sum_kernel(F f, int64_t N, int64_t per_cta,
+                                                                 unsigned long long* __restrict__ part) {
+  __shared__ unsigned long long sh[32];
+  const int64_t c0 = (int64_t)blockIdx.x * per_cta, c1 = min(N, c0 + per_cta);
+  unsigned long long v = 0;
+  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) v += f(i);
+  unsigned long long tot;
+  block_exscan_u64(v, sh, &tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+// part[0..G) -> exclusive prefixes in place (from base); *end = base + the
+// total, and *err = 1 if that exceeds limit (err may be null)
+__global__ void __launch_bounds__(kScanThreads) range_top_kernel(unsigned long long* __restrict__ part, int G,
+                                                                 unsigned long long base, uint64_t* __restrict__ end,
+                                                                 unsigned long long limit, int* __restrict__ err) {
+  __shared__ unsigned long long sh[32];
+  const int per = (G + kScanThreads - 1) / kScanThreads;
+  const int t0 = min(G, (int)threadIdx.x * per), t1 = min(G, t0 + per);
+  unsigned long long v = 0;
+  for (int i = t0; i < t1; ++i) v += part[i];
+  unsigned long long tot;
+  unsigned long long run = base + block_exscan_u64(v, sh, &tot);
+  for (int i = t0; i < t1; ++i) {
+    const unsigned long long x = part[i];
+    part[i] = run;
+    run += x;
+  }
+  if (threadIdx.x == 0) {
+    *end = base + tot;
+    if (err && base + tot > limit) atomicExch(err, 1);
+  }
+}
+template <typename F>
+__global__ void __launch_bounds__(kScanThreads) range_write_kernel(F f, int64_t N, int64_t per_cta,
+                                                                   const unsigned long long* __restrict__ part,
+                                                                   uint64_t* __restrict__ out) {
+  __shared__ unsigned long long sh[32];
+  const int64_t c0 = (int64_t)blockIdx.x * per_cta, c1 = min(N, c0 + per_cta);
+  const int64_t per = (per_cta + kScanThreads - 1) / kScanThreads;
+  const int64_t t0 = min(c1, c0 + (int64_t)threadIdx.x * per), t1 = min(c1, t0 + per);
+  unsigned long long v = 0;
+  for (int64_t i = t0; i < t1; ++i) v += f(i);
+  unsigned long long tot;
+  unsigned long long run = part[blockIdx.x] + block_exscan_u64(v, sh, &tot);
+  for (int64_t i = t0; i < t1; ++i) {
+    out[i] = run;
+    run += f(i);
+  }
+}
+// out[0..N) = exclusive prefixes of f (from base), out[N] = base + the total
+// (err set when it exceeds limit); scratch: range_scan_parts(N) u64
+int range_scan_parts(int64_t N) {
+  const int64_t g = (N + 4095) / 4096;
+  return (int)(g < 1 ? 1 : (g > 1216 ? 1216 : g));
+}
+template <typename F>
+int range_scan(F f, int64_t N, unsigned long long base, unsigned long long* scratch, uint64_t* out,
+               unsigned long long limit, int* err, cudaStream_t s) {
+  const int G = range_scan_parts(N);
+  const int64_t per_cta = (N + G - 1) / G;
+  range_sum_kernel<F><<<G, kScanThreads, 0, s>>>(f, N, per_cta, scratch);
+  range_top_kernel<<<1, kScanThreads, 0, s>>>(scratch, G, base, out + N, limit, err);
+  range_write_kernel<F><<<G, kScanThreads, 0, s>>>(f, N, per_cta, scratch, out);
+  ATC_LAUNCHED(3);
+  return ATC_OK;
+}
+
 
 // ------------------------------------------------------------------- decoder
 struct DecParams {
@@ -1373,56 +1470,6 @@ __device__ __forceinline__ int lowest_plane(uint64_t a, int64_t j, int p_star, i
 
 __device__ __forceinline__ uint32_t rd32(const uint8_t* p) {
   return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-}
-
-// Payload offset of every block: the sizes of its (block, plane) chunks from
-// the size table, summed per contiguous range of blocks by each thread, then a
-// block-wide exclusive scan (one CTA of kOffThreads).
-constexpr int kOffThreads = 1024;
-__global__ void __launch_bounds__(kOffThreads) block_offsets_kernel(DecParams D, uint64_t* boff) {
-  __shared__ unsigned long long sh[32];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t per = (D.nblocks + kOffThreads - 1) / kOffThreads;
-  const int64_t b0 = min((int64_t)tid * per, D.nblocks), b1 = min(D.nblocks, b0 + per);
-  auto block_bytes = [&](int64_t b) -> unsigned long long {
-    unsigned long long t = 0;
-    for (int pi = 0; pi < D.nplanes; ++pi) {
-      const uint8_t* e = D.sec + D.tab + (b * D.nplanes + pi) * 8;
-      t += (unsigned long long)rd32(e) + rd32(e + 4);
-    }
-    return t;
-  };
-  unsigned long long mine = 0;
-  for (int64_t b = b0; b < b1; ++b) mine += block_bytes(b);
-  unsigned long long inc = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += u;
-  }
-  if (lane == 31) sh[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    unsigned long long x = sh[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long u = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += u;
-    }
-    sh[lane] = x;
-  }
-  __syncthreads();
-  const unsigned long long base = D.tab + (unsigned long long)D.nblocks * D.nplanes * 8;
-  unsigned long long pos = base + (w > 0 ? sh[w - 1] : 0ull) + (inc - mine);
-  for (int64_t b = b0; b < b1; ++b) {
-    boff[b] = pos;
-    pos += block_bytes(b);
-  }
-  if (tid == 0) {
-    const unsigned long long end = base + sh[31];
-    boff[D.nblocks] = end;
-    if (end > (unsigned long long)D.nbytes) atomicExch(D.err, 1);
-  }
 }
 
 // One thread per block: planes 63 .. p_star in order, then dequantize.
@@ -1819,102 +1866,151 @@ __global__ void decode_runs_kernel(RunParams P) {
   *nr = k;
 }
 
+// Phase B, one CTA per block of at most kDecMax coefficients, 16 consecutive
+// coefficients a thread held in registers (magnitudes, significance and sign
+// masks: no shared-memory traffic per coefficient and plane).  Per plane: one
+// block scan gives both the thread's first rank among the active leading bits
+// and its first position in the run list (two 32-bit counts in one 64-bit
+// sum); the runs mark the new leading 1s in a shared bit map; a second scan
+// places the thread's raw bits, read as one window of at most three bytes.
 __global__ void __launch_bounds__(kDecThreads) decode_place_kernel(DecParams D, const uint32_t* __restrict__ runs,
                                                                    const int* __restrict__ nruns) {
-  __shared__ unsigned long long qs[kDecMax];
-  __shared__ uint8_t ss[kDecMax];
-  __shared__ uint32_t newbm[kDecMax / 32];
+  __shared__ uint32_t newbm[kDecMax / 32 + 2];
   __shared__ int64_t scan_sh[24];
   __shared__ int s_err;
-  __shared__ uint32_t s_rl, s_wl;
+  __shared__ uint32_t s_rl[64], s_wl[64], s_po[64];
+  __shared__ int s_nr[64];
   constexpr int kRunPer = (kDecMax + 2 + kDecThreads - 1) / kDecThreads;  // runs per thread (17)
   const int64_t b = blockIdx.x;
   const int tid = threadIdx.x;
   const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
   const int cap = D.block_size + 2;
-  for (int i = tid; i < kDecMax; i += kDecThreads) { qs[i] = 0; ss[i] = 0; }
   if (tid == 0) s_err = (*D.err != 0) ? -1 : 0;
+  // size table, run counts and payload offsets of the block's planes
+  const uint64_t base = D.boff[b];
+  if (tid < 32) {
+    uint64_t acc = 0;
+    for (int p0 = 0; p0 < D.nplanes; p0 += 32) {
+      const int pi = p0 + tid;
+      uint32_t rl = 0, wl = 0;
+      int nr = 0;
+      if (pi < D.nplanes) {
+        const uint8_t* te = D.sec + D.tab + (b * D.nplanes + pi) * 8;
+        rl = rd32(te);
+        wl = rd32(te + 4);
+        nr = nruns[b * D.nplanes + pi];
+      }
+      uint64_t inc = (uint64_t)rl + wl;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (tid >= o) inc += t;
+      }
+      if (pi < D.nplanes) {
+        s_rl[pi] = rl;
+        s_wl[pi] = wl;
+        s_nr[pi] = nr;
+        s_po[pi] = (uint32_t)(acc + inc - ((uint64_t)rl + wl));
+      }
+      acc += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (tid == 0 && base + acc > (uint64_t)D.nbytes && s_err == 0) s_err = 2;
+  }
   __syncthreads();
-  if (s_err) return;
-  uint64_t pos = D.boff[b];
+  if (s_err) {
+    if (tid == 0 && s_err > 0) atomicExch(D.err, s_err);
+    return;
+  }
   const int64_t j0 = lo + (int64_t)tid * kDecPer;
+  const int nvalid = (int)max((int64_t)0, min((int64_t)kDecPer, hi_all - j0));
+  uint64_t qv[kDecPer];
+#pragma unroll
+  for (int u = 0; u < kDecPer; ++u) qv[u] = 0;
+  uint32_t sigall = 0, sgn = 0;  // significant so far, sign bits
+  const int k0 = tid * kRunPer;
   for (int pi = 0; pi < D.nplanes; ++pi) {
     const int p = 63 - pi;
     const int64_t hl = cat_end(lo, hi_all, p, D.p_star, D.i_lead), ht = cat_end(lo, hi_all, p, D.p_star, D.i_trail);
-    for (int i = tid; i < kDecMax / 32; i += kDecThreads) newbm[i] = 0u;
-    if (tid == 0) {
-      const uint8_t* t = D.sec + D.tab + (b * D.nplanes + pi) * 8;
-      s_rl = rd32(t);
-      s_wl = rd32(t + 4);
-    }
-    // active: a significant coefficient before ht (trailing bit), an
+    for (int i = tid; i < kDecMax / 32 + 2; i += kDecThreads) newbm[i] = 0u;
+    // active coefficients: a significant one before ht (trailing bit), an
     // insignificant one before hl (leading bit)
-    uint32_t sigm = 0, actm = 0;
-    for (int u = 0; u < kDecPer; ++u) {
-      const int64_t j = j0 + u;
-      if (j < hi_all) {
-        const bool sg_ = qs[j - lo] != 0;
-        if (sg_ ? j < ht : j < hl) {
-          actm |= 1u << u;
-          if (sg_) sigm |= 1u << u;
-        }
-      }
+    const int nt = (int)max((int64_t)0, min((int64_t)nvalid, ht - j0));
+    const int nl = (int)max((int64_t)0, min((int64_t)nvalid, hl - j0));
+    const uint32_t lowt = nt >= 32 ? ~0u : ((1u << nt) - 1u), lowl = nl >= 32 ? ~0u : ((1u << nl) - 1u);
+    const uint32_t sigm = sigall & lowt, insm = ~sigall & lowl;
+    const int nr = s_nr[pi];
+    const uint32_t* rr = runs + (b * D.nplanes + pi) * (int64_t)cap;
+    uint32_t rv[kRunPer];
+    int64_t loc = 0;
+#pragma unroll
+    for (int u = 0; u < kRunPer; ++u) {
+      rv[u] = (nr != kRunsImplicit && k0 + u < nr) ? __ldg(rr + k0 + u) : 0u;
+      if (nr != kRunsImplicit && k0 + u < nr) loc += (int64_t)rv[u] + 1;
     }
-    int64_t n_insig = 0;
-    const int64_t rank0 = dec_scan(__popc(actm & ~sigm), scan_sh, &n_insig);  // (barriers inside)
-    // runs -> ranks of the new leading bits
-    const int64_t chunk = b * D.nplanes + pi;
-    const int nr = nruns[chunk];
+    // one scan: (insignificant active count) << 32 | (run-list position)
+    int64_t tot = 0;
+    const int64_t ex = dec_scan(((int64_t)__popc(insm) << 32) | loc, scan_sh, &tot);
+    const int64_t rank0 = ex >> 32, n_insig = tot >> 32;
+    int64_t q = ex & 0xffffffffll;
     if (nr == kRunsImplicit) {
       for (int64_t r = tid; r < n_insig; r += kDecThreads) atomicOr(&newbm[r >> 5], 1u << (r & 31));
     } else {
-      const uint32_t* rr = runs + chunk * (int64_t)cap;
-      const int k0 = tid * kRunPer;
-      int64_t loc = 0;
-      for (int u = 0; u < kRunPer; ++u)
-        if (k0 + u < nr) loc += (int64_t)rr[k0 + u] + 1;
-      int64_t total = 0;
-      int64_t q = dec_scan(loc, scan_sh, &total);
+#pragma unroll
       for (int u = 0; u < kRunPer; ++u) {
         const int k = k0 + u;
-        if (k >= nr) break;
-        const int64_t at = q + rr[k];  // rank of this run's 1
-        if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rr[k] + 1)) s_err = 11;  // symbol count
-        if (at < n_insig) atomicOr(&newbm[at >> 5], 1u << (at & 31));
-        q += (int64_t)rr[k] + 1;
+        if (k < nr) {
+          const int64_t at = q + rv[u];  // rank of this run's 1
+          if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rv[u] + 1)) s_err = 11;  // symbol count
+          if (at < n_insig) atomicOr(&newbm[at >> 5], 1u << (at & 31));
+          q += (int64_t)rv[u] + 1;
+        }
       }
       if (tid == 0 && nr == 0 && n_insig > 0) s_err = 5;
     }
     __syncthreads();
     if (s_err) break;
+    // the thread's leading bits have consecutive ranks rank0 ..: a window of the bit map
     uint32_t newm = 0;
     {
-      int64_t r = rank0;
+      const uint32_t w0 = newbm[rank0 >> 5], w1 = newbm[(rank0 >> 5) + 1];
+      const uint32_t win = (uint32_t)((((uint64_t)w1 << 32) | w0) >> (rank0 & 31));
+      int k = 0;
+#pragma unroll
       for (int u = 0; u < kDecPer; ++u)
-        if ((actm >> u & 1u) && !(sigm >> u & 1u)) {
-          if (newbm[r >> 5] >> (r & 31) & 1u) newm |= 1u << u;
-          ++r;
+        if (insm >> u & 1u) {
+          if (win >> k & 1u) newm |= 1u << u;
+          ++k;
         }
     }
     const uint32_t consm = sigm | newm;
     int64_t ncons = 0;
     const int64_t rb0 = dec_scan(__popc(consm), scan_sh, &ncons);
-    const uint64_t rcap = (uint64_t)s_wl * 8;
-    if ((uint64_t)ncons > rcap) {
+    const uint32_t wl = s_wl[pi];
+    if ((uint64_t)ncons > (uint64_t)wl * 8) {
       if (tid == 0) s_err = 4;
-    } else {
-      const uint8_t* raw = D.sec + pos + s_rl;
-      int64_t rbit = rb0;
+    } else if (consm) {
+      // this thread's raw bits [rb0, rb0 + popc(consm)), at most 16: three bytes
+      const uint8_t* raw = D.sec + base + s_po[pi] + s_rl[pi];
+      const int64_t by = rb0 >> 3;
+      const int64_t last = (rb0 + __popc(consm) - 1) >> 3;
+      uint32_t win = 0;
+      for (int64_t t = by; t <= last; ++t) win |= (uint32_t)__ldg(raw + t) << (8 * (int)(t - by));
+      win >>= (rb0 & 7);
+      int k = 0;
+#pragma unroll
       for (int u = 0; u < kDecPer; ++u) {
         if (!(consm >> u & 1u)) continue;
-        const uint32_t bit = (__ldg(raw + (rbit >> 3)) >> (rbit & 7)) & 1u;
-        ++rbit;
-        const int64_t jj = j0 + u - lo;
-        if (sigm >> u & 1u) qs[jj] |= (unsigned long long)bit << p;
-        else { qs[jj] |= 1ull << p; ss[jj] = (uint8_t)bit; }
+        const uint32_t bit = (win >> k) & 1u;
+        ++k;
+        if (sigm >> u & 1u) {
+          qv[u] |= (uint64_t)bit << p;
+        } else {
+          qv[u] |= 1ull << p;
+          sgn |= bit << u;
+          sigall |= 1u << u;
+        }
       }
     }
-    pos += s_rl + s_wl;
     __syncthreads();
     if (s_err) break;
   }
@@ -1922,28 +2018,28 @@ __global__ void __launch_bounds__(kDecThreads) decode_place_kernel(DecParams D, 
     if (tid == 0 && s_err > 0) atomicExch(D.err, s_err);
     return;
   }
+#pragma unroll
   for (int u = 0; u < kDecPer; ++u) {
     const int64_t j = j0 + u;
-    if (j >= hi_all) break;
-    const uint64_t a = qs[j - lo];
+    if (u >= nvalid) break;
+    const uint64_t a = qv[u];
     if (a == 0) { D.out[j] = 0.0; continue; }
     const int pj = lowest_plane(a, j, D.p_star, D.i_trail);
     const uint64_t v = a + ((pj >= 1) ? (1ull << (pj - 1)) : 0ull);
     const double m = mul_pow2(__ull2double_rn(v), -D.k);
-    D.out[j] = ss[j - lo] ? -m : m;
+    D.out[j] = (sgn >> u & 1u) ? -m : m;
   }
 }
 
 // Blocks of at most 512 coefficients: one WARP per block (16 consecutive
-// coefficients a lane), the placement of decode_place_kernel with warp scans
-// instead of block scans, so a plane costs no CTA barrier.  The block's size
-// table entries, plane offsets and (when it fits) its whole payload are
-// staged in shared memory first, and the runs of plane p + 1 are loaded while
-// plane p is placed, so the plane loop waits on no global load.  Same result.
+// coefficients a lane, in registers), the placement of decode_place_kernel
+// with warp scans instead of block scans, so a plane costs no CTA barrier.
+// The block's size table entries, plane offsets and (when it fits) its whole
+// payload are staged in shared memory first.  Same result.
 constexpr int kWDecPer = 16;
 constexpr int kWDecMax = 32 * kWDecPer;
 constexpr int kWDecWarps = 4;    // blocks per CTA
-constexpr int kWDecStage = 5120; // payload bytes staged per block
+constexpr int kWDecStage = 8192; // payload bytes staged per block
 __device__ __forceinline__ int64_t warp_exscan64(int64_t v, int64_t* total) {
   const int lane = threadIdx.x & 31;
   int64_t inc = v;
@@ -1959,9 +2055,7 @@ __device__ __forceinline__ int64_t warp_exscan64(int64_t v, int64_t* total) {
 __global__ void __launch_bounds__(32 * kWDecWarps) decode_place_warp_kernel(DecParams D,
                                                                             const uint32_t* __restrict__ runs,
                                                                             const int* __restrict__ nruns) {
-  __shared__ unsigned long long qs_all[kWDecWarps][kWDecMax];
-  __shared__ uint8_t ss_all[kWDecWarps][kWDecMax];
-  __shared__ uint32_t nb_all[kWDecWarps][kWDecMax / 32];
+  __shared__ uint32_t nb_all[kWDecWarps][kWDecMax / 32 + 2];
   __shared__ uint32_t rl_all[kWDecWarps][64], wl_all[kWDecWarps][64], po_all[kWDecWarps][64];
   __shared__ int nr_all[kWDecWarps][64];
   __shared__ __align__(16) uint8_t pay_all[kWDecWarps][kWDecStage];
@@ -1969,15 +2063,12 @@ __global__ void __launch_bounds__(32 * kWDecWarps) decode_place_warp_kernel(DecP
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t b = (int64_t)blockIdx.x * kWDecWarps + w;
   if (b >= D.nblocks) return;  // the whole warp: nothing below synchronises the CTA
-  unsigned long long* qs = qs_all[w];
-  uint8_t* ss = ss_all[w];
   uint32_t* newbm = nb_all[w];
   uint32_t *rlp = rl_all[w], *wlp = wl_all[w], *pop = po_all[w];
   int* nrp = nr_all[w];
   uint8_t* pay = pay_all[w];
   const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
   const int cap = D.block_size + 2;
-  for (int i = lane; i < kWDecMax; i += 32) { qs[i] = 0; ss[i] = 0; }
   int err = (*D.err != 0) ? -1 : 0;
   err = __reduce_max_sync(0xffffffffu, err);
   if (err) return;
@@ -2014,60 +2105,46 @@ __global__ void __launch_bounds__(32 * kWDecWarps) decode_place_warp_kernel(DecP
     return;
   }
   const int64_t j0 = lo + (int64_t)lane * kWDecPer;
-  const int k0 = lane * kRunPerW;
-  uint32_t rcur[kRunPerW];
-  {
-    const int nr0 = D.nplanes > 0 ? nrp[0] : 0;
-    const uint32_t* rr = runs + (b * D.nplanes) * (int64_t)cap;
+  const int nvalid = (int)max((int64_t)0, min((int64_t)kWDecPer, hi_all - j0));
+  uint64_t qv[kWDecPer];
 #pragma unroll
-    for (int u = 0; u < kRunPerW; ++u) rcur[u] = (k0 + u < nr0) ? __ldg(rr + k0 + u) : 0u;
-  }
+  for (int u = 0; u < kWDecPer; ++u) qv[u] = 0;
+  uint32_t sigall = 0, sgn = 0;
+  const int k0 = lane * kRunPerW;
   for (int pi = 0; pi < D.nplanes; ++pi) {
     const int p = 63 - pi;
     const int64_t hl = cat_end(lo, hi_all, p, D.p_star, D.i_lead), ht = cat_end(lo, hi_all, p, D.p_star, D.i_trail);
-    if (lane < kWDecMax / 32) newbm[lane] = 0u;
-    const uint32_t rl = rlp[pi], wl = wlp[pi];
+    for (int i = lane; i < kWDecMax / 32 + 2; i += 32) newbm[i] = 0u;
+    const int nt = (int)max((int64_t)0, min((int64_t)nvalid, ht - j0));
+    const int nl = (int)max((int64_t)0, min((int64_t)nvalid, hl - j0));
+    const uint32_t lowt = (1u << nt) - 1u, lowl = (1u << nl) - 1u;  // nt, nl <= 16
+    const uint32_t sigm = sigall & lowt, insm = ~sigall & lowl;
     const int nr = nrp[pi];
-    // the next plane's runs, loaded while this plane is placed
-    uint32_t rnext[kRunPerW];
-    {
-      const int nrn = (pi + 1 < D.nplanes) ? nrp[pi + 1] : 0;
-      const uint32_t* rr = runs + (b * D.nplanes + pi + 1) * (int64_t)cap;
+    const uint32_t* rr = runs + (b * D.nplanes + pi) * (int64_t)cap;
+    uint32_t rv[kRunPerW];
+    int64_t loc = 0;
 #pragma unroll
-      for (int u = 0; u < kRunPerW; ++u) rnext[u] = (k0 + u < nrn) ? __ldg(rr + k0 + u) : 0u;
+    for (int u = 0; u < kRunPerW; ++u) {
+      const bool has = nr != kRunsImplicit && k0 + u < nr;
+      rv[u] = has ? __ldg(rr + k0 + u) : 0u;
+      if (has) loc += (int64_t)rv[u] + 1;
     }
-    uint32_t sigm = 0, actm = 0;
-#pragma unroll
-    for (int u = 0; u < kWDecPer; ++u) {
-      const int64_t j = j0 + u;
-      if (j < hi_all) {
-        const bool sg_ = qs[j - lo] != 0;
-        if (sg_ ? j < ht : j < hl) {
-          actm |= 1u << u;
-          if (sg_) sigm |= 1u << u;
-        }
-      }
-    }
-    int64_t n_insig = 0;
-    const int64_t rank0 = warp_exscan64(__popc(actm & ~sigm), &n_insig);
+    int64_t tot = 0;
+    const int64_t ex = warp_exscan64(((int64_t)__popc(insm) << 32) | loc, &tot);
+    const int64_t rank0 = ex >> 32, n_insig = tot >> 32;
+    int64_t q = ex & 0xffffffffll;
     __syncwarp();
     if (nr == kRunsImplicit) {
       for (int64_t r = lane; r < n_insig; r += 32) atomicOr(&newbm[r >> 5], 1u << (r & 31));
     } else {
-      int64_t loc = 0;
-#pragma unroll
-      for (int u = 0; u < kRunPerW; ++u)
-        if (k0 + u < nr) loc += (int64_t)rcur[u] + 1;
-      int64_t total = 0;
-      int64_t q = warp_exscan64(loc, &total);
 #pragma unroll
       for (int u = 0; u < kRunPerW; ++u) {
         const int k = k0 + u;
         if (k < nr) {
-          const int64_t at = q + rcur[u];  // rank of this run's 1
-          if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rcur[u] + 1)) err = 11;  // symbol count
+          const int64_t at = q + rv[u];  // rank of this run's 1
+          if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rv[u] + 1)) err = 11;  // symbol count
           if (at < n_insig) atomicOr(&newbm[at >> 5], 1u << (at & 31));
-          q += (int64_t)rcur[u] + 1;
+          q += (int64_t)rv[u] + 1;
         }
       }
       if (nr == 0 && n_insig > 0) err = 5;
@@ -2077,48 +2154,61 @@ __global__ void __launch_bounds__(32 * kWDecWarps) decode_place_warp_kernel(DecP
     if (err) break;
     uint32_t newm = 0;
     {
-      int64_t r = rank0;
+      const uint32_t w0 = newbm[rank0 >> 5], w1 = newbm[(rank0 >> 5) + 1];
+      const uint32_t win = (uint32_t)((((uint64_t)w1 << 32) | w0) >> (rank0 & 31));
+      int k = 0;
+#pragma unroll
       for (int u = 0; u < kWDecPer; ++u)
-        if ((actm >> u & 1u) && !(sigm >> u & 1u)) {
-          if (newbm[r >> 5] >> (r & 31) & 1u) newm |= 1u << u;
-          ++r;
+        if (insm >> u & 1u) {
+          if (win >> k & 1u) newm |= 1u << u;
+          ++k;
         }
     }
     const uint32_t consm = sigm | newm;
     int64_t ncons = 0;
     const int64_t rb0 = warp_exscan64(__popc(consm), &ncons);
-    if ((uint64_t)ncons > (uint64_t)wl * 8) {
+    if ((uint64_t)ncons > (uint64_t)wlp[pi] * 8) {
       err = 4;
       break;
     }
-    const uint32_t roff = pop[pi] + rl;  // raw bytes of this plane, relative to the block's payload
-    int64_t rbit = rb0;
-    for (int u = 0; u < kWDecPer; ++u) {
-      if (!(consm >> u & 1u)) continue;
-      const uint32_t byte = staged ? pay[roff + (uint32_t)(rbit >> 3)] : __ldg(D.sec + base + roff + (rbit >> 3));
-      const uint32_t bit = (byte >> (rbit & 7)) & 1u;
-      ++rbit;
-      const int64_t jj = j0 + u - lo;
-      if (sigm >> u & 1u) qs[jj] |= (unsigned long long)bit << p;
-      else { qs[jj] |= 1ull << p; ss[jj] = (uint8_t)bit; }
-    }
+    if (consm) {
+      const uint32_t roff = pop[pi] + rlp[pi];  // raw bytes of this plane, relative to the block's payload
+      const int64_t by = rb0 >> 3, last = (rb0 + __popc(consm) - 1) >> 3;
+      uint32_t win = 0;
+      for (int64_t t = by; t <= last; ++t)
+        win |= (uint32_t)(staged ? pay[roff + (uint32_t)t] : __ldg(D.sec + base + roff + t)) << (8 * (int)(t - by));
+      win >>= (rb0 & 7);
+      int k = 0;
 #pragma unroll
-    for (int u = 0; u < kRunPerW; ++u) rcur[u] = rnext[u];
+      for (int u = 0; u < kWDecPer; ++u) {
+        if (!(consm >> u & 1u)) continue;
+        const uint32_t bit = (win >> k) & 1u;
+        ++k;
+        if (sigm >> u & 1u) {
+          qv[u] |= (uint64_t)bit << p;
+        } else {
+          qv[u] |= 1ull << p;
+          sgn |= bit << u;
+          sigall |= 1u << u;
+        }
+      }
+    }
     __syncwarp();
   }
   if (err) {
     if (lane == 0 && err > 0) atomicExch(D.err, err);
     return;
   }
+#pragma unroll
   for (int u = 0; u < kWDecPer; ++u) {
+    if (u >= nvalid) break;
     const int64_t j = j0 + u;
-    if (j >= hi_all) break;
-    const uint64_t a = qs[j - lo];
+    const uint64_t a = qv[u];
     if (a == 0) { D.out[j] = 0.0; continue; }
     const int pj = lowest_plane(a, j, D.p_star, D.i_trail);
     const uint64_t v = a + ((pj >= 1) ? (1ull << (pj - 1)) : 0ull);
     const double m = mul_pow2(__ull2double_rn(v), -D.k);
-    D.out[j] = ss[j - lo] ? -m : m;
+    D.out[j] = (sgn >> u & 1u) ? -m : m;
   }
 }
 
@@ -2156,7 +2246,7 @@ static int quant_pinned(size_t bytes, void** p) {
   return ATC_OK;
 }
 
-int quantize_encode(const double* core, int64_t n, double target, int block_size, cudaStream_t s, std::string* out,
+int quantize_encode(const double* core, int64_t n, double target, int block_size, cudaStream_t s, QuantSection* out,
                     QuantResult* res, float* ms_quant, float* ms_encode) {
   if (n < 1) return fail(ATC_EINVAL, "empty core");
   if (block_size < 32 || block_size > 65535 || (block_size % 32)) return fail(ATC_EINVAL, "bad block_size %d", block_size);
@@ -2352,11 +2442,16 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
   put64(head.data() + 40, (uint64_t)i_trail);
   put32(head.data() + 48, (uint32_t)nplanes);
   put32(head.data() + 52, kNsym);
-  std::string result;
+  out->payload = nullptr;
+  out->payload_bytes = 0;
   if (nplanes > 0) {
     ATC_TRY(size_pass(63, nplanes, i_lead, i_trail));
-    scan_kernel<<<1, 1024, 0, s>>>(rsize, wsize, nchunks, off);
-    ATC_LAUNCHED(1);
+    {
+      unsigned long long* sc = nullptr;
+      ATC_TRY(Scratch::get(SLOT_SCAN, sizeof(unsigned long long) * (range_scan_parts(nchunks) + 8), (void**)&sc));
+      ChunkBytes f{rsize, wsize};
+      ATC_TRY(range_scan(f, nchunks, 0ull, sc, off, ~0ull, nullptr, s));
+    }
     uint64_t* ptotal = reinterpret_cast<uint64_t*>(hstp + 1);
     uint32_t* hfc = reinterpret_cast<uint32_t*>(ptotal + 2);
     ATC_CUDA_TRY(cudaMemcpyAsync(ptotal, off + nchunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -2381,12 +2476,8 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
       enc_rans_kernel<<<(unsigned)((nchunks + kEncWarps - 1) / kEncWarps), 32 * kEncWarps, 0, s>>>(P, 0, spill);
     }
     ATC_LAUNCHED(1);
-    result.resize(hdr + tabb + total);
-    memcpy(&result[0], head.data(), hdr);
-    ATC_CUDA_TRY(cudaMemcpyAsync(&result[hdr], dout, tabb + total, cudaMemcpyDeviceToHost, s));
-    ATC_CUDA_TRY(cudaStreamSynchronize(s));
-  } else {
-    result.assign((const char*)head.data(), hdr);
+    out->payload = dout;
+    out->payload_bytes = tabb + total;
   }
   ATC_CUDA_TRY(cudaEventRecord(e2, s));
   ATC_CUDA_TRY(cudaEventSynchronize(e2));
@@ -2406,7 +2497,7 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     res->i_trail = i_trail;
     res->sse_pred = ldexp(i192_to_double(hst.e_star), -2 * k);
   }
-  out->swap(result);
+  out->head.swap(head);
   return ATC_OK;
 }
 
@@ -2518,8 +2609,14 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
   uint64_t* boff = reinterpret_cast<uint64_t*>(small + 64);
   ATC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   D.sec = dsec; D.qt = qt; D.sg = sg; D.out = core; D.err = err; D.boff = boff;
-  block_offsets_kernel<<<1, kOffThreads, 0, s>>>(D, boff);
-  ATC_LAUNCHED(1);
+  {
+    // payload offset of every block (the sizes of its chunks from the size table)
+    unsigned long long* sc = nullptr;
+    ATC_TRY(Scratch::get(SLOT_SCAN, sizeof(unsigned long long) * (range_scan_parts(D.nblocks) + 8), (void**)&sc));
+    BlockBytes f{dsec + D.tab, D.nplanes};
+    const unsigned long long base = (unsigned long long)D.tab + (unsigned long long)D.nblocks * D.nplanes * 8;
+    ATC_TRY(range_scan(f, D.nblocks, base, sc, boff, (unsigned long long)D.nbytes, err, s));
+  }
   if (D.block_size <= kDecMax && D.nplanes > 0) {
     // phase A: every (block, plane) chunk's runs in parallel; phase B: placement
     RunParams RP;
