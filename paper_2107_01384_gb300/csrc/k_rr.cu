@@ -13,8 +13,12 @@
 //   1. cyclic Jacobi in FP32 on B scaled by a power of two, parallel ordering
 //      (circle method: 16 disjoint rotations a round, 31 rounds a sweep), each
 //      round an update of all 32 x 32 entries of B and of the accumulated
-//      rotations Y, one thread per entry, ping-pong buffers in shared memory;
-//      four sweeps (fewer when a sweep rotates nothing);
+//      rotations Y by the first 16 warps (warps 0-7 four entries of B a
+//      thread, warps 8-15 four entries of Y, one named barrier of 512 threads:
+//      the rounds are a chain, and fewer warps at each barrier shorten it; each
+//      thread loads all its inputs before it stores, so its four entries are
+//      independent chains), ping-pong buffers in shared memory; four sweeps
+//      (fewer when a sweep rotates nothing);
 //   2. Ritz values sorted descending (rank by comparison, ties by index);
 //   3. one first-order correction Y <- Y (I + F), F_ij = (Y^T B Y)_ij / (theta_j
 //      - theta_i) for Ritz values more than 1 % apart (FP32): what the remaining
@@ -70,7 +74,11 @@ struct JacShared {
   int perm[kJ];
   int rot[2];
   int nv;
+  int buf;                     // the ping-pong buffer holding the Jacobi result
 };
+
+constexpr int kJacThreads = 512;  // threads of the Jacobi rounds (warps 0-7: B, 8-15: Y)
+__device__ __forceinline__ void jac_bar() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 
 // 2^e as a double for |e| < 1022, by its bit pattern (ldexp is a long FP64
 // routine, and FP64 issues at 1/64 of the FP32 rate on this GPU)
@@ -108,60 +116,96 @@ __global__ void __launch_bounds__(kJThreads, 1)
   // ---- 1. cyclic Jacobi, parallel ordering.  Lanes 0..15 of warp 0 form the
   // round's 16 rotations (MUFU reciprocal / square roots: the rotations only
   // need c^2 + s^2 = 1 to FP32 level, the vectors are re-orthonormalised below),
-  // then every thread updates its entry of A and of Y.
-  int buf = 0;
-  // this thread's column partner per round moves by a fixed rule: j' = 2r - j (mod 31) for j < 31
-  for (int sweep = 0; sweep < kJSweeps; ++sweep) {
-    if (tid == 0) S.rot[sweep & 1] = 0;
-    __syncthreads();
-    for (int r = 0; r < kJ - 1; ++r) {
-      if (tid < kJ / 2) {
-        // pair k of round r: (r, 31) for k = 0, (r + k, r - k) mod 31 otherwise
-        int p = r, q = kJ - 1;
-        if (tid > 0) {
-          p = r + tid;
-          p = p >= kJ - 1 ? p - (kJ - 1) : p;
-          q = r - tid;
-          q = q < 0 ? q + (kJ - 1) : q;
+  // then the threads of warps 0-7 update four entries of A and of Y each.
+  __syncthreads();  // B and Y initialised by all 1024 threads
+  if (tid < kJacThreads) {
+    int buf = 0;
+    const int wj = (tid >> 5) & 7;  // this thread's rows: wj, wj + 8, wj + 16, wj + 24 (column j = lane)
+    for (int sweep = 0; sweep < kJSweeps; ++sweep) {
+      if (tid == 0) S.rot[sweep & 1] = 0;
+      jac_bar();
+      for (int r = 0; r < kJ - 1; ++r) {
+        if (tid < kJ / 2) {
+          // pair k of round r: (r, 31) for k = 0, (r + k, r - k) mod 31 otherwise
+          int p = r, q = kJ - 1;
+          if (tid > 0) {
+            p = r + tid;
+            p = p >= kJ - 1 ? p - (kJ - 1) : p;
+            q = r - tid;
+            q = q < 0 ? q + (kJ - 1) : q;
+          }
+          const int lo = min(p, q), hi = max(p, q);
+          const float app = S.A[buf][lo][lo], aqq = S.A[buf][hi][hi], apq = S.A[buf][lo][hi];
+          float c = 1.f, ss = 0.f, tt = 0.f;
+          // the relative test |apq| > u sqrt(|app aqq|) squared; the rotation from
+          // MUFU reciprocals and square roots (FP32 level is all it needs)
+          if (apq != 0.f && apq * apq > (kJTol * kJTol) * fabsf(app * aqq)) {
+            const float zeta = __fdividef(aqq - app, 2.f * apq);
+            const float y = fmaf(zeta, zeta, 1.f);
+            tt = copysignf(__fdividef(1.f, fabsf(zeta) + y * rsqrtf(y)), zeta);
+            c = rsqrtf(fmaf(tt, tt, 1.f));
+            ss = tt * c;
+            S.rot[sweep & 1] = 1;
+          }
+          // per index: (c, signed coefficient of the partner); t signed so that the
+          // diagonal update is a_ii + t_i a_{lo,hi} for both members of the pair
+          S.cs[lo] = make_float2(c, -ss);
+          S.cs[hi] = make_float2(c, ss);
+          S.t[lo] = -tt;
+          S.t[hi] = tt;
         }
-        const int lo = min(p, q), hi = max(p, q);
-        const float app = S.A[buf][lo][lo], aqq = S.A[buf][hi][hi], apq = S.A[buf][lo][hi];
-        float c = 1.f, ss = 0.f, tt = 0.f;
-        if (apq != 0.f && fabsf(apq) > kJTol * sqrtf(fabsf(app * aqq))) {
-          const float zeta = (aqq - app) * __frcp_rn(2.f * apq);
-          const float y = fmaf(zeta, zeta, 1.f);
-          tt = copysignf(__frcp_rn(fabsf(zeta) + y * rsqrtf(y)), zeta);
-          c = rsqrtf(fmaf(tt, tt, 1.f));
-          ss = tt * c;
-          S.rot[sweep & 1] = 1;
+        jac_bar();
+        const int pj = jac_partner(j, r);
+        const float2 csj = S.cs[j];
+        if (tid >= kJacThreads / 2) {
+          // Y <- Y J: column j mixes with its partner's
+          float y0[kJ / 8], y1[kJ / 8];
+#pragma unroll
+          for (int k = 0; k < kJ / 8; ++k) {
+            y0[k] = S.Y[buf][wj + 8 * k][j];
+            y1[k] = S.Y[buf][wj + 8 * k][pj];
+          }
+#pragma unroll
+          for (int k = 0; k < kJ / 8; ++k) S.Y[buf ^ 1][wj + 8 * k][j] = fmaf(csj.x, y0[k], csj.y * y1[k]);
+        } else {
+          const float(*Ab)[kJP] = S.A[buf];
+          float aij[kJ / 8], aipj[kJ / 8], apij[kJ / 8], apipj[kJ / 8], ti[kJ / 8];
+          float2 csi[kJ / 8];
+          int pi[kJ / 8];
+#pragma unroll
+          for (int k = 0; k < kJ / 8; ++k) {
+            const int ii = wj + 8 * k;
+            pi[k] = jac_partner(ii, r);
+            csi[k] = S.cs[ii];
+            ti[k] = S.t[ii];
+            aij[k] = Ab[ii][j];
+            aipj[k] = Ab[ii][pj];
+            apij[k] = Ab[pi[k]][j];
+            apipj[k] = Ab[pi[k]][pj];
+          }
+#pragma unroll
+          for (int k = 0; k < kJ / 8; ++k) {
+            const int ii = wj + 8 * k;
+            // general entry of J^T A J; the two entries of a rotated pair's 2 x 2 block
+            // on the diagonal take the accurate update a_ii + t_i a_lo,hi, the
+            // off-diagonal pair entries become 0 (branch-free selects)
+            const float gen = csi[k].x * (csj.x * aij[k] + csj.y * aipj[k]) +
+                              csi[k].y * (csj.x * apij[k] + csj.y * apipj[k]);
+            const float apq = (ii < pi[k]) ? aipj[k] : apij[k];  // a_{lo,hi} of ii's pair, used when ii == j
+            float anew = (ii == j) ? fmaf(ti[k], apq, aij[k]) : gen;
+            anew = (j == pi[k] && ti[k] != 0.f) ? 0.f : anew;
+            S.A[buf ^ 1][ii][j] = anew;
+          }
         }
-        // per index: (c, signed coefficient of the partner); t signed so that the
-        // diagonal update is a_ii + t_i a_{lo,hi} for both members of the pair
-        S.cs[lo] = make_float2(c, -ss);
-        S.cs[hi] = make_float2(c, ss);
-        S.t[lo] = -tt;
-        S.t[hi] = tt;
+        buf ^= 1;
+        jac_bar();
       }
-      __syncthreads();
-      const int pi = jac_partner(i, r), pj = jac_partner(j, r);
-      const float2 csi = S.cs[i], csj = S.cs[j];
-      const float ti = S.t[i];
-      const float(*Ab)[kJP] = S.A[buf];
-      const float aij = Ab[i][j], aipj = Ab[i][pj], apij = Ab[pi][j], apipj = Ab[pi][pj];
-      // general entry of J^T A J; the two entries of a rotated pair's 2 x 2 block
-      // on the diagonal take the accurate update a_ii + t_i a_lo,hi, the
-      // off-diagonal pair entries become 0 (branch-free selects)
-      const float gen = csi.x * (csj.x * aij + csj.y * aipj) + csi.y * (csj.x * apij + csj.y * apipj);
-      const float apq = (i < pi) ? aipj : apij;  // a_{lo,hi} of i's pair, used when i == j
-      float anew = (i == j) ? fmaf(ti, apq, aij) : gen;
-      anew = (j == pi && ti != 0.f) ? 0.f : anew;
-      S.A[buf ^ 1][i][j] = anew;
-      S.Y[buf ^ 1][i][j] = fmaf(csj.x, S.Y[buf][i][j], csj.y * S.Y[buf][i][pj]);
-      buf ^= 1;
-      __syncthreads();
+      if (S.rot[sweep & 1] == 0) break;
     }
-    if (S.rot[sweep & 1] == 0) break;
+    if (tid == 0) S.buf = buf;
   }
+  __syncthreads();
+  const int buf = S.buf;
   // ---- 2. sort the Ritz values (descending; padding last)
   if (tid < kJ) {
     const float th = (tid < K) ? S.A[buf][tid][tid] : -INFINITY;

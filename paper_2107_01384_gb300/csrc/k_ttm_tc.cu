@@ -94,6 +94,10 @@ struct TtmArgs {
   int tma;
   int rb_log2;
   int nraw;
+  // one output chunk whose factor slices fit: they are copied into shared
+  // memory once per CTA (after the stages and the raw ring) instead of once
+  // per K step, so no MMA waits on an L2 round trip for its B tile
+  int bres;
   // work items: chunk_fast -> item w = (M tile w / nchunk, chunk w % nchunk),
   // so that the chunks of one M tile run side by side, CTA blockIdx.x taking
   // items blockIdx.x + t gridDim.x; else item = M tile, chunk = blockIdx.y
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t A_BYTES = 128 * 128;  // 128 rows x 64 16-bit
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full_bar[MAXST], bfull_bar[MAXST], empty_bar[MAXST], accf_bar[2], acce_bar[2], done_bar;
-  __shared__ uint64_t raw_full[kMaxRaw], raw_empty[kMaxRaw];
+  __shared__ uint64_t raw_full[kMaxRaw], raw_empty[kMaxRaw], bres_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -164,8 +168,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     return cf ? w - (w / nch) * nch : (int64_t)blockIdx.y;
   };
   const uint32_t B_BYTES = (uint32_t)a.apad * 128u;
-  const uint32_t STAGE = 3 * A_BYTES + ((3 * B_BYTES + 1023u) & ~1023u);
+  const uint32_t STAGE = 3 * A_BYTES + (a.bres ? 0u : ((3 * B_BYTES + 1023u) & ~1023u));
   uint8_t* rawbuf = smem + (size_t)NSTAGE * STAGE;  // raw-tile ring (TMA path)
+  uint8_t* bresbuf = rawbuf + (size_t)NRAW * kRawBytes;  // resident factor slices [slice][kt][apad][128 B]
   const int64_t nmine = (nwork > wb0) ? (nwork - 1 - wb0) / wst + 1 : 0;
   const int64_t iters = nmine * a.nkt;
   const int64_t LR = a.L * a.R;
@@ -181,6 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&raw_full[s], 1);
       mbar_init(&raw_empty[s], kConvThreads);
     }
+    mbar_init(&bres_bar, 1);
     mbar_init(&done_bar, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf_bar[b], 1);
@@ -358,7 +364,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == kProdWarp) {
     // ---------------------------------------------------------- B producer
-    if (lane == 0) {
+    if (lane == 0 && a.bres) {
+      // every K tile of the three slices at once (each slice is contiguous)
+      const uint32_t slice_bytes = (uint32_t)a.nkt * B_BYTES;
+      mbar_arrive_expect_tx(&bres_bar, 3 * slice_bytes);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) bulk_g2s(bresbuf + q * slice_bytes, a.bw + (size_t)q * slice_bytes, slice_bytes, &bres_bar);
+      mbar_wait_drain(&bres_bar, 0);
+    } else if (lane == 0) {
       const size_t slice_bytes = (size_t)a.nkt * B_BYTES;
       int64_t issued = 0;
       for (int64_t it = 0; it < iters; ++it) {
@@ -408,6 +421,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_f16(BF16 ? 1 : 0, 128, a.apad);
       int64_t it = 0;
       bool ok = true;
+      if (a.bres && nmine > 0) ok = mbar_wait(&bres_bar, 0u, abort);
+      const uint32_t bslice = a.bres ? (uint32_t)a.nkt * B_BYTES : B_BYTES;  // distance between slices
       for (int64_t t = 0; t < nmine && ok; ++t) {
         const int ab = (int)(t & 1);
         if (!mbar_wait(&acce_bar[ab], ((uint32_t)(t >> 1) & 1u) ^ 1u, abort)) break;
@@ -416,15 +431,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kt = 0; kt < a.nkt; ++kt, ++it) {
           const int s = (int)(it % NSTAGE);
           if (!mbar_wait(&full_bar[s], (uint32_t)(it / NSTAGE) & 1u, abort) ||
-              !mbar_wait(&bfull_bar[s], (uint32_t)(it / NSTAGE) & 1u, abort)) { ok = false; break; }
+              (!a.bres && !mbar_wait(&bfull_bar[s], (uint32_t)(it / NSTAGE) & 1u, abort))) { ok = false; break; }
           tc_fence_after();
           const uint32_t xa = smem_u32(smem + (size_t)s * STAGE);
-          const uint32_t wa = xa + 3 * A_BYTES;
+          const uint32_t wa = a.bres ? smem_u32(bresbuf) + (uint32_t)kt * B_BYTES : xa + 3 * A_BYTES;
 #pragma unroll
           for (int j = 0; j < KT / 16; ++j) {
             const uint32_t o = 32u * j;
             const uint64_t X0 = desc_k128(xa + o), X1 = desc_k128(xa + A_BYTES + o), X2 = desc_k128(xa + 2 * A_BYTES + o);
-            const uint64_t W0 = desc_k128(wa + o), W1 = desc_k128(wa + B_BYTES + o), W2 = desc_k128(wa + 2 * B_BYTES + o);
+            const uint64_t W0 = desc_k128(wa + o), W1 = desc_k128(wa + bslice + o), W2 = desc_k128(wa + 2 * bslice + o);
             const uint32_t acc = (kt | j) ? 1u : 0u;
             umma_f16(d, X0, W0, idesc, acc);
             umma_f16(d + kOrdStride, X0, W1, idesc, acc);
@@ -676,6 +691,8 @@ int g_nsm_ttm = 0;
 __device__ SliceScale g_unit_scale;
 // largest pre-sliced data image (6 bytes per element of the data operand)
 constexpr size_t kMaxImageBytes = (size_t)16 << 30;
+// largest factor slice image kept resident in shared memory
+constexpr size_t kMaxResidentB = (size_t)48 << 10;
 
 }  // namespace
 
@@ -759,7 +776,10 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
     a.nraw = 0;
     a.chunk_fast = nchunk > 1 ? 1 : 0;
     const uint32_t bbytes = (uint32_t)a.apad * 128u;
-    const uint32_t stage = 3u * 128u * 128u + ((3u * bbytes + 1023u) & ~1023u);
+    const size_t bres_bytes = (size_t)3 * nkt * bbytes;
+    a.bres = (nchunk == 1 && bres_bytes <= kMaxResidentB) ? 1 : 0;
+    const uint32_t stage = 3u * 128u * 128u + (a.bres ? 0u : ((3u * bbytes + 1023u) & ~1023u));
+    const size_t bres_smem = a.bres ? ((bres_bytes + 1023) & ~(size_t)1023) : 0;
     // the data operand: pre-sliced image (several chunks), raw FP32 tiles by
     // TMA (tensor-map geometry), or the converters' global loads
     const size_t img_bytes = (size_t)mtiles * nkt * 3 * 128 * 128;
@@ -784,7 +804,7 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
       }
       if (!ok) cudaGetLastError();
       for (int nraw = kMaxRaw; ok && nraw >= 2 && !a.tma; --nraw) {
-        if ((size_t)224 * 1024 >= (size_t)nraw * kRawBytes + 2 * (size_t)stage) {
+        if ((size_t)224 * 1024 >= (size_t)nraw * kRawBytes + 2 * (size_t)stage + bres_smem) {
           a.tma = 1;
           a.nraw = nraw;
           a.rb_log2 = rbl;
@@ -792,10 +812,10 @@ int ttm_run(const void* x, int xdtype, int64_t L, int64_t n, int64_t R, const do
       }
     }
     const size_t raw_bytes = (size_t)a.nraw * kRawBytes;
-    a.nstage = (int)(((size_t)224 * 1024 - raw_bytes) / stage);
+    a.nstage = (int)(((size_t)224 * 1024 - raw_bytes - bres_smem) / stage);
     if (a.nstage > 4) a.nstage = 4;
     if (a.nstage < 2) return fail(ATC_EUNSUP, "TTM stage does not fit in shared memory");
-    const int smem = (int)(a.nstage * stage + raw_bytes + 1024);
+    const int smem = (int)(a.nstage * stage + raw_bytes + bres_smem + 1024);
     {
       const int64_t tot = (int64_t)nkt * a.apad * 64 * nchunk;
       const int blocks = (int)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096);
