@@ -144,6 +144,10 @@ int atc_get_factor(const atc_compressed* c, int mode, const double** u_dev);
 /* *bytes <- borrowed HOST pointer to the compressed stream ("ATC1"), *nbytes its size. */
 int atc_get_stream(const atc_compressed* c, const uint8_t** bytes, size_t* nbytes);
 int atc_get_stats(const atc_compressed* c, atc_stats* stats);
+/* Release a handle.  Its core and factors live in the device's stream-ordered
+ * memory pool and go back to it in order on the legacy default stream: work of
+ * the caller that still reads them (through atc_get_core / atc_get_factor)
+ * must be finished, or ordered before that stream, when atc_free is called. */
 void atc_free(atc_compressed* c);
 
 /* Read ndim, dims (<= 8 entries) and dtype from a stream header (host only). */

@@ -391,12 +391,33 @@ std::vector<int> decompression_order(int d, const int64_t* dims, const int64_t* 
   return best;
 }
 
+// The handle's core and factors come from the device's stream-ordered memory
+// pool (kept by the pool between calls, so a compress costs no cudaMalloc and
+// a free no device synchronisation).  The pool keeps what it holds: its
+// release threshold is raised once per device.
+int handle_alloc(void** p, size_t bytes, cudaStream_t s) {
+  static bool pool_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !pool_set[dev]) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    pool_set[dev] = true;
+  }
+  return cudaMallocAsync(p, bytes, s) == cudaSuccess ? ATC_OK : ATC_ENOMEM;
+}
+
 void free_compressed(atc_compressed* c) {
   if (!c) return;
   free(c->stream);
-  if (c->core) cudaFree(c->core);
+  // the handle's work on its stream ended before it was returned: freeing on
+  // the legacy stream is ordered after it
+  if (c->core) cudaFreeAsync(c->core, 0);
   for (int i = 0; i < 8; ++i)
-    if (c->factors[i]) cudaFree(c->factors[i]);
+    if (c->factors[i]) cudaFreeAsync(c->factors[i], 0);
   delete c;
 }
 
@@ -642,6 +663,8 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   for (int i = 0; i < 8; ++i) st.order[i] = st.storage_order[i] = -1;
   for (int i = 0; i < d; ++i) st.order[i] = order[i];
   auto bail = [&](int rc) {
+    cudaStreamSynchronize(s);  // nothing of this call may still run when its buffers go back to the pool
+    cudaGetLastError();
     free_compressed(c);
     return rc;
   };
@@ -781,7 +804,7 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
             }
             r = rn;
             disc = tail;
-            if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
+            if (handle_alloc((void**)&c->factors[m], sizeof(double) * (size_t)n * r, s) != ATC_OK)
               return fail(ATC_ENOMEM, "factor allocation failed");
             if (cudaMemcpy2DAsync(c->factors[m], sizeof(double) * r, cand, sizeof(double) * rh, sizeof(double) * r, n,
                                   cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -905,7 +928,7 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
           if (rc < 0) return bail(rc);
           clk.mark(PH_TTM);
         } else {
-          if (cudaMalloc(&c->factors[m], sizeof(double) * (size_t)n * r) != cudaSuccess)
+          if (handle_alloc((void**)&c->factors[m], sizeof(double) * (size_t)n * r, s) != ATC_OK)
             return bail(fail(ATC_ENOMEM, "factor allocation failed"));
           rc = launch_eig_vectors((int)n, r, c->factors[m], s);
           if (rc) return bail(rc);
@@ -929,7 +952,7 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   st.sse_trunc = used;
   int64_t ncore = 1;
   for (int i = 0; i < d; ++i) ncore *= c->ranks[i];
-  if (cudaMalloc(&c->core, sizeof(double) * (size_t)ncore) != cudaSuccess)
+  if (handle_alloc((void**)&c->core, sizeof(double) * (size_t)ncore, s) != ATC_OK)
     return bail(fail(ATC_ENOMEM, "core allocation failed"));
   rc = launch_convert_to_f64(curp, curdt, ncore, c->core, s);
   if (rc) return bail(rc);
