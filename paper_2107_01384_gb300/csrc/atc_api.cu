@@ -766,28 +766,36 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         auto certify = [&](int rh, int rh_cap, const std::function<int(int, double*)>& get_cand) -> int {
           for (;;) {
             double* cand = nullptr;
-            int rc2 = Scratch::get(SLOT_CAND, sizeof(double) * ((size_t)n * rh + rh + 8), (void**)&cand);
+            const size_t nparts = (size_t)(rh + 1) * kRaySplitMax;
+            int rc2 = Scratch::get(SLOT_CAND, sizeof(double) * ((size_t)n * rh + nparts + 8), (void**)&cand);
             if (rc2) return rc2;
-            double* edev = cand + (size_t)n * rh;  // rho[0..rh), then trace(G)
+            double* edev = cand + (size_t)n * rh;  // parts of rho[0..rh), then of trace(G)
+            const int ns = rayleigh_splits(n, rh);
             rc2 = get_cand(rh, cand);
             if (!rc2) rc2 = launch_rayleigh(G, n, cand, rh, edev, s);
             if (rc2) return rc2;
             PinnedReadback pb;
-            rc2 = pinned_readback((size_t)rh + 1, &pb);
+            rc2 = pinned_readback((size_t)(rh + 1) * ns, &pb);
             if (rc2) return rc2;
             const double* eh = pb.dbl;
-            if (cudaMemcpyAsync(pb.dbl, edev, sizeof(double) * (rh + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            if (cudaMemcpyAsync(pb.dbl, edev, sizeof(double) * (rh + 1) * ns, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                 cudaMemcpyAsync(&pb.ints[1], tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
               return fail(ATC_ECUDA, "Rayleigh quotient readback failed");
             rc2 = eig_check(s);
             if (rc2) return rc2;
             he = pb.ints[1];
             if (he) return fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)");
-            const double tr = eh[rh];
+            // each quotient and the trace: their row-chunk parts added in order
+            auto part_sum = [&](int j) {
+              double v = 0.0;
+              for (int c2 = 0; c2 < ns; ++c2) v += eh[(size_t)j * ns + c2];
+              return v;
+            };
+            const double tr = part_sum(rh);
             int rn = -1;
             double tail = 0.0, acc = 0.0;
             for (int rr = 1; rr <= rh; ++rr) {
-              acc += eh[rr - 1];
+              acc += part_sum(rr - 1);
               double t = tr - acc;
               if (t < 0.0) t = 0.0;
               if (t <= budget) { rn = rr; tail = t; break; }

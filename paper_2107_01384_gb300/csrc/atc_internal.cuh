@@ -95,6 +95,11 @@ int launch_convert_to_f64(const void* x, int dtype, int64_t n, double* y, cudaSt
 int launch_convert_f64_to(const double* x, int64_t n, void* y, int dtype, cudaStream_t s);
 // e[j] = sum over (l, c) of y[(l r + j) R + c]^2 in FP64 (fixed order)
 // out[j] = u_j^T G u_j for the rh columns of U (n x rh row-major, FP64), out[rh] = trace(G); n <= 1024
+// u_j^T G u_j (j < rh, U n x rh row-major) and trace(G) in FP64, each as
+// rayleigh_splits(n, rh) parts over row chunks of G: out[j * ns + c], the
+// trace at j = rh; out holds (rh + 1) * kRaySplitMax doubles.
+constexpr int kRaySplitMax = 16;
+int rayleigh_splits(int64_t n, int rh);
 int launch_rayleigh(const double* G, int64_t n, const double* U, int rh, double* out, cudaStream_t s);
 // (L, rh, R) -> (L, r, R): the leading r of every rh rows
 int launch_permute(const double* x, const int64_t* dims, const int* perm, int ndim, double* y, int inverse,

@@ -139,6 +139,60 @@ __device__ __forceinline__ I192 plane_reduction(uint64_t v, int p) {
   const I192 m = i192_from_u128((u128)(base < 0 ? -base : base) << (p - 1));
   return base < 0 ? i192_neg(m) : m;
 }
+// The same reduction with the power of two taken out: D_i(p) = x * 2^(p-1) for
+// p >= 1 (x * 2^0 at plane 0), x an integer with |x| < 15 * 2^(p-1):
+//   leading 3 (c + 2r), trailing 1: 2r - c, trailing 0: 3c - 2r.
+// X = int64_t holds x for p <= 60, __int128 for every plane.  Sums of x over a
+// thread's range are shifted back once, by plane_shift(p), when they leave it.
+template <typename X>
+__device__ __forceinline__ X plane_factor(uint64_t v, int p) {
+  if ((v >> p) == 0) return (X)0;
+  if (p == 0) return (v == 1 || (v & 1ull) == 0) ? (X)1 : (X)0;
+  const uint64_t c = 1ull << (p - 1);
+  const uint64_t r = v & ((c << 1) - 1ull);
+  if (p == 63 || (v >> (p + 1)) == 0) return (X)3 * ((X)c + (X)2 * (X)r);
+  return ((v >> p) & 1ull) ? (X)2 * (X)r - (X)c : (X)3 * (X)c - (X)2 * (X)r;
+}
+__device__ __forceinline__ int plane_shift(int p) { return p > 0 ? p - 1 : 0; }
+// v * 2^sh as a signed 192-bit value (|v| < 2^127, sh <= 63)
+__device__ __forceinline__ I192 i192_from_i128_shl(__int128 v, int sh) {
+  const bool neg = v < 0;
+  const u128 u = neg ? (u128)0 - (u128)v : (u128)v;
+  const uint64_t lo = (uint64_t)u, hi = (uint64_t)(u >> 64);
+  I192 r;
+  if (sh == 0) r = {lo, hi, 0ull};
+  else r = {lo << sh, (hi << sh) | (lo >> (64 - sh)), hi >> (64 - sh)};
+  return neg ? i192_neg(r) : r;
+}
+// ceil(v / 2^sh) of a signed 192-bit v as a 128-bit integer, saturated to
+// [-(2^126), 2^126] (a first-passage threshold: a saturated one is out of reach
+// of every sum it is compared with)
+__device__ __forceinline__ __int128 i192_ceil_shr(I192 v, int sh) {
+  const bool neg = (int64_t)v.w2 < 0;
+  if (neg) v = i192_neg(v);
+  // |v| >> sh, and whether bits were dropped
+  uint64_t w0 = v.w0, w1 = v.w1, w2 = v.w2;
+  bool frac = false;
+  if (sh > 0) {
+    frac = (w0 << (64 - sh)) != 0;
+    w0 = (w0 >> sh) | (w1 << (64 - sh));
+    w1 = (w1 >> sh) | (w2 << (64 - sh));
+    w2 >>= sh;
+  }
+  const __int128 cap = (__int128)1 << 126;
+  if (w2 != 0 || (w1 >> 62) != 0) return neg ? -cap : cap;
+  __int128 r = (__int128)(((u128)w1 << 64) | w0);
+  // ceil of v / 2^sh: up for a positive v with dropped bits, truncation for a negative one
+  if (!neg) return frac ? r + 1 : r;
+  return -r;
+}
+template <typename A>
+__device__ __forceinline__ A acc_lowest();
+template <>
+__device__ __forceinline__ int64_t acc_lowest<int64_t>() { return INT64_MIN; }
+template <>
+__device__ __forceinline__ __int128 acc_lowest<__int128>() { return (__int128)((u128)1 << 127); }
+
 __device__ __forceinline__ uint64_t shfl_down_u64(uint64_t v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
 
 __device__ Seg warp_seg_reduce(Seg x) {
@@ -255,12 +309,87 @@ __global__ void scale_exp_kernel(const unsigned long long* __restrict__ mx, doub
   st->p_star = -1;
 }
 
-// Per segment (one CTA, contiguous coefficients) and plane p in [plo, plo+15]:
-// the ordered summary of D_i(p); plus sum q_i^2 when first_pass.
+__device__ __forceinline__ __int128 shfl_down_i128(__int128 v, int d) {
+  const uint64_t lo = shfl_down_u64((uint64_t)(u128)v, d), hi = shfl_down_u64((uint64_t)((u128)v >> 64), d);
+  return (__int128)(((u128)hi << 64) | lo);
+}
+
+// One group of up to kPlaneGroup planes (pg down to max(plo, pg - 7)) over
+// the thread range [t_lo, t_hi): per plane the running sum of the factors x
+// (plane_factor) and its largest prefix, in X / A integers; then per plane an
+// ordered warp tree in 128 bits (an empty range: sum 0, largest prefix kNone,
+// far below any real prefix, so that combining with it changes nothing), and
+// one thread per plane combining the warps in order, shifted back to
+// D = x * 2^(p-1).  wsum: kPlaneGroup x (kSegThreads / 32) summaries.
+template <typename X, typename A>
+__device__ __forceinline__ void plane_group(const uint64_t* __restrict__ q, int64_t t_lo, int64_t t_hi, int pg, int plo,
+                                            int phi, Seg* wsum, Seg* __restrict__ out) {
+  constexpr int kW = kSegThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  A s[kPlaneGroup], m[kPlaneGroup];
+#pragma unroll
+  for (int k = 0; k < kPlaneGroup; ++k) {
+    s[k] = (A)0;
+    m[k] = acc_lowest<A>();
+  }
+  const int pgl = max(plo, pg - kPlaneGroup + 1);  // lowest plane of this group
+  for (int64_t i = t_lo; i < t_hi; ++i) {
+    const uint64_t v = q[i];
+    // zero through every plane of the group: x = 0 there, which leaves the sum
+    // and (once the first element has set it) the largest prefix unchanged
+    if ((v >> pgl) == 0 && i != t_lo) continue;
+#pragma unroll
+    for (int k = 0; k < kPlaneGroup; ++k) {
+      const int p = pg - k;
+      if (p >= pgl) {
+        s[k] += (A)plane_factor<X>(v, p);
+        if (m[k] < s[k]) m[k] = s[k];
+      }
+    }
+  }
+  const bool empty = t_lo >= t_hi;
+  const __int128 kNone = -((__int128)1 << 126);
+#pragma unroll
+  for (int k = 0; k < kPlaneGroup; ++k) {
+    const int p = pg - k;
+    if (p < pgl) break;
+    __int128 ws = empty ? (__int128)0 : (__int128)s[k];
+    __int128 wm = empty ? kNone : (__int128)m[k];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const __int128 os = shfl_down_i128(ws, off), om = shfl_down_i128(wm, off);
+      if ((lane & (2 * off - 1)) == 0 && lane + off < 32) {
+        const __int128 t = ws + om;
+        if (wm < t) wm = t;
+        ws += os;
+      }
+    }
+    if (lane == 0) {
+      Seg r;
+      r.empty = wm <= kNone / 2;
+      r.s = r.empty ? i192_zero() : i192_from_i128_shl(ws, plane_shift(p));
+      r.m = r.empty ? i192_zero() : i192_from_i128_shl(wm, plane_shift(p));
+      wsum[k * kW + warp] = r;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kPlaneGroup && pg - (int)threadIdx.x >= pgl) {
+    const int k = threadIdx.x, p = pg - k;
+    Seg t = wsum[k * kW];
+    for (int w = 1; w < kW; ++w) t = seg_combine(t, wsum[k * kW + w]);
+    out[(int64_t)(phi - p) * gridDim.x + blockIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// Per segment (one CTA, contiguous coefficients) and plane p in [plo, phi]
+// (at most kPlaneChunk planes): the ordered summary of D_i(p); plus sum q_i^2
+// when first_pass.  Planes above 60 take 128-bit factors; below, 64-bit
+// factors, summed in 64 bits where a thread range cannot overflow them.
 __global__ void __launch_bounds__(kSegThreads, 2) plane_stats_kernel(const uint64_t* __restrict__ q, int64_t n,
                                                                    int64_t seg_len, int plo, int phi, int first_pass,
                                                                    Seg* __restrict__ out, I192* __restrict__ e64_out) {
-  __shared__ Seg wsum[kSegThreads / 32];
+  __shared__ Seg wsum[kPlaneGroup * (kSegThreads / 32)];
   const int64_t s_lo = blockIdx.x * seg_len;
   const int64_t s_hi = min(n, s_lo + seg_len);
   const int64_t per = (seg_len + blockDim.x - 1) / blockDim.x;
@@ -284,44 +413,12 @@ __global__ void __launch_bounds__(kSegThreads, 2) plane_stats_kernel(const uint6
     }
     __syncthreads();
   }
-  // kPlaneGroup planes per load of each magnitude (the per-plane summaries are
-  // independent, so the order of the element loop is unchanged)
+  // bits of the longest thread range: |sum x| < per * 15 * 2^(pg-1) < 2^(lb + pg + 3)
+  const int lb = per > 0 ? 64 - __clzll((unsigned long long)per) : 0;
   for (int pg = phi; pg >= plo; pg -= kPlaneGroup) {
-    Seg a[kPlaneGroup];
-#pragma unroll
-    for (int k = 0; k < kPlaneGroup; ++k) {
-      a[k].s = i192_zero();
-      a[k].m = i192_zero();
-      a[k].empty = (t_lo >= t_hi);
-    }
-    const int pgl = max(plo, pg - kPlaneGroup + 1);  // lowest plane of this group
-    for (int64_t i = t_lo; i < t_hi; ++i) {
-      const uint64_t v = q[i];
-      // zero through every plane of the group: D = 0 there, and skipping it
-      // leaves both the sum and the largest prefix (which starts at 0) unchanged
-      if ((v >> pgl) == 0) continue;
-#pragma unroll
-      for (int k = 0; k < kPlaneGroup; ++k) {
-        const int p = pg - k;
-        const I192 d = (p >= plo) ? plane_reduction(v, p) : i192_zero();
-        a[k].s = i192_add(a[k].s, d);
-        if (i192_lt(a[k].m, a[k].s) || i == t_lo) a[k].m = a[k].s;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kPlaneGroup; ++k) {
-      const int p = pg - k;
-      if (p < plo) break;
-      Seg r = warp_seg_reduce(a[k]);
-      if (lane == 0) wsum[warp] = r;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        Seg t = wsum[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = seg_combine(t, wsum[w]);
-        out[(int64_t)(phi - p) * gridDim.x + blockIdx.x] = t;
-      }
-      __syncthreads();
-    }
+    if (pg > 60) plane_group<__int128, __int128>(q, t_lo, t_hi, pg, plo, phi, wsum, out);
+    else if (lb + pg + 3 <= 63) plane_group<int64_t, int64_t>(q, t_lo, t_hi, pg, plo, phi, wsum, out);
+    else plane_group<int64_t, __int128>(q, t_lo, t_hi, pg, plo, phi, wsum, out);
   }
 }
 
@@ -477,33 +574,40 @@ __global__ void __launch_bounds__(kIstarThreads) istar_kernel(const uint64_t* __
   const int64_t per = (seg_len + blockDim.x - 1) / blockDim.x;
   const int64_t t_lo = min(s_hi, s_lo + tid * per);
   const int64_t t_hi = min(s_hi, t_lo + per);
-  Seg a;
-  a.empty = 1;
-  a.s = a.m = i192_zero();
-  for (int64_t i = t_lo; i < t_hi; ++i) {
-    const uint64_t v = q[i];
-    const I192 d = plane_reduction(v, p);
-    if (a.empty) { a.s = d; a.m = d; a.empty = 0; }
-    else {
-      a.s = i192_add(a.s, d);
-      if (i192_lt(a.m, a.s)) a.m = a.s;
+  const int sh_p = plane_shift(p);
+  __int128 xs = 0, xm = acc_lowest<__int128>();
+  if (p > 60) {
+    for (int64_t i = t_lo; i < t_hi; ++i) {
+      xs += plane_factor<__int128>(q[i], p);
+      if (xm < xs) xm = xs;
+    }
+  } else {
+    for (int64_t i = t_lo; i < t_hi; ++i) {
+      xs += (__int128)plane_factor<int64_t>(q[i], p);
+      if (xm < xs) xm = xs;
     }
   }
+  Seg a;
+  a.empty = t_lo >= t_hi;
+  a.s = a.empty ? i192_zero() : i192_from_i128_shl(xs, sh_p);
+  a.m = a.empty ? i192_zero() : i192_from_i128_shl(xm, sh_p);
   const I192 pre2 = i192_add(seg_pre, i192_block_exscan(a.empty ? i192_zero() : a.s, sh, &tot));
   if (tid == 0) s_first = INT_MAX;
   __syncthreads();
   if (!a.empty && i192_le(i192_sub(E1, i192_add(pre2, a.m)), T)) atomicMin(&s_first, tid);
   __syncthreads();
-  // 3. element by element inside the hit thread's range
+  // 3. element by element inside the hit thread's range: the first prefix of
+  // factors reaching ceil((E1 - pre2 - T) / 2^(p-1)), which the range's largest
+  // prefix does, so the threshold fits the 128-bit sum
   if (tid == s_first) {
-    I192 run = i192_sub(E1, pre2);
+    const I192 run0 = i192_sub(E1, pre2);
+    const __int128 tau = i192_ceil_shr(i192_sub(run0, T), sh_p);
+    __int128 acc = 0;
     for (int64_t i = t_lo; i < t_hi; ++i) {
-      const uint64_t v = q[i];
-      const I192 d = plane_reduction(v, p);
-      run = i192_sub(run, d);
-      if (i192_le(run, T)) {
+      acc += (p > 60) ? plane_factor<__int128>(q[i], p) : (__int128)plane_factor<int64_t>(q[i], p);
+      if (acc >= tau) {
         st->i_star = i;
-        st->e_star = run;
+        st->e_star = i192_sub(run0, i192_from_i128_shl(acc, sh_p));
         break;
       }
     }
@@ -520,6 +624,13 @@ __device__ __forceinline__ I192 cat_reduction(uint64_t v, int p, int cat) {
   const int sig = (p == 63) ? 0 : ((v >> (p + 1)) != 0 ? 1 : 0);
   if (sig != cat) return i192_zero();
   return plane_reduction(v, p);
+}
+
+template <typename X>
+__device__ __forceinline__ X cat_factor(uint64_t v, int p, int cat) {
+  if ((v >> p) == 0) return (X)0;
+  const int sig = (p == 63) ? 0 : ((v >> (p + 1)) != 0 ? 1 : 0);
+  return sig == cat ? plane_factor<X>(v, p) : (X)0;
 }
 
 // Per segment of the tracker's segmentation: the ordered summaries of the
@@ -557,6 +668,30 @@ __device__ I192 warp_i192_sum(I192 e) {
   return e;  // lane 0 holds the sum (other lanes: partial sums, mod 2^192)
 }
 
+template <typename X>
+__device__ __forceinline__ void split_stats_range(const uint64_t* __restrict__ q, int64_t t_lo, int64_t t_hi, int p,
+                                                  __int128 (&xs)[2], __int128 (&xm)[2], __int128 (&xd)[2],
+                                                  unsigned long long (&c)[2]) {
+  for (int64_t i = t_lo; i < t_hi; ++i) {
+    const uint64_t v = q[i];
+    if ((v >> p) == 0) continue;
+    const bool sig = p < 63 && (v >> (p + 1)) != 0;
+    const __int128 x = (__int128)plane_factor<X>(v, p);
+    // only the category the bit belongs to moves; the other keeps its prefix
+    if (sig) {
+      xs[1] += x;
+      if (xm[1] < xs[1]) xm[1] = xs[1];
+      // plane p + 1: this coefficient's bit there is leading or trailing
+      const __int128 x1 = (__int128)plane_factor<X>(v, p + 1);
+      if (p + 1 < 63 && (v >> (p + 2)) != 0) { xd[1] += x1; ++c[1]; }
+      else { xd[0] += x1; ++c[0]; }
+    } else {
+      xs[0] += x;
+      if (xm[0] < xs[0]) xm[0] = xs[0];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kSegThreads) split_stats_kernel(const uint64_t* __restrict__ q, int64_t n,
                                                                    int64_t seg_len, int p, SplitSeg* __restrict__ out) {
   __shared__ Seg wsum[kSegThreads / 32];
@@ -568,31 +703,19 @@ __global__ void __launch_bounds__(kSegThreads) split_stats_kernel(const uint64_t
   const int64_t t_lo = min(s_hi, s_lo + threadIdx.x * per);
   const int64_t t_hi = min(s_hi, t_lo + per);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Seg a[2];
-  I192 d[2] = {i192_zero(), i192_zero()};
+  // factors of plane p per category (sum and largest prefix, the empty prefix
+  // included) and of plane p + 1 per category (order-free sums)
+  __int128 xs[2] = {0, 0}, xm[2] = {0, 0}, xd[2] = {0, 0};
   unsigned long long c[2] = {0ull, 0ull};
-  for (int k = 0; k < 2; ++k) { a[k].s = a[k].m = i192_zero(); a[k].empty = 0; }
-  const bool above = p <= 62;
-  for (int64_t i = t_lo; i < t_hi; ++i) {
-    const uint64_t v = q[i];
-    if ((v >> p) != 0) {
-      const int sig = (p == 63) ? 0 : ((v >> (p + 1)) != 0 ? 1 : 0);
-      const I192 r = plane_reduction(v, p);
-      // only the category the bit belongs to moves; the other keeps its prefix
-      if (sig) {
-        a[1].s = i192_add(a[1].s, r);
-        if (i192_lt(a[1].m, a[1].s)) a[1].m = a[1].s;
-      } else {
-        a[0].s = i192_add(a[0].s, r);
-        if (i192_lt(a[0].m, a[0].s)) a[0].m = a[0].s;
-      }
-      if (above && (v >> (p + 1)) != 0) {
-        const int sig1 = (p + 1 == 63) ? 0 : ((v >> (p + 2)) != 0 ? 1 : 0);
-        const I192 r1 = plane_reduction(v, p + 1);
-        if (sig1) { d[1] = i192_add(d[1], r1); ++c[1]; }
-        else { d[0] = i192_add(d[0], r1); ++c[0]; }
-      }
-    }
+  if (p >= 60) split_stats_range<__int128>(q, t_lo, t_hi, p, xs, xm, xd, c);
+  else split_stats_range<int64_t>(q, t_lo, t_hi, p, xs, xm, xd, c);
+  Seg a[2];
+  I192 d[2];
+  for (int k = 0; k < 2; ++k) {
+    a[k].empty = 0;
+    a[k].s = i192_from_i128_shl(xs[k], plane_shift(p));
+    a[k].m = i192_from_i128_shl(xm[k], plane_shift(p));
+    d[k] = p <= 62 ? i192_from_i128_shl(xd[k], plane_shift(p + 1)) : i192_zero();
   }
   const Seg l = block_seg_reduce(a[0], wsum);
   const Seg t = block_seg_reduce(a[1], wsum);
@@ -691,14 +814,23 @@ __device__ int64_t split_first_passage(const uint64_t* __restrict__ q, int64_t n
   const int64_t per = (seg_len + blockDim.x - 1) / blockDim.x;
   const int64_t t_lo = min(s_hi, s_lo + tid * per);
   const int64_t t_hi = min(s_hi, t_lo + per);
+  const int sh_p = plane_shift(p);
+  __int128 xs = 0, xm = 0;
+  if (p > 60) {
+    for (int64_t i = t_lo; i < t_hi; ++i) {
+      xs += cat_factor<__int128>(q[i], p, cat);
+      if (xm < xs) xm = xs;
+    }
+  } else {
+    for (int64_t i = t_lo; i < t_hi; ++i) {
+      xs += (__int128)cat_factor<int64_t>(q[i], p, cat);
+      if (xm < xs) xm = xs;
+    }
+  }
   Seg a;
   a.empty = 0;
-  a.s = a.m = i192_zero();
-  for (int64_t i = t_lo; i < t_hi; ++i) {
-    const I192 d = cat_reduction(q[i], p, cat);
-    a.s = i192_add(a.s, d);
-    if (i192_lt(a.m, a.s)) a.m = a.s;
-  }
+  a.s = i192_from_i128_shl(xs, sh_p);
+  a.m = i192_from_i128_shl(xm, sh_p);
   I192 tot2;
   const I192 pre2 = i192_add(seg_pre, i192_block_exscan(a.s, S->sh, &tot2));
   if (tid == 0) S->first = INT_MAX;
@@ -706,12 +838,15 @@ __device__ int64_t split_first_passage(const uint64_t* __restrict__ q, int64_t n
   if (i192_le(i192_sub(start, i192_add(pre2, a.m)), T)) atomicMin(&S->first, tid);
   __syncthreads();
   if (tid == S->first) {
-    I192 run = i192_sub(start, pre2);
+    // the first prefix of factors reaching ceil((start - pre2 - T) / 2^(p-1))
+    const I192 run0 = i192_sub(start, pre2);
+    const __int128 tau = i192_ceil_shr(i192_sub(run0, T), sh_p);
+    __int128 acc = 0;
     for (int64_t i = t_lo; i < t_hi; ++i) {
-      run = i192_sub(run, cat_reduction(q[i], p, cat));
-      if (i192_le(run, T)) {
+      acc += (p > 60) ? cat_factor<__int128>(q[i], p, cat) : (__int128)cat_factor<int64_t>(q[i], p, cat);
+      if (acc >= tau) {
         S->j = i;
-        S->run = run;
+        S->run = i192_sub(run0, i192_from_i128_shl(acc, sh_p));
         S->hit = 1;
         break;
       }
@@ -1063,6 +1198,8 @@ __global__ void __launch_bounds__(32 * kEncWarps) enc_rans_kernel(EncParams P, i
 // final place together with the chunk's raw bytes and its table entry.
 constexpr int kEncBlockMax = 4096;
 constexpr int kEncBlockThreads = 256;
+constexpr int kEncBlockResident = 8;  // CTAs per SM of the persistent pass 1
+int g_enc_nsm = 0;
 
 struct BlockEncParams {
   const uint64_t* q;
@@ -1085,176 +1222,217 @@ struct BlockEncParams {
   unsigned long long* hist;    // nplanes x 17
 };
 
+// Pass 1 over the blocks b = blockIdx.x, blockIdx.x + gridDim.x, ... (one
+// wave of CTAs, the run-symbol histogram kept in shared memory and added to
+// the global one once per CTA).  Dynamic shared memory: the block's
+// magnitudes (8 B), signs and leading-bit positions (1 B each), block_size of
+// each.
 __global__ void __launch_bounds__(kEncBlockThreads) enc_block_kernel(BlockEncParams P) {
-  __shared__ unsigned long long qs[kEncBlockMax];
-  __shared__ uint8_t ss[kEncBlockMax];
-  __shared__ signed char ms[kEncBlockMax];   // leading-bit position, -1 for zero
+  extern __shared__ __align__(16) unsigned char enc_dyn[];
+  unsigned long long* qs = reinterpret_cast<unsigned long long*>(enc_dyn);
+  uint8_t* ss = enc_dyn + 8 * (size_t)P.block_size;
+  signed char* ms = reinterpret_cast<signed char*>(ss + P.block_size);  // leading-bit position, -1 for zero
   __shared__ uint32_t s_cnt[65], s_hpos[65];  // per leading-bit position m + 1: count, last index + 1
-  __shared__ uint32_t s_low[64];
+  __shared__ uint32_t s_pre[66], s_low[64];   // exclusive prefix sums of s_cnt; prefix maxima of s_hpos
   __shared__ uint32_t s_lastones[2], s_lastlow[2], s_cnt_last[2];  // last plane: [leading 1s/last 1, ...]
   __shared__ uint32_t s_roff[64], s_woff[64];
   __shared__ unsigned s_hist[64 * kNsym];
-  const int64_t b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t lo = b * P.block_size, hi_all = min(P.n, lo + P.block_size);
-  const int len = (int)(hi_all - lo);
   const int np = P.nplanes;
-  // the last plane's category bounds inside this block (exclusive, relative to lo)
-  const int hl = (int)max((int64_t)0, min((int64_t)len, P.i_lead + 1 - lo));
-  const int ht = (int)max((int64_t)0, min((int64_t)len, P.i_trail + 1 - lo));
-  for (int i = tid; i < 65; i += kEncBlockThreads) { s_cnt[i] = 0; s_hpos[i] = 0; }
-  if (tid < 2) { s_lastones[tid] = 0; s_lastlow[tid] = 0; s_cnt_last[tid] = 0; }
-  for (int i = tid; i < 64 * kNsym; i += kEncBlockThreads) s_hist[i] = 0;
-  __syncthreads();
   const int plast = P.p_top - (np - 1);   // == p_star unless this is the single-plane cost pass
   const bool last_split = (plast == P.p_star);
-  for (int g = 0; g < len; g += kEncBlockThreads) {
-    const int i = g + tid;
-    const bool valid = i < len;
-    const uint64_t v = valid ? P.q[lo + i] : 0ull;
-    const int m = valid ? (v ? 63 - __clzll((long long)v) : -1) : -2;
-    if (valid) {
-      qs[i] = v;
-      ss[i] = P.sg[lo + i];
-      ms[i] = (signed char)m;
+  for (int i = tid; i < np * kNsym; i += kEncBlockThreads) s_hist[i] = 0;
+  for (int64_t b = blockIdx.x; b < P.nblocks; b += gridDim.x) {
+    const int64_t lo = b * P.block_size, hi_all = min(P.n, lo + P.block_size);
+    const int len = (int)(hi_all - lo);
+    // the last plane's category bounds inside this block (exclusive, relative to lo)
+    const int hl = (int)max((int64_t)0, min((int64_t)len, P.i_lead + 1 - lo));
+    const int ht = (int)max((int64_t)0, min((int64_t)len, P.i_trail + 1 - lo));
+    for (int i = tid; i < 65; i += kEncBlockThreads) { s_cnt[i] = 0; s_hpos[i] = 0; }
+    if (tid < 2) { s_lastones[tid] = 0; s_lastlow[tid] = 0; s_cnt_last[tid] = 0; }
+    __syncthreads();
+    for (int g = 0; g < len; g += kEncBlockThreads) {
+      const int i = g + tid;
+      const bool valid = i < len;
+      const uint64_t v = valid ? P.q[lo + i] : 0ull;
+      const int m = valid ? (v ? 63 - __clzll((long long)v) : -1) : -2;
+      if (valid) {
+        qs[i] = v;
+        ss[i] = P.sg[lo + i];
+        ms[i] = (signed char)m;
+      }
+      // whole planes: a histogram over the leading-bit positions, one atomic pair
+      // per distinct position in the warp (count, last index + 1)
+      const unsigned peers = __match_any_sync(0xffffffffu, m);
+      if (valid && lane == __ffs(peers) - 1) {
+        atomicAdd(&s_cnt[m + 1], (uint32_t)__popc(peers));
+        atomicMax(&s_hpos[m + 1], (uint32_t)(g + warp * 32 + (31 - __clz(peers)) + 1));
+      }
     }
-    // whole planes: a histogram over the leading-bit positions, one atomic pair
-    // per distinct position in the warp (count, last index + 1)
-    const unsigned peers = __match_any_sync(0xffffffffu, m);
-    if (valid && lane == __ffs(peers) - 1) {
-      atomicAdd(&s_cnt[m + 1], (uint32_t)__popc(peers));
-      atomicMax(&s_hpos[m + 1], (uint32_t)(g + warp * 32 + (31 - __clz(peers)) + 1));
-    }
-  }
-  __syncthreads();
-  // the last plane (its category bounds): leading ones and trailing bits in range,
-  // the last leading one and the last leading zero in range (warp-aggregated)
-  if (last_split) {
-    const int p = plast;
-    uint32_t n1 = 0, nt = 0, l1 = 0, l0 = 0;
-    for (int i = tid; i < len; i += kEncBlockThreads) {
-      const int m = ms[i];
-      if (m > p && i < ht) ++nt;
-      if (m == p && i < hl) { ++n1; l1 = max(l1, (uint32_t)(i + 1)); }
-      if (m < p && i < hl) l0 = max(l0, (uint32_t)(i + 1));
-    }
+    __syncthreads();
+    // the last plane (its category bounds): leading ones and trailing bits in range,
+    // the last leading one and the last leading zero in range (warp-aggregated)
+    if (last_split) {
+      const int p = plast;
+      uint32_t n1 = 0, nt = 0, l1 = 0, l0 = 0;
+      for (int i = tid; i < len; i += kEncBlockThreads) {
+        const int m = ms[i];
+        if (m > p && i < ht) ++nt;
+        if (m == p && i < hl) { ++n1; l1 = max(l1, (uint32_t)(i + 1)); }
+        if (m < p && i < hl) l0 = max(l0, (uint32_t)(i + 1));
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      n1 += __shfl_xor_sync(0xffffffffu, n1, o);
-      nt += __shfl_xor_sync(0xffffffffu, nt, o);
-      l1 = max(l1, __shfl_xor_sync(0xffffffffu, l1, o));
-      l0 = max(l0, __shfl_xor_sync(0xffffffffu, l0, o));
-    }
-    if (lane == 0) {
-      atomicAdd(&s_cnt_last[0], n1);
-      atomicAdd(&s_cnt_last[1], nt);
-      atomicMax(&s_lastones[0], l1);
-      atomicMax(&s_lastlow[0], l0);
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    // whole plane p: runs = leading ones (m == p) + a final run when a leading
-    // zero (m < p) follows the last leading one; raw bits = ones (signs) + trailing (m > p)
-    uint32_t ro = 0, wo = 0;
-    uint32_t above = 0;                     // coefficients with m > p
-    for (int m = 63; m > P.p_top; --m) above += s_cnt[m + 1];
-    uint32_t low = s_hpos[0];               // s_low[p]: last index + 1 of a coefficient with m < p
-    for (int m = 0; m <= 63; ++m) {
-      s_low[m] = low;
-      low = max(low, s_hpos[m + 1]);
-    }
-    for (int pi = 0; pi < np; ++pi) {
-      const int p = P.p_top - pi;
-      uint32_t ones, trail, endrun;
-      if (pi == np - 1 && last_split) {
-        ones = s_cnt_last[0];
-        trail = s_cnt_last[1];
-        endrun = (s_lastlow[0] > s_lastones[0]) ? 1u : 0u;
-      } else {
-        ones = s_cnt[p + 1];
-        trail = above;
-        endrun = (s_low[p] > s_hpos[p + 1]) ? 1u : 0u;
+      for (int o = 16; o > 0; o >>= 1) {
+        n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+        nt += __shfl_xor_sync(0xffffffffu, nt, o);
+        l1 = max(l1, __shfl_xor_sync(0xffffffffu, l1, o));
+        l0 = max(l0, __shfl_xor_sync(0xffffffffu, l0, o));
       }
-      above += s_cnt[p + 1];
-      s_roff[pi] = ro;
-      s_woff[pi] = wo;
-      const uint32_t nr = ones + endrun;
-      const uint32_t wb = (ones + trail + 7) / 8;
-      const int64_t chunk = b * np + pi;
-      P.nruns[chunk] = nr;
-      P.run_off[chunk] = ro;
-      P.raw_off[chunk] = wo;
-      P.wsize[chunk] = wb;
-      ro += nr;
-      wo += wb;
+      if (lane == 0) {
+        atomicAdd(&s_cnt_last[0], n1);
+        atomicAdd(&s_cnt_last[1], nt);
+        atomicMax(&s_lastones[0], l1);
+        atomicMax(&s_lastlow[0], l0);
+      }
     }
-  }
-  __syncthreads();
-  const unsigned lt = (1u << lane) - 1u;
-  for (int pi = warp; pi < np; pi += kEncBlockThreads / 32) {
-    const int p = P.p_top - pi;
-    const bool lastp = (pi == np - 1) && last_split;
-    const int cl = lastp ? hl : len, ct = lastp ? ht : len;  // category bounds of this chunk
-    const int clen = max(cl, ct);
-    uint32_t* runs = P.runs + b * P.run_slot + s_roff[pi];
-    uint8_t* rawp = P.raw + b * P.raw_slot + s_woff[pi];
-    unsigned* h = s_hist + pi * kNsym;
-    uint32_t nr = 0, carry = 0;
-    uint64_t acc = 0;
-    int nacc = 0;
-    for (int g = 0; g < clen; g += 32) {
-      const int i = g + lane;
-      const int m = (i < clen) ? ms[i] : -1;
-      const bool sig_in = i < ct && m > p;          // an encoded trailing bit
-      const bool lead = i < cl && m <= p;            // an encoded leading bit
-      const bool one = lead && m == p;
-      const bool rawp_b = sig_in || one;
-      const bool rawv = sig_in ? ((qs[i] >> p) & 1ull) : (one ? (ss[i] != 0) : false);
-      const unsigned lead_m = __ballot_sync(0xffffffffu, lead);
-      const unsigned one_m = __ballot_sync(0xffffffffu, one);
-      const unsigned raw_m = __ballot_sync(0xffffffffu, rawp_b);
-      const int rank = __popc(raw_m & lt);
-      const unsigned packed = __reduce_or_sync(0xffffffffu, (rawp_b && rawv) ? (1u << rank) : 0u);
-      const int cnt = __popc(raw_m);
-      // runs: lane l holding a leading 1 emits the zeros since the previous leading 1
-      const unsigned zero_m = lead_m & ~one_m;
-      if (one) {
-        const unsigned prevmask = one_m & lt;
-        uint32_t run;
-        if (prevmask) {
-          const int pl = 31 - __clz(prevmask);
-          const unsigned from = (pl == 31) ? 0u : ~((2u << pl) - 1u);
-          run = __popc(zero_m & lt & from);
-        } else {
-          run = carry + __popc(zero_m & lt);
+    __syncthreads();
+    if (warp == 0) {
+      // scans over the leading-bit positions t = m + 1 in [0, 64]: lane l holds
+      // t = l and l + 32 (t = 64 added after): s_pre[t] = sum_{t' < t} cnt,
+      // s_low[p] = max_{t <= p} hpos (last index + 1 of a coefficient with m < p)
+      uint32_t c0 = s_cnt[lane], c1 = s_cnt[lane + 32];
+      uint32_t h0 = s_hpos[lane], h1 = s_hpos[lane + 32];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a0 = __shfl_up_sync(0xffffffffu, c0, o), a1 = __shfl_up_sync(0xffffffffu, c1, o);
+        const uint32_t g0 = __shfl_up_sync(0xffffffffu, h0, o), g1 = __shfl_up_sync(0xffffffffu, h1, o);
+        if (lane >= o) { c0 += a0; c1 += a1; h0 = max(h0, g0); h1 = max(h1, g1); }
+      }
+      const uint32_t tot0 = __shfl_sync(0xffffffffu, c0, 31), max0 = __shfl_sync(0xffffffffu, h0, 31);
+      c1 += tot0;
+      h1 = max(h1, max0);
+      s_pre[lane + 1] = c0;
+      s_pre[lane + 33] = c1;
+      if (lane == 0) s_pre[0] = 0;
+      if (lane == 31) s_pre[65] = c1 + s_cnt[64];
+      s_low[lane] = h0;
+      s_low[lane + 32] = h1;
+      __syncwarp();
+      // per plane pi = lane, lane + 32: runs = leading ones + a final run when a
+      // leading zero follows the last leading one; raw bits = ones (signs) +
+      // trailing bits; then the chunks' offsets inside the block's slots
+      uint32_t nr[2], wb[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int pi = lane + 32 * k;
+        nr[k] = 0;
+        wb[k] = 0;
+        if (pi < np) {
+          const int p = P.p_top - pi;
+          uint32_t ones, trail, endrun;
+          if (pi == np - 1 && last_split) {
+            ones = s_cnt_last[0];
+            trail = s_cnt_last[1];
+            endrun = (s_lastlow[0] > s_lastones[0]) ? 1u : 0u;
+          } else {
+            ones = s_cnt[p + 1];
+            trail = s_pre[65] - s_pre[p + 2];  // coefficients with m > p
+            endrun = (s_low[p] > s_hpos[p + 1]) ? 1u : 0u;
+          }
+          nr[k] = ones + endrun;
+          wb[k] = (ones + trail + 7) / 8;
         }
-        runs[nr + __popc(one_m & lt)] = run;
-        atomicAdd(&h[bucket_of(run)], 1u);
       }
-      nr += __popc(one_m);
-      if (one_m) {
-        const int ll = 31 - __clz(one_m);
-        const unsigned above_m = (ll == 31) ? 0u : ~((2u << ll) - 1u);
-        carry = __popc(zero_m & above_m);
-      } else {
-        carry += __popc(zero_m);
+      uint32_t r0 = nr[0], r1 = nr[1], w0 = wb[0], w1 = wb[1];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a0 = __shfl_up_sync(0xffffffffu, r0, o), a1 = __shfl_up_sync(0xffffffffu, r1, o);
+        const uint32_t b0 = __shfl_up_sync(0xffffffffu, w0, o), b1 = __shfl_up_sync(0xffffffffu, w1, o);
+        if (lane >= o) { r0 += a0; r1 += a1; w0 += b0; w1 += b1; }
       }
-      if (lane == 0 && cnt > 0) {
-        acc |= (uint64_t)packed << nacc;
-        nacc += cnt;
-        while (nacc >= 8) { *rawp++ = (uint8_t)(acc & 0xff); acc >>= 8; nacc -= 8; }
+      r1 += __shfl_sync(0xffffffffu, r0, 31);
+      w1 += __shfl_sync(0xffffffffu, w0, 31);
+      const uint32_t ro[2] = {r0 - nr[0], r1 - nr[1]}, wo[2] = {w0 - wb[0], w1 - wb[1]};
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int pi = lane + 32 * k;
+        if (pi < np) {
+          s_roff[pi] = ro[k];
+          s_woff[pi] = wo[k];
+          const int64_t chunk = b * np + pi;
+          P.nruns[chunk] = nr[k];
+          P.run_off[chunk] = ro[k];
+          P.raw_off[chunk] = wo[k];
+          P.wsize[chunk] = wb[k];
+        }
       }
     }
-    if (lane == 0) {
-      if (nacc > 0) *rawp = (uint8_t)(acc & 0xff);
-      if (carry > 0) {
-        runs[nr] = carry;
-        atomicAdd(&h[bucket_of(carry)], 1u);
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int pi = warp; pi < np; pi += kEncBlockThreads / 32) {
+      const int p = P.p_top - pi;
+      const bool lastp = (pi == np - 1) && last_split;
+      const int cl = lastp ? hl : len, ct = lastp ? ht : len;  // category bounds of this chunk
+      const int clen = max(cl, ct);
+      uint32_t* runs = P.runs + b * P.run_slot + s_roff[pi];
+      uint8_t* rawp = P.raw + b * P.raw_slot + s_woff[pi];
+      unsigned* h = s_hist + pi * kNsym;
+      uint32_t nrun = 0, carry = 0;
+      uint64_t acc = 0;
+      int nacc = 0;
+      for (int g = 0; g < clen; g += 32) {
+        const int i = g + lane;
+        const int m = (i < clen) ? ms[i] : -1;
+        const bool sig_in = i < ct && m > p;          // an encoded trailing bit
+        const bool lead = i < cl && m <= p;            // an encoded leading bit
+        const bool one = lead && m == p;
+        const bool rawp_b = sig_in || one;
+        const bool rawv = sig_in ? ((qs[i] >> p) & 1ull) : (one ? (ss[i] != 0) : false);
+        const unsigned lead_m = __ballot_sync(0xffffffffu, lead);
+        const unsigned one_m = __ballot_sync(0xffffffffu, one);
+        const unsigned raw_m = __ballot_sync(0xffffffffu, rawp_b);
+        const int rank = __popc(raw_m & lt);
+        const unsigned packed = __reduce_or_sync(0xffffffffu, (rawp_b && rawv) ? (1u << rank) : 0u);
+        const int cnt = __popc(raw_m);
+        // runs: lane l holding a leading 1 emits the zeros since the previous leading 1
+        const unsigned zero_m = lead_m & ~one_m;
+        if (one) {
+          const unsigned prevmask = one_m & lt;
+          uint32_t run;
+          if (prevmask) {
+            const int pl = 31 - __clz(prevmask);
+            const unsigned from = (pl == 31) ? 0u : ~((2u << pl) - 1u);
+            run = __popc(zero_m & lt & from);
+          } else {
+            run = carry + __popc(zero_m & lt);
+          }
+          runs[nrun + __popc(one_m & lt)] = run;
+          atomicAdd(&h[bucket_of(run)], 1u);
+        }
+        nrun += __popc(one_m);
+        if (one_m) {
+          const int ll = 31 - __clz(one_m);
+          const unsigned above_m = (ll == 31) ? 0u : ~((2u << ll) - 1u);
+          carry = __popc(zero_m & above_m);
+        } else {
+          carry += __popc(zero_m);
+        }
+        if (lane == 0 && cnt > 0) {
+          acc |= (uint64_t)packed << nacc;
+          nacc += cnt;
+          while (nacc >= 8) { *rawp++ = (uint8_t)(acc & 0xff); acc >>= 8; nacc -= 8; }
+        }
+      }
+      if (lane == 0) {
+        if (nacc > 0) *rawp = (uint8_t)(acc & 0xff);
+        if (carry > 0) {
+          runs[nrun] = carry;
+          atomicAdd(&h[bucket_of(carry)], 1u);
+        }
       }
     }
+    __syncthreads();  // the block's staging and counters are reused by the next block
   }
-  __syncthreads();
   for (int i = tid; i < np * kNsym; i += kEncBlockThreads)
     if (s_hist[i]) atomicAdd(&P.hist[i], (unsigned long long)s_hist[i]);
 }
@@ -2367,6 +2545,11 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     }
   }
   // passes over `np` planes from p_top: histograms, tables, rANS sizes
+  if (g_enc_nsm == 0) {
+    int dev = 0;
+    ATC_CUDA_TRY(cudaGetDevice(&dev));
+    ATC_CUDA_TRY(cudaDeviceGetAttribute(&g_enc_nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
   auto size_pass = [&](int p_top, int np, int64_t il, int64_t it) -> int {
     const int64_t nch = nblocks * np;
     ATC_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * np * kNsym, s));
@@ -2374,7 +2557,9 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
       B.p_top = p_top; B.nplanes = np; B.i_lead = il; B.i_trail = it;
       {
         KTimed kt_(s, "enc_block_kernel", (double)n * 9.0 + (double)nblocks * (double)B.run_slot * 4.0 * np / nplanes);
-        enc_block_kernel<<<(unsigned)nblocks, kEncBlockThreads, 0, s>>>(B);
+        const size_t dyn = (size_t)10 * B.block_size;
+        const int64_t waves = (int64_t)g_enc_nsm * kEncBlockResident;
+        enc_block_kernel<<<(unsigned)(nblocks < waves ? nblocks : waves), kEncBlockThreads, dyn, s>>>(B);
       }
       ATC_LAUNCHED(1);
       freq_kernel<<<(np + 63) / 64, 64, 0, s>>>(hist, np, fc);

@@ -126,51 +126,66 @@ int grid_for(int64_t n, int threads) {
 // shared memory; a warp forms (G u_j)_i for one row i at a time (lanes over
 // the contiguous row, a fixed butterfly), then a fixed-order block sum.  FP64
 // throughout, the same order on every run.
-constexpr int kRayThreads = 512;
+constexpr int kRayThreads = 256;
 constexpr int kRayMaxN = 1024;
+// CTA (j, c): the part of u_j^T G u_j from rows [c * chunk, (c + 1) * chunk)
+// of G, i.e. sum_i u_ij (G u_j)_i over the chunk; CTA (rh, c) sums the
+// chunk's diagonal of G instead.  out[j * nsplit + c]; the caller adds the
+// nsplit parts of each j in order.
 __global__ void __launch_bounds__(kRayThreads) rayleigh_kernel(const double* __restrict__ G, int n,
-                                                               const double* __restrict__ U, int rh,
+                                                               const double* __restrict__ U, int rh, int chunk,
                                                                double* __restrict__ out) {
   __shared__ double uj[kRayMaxN];
   __shared__ double sh[32];
-  const int j = blockIdx.x;
-  if (j > rh) return;
+  const int j = blockIdx.x, c = blockIdx.y;
+  const int r0 = c * chunk, r1 = min(n, r0 + chunk);
   double acc = 0.0;
   if (j == rh) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += G[(int64_t)i * n + i];
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) acc += G[(int64_t)i * n + i];
   } else {
     for (int i = threadIdx.x; i < n; i += blockDim.x) uj[i] = U[(int64_t)i * rh + j];
     __syncthreads();
     // four rows per warp at a time: independent FMA chains hide the FP64
     // latency (GB300 issues FP64 at a low rate with a long pipeline)
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int i0 = 4 * (threadIdx.x >> 5); i0 < n; i0 += 4 * nw) {
+    for (int i0 = r0 + 4 * (threadIdx.x >> 5); i0 < r1; i0 += 4 * nw) {
       double w[4] = {0.0, 0.0, 0.0, 0.0};
       for (int k = lane; k < n; k += 32) {
         const double u = uj[k];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          if (i0 + q < n) w[q] = fma(G[(int64_t)(i0 + q) * n + k], u, w[q]);
+          if (i0 + q < r1) w[q] = fma(G[(int64_t)(i0 + q) * n + k], u, w[q]);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const double t = warp_sum(w[q]);
-        if (lane == 0 && i0 + q < n) acc = fma(uj[i0 + q], t, acc);
+        if (lane == 0 && i0 + q < r1) acc = fma(uj[i0 + q], t, acc);
       }
     }
   }
   const double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) out[j] = t;
+  if (threadIdx.x == 0) out[(int64_t)j * gridDim.y + c] = t;
 }
 
 }  // namespace
 
+int rayleigh_splits(int64_t n, int rh) {
+  // about two CTAs per SM over the (rh + 1) x nsplit grid, chunks of >= 16 rows
+  int ns = (int)((2 * 152 + rh) / (rh + 1));
+  const int by_rows = (int)((n + 15) / 16);
+  if (ns > by_rows) ns = by_rows;
+  if (ns > kRaySplitMax) ns = kRaySplitMax;
+  return ns < 1 ? 1 : ns;
+}
+
 int launch_rayleigh(const double* G, int64_t n, const double* U, int rh, double* out, cudaStream_t s) {
   if (n < 1 || n > kRayMaxN || rh < 0) return fail(ATC_EINVAL, "launch_rayleigh: bad sizes");
+  const int ns = rayleigh_splits(n, rh);
+  const int chunk = (int)((n + ns - 1) / ns);
   {
     KTimed kt_(s, "rayleigh_kernel", (double)n * (double)n * 8.0 + (double)n * rh * 8.0,
                2.0 * (double)n * (double)n * rh);
-    rayleigh_kernel<<<rh + 1, kRayThreads, 0, s>>>(G, (int)n, U, rh, out);
+    rayleigh_kernel<<<dim3(rh + 1, ns), kRayThreads, 0, s>>>(G, (int)n, U, rh, chunk, out);
   }
   ATC_LAUNCHED(1);
   return ATC_OK;
