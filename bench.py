@@ -281,12 +281,15 @@ def run_reference(args, world, rank):
 FP32_OPS_PER_CLK_SM = 128   # FP32 lanes per SM (4 SMSPs x 32)
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal, dense; the profiling recipe's table)
 TENSOR_KERNELS = ("gram_raw_kernel", "gram_tma_kernel", "ttm_tc_kernel")
-FP64_KERNELS = ("sub_gemm_part_kernel", "gram_fp64_kernel", "ttm_fp64_kernel")
+FP64_KERNELS = ("sub_gemm_kernel", "gram_fp64_kernel", "ttm_fp64_kernel")
 DD_KERNELS = ("qr_col_kernel", "sub_qr_kernel", "sub_qform_kernel", "rr_jacobi_kernel")
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # kernels as they stand, from the ncu captures summarised under profiles/
 # (file named per entry); a kernel changed since its capture has no entry.
-TRAFFIC = {}
+TRAFFIC = {
+    # one 32 x 32 Rayleigh-Ritz per mode, inputs L2-resident: 52.5 KB read, 0 written (mode-0 launch)
+    ("rr_jacobi_kernel", "bumps256"): (52480.0, "profiles/rr_jacobi_kernel_bumps256.md (mode-0 launch)"),
+}
 
 
 def roofline_of(name, d, hbm, bf16s, fp32_peak, fp64_peak, peak_src, sm_mhz, sms, args):

@@ -675,8 +675,15 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   int rc = Scratch::get(SLOT_SMALL, sizeof(double) * 2048, (void**)&small);
   if (rc) return bail(rc);
   double* dnorm = small + 1600;
+  // split paths: the input's slice scale (max |x|) comes out of the norm pass
+  SliceScale* xs0 = nullptr;
   {
-    rc = launch_norm2(x_dev, dtype, N, dnorm, s);
+    if (opt.precision != ATC_PREC_FP64) {
+      rc = slice_scale_begin(s, &xs0);
+      if (rc) return bail(rc);
+    }
+    rc = launch_norm2(x_dev, dtype, N, dnorm, s, xs0 ? &xs0->maxbits : nullptr);
+    if (!rc && xs0) rc = slice_scale_end(xs0, s);
     if (rc) return bail(rc);
     clk.mark(PH_NORM);
     PinnedReadback pb;
@@ -736,7 +743,8 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
     // split paths: one slice scale of the current tensor serves its Gram and its projection
     const SliceScale* xs = nullptr;
     if (opt.precision != ATC_PREC_FP64) {
-      rc = slice_scale(curp, curdt, L * n * R, s, &xs);
+      if (curp == x_dev && xs0) xs = xs0;
+      else rc = slice_scale(curp, curdt, L * n * R, s, &xs);
       if (rc) return bail(rc);
     }
     bool wide = wide_all;
@@ -763,6 +771,40 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
         // certify(): 1 = rank and factor set, 0 = it needs more than rh_cap
         // candidate vectors, < 0 = error.
         int he = 0;  // tensor-core wait flag, read with the host readbacks
+        // The rank from the quotients' row-chunk parts eh[j * ns + c] (j < rh,
+        // the trace at j = rh): the smallest r <= rh_used with tail(r) <=
+        // budget; -1 when none is.
+        auto select_rank = [&](const double* eh, int ns, int rh, int rh_used, double* tail_out) -> int {
+          auto part_sum = [&](int j) {
+            double v = 0.0;
+            for (int c2 = 0; c2 < ns; ++c2) v += eh[(size_t)j * ns + c2];
+            return v;
+          };
+          const double tr = part_sum(rh);
+          double acc = 0.0;
+          for (int rr = 1; rr <= rh_used; ++rr) {
+            acc += part_sum(rr - 1);
+            double t = tr - acc;
+            if (t < 0.0) t = 0.0;
+            if (t <= budget) { *tail_out = t; return rr; }
+          }
+          *tail_out = std::max(0.0, tr - acc);
+          return -1;
+        };
+        // the factor = the leading r columns of cand (row stride ldc), then the projection with r outputs
+        auto finish = [&](int rn, double tail, const double* cand, int ldc) -> int {
+          r = rn;
+          disc = tail;
+          if (handle_alloc((void**)&c->factors[m], sizeof(double) * (size_t)n * r, s) != ATC_OK)
+            return fail(ATC_ENOMEM, "factor allocation failed");
+          if (cudaMemcpy2DAsync(c->factors[m], sizeof(double) * r, cand, sizeof(double) * ldc, sizeof(double) * r, n,
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(ATC_ECUDA, "factor copy failed");
+          int rc2 = ttm_dispatch(curp, curdt, L, n, R, c->factors[m], r, 0, opt.precision, next, idt, s, xs);
+          if (rc2) return rc2;
+          have_y = true;
+          return 1;
+        };
         auto certify = [&](int rh, int rh_cap, const std::function<int(int, double*)>& get_cand) -> int {
           for (;;) {
             double* cand = nullptr;
@@ -777,7 +819,6 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
             PinnedReadback pb;
             rc2 = pinned_readback((size_t)(rh + 1) * ns, &pb);
             if (rc2) return rc2;
-            const double* eh = pb.dbl;
             if (cudaMemcpyAsync(pb.dbl, edev, sizeof(double) * (rh + 1) * ns, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                 cudaMemcpyAsync(&pb.ints[1], tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
               return fail(ATC_ECUDA, "Rayleigh quotient readback failed");
@@ -785,42 +826,16 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
             if (rc2) return rc2;
             he = pb.ints[1];
             if (he) return fail(ATC_ETIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)");
-            // each quotient and the trace: their row-chunk parts added in order
-            auto part_sum = [&](int j) {
-              double v = 0.0;
-              for (int c2 = 0; c2 < ns; ++c2) v += eh[(size_t)j * ns + c2];
-              return v;
-            };
-            const double tr = part_sum(rh);
-            int rn = -1;
-            double tail = 0.0, acc = 0.0;
-            for (int rr = 1; rr <= rh; ++rr) {
-              acc += part_sum(rr - 1);
-              double t = tr - acc;
-              if (t < 0.0) t = 0.0;
-              if (t <= budget) { rn = rr; tail = t; break; }
-            }
+            double tail = 0.0;
+            int rn = select_rank(pb.dbl, ns, rh, rh, &tail);
             if (rn < 0 && rh < n) {
               const int nrh = (int)std::min<int64_t>(n, 2 * (int64_t)rh);
               if (nrh > rh_cap) return 0;
               rh = nrh;
               continue;
             }
-            if (rn < 0) {
-              rn = (int)n;
-              tail = std::max(0.0, tr - acc);
-            }
-            r = rn;
-            disc = tail;
-            if (handle_alloc((void**)&c->factors[m], sizeof(double) * (size_t)n * r, s) != ATC_OK)
-              return fail(ATC_ENOMEM, "factor allocation failed");
-            if (cudaMemcpy2DAsync(c->factors[m], sizeof(double) * r, cand, sizeof(double) * rh, sizeof(double) * r, n,
-                                  cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-              return fail(ATC_ECUDA, "factor copy failed");
-            rc2 = ttm_dispatch(curp, curdt, L, n, R, c->factors[m], r, 0, opt.precision, next, idt, s, xs);
-            if (rc2) return rc2;
-            have_y = true;
-            return 1;
+            if (rn < 0) rn = (int)n;
+            return finish(rn, tail, cand, rh);
           }
         };
         bool done = false;
@@ -833,11 +848,20 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
           const int Ks = (int)std::min<int64_t>(n, kSubK), Ts = kSubIters;
           const int nmax = Ks - kSubMargin;
           double* Usub = nullptr;
+          double* edev = nullptr;
           PinnedReadback pb;
+          const int ns = rayleigh_splits(n, nmax);
           rc = Scratch::get(SLOT_SUB_U, sizeof(double) * (size_t)n * nmax, (void**)&Usub);
-          if (!rc) rc = pinned_readback(0, &pb);
+          if (!rc) rc = Scratch::get(SLOT_CAND, sizeof(double) * ((size_t)(nmax + 1) * kRaySplitMax + 8), (void**)&edev);
+          // sized for the quotients before anything is copied into it
+          if (!rc) rc = pinned_readback((size_t)(nmax + 1) * ns, &pb);
           // decision {rp, nv, passed, tensor-core error word} lands in pb.ints[2..5]
           if (!rc) rc = subspace_solve(G, (int)n, Ks, Ts, budget, kCertExtra, nmax, kSubConv, tc_err, Usub, &pb.ints[2], s);
+          // the certification of all nmax columns without waiting for the
+          // decision: the leading nv of them are the Ritz vectors when it passes
+          if (!rc) rc = launch_rayleigh(G, n, Usub, nmax, edev, s);
+          if (!rc && cudaMemcpyAsync(pb.dbl, edev, sizeof(double) * (nmax + 1) * ns, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            rc = fail(ATC_ECUDA, "Rayleigh quotient readback failed");
           if (rc) return bail(rc);
           if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(ATC_ECUDA, "stream synchronisation failed"));
           const int dec[4] = {pb.ints[2], pb.ints[3], pb.ints[4], pb.ints[5]};
@@ -846,15 +870,13 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
           if (dec[2] && dec[1] >= 1 && dec[1] <= nmax) {
             const int nv = dec[1];
             clk.mark(PH_EIG);
-            auto from_ritz = [&](int rh, double* cand) -> int {
-              if (cudaMemcpy2DAsync(cand, sizeof(double) * rh, Usub, sizeof(double) * nv, sizeof(double) * rh, n,
-                                    cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                return fail(ATC_ECUDA, "candidate copy failed");
-              return ATC_OK;
-            };
-            rc = certify(nv, nv, from_ritz);
-            if (rc < 0) return bail(rc);
-            if (rc == 1) {
+            double tail = 0.0;
+            int rn = select_rank(pb.dbl, ns, nmax, nv, &tail);
+            if (rn < 0 && nv >= n) rn = (int)n;
+            if (rn >= 1) {
+              rc = finish(rn, tail, Usub, nmax);  // 1, or an error (< 0)
+              if (rc < 0) return bail(rc);
+              rc = 0;
               done = true;
               ++st.subspace_modes;
               clk.mark(PH_TTM);

@@ -89,7 +89,9 @@ enum ScratchSlot {
 
 // ---------------------------------------------------------------- kernels
 // norm / reductions (k_reduce.cu)
-int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s);
+// ||x||^2 in FP64 into *out; mx_bits != nullptr: max |x| (float bits) is
+// atomicMax-ed into it in the same pass (a slice scale's maxbits).
+int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s, unsigned* mx_bits = nullptr);
 // *out = sum (x - z)^2 over n elements, x FP32/FP64 (dtype), z FP32; FP64 result
 int launch_convert_to_f64(const void* x, int dtype, int64_t n, double* y, cudaStream_t s);
 int launch_convert_f64_to(const double* x, int64_t n, void* y, int dtype, cudaStream_t s);
@@ -121,6 +123,11 @@ struct SliceScale {
   int shift;
 };
 int slice_scale(const void* x, int dtype, int64_t N, cudaStream_t s, const SliceScale** out);
+// The two halves of slice_scale() around a pass that fills the record's
+// maxbits itself (launch_norm2 with mx_bits): a zeroed record, then the
+// kernel that turns maxbits into the scale.
+int slice_scale_begin(cudaStream_t s, SliceScale** out);
+int slice_scale_end(SliceScale* sc, cudaStream_t s);
 // xs: the input's slice scale from slice_scale(), or nullptr to compute it here;
 // nslice: 3 (24-bit fixed point) or 4 (32-bit)
 int launch_gram_split(const void* x, int dtype, int64_t L, int64_t n, int64_t R, int precision, double* g,
@@ -148,8 +155,8 @@ int* eig_error_flag_dev();  // device word of the grid-barrier time-out flag, or
 // copy of decision_host[0..4) = {rp, nv, passed, *tc_err} (pinned host memory;
 // valid once the stream is synchronised): rp the smallest rank whose tail
 // trace(G) - sum_{j<rp} theta_j is <= budget, passed = 1 when rp >= 1, rp < n,
-// nv = rp + extra <= nmax and (|theta_K| / theta_rp)^T <= conv; then U_dev
-// (n x nv row-major, capacity n x nmax) holds the leading nv Ritz vectors.
+// nv = rp + extra <= nmax and (|theta_K| / theta_rp)^T <= conv; then the
+// leading nv columns of U_dev (n x nmax row-major) are the Ritz vectors.
 bool subspace_supported(int n, int K);
 int subspace_solve(const double* G, int n, int K, int T, double budget, int extra, int nmax, double conv,
                    const int* tc_err, double* U_dev, int* decision_host, cudaStream_t s);

@@ -932,8 +932,18 @@ __global__ void gram_tc_assemble(const double* __restrict__ part, int nsplit, in
     // tile index of (ti, cj): rows ti' < ti contribute nc64 - 2 ti' tiles each
     const int p = ti * nc64 - ti * (ti - 1) + (cj - 2 * ti);
     const int64_t ar = i - (int64_t)ti * TM, bc = j - (int64_t)cj * TN;
+    // the split partials added in split order; eight loads in flight at a time
+    const double* src = part + (int64_t)p * (TM * TN) + bc * TM + ar;
+    const int64_t sstride = (int64_t)npair * (TM * TN);
     double v = 0.0;
-    for (int s = 0; s < nsplit; ++s) v += part[((int64_t)s * npair + p) * (TM * TN) + bc * TM + ar];
+    for (int s0 = 0; s0 < nsplit; s0 += 8) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = (s0 + u < nsplit) ? __ldg(src + (s0 + u) * sstride) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < nsplit) v += t[u];
+    }
     g[orow * n + ocol] = v * f;
   }
 }
@@ -1041,6 +1051,21 @@ int slice_scale(const void* x, int dtype, int64_t N, cudaStream_t s, const Slice
   slice_scale_finish<<<1, 1, 0, s>>>(sc);
   ATC_LAUNCHED(1);
   *out = sc;
+  return ATC_OK;
+}
+
+int slice_scale_begin(cudaStream_t s, SliceScale** out) {
+  int* base = nullptr;
+  ATC_TRY(tc_error_flag(&base));
+  SliceScale* sc = reinterpret_cast<SliceScale*>(reinterpret_cast<uint8_t*>(base) + 64) + (g_scale_rot++ & 7);
+  ATC_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(SliceScale), s));
+  *out = sc;
+  return ATC_OK;
+}
+
+int slice_scale_end(SliceScale* sc, cudaStream_t s) {
+  slice_scale_finish<<<1, 1, 0, s>>>(sc);
+  ATC_LAUNCHED(1);
   return ATC_OK;
 }
 

@@ -32,43 +32,73 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// exact square of an FP32 value as a float pair, added to the double-float (hi, lo)
+__device__ __forceinline__ void sq_acc(float v, float& hi, float& lo) {
+  const float p = v * v;
+  const float e = fmaf(v, v, -p);
+  const float s = hi + p;
+  const float bp = s - hi;
+  lo += ((hi - (s - bp)) + (p - bp)) + e;
+  hi = s;
+}
+
+// Partial sums of x^2 per CTA; with mx_bits != nullptr also max |x| (as float
+// bits, atomicMax: non-negative floats order like their bit patterns), the
+// slice scale of the same tensor in the same pass.
 template <typename T>
 __global__ void __launch_bounds__(kNormThreads) norm2_partial(const T* __restrict__ x, int64_t n,
-                                                               double* __restrict__ part) {
+                                                               double* __restrict__ part, unsigned* __restrict__ mx_bits) {
   __shared__ double sh[32];
   double acc = 0.0;
+  float mx = 0.f;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t done = 0;
   if (sizeof(T) == 4 && ((uintptr_t)x & 15) == 0) {
-    // FP32 input: every square is exact as a float pair (v*v, fma(v, v, -v*v));
-    // four of them are summed as a double-float on the FP32 pipes and each
-    // group of four is added into the FP64 accumulator (GB300 issues FP64 at
-    // 1/64 of the FP32 rate, which would otherwise bound this HBM pass).
+    // FP32 input: every square is exact as a float pair (v*v, fma(v, v, -v*v)).
+    // Four float4 loads in flight a thread; their sixteen squares are summed as
+    // a double-float on the FP32 pipes and each group of sixteen is added into
+    // the FP64 accumulator (GB300 issues FP64 at 1/64 of the FP32 rate, which
+    // would otherwise bound this HBM pass).
     const int64_t n4 = n / 4;
     const float4* x4 = reinterpret_cast<const float4*>(x);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += stride) {
-      const float4 v = __ldg(x4 + i);
-      const float q[4] = {v.x, v.y, v.z, v.w};
+    int64_t i = t0;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(x4 + i + u * stride);
       float hi = 0.f, lo = 0.f;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float p = q[k] * q[k];
-        const float e = fmaf(q[k], q[k], -p);
-        const float s = hi + p;
-        const float bp = s - hi;
-        lo += ((hi - (s - bp)) + (p - bp)) + e;
-        hi = s;
+      for (int u = 0; u < 4; ++u) {
+        sq_acc(v[u].x, hi, lo);
+        sq_acc(v[u].y, hi, lo);
+        sq_acc(v[u].z, hi, lo);
+        sq_acc(v[u].w, hi, lo);
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
       }
       acc += (double)hi + (double)lo;
     }
-    for (int64_t i = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-      double v = (double)x[i];
-      acc = fma(v, v, acc);
+    for (; i < n4; i += stride) {
+      const float4 v = __ldg(x4 + i);
+      float hi = 0.f, lo = 0.f;
+      sq_acc(v.x, hi, lo);
+      sq_acc(v.y, hi, lo);
+      sq_acc(v.z, hi, lo);
+      sq_acc(v.w, hi, lo);
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      acc += (double)hi + (double)lo;
     }
-  } else {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-      double v = (double)x[i];
-      acc = fma(v, v, acc);
-    }
+    done = n4 * 4;
+  }
+  for (int64_t i = done + t0; i < n; i += stride) {
+    const double v = (double)x[i];
+    acc = fma(v, v, acc);
+    mx = fmaxf(mx, fabsf((float)x[i]));
+  }
+  if (mx_bits) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(mx_bits, __float_as_uint(mx));
   }
   double t = block_sum(acc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -191,13 +221,13 @@ int launch_rayleigh(const double* G, int64_t n, const double* U, int rh, double*
   return ATC_OK;
 }
 
-int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s) {
+int launch_norm2(const void* x, int dtype, int64_t n, double* out, cudaStream_t s, unsigned* mx_bits) {
   double* part = nullptr;
   ATC_TRY(Scratch::get(SLOT_SMALL, sizeof(double) * (kNormBlocks + 64), (void**)&part));
   if (dtype == ATC_F32)
-    { KTimed kt_(s, "norm2_partial", (double)n * 4.0); norm2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, n, part); }
+    { KTimed kt_(s, "norm2_partial", (double)n * 4.0); norm2_partial<float><<<kNormBlocks, kNormThreads, 0, s>>>((const float*)x, n, part, mx_bits); }
   else
-    { KTimed kt_(s, "norm2_partial", (double)n * 8.0); norm2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, n, part); }
+    { KTimed kt_(s, "norm2_partial", (double)n * 8.0); norm2_partial<double><<<kNormBlocks, kNormThreads, 0, s>>>((const double*)x, n, part, mx_bits); }
   ATC_LAUNCHED(1);
   sum_partials<<<1, kNormThreads, 0, s>>>(part, kNormBlocks, out);
   ATC_LAUNCHED(1);

@@ -51,65 +51,69 @@ __global__ void sub_init_kernel(double* __restrict__ V, int n, int K) {
   }
 }
 
-// From the diagonal of G, one warp: *trace = trace(G) and *ex = the exponent e
-// with max_i G[i][i] * 2^-e in [0.5, 1) (G is PSD, so its diagonal bounds |G|;
-// 0 for a zero matrix), the scale of the double-float copy of G V.
-__global__ void sub_diag_kernel(const double* __restrict__ G, int n, double* __restrict__ trace, int* __restrict__ ex) {
-  double m = 0.0, t = 0.0;
-  for (int i = threadIdx.x; i < n; i += 32) {
-    const double g = G[(int64_t)i * n + i];
-    m = fmax(m, fabs(g));
-    t += g;
-  }
+// W = G V (G n x n symmetric, V K columns of n): CTA (x, c) computes rows
+// [32 x, 32 x + 32) of column c; its eight warps take eight consecutive k
+// ranges (four FMA chains a lane), then warp 0 adds the eight parts in warp
+// order.  Wd != nullptr: the result as double-floats scaled by 2^-(*ex)
+// (|W| <= sqrt(n) then, since |G| <= max diag and V has orthonormal columns),
+// so that the QR needs no FP64 arithmetic; else FP64 into W.
+constexpr int kGemmWarps = 8;
+// trace != nullptr (the first product of a solve): from the diagonal of G
+// every CTA also takes the exponent e with max_i G_ii 2^-e in [0.5, 1) (G is
+// PSD, so its diagonal bounds |G|; 0 for a zero matrix) for its own scaling,
+// and CTA (0, 0) stores e and trace(G).
+__global__ void __launch_bounds__(32 * kGemmWarps) sub_gemm_kernel(const double* __restrict__ G, int n,
+                                                                  const double* __restrict__ V, double* __restrict__ W,
+                                                                  dd* __restrict__ Wd, int* __restrict__ ex,
+                                                                  double* __restrict__ trace) {
+  __shared__ double red[kGemmWarps][32];
+  __shared__ int s_ex;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (trace && warp == kGemmWarps - 1) {
+    double m = 0.0, t = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double g = G[(int64_t)i * n + i];
+      m = fmax(m, fabs(g));
+      t += g;
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    t += __shfl_xor_sync(0xffffffffu, t, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    if (lane == 0) {
+      int e = 0;
+      if (m > 0.0) frexp(m, &e);
+      s_ex = e;
+      if (blockIdx.x == 0 && blockIdx.y == 0) {
+        *ex = e;
+        *trace = t;
+      }
+    }
   }
-  if (threadIdx.x == 0) {
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);
-    *ex = e;
-    *trace = t;
-  }
-}
-
-// Partial products P[z][c][i] = sum_{k in split z} G[k][i] V[c][k] (= (G V)[i][c]
-// for symmetric G): a thread per (i, c, z); G is read column-wise by the 32
-// lanes of a warp (consecutive i, coalesced), V[c][k] is a warp broadcast, four
-// independent FP64 accumulators.  Grid (ceil(n/32), ceil(K/8), kSubSplit),
-// 8 warps per CTA (one column c each).
-constexpr int kSubSplit = 16;  // k-split: enough warps in flight to hide the L2 latency of G
-__global__ void __launch_bounds__(256) sub_gemm_part_kernel(const double* __restrict__ G, int n,
-                                                            const double* __restrict__ V, int K,
-                                                            double* __restrict__ part) {
-  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int c = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (i >= n || c >= K) return;
-  const int k0 = (int)((int64_t)n * blockIdx.z / kSubSplit), k1 = (int)((int64_t)n * (blockIdx.z + 1) / kSubSplit);
+  const int i = blockIdx.x * 32 + lane;
+  const int c = blockIdx.y;
+  const int k0 = (int)((int64_t)n * warp / kGemmWarps), k1 = (int)((int64_t)n * (warp + 1) / kGemmWarps);
   const double* vc = V + (int64_t)c * n;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int k = k0;
-  for (; k + 3 < k1; k += 4) {
-    a0 = fma(G[(int64_t)k * n + i], vc[k], a0);
-    a1 = fma(G[(int64_t)(k + 1) * n + i], vc[k + 1], a1);
-    a2 = fma(G[(int64_t)(k + 2) * n + i], vc[k + 2], a2);
-    a3 = fma(G[(int64_t)(k + 3) * n + i], vc[k + 3], a3);
+  if (i < n) {
+    int k = k0;
+    for (; k + 3 < k1; k += 4) {
+      a0 = fma(__ldg(G + (int64_t)k * n + i), __ldg(vc + k), a0);
+      a1 = fma(__ldg(G + (int64_t)(k + 1) * n + i), __ldg(vc + k + 1), a1);
+      a2 = fma(__ldg(G + (int64_t)(k + 2) * n + i), __ldg(vc + k + 2), a2);
+      a3 = fma(__ldg(G + (int64_t)(k + 3) * n + i), __ldg(vc + k + 3), a3);
+    }
+    for (; k < k1; ++k) a0 = fma(__ldg(G + (int64_t)k * n + i), __ldg(vc + k), a0);
   }
-  for (; k < k1; ++k) a0 = fma(G[(int64_t)k * n + i], vc[k], a0);
-  part[((int64_t)blockIdx.z * K + c) * n + i] = (a0 + a1) + (a2 + a3);
-}
-// W[c][i] = sum_z P[z][c][i] in a fixed order; Wd != nullptr: as double-floats
-// scaled by 2^-(*ex) (|W| <= sqrt(n) then, since |G| <= max diag and V has
-// orthonormal columns), so that the QR needs no FP64 arithmetic; else FP64.
-__global__ void sub_gemm_sum_kernel(const double* __restrict__ part, int n, int K, double* __restrict__ W,
-                                    dd* __restrict__ Wd, const int* __restrict__ ex) {
-  const int64_t nk = (int64_t)n * K;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
-    double v = part[e];
+  red[warp][lane] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  if (warp == 0 && i < n) {
+    double v = red[0][lane];
 #pragma unroll
-    for (int z = 1; z < kSubSplit; ++z) v += part[z * nk + e];
-    if (Wd) Wd[e] = dd_from(v * __longlong_as_double((long long)(1023 - *ex) << 52));  // v 2^-ex
+    for (int w = 1; w < kGemmWarps; ++w) v += red[w][lane];
+    const int64_t e = (int64_t)c * n + i;
+    if (Wd) Wd[e] = dd_from(v * __longlong_as_double((long long)(1023 - (trace ? s_ex : *ex)) << 52));  // v 2^-ex
     else W[e] = v;
   }
 }
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(256) sub_proj_kernel(const double* __restrict_
 // U[i][j] = sum_a V[a][i] Y[a][j] (U n x m row-major; Y K x m row-major), m = *m_dev
 // (the vector count chosen on the device by the Rayleigh-Ritz kernel; 0: nothing)
 __global__ void sub_rotate_kernel(const double* __restrict__ V, int n, int K, const double* __restrict__ Y,
-                                  const int* __restrict__ m_dev, double* __restrict__ U) {
+                                  const int* __restrict__ m_dev, double* __restrict__ U, int ldu) {
   const int m = *m_dev;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * m; e += gridDim.x * blockDim.x) {
     const int i = e / m, j = e - i * m;
@@ -146,7 +150,7 @@ __global__ void sub_rotate_kernel(const double* __restrict__ V, int n, int K, co
       s1 = fma(V[(int64_t)(a + 1) * n + i], Y[(a + 1) * m + j], s1);
     }
     if (a < K) s0 = fma(V[(int64_t)a * n + i], Y[a * m + j], s0);
-    U[e] = s0 + s1;
+    U[(int64_t)i * ldu + j] = s0 + s1;
   }
 }
 
@@ -632,9 +636,8 @@ int subspace_solve(const double* G, int n, int K, int T, double budget, int extr
   if (nmax < 1 || nmax > K || T < 1) return fail(ATC_EINVAL, "subspace_solve: nmax = %d, T = %d", nmax, T);
   const size_t nk = (size_t)n * K;
   const int npan = (K + kQrNb - 1) / kQrNb;
-  // V, W, B, theta, trace (8), Vg, Tg, Y, decision + exponent (8), split-K partials
-  const size_t nd = 2 * nk + (size_t)K * K + K + 8 + nk + (size_t)npan * kQrNb * kQrNb + (size_t)K * nmax + 8 +
-                    (size_t)kSubSplit * nk;
+  // V, W, B, theta, trace (8), Vg, Tg, Y, decision + exponent (8)
+  const size_t nd = 2 * nk + (size_t)K * K + K + 8 + nk + (size_t)npan * kQrNb * kQrNb + (size_t)K * nmax + 8;
   double* base = nullptr;
   ATC_TRY(Scratch::get(SLOT_SUBSPACE, sizeof(double) * nd, (void**)&base));
   double* V = base;
@@ -647,7 +650,6 @@ int subspace_solve(const double* G, int n, int K, int T, double budget, int extr
   double* Y = reinterpret_cast<double*>(Tg + (size_t)npan * kQrNb * kQrNb);
   int* dec = reinterpret_cast<int*>(Y + (size_t)K * nmax);
   int* gex = dec + 4;
-  double* part = Y + (size_t)K * nmax + 8;
   dd* Wd = reinterpret_cast<dd*>(W);  // the double-float copy of G V reuses the FP64 block
   // the start frame depends on (n, K) only: kept in its own slot per device
   double* V0 = nullptr;
@@ -676,14 +678,10 @@ int subspace_solve(const double* G, int n, int K, int T, double budget, int extr
   }
   // column-owner QR for n <= 256 (K <= 32 warps), the blocked one-CTA QR above
   const bool qr_col = n <= 32 * kQcRpl && K <= 32;
-  { KTimed kt_(s, "sub_diag_kernel"); sub_diag_kernel<<<1, 32, 0, s>>>(G, n, tr, gex); }
-  ATC_LAUNCHED(1);
-  const dim3 ggrid((n + 31) / 32, (K + 7) / 8, kSubSplit);
-  const int sblocks = (int)((nk + 255) / 256 < 1024 ? (nk + 255) / 256 : 1024);
+  const dim3 ggrid((n + 31) / 32, K);
   for (int t = 0; t < T; ++t) {
-    { KTimed kt_(s, "sub_gemm_part_kernel", (double)n * n * 8.0 + 2.0 * (double)nk * 8.0, 2.0 * (double)n * n * K); sub_gemm_part_kernel<<<ggrid, 256, 0, s>>>(G, n, t == 0 ? V0 : V, K, part); }
-    { KTimed kt_(s, "sub_gemm_sum_kernel"); sub_gemm_sum_kernel<<<sblocks, 256, 0, s>>>(part, n, K, nullptr, Wd, gex); }
-    ATC_LAUNCHED(2);
+    { KTimed kt_(s, "sub_gemm_kernel", (double)n * n * 8.0 + 2.0 * (double)nk * 8.0, 2.0 * (double)n * n * K); sub_gemm_kernel<<<ggrid, 32 * kGemmWarps, 0, s>>>(G, n, t == 0 ? V0 : V, nullptr, Wd, gex, t == 0 ? tr : nullptr); }
+    ATC_LAUNCHED(1);
     {
       KTimed kt_(s, qr_col ? "qr_col_kernel" : "sub_qr_kernel", 2.0 * (double)nk * 8.0, 2.0 * (double)n * K * K - 2.0 / 3.0 * (double)K * K * K);
       if (qr_col) qr_col_kernel<<<1, kQcThreads, sizeof(dd) * nk, s>>>(Wd, n, K, Vg, Tg);
@@ -693,15 +691,14 @@ int subspace_solve(const double* G, int n, int K, int T, double budget, int extr
     { KTimed kt_(s, "sub_qform_kernel", 2.0 * (double)nk * 8.0, 2.0 * (double)n * K * K); sub_qform_kernel<<<K, kQfThreads, 0, s>>>(Vg, Tg, n, K, V); }
     ATC_LAUNCHED(1);
   }
-  { KTimed kt_(s, "sub_gemm_part_kernel", (double)n * n * 8.0 + 2.0 * (double)nk * 8.0, 2.0 * (double)n * n * K); sub_gemm_part_kernel<<<ggrid, 256, 0, s>>>(G, n, V, K, part); }
-  { KTimed kt_(s, "sub_gemm_sum_kernel"); sub_gemm_sum_kernel<<<sblocks, 256, 0, s>>>(part, n, K, W, nullptr, gex); }
-  ATC_LAUNCHED(2);
+  { KTimed kt_(s, "sub_gemm_kernel", (double)n * n * 8.0 + 2.0 * (double)nk * 8.0, 2.0 * (double)n * n * K); sub_gemm_kernel<<<ggrid, 32 * kGemmWarps, 0, s>>>(G, n, V, W, nullptr, gex, nullptr); }
+  ATC_LAUNCHED(1);
   { KTimed kt_(s, "sub_proj_kernel"); sub_proj_kernel<<<(K * K * 32 + 255) / 256, 256, 0, s>>>(V, W, n, K, B); }
   ATC_LAUNCHED(1);
   // Rayleigh-Ritz on the K x K matrix B (one CTA), provisional rank and vector count on the device
   ATC_TRY(launch_rr_small(B, K, n, tr, budget, extra, nmax, conv, T, tc_err, th, dec, Y, s));
   const int rblocks = (int)(((size_t)n * nmax + 255) / 256 < 1024 ? ((size_t)n * nmax + 255) / 256 : 1024);
-  { KTimed kt_(s, "sub_rotate_kernel"); sub_rotate_kernel<<<rblocks, 256, 0, s>>>(V, n, K, Y, dec + 1, U_dev); }
+  { KTimed kt_(s, "sub_rotate_kernel"); sub_rotate_kernel<<<rblocks, 256, 0, s>>>(V, n, K, Y, dec + 1, U_dev, nmax); }
   ATC_LAUNCHED(1);
   ATC_CUDA_TRY(cudaMemcpyAsync(decision_host, dec, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
   return ATC_OK;
