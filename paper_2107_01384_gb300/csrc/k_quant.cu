@@ -1437,8 +1437,79 @@ __global__ void __launch_bounds__(kEncBlockThreads) enc_block_kernel(BlockEncPar
     if (s_hist[i]) atomicAdd(&P.hist[i], (unsigned long long)s_hist[i]);
 }
 
+// The cost pass of plane p = P.p_top alone (np = 1, no split: plane p_star + 1
+// encoded whole): the same runs, run-symbol histogram and chunk sizes as
+// enc_block_kernel with np = 1, one WARP per block reading the magnitudes
+// straight from global memory (each is used once), so that all eight warps of
+// a CTA walk blocks; the raw bits are counted, not written (only sizes are
+// taken from this pass).
+__global__ void __launch_bounds__(kEncBlockThreads) enc_cost_plane_kernel(BlockEncParams P) {
+  __shared__ unsigned s_hist[kNsym];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = P.p_top;
+  for (int i = threadIdx.x; i < kNsym; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t wpc = kEncBlockThreads / 32;
+  for (int64_t b = blockIdx.x * wpc + warp; b < P.nblocks; b += (int64_t)gridDim.x * wpc) {
+    const int64_t lo = b * P.block_size;
+    const int len = (int)(min(P.n, lo + P.block_size) - lo);
+    uint32_t* runs = P.runs + b * P.run_slot;
+    uint32_t nrun = 0, carry = 0, nraw = 0;
+    for (int g = 0; g < len; g += 32) {
+      const int i = g + lane;
+      const uint64_t v = (i < len) ? __ldg(P.q + lo + i) : 0ull;
+      const int m = (i < len) ? (v ? 63 - __clzll((long long)v) : -1) : 64;  // 64: past the block
+      const bool sig_in = m > p && m < 64;     // a trailing bit
+      const bool lead = m <= p;                // a leading bit
+      const bool one = m == p;
+      const unsigned lead_m = __ballot_sync(0xffffffffu, lead);
+      const unsigned one_m = __ballot_sync(0xffffffffu, one);
+      const unsigned raw_m = __ballot_sync(0xffffffffu, sig_in || one);
+      nraw += __popc(raw_m);
+      const unsigned zero_m = lead_m & ~one_m;
+      if (one) {
+        const unsigned prevmask = one_m & lt;
+        uint32_t run;
+        if (prevmask) {
+          const int pl = 31 - __clz(prevmask);
+          const unsigned from = (pl == 31) ? 0u : ~((2u << pl) - 1u);
+          run = __popc(zero_m & lt & from);
+        } else {
+          run = carry + __popc(zero_m & lt);
+        }
+        runs[nrun + __popc(one_m & lt)] = run;
+        atomicAdd(&s_hist[bucket_of(run)], 1u);
+      }
+      nrun += __popc(one_m);
+      if (one_m) {
+        const int ll = 31 - __clz(one_m);
+        const unsigned above_m = (ll == 31) ? 0u : ~((2u << ll) - 1u);
+        carry = __popc(zero_m & above_m);
+      } else {
+        carry += __popc(zero_m);
+      }
+    }
+    if (lane == 0) {
+      // a final run when a leading zero follows the last leading one
+      if (carry > 0) {
+        runs[nrun] = carry;
+        atomicAdd(&s_hist[bucket_of(carry)], 1u);
+        ++nrun;
+      }
+      P.nruns[b] = nrun;
+      P.run_off[b] = 0;
+      P.raw_off[b] = 0;
+      P.wsize[b] = (nraw + 7) / 8;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kNsym; i += blockDim.x)
+    if (s_hist[i]) atomicAdd(&P.hist[i], (unsigned long long)s_hist[i]);
+}
+
 struct RansThreadParams {
-  const uint32_t* runs;
+  uint32_t* runs;         // the sizes pass writes its bytes over them
   const uint8_t* raw;
   int64_t run_slot, raw_slot;
   const uint32_t* nruns;
@@ -1449,15 +1520,44 @@ struct RansThreadParams {
   int nplanes;
   int64_t nchunks;
   uint32_t* rsize;        // nchunks
+  uint32_t* rstate;       // nchunks: final rANS state (sizes pass)
   const uint64_t* off;    // nchunks + 1 (payload offsets), write pass only
   uint8_t* out;           // payload base, write pass only
   uint32_t* table;        // size table, write pass only
 };
 
-// one thread per (block, plane) chunk: rANS of its runs, backwards (the
-// sizes pass emits nothing; the write pass writes the bytes before the end of
-// the chunk's rANS area, the 4-byte state first, then copies the raw bytes)
+// one thread per (block, plane) chunk: rANS of its runs, backwards.  The
+// sizes pass writes the bytes in place over the chunk's runs, backwards from
+// their end (a run puts at most 4 bytes -- at most 2 for its extra bits, 2 for
+// its symbol, with the state in [2^23, 2^31) -- so the bytes of runs t + 1 ..
+// never reach run t before it is read) and the final state into rstate; the
+// write pass copies the 4-byte state, those bytes and the chunk's raw bytes to
+// their final place and fills its table entry.
 __global__ void enc_rans_thread_kernel(RansThreadParams P, int write) {
+  const int64_t chunk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (write) {
+    if (chunk >= P.nchunks) return;
+    const int64_t blk = chunk / P.nplanes;
+    const uint32_t nr = P.nruns[chunk];
+    uint8_t* base = P.out + P.off[chunk];
+    const uint32_t rs = P.rsize[chunk];
+    if (nr) {
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(P.runs + blk * P.run_slot + P.run_off[chunk] + nr) - (rs - 4);
+      const uint32_t x = P.rstate[chunk];
+      base[0] = (uint8_t)x;
+      base[1] = (uint8_t)(x >> 8);
+      base[2] = (uint8_t)(x >> 16);
+      base[3] = (uint8_t)(x >> 24);
+      for (uint32_t k = 0; k < rs - 4; ++k) base[4 + k] = src[k];
+    }
+    const uint32_t ws = P.wsize[chunk];
+    const uint8_t* raw = P.raw + blk * P.raw_slot + P.raw_off[chunk];
+    uint8_t* dst = base + rs;
+    for (uint32_t k = 0; k < ws; ++k) dst[k] = raw[k];
+    P.table[2 * chunk] = rs;
+    P.table[2 * chunk + 1] = ws;
+    return;
+  }
   __shared__ uint32_t f_sm[64 * kNsym], c_sm[64 * kNsym];
   __shared__ uint64_t i_sm[64 * kNsym];
   for (int i = threadIdx.x; i < P.nplanes * kNsym; i += blockDim.x) {
@@ -1467,38 +1567,19 @@ __global__ void enc_rans_thread_kernel(RansThreadParams P, int write) {
     i_sm[i] = f ? ((1ull << 44) + f - 1) / f : 0ull;
   }
   __syncthreads();
-  const int64_t chunk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (chunk >= P.nchunks) return;
   const int64_t blk = chunk / P.nplanes;
   const int pi = (int)(chunk - blk * P.nplanes);
   const uint32_t nr = P.nruns[chunk];
-  const uint32_t* runs = P.runs + blk * P.run_slot + P.run_off[chunk];
+  uint32_t* runs = P.runs + blk * P.run_slot + P.run_off[chunk];
   const uint32_t* f = f_sm + pi * kNsym;
   const uint32_t* cum = c_sm + pi * kNsym;
   const uint64_t* inv = i_sm + pi * kNsym;
   RansEnc r = {kRansL, 0};
-  if (!write) {
-    for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, inv, [](uint8_t) {});
-    P.rsize[chunk] = nr ? (r.nbytes + 4) : 0;
-    return;
-  }
-  uint8_t* base = P.out + P.off[chunk];
-  const uint32_t rs = P.rsize[chunk];
-  if (nr) {
-    uint8_t* w = base + rs;
-    for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, inv, [&](uint8_t by) { *--w = by; });
-    w -= 4;
-    w[0] = (uint8_t)r.x;
-    w[1] = (uint8_t)(r.x >> 8);
-    w[2] = (uint8_t)(r.x >> 16);
-    w[3] = (uint8_t)(r.x >> 24);
-  }
-  const uint32_t ws = P.wsize[chunk];
-  const uint8_t* src = P.raw + blk * P.raw_slot + P.raw_off[chunk];
-  uint8_t* dst = base + rs;
-  for (uint32_t k = 0; k < ws; ++k) dst[k] = src[k];
-  P.table[2 * chunk] = rs;
-  P.table[2 * chunk + 1] = ws;
+  uint8_t* w = reinterpret_cast<uint8_t*>(runs + nr);
+  for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, inv, [&](uint8_t by) { *--w = by; });
+  P.rsize[chunk] = nr ? (r.nbytes + 4) : 0;
+  P.rstate[chunk] = r.x;
 }
 
 // Exclusive prefix sums of item sizes f(i) over many CTAs (the payload
@@ -2525,13 +2606,14 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
       uint8_t* work = nullptr;
       const size_t runs_b = sizeof(uint32_t) * (size_t)nblocks * (size_t)B.run_slot;
       const size_t raw_b = ((size_t)nblocks * (size_t)B.raw_slot + 255) & ~(size_t)255;
-      const size_t meta_b = sizeof(uint32_t) * 4 * (size_t)nchunks + 256;
+      const size_t meta_b = sizeof(uint32_t) * 4 * (size_t)nchunks + 256;  // nruns, run_off, raw_off, rstate
       ATC_TRY(Scratch::get(SLOT_SPILL, runs_b + raw_b + meta_b, (void**)&work));
       B.runs = reinterpret_cast<uint32_t*>(work);
       B.raw = work + runs_b;
       B.nruns = reinterpret_cast<uint32_t*>(work + runs_b + raw_b);
       B.run_off = B.nruns + nchunks;
       B.raw_off = B.run_off + nchunks;
+      R.rstate = B.raw_off + nchunks;
       B.wsize = wsize;
       B.hist = hist;
       R.runs = B.runs; R.raw = B.raw; R.run_slot = B.run_slot; R.raw_slot = B.raw_slot;
@@ -2555,10 +2637,15 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
     ATC_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * np * kNsym, s));
     if (block_path) {
       B.p_top = p_top; B.nplanes = np; B.i_lead = il; B.i_trail = it;
-      {
+      const int64_t waves = (int64_t)g_enc_nsm * kEncBlockResident;
+      if (np == 1 && p_top != p_star) {
+        // the cost pass of plane p_star + 1: a warp per block
+        KTimed kt_(s, "enc_cost_plane_kernel", (double)n * 8.0 + (double)nblocks * (double)B.run_slot * 4.0 / nplanes);
+        const int64_t ctas = (nblocks + kEncBlockThreads / 32 - 1) / (kEncBlockThreads / 32);
+        enc_cost_plane_kernel<<<(unsigned)(ctas < waves ? ctas : waves), kEncBlockThreads, 0, s>>>(B);
+      } else {
         KTimed kt_(s, "enc_block_kernel", (double)n * 9.0 + (double)nblocks * (double)B.run_slot * 4.0 * np / nplanes);
         const size_t dyn = (size_t)10 * B.block_size;
-        const int64_t waves = (int64_t)g_enc_nsm * kEncBlockResident;
         enc_block_kernel<<<(unsigned)(nblocks < waves ? nblocks : waves), kEncBlockThreads, dyn, s>>>(B);
       }
       ATC_LAUNCHED(1);
