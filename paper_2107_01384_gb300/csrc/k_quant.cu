@@ -1577,7 +1577,17 @@ __global__ void enc_rans_thread_kernel(RansThreadParams P, int write) {
   const uint64_t* inv = i_sm + pi * kNsym;
   RansEnc r = {kRansL, 0};
   uint8_t* w = reinterpret_cast<uint8_t*>(runs + nr);
-  for (int64_t t = (int64_t)nr - 1; t >= 0; --t) rans_put_run(r, runs[t], f, cum, inv, [&](uint8_t by) { *--w = by; });
+  // eight runs loaded ahead of their encoding: the bytes of runs t + 1 .. lie
+  // in [4 (t + 1), 4 nr), so runs t - 7 .. t are intact when loaded
+  int64_t t = (int64_t)nr - 1;
+  for (; t >= 7; t -= 8) {
+    uint32_t rb[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) rb[u] = runs[t - u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) rans_put_run(r, rb[u], f, cum, inv, [&](uint8_t by) { *--w = by; });
+  }
+  for (; t >= 0; --t) rans_put_run(r, runs[t], f, cum, inv, [&](uint8_t by) { *--w = by; });
   P.rsize[chunk] = nr ? (r.nbytes + 4) : 0;
   P.rstate[chunk] = r.x;
 }
@@ -1712,7 +1722,8 @@ struct DecParams {
   int nplanes;
   int64_t nblocks;
   int64_t tab;          // offset of the size table
-  const uint64_t* boff; // per block payload offset (nblocks)
+  const uint64_t* boff; // payload offsets: of block b at boff[b * boff_stride]
+  int64_t boff_stride;  // 1 (block offsets) or nplanes (chunk offsets)
   uint64_t* qt;
   uint8_t* sg;
   double* out;
@@ -1738,7 +1749,7 @@ __global__ void decode_kernel(DecParams D) {
   if (*D.err) return;
   const int64_t lo = b * D.block_size, hi_all = min(D.n, lo + D.block_size);
   for (int64_t j = lo; j < hi_all; ++j) { D.qt[j] = 0; D.sg[j] = 0; }
-  uint64_t pos = D.boff[b];
+  uint64_t pos = D.boff[b * D.boff_stride];
   const uint8_t* ftab = D.sec + kQHdr;
   for (int pi = 0; pi < D.nplanes; ++pi) {
     const int p = 63 - pi;
@@ -1879,7 +1890,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_block_kernel(DecParams D) 
   if (tid == 0) s_err = (*D.err != 0) ? -1 : 0;
   __syncthreads();
   if (s_err) return;
-  uint64_t pos = D.boff[b];
+  uint64_t pos = D.boff[b * D.boff_stride];
   const uint8_t* ftab = D.sec + kQHdr;
   const int64_t j0 = lo + (int64_t)tid * kDecPer;  // this thread's first coefficient
   for (int pi = 0; pi < D.nplanes; ++pi) {
@@ -2058,42 +2069,67 @@ struct RunParams {
   int nplanes;
   int64_t nblocks;
   int block_size;
-  const uint64_t* boff;
+  const uint64_t* coff;  // payload offset of every chunk (nblocks * nplanes + 1)
   uint32_t* runs;  // [chunk][block_size + 2]
   int* nruns;      // [chunk]
   int* err;
 };
 
-__global__ void decode_runs_kernel(RunParams P) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= P.nblocks * P.nplanes) return;
-  const int64_t b = c / P.nplanes;
-  const int pi = (int)(c % P.nplanes);
-  const int cap = P.block_size + 2;
-  // byte offset of this chunk: the block's payload start plus its earlier planes
-  uint64_t pos = P.boff[b];
-  for (int q = 0; q < pi; ++q) {
-    const uint8_t* t = P.sec + P.tab + (b * P.nplanes + q) * 8;
-    pos += (uint64_t)rd32(t) + rd32(t + 4);
+// payload bytes of one (block, plane) chunk from the size table: rANS + raw
+struct TabBytes {
+  const uint8_t* tab;
+  __device__ unsigned long long operator()(int64_t c) const {
+    const uint8_t* e = tab + c * 8;
+    return (unsigned long long)(e[0] | (e[1] << 8) | (e[2] << 16) | ((uint32_t)e[3] << 24)) +
+           (unsigned long long)(e[4] | (e[5] << 8) | (e[6] << 16) | ((uint32_t)e[7] << 24));
   }
-  const uint8_t* t = P.sec + P.tab + (b * P.nplanes + pi) * 8;
+};
+
+// Phase A: the runs of every chunk.  CTA (x, pi) takes plane pi of blocks
+// [x * kRunThreads, (x + 1) * kRunThreads), a thread per chunk, so that the
+// plane's slot -> symbol table (the 2^12 slots of its frequency table) sits in
+// shared memory and a symbol costs one table read instead of a search.
+constexpr int kRunThreads = 128;
+__global__ void __launch_bounds__(kRunThreads) decode_runs_kernel(RunParams P) {
+  __shared__ uint8_t lut[kM];
+  __shared__ uint32_t s_f[kNsym], s_c[kNsym];
+  __shared__ int s_single;
+  const int pi = blockIdx.y;
+  const uint8_t* ftab = P.sec + kQHdr + 2 * pi * kNsym;
+  if (threadIdx.x == 0) {
+    uint32_t ca = 0;
+    int single = -1;
+    for (int i = 0; i < kNsym; ++i) {
+      const uint32_t f = (uint32_t)ftab[2 * i] | ((uint32_t)ftab[2 * i + 1] << 8);
+      s_f[i] = f;
+      s_c[i] = ca;
+      ca += f;
+      if (f == kM) single = i;
+    }
+    s_single = single;
+  }
+  __syncthreads();
+  // slot -> the symbol whose interval [cum, cum + f) holds it (0xff: none)
+  for (int sl = threadIdx.x; sl < (int)kM; sl += blockDim.x) {
+    int sb = 0xff;
+#pragma unroll
+    for (int i = 0; i < kNsym; ++i)
+      if (s_f[i] && (uint32_t)sl >= s_c[i] && (uint32_t)sl < s_c[i] + s_f[i]) sb = i;
+    lut[sl] = (uint8_t)sb;
+  }
+  __syncthreads();
+  const int64_t b = blockIdx.x * (int64_t)kRunThreads + threadIdx.x;
+  if (b >= P.nblocks) return;
+  const int64_t c = b * P.nplanes + pi;
+  const int cap = P.block_size + 2;
+  const uint64_t pos = P.coff[c];
+  const uint8_t* t = P.sec + P.tab + c * 8;
   const uint32_t rl = rd32(t), wl = rd32(t + 4);
   int* nr = P.nruns + c;
   if (pos + rl + wl > (uint64_t)P.nbytes) { atomicExch(P.err, 2); *nr = 0; return; }
   if (rl == 0) { *nr = 0; return; }
   if (rl < 4) { atomicExch(P.err, 3); *nr = 0; return; }
-  const uint8_t* ftab = P.sec + kQHdr + 2 * pi * kNsym;
-  uint32_t f[kNsym], cum[kNsym];
-  uint32_t ca = 0;
-  int single = -1;
-#pragma unroll
-  for (int i = 0; i < kNsym; ++i) {
-    f[i] = (uint32_t)ftab[2 * i] | ((uint32_t)ftab[2 * i + 1] << 8);
-    cum[i] = ca;
-    ca += f[i];
-    if (f[i] == kM) single = i;
-  }
-  if (single == 0) { *nr = kRunsImplicit; return; }
+  if (s_single == 0) { *nr = kRunsImplicit; return; }
   const uint8_t* rp = P.sec + pos;
   const uint8_t* rend = rp + rl;
   uint32_t x = rd32(rp);
@@ -2102,13 +2138,9 @@ __global__ void decode_runs_kernel(RunParams P) {
   int k = 0;
   while (!(x == kRansL && rp == rend)) {
     const uint32_t slot = x & (kM - 1);
-    uint32_t fs = 0, cs = 0;
-    int sb = -1;
-#pragma unroll
-    for (int i = 0; i < kNsym; ++i)
-      if (f[i] && slot >= cum[i] && slot < cum[i] + f[i]) { fs = f[i]; cs = cum[i]; sb = i; }
-    if (sb < 0) { atomicExch(P.err, 6); break; }
-    x = fs * (x >> kScaleBits) + slot - cs;
+    const int sb = lut[slot];
+    if (sb == 0xff) { atomicExch(P.err, 6); break; }
+    x = s_f[sb] * (x >> kScaleBits) + slot - s_c[sb];
     bool bad = false;
     while (x < kRansL) { if (rp >= rend) { bad = true; break; } x = (x << 8) | *rp++; }
     if (bad) { atomicExch(P.err, 7); break; }
@@ -2146,7 +2178,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_place_kernel(DecParams D, 
   const int cap = D.block_size + 2;
   if (tid == 0) s_err = (*D.err != 0) ? -1 : 0;
   // size table, run counts and payload offsets of the block's planes
-  const uint64_t base = D.boff[b];
+  const uint64_t base = D.boff[b * D.boff_stride];
   if (tid < 32) {
     uint64_t acc = 0;
     for (int p0 = 0; p0 < D.nplanes; p0 += 32) {
@@ -2332,7 +2364,7 @@ __global__ void __launch_bounds__(32 * kWDecWarps) decode_place_warp_kernel(DecP
   err = __reduce_max_sync(0xffffffffu, err);
   if (err) return;
   // size table entries, run counts and payload offsets of this block's planes
-  const uint64_t base = D.boff[b];
+  const uint64_t base = D.boff[b * D.boff_stride];
   uint64_t acc = 0;
   for (int p0 = 0; p0 < D.nplanes; p0 += 32) {
     const int pi = p0 + lane;
@@ -2876,25 +2908,34 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
   ATC_TRY(Scratch::get(SLOT_Q, sizeof(uint64_t) * n, (void**)&qt));
   ATC_TRY(Scratch::get(SLOT_QS, (size_t)n, (void**)&sg));
   uint8_t* small = nullptr;
-  ATC_TRY(Scratch::get(SLOT_ENC, sizeof(uint64_t) * (D.nblocks + 1) + 64, (void**)&small));
+  const int64_t nchunk = D.nblocks * D.nplanes;
+  const bool run_path = D.block_size <= kDecMax && D.nplanes > 0;
+  const int64_t noff = run_path ? nchunk : D.nblocks;
+  ATC_TRY(Scratch::get(SLOT_ENC, sizeof(uint64_t) * (noff + 1) + 64, (void**)&small));
   int* err = reinterpret_cast<int*>(small);
   uint64_t* boff = reinterpret_cast<uint64_t*>(small + 64);
   ATC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   D.sec = dsec; D.qt = qt; D.sg = sg; D.out = core; D.err = err; D.boff = boff;
   {
-    // payload offset of every block (the sizes of its chunks from the size table)
+    // payload offset of every chunk (run path) or block, from the size table
     unsigned long long* sc = nullptr;
-    ATC_TRY(Scratch::get(SLOT_SCAN, sizeof(unsigned long long) * (range_scan_parts(D.nblocks) + 8), (void**)&sc));
-    BlockBytes f{dsec + D.tab, D.nplanes};
+    ATC_TRY(Scratch::get(SLOT_SCAN, sizeof(unsigned long long) * (range_scan_parts(noff) + 8), (void**)&sc));
     const unsigned long long base = (unsigned long long)D.tab + (unsigned long long)D.nblocks * D.nplanes * 8;
-    ATC_TRY(range_scan(f, D.nblocks, base, sc, boff, (unsigned long long)D.nbytes, err, s));
+    if (run_path) {
+      TabBytes f{dsec + D.tab};
+      ATC_TRY(range_scan(f, nchunk, base, sc, boff, (unsigned long long)D.nbytes, err, s));
+      D.boff_stride = D.nplanes;
+    } else {
+      BlockBytes f{dsec + D.tab, D.nplanes};
+      ATC_TRY(range_scan(f, D.nblocks, base, sc, boff, (unsigned long long)D.nbytes, err, s));
+      D.boff_stride = 1;
+    }
   }
-  if (D.block_size <= kDecMax && D.nplanes > 0) {
+  if (run_path) {
     // phase A: every (block, plane) chunk's runs in parallel; phase B: placement
     RunParams RP;
     RP.sec = dsec; RP.nbytes = D.nbytes; RP.tab = D.tab; RP.nplanes = D.nplanes; RP.nblocks = D.nblocks;
-    RP.block_size = D.block_size; RP.boff = boff; RP.err = err;
-    const int64_t nchunk = D.nblocks * D.nplanes;
+    RP.block_size = D.block_size; RP.coff = boff; RP.err = err;
     uint8_t* rbuf = nullptr;
     ATC_TRY(Scratch::get(SLOT_DEC_RUNS, sizeof(uint32_t) * (size_t)nchunk * (D.block_size + 2) +
                                             sizeof(int) * (size_t)nchunk + 256, (void**)&rbuf));
@@ -2902,7 +2943,8 @@ int decode_dequantize(const uint8_t* bytes, size_t nbytes, double* core, int64_t
     RP.nruns = reinterpret_cast<int*>(rbuf + sizeof(uint32_t) * (size_t)nchunk * (D.block_size + 2));
     {
       KTimed kt_(s, "decode_runs_kernel");
-      decode_runs_kernel<<<(unsigned)((nchunk + 63) / 64), 64, 0, s>>>(RP);
+      decode_runs_kernel<<<dim3((unsigned)((D.nblocks + kRunThreads - 1) / kRunThreads), (unsigned)D.nplanes),
+                           kRunThreads, 0, s>>>(RP);
     }
     if (D.block_size <= kWDecMax) {
       KTimed kt_(s, "decode_place_warp_kernel");
