@@ -2231,13 +2231,11 @@ __global__ void __launch_bounds__(kDecThreads) decode_place_kernel(DecParams D, 
     const uint32_t sigm = sigall & lowt, insm = ~sigall & lowl;
     const int nr = s_nr[pi];
     const uint32_t* rr = runs + (b * D.nplanes + pi) * (int64_t)cap;
-    uint32_t rv[kRunPer];
+    // this thread's runs k0 .. k0 + kend - 1 (read twice from L1/L2: a loop over
+    // only the runs there are, instead of kRunPer predicated slots)
+    const int kend = (nr == kRunsImplicit) ? 0 : max(0, min(kRunPer, nr - k0));
     int64_t loc = 0;
-#pragma unroll
-    for (int u = 0; u < kRunPer; ++u) {
-      rv[u] = (nr != kRunsImplicit && k0 + u < nr) ? __ldg(rr + k0 + u) : 0u;
-      if (nr != kRunsImplicit && k0 + u < nr) loc += (int64_t)rv[u] + 1;
-    }
+    for (int u = 0; u < kend; ++u) loc += (int64_t)__ldg(rr + k0 + u) + 1;
     // one scan: (insignificant active count) << 32 | (run-list position)
     int64_t tot = 0;
     const int64_t ex = dec_scan(((int64_t)__popc(insm) << 32) | loc, scan_sh, &tot);
@@ -2246,15 +2244,13 @@ __global__ void __launch_bounds__(kDecThreads) decode_place_kernel(DecParams D, 
     if (nr == kRunsImplicit) {
       for (int64_t r = tid; r < n_insig; r += kDecThreads) atomicOr(&newbm[r >> 5], 1u << (r & 31));
     } else {
-#pragma unroll
-      for (int u = 0; u < kRunPer; ++u) {
+      for (int u = 0; u < kend; ++u) {
         const int k = k0 + u;
-        if (k < nr) {
-          const int64_t at = q + rv[u];  // rank of this run's 1
-          if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rv[u] + 1)) s_err = 11;  // symbol count
-          if (at < n_insig) atomicOr(&newbm[at >> 5], 1u << (at & 31));
-          q += (int64_t)rv[u] + 1;
-        }
+        const uint32_t rv = __ldg(rr + k);
+        const int64_t at = q + rv;  // rank of this run's 1
+        if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rv + 1)) s_err = 11;  // symbol count
+        if (at < n_insig) atomicOr(&newbm[at >> 5], 1u << (at & 31));
+        q += (int64_t)rv + 1;
       }
       if (tid == 0 && nr == 0 && n_insig > 0) s_err = 5;
     }
@@ -2412,14 +2408,10 @@ __global__ void __launch_bounds__(32 * kWDecWarps) decode_place_warp_kernel(DecP
     const uint32_t sigm = sigall & lowt, insm = ~sigall & lowl;
     const int nr = nrp[pi];
     const uint32_t* rr = runs + (b * D.nplanes + pi) * (int64_t)cap;
-    uint32_t rv[kRunPerW];
+    // this lane's runs k0 .. k0 + kend - 1 (a loop over only the runs there are)
+    const int kend = (nr == kRunsImplicit) ? 0 : max(0, min(kRunPerW, nr - k0));
     int64_t loc = 0;
-#pragma unroll
-    for (int u = 0; u < kRunPerW; ++u) {
-      const bool has = nr != kRunsImplicit && k0 + u < nr;
-      rv[u] = has ? __ldg(rr + k0 + u) : 0u;
-      if (has) loc += (int64_t)rv[u] + 1;
-    }
+    for (int u = 0; u < kend; ++u) loc += (int64_t)__ldg(rr + k0 + u) + 1;
     int64_t tot = 0;
     const int64_t ex = warp_exscan64(((int64_t)__popc(insm) << 32) | loc, &tot);
     const int64_t rank0 = ex >> 32, n_insig = tot >> 32;
@@ -2428,15 +2420,13 @@ __global__ void __launch_bounds__(32 * kWDecWarps) decode_place_warp_kernel(DecP
     if (nr == kRunsImplicit) {
       for (int64_t r = lane; r < n_insig; r += 32) atomicOr(&newbm[r >> 5], 1u << (r & 31));
     } else {
-#pragma unroll
-      for (int u = 0; u < kRunPerW; ++u) {
+      for (int u = 0; u < kend; ++u) {
         const int k = k0 + u;
-        if (k < nr) {
-          const int64_t at = q + rv[u];  // rank of this run's 1
-          if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rv[u] + 1)) err = 11;  // symbol count
-          if (at < n_insig) atomicOr(&newbm[at >> 5], 1u << (at & 31));
-          q += (int64_t)rv[u] + 1;
-        }
+        const uint32_t rv = __ldg(rr + k);
+        const int64_t at = q + rv;  // rank of this run's 1
+        if (k == nr - 1 && !(q < n_insig && n_insig <= q + (int64_t)rv + 1)) err = 11;  // symbol count
+        if (at < n_insig) atomicOr(&newbm[at >> 5], 1u << (at & 31));
+        q += (int64_t)rv + 1;
       }
       if (nr == 0 && n_insig > 0) err = 5;
     }
