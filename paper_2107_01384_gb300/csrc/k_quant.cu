@@ -1232,6 +1232,7 @@ __global__ void __launch_bounds__(kEncBlockThreads) enc_block_kernel(BlockEncPar
   unsigned long long* qs = reinterpret_cast<unsigned long long*>(enc_dyn);
   uint8_t* ss = enc_dyn + 8 * (size_t)P.block_size;
   signed char* ms = reinterpret_cast<signed char*>(ss + P.block_size);  // leading-bit position, -1 for zero
+  signed char* gmax = ms + P.block_size;  // per group of 32: the largest leading-bit position
   __shared__ uint32_t s_cnt[65], s_hpos[65];  // per leading-bit position m + 1: count, last index + 1
   __shared__ uint32_t s_pre[66], s_low[64];   // exclusive prefix sums of s_cnt; prefix maxima of s_hpos
   __shared__ uint32_t s_lastones[2], s_lastlow[2], s_cnt_last[2];  // last plane: [leading 1s/last 1, ...]
@@ -1263,6 +1264,8 @@ __global__ void __launch_bounds__(kEncBlockThreads) enc_block_kernel(BlockEncPar
       }
       // whole planes: a histogram over the leading-bit positions, one atomic pair
       // per distinct position in the warp (count, last index + 1)
+      const int gm = __reduce_max_sync(0xffffffffu, m + 2) - 2;  // -2: no coefficient
+      if (lane == 0 && g + 32 * warp < len) gmax[(g >> 5) + warp] = (signed char)gm;
       const unsigned peers = __match_any_sync(0xffffffffu, m);
       if (valid && lane == __ffs(peers) - 1) {
         atomicAdd(&s_cnt[m + 1], (uint32_t)__popc(peers));
@@ -1381,6 +1384,12 @@ __global__ void __launch_bounds__(kEncBlockThreads) enc_block_kernel(BlockEncPar
       uint64_t acc = 0;
       int nacc = 0;
       for (int g = 0; g < clen; g += 32) {
+        if (gmax[g >> 5] < p) {
+          // every coefficient of the group is zero through plane p: leading zeros
+          // only (no run ends here, no raw bit)
+          carry += (uint32_t)max(0, min(32, cl - g));
+          continue;
+        }
         const int i = g + lane;
         const int m = (i < clen) ? ms[i] : -1;
         const bool sig_in = i < ct && m > p;          // an encoded trailing bit
@@ -2667,7 +2676,7 @@ int quantize_encode(const double* core, int64_t n, double target, int block_size
         enc_cost_plane_kernel<<<(unsigned)(ctas < waves ? ctas : waves), kEncBlockThreads, 0, s>>>(B);
       } else {
         KTimed kt_(s, "enc_block_kernel", (double)n * 9.0 + (double)nblocks * (double)B.run_slot * 4.0 * np / nplanes);
-        const size_t dyn = (size_t)10 * B.block_size;
+        const size_t dyn = (size_t)10 * B.block_size + B.block_size / 32;
         enc_block_kernel<<<(unsigned)(nblocks < waves ? nblocks : waves), kEncBlockThreads, dyn, s>>>(B);
       }
       ATC_LAUNCHED(1);
