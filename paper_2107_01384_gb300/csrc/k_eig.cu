@@ -861,34 +861,44 @@ __global__ void __launch_bounds__(256) cholqr_group_kernel(EigState st, const in
 // The same CholQR2 of one block of a large group spread over the GPU (the
 // block Gram-Schmidt of a large cluster runs its blocks in turn, so a one-CTA
 // block leaves the other SMs idle through a long FP64 chain): W = Z^T Z by
-// blk_dot_kernel (a warp per entry), the Cholesky factor by one warp
+// blk_dot_kernel (a warp per entry), the Cholesky factor by one CTA
 // (cholqr_chol_kernel), Z <- Z R^-1 a thread per row (cholqr_trsm_kernel).
 // Every value is formed as in cholqr_block, in the same order.
-__global__ void __launch_bounds__(32) cholqr_chol_kernel(const double* __restrict__ Wg, int g, double* __restrict__ Rg) {
+constexpr int kCholThreads = 256;
+__global__ void __launch_bounds__(kCholThreads) cholqr_chol_kernel(const double* __restrict__ Wg, int g,
+                                                                  double* __restrict__ Rg) {
+  // right-looking: every entry takes its updates in the order k = 0, 1, ...
+  // with the same expressions as cholqr_block (the threads of the CTA share
+  // the trailing update of each step)
   __shared__ double W[kQrMax * kQrMax];
-  const int lane = threadIdx.x;
-  for (int e = lane; e < g * g; e += 32) W[(e / g) * kQrMax + (e % g)] = Wg[e];
-  __syncwarp();
+  const int tid = threadIdx.x;
+  for (int e = tid; e < g * g; e += kCholThreads) W[(e / g) * kQrMax + (e % g)] = Wg[e];
+  __syncthreads();
   for (int k = 0; k < g; ++k) {
     const double dkk = sqrt(fmax(W[k * kQrMax + k], 1e-300));
     const double inv = 1.0 / dkk;
-    __syncwarp();
-    for (int c = k + 1 + lane; c < g; c += 32) W[k * kQrMax + c] *= inv;
-    if (lane == 0) W[k * kQrMax + k] = dkk;
-    __syncwarp();
-    for (int e = lane; e < (g - k - 1) * (g - k - 1); e += 32) {
-      const int a = k + 1 + e / (g - k - 1), c = k + 1 + e % (g - k - 1);
+    __syncthreads();
+    for (int c = k + 1 + tid; c < g; c += kCholThreads) W[k * kQrMax + c] *= inv;
+    if (tid == 0) W[k * kQrMax + k] = dkk;
+    __syncthreads();
+    const int m = g - k - 1;
+    for (int e = tid; e < m * m; e += kCholThreads) {
+      const int a = k + 1 + e / m, c = k + 1 + e % m;
       if (c >= a) W[a * kQrMax + c] -= W[k * kQrMax + a] * W[k * kQrMax + c];
     }
-    __syncwarp();
+    __syncthreads();
   }
-  for (int e = lane; e < kQrMax * kQrMax; e += 32) Rg[e] = W[e];
+  for (int e = tid; e < kQrMax * kQrMax; e += kCholThreads) Rg[e] = W[e];
 }
-constexpr int kTrsmThreads = 8;  // rows per CTA: the rows spread over the SMs (FP64 is slow per SM)
+constexpr int kTrsmThreads = 32;  // rows per CTA (a warp; the FP64 chain of a row sets the time)
 __global__ void __launch_bounds__(kTrsmThreads) cholqr_trsm_kernel(double* __restrict__ Z, int g, int n,
                                                                     const double* __restrict__ Rg) {
   __shared__ double R[kQrMax * kQrMax];
-  for (int e = threadIdx.x; e < kQrMax * kQrMax; e += blockDim.x) R[e] = Rg[e];
+  // the upper triangle of the g x g factor is all the solve reads
+  for (int e = threadIdx.x; e < g * g; e += blockDim.x) {
+    const int c = e / g, d = e - c * g;
+    if (d >= c) R[c * kQrMax + d] = Rg[c * kQrMax + d];
+  }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -1506,7 +1516,10 @@ int launch_eig_values_impl(const double* g, int n, cudaStream_t s, bool use_dd =
     if (P > 128) P = 128;
     if (P < 1) P = 1;
     void* args[] = {(void*)&st};
-    ATC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tridiag_kernel, dim3(P), dim3(kTriThreads), args, smem, s));
+    {
+      KTimed kt_(s, "tridiag_kernel");
+      ATC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tridiag_kernel, dim3(P), dim3(kTriThreads), args, smem, s));
+    }
     __atomic_add_fetch(&g_kernel_launches, 1, __ATOMIC_RELAXED);
   }
   scale_kernel<<<1, 256, 0, s>>>(st);
@@ -1528,8 +1541,11 @@ int launch_eig_more(int n, int K, double* lam, cudaStream_t s) {
   if (g_state.n != n) return fail(ATC_EINVAL, "eigenvalues requested without a tridiagonal matrix");
   if (K > n) K = n;
   EigState st = g_state;
-  if (g_state_dd) msect_dd_kernel<<<K, kMsThreads, sizeof(dd) * 2 * n, s>>>(st, K);
-  else msect_kernel<<<K, kMsThreads, sizeof(double) * 2 * n, s>>>(st, K);
+  {
+    KTimed kt_(s, "msect_kernel");
+    if (g_state_dd) msect_dd_kernel<<<K, kMsThreads, sizeof(dd) * 2 * n, s>>>(st, K);
+    else msect_kernel<<<K, kMsThreads, sizeof(double) * 2 * n, s>>>(st, K);
+  }
   ATC_LAUNCHED(1);
   if (lam) {
     unscale_kernel<<<(K + 255) / 256, 256, 0, s>>>(st, lam, K);
@@ -1559,11 +1575,14 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
   ATC_LAUNCHED(1);
   std::vector<int> hg((size_t)nvec + 2);
   ATC_CUDA_TRY(cudaMemcpyAsync(hg.data(), grp, sizeof(int) * (nvec + 2), cudaMemcpyDeviceToHost, s));
-  if (g_state_dd) invit_dd_kernel<<<nvec, 32, (sizeof(dd) * 5 + 1) * n, s>>>(st, nvec);
-  else invit_par_kernel<<<nvec, 32, sizeof(double) * 6 * n, s>>>(st, nvec);
+  {
+    KTimed kt_(s, "invit_kernel");
+    if (g_state_dd) invit_dd_kernel<<<nvec, 32, (sizeof(dd) * 5 + 1) * n, s>>>(st, nvec);
+    else invit_par_kernel<<<nvec, 32, sizeof(double) * 6 * n, s>>>(st, nvec);
+  }
   ATC_LAUNCHED(1);
   // CholQR2 for the groups of <= kQrMax vectors (one CTA each) ...
-  cholqr_group_kernel<<<nvec, 256, 0, s>>>(st, grp, ngrp, kQrMax);
+  { KTimed kt_(s, "cholqr_group_kernel"); cholqr_group_kernel<<<nvec, 256, 0, s>>>(st, grp, ngrp, kQrMax); }
   ATC_LAUNCHED(1);
   // ... and block Gram-Schmidt (two passes) + CholQR2 per block for the larger ones
   int hn = 0;
@@ -1579,30 +1598,36 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
       const int nb = std::min(kQrMax, g1 - k0), np = k0 - g0;
       for (int pass = 0; pass < 2; ++pass) {
         if (np > 0) {
-          blk_dot_kernel<<<(np * nb + 7) / 8, 256, 0, s>>>(st.z, n, g0, np, k0, nb, W);
-          blk_update_kernel<<<(int)(((int64_t)nb * n + 255) / 256), 256, 0, s>>>(st.z, n, g0, np, k0, nb, W);
+          { KTimed kt_(s, "blk_dot_kernel"); blk_dot_kernel<<<(np * nb + 7) / 8, 256, 0, s>>>(st.z, n, g0, np, k0, nb, W); }
+          { KTimed kt_(s, "blk_update_kernel"); blk_update_kernel<<<(int)(((int64_t)nb * n + 255) / 256), 256, 0, s>>>(st.z, n, g0, np, k0, nb, W); }
           ATC_LAUNCHED(2);
         }
         // CholQR2 of the block across the GPU (two passes, as cholqr_block)
         for (int cq = 0; cq < 2; ++cq) {
-          blk_dot_kernel<<<(nb * nb + 7) / 8, 256, 0, s>>>(st.z, n, k0, nb, k0, nb, Wq);
-          cholqr_chol_kernel<<<1, 32, 0, s>>>(Wq, nb, Rq);
-          cholqr_trsm_kernel<<<(n + kTrsmThreads - 1) / kTrsmThreads, kTrsmThreads, 0, s>>>(
-              st.z + (int64_t)k0 * n, nb, n, Rq);
+          { KTimed kt_(s, "blk_dot_kernel"); blk_dot_kernel<<<(nb * nb + 7) / 8, 256, 0, s>>>(st.z, n, k0, nb, k0, nb, Wq); }
+          { KTimed kt_(s, "cholqr_chol_kernel"); cholqr_chol_kernel<<<1, kCholThreads, 0, s>>>(Wq, nb, Rq); }
+          {
+            KTimed kt_(s, "cholqr_trsm_kernel");
+            cholqr_trsm_kernel<<<(n + kTrsmThreads - 1) / kTrsmThreads, kTrsmThreads, 0, s>>>(
+                st.z + (int64_t)k0 * n, nb, n, Rq);
+          }
           ATC_LAUNCHED(3);
         }
       }
     }
   }
-  if (g_state_dd) {
-    if (n <= 256) backtransform_dd_kernel<8><<<nvec, 32, 0, s>>>(st, nvec, v);
-    else backtransform_dd_kernel<16><<<nvec, 32, 0, s>>>(st, nvec, v);
-  } else if (n <= 256) {
-    backtransform_kernel<8><<<nvec, 32, 0, s>>>(st, nvec, v);
-  } else if (n <= 512) {
-    backtransform_kernel<16><<<nvec, 32, 0, s>>>(st, nvec, v);
-  } else {
-    backtransform_kernel<32><<<nvec, 32, 0, s>>>(st, nvec, v);
+  {
+    KTimed kt_(s, "backtransform_kernel");
+    if (g_state_dd) {
+      if (n <= 256) backtransform_dd_kernel<8><<<nvec, 32, 0, s>>>(st, nvec, v);
+      else backtransform_dd_kernel<16><<<nvec, 32, 0, s>>>(st, nvec, v);
+    } else if (n <= 256) {
+      backtransform_kernel<8><<<nvec, 32, 0, s>>>(st, nvec, v);
+    } else if (n <= 512) {
+      backtransform_kernel<16><<<nvec, 32, 0, s>>>(st, nvec, v);
+    } else {
+      backtransform_kernel<32><<<nvec, 32, 0, s>>>(st, nvec, v);
+    }
   }
   ATC_LAUNCHED(1);
   return ATC_OK;
