@@ -862,7 +862,7 @@ __global__ void __launch_bounds__(256) cholqr_group_kernel(EigState st, const in
 // block Gram-Schmidt of a large cluster runs its blocks in turn, so a one-CTA
 // block leaves the other SMs idle through a long FP64 chain): W = Z^T Z by
 // blk_dot_kernel (a warp per entry), the Cholesky factor by one CTA
-// (cholqr_chol_kernel), Z <- Z R^-1 a thread per row (cholqr_trsm_kernel).
+// (cholqr_chol_kernel), Z <- Z R^-1 a warp per row (cholqr_trsm_kernel).
 // Every value is formed as in cholqr_block, in the same order.
 constexpr int kCholThreads = 256;
 __global__ void __launch_bounds__(kCholThreads) cholqr_chol_kernel(const double* __restrict__ Wg, int g,
@@ -890,9 +890,9 @@ __global__ void __launch_bounds__(kCholThreads) cholqr_chol_kernel(const double*
   }
   for (int e = tid; e < kQrMax * kQrMax; e += kCholThreads) Rg[e] = W[e];
 }
-constexpr int kTrsmThreads = 32;  // rows per CTA (a warp; the FP64 chain of a row sets the time)
-__global__ void __launch_bounds__(kTrsmThreads) cholqr_trsm_kernel(double* __restrict__ Z, int g, int n,
-                                                                    const double* __restrict__ Rg) {
+constexpr int kTrsmWarps = 8;  // rows per CTA: a warp per row, a lane per column (two when g > 32)
+__global__ void __launch_bounds__(32 * kTrsmWarps) cholqr_trsm_kernel(double* __restrict__ Z, int g, int n,
+                                                                       const double* __restrict__ Rg) {
   __shared__ double R[kQrMax * kQrMax];
   // the upper triangle of the g x g factor is all the solve reads
   for (int e = threadIdx.x; e < g * g; e += blockDim.x) {
@@ -900,25 +900,27 @@ __global__ void __launch_bounds__(kTrsmThreads) cholqr_trsm_kernel(double* __res
     if (d >= c) R[c * kQrMax + d] = Rg[c * kQrMax + d];
   }
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kTrsmWarps + (threadIdx.x >> 5);
   if (i >= n) return;
-  // forward substitution y R = z, right-looking (for each y_d the terms are
-  // subtracted in the order a = 0, 1, ..., as in cholqr_block)
-  double y[kQrMax];
-#pragma unroll
-  for (int c = 0; c < kQrMax; ++c) y[c] = (c < g) ? Z[(int64_t)c * n + i] : 0.0;
-#pragma unroll
-  for (int c = 0; c < kQrMax; ++c) {
-    if (c < g) {
-      y[c] = y[c] / R[c * kQrMax + c];
-#pragma unroll
-      for (int d = c + 1; d < kQrMax; ++d)
-        if (d < g) y[d] -= y[c] * R[c * kQrMax + d];
+  // forward substitution y R = z for row i, right-looking: pivot c divides
+  // y_c (its lane), broadcasts it, and every later y_d takes its term; for each
+  // y_d the terms are subtracted in the order c = 0, 1, ..., as in cholqr_block
+  const int d0 = lane, d1 = lane + 32;
+  double y0 = (d0 < g) ? Z[(int64_t)d0 * n + i] : 0.0;
+  double y1 = (d1 < g) ? Z[(int64_t)d1 * n + i] : 0.0;
+  for (int c = 0; c < g; ++c) {
+    const bool lo = c < 32;
+    if (lane == (c & 31)) {
+      if (lo) y0 = y0 / R[c * kQrMax + c];
+      else y1 = y1 / R[c * kQrMax + c];
     }
+    const double yc = __shfl_sync(0xffffffffu, lo ? y0 : y1, c & 31);
+    if (d0 > c && d0 < g) y0 -= yc * R[c * kQrMax + d0];
+    if (d1 > c && d1 < g) y1 -= yc * R[c * kQrMax + d1];
   }
-#pragma unroll
-  for (int c = 0; c < kQrMax; ++c)
-    if (c < g) Z[(int64_t)c * n + i] = y[c];
+  if (d0 < g) Z[(int64_t)d0 * n + i] = y0;
+  if (d1 < g) Z[(int64_t)d1 * n + i] = y1;
 }
 
 // Block Gram-Schmidt step against the earlier vectors g0 .. g0+np-1 of a group:
@@ -1608,7 +1610,7 @@ int launch_eig_vectors(int n, int nvec, double* v, cudaStream_t s) {
           { KTimed kt_(s, "cholqr_chol_kernel"); cholqr_chol_kernel<<<1, kCholThreads, 0, s>>>(Wq, nb, Rq); }
           {
             KTimed kt_(s, "cholqr_trsm_kernel");
-            cholqr_trsm_kernel<<<(n + kTrsmThreads - 1) / kTrsmThreads, kTrsmThreads, 0, s>>>(
+            cholqr_trsm_kernel<<<(n + kTrsmWarps - 1) / kTrsmWarps, 32 * kTrsmWarps, 0, s>>>(
                 st.z + (int64_t)k0 * n, nb, n, Rq);
           }
           ATC_LAUNCHED(3);
