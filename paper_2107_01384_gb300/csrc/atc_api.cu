@@ -991,11 +991,17 @@ int atc_compress(const void* x_dev, const int64_t* dims, int ndim, int dtype, do
   for (int i = 0; i < d; ++i) perm[i] = i;
   std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return c->ranks[a] < c->ranks[b]; });
   for (int i = 0; i < d; ++i) st.storage_order[i] = perm[i];
-  double* vec = nullptr;
-  rc = Scratch::get(SLOT_CORE, sizeof(double) * (size_t)ncore, (void**)&vec);
-  if (rc) return bail(rc);
-  rc = launch_permute(c->core, c->ranks, perm.data(), d, vec, 0, s);
-  if (rc) return bail(rc);
+  bool ident = true;
+  for (int i = 0; i < d; ++i) ident = ident && perm[i] == i;
+  // the vectorised core: the core itself when the storage order keeps the mode
+  // order (the quantizer only reads it), else its permuted copy
+  double* vec = c->core;
+  if (!ident) {
+    rc = Scratch::get(SLOT_CORE, sizeof(double) * (size_t)ncore, (void**)&vec);
+    if (rc) return bail(rc);
+    rc = launch_permute(c->core, c->ranks, perm.data(), d, vec, 0, s);
+    if (rc) return bail(rc);
+  }
   QuantSection section;
   QuantResult qr;
   float msq = 0.f, mse = 0.f;

@@ -263,6 +263,13 @@ int launch_permute(const double* x, const int64_t* dims, const int* perm, int nd
   int64_t total = 1;
   for (int i = 0; i < ndim; ++i) total *= dims[i];
   if (total == 0) return ATC_OK;
+  bool ident = true;
+  for (int i = 0; i < ndim; ++i) ident = ident && perm[i] == i;
+  if (ident) {
+    // the identity (equal ranks keep the mode order): a plain device copy
+    ATC_CUDA_TRY(cudaMemcpyAsync(y, x, sizeof(double) * (size_t)total, cudaMemcpyDeviceToDevice, s));
+    return ATC_OK;
+  }
   // permuted dims: pdims[i] = dims[perm[i]]
   int64_t pdims[8], pstride[8], ostride[8];
   for (int i = 0; i < ndim; ++i) pdims[i] = dims[perm[i]];
