@@ -1192,10 +1192,14 @@ __global__ void __launch_bounds__(32 * kEncWarps) enc_rans_kernel(EncParams P, i
 // follows the plane's last leading 1), hence the offsets of every (block,
 // plane) chunk inside the block's run and raw slots; then each warp walks its
 // planes from shared memory (the walk of chunk_walk), writing the runs and the
-// packed raw bits and counting the run symbols per plane.  Pass 2
-// (enc_rans_thread_kernel): one THREAD per chunk runs rANS over the chunk's
-// stored runs -- sizes first, then, after the offset scan, the bytes at their
-// final place together with the chunk's raw bytes and its table entry.
+// packed raw bits and counting the run symbols per plane (a CTA takes blocks
+// in turn; groups of 32 coefficients zero through a plane only add leading
+// zeros to the current run).  Pass 2 (enc_rans_thread_kernel): one THREAD per
+// chunk runs rANS over the chunk's stored runs, writing the bytes in place
+// over them, and records the sizes; after the offset scan a copy pass moves
+// the bytes, the chunk's raw bytes and its table entry to their final place.
+// The split priority's cost pass of plane p* + 1 alone walks a block per warp
+// (enc_cost_plane_kernel).
 constexpr int kEncBlockMax = 4096;
 constexpr int kEncBlockThreads = 256;
 constexpr int kEncBlockResident = 8;  // CTAs per SM of the persistent pass 1
