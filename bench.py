@@ -289,6 +289,9 @@ DD_KERNELS = ("qr_col_kernel", "sub_qr_kernel", "sub_qform_kernel", "rr_jacobi_k
 TRAFFIC = {
     # one 32 x 32 Rayleigh-Ritz per mode, inputs L2-resident: 52.5 KB read, 0 written (mode-0 launch)
     ("rr_jacobi_kernel", "bumps256"): (52480.0, "profiles/rr_jacobi_kernel_bumps256.md (mode-0 launch)"),
+    # averages over one step's launches (three Grams; three projections + three expansions)
+    ("gram_raw_kernel", "bumps256"): (25042603.0, "profiles/gram_ttm_traffic_bumps256.md (mean of the 3 launches)"),
+    ("ttm_tc_kernel", "bumps256"): (17474859.0, "profiles/gram_ttm_traffic_bumps256.md (mean of the 6 launches)"),
 }
 
 
